@@ -1,0 +1,26 @@
+"""Plain, slow FP64 CPU oracle for the PauliNet VMC hot path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path imports, calls or
+executes this package; only the test-suite, the smoke check and the CPU
+baseline leg of the benchmark do.  It shares no code with the CUDA library:
+its one shared input is the seeded generator module
+``paper_1909_08423_gb300.synth``, which holds none of the method's arithmetic.
+
+Modules
+  ansatz      psi of Eq. (ansatz), orbitals with the Ma et al. nuclear cusp
+              splice, the SchNet-style network (Methods, "PauliNet extension
+              of SchNet"), determinants, gamma, Coulomb potential, local
+              energy (Eq. monte-carlo) and the parameter gradient of ln|psi|
+              (Eq. trainig).  Exact derivatives come from torch.autograd in
+              float64 -- a different algorithm from the GPU's forward jet.
+  cusp        host-side coefficients of the nuclear cusp correction.
+  philox      Philox4x32-10 counter-based generator (Salmon et al., SC'11)
+              and Box-Muller normals.
+  sampling    Metropolis walker update and walker initialisation.
+  clip        smooth logarithmic clipping of local energies (Methods,
+              "Ansatz optimization").
+
+Parity status of each function is listed in its docstring; the network's
+interior (filters, messages, heads) is pinned only through invariants,
+cusplessness and finite differences ("parity unpinned" beyond those).
+"""

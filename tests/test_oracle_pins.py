@@ -1,0 +1,391 @@
+"""Pins of the CPU oracle to facts the paper and the mathematics fix.
+
+Each test names what it pins.  None of them retypes an oracle formula: they
+use closed forms, brute force, finite differences, symmetries and limits.
+"""
+
+import itertools
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import clip as oclip
+from oracle import philox, sampling
+from oracle.ansatz import DT, Oracle, features, network, params_to_torch
+from paper_1909_08423_gb300 import synth
+
+RNG = np.random.default_rng(1234)
+
+
+def _pts(W, N, scale=1.5, seed=0):
+    return np.random.default_rng(seed).normal(scale=scale, size=(W, N, 3))
+
+
+# ---------------------------------------------------------------- closed forms
+
+def test_hydrogen_atom_local_energy_is_minus_half():
+    """psi = exp(-r) for the hydrogen atom gives E_loc = -1/2 Ha everywhere."""
+    o = Oracle(synth.hydrogen_like_sto(1.0, 1.0))
+    E, _, _ = o.local_energy(_pts(64, 1))
+    assert np.max(np.abs(E + 0.5)) < 1e-12
+
+
+@pytest.mark.parametrize("Z,zeta", [(1.0, 1.3), (3.0, 2.2), (2.0, 0.6)])
+def test_hydrogen_like_sto_closed_form(Z, zeta):
+    """exp(-zeta r) in a nucleus of charge Z: E_loc = -zeta^2/2 + (zeta - Z)/r."""
+    o = Oracle(synth.hydrogen_like_sto(Z, zeta))
+    r = _pts(64, 1, seed=2)
+    E, _, _ = o.local_energy(r)
+    d = np.linalg.norm(r[:, 0], axis=-1)
+    assert np.max(np.abs(E - (-zeta ** 2 / 2 + (zeta - Z) / d))) < 1e-11
+
+
+@pytest.mark.parametrize("Z,alpha", [(1.0, 0.7), (4.0, 2.5)])
+def test_single_gaussian_closed_form(Z, alpha):
+    """exp(-alpha r^2): lap psi / psi = 4 alpha^2 r^2 - 6 alpha."""
+    o = Oracle(synth.single_gto(Z, alpha))
+    r = _pts(64, 1, seed=3)
+    E, _, _ = o.local_energy(r)
+    d = np.linalg.norm(r[:, 0], axis=-1)
+    assert np.max(np.abs(E - (-0.5 * (4 * alpha ** 2 * d ** 2 - 6 * alpha) - Z / d))) < 1e-10
+
+
+def test_helium_like_product_closed_form():
+    """exp(-zeta (r1 + r2)), 1 up 1 down, gamma off:
+    E_loc = -zeta^2 + (zeta - Z)(1/r1 + 1/r2) + 1/r12."""
+    Z, zeta = 2.0, 1.6875
+    o = Oracle(synth.helium_like_product(Z, zeta))
+    r = _pts(64, 2, seed=4)
+    E, _, _ = o.local_energy(r)
+    r1 = np.linalg.norm(r[:, 0], axis=-1)
+    r2 = np.linalg.norm(r[:, 1], axis=-1)
+    r12 = np.linalg.norm(r[:, 0] - r[:, 1], axis=-1)
+    assert np.max(np.abs(E - (-zeta ** 2 + (zeta - Z) * (1 / r1 + 1 / r2) + 1 / r12))) < 1e-11
+
+
+# ------------------------------------------------------------- determinants
+
+def _leibniz(A):
+    n = A.shape[-1]
+    tot = np.zeros(A.shape[0])
+    for perm in itertools.permutations(range(n)):
+        inv = sum(1 for a in range(n) for b in range(a + 1, n) if perm[a] > perm[b])
+        term = np.ones(A.shape[0])
+        for row, col in enumerate(perm):
+            term = term * A[:, row, col]
+        tot += (-1) ** inv * term
+    return tot
+
+
+@pytest.mark.parametrize("make", [synth.be, synth.h10])
+def test_determinants_match_permutation_sums(make):
+    """Eq. (ansatz) assembled by Leibniz permutation sums (n_sigma <= 5)."""
+    S = make()
+    o = Oracle(S)
+    r = synth.random_walkers(S, 6, 7)
+    c = o.components(r)
+    phit = c["phi"] * c["f"]
+    nu = S["n_up"]
+    tot = np.zeros(len(r))
+    for p in range(len(S["ci"])):
+        du = _leibniz(phit[:, :nu][:, :, S["occ_up"][p]])
+        dd = _leibniz(phit[:, nu:][:, :, S["occ_dn"][p]])
+        tot += S["ci"][p] * du * dd
+    from oracle.ansatz import gamma
+    g = gamma(S, torch.as_tensor(r, dtype=DT)).numpy()
+    psi = np.exp(g + c["J"]) * tot
+    lp, sg = o.eval_logpsi(r)
+    np.testing.assert_allclose(lp, np.log(np.abs(psi)), rtol=0, atol=1e-11)
+    np.testing.assert_array_equal(sg, np.sign(psi))
+
+
+# ---------------------------------------------------- finite differences
+
+@pytest.mark.parametrize("make", [synth.h2, synth.be, synth.h10])
+def test_derivatives_match_central_differences(make):
+    """grad ln|psi| and lap ln|psi| against 4th-order central differences of
+    ln|psi| itself."""
+    S = make()
+    o = Oracle(S)
+    r = synth.random_walkers(S, 3, 11)
+    lp, _, g, lap = o.derivatives(r)
+    h = 1e-3
+    N = r.shape[1]
+    gfd = np.zeros_like(g)
+    lfd = np.zeros(len(r))
+    f0 = o.eval_logpsi(r)[0]
+    for i in range(N):
+        for a in range(3):
+            vals = {}
+            for k in (-2, -1, 1, 2):
+                rr = r.copy()
+                rr[:, i, a] += k * h
+                vals[k] = o.eval_logpsi(rr)[0]
+            gfd[:, i, a] = (vals[-2] - 8 * vals[-1] + 8 * vals[1] - vals[2]) / (12 * h)
+            lfd += (-vals[-2] + 16 * vals[-1] - 30 * f0 + 16 * vals[1] - vals[2]) / (12 * h * h)
+    np.testing.assert_allclose(g, gfd, atol=2e-7 * max(1, np.abs(g).max()))
+    np.testing.assert_allclose(lap, lfd, atol=2e-5 * max(1, np.abs(lap).max()))
+
+
+# ------------------------------------------------------------ symmetries
+
+@pytest.mark.parametrize("make", [synth.be, synth.h10, synth.n2])
+def test_antisymmetry_same_spin_exchange(make):
+    """Eq. (antisymmetry): exchanging two same-spin electrons flips the sign
+    and leaves ln|psi| unchanged."""
+    S = make()
+    o = Oracle(S)
+    r = synth.random_walkers(S, 4, 5)
+    lp, sg = o.eval_logpsi(r)
+    nu = S["n_up"]
+    for (i, j) in ((0, 1), (nu, nu + 1)):
+        rs = r.copy()
+        rs[:, [i, j]] = rs[:, [j, i]]
+        lp2, sg2 = o.eval_logpsi(rs)
+        np.testing.assert_allclose(lp2, lp, atol=1e-11)
+        np.testing.assert_array_equal(sg2, -sg)
+
+
+@pytest.mark.parametrize("make", [synth.be, synth.h10])
+def test_jastrow_invariant_backflow_equivariant(make):
+    """J(P r) = J(r) and f_{mu i}(P r) = f_{mu P(i)}(r) for same-spin
+    permutations; with n_up = n_dn, J is also invariant under exchanging the
+    whole up and down blocks (the channels are relative, not absolute)."""
+    S = make()
+    P = params_to_torch(S)
+    r = torch.as_tensor(synth.random_walkers(S, 4, 9), dtype=DT)
+    J, f = network(S, P, r)
+    nu, N = S["n_up"], S["n_up"] + S["n_dn"]
+    perm = list(range(N))
+    perm[0], perm[nu - 1] = perm[nu - 1], perm[0]
+    perm[nu], perm[N - 1] = perm[N - 1], perm[nu]
+    J2, f2 = network(S, P, r[:, perm])
+    torch.testing.assert_close(J2, J, atol=1e-12, rtol=0)
+    torch.testing.assert_close(f2, f[:, perm], atol=1e-12, rtol=0)
+    flip = list(range(nu, N)) + list(range(nu))
+    J3, f3 = network(S, P, r[:, flip])
+    torch.testing.assert_close(J3, J, atol=1e-12, rtol=0)
+    torch.testing.assert_close(f3, f[:, flip], atol=1e-12, rtol=0)
+
+
+def test_network_rotation_invariant_for_an_atom():
+    """For one nucleus at the origin the network sees distances only, so J
+    and f do not change when all electrons rotate about the nucleus."""
+    S = synth.be()
+    P = params_to_torch(S)
+    r = torch.as_tensor(synth.random_walkers(S, 4, 2), dtype=DT)
+    q, _ = np.linalg.qr(RNG.normal(size=(3, 3)))
+    Q = torch.as_tensor(q, dtype=DT)
+    J, f = network(S, P, r)
+    J2, f2 = network(S, P, r @ Q.T)
+    torch.testing.assert_close(J2, J, atol=1e-12, rtol=0)
+    torch.testing.assert_close(f2, f, atol=1e-12, rtol=0)
+
+
+# ------------------------------------------------------------------- cusps
+
+def _unit_dirs(n, seed):
+    v = np.random.default_rng(seed).normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+@pytest.mark.parametrize("make,I", [(synth.h2, 0), (synth.be, 0), (synth.n2, 1)])
+def test_electron_nucleus_cusp(make, I):
+    """Methods (cusp conditions, Kato): the spherical average of psi around a
+    nucleus has slope -Z_I psi at the nucleus."""
+    S = make()
+    o = Oracle(S)
+    base = synth.random_walkers(S, 1, 3)[0]
+    base[0] = S["R"][I]
+    dirs = _unit_dirs(24, 1)
+    psi0 = np.exp(o.eval_logpsi(base[None])[0][0])
+
+    def avg(h):
+        rs = np.repeat(base[None], 2 * len(dirs), 0)
+        rs[:len(dirs), 0] += h * dirs
+        rs[len(dirs):, 0] -= h * dirs
+        lp, sg = o.eval_logpsi(rs)
+        return np.mean(sg * np.exp(lp)) * np.sign(o.eval_logpsi(base[None])[1][0])
+
+    h = 1e-5
+    slope = (avg(h) / psi0 - 1) / h
+    slope2 = (avg(2 * h) / psi0 - 1) / (2 * h)
+    est = 2 * slope - slope2
+    assert abs(est + S["Z"][I]) < 2e-3 * S["Z"][I]
+
+
+@pytest.mark.parametrize("make", [synth.h2, synth.be])
+def test_electron_electron_cusps(make):
+    """Methods (gamma): opposite spins give a kink of slope 1/2, same spins a
+    relative factor (1 + r/4) on the odd part."""
+    S = make()
+    o = Oracle(S)
+    base = synth.random_walkers(S, 1, 8)[0]
+    nu = S["n_up"]
+    n = _unit_dirs(1, 4)[0]
+
+    def at(i, j, u):
+        r = base.copy()
+        c = 0.5 * (base[i] + base[j])
+        r[i] = c + u / 2
+        r[j] = c - u / 2
+        lp, sg = o.eval_logpsi(r[None])
+        return sg[0] * np.exp(lp[0])
+
+    # opposite spin
+    i, j = 0, nu
+    p0 = at(i, j, np.zeros(3))
+    ests = []
+    for h in (1e-5, 2e-5):
+        ests.append(((at(i, j, h * n) + at(i, j, -h * n)) / 2 / p0 - 1) / h)
+    est = 2 * ests[0] - ests[1]
+    assert abs(est - 0.5) < 1e-3
+    # same spin (needs two up electrons)
+    if nu >= 2:
+        h = 1e-4
+        c1 = (at(0, 1, 2 * h * n) / (2 * at(0, 1, h * n)) - 1) / h
+        c2 = (at(0, 1, 4 * h * n) / (2 * at(0, 1, 2 * h * n)) - 1) / (2 * h)
+        assert abs((2 * c1 - c2) - 0.25) < 1e-3
+
+
+def test_features_vanish_quadratically_at_zero():
+    """e_k(0) = e_k'(0) = 0: e_k(h)/h^2 tends to a finite limit."""
+    S = synth.be()
+    d = torch.tensor([0.0, 1e-4, 2e-4], dtype=DT)
+    e = features(S, d).numpy()
+    assert np.all(e[0] == 0.0)
+    ratio = e[1] / 1e-8, e[2] / 4e-8
+    np.testing.assert_allclose(ratio[0], ratio[1], rtol=1e-3)
+
+
+@pytest.mark.parametrize("kind", ["ee", "en"])
+def test_network_is_cuspless(kind):
+    """Eq. (cuspless): J and f have no kink where an electron meets another
+    electron or a nucleus (antipodal slope -> 0)."""
+    S = synth.be()
+    P = params_to_torch(S)
+    base = torch.as_tensor(synth.random_walkers(S, 1, 6), dtype=DT)
+    n = torch.as_tensor(_unit_dirs(1, 9)[0], dtype=DT)
+
+    def at(u):
+        r = base.clone()
+        if kind == "ee":
+            c = 0.5 * (base[0, 0] + base[0, 2])
+            r[0, 0] = c + u / 2
+            r[0, 2] = c - u / 2
+        else:
+            r[0, 0] = u
+        with torch.no_grad():
+            J, f = network(S, P, r)
+        return J[0].item(), f[0].numpy()
+
+    J0, f0 = at(torch.zeros(3, dtype=DT))
+    h = 1e-4
+    Jp, fp = at(h * n)
+    Jm, fm = at(-h * n)
+    assert abs(((Jp + Jm) / 2 - J0) / h) < 1e-3
+    assert np.max(np.abs(((fp + fm) / 2 - f0) / h)) < 1e-3
+
+
+@pytest.mark.parametrize("make", [synth.h2, synth.be, synth.n2])
+def test_cusp_splice_is_smooth_at_rc(make):
+    """The spliced orbital continues value, slope and curvature across r_c
+    (the three matching conditions of the Ma et al. correction)."""
+    S = make()
+    o = Oracle(S)
+    I = 0
+    rc = o.cusp[I]["rc"]
+    n = _unit_dirs(1, 3)[0]
+    eps = 1e-6
+
+    def phi(rad):
+        p = torch.as_tensor(S["R"][I] + rad * n, dtype=DT).reshape(1, 1, 3)
+        with torch.no_grad():
+            return o.orbitals(p).numpy()[0, 0]
+
+    hs = 1e-3
+    inside = [phi(rc - eps - k * hs) for k in range(3)]
+    outside = [phi(rc + eps + k * hs) for k in range(3)]
+    scale = np.abs(outside[0]).max()
+    np.testing.assert_allclose(inside[0], outside[0], atol=1e-5 * scale)
+    d_in = (inside[0] - inside[1]) / hs
+    d_out = (outside[1] - outside[0]) / hs
+    np.testing.assert_allclose(d_in, d_out, atol=2e-2 * max(1, np.abs(d_out).max()))
+
+
+# ----------------------------------------------------------------- sampling
+
+def test_philox_normals_are_standard_and_reproducible():
+    a = philox.normals(7, np.arange(20000), 3, 12)
+    b = philox.normals(7, np.arange(20000), 3, 12)
+    np.testing.assert_array_equal(a, b)
+    assert abs(a.mean()) < 5e-3 and abs(a.std() - 1) < 5e-3
+    c = philox.normals(8, np.arange(20000), 3, 12)
+    assert abs(np.corrcoef(a.reshape(-1), c.reshape(-1))[0, 1]) < 5e-3
+    u = philox.accept_uniform(7, np.arange(200000), 3, 12)
+    assert 0 < u.min() and u.max() < 1 and abs(u.mean() - 0.5) < 3e-3
+
+
+def test_metropolis_samples_hydrogen_density():
+    """|psi|^2 = exp(-2r) has <r> = 3/2 and <r^2> = 3 (sampling of Eq.
+    monte-carlo); the Gaussian proposal must reproduce them."""
+    S = synth.hydrogen_like_sto(1.0, 1.0)
+    o = Oracle(S)
+    W = 2048
+    r = sampling.init_walkers(S, W, seed=5)
+    lp, _ = o.eval_logpsi(r)
+    r, lp, acc = sampling.metropolis(o, r, lp, 60, 0.5, seed=5, step0=0)
+    rs = []
+    for k in range(8):
+        r, lp, _ = sampling.metropolis(o, r, lp, 10, 0.5, seed=5, step0=60 + 10 * k)
+        rs.append(np.linalg.norm(r[:, 0], axis=-1))
+    rs = np.concatenate(rs)
+    assert abs(rs.mean() - 1.5) < 0.04
+    assert abs((rs ** 2).mean() - 3.0) < 0.15
+
+
+# ----------------------------------------------------------------- clipping
+
+def test_clipping_window_and_smoothness():
+    E = np.concatenate([RNG.normal(-14.6, 0.3, 1000), [50.0, -200.0, 1e4]])
+    out = oclip.clip_local_energy(E)
+    m = np.median(E)
+    L = 5 * np.mean(np.abs(E - m))
+    inside = np.abs(E - m) <= L
+    np.testing.assert_array_equal(out[inside], E[inside])
+    assert np.all(np.abs(out[~inside] - m) < np.abs(E[~inside] - m))
+    # continuity and unit slope at the window edge
+    for sgn in (1, -1):
+        e0 = m + sgn * L
+        probe = np.concatenate([E, [e0 - 1e-7, e0 + 1e-7]])
+        # the probes barely move median and mean deviation; recompute window
+        o2 = oclip.clip_local_energy(probe)
+        slope = (o2[-1] - o2[-2]) / 2e-7
+        assert abs(slope - 1) < 1e-3
+
+
+# ---------------------------------------------------------------- gradient
+
+@pytest.mark.parametrize("make", [synth.be, synth.h10])
+def test_parameter_gradient_matches_finite_differences(make):
+    """grad_theta ln|psi| (Eq. trainig needs only this) against central
+    differences on 16 seeded parameter indices."""
+    S = make()
+    o = Oracle(S)
+    r = synth.random_walkers(S, 3, 4)
+    cot = np.array([0.7, -1.3, 0.4])
+    g = o.grad_logpsi(r, cot)
+    flat = synth.flatten_params(S)
+    idx = np.random.default_rng(3).choice(len(flat), 16, replace=False)
+    h = 1e-5
+    for k in idx:
+        vals = []
+        for s in (1, -1):
+            fl = flat.copy()
+            fl[k] += s * h
+            S2 = synth.with_params(S, synth.unflatten_params(S, fl))
+            vals.append((Oracle(S2).eval_logpsi(r)[0] * cot).sum())
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - g[k]) < 1e-6 * max(1.0, abs(g[k])), (k, fd, g[k])
