@@ -1,0 +1,392 @@
+"""Benchmark: walker local energies per second on one GB300 (per rank).
+
+One step = one pass of the whole hot path over the Be-atom workload (seeded
+synthetic Be: Z=4, 2 up 2 down electrons, 4 determinants, 4s2p basis, D=64,
+L=3, K=32; 4096 walkers): 100 Metropolis steps (Gaussian proposal sigma =
+0.2 bohr), local energies of all walkers (forward Laplacian jet), clipping,
+and the hand-written backward of ln|psi| for the VMC loss gradient.
+value = walkers x ranks / step time.  The headline runs the mixed path; the
+same step is also timed on the plain FP64 path.
+
+--impl reference times the CPU oracle (the plain FP64 definition) on the
+host cores on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "be"
+W_PER_RANK = 4096
+N_METROPOLIS = 100
+SIGMA = 0.2
+METRIC = "walker local energies/s"
+UNIT = "walkers/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# Algorithmic floating-point work per launch class (multiply-add = 2), per
+# walker, for the value pass (T = 1) and the jet pass (T = 3N + 2).
+def algorithmic_flops(sysd, kernel, mode):
+    N = sysd["n_up"] + sysd["n_dn"]
+    M = len(sysd["Z"])
+    D, Zd, K, L = sysd["D"], sysd["Zd"], sysd["K"], sysd["L"]
+    Hw = max(K, Zd)
+    no = sysd["mo_coeffs"].shape[1]
+    nd = len(sysd["ci"])
+    P = N * (N - 1) // 2 + N * M
+    T = 1 if mode == "value" else 3 * N + 2
+    jc = 1 if mode == "value" else 3
+    if kernel == "k_filter":
+        return L * P * jc * 2 * (K * Hw + Hw * Zd)
+    if kernel == "k_linear":
+        per_layer = N * T * 2 * (D * Zd + 3 * Zd * D)
+        heads = N * T * 2 * (D * D * 2 + D * no) + T * 2 * (2 * D * D + D)
+        return L * per_layer + heads
+    if kernel == "k_message":
+        # value: 2 per partner; derivative rows 4; Laplacian row ~ 20
+        per_row = 2 if T == 1 else (2 + 4 * (T - 2) + 20) / T
+        return L * N * T * Zd * (N - 1 + M) * per_row
+    if kernel == "k_slater":
+        nsig = [sysd["n_up"], sysd["n_dn"]]
+        f = 0
+        for ns in nsig:
+            if ns == 0:
+                continue
+            f += 2 / 3 * ns ** 3 * 2
+            if T > 1:
+                f += 2 * ns ** 3 + 2 * ns ** 2 + 3 * N * (2 * ns ** 3 + 2 * ns ** 2 + 2 * ns ** 2)
+        return nd * f
+    return None
+
+
+def _clock_sampler(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                                stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except Exception:
+        return None
+
+
+def _clock_summary(path, dev_index):
+    try:
+        rows = [l.strip().split(", ") for l in open(path) if l.strip()]
+    except Exception:
+        return None
+    rows = [r for r in rows if len(r) >= 9 and r[0] == str(dev_index)]
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    reasons = set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        for k, nm in enumerate(names):
+            if "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                reasons.add(nm)
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+    from oracle import clip as oclip
+    from oracle import sampling
+    from oracle.ansatz import Oracle
+    from paper_1909_08423_gb300 import synth
+    sysd = synth.WORKLOADS[WORKLOAD]["make"]()
+    o = Oracle(sysd)
+    Ws = args.ref_walkers
+    r = sampling.init_walkers(sysd, Ws, 1)
+    lp, _ = o.eval_logpsi(r)
+
+    def step(k):
+        nonlocal r, lp
+        r, lp, _ = sampling.metropolis(o, r, lp, N_METROPOLIS, SIGMA, seed=1, step0=k * N_METROPOLIS)
+        E, _, _ = o.local_energy(r)
+        Ec = oclip.clip_local_energy(E)
+        o.grad_logpsi(r, oclip.loss_cotangent(Ec))
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = Ws / dt
+    cores = torch.get_num_threads()
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"Be atom, {Ws} walkers sample of {W_PER_RANK}, {N_METROPOLIS} Metropolis steps "
+                                   "+ E_loc + clip + grad per step", "walkers": Ws},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{Ws} walkers per step of the {W_PER_RANK}-walker Be workload"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample(n_walkers=96):
+    """Oracle timing on the host cores for the cpu_baseline key."""
+    import torch
+    from oracle import clip as oclip
+    from oracle import sampling
+    from oracle.ansatz import Oracle
+    from paper_1909_08423_gb300 import synth
+    sysd = synth.WORKLOADS[WORKLOAD]["make"]()
+    o = Oracle(sysd)
+    r = sampling.init_walkers(sysd, n_walkers, 1)
+    lp, _ = o.eval_logpsi(r)
+    t0 = time.perf_counter()
+    r, lp, _ = sampling.metropolis(o, r, lp, N_METROPOLIS, SIGMA, seed=1, step0=0)
+    E, _, _ = o.local_energy(r)
+    Ec = oclip.clip_local_energy(E)
+    o.grad_logpsi(r, oclip.loss_cotangent(Ec))
+    dt = time.perf_counter() - t0
+    return {"value": n_walkers / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{n_walkers} walkers: {N_METROPOLIS} Metropolis steps + E_loc + clip + grad (one step)",
+            "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-walkers", type=int, default=32)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1909_08423_gb300 import binding, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = binding.load()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sysd = synth.WORKLOADS[WORKLOAD]["make"]()
+    W = W_PER_RANK
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def make_state(precision):
+        s = binding.System(sysd, precision=precision, max_walkers=W)
+        r = torch.empty(W, s.N, 3, dtype=torch.float64, device=dev)
+        s.init_walkers(r, 1000 + rank)
+        lp = torch.empty(W, dtype=torch.float64, device=dev)
+        sg = torch.empty_like(lp)
+        s.eval_logpsi(r, lp, sg)
+        st = dict(s=s, r=r, lp=lp, E=torch.empty_like(lp), Ec=torch.empty_like(lp), cot=torch.empty_like(lp),
+                  g=torch.empty(s.n_params, dtype=torch.float64, device=dev),
+                  nacc=torch.zeros(1, dtype=torch.int64, device=dev), k=0)
+        return st
+
+    def step(st):
+        s = st["s"]
+        s.metropolis_step(st["r"], st["lp"], N_METROPOLIS, SIGMA, 7 + rank, st["k"] * N_METROPOLIS, st["nacc"])
+        s.eval_local_energy(st["r"], st["E"])
+        binding.clip_local_energy(st["E"], st["Ec"], st["cot"])
+        s.grad_logpsi(st["r"], st["cot"], st["g"])
+        st["k"] += 1
+
+    def timed(st, steps, warmup, prof_kernel=None):
+        for _ in range(warmup):
+            step(st)
+        barrier()
+        if prof_kernel:
+            lib.pn_profile_kernel(prof_kernel.encode())
+        n0 = lib.pn_launch_count()
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            step(st)
+            b.record()
+            times.append((a, b))
+        barrier()
+        launches = lib.pn_launch_count() - n0
+        ms = sum(a.elapsed_time(b) for a, b in times) / steps
+        kern = None
+        if prof_kernel:
+            cnt = C_int64()
+            tot = C_double()
+            binding.check(lib.pn_profile_read(ctypes.byref(cnt), ctypes.byref(tot)))
+            lib.pn_profile_kernel(None)
+            kern = (cnt.value, tot.value)
+        return ms, launches, kern
+
+    import ctypes
+    C_int64, C_double = ctypes.c_int64, ctypes.c_double
+    lib.pn_launch_count.restype = ctypes.c_ulonglong
+    lib.pn_profile_kernel.argtypes = [ctypes.c_char_p]
+    lib.pn_profile_read.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+
+    mixed = make_state(binding.PN_MIXED)
+    # find the dominant kernel class of the step (one profiled step each)
+    for _ in range(max(1, args.warmup)):
+        step(mixed)
+    candidates = ["k_linear", "k_filter", "k_message", "k_slater", "k_orbitals", "k_combine", "k_features",
+                  "k_ssp_jet", "k_wgrad", "k_slater_bwd", "k_propose", "k_accept", "k_geometry"]
+    share = {}
+    for kname in candidates:
+        lib.pn_profile_kernel(kname.encode())
+        step(mixed)
+        torch.cuda.synchronize()
+        cnt, tot = C_int64(), C_double()
+        binding.check(lib.pn_profile_read(ctypes.byref(cnt), ctypes.byref(tot)))
+        share[kname] = (cnt.value, tot.value)
+    lib.pn_profile_kernel(None)
+    dom = max(share, key=lambda k: share[k][1])
+
+    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/pn_clocks_{rank}.csv"
+    sampler = _clock_sampler(clk_path)
+    ms, launches, kern = timed(mixed, args.steps, 0, prof_kernel=dom)
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    clocks = _clock_summary(clk_path, local)
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = W * world / (ms_max / 1e3)
+    acc_rate = float(mixed["nacc"].item()) / (W * N_METROPOLIS)
+
+    # FP64 path, same step (fewer steps: it is the slow comparator)
+    f64 = make_state(binding.PN_FP64)
+    ms64, _, _ = timed(f64, args.fp64_steps, 1)
+    e64 = f64["E"].clone()
+
+    # accuracy of the mixed path on the same sampled walkers
+    mixed_err = None
+    E_m = torch.empty_like(mixed["E"])
+    E_d = torch.empty_like(mixed["E"])
+    mixed["s"].eval_local_energy(mixed["r"], E_m)
+    f64_check = binding.System(sysd, precision=binding.PN_FP64, max_walkers=W)
+    f64_check.eval_local_energy(mixed["r"], E_d)
+    torch.cuda.synchronize()
+    err = (E_m - E_d).abs().cpu().numpy()
+    mixed_err = {"max": float(err.max()), "p999": float(np.quantile(err, 0.999)), "mean": float(err.mean())}
+
+    # end to end through the C ABI with host buffers (copies inside the region)
+    e2e = None
+    if not args.no_e2e:
+        s = mixed["s"]
+        rh = mixed["r"].cpu().numpy().copy()
+        lph = mixed["lp"].cpu().numpy().copy()
+        Eh = np.empty(W)
+        Ech = np.empty(W)
+        coth = np.empty(W)
+        gh = np.empty(s.n_params)
+        nah = np.zeros(1, dtype=np.int64)
+
+        def host_step(k):
+            s.metropolis_step(rh, lph, N_METROPOLIS, SIGMA, 11 + rank, k * N_METROPOLIS, nah)
+            s.eval_local_energy(rh, Eh)
+            binding.clip_local_energy(Eh, Ech, coth)
+            s.grad_logpsi(rh, coth, gh)
+
+        host_step(0)
+        torch.cuda.synchronize()
+        n_e2e = max(1, args.steps)
+        t0 = time.perf_counter()
+        for k in range(n_e2e):
+            host_step(1 + k)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / n_e2e
+        rb, lb = rh.nbytes, lph.nbytes
+        h2d = rb + lb + rb + W * 8 + rb + W * 8
+        d2h = rb + lb + 8 + W * 8 + 2 * W * 8 + gh.nbytes
+        e2e = {"value": W * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": dt * 1e3}
+
+    peaks, peak_src = _peaks()
+    roof = None
+    fl = algorithmic_flops(sysd, dom, "value")
+    if kern and kern[0] > 0:
+        # per step: value-pass launches dominate (Metropolis); count the
+        # algorithmic work of all timed launches of this class in the step
+        per_step_flops = None
+        if dom in ("k_filter", "k_linear", "k_message", "k_slater"):
+            per_step_flops = W * (N_METROPOLIS * algorithmic_flops(sysd, dom, "value") +
+                                  algorithmic_flops(sysd, dom, "jet"))
+        kern_ms_per_step = kern[1] / args.steps
+        if per_step_flops:
+            achieved = per_step_flops / (kern_ms_per_step / 1e3) / 1e12
+            # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+            fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+            roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp32_peak, "traffic": None,
+                    "launches_per_step": kern[0] / args.steps, "kernel_ms_per_step": kern_ms_per_step,
+                    "peak_source": "fp32 CUDA-core nominal from unit counts and max clock"}
+        else:
+            roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+                    "traffic": None, "kernel_ms_per_step": kern_ms_per_step}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"Be atom (Z=4, 4 e, 4 dets, 4s2p, D=64 L=3 K=32), {W} walkers/GPU; step = "
+                                   f"{N_METROPOLIS} Metropolis steps (sigma {SIGMA}) + E_loc + clip + grad ln|psi|",
+                       "walkers_per_gpu": W, "precision": "mixed (float32 network, float64 orbitals/dets/sums)",
+                       "l2": "flushed (256 MB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "fp64": {"value": W * world / (ms64 / 1e3), "ms_per_step": ms64, "steps": args.fp64_steps},
+            "mixed_vs_fp64_eloc_err_ha": mixed_err,
+            "accept_rate": acc_rate,
+            "kernel_share": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(share.items(), key=lambda x: -x[1][1])},
+            "roofline": roof, "peaks_source": peak_src, "gpu_launches": int(launches),
+            "clocks": clocks, "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

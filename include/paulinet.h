@@ -1,0 +1,266 @@
+/*
+ * paulinet.h -- C ABI of libpaulinet.so, the GB300 (sm_103a) hot path of
+ * PauliNet variational quantum Monte Carlo (Hermann, Schaetzle & Noe,
+ * arXiv:1909.08423).
+ *
+ * Conventions shared by every call
+ *  - Return value: PN_OK (0) or a PN_E* code; pn_last_error() gives a
+ *    thread-local message for the last failure on the calling thread.
+ *  - Units: bohr and hartree.  Walker positions r are walker-major
+ *    [W][N][3] float64 with the n_up up-spin electrons first.
+ *  - Buffers may be device pointers or host pointers (pageable or pinned);
+ *    the library asks the CUDA runtime which.  Device buffers are used in
+ *    place and the call is asynchronous on `stream` (a cudaStream_t, NULL for
+ *    the legacy default stream).  If any buffer of a call is a host pointer,
+ *    the library stages it through its own device buffers on `stream` and
+ *    synchronises `stream` before returning.
+ *  - Ownership: the caller owns every buffer it passes; the library copies
+ *    what it keeps (pn_init_system, pn_set_params) and owns its handles.
+ *  - A system handle is not safe to use from two host threads at once and
+ *    its direct calls share one workspace: do not overlap two calls on one
+ *    handle on different streams.  The serving loop (pn_server_*) owns
+ *    separate workspaces per slot.
+ */
+#ifndef PAULINET_H
+#define PAULINET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PN_OK = 0,
+  PN_EINVAL = 1,      /* bad argument, size beyond a compiled limit        */
+  PN_ENOMEM = 2,      /* device allocation failed                          */
+  PN_EBUDGET = 3,     /* job can never fit the server's memory budget      */
+  PN_ENOTREADY = 4,   /* job still queued or running                       */
+  PN_ETIMEOUT = 5,    /* a bounded wait ran out                            */
+  PN_EDEVICE = 6,     /* CUDA runtime error                                */
+  PN_ECANCELLED = 7   /* job was cancelled                                 */
+};
+
+enum { PN_FP64 = 0, PN_MIXED = 1 };
+
+/* Per-walker status word written by the evaluation calls. */
+enum { PN_WALKER_OK = 0, PN_WALKER_NONFINITE = 1, PN_WALKER_SINGULAR = 2 };
+
+/* Compiled limits (checked by pn_init_system). */
+#define PN_MAX_ELECTRONS 32
+#define PN_MAX_SPIN 16
+#define PN_MAX_ORBITALS 32
+#define PN_MAX_DETS 64
+#define PN_MAX_NUCLEI 16
+#define PN_MAX_LAYERS 8
+#define PN_MAX_DIM 256
+
+typedef struct pn_system_s* pn_system_t;
+
+/*
+ * System description (all host pointers; copied by pn_init_system).
+ *
+ * Eq. (ansatz) of the paper:
+ *   psi(r) = exp(gamma + J) sum_p c_p det[phi~_up] det[phi~_dn],
+ *   phi~_{mu i} = phi_mu(r_i) f_{mu i}(r),  f = 1 + kappa(x_i^(L)),
+ *   J = eta(sum_i x_i^(L)), gamma = sum_{i<j} -c_ij/(1 + r_ij) with
+ *   c_ij = 1/4 (same spin) or 1/2 (opposite spin) (Methods, cusp conditions).
+ *
+ * Basis (Methods, computational details; the paper uses 6-311G):
+ *   shell s is centred on nucleus shell_center[s] with l = shell_l[s]:
+ *   l = 0, 1, 2: Cartesian Gaussians x^a y^b z^c sum_k d_k exp(-alpha_k r^2)
+ *   with components (1) | (x,y,z) | (xx,xy,xz,yy,yz,zz); l = -1: Slater 1s
+ *   d exp(-zeta r) (one "primitive" holds zeta and d).  Primitives of shell s
+ *   are consecutive in prim_exp/prim_coef; coefficients are used as given.
+ *   mo_coeffs is [n_b][n_orb] (basis-function-major): phi = C^T chi.
+ * Determinants: occ_up [n_det][n_up], occ_dn [n_det][n_dn] orbital indices,
+ *   ci [n_det] the expansion coefficients c_p.
+ * Network (Methods, PauliNet extension of SchNet; Table 2): D = dim x,
+ *   Zd = dim z, K = number of distance features, L = interaction layers,
+ *   r_c the feature cutoff.  params is the flat float64 vector
+ *   (n_params = pn_num_params_for(D, Zd, K, L, M, n_orb)) in this order,
+ *   every linear map stored [in][out] (y = x W + b), Hw = max(K, Zd):
+ *     x0[D], Y[M][Zd],
+ *     for n < L:  hW[D][Zd], hb[Zd],
+ *                 for c in (same, anti, nuc): W1[K][Hw], b1[Hw], W2[Hw][Zd], b2[Zd]
+ *                 for c in (same, anti, nuc): GW[Zd][D], Gb[D]
+ *     eta:   W1[D][D] b1[D] W2[D][D] b2[D] W3[D][1] b3[1]
+ *     kappa: W1[D][D] b1[D] W2[D][D] b2[D] W3[D][n_orb] b3[n_orb]
+ *   Activation between layers: shifted softplus ln(e^x/2 + 1/2).
+ * Nuclear cusps (Methods, cusp conditions; Ma et al. 2005): with use_cusp,
+ *   inside r_c = 0.5/Z_I of each nucleus the l=0 Gaussian part of every
+ *   orbital is replaced by C + s exp(quartic(r)) matching value, slope and
+ *   curvature at r_c and Kato's cusp at the nucleus.  cusp_phi0 [n_orb][M]
+ *   gives the s part's value at the nucleus (NULL: keep the Gaussian value).
+ * precision: PN_FP64 (every step in float64) or PN_MIXED (network in
+ *   float32, orbitals, determinants, log-sum, Laplacian sum and Coulomb
+ *   terms in float64).
+ * max_walkers: walkers per chunk of the library's workspace (the workspace
+ *   grows with it; calls with more walkers run chunk by chunk).
+ */
+typedef struct pn_system_desc {
+  int M;
+  const double* Z;           /* [M]   */
+  const double* R;           /* [M][3] */
+  int n_shells;
+  const int* shell_center;   /* [n_shells] */
+  const int* shell_l;        /* [n_shells] */
+  const int* shell_nprim;    /* [n_shells] */
+  const double* prim_exp;    /* [sum nprim] */
+  const double* prim_coef;   /* [sum nprim] */
+  int n_up, n_dn, n_orb;
+  const double* mo_coeffs;   /* [n_b][n_orb] */
+  int n_det;
+  const int* occ_up;         /* [n_det][n_up] */
+  const int* occ_dn;         /* [n_det][n_dn] */
+  const double* ci;          /* [n_det] */
+  int D, Zd, K, L;
+  double r_c;
+  const double* params;      /* [n_params] */
+  int64_t n_params;
+  const double* cusp_phi0;   /* [n_orb][M] or NULL */
+  int use_cusp, use_gamma;
+  int precision;             /* PN_FP64 | PN_MIXED */
+  int max_walkers;           /* workspace chunk (walkers) */
+} pn_system_desc;
+
+/* Number of network parameters for the given sizes (layout above). */
+int64_t pn_num_params_for(int D, int Zd, int K, int L, int M, int n_orb);
+
+/* Validate, precompute the cusp coefficients (host, float64), upload the
+ * system and allocate the workspace for max_walkers walkers.
+ * Errors: PN_EINVAL (sizes, indices, limits), PN_ENOMEM, PN_EDEVICE. */
+int pn_init_system(const pn_system_desc* desc, pn_system_t* out);
+int pn_destroy_system(pn_system_t sys);
+
+/* Replace the network parameters (same layout; host or device pointer).
+ * Synchronous. */
+int pn_set_params(pn_system_t sys, const double* params, int64_t n_params);
+int64_t pn_num_params(pn_system_t sys);
+/* Bytes of device workspace held by the handle. */
+size_t pn_workspace_bytes(pn_system_t sys);
+
+/* ln|psi| and sign(psi) of Eq. (ansatz) for W walkers.
+ * r [W][N][3]; logabs, sign [W] float64; status [W] int (PN_WALKER_*). */
+int pn_eval_logpsi(pn_system_t sys, const double* r, int W, double* logabs,
+                   double* sign, int* status, void* stream);
+
+/* Local energy E_loc = -1/2 lap psi / psi + V (Eq. monte-carlo) with the
+ * Laplacian carried forward through the whole ansatz as a jet (value, 3N
+ * first derivatives, Laplacian).  eloc, logabs, sign [W] float64 (logabs and
+ * sign may be NULL); status [W] int or NULL. */
+int pn_eval_local_energy(pn_system_t sys, const double* r, int W, double* eloc,
+                         double* logabs, double* sign, int* status,
+                         void* stream);
+
+/* Intermediate quantities of the value pass, for step-by-step checks:
+ * phi [W][N][n_orb] orbitals, J [W], f [W][N][n_orb] backflow,
+ * ld [W][n_det] ln|det_up det_dn| per determinant (each may be NULL). */
+int pn_eval_components(pn_system_t sys, const double* r, int W, double* phi,
+                       double* J, double* f, double* ld, void* stream);
+
+/* n_steps Metropolis steps for each walker (Methods, ansatz optimisation:
+ * sampling of |psi|^2; Gaussian all-electron proposal of width sigma):
+ * r' = r + sigma xi, accept iff u < exp(2 (ln|psi(r')| - ln|psi(r)|)).
+ * r [W][N][3] and logabs [W] are updated in place (logabs must hold
+ * ln|psi(r)| on entry).  xi and u come from Philox4x32-10 with key = seed
+ * and counter (j, walker0 + w, step, step >> 32) for step = step0 .. step0 +
+ * n_steps - 1 (walker0 = 0 here).  n_accept (one int64, may be NULL) receives
+ * the number of accepted moves summed over walkers and steps. */
+int pn_metropolis_step(pn_system_t sys, double* r, double* logabs, int W,
+                       int n_steps, double sigma, uint64_t seed, uint64_t step0,
+                       int64_t* n_accept, void* stream);
+
+/* Initial walkers: electron e at R[nucleus(e)] + N(0, 1) per coordinate
+ * (Methods: Gaussians around the nuclei), nucleus(e) from the list of nuclei
+ * repeated Z_I times, up electron k -> entry 2k, down electron k -> 2k+1
+ * (modulo the list length); normals from the Philox stream at step 2^64-1. */
+int pn_init_walkers(pn_system_t sys, double* r, int W, uint64_t seed, void* stream);
+
+/* grad[P] = sum_w cotangent[w] d ln|psi(r_w)| / d theta over the network
+ * parameters (layout above) -- the backward pass needed by Eq. (trainig).
+ * The value pass is recomputed chunk by chunk so that the stored activations
+ * stay within mem_budget_bytes (0: the handle's workspace chunk). */
+int pn_grad_logpsi(pn_system_t sys, const double* r, int W, const double* cotangent,
+                   double* grad, size_t mem_budget_bytes, void* stream);
+
+/* Smooth clipping of local energies (Methods, ansatz optimisation): with
+ * m = median, d = mean |E - m|, Lq = q d: E' = E inside |E - m| <= Lq, else
+ * m + sgn(E - m) Lq (1 + ln(|E - m| / Lq)).  Also writes, if non-NULL,
+ * cot[W] = 2 (E'_w - mean E') / W, the per-walker weights of the loss
+ * gradient in Eq. (trainig).  W <= 16384. */
+int pn_clip_local_energy(const double* eloc, int W, double q, double* out,
+                         double* cot, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Serving loop: a persistent host thread that admits jobs by device-memory
+ * footprint as slots free up and runs admitted jobs concurrently on
+ * separate streams (continuous batching across molecules).
+ */
+typedef struct pn_server_s* pn_server_t;
+
+typedef struct pn_server_cfg {
+  size_t hbm_budget_bytes;   /* total device memory the server may hold */
+  int n_slots;               /* concurrent jobs (one stream each)       */
+  int chunk_walkers;         /* walkers per workspace chunk per slot    */
+} pn_server_cfg;
+
+enum { PN_JOB_ELOC = 0, PN_JOB_SWEEP = 1 };
+
+typedef struct pn_job {
+  int kind;          /* PN_JOB_ELOC: E_loc of the walkers; PN_JOB_SWEEP:
+                        n_steps Metropolis steps, then E_loc            */
+  int W;
+  int n_steps;
+  double sigma;
+  uint64_t seed;
+  const double* r_init;  /* [W][N][3] host or device, or NULL -> pn_init_walkers */
+  double* eloc_out;      /* [W] host or device, or NULL                 */
+  double* r_out;         /* [W][N][3] host or device, or NULL           */
+} pn_job;
+
+typedef struct pn_result {
+  int status;            /* PN_OK, PN_ECANCELLED or an error code        */
+  int W;
+  double e_mean;         /* mean E_loc over finite walkers              */
+  double e_stderr;       /* standard error of the mean                  */
+  double accept_rate;    /* sweeps only                                 */
+  int64_t n_nonfinite;   /* walkers with status != PN_WALKER_OK        */
+  double queue_ms;       /* submit -> admission                         */
+  double run_ms;         /* admission -> completion                     */
+} pn_result;
+
+int pn_server_create(const pn_server_cfg* cfg, pn_server_t* out);
+/* Stops the loop after the running jobs finish; queued jobs are cancelled. */
+int pn_server_destroy(pn_server_t srv);
+/* Queue a job.  PN_EBUDGET at once if its footprint can never fit. */
+int pn_submit(pn_server_t srv, pn_system_t sys, const pn_job* job, uint64_t* job_id);
+/* PN_OK with *res filled once done (the job is then forgotten),
+ * PN_ENOTREADY if timeout_us == 0 and not done, PN_ETIMEOUT if it did not
+ * finish within timeout_us (> 0), PN_EINVAL for an unknown id. */
+int pn_poll(pn_server_t srv, uint64_t job_id, pn_result* res, int64_t timeout_us);
+/* Cancel a queued job (PN_OK) -- running jobs complete (PN_ENOTREADY). */
+int pn_cancel(pn_server_t srv, uint64_t job_id);
+/* Device bytes a job of this size would hold. */
+size_t pn_job_footprint(pn_system_t sys, int W, int chunk_walkers);
+
+/* ---------------------------------------------------------------------
+ * Measurement hooks (no counterpart in the paper).
+ * pn_launch_count: kernels this library has launched since load.
+ * pn_profile_kernel: time every later launch of the kernel class `name`
+ *   (NULL or "" stops) with a CUDA event pair on the launch's own stream;
+ *   clears earlier records.
+ * pn_profile_read: synchronises those events and returns how many launches
+ *   were timed and their summed duration in ms.
+ */
+unsigned long long pn_launch_count(void);
+int pn_profile_kernel(const char* name);
+int pn_profile_read(int64_t* count, double* total_ms);
+
+const char* pn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAULINET_H */

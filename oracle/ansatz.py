@@ -312,4 +312,7 @@ class Oracle(Model):
         (lp * _t(cot)).sum().backward()
         shapes = synth.param_shapes(self.sys["D"], self.sys["Zd"], self.sys["K"], self.sys["L"],
                                     len(self.sys["Z"]), self.sys["mo_coeffs"].shape[1])
-        return np.concatenate([P[k].grad.numpy().reshape(-1) for k, _ in shapes])
+        # parameters that do not enter (e.g. same-spin filters with one
+        # electron per spin) have zero gradient
+        return np.concatenate([(P[k].grad if P[k].grad is not None else torch.zeros_like(P[k])).numpy().reshape(-1)
+                               for k, _ in shapes])

@@ -1,0 +1,372 @@
+// C ABI entry points for evaluation, sampling and clipping.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+#include "pn_internal.cuh"
+
+namespace {
+
+inline unsigned nblk(size_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <typename R>
+Work<R>& work_of(pn_system_s* s);
+template <>
+Work<double>& work_of<double>(pn_system_s* s) { return s->w64; }
+template <>
+Work<float>& work_of<float>(pn_system_s* s) { return s->w32; }
+
+// ---------------------------------------------------------------- sampling
+// r' = r + sigma xi for every coordinate of walker w (walker id walker0 + w).
+__global__ void k_propose(const double* __restrict__ r, double* __restrict__ rp, int Wn, int N, unsigned walker0,
+                          unsigned long long seed, unsigned long long step, double sigma) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= Wn) return;
+  const int n3 = 3 * N;
+  for (int j = 0; j * 4 < n3; ++j) {
+    double z[4];
+    pn_normals4(seed, walker0 + w, step, j, z);
+    for (int k = 0; k < 4; ++k) {
+      const int m = 4 * j + k;
+      if (m < n3) rp[(size_t)w * n3 + m] = r[(size_t)w * n3 + m] + sigma * z[k];
+    }
+  }
+}
+
+// accept iff u < exp(2 (lp' - lp)); u is word 0 of block ceil(3N/4).
+__global__ void k_accept(double* __restrict__ r, double* __restrict__ lp, const double* __restrict__ rp,
+                         const double* __restrict__ lpp, int Wn, int N, unsigned walker0, unsigned long long seed,
+                         unsigned long long step, unsigned long long* n_acc) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= Wn) return;
+  const int n3 = 3 * N;
+  unsigned c[4] = {(unsigned)((n3 + 3) / 4), walker0 + w, (unsigned)(step & 0xffffffffull), (unsigned)(step >> 32)};
+  pn_philox(c, (unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
+  const double u = pn_u01(c[0]);
+  const bool acc = u < exp(2.0 * (lpp[w] - lp[w]));
+  if (acc) {
+    for (int m = 0; m < n3; ++m) r[(size_t)w * n3 + m] = rp[(size_t)w * n3 + m];
+    lp[w] = lpp[w];
+    atomicAdd(n_acc, 1ull);
+  }
+}
+
+// electron e at R[nuc(e)] + normal, normals at step 2^64 - 1.
+__global__ void k_init_walkers(DevSys s, const int* __restrict__ nuc, double* __restrict__ r, int W,
+                               unsigned long long seed) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  const int n3 = 3 * s.N;
+  const unsigned long long step = ~0ull;
+  for (int j = 0; j * 4 < n3; ++j) {
+    double z[4];
+    pn_normals4(seed, (unsigned)w, step, j, z);
+    for (int k = 0; k < 4; ++k) {
+      const int m = 4 * j + k;
+      if (m < n3) r[(size_t)w * n3 + m] = s.R[3 * nuc[m / 3] + m % 3] + z[k];
+    }
+  }
+}
+
+// Value-pass components for step-by-step checks.
+template <typename R>
+__global__ void k_components(DevSys s, const double* __restrict__ phi, const R* __restrict__ F,
+                             const R* __restrict__ Jj, const double* __restrict__ det, int Wn, double* __restrict__ ophi,
+                             double* __restrict__ oJ, double* __restrict__ of, double* __restrict__ old) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= Wn) return;
+  const int N = s.N, no = s.n_orb, stride = 3 + 3 * N;
+  for (int k = 0; k < N * no; ++k) {
+    if (ophi) ophi[(size_t)w * N * no + k] = phi[((size_t)w * N * no + k) * 5];
+    if (of) of[(size_t)w * N * no + k] = 1.0 + (double)F[(size_t)w * N * no + k];
+  }
+  if (oJ) oJ[w] = (double)Jj[w];
+  if (old)
+    for (int p = 0; p < s.n_det; ++p) {
+      const double* d = det + ((size_t)w * s.n_det + p) * 2 * stride;
+      old[(size_t)w * s.n_det + p] = d[0] + d[stride];
+    }
+}
+
+// ---------------------------------------------------------------- clipping
+// One block: bitonic sort of the batch in shared memory for the median,
+// mean absolute deviation, logarithmic clipping, then the loss weights.
+__global__ void k_clip(const double* __restrict__ E, int W, double q, double* __restrict__ out,
+                       double* __restrict__ cot) {
+  extern __shared__ double sh[];
+  __shared__ double red[32];
+  int n = 1;
+  while (n < W) n <<= 1;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sh[i] = i < W ? E[i] : INFINITY;
+  __syncthreads();
+  for (int k = 2; k <= n; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const double a = sh[i], b = sh[l];
+          if ((a > b) == up) { sh[i] = b; sh[l] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  const double m = 0.5 * (sh[(W - 1) / 2] + sh[W / 2]);
+  auto block_sum = [&](double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    return t;
+  };
+  double a = 0;
+  for (int i = threadIdx.x; i < W; i += blockDim.x) a += fabs(E[i] - m);
+  const double dev = block_sum(a) / W;
+  const double Lq = q * dev;
+  double sum = 0;
+  for (int i = threadIdx.x; i < W; i += blockDim.x) {
+    const double x = E[i] - m;
+    double v = E[i];
+    if (fabs(x) > Lq) v = m + copysign(Lq * (1.0 + log(fabs(x) / Lq)), x);
+    out[i] = v;
+    sum += v;
+  }
+  const double mean = block_sum(sum) / W;
+  if (cot)
+    for (int i = threadIdx.x; i < W; i += blockDim.x) cot[i] = 2.0 * (out[i] - mean) / W;
+}
+
+bool is_host(const void* p) { return p && !pn_is_device_ptr(p); }
+
+int set_device(pn_system_s* s) {
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != s->device) PN_CUDA(cudaSetDevice(s->device));
+  return PN_OK;
+}
+
+template <typename R>
+int eval_impl(pn_system_s* s, const double* r, int W, int jet, double* eloc, double* logabs, double* sign, int* status,
+              cudaStream_t st) {
+  Work<R>& w = work_of<R>(s);
+  const DevNet<R> net = pn_devnet<R>(s);
+  const DevSys& ds = s->ds;
+  const int N = ds.N;
+  const bool rdev = pn_is_device_ptr(r);
+  const bool sync = !rdev || is_host(eloc) || is_host(logabs) || is_host(sign) || is_host(status);
+  for (int c0 = 0; c0 < W; c0 += s->Wc) {
+    const int Wn = std::min(s->Wc, W - c0);
+    const double* rc = r + (size_t)c0 * N * 3;
+    if (!rdev) {
+      PN_CUDA(cudaMemcpyAsync(w.r, rc, (size_t)Wn * N * 3 * 8, cudaMemcpyHostToDevice, st));
+      rc = w.r;
+    }
+    if (int e = pn_forward_chunk<R>(ds, net, w, rc, Wn, jet, st)) return e;
+    if (eloc && jet) PN_CUDA(cudaMemcpyAsync(eloc + c0, w.out_eloc, Wn * 8, cudaMemcpyDefault, st));
+    if (logabs) PN_CUDA(cudaMemcpyAsync(logabs + c0, w.out_logabs, Wn * 8, cudaMemcpyDefault, st));
+    if (sign) PN_CUDA(cudaMemcpyAsync(sign + c0, w.out_sign, Wn * 8, cudaMemcpyDefault, st));
+    if (status) PN_CUDA(cudaMemcpyAsync(status + c0, w.out_status, Wn * 4, cudaMemcpyDefault, st));
+  }
+  if (sync) PN_CUDA(cudaStreamSynchronize(st));
+  return PN_OK;
+}
+
+template <typename R>
+int components_impl(pn_system_s* s, const double* r, int W, double* phi, double* J, double* f, double* ld,
+                    cudaStream_t st) {
+  Work<R>& w = work_of<R>(s);
+  const DevNet<R> net = pn_devnet<R>(s);
+  const DevSys& ds = s->ds;
+  const int N = ds.N, no = ds.n_orb;
+  const bool rdev = pn_is_device_ptr(r);
+  const bool host_out = is_host(phi) || is_host(J) || is_host(f) || is_host(ld);
+  // call-scoped staging for the gathered outputs (a diagnostic entry point)
+  double* tmp = nullptr;
+  const size_t per_w = (size_t)2 * N * no + 1 + ds.n_det;
+  PN_CUDA(cudaMallocAsync((void**)&tmp, (size_t)s->Wc * per_w * 8, st));
+  for (int c0 = 0; c0 < W; c0 += s->Wc) {
+    const int Wn = std::min(s->Wc, W - c0);
+    const double* rc = r + (size_t)c0 * N * 3;
+    if (!rdev) {
+      PN_CUDA(cudaMemcpyAsync(w.r, rc, (size_t)Wn * N * 3 * 8, cudaMemcpyHostToDevice, st));
+      rc = w.r;
+    }
+    if (int e = pn_forward_chunk<R>(ds, net, w, rc, Wn, 0, st)) return e;
+    double* tphi = tmp;
+    double* tf = tphi + (size_t)Wn * N * no;
+    double* tJ = tf + (size_t)Wn * N * no;
+    double* tld = tJ + Wn;
+    PN_LAUNCH("k_components", st, k_components<R><<<nblk(Wn, 64), 64, 0, st>>>(ds, w.phi, w.F, w.Jj, w.det, Wn, tphi, tJ, tf, tld));
+    if (phi) PN_CUDA(cudaMemcpyAsync(phi + (size_t)c0 * N * no, tphi, (size_t)Wn * N * no * 8, cudaMemcpyDefault, st));
+    if (f) PN_CUDA(cudaMemcpyAsync(f + (size_t)c0 * N * no, tf, (size_t)Wn * N * no * 8, cudaMemcpyDefault, st));
+    if (J) PN_CUDA(cudaMemcpyAsync(J + c0, tJ, (size_t)Wn * 8, cudaMemcpyDefault, st));
+    if (ld) PN_CUDA(cudaMemcpyAsync(ld + (size_t)c0 * ds.n_det, tld, (size_t)Wn * ds.n_det * 8, cudaMemcpyDefault, st));
+    // the staging area is reused by the next chunk
+    PN_CUDA(cudaStreamSynchronize(st));
+  }
+  (void)host_out;
+  PN_CUDA(cudaFreeAsync(tmp, st));
+  PN_CUDA(cudaStreamSynchronize(st));
+  return PN_OK;
+}
+
+template <typename R>
+int metropolis_impl(pn_system_s* s, double* r, double* logabs, int W, int n_steps, double sigma,
+                    unsigned long long seed, unsigned long long step0, int64_t* n_accept, cudaStream_t st) {
+  Work<R>& w = work_of<R>(s);
+  const DevNet<R> net = pn_devnet<R>(s);
+  const DevSys& ds = s->ds;
+  const int N = ds.N;
+  const bool rdev = pn_is_device_ptr(r), ldev = pn_is_device_ptr(logabs);
+  PN_CUDA(cudaMemsetAsync(w.n_acc, 0, 8, st));
+  for (int c0 = 0; c0 < W; c0 += s->Wc) {
+    const int Wn = std::min(s->Wc, W - c0);
+    double* rc = r + (size_t)c0 * N * 3;
+    double* lc = logabs + c0;
+    if (!rdev) {
+      PN_CUDA(cudaMemcpyAsync(w.r, rc, (size_t)Wn * N * 3 * 8, cudaMemcpyHostToDevice, st));
+      rc = w.r;
+    }
+    if (!ldev) {
+      PN_CUDA(cudaMemcpyAsync(w.lp_prop, lc, (size_t)Wn * 8, cudaMemcpyHostToDevice, st));
+      lc = w.lp_prop;
+    }
+    for (int k = 0; k < n_steps; ++k) {
+      const unsigned long long step = step0 + (unsigned long long)k;
+      PN_LAUNCH("k_propose", st, k_propose<<<nblk(Wn, 128), 128, 0, st>>>(rc, w.r_prop, Wn, N, (unsigned)c0, seed, step, sigma));
+      if (int e = pn_forward_chunk<R>(ds, net, w, w.r_prop, Wn, 0, st)) return e;
+      PN_LAUNCH("k_accept", st, k_accept<<<nblk(Wn, 128), 128, 0, st>>>(rc, lc, w.r_prop, w.out_logabs, Wn, N, (unsigned)c0, seed, step, w.n_acc));
+    }
+    if (!rdev) PN_CUDA(cudaMemcpyAsync(r + (size_t)c0 * N * 3, rc, (size_t)Wn * N * 3 * 8, cudaMemcpyDeviceToHost, st));
+    if (!ldev) PN_CUDA(cudaMemcpyAsync(logabs + c0, lc, (size_t)Wn * 8, cudaMemcpyDeviceToHost, st));
+  }
+  if (n_accept) PN_CUDA(cudaMemcpyAsync(n_accept, w.n_acc, 8, cudaMemcpyDefault, st));
+  if (!rdev || !ldev || is_host(n_accept)) PN_CUDA(cudaStreamSynchronize(st));
+  return PN_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------- C ABI
+#define PN_SYS_CHECK(s)                                   \
+  do {                                                    \
+    if (!(s)) { pn_set_error("null system"); return PN_EINVAL; } \
+    if (int e_ = set_device(s)) return e_;                \
+  } while (0)
+
+extern "C" int pn_eval_logpsi(pn_system_t s, const double* r, int W, double* logabs, double* sign, int* status,
+                              void* stream) {
+  PN_SYS_CHECK(s);
+  if (W < 0 || (W > 0 && (!r || !logabs))) { pn_set_error("bad arguments"); return PN_EINVAL; }
+  if (W == 0) return PN_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  return s->precision == PN_FP64 ? eval_impl<double>(s, r, W, 0, nullptr, logabs, sign, status, st)
+                                 : eval_impl<float>(s, r, W, 0, nullptr, logabs, sign, status, st);
+}
+
+extern "C" int pn_eval_local_energy(pn_system_t s, const double* r, int W, double* eloc, double* logabs, double* sign,
+                                    int* status, void* stream) {
+  PN_SYS_CHECK(s);
+  if (W < 0 || (W > 0 && (!r || !eloc))) { pn_set_error("bad arguments"); return PN_EINVAL; }
+  if (W == 0) return PN_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  return s->precision == PN_FP64 ? eval_impl<double>(s, r, W, 1, eloc, logabs, sign, status, st)
+                                 : eval_impl<float>(s, r, W, 1, eloc, logabs, sign, status, st);
+}
+
+extern "C" int pn_eval_components(pn_system_t s, const double* r, int W, double* phi, double* J, double* f, double* ld,
+                                  void* stream) {
+  PN_SYS_CHECK(s);
+  if (W < 0 || (W > 0 && !r)) { pn_set_error("bad arguments"); return PN_EINVAL; }
+  if (W == 0) return PN_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  return s->precision == PN_FP64 ? components_impl<double>(s, r, W, phi, J, f, ld, st)
+                                 : components_impl<float>(s, r, W, phi, J, f, ld, st);
+}
+
+extern "C" int pn_metropolis_step(pn_system_t s, double* r, double* logabs, int W, int n_steps, double sigma,
+                                  uint64_t seed, uint64_t step0, int64_t* n_accept, void* stream) {
+  PN_SYS_CHECK(s);
+  if (W < 0 || n_steps < 0 || !(sigma > 0) || (W > 0 && (!r || !logabs))) {
+    pn_set_error("bad arguments");
+    return PN_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (W == 0 || n_steps == 0) {
+    if (n_accept) {
+      int64_t z = 0;
+      PN_CUDA(cudaMemcpyAsync(n_accept, &z, 8, cudaMemcpyDefault, st));
+      PN_CUDA(cudaStreamSynchronize(st));
+    }
+    return PN_OK;
+  }
+  return s->precision == PN_FP64 ? metropolis_impl<double>(s, r, logabs, W, n_steps, sigma, seed, step0, n_accept, st)
+                                 : metropolis_impl<float>(s, r, logabs, W, n_steps, sigma, seed, step0, n_accept, st);
+}
+
+extern "C" int pn_init_walkers(pn_system_t s, double* r, int W, uint64_t seed, void* stream) {
+  PN_SYS_CHECK(s);
+  if (W < 0 || (W > 0 && !r)) { pn_set_error("bad arguments"); return PN_EINVAL; }
+  if (W == 0) return PN_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const DevSys& ds = s->ds;
+  // nucleus per electron: nuclei repeated Z_I times; up k -> 2k, down k -> 2k+1
+  std::vector<double> Z(ds.M);
+  PN_CUDA(cudaMemcpy(Z.data(), ds.Z, ds.M * 8, cudaMemcpyDeviceToHost));
+  std::vector<int> lst;
+  for (int I = 0; I < ds.M; ++I)
+    for (int k = 0; k < (int)llround(Z[I]); ++k) lst.push_back(I);
+  if (lst.empty()) lst.push_back(0);
+  std::vector<int> nuc(ds.N);
+  for (int k = 0; k < ds.n_up; ++k) nuc[k] = lst[(2 * k) % lst.size()];
+  for (int k = 0; k < ds.n_dn; ++k) nuc[ds.n_up + k] = lst[(2 * k + 1) % lst.size()];
+  int* dnuc = nullptr;
+  // the nucleus table is tiny; keep one per call in the workspace's n_acc slot area is not enough, so allocate
+  PN_CUDA(cudaMallocAsync((void**)&dnuc, ds.N * sizeof(int), st));
+  PN_CUDA(cudaMemcpyAsync(dnuc, nuc.data(), ds.N * sizeof(int), cudaMemcpyHostToDevice, st));
+  const bool rdev = pn_is_device_ptr(r);
+  double* rd = r;
+  if (!rdev) PN_CUDA(cudaMallocAsync((void**)&rd, (size_t)W * ds.N * 3 * 8, st));
+  PN_LAUNCH("k_init_walkers", st, k_init_walkers<<<nblk(W, 128), 128, 0, st>>>(ds, dnuc, rd, W, seed));
+  if (!rdev) {
+    PN_CUDA(cudaMemcpyAsync(r, rd, (size_t)W * ds.N * 3 * 8, cudaMemcpyDeviceToHost, st));
+    PN_CUDA(cudaFreeAsync(rd, st));
+  }
+  PN_CUDA(cudaFreeAsync(dnuc, st));
+  PN_CUDA(cudaStreamSynchronize(st));
+  return PN_OK;
+}
+
+extern "C" int pn_clip_local_energy(const double* eloc, int W, double q, double* out, double* cot, void* stream) {
+  if (W <= 0 || W > 16384 || !eloc || !out || !(q > 0)) {
+    pn_set_error("clip: need 0 < W <= 16384, q > 0 and buffers");
+    return PN_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool host = is_host(eloc) || is_host(out) || is_host(cot);
+  const double* e = eloc;
+  double *o = out, *c = cot, *tmp = nullptr;
+  if (host) {
+    PN_CUDA(cudaMallocAsync((void**)&tmp, (size_t)W * 3 * 8, st));
+    PN_CUDA(cudaMemcpyAsync(tmp, eloc, (size_t)W * 8, cudaMemcpyDefault, st));
+    e = tmp;
+    o = tmp + W;
+    c = cot ? tmp + 2 * W : nullptr;
+  }
+  int n = 1;
+  while (n < W) n <<= 1;
+  const size_t smem = (size_t)n * 8;
+  PN_CUDA(cudaFuncSetAttribute(k_clip, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8));
+  PN_LAUNCH("k_clip", st, k_clip<<<1, 1024, smem, st>>>(e, W, q, o, c));
+  if (host) {
+    PN_CUDA(cudaMemcpyAsync(out, o, (size_t)W * 8, cudaMemcpyDefault, st));
+    if (cot) PN_CUDA(cudaMemcpyAsync(cot, c, (size_t)W * 8, cudaMemcpyDefault, st));
+    PN_CUDA(cudaFreeAsync(tmp, st));
+    PN_CUDA(cudaStreamSynchronize(st));
+  }
+  return PN_OK;
+}

@@ -1,0 +1,717 @@
+// Parameter gradient of ln|psi| (reverse mode, hand written): the backward
+// pass needed by the VMC loss gradient, Eq. (trainig) of the paper:
+//   grad_theta L = 2 E[(E_loc - L) grad_theta ln|psi|]
+// = sum_w u_w grad_theta ln|psi_w| with per-walker weights u_w (cotangent).
+//
+// For each chunk of walkers the value pass is recomputed with every
+// activation kept on a tape; then the chain runs back through the
+// determinants, the backflow and Jastrow heads, the interaction layers
+// (receiving maps g, messages, filters w, input maps h) to x0 and Y.
+// Weight gradients are sums over rows (walkers x electrons or pairs): each
+// is formed as per-block partial tiles in float64 and reduced in a fixed
+// order, so the result is deterministic.
+#include <math.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+#include "pn_internal.cuh"
+
+namespace pnb {
+
+inline unsigned nblk(size_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <typename R>
+__device__ inline R sigm_(R x) { return R(1) / (R(1) + exp(-x)); }
+template <typename R>
+__device__ inline R ssp_(R x) {
+  return (x > R(0) ? x : R(0)) + log1p(exp(-fabs(x))) - R(0.69314718055994530942);
+}
+
+__device__ inline int pair_channel(const DevSys& s, int p) {
+  if (p >= s.Pee) return 2;
+  int a = 0, rem = p;
+  while (rem >= s.N - 1 - a) { rem -= s.N - 1 - a; ++a; }
+  int b = a + 1 + rem;
+  return ((a < s.n_up) == (b < s.n_up)) ? 0 : 1;
+}
+
+// ------------------------------------------------------------ forward tape
+// Value-only filter nets keeping the hidden pre-activation:
+// Ah[row][h] = b1 + e W1, w[row][z] = b2 + ssp(Ah) W2.
+template <typename R>
+__global__ void k_filter_tape(DevSys s, DevNet<R> net, int n, const R* __restrict__ ef, int Wn, R* __restrict__ Ah,
+                              R* __restrict__ wout) {
+  __shared__ R sh_e[8][64];
+  __shared__ R sh_h[8][128];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const size_t row = (size_t)blockIdx.x * 8 + wid;
+  if (row >= (size_t)Wn * s.Ppair) return;
+  const int ch = pair_channel(s, row % s.Ppair);
+  const int K = s.K, Hw = s.Hw, Zd = s.Zd;
+  for (int k = lane; k < K; k += 32) sh_e[wid][k] = ef[row * 3 * K + k];
+  __syncwarp();
+  const R* W1 = net.p + net.off.W1[n][ch];
+  const R* b1 = net.p + net.off.b1[n][ch];
+  const R* W2 = net.p + net.off.W2[n][ch];
+  const R* b2 = net.p + net.off.b2[n][ch];
+  for (int h = lane; h < Hw; h += 32) {
+    R a = b1[h];
+    for (int k = 0; k < K; ++k) a += sh_e[wid][k] * W1[k * Hw + h];
+    Ah[row * Hw + h] = a;
+    sh_h[wid][h] = ssp_(a);
+  }
+  __syncwarp();
+  for (int z = lane; z < Zd; z += 32) {
+    R o = b2[z];
+    for (int h = 0; h < Hw; ++h) o += sh_h[wid][h] * W2[h * Zd + z];
+    wout[row * Zd + z] = o;
+  }
+}
+
+// Value-only messages: Z[w][i][c*Zd + z] from filter outputs w[w][p][z].
+template <typename R>
+__global__ void k_message_value(DevSys s, const R* __restrict__ Y, const R* __restrict__ wv, const R* __restrict__ H,
+                                int Wn, R* __restrict__ Z) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int Zd = s.Zd, N = s.N;
+  if (idx >= (size_t)Wn * N * Zd) return;
+  const int z = idx % Zd;
+  const int i = (idx / Zd) % N;
+  const int w = idx / ((size_t)Zd * N);
+  const R* ww = wv + (size_t)w * s.Ppair * Zd;
+  const R* hw = H + (size_t)w * N * Zd;
+  R zs = 0, za = 0, zn = 0;
+  const bool si = i < s.n_up;
+  for (int j = 0; j < N; ++j) {
+    if (j == i) continue;
+    const int p = i < j ? pn_pair_index(i, j, N) : pn_pair_index(j, i, N);
+    const R v = ww[(size_t)p * Zd + z] * hw[(size_t)j * Zd + z];
+    if ((j < s.n_up) == si) zs += v; else za += v;
+  }
+  for (int I = 0; I < s.M; ++I) zn += ww[(size_t)(s.Pee + i * s.M + I) * Zd + z] * Y[I * Zd + z];
+  R* o = Z + ((size_t)w * N + i) * 3 * Zd;
+  o[z] = zs;
+  o[Zd + z] = za;
+  o[2 * Zd + z] = zn;
+}
+
+template <typename R>
+__global__ void k_ssp_copy(const R* __restrict__ A, R* __restrict__ S, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) S[i] = ssp_(A[i]);
+}
+
+// ---------------------------------------------------------- backward kernels
+// Determinant part: d ln|psi| / d F[w][i][mu] (f = 1 + F) for weight u_w,
+// with omega_p = c_p s_p e^{ld_p} / S and d ln|det A| / dA = A^{-T}.
+// Also writes the walker's J cotangent (= u_w).  One thread per walker.
+template <typename R>
+__global__ void k_slater_bwd(DevSys s, const double* __restrict__ phi, const R* __restrict__ F, const double* __restrict__ u,
+                             int Wn, R* __restrict__ dF, R* __restrict__ dJ) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= Wn) return;
+  const int N = s.N, no = s.n_orb, nd = s.n_det;
+  constexpr int NS = PN_MAX_SPIN;
+  const double* phw = phi + (size_t)w * N * no * 5;
+  const R* Fw = F + (size_t)w * N * no;
+  double ld[PN_MAX_DETS], sg[PN_MAX_DETS];
+  // pass 1: ln|det| and signs
+  for (int p = 0; p < nd; ++p) {
+    double l = 0, sgn = 1;
+    for (int sp = 0; sp < 2; ++sp) {
+      const int ns = sp ? s.n_dn : s.n_up, e0 = sp ? s.n_up : 0;
+      if (ns == 0) continue;
+      const int* occ = s.occ + p * N + e0;
+      double LU[NS * NS];
+      for (int a = 0; a < ns; ++a)
+        for (int b = 0; b < ns; ++b)
+          LU[a * ns + b] = phw[((e0 + a) * no + occ[b]) * 5] * (1.0 + (double)Fw[(e0 + a) * no + occ[b]]);
+      for (int c = 0; c < ns; ++c) {
+        int best = c;
+        double bv = fabs(LU[c * ns + c]);
+        for (int rr = c + 1; rr < ns; ++rr)
+          if (fabs(LU[rr * ns + c]) > bv) { bv = fabs(LU[rr * ns + c]); best = rr; }
+        if (!(bv > 0.0)) { sgn = 0; break; }
+        if (best != c) {
+          for (int k = 0; k < ns; ++k) { double t = LU[c * ns + k]; LU[c * ns + k] = LU[best * ns + k]; LU[best * ns + k] = t; }
+          sgn = -sgn;
+        }
+        const double piv = LU[c * ns + c];
+        if (piv < 0) sgn = -sgn;
+        l += log(fabs(piv));
+        for (int rr = c + 1; rr < ns; ++rr) {
+          const double f = LU[rr * ns + c] / piv;
+          LU[rr * ns + c] = f;
+          for (int k = c + 1; k < ns; ++k) LU[rr * ns + k] -= f * LU[c * ns + k];
+        }
+      }
+      if (sgn == 0) break;
+    }
+    ld[p] = l;
+    sg[p] = sgn;
+  }
+  double m = -INFINITY;
+  for (int p = 0; p < nd; ++p)
+    if (s.ci[p] != 0.0 && sg[p] != 0.0) m = fmax(m, ld[p]);
+  double S = 0;
+  for (int p = 0; p < nd; ++p)
+    if (sg[p] != 0.0) S += s.ci[p] * sg[p] * exp(ld[p] - m);
+  const double uw = u[w];
+  dJ[w] = (R)uw;
+  double dphit[PN_MAX_ELECTRONS * PN_MAX_ORBITALS];
+  for (int k = 0; k < N * no; ++k) dphit[k] = 0;
+  if (S != 0.0 && m > -INFINITY) {
+    for (int p = 0; p < nd; ++p) {
+      if (sg[p] == 0.0) continue;
+      const double om = uw * s.ci[p] * sg[p] * exp(ld[p] - m) / S;
+      for (int sp = 0; sp < 2; ++sp) {
+        const int ns = sp ? s.n_dn : s.n_up, e0 = sp ? s.n_up : 0;
+        if (ns == 0) continue;
+        const int* occ = s.occ + p * N + e0;
+        double LU[NS * NS];
+        int perm[NS];
+        for (int a = 0; a < ns; ++a)
+          for (int b = 0; b < ns; ++b)
+            LU[a * ns + b] = phw[((e0 + a) * no + occ[b]) * 5] * (1.0 + (double)Fw[(e0 + a) * no + occ[b]]);
+        for (int c = 0; c < ns; ++c) perm[c] = c;
+        for (int c = 0; c < ns; ++c) {
+          int best = c;
+          double bv = fabs(LU[c * ns + c]);
+          for (int rr = c + 1; rr < ns; ++rr)
+            if (fabs(LU[rr * ns + c]) > bv) { bv = fabs(LU[rr * ns + c]); best = rr; }
+          if (best != c) {
+            for (int k = 0; k < ns; ++k) { double t = LU[c * ns + k]; LU[c * ns + k] = LU[best * ns + k]; LU[best * ns + k] = t; }
+            int t = perm[c]; perm[c] = perm[best]; perm[best] = t;
+          }
+          const double piv = LU[c * ns + c];
+          for (int rr = c + 1; rr < ns; ++rr) {
+            const double f = LU[rr * ns + c] / piv;
+            LU[rr * ns + c] = f;
+            for (int k = c + 1; k < ns; ++k) LU[rr * ns + k] -= f * LU[c * ns + k];
+          }
+        }
+        // column `col` of A^{-1}; d ln|det| / dA[a][b] = Ainv[b][a]
+        for (int col = 0; col < ns; ++col) {
+          double y[NS];
+          for (int rr = 0; rr < ns; ++rr) {
+            double v = (perm[rr] == col) ? 1.0 : 0.0;
+            for (int k = 0; k < rr; ++k) v -= LU[rr * ns + k] * y[k];
+            y[rr] = v;
+          }
+          for (int rr = ns - 1; rr >= 0; --rr) {
+            double v = y[rr];
+            for (int k = rr + 1; k < ns; ++k) v -= LU[rr * ns + k] * y[k];
+            y[rr] = v / LU[rr * ns + rr];
+          }
+          // y = Ainv[:, col]; entry Ainv[b][col] pairs with A[col][b]
+          for (int b = 0; b < ns; ++b) dphit[(e0 + col) * no + occ[b]] += om * y[b];
+        }
+      }
+    }
+  }
+  for (int i = 0; i < N; ++i)
+    for (int mu = 0; mu < no; ++mu)
+      dF[((size_t)w * N + i) * no + mu] = (R)(dphit[i * no + mu] * phw[(i * no + mu) * 5]);
+}
+
+// out = d * sigmoid(a)
+template <typename R>
+__global__ void k_mul_sigmoid(const R* __restrict__ d, const R* __restrict__ a, R* __restrict__ out, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = d[i] * sigm_(a[i]);
+}
+
+// dJ [Wn] times eta.W3^T -> dS2s [Wn][D]
+template <typename R>
+__global__ void k_outer_row(const R* __restrict__ dj, const R* __restrict__ w3, R* __restrict__ out, int Wn, int D) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < (size_t)Wn * D) out[i] = dj[i / D] * w3[i % D];
+}
+
+// dX[w][i][d] += dXs[w][d]
+template <typename R>
+__global__ void k_bcast_add(R* __restrict__ dX, const R* __restrict__ dXs, int Wn, int N, int D) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)Wn * N * D) return;
+  const int d = i % D;
+  const int w = i / ((size_t)N * D);
+  dX[i] += dXs[(size_t)w * D + d];
+}
+
+// Message backward, filter side: dw[w][p][z].
+template <typename R>
+__global__ void k_msg_bwd_w(DevSys s, const R* __restrict__ Y, const R* __restrict__ H, const R* __restrict__ dZ, int Wn,
+                            R* __restrict__ dw) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int Zd = s.Zd, N = s.N;
+  if (idx >= (size_t)Wn * s.Ppair * Zd) return;
+  const int z = idx % Zd;
+  const int p = (idx / Zd) % s.Ppair;
+  const int w = idx / ((size_t)Zd * s.Ppair);
+  const R* dZw = dZ + (size_t)w * N * 3 * Zd;
+  R v;
+  if (p < s.Pee) {
+    int a = 0, rem = p;
+    while (rem >= N - 1 - a) { rem -= N - 1 - a; ++a; }
+    const int b = a + 1 + rem;
+    const int c = ((a < s.n_up) == (b < s.n_up)) ? 0 : 1;
+    const R* Hw_ = H + (size_t)w * N * Zd;
+    v = dZw[(size_t)a * 3 * Zd + c * Zd + z] * Hw_[(size_t)b * Zd + z] +
+        dZw[(size_t)b * 3 * Zd + c * Zd + z] * Hw_[(size_t)a * Zd + z];
+  } else {
+    const int q = p - s.Pee, i = q / s.M, I = q % s.M;
+    v = dZw[(size_t)i * 3 * Zd + 2 * Zd + z] * Y[I * Zd + z];
+  }
+  dw[idx] = v;
+}
+
+// Message backward, sender side: dH[w][j][z] = sum_i w_ij dZ_{c(i,j)}[i][z];
+// nuclear embedding rows: dYr[w][i][I*Zd + z] = w_iI dZ_nuc[i][z].
+template <typename R>
+__global__ void k_msg_bwd_h(DevSys s, const R* __restrict__ wv, const R* __restrict__ dZ, int Wn, R* __restrict__ dH,
+                            R* __restrict__ dYr) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int Zd = s.Zd, N = s.N;
+  if (idx >= (size_t)Wn * N * Zd) return;
+  const int z = idx % Zd;
+  const int j = (idx / Zd) % N;
+  const int w = idx / ((size_t)Zd * N);
+  const R* ww = wv + (size_t)w * s.Ppair * Zd;
+  const R* dZw = dZ + (size_t)w * N * 3 * Zd;
+  R acc = 0;
+  for (int i = 0; i < N; ++i) {
+    if (i == j) continue;
+    const int p = i < j ? pn_pair_index(i, j, N) : pn_pair_index(j, i, N);
+    const int c = ((i < s.n_up) == (j < s.n_up)) ? 0 : 1;
+    acc += ww[(size_t)p * Zd + z] * dZw[(size_t)i * 3 * Zd + c * Zd + z];
+  }
+  dH[idx] = acc;
+  for (int I = 0; I < s.M; ++I)
+    dYr[(((size_t)w * N + j) * s.M + I) * Zd + z] =
+        ww[(size_t)(s.Pee + j * s.M + I) * Zd + z] * dZw[(size_t)j * 3 * Zd + 2 * Zd + z];
+}
+
+// Filter backward through the hidden layer: dAh = (dw W2^T) * sigmoid(Ah),
+// Sh = ssp(Ah) kept for the W2 gradient.  One warp per pair row.
+template <typename R>
+__global__ void k_filter_bwd(DevSys s, DevNet<R> net, int n, const R* __restrict__ Ah, const R* __restrict__ dw, int Wn,
+                             R* __restrict__ dAh, R* __restrict__ Sh) {
+  __shared__ R sh_d[8][128];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const size_t row = (size_t)blockIdx.x * 8 + wid;
+  if (row >= (size_t)Wn * s.Ppair) return;
+  const int ch = pair_channel(s, row % s.Ppair);
+  const int Hw = s.Hw, Zd = s.Zd;
+  for (int z = lane; z < Zd; z += 32) sh_d[wid][z] = dw[row * Zd + z];
+  __syncwarp();
+  const R* W2 = net.p + net.off.W2[n][ch];
+  for (int h = lane; h < Hw; h += 32) {
+    R acc = 0;
+    for (int z = 0; z < Zd; ++z) acc += sh_d[wid][z] * W2[h * Zd + z];
+    const R a = Ah[row * Hw + h];
+    dAh[row * Hw + h] = acc * sigm_(a);
+    Sh[row * Hw + h] = ssp_(a);
+  }
+}
+
+// ------------------------------------------------------------ weight grads
+// part[split][ka][nb] = sum over this split's rows r (whose pair channel is
+// `ch`, or all rows if ch < 0) of A[r][ka] * B[r][nb]; A == nullptr means a
+// column of ones (bias gradient, Ka = 1).  32x32 tile per block.
+template <typename R>
+__global__ void k_wgrad(const R* __restrict__ A, int lda, const R* __restrict__ B, int ldb, int rows, int Ka, int Nb,
+                        int rows_per_split, DevSys s, int ch, double* __restrict__ part) {
+  __shared__ R As[32][33];
+  __shared__ R Bs[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  const int r_begin = blockIdx.z * rows_per_split;
+  const int r_end = min(rows, r_begin + rows_per_split);
+  double acc[4] = {0, 0, 0, 0};
+  for (int r0 = r_begin; r0 < r_end; r0 += 32) {
+    for (int q = ty; q < 32; q += 8) {
+      const int r = r0 + q;
+      bool ok = r < r_end;
+      if (ok && ch >= 0) ok = pair_channel(s, r % s.Ppair) == ch;
+      As[q][tx] = (ok && k0 + tx < Ka) ? (A ? A[(size_t)r * lda + k0 + tx] : R(1)) : R(0);
+      Bs[q][tx] = (ok && n0 + tx < Nb) ? B[(size_t)r * ldb + n0 + tx] : R(0);
+    }
+    __syncthreads();
+    for (int q = 0; q < 32; ++q) {
+      const double b = (double)Bs[q][tx];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[e] += (double)As[q][ty + 8 * e] * b;
+    }
+    __syncthreads();
+  }
+  for (int e = 0; e < 4; ++e) {
+    const int k = k0 + ty + 8 * e, nn = n0 + tx;
+    if (k < Ka && nn < Nb) part[((size_t)blockIdx.z * Ka + k) * Nb + nn] = acc[e];
+  }
+}
+
+// grad[dst(k, n)] += sum_split part[split][k][n].  dst = base + k*Nb + n, or
+// for the stacked receiving maps the (channel, z) row split into three.
+__global__ void k_reduce_part(const double* __restrict__ part, int nsplit, int Ka, int Nb, double* __restrict__ grad,
+                              int64_t base, int64_t stride_c, int rows_per_c) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)Ka * Nb) return;
+  double acc = 0;
+  for (int sp = 0; sp < nsplit; ++sp) acc += part[(size_t)sp * Ka * Nb + i];
+  const int k = i / Nb, n = i % Nb;
+  int64_t dst;
+  if (rows_per_c > 0) {
+    const int c = k / rows_per_c, kk = k % rows_per_c;
+    dst = base + c * stride_c + (int64_t)kk * Nb + n;
+  } else {
+    dst = base + (int64_t)k * Nb + n;
+  }
+  grad[dst] += acc;
+}
+
+__global__ void k_add_to(double* __restrict__ grad, int64_t off, const double* __restrict__ v, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) grad[off + i] += v[i];
+}
+
+}  // namespace pnb
+
+using namespace pnb;
+
+
+// Y (+)= X W^T for W stored [Nout][Kd] (the backward of y = x W).
+template <typename R>
+__global__ void __launch_bounds__(256) k_linear_bt(const R* __restrict__ X, int ldx, const R* __restrict__ W, int ldw,
+                                                   R* __restrict__ Y, int ldy, int rows, int Kd, int Nout, int accumulate) {
+  __shared__ R As[16][64 + 1];
+  __shared__ R Bs[16][64 + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+  R acc[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  for (int k0 = 0; k0 < Kd; k0 += 16) {
+    for (int l = 0; l < 4; ++l) {
+      const int e = threadIdx.x + l * 256;
+      const int rr = e >> 4, kk = e & 15;
+      As[kk][rr] = (row0 + rr < rows && k0 + kk < Kd) ? X[(size_t)(row0 + rr) * ldx + k0 + kk] : R(0);
+      // B(k, n) = W[n][k]
+      const int cb = e >> 4, kb = e & 15;
+      Bs[kb][cb] = (k0 + kb < Kd && col0 + cb < Nout) ? W[(size_t)(col0 + cb) * ldw + k0 + kb] : R(0);
+    }
+    __syncthreads();
+    for (int kk = 0; kk < 16; ++kk) {
+      R a[4], b[4];
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < 4; ++i) {
+    const int gr = row0 + ty * 4 + i;
+    if (gr >= rows) continue;
+    for (int j = 0; j < 4; ++j) {
+      const int gc = col0 + tx * 4 + j;
+      if (gc >= Nout) continue;
+      R* y = Y + (size_t)gr * ldy + gc;
+      *y = accumulate ? *y + acc[i][j] : acc[i][j];
+    }
+  }
+}
+
+namespace {
+
+template <typename R>
+struct Tape {
+  int Wb;
+  double* geo;
+  double* phi;
+  double* u;
+  R *ef, *X, *H, *Z, *Ah, *wv;            // per layer stacks
+  R *kA1, *kS1, *kA2, *kS2, *F;           // kappa
+  R *Xs, *eA1, *eS1, *eA2, *eS2, *J;      // eta
+  R *dX, *dX2, *dH, *dZ, *dw, *dAh, *Sh, *dYr, *dF, *dJ, *dA, *dB, *dXs, *dAs, *dBs;
+  double* part;
+  size_t part_elems;
+  double* bias_tmp;
+  char* end;  // one past the last carved byte
+};
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename R>
+size_t tape_bytes_per_walker(const DevSys& s) {
+  const size_t N = s.N, D = s.D, Zd = s.Zd, L = s.L, P = s.Ppair, Hw = s.Hw, no = s.n_orb;
+  size_t e = 0;
+  e += P * 3 * s.K + (L + 1) * N * D + L * N * Zd + L * N * 3 * Zd + L * P * Hw + L * P * Zd;
+  e += 4 * N * D + N * no + 5 * D + 1;
+  e += 2 * N * D + N * Zd + N * 3 * Zd + P * Zd + 2 * P * Hw + N * s.M * Zd + N * no + 1 + 2 * N * D + 3 * D;
+  return e * sizeof(R) + (P * 4 + N * no * 5 + 1) * 8 + 64 * 24;
+}
+
+template <typename R>
+Tape<R> carve_tape(const DevSys& s, int Wb, void* base, size_t part_elems) {
+  Tape<R> t;
+  char* p = (char*)base;
+  const size_t W = Wb, N = s.N, D = s.D, Zd = s.Zd, L = s.L, P = s.Ppair, Hw = s.Hw, no = s.n_orb;
+  auto take = [&](size_t bytes) { char* q = p; p += al(bytes); return (void*)q; };
+  const size_t r = sizeof(R);
+  t.Wb = Wb;
+  t.geo = (double*)take(W * P * 4 * 8);
+  t.phi = (double*)take(W * N * no * 5 * 8);
+  t.u = (double*)take(W * 8);
+  t.ef = (R*)take(W * P * 3 * s.K * r);
+  t.X = (R*)take((L + 1) * W * N * D * r);
+  t.H = (R*)take(L * W * N * Zd * r + r);
+  t.Z = (R*)take(L * W * N * 3 * Zd * r + r);
+  t.Ah = (R*)take(L * W * P * Hw * r + r);
+  t.wv = (R*)take(L * W * P * Zd * r + r);
+  t.kA1 = (R*)take(W * N * D * r);
+  t.kS1 = (R*)take(W * N * D * r);
+  t.kA2 = (R*)take(W * N * D * r);
+  t.kS2 = (R*)take(W * N * D * r);
+  t.F = (R*)take(W * N * no * r);
+  t.Xs = (R*)take(W * D * r);
+  t.eA1 = (R*)take(W * D * r);
+  t.eS1 = (R*)take(W * D * r);
+  t.eA2 = (R*)take(W * D * r);
+  t.eS2 = (R*)take(W * D * r);
+  t.J = (R*)take(W * r);
+  t.dX = (R*)take(W * N * D * r);
+  t.dX2 = (R*)take(W * N * D * r);
+  t.dH = (R*)take(W * N * Zd * r);
+  t.dZ = (R*)take(W * N * 3 * Zd * r);
+  t.dw = (R*)take(W * P * Zd * r);
+  t.dAh = (R*)take(W * P * Hw * r);
+  t.Sh = (R*)take(W * P * Hw * r);
+  t.dYr = (R*)take(W * N * s.M * Zd * r);
+  t.dF = (R*)take(W * N * no * r);
+  t.dJ = (R*)take(W * r);
+  t.dA = (R*)take(W * N * D * r);
+  t.dB = (R*)take(W * N * D * r);
+  t.dXs = (R*)take(W * D * r);
+  t.dAs = (R*)take(W * D * r);
+  t.dBs = (R*)take(W * D * r);
+  t.part = (double*)take(part_elems * 8);
+  t.part_elems = part_elems;
+  t.bias_tmp = nullptr;
+  t.end = p;
+  return t;
+}
+
+// grad += sum_rows A^T B (or column sums of B when A is null) into the
+// parameter block at `base`; rows_per_c > 0 splits the K rows over three
+// parameter blocks stride_c apart (stacked receiving maps).
+template <typename R>
+int wgrad(Tape<R>& t, const R* A, int lda, const R* B, int ldb, int rows, int Ka, int Nb, const DevSys& s, int ch,
+          double* grad, int64_t base, int64_t stride_c, int rows_per_c, cudaStream_t st) {
+  if (rows <= 0) return PN_OK;
+  const size_t tile = (size_t)Ka * Nb;
+  int nsplit = std::max(1, std::min<int>((rows + 1023) / 1024, (int)(t.part_elems / tile)));
+  nsplit = std::min(nsplit, 1024);
+  const int rps = (rows + nsplit - 1) / nsplit;
+  dim3 grid((Nb + 31) / 32, (Ka + 31) / 32, nsplit);
+  PN_LAUNCH("k_wgrad", st, k_wgrad<R><<<grid, 256, 0, st>>>(A, lda, B, ldb, rows, Ka, Nb, rps, s, ch, t.part));
+  PN_LAUNCH("k_reduce_part", st, k_reduce_part<<<nblk(tile, 256), 256, 0, st>>>(t.part, nsplit, Ka, Nb, grad, base, stride_c, rows_per_c));
+  return PN_OK;
+}
+
+template <typename R>
+int linear_bt(const R* X, int ldx, const R* W, int ldw, R* Y, int ldy, int rows, int Kd, int Nout, int acc,
+              cudaStream_t st) {
+  if (rows <= 0) return PN_OK;
+  dim3 grid((Nout + 63) / 64, (rows + 63) / 64);
+  PN_LAUNCH("k_linear_bt", st, k_linear_bt<R><<<grid, 256, 0, st>>>(X, ldx, W, ldw, Y, ldy, rows, Kd, Nout, acc));
+  return PN_OK;
+}
+
+}  // namespace
+
+
+
+template <typename R>
+static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const double* r, const double* u, int Wn,
+                      double* grad, cudaStream_t st) {
+  const int N = s.N, D = s.D, Zd = s.Zd, L = s.L, P = s.Ppair, Hw = s.Hw, no = s.n_orb, K = s.K;
+  const NetOff& o = net.off;
+  const int rows = Wn * N;
+  const size_t WND = (size_t)Wn * N * D;
+  // ---------------- value pass with the tape
+  if (int e = pn_launch_geometry_orbitals(s, r, Wn, t.geo, t.phi, st)) return e;
+  if (int e = pn_launch_features_init<R>(s, net.p + o.x0, t.geo, Wn, t.ef, t.X, st)) return e;
+  for (int n = 0; n < L; ++n) {
+    R* Xn = t.X + (size_t)n * WND;
+    R* Xn1 = t.X + (size_t)(n + 1) * WND;
+    R* Hn = t.H + (size_t)n * rows * Zd;
+    R* Zn = t.Z + (size_t)n * rows * 3 * Zd;
+    R* Ahn = t.Ah + (size_t)n * Wn * P * Hw;
+    R* wn = t.wv + (size_t)n * Wn * P * Zd;
+    if (int e = pn_linear<R>(Xn, D, net.p + o.hW[n], Zd, net.p + o.hb[n], Hn, Zd, rows, D, Zd, 1, 0, st)) return e;
+    PN_LAUNCH("k_filter_tape", st, k_filter_tape<R><<<nblk((size_t)Wn * P, 8), 256, 0, st>>>(s, net, n, t.ef, Wn, Ahn, wn));
+    PN_LAUNCH("k_message_value", st, k_message_value<R><<<nblk((size_t)rows * Zd, 256), 256, 0, st>>>(s, net.p + o.Y, wn, Hn, Wn, Zn));
+    PN_CUDA(cudaMemcpyAsync(Xn1, Xn, WND * sizeof(R), cudaMemcpyDeviceToDevice, st));
+    if (int e = pn_linear<R>(Zn, 3 * Zd, net.Gcat + (size_t)n * 3 * Zd * D, D, net.Gb + (size_t)n * D, Xn1, D, rows,
+                             3 * Zd, D, 1, 1, st))
+      return e;
+  }
+  R* XL = t.X + (size_t)L * WND;
+  // kappa
+  if (int e = pn_linear<R>(XL, D, net.p + o.kW[0], D, net.p + o.kb[0], t.kA1, D, rows, D, D, 1, 0, st)) return e;
+  PN_LAUNCH("k_ssp_copy", st, k_ssp_copy<R><<<nblk(WND, 256), 256, 0, st>>>(t.kA1, t.kS1, WND));
+  if (int e = pn_linear<R>(t.kS1, D, net.p + o.kW[1], D, net.p + o.kb[1], t.kA2, D, rows, D, D, 1, 0, st)) return e;
+  PN_LAUNCH("k_ssp_copy", st, k_ssp_copy<R><<<nblk(WND, 256), 256, 0, st>>>(t.kA2, t.kS2, WND));
+  if (int e = pn_linear<R>(t.kS2, D, net.p + o.kW[2], no, net.p + o.kb[2], t.F, no, rows, D, no, 1, 0, st)) return e;
+  // eta
+  if (int e = pn_launch_sum_electrons<R>(XL, t.Xs, Wn, N, D, st)) return e;
+  if (int e = pn_linear<R>(t.Xs, D, net.p + o.eW[0], D, net.p + o.eb[0], t.eA1, D, Wn, D, D, 1, 0, st)) return e;
+  PN_LAUNCH("k_ssp_copy", st, k_ssp_copy<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.eA1, t.eS1, (size_t)Wn * D));
+  if (int e = pn_linear<R>(t.eS1, D, net.p + o.eW[1], D, net.p + o.eb[1], t.eA2, D, Wn, D, D, 1, 0, st)) return e;
+  PN_LAUNCH("k_ssp_copy", st, k_ssp_copy<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.eA2, t.eS2, (size_t)Wn * D));
+
+  // ---------------- backward
+  PN_LAUNCH("k_slater_bwd", st, k_slater_bwd<R><<<nblk(Wn, 32), 32, 0, st>>>(s, t.phi, t.F, u, Wn, t.dF, t.dJ));
+  // kappa head
+  if (int e = wgrad<R>(t, t.kS2, D, t.dF, no, rows, D, no, s, -1, grad, o.kW[2], 0, 0, st)) return e;
+  if (int e = wgrad<R>(t, nullptr, 0, t.dF, no, rows, 1, no, s, -1, grad, o.kb[2], 0, 0, st)) return e;
+  if (int e = linear_bt<R>(t.dF, no, net.p + o.kW[2], no, t.dA, D, rows, no, D, 0, st)) return e;
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dA, t.kA2, t.dA, WND));
+  if (int e = wgrad<R>(t, t.kS1, D, t.dA, D, rows, D, D, s, -1, grad, o.kW[1], 0, 0, st)) return e;
+  if (int e = wgrad<R>(t, nullptr, 0, t.dA, D, rows, 1, D, s, -1, grad, o.kb[1], 0, 0, st)) return e;
+  if (int e = linear_bt<R>(t.dA, D, net.p + o.kW[1], D, t.dB, D, rows, D, D, 0, st)) return e;
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dB, t.kA1, t.dB, WND));
+  if (int e = wgrad<R>(t, XL, D, t.dB, D, rows, D, D, s, -1, grad, o.kW[0], 0, 0, st)) return e;
+  if (int e = wgrad<R>(t, nullptr, 0, t.dB, D, rows, 1, D, s, -1, grad, o.kb[0], 0, 0, st)) return e;
+  if (int e = linear_bt<R>(t.dB, D, net.p + o.kW[0], D, t.dX, D, rows, D, D, 0, st)) return e;
+  // eta head (J = eta(sum_i x_i); dJ/d out = u)
+  if (int e = wgrad<R>(t, t.eS2, D, t.dJ, 1, Wn, D, 1, s, -1, grad, o.eW[2], 0, 0, st)) return e;
+  if (int e = wgrad<R>(t, nullptr, 0, t.dJ, 1, Wn, 1, 1, s, -1, grad, o.eb[2], 0, 0, st)) return e;
+  PN_LAUNCH("k_outer_row", st, k_outer_row<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dJ, net.p + o.eW[2], t.dAs, Wn, D));
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dAs, t.eA2, t.dAs, (size_t)Wn * D));
+  if (int e = wgrad<R>(t, t.eS1, D, t.dAs, D, Wn, D, D, s, -1, grad, o.eW[1], 0, 0, st)) return e;
+  if (int e = wgrad<R>(t, nullptr, 0, t.dAs, D, Wn, 1, D, s, -1, grad, o.eb[1], 0, 0, st)) return e;
+  if (int e = linear_bt<R>(t.dAs, D, net.p + o.eW[1], D, t.dBs, D, Wn, D, D, 0, st)) return e;
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dBs, t.eA1, t.dBs, (size_t)Wn * D));
+  if (int e = wgrad<R>(t, t.Xs, D, t.dBs, D, Wn, D, D, s, -1, grad, o.eW[0], 0, 0, st)) return e;
+  if (int e = wgrad<R>(t, nullptr, 0, t.dBs, D, Wn, 1, D, s, -1, grad, o.eb[0], 0, 0, st)) return e;
+  if (int e = linear_bt<R>(t.dBs, D, net.p + o.eW[0], D, t.dXs, D, Wn, D, D, 0, st)) return e;
+  PN_LAUNCH("k_bcast_add", st, k_bcast_add<R><<<nblk(WND, 256), 256, 0, st>>>(t.dX, t.dXs, Wn, N, D));
+  // interaction layers, last to first; t.dX holds d/dX^(n+1)
+  for (int n = L - 1; n >= 0; --n) {
+    R* Xn = t.X + (size_t)n * WND;
+    R* Hn = t.H + (size_t)n * rows * Zd;
+    R* Zn = t.Z + (size_t)n * rows * 3 * Zd;
+    R* Ahn = t.Ah + (size_t)n * Wn * P * Hw;
+    R* wn = t.wv + (size_t)n * Wn * P * Zd;
+    // receiving maps: X^(n+1) = X^(n) + [z_same z_anti z_nuc] Gcat + sum of biases
+    if (int e = wgrad<R>(t, Zn, 3 * Zd, t.dX, D, rows, 3 * Zd, D, s, -1, grad, o.GW[n][0], o.GW[n][1] - o.GW[n][0], Zd,
+                         st))
+      return e;
+    for (int c = 0; c < 3; ++c)
+      if (int e = wgrad<R>(t, nullptr, 0, t.dX, D, rows, 1, D, s, -1, grad, o.Gb[n][c], 0, 0, st)) return e;
+    if (int e = linear_bt<R>(t.dX, D, net.Gcat + (size_t)n * 3 * Zd * D, D, t.dZ, 3 * Zd, rows, D, 3 * Zd, 0, st))
+      return e;
+    // messages
+    PN_LAUNCH("k_msg_bwd_w", st, k_msg_bwd_w<R><<<nblk((size_t)Wn * P * Zd, 256), 256, 0, st>>>(s, net.p + o.Y, Hn, t.dZ, Wn, t.dw));
+    PN_LAUNCH("k_msg_bwd_h", st, k_msg_bwd_h<R><<<nblk((size_t)rows * Zd, 256), 256, 0, st>>>(s, wn, t.dZ, Wn, t.dH, t.dYr));
+    if (int e = wgrad<R>(t, nullptr, 0, t.dYr, s.M * Zd, rows, 1, s.M * Zd, s, -1, grad, o.Y, 0, 0, st)) return e;
+    // filters, per channel
+    PN_LAUNCH("k_filter_bwd", st, k_filter_bwd<R><<<nblk((size_t)Wn * P, 8), 256, 0, st>>>(s, net, n, Ahn, t.dw, Wn, t.dAh, t.Sh));
+    for (int c = 0; c < 3; ++c) {
+      if (int e = wgrad<R>(t, t.Sh, Hw, t.dw, Zd, Wn * P, Hw, Zd, s, c, grad, o.W2[n][c], 0, 0, st)) return e;
+      if (int e = wgrad<R>(t, nullptr, 0, t.dw, Zd, Wn * P, 1, Zd, s, c, grad, o.b2[n][c], 0, 0, st)) return e;
+      if (int e = wgrad<R>(t, t.ef, 3 * K, t.dAh, Hw, Wn * P, K, Hw, s, c, grad, o.W1[n][c], 0, 0, st)) return e;
+      if (int e = wgrad<R>(t, nullptr, 0, t.dAh, Hw, Wn * P, 1, Hw, s, c, grad, o.b1[n][c], 0, 0, st)) return e;
+    }
+    // input map h
+    if (int e = wgrad<R>(t, Xn, D, t.dH, Zd, rows, D, Zd, s, -1, grad, o.hW[n], 0, 0, st)) return e;
+    if (int e = wgrad<R>(t, nullptr, 0, t.dH, Zd, rows, 1, Zd, s, -1, grad, o.hb[n], 0, 0, st)) return e;
+    // d/dX^(n) = d/dX^(n+1) + dH Wh^T
+    if (int e = linear_bt<R>(t.dH, Zd, net.p + o.hW[n], Zd, t.dX, D, rows, Zd, D, 1, st)) return e;
+  }
+  // shared electron embedding
+  if (int e = wgrad<R>(t, nullptr, 0, t.dX, D, rows, 1, D, s, -1, grad, o.x0, 0, 0, st)) return e;
+  return PN_OK;
+}
+
+template <typename R>
+static int grad_impl(pn_system_s* sys, const double* r, int W, const double* cot, double* grad, size_t budget,
+                     cudaStream_t st) {
+  const DevSys& s = sys->ds;
+  const DevNet<R> net = pn_devnet<R>(sys);
+  const int N = s.N;
+  const size_t per = tape_bytes_per_walker<R>(s);
+  if (budget == 0) budget = sys->work_bytes;
+  // partial tiles: enough for the largest weight block times 64 splits
+  size_t maxKN = std::max<size_t>({(size_t)s.D * s.D, (size_t)3 * s.Zd * s.D, (size_t)s.K * s.Hw,
+                                   (size_t)s.Hw * s.Zd, (size_t)s.D * s.n_orb, (size_t)s.M * s.Zd, 1});
+  const size_t part_elems = maxKN * 64;
+  const size_t fixed = part_elems * 8 + 4096 * 64;
+  if (budget <= fixed + per) {
+    pn_set_error("grad: memory budget %zu below one walker's tape (%zu bytes)", budget, fixed + per);
+    return PN_EINVAL;
+  }
+  int Wb = (int)std::min<size_t>((size_t)W, (budget - fixed) / per);
+  Wb = std::max(1, Wb);
+  const size_t bytes = fixed + per * Wb + 65536;
+  if (bytes > sys->tape_bytes) {
+    if (sys->tape_mem) cudaFree(sys->tape_mem);
+    sys->tape_mem = nullptr;
+    sys->tape_bytes = 0;
+    if (cudaMalloc(&sys->tape_mem, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      pn_set_error("grad: cannot allocate %zu bytes of tape", bytes);
+      return PN_ENOMEM;
+    }
+    sys->tape_bytes = bytes;
+  }
+  Tape<R> t = carve_tape<R>(s, Wb, sys->tape_mem, part_elems);
+  if (t.end > (char*)sys->tape_mem + sys->tape_bytes) {
+    pn_set_error("grad: tape layout (%zu bytes) exceeds its allocation (%zu)", (size_t)(t.end - (char*)sys->tape_mem),
+                 sys->tape_bytes);
+    return PN_EINVAL;
+  }
+  const bool rdev = pn_is_device_ptr(r), udev = pn_is_device_ptr(cot), gdev = pn_is_device_ptr(grad);
+  double* gd = grad;
+  if (!gdev) {
+    PN_CUDA(cudaMallocAsync((void**)&gd, (size_t)sys->off.total * 8, st));
+  }
+  PN_CUDA(cudaMemsetAsync(gd, 0, (size_t)sys->off.total * 8, st));
+  // r staging reuses the system workspace's position buffer when needed
+  double* rstage = nullptr;
+  if (!rdev) PN_CUDA(cudaMallocAsync((void**)&rstage, (size_t)Wb * N * 3 * 8, st));
+  for (int c0 = 0; c0 < W; c0 += Wb) {
+    const int Wn = std::min(Wb, W - c0);
+    const double* rc = r + (size_t)c0 * N * 3;
+    if (!rdev) {
+      PN_CUDA(cudaMemcpyAsync(rstage, rc, (size_t)Wn * N * 3 * 8, cudaMemcpyHostToDevice, st));
+      rc = rstage;
+    }
+    PN_CUDA(cudaMemcpyAsync(t.u, cot + c0, (size_t)Wn * 8, udev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (int e = grad_chunk<R>(s, net, t, rc, t.u, Wn, gd, st)) return e;
+  }
+  if (!gdev) {
+    PN_CUDA(cudaMemcpyAsync(grad, gd, (size_t)sys->off.total * 8, cudaMemcpyDeviceToHost, st));
+    PN_CUDA(cudaFreeAsync(gd, st));
+  }
+  if (rstage) PN_CUDA(cudaFreeAsync(rstage, st));
+  if (!rdev || !udev || !gdev) PN_CUDA(cudaStreamSynchronize(st));
+  return PN_OK;
+}
+
+extern "C" int pn_grad_logpsi(pn_system_t s, const double* r, int W, const double* cot, double* grad, size_t budget,
+                              void* stream) {
+  if (!s || W < 0 || !grad || (W > 0 && (!r || !cot))) { pn_set_error("bad arguments"); return PN_EINVAL; }
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != s->device) PN_CUDA(cudaSetDevice(s->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (W == 0) {
+    PN_CUDA(cudaMemsetAsync(grad, 0, (size_t)s->off.total * 8, st));
+    return PN_OK;
+  }
+  return s->precision == PN_FP64 ? grad_impl<double>(s, r, W, cot, grad, budget, st)
+                                 : grad_impl<float>(s, r, W, cot, grad, budget, st);
+}

@@ -1,0 +1,746 @@
+// Forward pass of the ansatz over a chunk of walkers, in value mode (T = 1)
+// or jet mode (T = 3N + 2 rows: value, d/dr_{k,a} for every coordinate,
+// Laplacian).  The network runs in R (double or float); orbitals,
+// geometry, determinants and the final combination run in double.
+//
+// Jet row index t: 0 value, 1 + 3k + a derivative along coordinate a of
+// electron k, 3N + 1 Laplacian (sum over all 3N second derivatives).
+#include <math.h>
+
+#include "kernels.cuh"
+#include "pn_internal.cuh"
+
+namespace pnk {
+
+// ------------------------------------------------------------ geometry
+// geo[w][p] = (d, unit vector).  Electron pairs a<b store (r_a - r_b)/d,
+// electron-nucleus pairs (i, I) store (r_i - R_I)/d.
+__global__ void k_geometry(DevSys s, const double* __restrict__ r, int Wn, double* __restrict__ geo) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Wn * s.Ppair) return;
+  int w = idx / s.Ppair, p = idx - w * s.Ppair;
+  const double* rw = r + (size_t)w * s.N * 3;
+  double v[3];
+  if (p < s.Pee) {
+    int a = 0, rem = p;
+    while (rem >= s.N - 1 - a) { rem -= s.N - 1 - a; ++a; }
+    int b = a + 1 + rem;
+    for (int x = 0; x < 3; ++x) v[x] = rw[3 * a + x] - rw[3 * b + x];
+  } else {
+    int q = p - s.Pee, i = q / s.M, I = q - i * s.M;
+    for (int x = 0; x < 3; ++x) v[x] = rw[3 * i + x] - s.R[3 * I + x];
+  }
+  double d = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  double inv = 1.0 / d;
+  double* g = geo + (size_t)idx * 4;
+  g[0] = d;
+  g[1] = v[0] * inv;
+  g[2] = v[1] * inv;
+  g[3] = v[2] * inv;
+}
+
+// ------------------------------------------------------------- orbitals
+// phi[w][i][mu][0..4] = value, gradient (3), Laplacian of the cusp-spliced
+// molecular orbital mu at electron i (one thread per electron).
+__device__ inline double pw(double x, int n) { return n == 0 ? 1.0 : (n == 1 ? x : x * x); }
+
+__global__ void k_orbitals(DevSys s, const double* __restrict__ r, int Wn, double* __restrict__ phi) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Wn * s.N) return;
+  const double* re = r + (size_t)idx * 3;
+  double acc[PN_MAX_ORBITALS * 5];
+  const int no = s.n_orb;
+  for (int k = 0; k < no * 5; ++k) acc[k] = 0.0;
+  int Ic = -1;
+  double vc[3] = {0, 0, 0}, dcn = 0;
+  if (s.use_cusp) {
+    for (int I = 0; I < s.M; ++I) {
+      double v0 = re[0] - s.R[3 * I], v1 = re[1] - s.R[3 * I + 1], v2 = re[2] - s.R[3 * I + 2];
+      double d = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+      if (d < s.cusp_rc[I]) { Ic = I; vc[0] = v0; vc[1] = v1; vc[2] = v2; dcn = d; }
+    }
+  }
+  for (int sh = 0; sh < s.n_shells; ++sh) {
+    const int c = s.sh_center[sh], l = s.sh_l[sh], np = s.sh_nprim[sh], po = s.sh_poff[sh], bo = s.sh_boff[sh];
+    const double v[3] = {re[0] - s.R[3 * c], re[1] - s.R[3 * c + 1], re[2] - s.R[3 * c + 2]};
+    const double r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    if (l == -1) {
+      const double zeta = s.pexp[po], d = sqrt(r2);
+      const double e = s.pcoef[po] * exp(-zeta * d);
+      const double gfac = -zeta * e / d;
+      const double jet[5] = {e, gfac * v[0], gfac * v[1], gfac * v[2], zeta * zeta * e - 2.0 * zeta * e / d};
+      const double* mrow = s.mo + (size_t)bo * no;
+      for (int mu = 0; mu < no; ++mu)
+        for (int q = 0; q < 5; ++q) acc[mu * 5 + q] += mrow[mu] * jet[q];
+      continue;
+    }
+    double E0 = 0, E1 = 0, E2 = 0;
+    for (int k = 0; k < np; ++k) {
+      const double a = s.pexp[po + k];
+      const double e = s.pcoef[po + k] * exp(-a * r2);
+      E0 += e;
+      E1 += a * e;
+      E2 += a * a * e;
+    }
+    const bool skip_s = (l == 0 && c == Ic);  // replaced inside the cusp sphere
+    const int nc = l == 0 ? 1 : (l == 1 ? 3 : 6);
+    for (int cc = 0; cc < nc; ++cc) {
+      int ex, ey, ez;
+      if (l == 0) { ex = ey = ez = 0; }
+      else if (l == 1) { ex = cc == 0; ey = cc == 1; ez = cc == 2; }
+      else {
+        const int t2[6][3] = {{2, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
+        ex = t2[cc][0]; ey = t2[cc][1]; ez = t2[cc][2];
+      }
+      const double px = pw(v[0], ex), py = pw(v[1], ey), pz = pw(v[2], ez);
+      const double P = px * py * pz;
+      const double dPx = ex ? ex * pw(v[0], ex - 1) * py * pz : 0.0;
+      const double dPy = ey ? ey * px * pw(v[1], ey - 1) * pz : 0.0;
+      const double dPz = ez ? ez * px * py * pw(v[2], ez - 1) : 0.0;
+      const double lapP = (ex == 2 ? 2.0 * py * pz : 0.0) + (ey == 2 ? 2.0 * px * pz : 0.0) + (ez == 2 ? 2.0 * px * py : 0.0);
+      // chi = P E(r^2): grad = grad P E0 - 2 v P E1,
+      // lap = lap P E0 - 4 l P E1 + P (4 r^2 E2 - 6 E1)
+      const double jet[5] = {P * E0, dPx * E0 - 2.0 * v[0] * P * E1, dPy * E0 - 2.0 * v[1] * P * E1,
+                             dPz * E0 - 2.0 * v[2] * P * E1,
+                             lapP * E0 - 4.0 * l * P * E1 + P * (4.0 * r2 * E2 - 6.0 * E1)};
+      const double* mrow = s.mo + (size_t)(bo + cc) * no;
+      for (int mu = 0; mu < no; ++mu) {
+        if (skip_s && s.cusp_on[Ic * no + mu]) continue;
+        for (int q = 0; q < 5; ++q) acc[mu * 5 + q] += mrow[mu] * jet[q];
+      }
+    }
+  }
+  if (Ic >= 0) {
+    const double d = dcn, inv = 1.0 / d;
+    for (int mu = 0; mu < no; ++mu) {
+      const int k = Ic * no + mu;
+      if (!s.cusp_on[k]) continue;
+      const double* a = s.cusp_a + (size_t)k * 5;
+      const double p = a[0] + d * (a[1] + d * (a[2] + d * (a[3] + d * a[4])));
+      const double p1 = a[1] + d * (2.0 * a[2] + d * (3.0 * a[3] + d * 4.0 * a[4]));
+      const double p2 = 2.0 * a[2] + d * (6.0 * a[3] + d * 12.0 * a[4]);
+      const double f = s.cusp_s[k] * exp(p);
+      const double f1 = f * p1, f2 = f * (p2 + p1 * p1);
+      acc[mu * 5 + 0] += s.cusp_C[k] + f;
+      acc[mu * 5 + 1] += f1 * vc[0] * inv;
+      acc[mu * 5 + 2] += f1 * vc[1] * inv;
+      acc[mu * 5 + 3] += f1 * vc[2] * inv;
+      acc[mu * 5 + 4] += f2 + 2.0 * f1 * inv;
+    }
+  }
+  double* o = phi + (size_t)idx * no * 5;
+  for (int k = 0; k < no * 5; ++k) o[k] = acc[k];
+}
+
+// ------------------------------------------------------------- features
+// e_k(d) = d^2 exp(-d - (d - mu_k)^2 / sigma_k^2) and its first two
+// derivatives in d, for every pair: efeat[w][p][c][k], c = value, d/dd, d2/dd2.
+template <typename R>
+__global__ void k_features(DevSys s, const double* __restrict__ geo, int Wn, int jet, R* __restrict__ ef) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t total = (size_t)Wn * s.Ppair * s.K;
+  if (idx >= total) return;
+  const int k = idx % s.K;
+  const size_t wp = idx / s.K;
+  const double d = geo[wp * 4];
+  const double mu = s.feat_mu[k], is2 = s.feat_isig2[k];
+  const double E = exp(-d - (d - mu) * (d - mu) * is2);
+  R* o = ef + wp * 3 * s.K;
+  o[k] = (R)(d * d * E);
+  if (jet) {
+    const double q = -1.0 - 2.0 * (d - mu) * is2;  // derivative of the exponent
+    o[s.K + k] = (R)(E * (2.0 * d + d * d * q));
+    o[2 * s.K + k] = (R)(E * (2.0 + 4.0 * d * q + d * d * (q * q - 2.0 * is2)));
+  }
+}
+
+template <typename R>
+__device__ inline R ssp_(R x) {
+  return (x > R(0) ? x : R(0)) + log1p(exp(-fabs(x))) - R(0.69314718055994530942);
+}
+template <typename R>
+__device__ inline R sigm_(R x) { return R(1) / (R(1) + exp(-x)); }
+
+// ------------------------------------------------------------- filters
+// w^{(n,c)}(e) = W2 ssp(W1 e + b1) + b2 for every pair, carrying the jet in
+// the scalar distance (value, d/dd, d2/dd2).  One warp per pair row.
+// Channel: same-spin electron pair 0, opposite spin 1, electron-nucleus 2.
+constexpr int FW = 8;  // warps per block
+
+template <typename R>
+__global__ void __launch_bounds__(FW * 32) k_filter(DevSys s, DevNet<R> net, int n, const R* __restrict__ ef,
+                                                    int Wn, int jet, R* __restrict__ wj) {
+  __shared__ R sh_e[FW][3 * 64];
+  __shared__ R sh_h[FW][3 * 128];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const size_t row = (size_t)blockIdx.x * FW + wid;
+  if (row >= (size_t)Wn * s.Ppair) return;
+  const int p = row % s.Ppair;
+  int ch;
+  if (p >= s.Pee) ch = 2;
+  else {
+    int a = 0, rem = p;
+    while (rem >= s.N - 1 - a) { rem -= s.N - 1 - a; ++a; }
+    int b = a + 1 + rem;
+    ch = ((a < s.n_up) == (b < s.n_up)) ? 0 : 1;
+  }
+  const int K = s.K, Hw = s.Hw, Zd = s.Zd;
+  const int nc = jet ? 3 : 1;
+  const R* e = ef + row * 3 * K;
+  for (int k = lane; k < K; k += 32)
+    for (int c = 0; c < nc; ++c) sh_e[wid][c * K + k] = e[c * K + k];
+  __syncwarp();
+  const R* W1 = net.p + net.off.W1[n][ch];
+  const R* b1 = net.p + net.off.b1[n][ch];
+  const R* W2 = net.p + net.off.W2[n][ch];
+  const R* b2 = net.p + net.off.b2[n][ch];
+  for (int h = lane; h < Hw; h += 32) {
+    R a0 = b1[h], a1 = 0, a2 = 0;
+    for (int k = 0; k < K; ++k) {
+      const R wv = W1[k * Hw + h];
+      a0 += sh_e[wid][k] * wv;
+      if (jet) {
+        a1 += sh_e[wid][K + k] * wv;
+        a2 += sh_e[wid][2 * K + k] * wv;
+      }
+    }
+    const R sg = sigm_(a0);
+    sh_h[wid][h] = ssp_(a0);
+    if (jet) {
+      sh_h[wid][Hw + h] = sg * a1;
+      sh_h[wid][2 * Hw + h] = sg * a2 + sg * (R(1) - sg) * a1 * a1;
+    }
+  }
+  __syncwarp();
+  R* o = wj + row * 3 * Zd;
+  for (int z = lane; z < Zd; z += 32) {
+    R o0 = b2[z], o1 = 0, o2 = 0;
+    for (int h = 0; h < Hw; ++h) {
+      const R wv = W2[h * Zd + z];
+      o0 += sh_h[wid][h] * wv;
+      if (jet) {
+        o1 += sh_h[wid][Hw + h] * wv;
+        o2 += sh_h[wid][2 * Hw + h] * wv;
+      }
+    }
+    o[z] = o0;
+    if (jet) {
+      o[Zd + z] = o1;
+      o[2 * Zd + z] = o2;
+    }
+  }
+}
+
+// --------------------------------------------------------------- linear
+// Y[rows][Nout] (+)= X[rows][Kd] W[Kd][Nout] + b on value rows (row % T == 0).
+// 64x64 output tile, 16-deep k tiles, 4x4 outputs per thread.
+template <typename R>
+__global__ void __launch_bounds__(256) k_linear(const R* __restrict__ X, int ldx, const R* __restrict__ Wt, int ldw,
+                                                const R* __restrict__ bias, R* __restrict__ Y, int ldy, int rows,
+                                                int Kd, int Nout, int T, int accumulate) {
+  __shared__ R As[16][64 + 1];
+  __shared__ R Bs[16][64];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+  R acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  for (int k0 = 0; k0 < Kd; k0 += 16) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int e = threadIdx.x + l * 256;
+      const int rr = e >> 4, kk = e & 15;
+      const int gr = row0 + rr, gk = k0 + kk;
+      As[kk][rr] = (gr < rows && gk < Kd) ? X[(size_t)gr * ldx + gk] : R(0);
+      const int kb = e >> 6, cb = e & 63;
+      const int gkb = k0 + kb, gc = col0 + cb;
+      Bs[kb][cb] = (gkb < Kd && gc < Nout) ? Wt[(size_t)gkb * ldw + gc] : R(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      R a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gr = row0 + ty * 4 + i;
+    if (gr >= rows) continue;
+    const bool val = (gr % T) == 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gc = col0 + tx * 4 + j;
+      if (gc >= Nout) continue;
+      R v = acc[i][j] + ((bias && val) ? bias[gc] : R(0));
+      R* y = Y + (size_t)gr * ldy + gc;
+      *y = accumulate ? *y + v : v;
+    }
+  }
+}
+
+// x^(0): the shared electron embedding on value rows, zero derivatives.
+template <typename R>
+__global__ void k_init_x(const R* __restrict__ x0, R* __restrict__ X, size_t groups, int T, int D) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= groups * T * D) return;
+  const int d = idx % D;
+  const int t = (idx / D) % T;
+  X[idx] = t == 0 ? x0[d] : R(0);
+}
+
+// ------------------------------------------------------------- messages
+// z_i^{same|anti} = sum_j w_ij * h_j, z_i^nuc = sum_I w_iI * Y_I with the
+// product rule through the jet.  Zb[w][i][t][c*Zd + z].
+template <typename R>
+__global__ void k_message(DevSys s, const R* __restrict__ Y, const double* __restrict__ geo, const R* __restrict__ wj,
+                          const R* __restrict__ H, int ldH, int Wn, int T, R* __restrict__ Zb, int ldZ) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int Zd = s.Zd, N = s.N;
+  if (idx >= (size_t)Wn * N * T * Zd) return;
+  const int z = idx % Zd;
+  size_t q = idx / Zd;
+  const int t = q % T;
+  q /= T;
+  const int i = q % N;
+  const int w = q / N;
+  const int lap = T - 1;
+  int tk = -1, ta = 0;
+  if (t > 0 && t < lap) { tk = (t - 1) / 3; ta = (t - 1) % 3; }
+  const bool si = i < s.n_up;
+  R zs = 0, za = 0, zn = 0;
+  const R* Hw_ = H + (size_t)w * N * T * ldH;
+  const double* gw = geo + (size_t)w * s.Ppair * 4;
+  const R* ww = wj + (size_t)w * s.Ppair * 3 * Zd;
+  for (int j = 0; j < N; ++j) {
+    if (j == i) continue;
+    int p;
+    double sgn;
+    if (i < j) { p = pn_pair_index(i, j, N); sgn = 1.0; }
+    else { p = pn_pair_index(j, i, N); sgn = -1.0; }
+    const double* g = gw + p * 4;
+    const R w0 = ww[(size_t)p * 3 * Zd + z];
+    const R* hj = Hw_ + (size_t)j * T * ldH;
+    const R h0 = hj[z];
+    R v;
+    if (t == 0) {
+      v = w0 * h0;
+    } else if (t < lap) {
+      const R w1 = ww[(size_t)p * 3 * Zd + Zd + z];
+      // unit vector u = (r_i - r_j)/d
+      const R u = (R)(sgn * g[1 + ta]);
+      const R dd = (tk == i) ? u : ((tk == j) ? -u : R(0));
+      v = w1 * dd * h0 + w0 * hj[(size_t)t * ldH + z];
+    } else {
+      const R w1 = ww[(size_t)p * 3 * Zd + Zd + z];
+      const R w2 = ww[(size_t)p * 3 * Zd + 2 * Zd + z];
+      const R d = (R)g[0];
+      R cross = 0;
+      for (int a = 0; a < 3; ++a) {
+        const R u = (R)(sgn * g[1 + a]);
+        cross += u * (hj[(size_t)(1 + 3 * i + a) * ldH + z] - hj[(size_t)(1 + 3 * j + a) * ldH + z]);
+      }
+      v = (R(2) * w2 + R(4) * w1 / d) * h0 + w0 * hj[(size_t)lap * ldH + z] + R(2) * w1 * cross;
+    }
+    if ((j < s.n_up) == si) zs += v; else za += v;
+  }
+  for (int I = 0; I < s.M; ++I) {
+    const int p = s.Pee + i * s.M + I;
+    const double* g = gw + p * 4;
+    const R y = Y[I * Zd + z];
+    const R* wp = ww + (size_t)p * 3 * Zd;
+    if (t == 0) zn += wp[z] * y;
+    else if (t < lap) {
+      if (tk == i) zn += wp[Zd + z] * (R)g[1 + ta] * y;
+    } else {
+      zn += (wp[2 * Zd + z] + R(2) * wp[Zd + z] / (R)g[0]) * y;
+    }
+  }
+  R* o = Zb + ((size_t)(w * N + i) * T + t) * ldZ;
+  o[z] = zs;
+  o[Zd + z] = za;
+  o[2 * Zd + z] = zn;
+}
+
+// ---------------------------------------------------- activation on a jet
+// s = ssp(a): s_t = sigma(a) a_t, lap s = sigma(a) lap a + sigma'(a) sum_t a_t^2.
+template <typename R>
+__global__ void k_ssp_jet(R* __restrict__ A, int ld, size_t groups, int T, int dim) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= groups * dim) return;
+  const int d = idx % dim;
+  const size_t g = idx / dim;
+  R* a = A + g * T * ld + d;
+  const R a0 = a[0];
+  const R sg = sigm_(a0);
+  a[0] = ssp_(a0);
+  if (T == 1) return;
+  R sq = 0;
+  for (int t = 1; t < T - 1; ++t) {
+    const R v = a[(size_t)t * ld];
+    sq += v * v;
+    a[(size_t)t * ld] = sg * v;
+  }
+  a[(size_t)(T - 1) * ld] = sg * a[(size_t)(T - 1) * ld] + sg * (R(1) - sg) * sq;
+}
+
+// Xs[w][t][d] = sum_i X[w][i][t][d]
+template <typename R>
+__global__ void k_sum_electrons(const R* __restrict__ X, R* __restrict__ Xs, int Wn, int N, int T, int D) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)Wn * T * D) return;
+  const int d = idx % D;
+  const int t = (idx / D) % T;
+  const int w = idx / ((size_t)D * T);
+  R acc = 0;
+  for (int i = 0; i < N; ++i) acc += X[(((size_t)w * N + i) * T + t) * D + d];
+  Xs[idx] = acc;
+}
+
+// ----------------------------------------------------------- determinants
+// One thread per (walker, determinant, spin).  A[a][b] = phi~(e0 + a, occ_b),
+// LU with partial pivoting; jet mode adds grad_t ln|det| = tr(A^-1 dA_t) and
+// lap ln|det| = tr(A^-1 lap A) - sum_t tr((A^-1 dA_t)^2).
+// det[w][p][s] = {ln|det|, sign, lap, grad[3N]}.
+template <typename R>
+__global__ void k_slater(DevSys s, const double* __restrict__ phi, const R* __restrict__ F, int Wn, int T, int jet,
+                         double* __restrict__ det) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Wn * s.n_det * 2) return;
+  const int sg = idx & 1;
+  const int p = (idx >> 1) % s.n_det;
+  const int w = (idx >> 1) / s.n_det;
+  const int N = s.N, no = s.n_orb;
+  const int ns = sg ? s.n_dn : s.n_up;
+  const int e0 = sg ? s.n_up : 0;
+  const int stride = 3 + 3 * N;
+  double* out = det + (size_t)idx * stride;
+  if (ns == 0) {
+    out[0] = 0; out[1] = 1; out[2] = 0;
+    if (jet) for (int t = 0; t < 3 * N; ++t) out[3 + t] = 0;
+    return;
+  }
+  const int* occ = s.occ + p * N + e0;
+  constexpr int NS = PN_MAX_SPIN;
+  double LU[NS * NS];
+  int perm[NS];
+  const double* phw = phi + (size_t)w * N * no * 5;
+  const R* Fw = F + (size_t)w * N * T * no;
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b < ns; ++b) {
+      const int i = e0 + a, mu = occ[b];
+      LU[a * ns + b] = phw[(i * no + mu) * 5] * (1.0 + (double)Fw[(size_t)i * T * no + mu]);
+    }
+  double ld = 0, sign = 1;
+  bool sing = false;
+  for (int c = 0; c < ns; ++c) perm[c] = c;
+  for (int c = 0; c < ns; ++c) {
+    int best = c;
+    double bv = fabs(LU[c * ns + c]);
+    for (int rr = c + 1; rr < ns; ++rr) {
+      const double v = fabs(LU[rr * ns + c]);
+      if (v > bv) { bv = v; best = rr; }
+    }
+    if (!(bv > 0.0)) { sing = true; break; }
+    if (best != c) {
+      for (int k = 0; k < ns; ++k) {
+        const double t0 = LU[c * ns + k];
+        LU[c * ns + k] = LU[best * ns + k];
+        LU[best * ns + k] = t0;
+      }
+      const int tp = perm[c]; perm[c] = perm[best]; perm[best] = tp;
+      sign = -sign;
+    }
+    const double piv = LU[c * ns + c];
+    if (piv < 0) sign = -sign;
+    ld += log(fabs(piv));
+    for (int rr = c + 1; rr < ns; ++rr) {
+      const double f = LU[rr * ns + c] / piv;
+      LU[rr * ns + c] = f;
+      for (int k = c + 1; k < ns; ++k) LU[rr * ns + k] -= f * LU[c * ns + k];
+    }
+  }
+  if (sing) {
+    out[0] = -INFINITY; out[1] = 0; out[2] = 0;
+    if (jet) for (int t = 0; t < 3 * N; ++t) out[3 + t] = 0;
+    return;
+  }
+  out[0] = ld;
+  out[1] = sign;
+  if (!jet) return;
+  // inverse: solve A X = I with the factors (P A = L U)
+  double Ai[NS * NS];
+  for (int col = 0; col < ns; ++col) {
+    double y[NS];
+    for (int rr = 0; rr < ns; ++rr) {
+      double v = (perm[rr] == col) ? 1.0 : 0.0;
+      for (int k = 0; k < rr; ++k) v -= LU[rr * ns + k] * y[k];
+      y[rr] = v;
+    }
+    for (int rr = ns - 1; rr >= 0; --rr) {
+      double v = y[rr];
+      for (int k = rr + 1; k < ns; ++k) v -= LU[rr * ns + k] * y[k];
+      y[rr] = v / LU[rr * ns + rr];
+    }
+    for (int rr = 0; rr < ns; ++rr) Ai[rr * ns + col] = y[rr];
+  }
+  const int lap = T - 1;
+  // tr(A^-1 lap A)
+  double trl = 0;
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b < ns; ++b) {
+      const int i = e0 + a, mu = occ[b];
+      const double* ph = phw + (i * no + mu) * 5;
+      const R* f = Fw + (size_t)i * T * no + mu;
+      const double f0 = 1.0 + (double)f[0];
+      double l = ph[4] * f0 + ph[0] * (double)f[(size_t)lap * no];
+      for (int x = 0; x < 3; ++x) l += 2.0 * ph[1 + x] * (double)f[(size_t)(1 + 3 * i + x) * no];
+      trl += Ai[b * ns + a] * l;
+    }
+  double lsum = trl;
+  for (int t = 1; t < lap; ++t) {
+    const int tk = (t - 1) / 3, ta = (t - 1) % 3;
+    double dA[NS * NS];
+    for (int a = 0; a < ns; ++a)
+      for (int b = 0; b < ns; ++b) {
+        const int i = e0 + a, mu = occ[b];
+        const double* ph = phw + (i * no + mu) * 5;
+        const R* f = Fw + (size_t)i * T * no + mu;
+        double v = ph[0] * (double)f[(size_t)t * no];
+        if (tk == i) v += ph[1 + ta] * (1.0 + (double)f[0]);
+        dA[a * ns + b] = v;
+      }
+    double B[NS * NS];
+    double tr = 0;
+    for (int a = 0; a < ns; ++a)
+      for (int b = 0; b < ns; ++b) {
+        double v = 0;
+        for (int c = 0; c < ns; ++c) v += Ai[a * ns + c] * dA[c * ns + b];
+        B[a * ns + b] = v;
+        if (a == b) tr += v;
+      }
+    double tr2 = 0;
+    for (int a = 0; a < ns; ++a)
+      for (int b = 0; b < ns; ++b) tr2 += B[a * ns + b] * B[b * ns + a];
+    out[3 + t - 1] = tr;
+    lsum -= tr2;
+  }
+  out[2] = lsum;
+}
+
+// ------------------------------------------------------------ combination
+// ln|psi| = gamma + J + ln|sum_p c_p s_p e^{ld_p}| (signed log-sum-exp over
+// determinants) and, in jet mode, E_loc = -1/2 (lap ln|psi| + |grad|^2) + V.
+template <typename R>
+__global__ void k_combine(DevSys s, const double* __restrict__ geo, const double* __restrict__ det,
+                          const R* __restrict__ Jj, int Wn, int T, int jet, double* __restrict__ logabs,
+                          double* __restrict__ sign, double* __restrict__ eloc, int* __restrict__ status) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= Wn) return;
+  const int N = s.N, nd = s.n_det, stride = 3 + 3 * N;
+  const double* dw = det + (size_t)w * nd * 2 * stride;
+  double m = -INFINITY;
+  for (int p = 0; p < nd; ++p) {
+    const double* u = dw + (size_t)(2 * p) * stride;
+    const double* d = u + stride;
+    if (s.ci[p] != 0.0 && u[1] != 0.0 && d[1] != 0.0) m = fmax(m, u[0] + d[0]);
+  }
+  double S = 0;
+  if (m > -INFINITY)
+    for (int p = 0; p < nd; ++p) {
+      const double* u = dw + (size_t)(2 * p) * stride;
+      const double* d = u + stride;
+      if (u[1] != 0.0 && d[1] != 0.0) S += s.ci[p] * u[1] * d[1] * exp(u[0] + d[0] - m);
+    }
+  const double* gw = geo + (size_t)w * s.Ppair * 4;
+  // electronic cusp factor gamma and the Coulomb potential
+  double gam = 0, V = s.Vnn;
+  for (int a = 0; a < N; ++a)
+    for (int b = a + 1; b < N; ++b) {
+      const double d = gw[pn_pair_index(a, b, N) * 4];
+      V += 1.0 / d;
+      if (s.use_gamma) {
+        const double c = ((a < s.n_up) == (b < s.n_up)) ? 0.25 : 0.5;
+        gam -= c / (1.0 + d);
+      }
+    }
+  for (int q = 0; q < s.Pen; ++q) V -= s.Z[q % s.M] / gw[(s.Pee + q) * 4];
+  const R* J = Jj + (size_t)w * T;
+  int st = PN_WALKER_OK;
+  if (!(S != 0.0) || !(m > -INFINITY)) st = PN_WALKER_SINGULAR;
+  const double la = gam + (double)J[0] + m + log(fabs(S));
+  logabs[w] = la;
+  sign[w] = S > 0 ? 1.0 : (S < 0 ? -1.0 : 0.0);
+  if (!jet) {
+    if (st == PN_WALKER_OK && !isfinite(la)) st = PN_WALKER_NONFINITE;
+    if (status) status[w] = st;
+    return;
+  }
+  double g[3 * PN_MAX_ELECTRONS];
+  const int n3 = 3 * N;
+  for (int t = 0; t < n3; ++t) g[t] = 0;
+  double lapS = 0;
+  if (st == PN_WALKER_OK) {
+    for (int p = 0; p < nd; ++p) {
+      const double* u = dw + (size_t)(2 * p) * stride;
+      const double* d = u + stride;
+      if (u[1] == 0.0 || d[1] == 0.0) continue;
+      const double om = s.ci[p] * u[1] * d[1] * exp(u[0] + d[0] - m) / S;
+      double sq = 0;
+      for (int t = 0; t < n3; ++t) {
+        const double gt = u[3 + t] + d[3 + t];
+        g[t] += om * gt;
+        sq += gt * gt;
+      }
+      lapS += om * (u[2] + d[2] + sq);
+    }
+  }
+  double g2 = 0;
+  for (int t = 0; t < n3; ++t) g2 += g[t] * g[t];
+  double lap = lapS - g2 + (double)J[T - 1];
+  for (int t = 0; t < n3; ++t) g[t] += (double)J[1 + t];
+  if (s.use_gamma) {
+    for (int a = 0; a < N; ++a)
+      for (int b = a + 1; b < N; ++b) {
+        const double* gg = gw + pn_pair_index(a, b, N) * 4;
+        const double d = gg[0];
+        const double c = ((a < s.n_up) == (b < s.n_up)) ? 0.25 : 0.5;
+        const double e = 1.0 / (1.0 + d);
+        const double g1 = c * e * e;          // d gamma_ab / d d
+        const double g2_ = -2.0 * c * e * e * e;
+        for (int x = 0; x < 3; ++x) {
+          g[3 * a + x] += g1 * gg[1 + x];
+          g[3 * b + x] -= g1 * gg[1 + x];
+        }
+        lap += 2.0 * (g2_ + 2.0 * g1 / d);
+      }
+  }
+  double gn = 0;
+  for (int t = 0; t < n3; ++t) gn += g[t] * g[t];
+  const double E = -0.5 * (lap + gn) + V;
+  eloc[w] = E;
+  if (st == PN_WALKER_OK && !(isfinite(E) && isfinite(la))) st = PN_WALKER_NONFINITE;
+  if (status) status[w] = st;
+}
+
+}  // namespace pnk
+
+// ------------------------------------------------------------------ driver
+using namespace pnk;
+
+static inline unsigned nblk(size_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <typename R>
+int pn_linear(const R* X, int ldx, const R* W, int ldw, const R* b, R* Y, int ldy, int rows, int Kd, int Nout, int T,
+              int acc, cudaStream_t st) {
+  if (rows <= 0) return PN_OK;
+  dim3 grid((Nout + 63) / 64, (rows + 63) / 64);
+  PN_LAUNCH("k_linear", st, k_linear<R><<<grid, 256, 0, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, Kd, Nout, T, acc));
+  return PN_OK;
+}
+template int pn_linear<double>(const double*, int, const double*, int, const double*, double*, int, int, int, int, int, int, cudaStream_t);
+template int pn_linear<float>(const float*, int, const float*, int, const float*, float*, int, int, int, int, int, int, cudaStream_t);
+
+template <typename R>
+int pn_ssp_jet(R* A, int ld, size_t groups, int T, int dim, cudaStream_t st) {
+  PN_LAUNCH("k_ssp_jet", st, k_ssp_jet<R><<<nblk(groups * dim, 256), 256, 0, st>>>(A, ld, groups, T, dim));
+  return PN_OK;
+}
+
+template <typename R>
+int pn_network_layers(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn, int T, int jet, cudaStream_t st) {
+  const size_t groups = (size_t)Wn * s.N;
+  const int rows = (int)(groups * T);
+  PN_LAUNCH("k_features", st, k_features<R><<<nblk((size_t)Wn * s.Ppair * s.K, 256), 256, 0, st>>>(s, w.geo, Wn, jet, w.efeat));
+  PN_LAUNCH("k_init_x", st, k_init_x<R><<<nblk(groups * T * s.D, 256), 256, 0, st>>>(net.p + net.off.x0, w.X, groups, T, s.D));
+  for (int n = 0; n < s.L; ++n) {
+    if (int e = pn_linear<R>(w.X, s.D, net.p + net.off.hW[n], s.Zd, net.p + net.off.hb[n], w.H, w.ldH, rows, s.D,
+                             s.Zd, T, 0, st))
+      return e;
+    PN_LAUNCH("k_filter", st, k_filter<R><<<nblk((size_t)Wn * s.Ppair, FW), FW * 32, 0, st>>>(s, net, n, w.efeat, Wn, jet, w.wjet));
+    PN_LAUNCH("k_message", st, k_message<R><<<nblk((size_t)rows * s.Zd, 256), 256, 0, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H, w.ldH, Wn,
+                                                                  T, w.Zb, w.ldZ));
+    if (int e = pn_linear<R>(w.Zb, w.ldZ, net.Gcat + (size_t)n * 3 * s.Zd * s.D, s.D, net.Gb + (size_t)n * s.D, w.X,
+                             s.D, rows, 3 * s.Zd, s.D, T, 1, st))
+      return e;
+  }
+  return PN_OK;
+}
+
+template <typename R>
+int pn_heads(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn, int T, cudaStream_t st) {
+  const size_t groups = (size_t)Wn * s.N;
+  const int rows = (int)(groups * T);
+  const NetOff& o = net.off;
+  const int D = s.D;
+  // backflow head kappa on every electron
+  if (int e = pn_linear<R>(w.X, D, net.p + o.kW[0], D, net.p + o.kb[0], w.Zb, w.ldZ, rows, D, D, T, 0, st)) return e;
+  if (int e = pn_ssp_jet<R>(w.Zb, w.ldZ, groups, T, D, st)) return e;
+  if (int e = pn_linear<R>(w.Zb, w.ldZ, net.p + o.kW[1], D, net.p + o.kb[1], w.H, w.ldH, rows, D, D, T, 0, st)) return e;
+  if (int e = pn_ssp_jet<R>(w.H, w.ldH, groups, T, D, st)) return e;
+  if (int e = pn_linear<R>(w.H, w.ldH, net.p + o.kW[2], s.n_orb, net.p + o.kb[2], w.F, s.n_orb, rows, D, s.n_orb, T, 0, st))
+    return e;
+  // Jastrow head eta on the electron sum
+  PN_LAUNCH("k_sum_electrons", st, k_sum_electrons<R><<<nblk((size_t)Wn * T * D, 256), 256, 0, st>>>(w.X, w.Xs, Wn, s.N, T, D));
+  const int rs = Wn * T;
+  if (int e = pn_linear<R>(w.Xs, D, net.p + o.eW[0], D, net.p + o.eb[0], w.As, D, rs, D, D, T, 0, st)) return e;
+  if (int e = pn_ssp_jet<R>(w.As, D, (size_t)Wn, T, D, st)) return e;
+  if (int e = pn_linear<R>(w.As, D, net.p + o.eW[1], D, net.p + o.eb[1], w.Bs, D, rs, D, D, T, 0, st)) return e;
+  if (int e = pn_ssp_jet<R>(w.Bs, D, (size_t)Wn, T, D, st)) return e;
+  if (int e = pn_linear<R>(w.Bs, D, net.p + o.eW[2], 1, net.p + o.eb[2], w.Jj, 1, rs, D, 1, T, 0, st)) return e;
+  return PN_OK;
+}
+
+template <typename R>
+int pn_forward_chunk(const DevSys& s, const DevNet<R>& net, Work<R>& w, const double* r, int Wn, int jet,
+                     cudaStream_t st) {
+  if (Wn <= 0) return PN_OK;
+  const int T = jet ? 3 * s.N + 2 : 1;
+  PN_LAUNCH("k_geometry", st, k_geometry<<<nblk((size_t)Wn * s.Ppair, 128), 128, 0, st>>>(s, r, Wn, w.geo));
+  PN_LAUNCH("k_orbitals", st, k_orbitals<<<nblk((size_t)Wn * s.N, 64), 64, 0, st>>>(s, r, Wn, w.phi));
+  if (int e = pn_network_layers<R>(s, net, w, Wn, T, jet, st)) return e;
+  if (int e = pn_heads<R>(s, net, w, Wn, T, st)) return e;
+  PN_LAUNCH("k_slater", st, k_slater<R><<<nblk((size_t)Wn * s.n_det * 2, 64), 64, 0, st>>>(s, w.phi, w.F, Wn, T, jet, w.det));
+  PN_LAUNCH("k_combine", st, k_combine<R><<<nblk(Wn, 64), 64, 0, st>>>(s, w.geo, w.det, w.Jj, Wn, T, jet, w.out_logabs, w.out_sign, w.out_eloc,
+                                            w.out_status));
+  return PN_OK;
+}
+
+template int pn_forward_chunk<double>(const DevSys&, const DevNet<double>&, Work<double>&, const double*, int, int,
+                                      cudaStream_t);
+template int pn_forward_chunk<float>(const DevSys&, const DevNet<float>&, Work<float>&, const double*, int, int,
+                                     cudaStream_t);
+
+// Launchers used by the backward pass (value mode).
+int pn_launch_geometry_orbitals(const DevSys& s, const double* r, int Wn, double* geo, double* phi, cudaStream_t st) {
+  PN_LAUNCH("k_geometry", st, k_geometry<<<nblk((size_t)Wn * s.Ppair, 128), 128, 0, st>>>(s, r, Wn, geo));
+  PN_LAUNCH("k_orbitals", st, k_orbitals<<<nblk((size_t)Wn * s.N, 64), 64, 0, st>>>(s, r, Wn, phi));
+  return PN_OK;
+}
+
+template <typename R>
+int pn_launch_features_init(const DevSys& s, const R* x0, const double* geo, int Wn, R* ef, R* X, cudaStream_t st) {
+  PN_LAUNCH("k_features", st, k_features<R><<<nblk((size_t)Wn * s.Ppair * s.K, 256), 256, 0, st>>>(s, geo, Wn, 0, ef));
+  PN_LAUNCH("k_init_x", st, k_init_x<R><<<nblk((size_t)Wn * s.N * s.D, 256), 256, 0, st>>>(x0, X, (size_t)Wn * s.N, 1, s.D));
+  return PN_OK;
+}
+template int pn_launch_features_init<double>(const DevSys&, const double*, const double*, int, double*, double*, cudaStream_t);
+template int pn_launch_features_init<float>(const DevSys&, const float*, const double*, int, float*, float*, cudaStream_t);
+
+template <typename R>
+int pn_launch_sum_electrons(const R* X, R* Xs, int Wn, int N, int D, cudaStream_t st) {
+  PN_LAUNCH("k_sum_electrons", st, k_sum_electrons<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(X, Xs, Wn, N, 1, D));
+  return PN_OK;
+}
+template int pn_launch_sum_electrons<double>(const double*, double*, int, int, int, cudaStream_t);
+template int pn_launch_sum_electrons<float>(const float*, float*, int, int, int, cudaStream_t);

@@ -1,0 +1,45 @@
+// Launch helpers shared between translation units.
+#pragma once
+
+#include "pn_internal.cuh"
+
+template <typename R>
+int pn_linear(const R* X, int ldx, const R* W, int ldw, const R* b, R* Y, int ldy, int rows, int Kd, int Nout, int T,
+              int acc, cudaStream_t st);
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the multiply-xor
+// bijection with the key bumped by the Weyl constants between rounds.
+__device__ inline void pn_philox(unsigned c[4], unsigned k0, unsigned k1) {
+  const unsigned M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    const unsigned hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+    const unsigned hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+    const unsigned n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+__device__ inline double pn_u01(unsigned x) { return ((double)x + 0.5) * 2.3283064365386962890625e-10; }
+
+// Normal number m (0-based) of stream (seed, walker, step): block m/4,
+// Box-Muller pair (m%4)/2, cosine for even m, sine for odd m.
+__device__ inline void pn_normals4(unsigned long long seed, unsigned walker, unsigned long long step, unsigned j,
+                                   double out[4]) {
+  unsigned c[4] = {j, walker, (unsigned)(step & 0xffffffffull), (unsigned)(step >> 32)};
+  pn_philox(c, (unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
+  for (int pr = 0; pr < 2; ++pr) {
+    const double u0 = pn_u01(c[2 * pr]), u1 = pn_u01(c[2 * pr + 1]);
+    const double rad = sqrt(-2.0 * log(u0));
+    const double ang = 2.0 * 3.141592653589793 * u1;
+    out[2 * pr] = rad * cos(ang);
+    out[2 * pr + 1] = rad * sin(ang);
+  }
+}
+
+int pn_launch_geometry_orbitals(const DevSys& s, const double* r, int Wn, double* geo, double* phi, cudaStream_t st);
+template <typename R>
+int pn_launch_features_init(const DevSys& s, const R* x0, const double* geo, int Wn, R* ef, R* X, cudaStream_t st);
+template <typename R>
+int pn_launch_sum_electrons(const R* X, R* Xs, int Wn, int N, int D, cudaStream_t st);

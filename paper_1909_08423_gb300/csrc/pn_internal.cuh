@@ -1,0 +1,172 @@
+// Internal declarations shared by the translation units of libpaulinet.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/paulinet.h"
+
+#define PN_LMAX PN_MAX_LAYERS
+
+// ---------------------------------------------------------------- errors
+void pn_set_error(const char* fmt, ...);
+
+#define PN_CUDA(call)                                                        \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      pn_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,                \
+                   cudaGetErrorString(e_));                                  \
+      return PN_EDEVICE;                                                     \
+    }                                                                        \
+  } while (0)
+
+// Launch bookkeeping (profile.cu): count, and optional event timing of one
+// kernel class.  PN_LAUNCH(name, stream, launch-expression).
+void pn_prof_begin(const char* name, cudaStream_t st);
+void pn_note_launch(const char* name, cudaStream_t st);
+#define PN_CHECK_LAUNCH() PN_CUDA(cudaGetLastError())
+#define PN_LAUNCH(name, st, ...)        \
+  do {                                  \
+    pn_prof_begin(name, st);            \
+    __VA_ARGS__;                        \
+    pn_note_launch(name, st);           \
+    PN_CHECK_LAUNCH();                  \
+  } while (0)
+
+// ------------------------------------------------------------- parameters
+// Offsets (in elements) of every tensor inside the flat parameter vector.
+struct NetOff {
+  int64_t x0, Y;
+  int64_t hW[PN_LMAX], hb[PN_LMAX];
+  int64_t W1[PN_LMAX][3], b1[PN_LMAX][3], W2[PN_LMAX][3], b2[PN_LMAX][3];
+  int64_t GW[PN_LMAX][3], Gb[PN_LMAX][3];
+  int64_t eW[3], eb[3], kW[3], kb[3];
+  int64_t total;
+};
+NetOff pn_net_offsets(int D, int Zd, int K, int L, int M, int n_orb);
+
+// ------------------------------------------------- device view of a system
+// Everything a kernel needs, passed by value.  Pointers are device memory.
+struct DevSys {
+  int N, n_up, n_dn, M, n_b, n_orb, n_det, n_shells;
+  int D, Zd, K, L, Hw;
+  int Pee;          // unordered electron pairs N(N-1)/2
+  int Pen;          // electron-nucleus pairs N*M
+  int Ppair;        // Pee + Pen
+  double r_c;
+  int use_cusp, use_gamma;
+  double Vnn;
+  const double* Z;        // [M]
+  const double* R;        // [M*3]
+  const int* sh_center;   // [n_shells]
+  const int* sh_l;
+  const int* sh_nprim;
+  const int* sh_poff;     // first primitive
+  const int* sh_boff;     // first basis function
+  const double* pexp;
+  const double* pcoef;
+  const double* mo;       // [n_b][n_orb]
+  const int* occ;         // [n_det][N]: up orbitals then down orbitals
+  const double* ci;       // [n_det]
+  const double* cusp_rc;  // [M]
+  const int* cusp_on;     // [M][n_orb]
+  const double* cusp_C;   // [M][n_orb]
+  const double* cusp_s;   // [M][n_orb]
+  const double* cusp_a;   // [M][n_orb][5]
+  const double* feat_mu;  // [K]
+  const double* feat_isig2;  // [K] 1/sigma^2
+};
+
+// Pair indexing: unordered electron pair (a<b) -> a*N - a*(a+1)/2 + (b-a-1)
+__host__ __device__ inline int pn_pair_index(int a, int b, int N) {
+  return a * N - a * (a + 1) / 2 + (b - a - 1);
+}
+
+// ------------------------------------------------------------- workspace
+// One chunk of walkers' intermediates.  T = jet rows (1 or 3N+2).
+template <typename R>
+struct Work {
+  int Wc;                 // walkers per chunk
+  int T;                  // jet rows the buffers were sized for
+  double* r;              // [Wc][N][3] staging of host positions
+  double* geo;            // [Wc][Ppair][4]  (d, unit vector)
+  double* phi;            // [Wc][N][n_orb][5] value, grad, lap
+  R* efeat;               // [Wc][Ppair][3][K] distance features e, e', e''
+  R* wjet;                // [Wc][Ppair][3][Zd]
+  R* X;                   // [Wc][N][T][D]
+  R* H;                   // [Wc][N][T][max(Zd, D)]
+  R* Zb;                  // [Wc][N][T][max(3 Zd, D)]
+  R* Xs;                  // [Wc][T][D]
+  R* As;                  // [Wc][T][D]
+  R* Bs;                  // [Wc][T][D]
+  R* F;                   // [Wc][N][T][n_orb]
+  R* Jj;                  // [Wc][T]
+  double* det;            // [Wc][n_det][2][3 + 3N] : ld, sign, lap, grad[3N]
+  double* out_logabs;     // [Wc]
+  double* out_sign;       // [Wc]
+  double* out_eloc;       // [Wc]
+  int* out_status;        // [Wc]
+  unsigned long long* n_acc;  // [1]
+  double* r_prop;         // [Wc][N][3]
+  double* lp_prop;        // [Wc]
+  int ldH, ldZ;           // row strides of H and Zb
+  char* end;              // one past the last carved byte
+};
+
+size_t pn_work_bytes(const DevSys& s, int Wc, int T, int elem);
+
+// Per-precision parameters on the device.
+template <typename R>
+struct DevNet {
+  const R* p;     // flat parameter vector in R
+  const R* Gcat;  // [L][3 Zd][D]  same, anti, nuc receiving maps stacked
+  const R* Gb;    // [L][D]        sum of the three receiving biases
+  NetOff off;
+};
+
+struct pn_system_s {
+  DevSys ds;
+  NetOff off;
+  int precision;
+  int Wc;
+  int Tjet;
+  // device allocations
+  std::vector<void*> allocs;
+  double* p64;
+  float* p32;
+  double* Gcat64;
+  double* Gb64;
+  float* Gcat32;
+  float* Gb32;
+  void* work_mem;
+  size_t work_bytes;
+  void* tape_mem;          // backward tape (grown on demand)
+  size_t tape_bytes;
+  Work<double> w64;
+  Work<float> w32;
+  // host copies
+  std::vector<double> h_params;
+  int device;
+};
+
+// Carve a workspace out of one allocation.
+template <typename R>
+Work<R> pn_carve_work(const DevSys& s, int Wc, int T, void* base);
+
+// ----------------------------------------------------------- forward path
+// mode: 0 value only (T = 1), 1 jet (T = 3N + 2)
+template <typename R>
+int pn_forward_chunk(const DevSys& s, const DevNet<R>& net, Work<R>& w,
+                     const double* r, int Wn, int jet, cudaStream_t st);
+
+template <typename R>
+DevNet<R> pn_devnet(pn_system_s* sys);
+
+// Host/device pointer check.
+bool pn_is_device_ptr(const void* p);
+
+int pn_get_stream_device(cudaStream_t st);

@@ -1,0 +1,537 @@
+// System set-up: validation, host precompute of the nuclear cusp splice,
+// parameter packing, device upload and workspace sizing.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "pn_internal.cuh"
+
+static thread_local std::string g_err;
+
+void pn_set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+extern "C" const char* pn_last_error(void) { return g_err.c_str(); }
+
+bool pn_is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------------ parameters
+NetOff pn_net_offsets(int D, int Zd, int K, int L, int M, int n_orb) {
+  NetOff o;
+  memset(&o, 0, sizeof o);
+  int Hw = std::max(K, Zd);
+  int64_t c = 0;
+  o.x0 = c; c += D;
+  o.Y = c; c += (int64_t)M * Zd;
+  for (int n = 0; n < L; ++n) {
+    o.hW[n] = c; c += (int64_t)D * Zd;
+    o.hb[n] = c; c += Zd;
+    for (int ch = 0; ch < 3; ++ch) {
+      o.W1[n][ch] = c; c += (int64_t)K * Hw;
+      o.b1[n][ch] = c; c += Hw;
+      o.W2[n][ch] = c; c += (int64_t)Hw * Zd;
+      o.b2[n][ch] = c; c += Zd;
+    }
+    for (int ch = 0; ch < 3; ++ch) {
+      o.GW[n][ch] = c; c += (int64_t)Zd * D;
+      o.Gb[n][ch] = c; c += D;
+    }
+  }
+  const int outs[3] = {D, D, 1};
+  for (int k = 0; k < 3; ++k) {
+    o.eW[k] = c; c += (int64_t)D * outs[k];
+    o.eb[k] = c; c += outs[k];
+  }
+  const int kouts[3] = {D, D, n_orb};
+  for (int k = 0; k < 3; ++k) {
+    o.kW[k] = c; c += (int64_t)D * kouts[k];
+    o.kb[k] = c; c += kouts[k];
+  }
+  o.total = c;
+  return o;
+}
+
+extern "C" int64_t pn_num_params_for(int D, int Zd, int K, int L, int M, int n_orb) {
+  if (L < 0 || L > PN_LMAX) return -1;
+  return pn_net_offsets(D, Zd, K, L, M, n_orb).total;
+}
+
+// -------------------------------------------------------- host basis eval
+namespace {
+
+int ncart(int l) { return l <= 0 ? 1 : (l == 1 ? 3 : 6); }
+
+const int CART2[6][3] = {{2, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
+const int CART1[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+void cart_exps(int l, int c, int e[3]) {
+  if (l <= 0) { e[0] = e[1] = e[2] = 0; return; }
+  const int* s = (l == 1) ? CART1[c] : CART2[c];
+  e[0] = s[0]; e[1] = s[1]; e[2] = s[2];
+}
+
+struct HostSys {
+  int M, N, n_up, n_dn, n_orb, n_b, n_det, n_shells;
+  std::vector<double> Z, R;
+  std::vector<int> sc, sl, sn, spo, sbo;
+  std::vector<double> pe, pc, mo;
+};
+
+// Uncorrected orbital values at a point.
+void host_orbitals(const HostSys& h, const double* p, std::vector<double>& phi) {
+  phi.assign(h.n_orb, 0.0);
+  for (int s = 0; s < h.n_shells; ++s) {
+    const double* Rc = &h.R[3 * h.sc[s]];
+    double v[3] = {p[0] - Rc[0], p[1] - Rc[1], p[2] - Rc[2]};
+    double r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    int l = h.sl[s];
+    if (l == -1) {
+      double val = h.pc[h.spo[s]] * exp(-h.pe[h.spo[s]] * sqrt(r2));
+      for (int mu = 0; mu < h.n_orb; ++mu) phi[mu] += h.mo[(size_t)h.sbo[s] * h.n_orb + mu] * val;
+      continue;
+    }
+    double rad = 0;
+    for (int k = 0; k < h.sn[s]; ++k) rad += h.pc[h.spo[s] + k] * exp(-h.pe[h.spo[s] + k] * r2);
+    for (int c = 0; c < ncart(l); ++c) {
+      int e[3];
+      cart_exps(l, c, e);
+      double pv = 1;
+      for (int a = 0; a < 3; ++a)
+        for (int q = 0; q < e[a]; ++q) pv *= v[a];
+      for (int mu = 0; mu < h.n_orb; ++mu)
+        phi[mu] += h.mo[(size_t)(h.sbo[s] + c) * h.n_orb + mu] * pv * rad;
+    }
+  }
+}
+
+// Radial s part of orbital mu on nucleus I and its two radial derivatives.
+void host_s_part(const HostSys& h, int I, int mu, double r, double* f, double* f1, double* f2) {
+  *f = *f1 = *f2 = 0;
+  for (int s = 0; s < h.n_shells; ++s) {
+    if (h.sl[s] != 0 || h.sc[s] != I) continue;
+    double c = h.mo[(size_t)h.sbo[s] * h.n_orb + mu];
+    for (int k = 0; k < h.sn[s]; ++k) {
+      double a = h.pe[h.spo[s] + k];
+      double d = h.pc[h.spo[s] + k] * c;
+      double e = exp(-a * r * r);
+      *f += d * e;
+      *f1 += -2.0 * a * r * d * e;
+      *f2 += (4.0 * a * a * r * r - 2.0 * a) * d * e;
+    }
+  }
+}
+
+bool solve3(double A[3][3], double b[3], double x[3]) {
+  // Gaussian elimination with partial pivoting on a 3x3 system.
+  int piv[3] = {0, 1, 2};
+  double M[3][4];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) M[i][j] = A[i][j];
+    M[i][3] = b[i];
+  }
+  for (int c = 0; c < 3; ++c) {
+    int best = c;
+    for (int r = c + 1; r < 3; ++r)
+      if (fabs(M[r][c]) > fabs(M[best][c])) best = r;
+    if (M[best][c] == 0.0) return false;
+    if (best != c)
+      for (int j = 0; j < 4; ++j) std::swap(M[c][j], M[best][j]);
+    for (int r = c + 1; r < 3; ++r) {
+      double f = M[r][c] / M[c][c];
+      for (int j = c; j < 4; ++j) M[r][j] -= f * M[c][j];
+    }
+  }
+  (void)piv;
+  for (int i = 2; i >= 0; --i) {
+    double acc = M[i][3];
+    for (int j = i + 1; j < 3; ++j) acc -= M[i][j] * x[j];
+    x[i] = acc / M[i][i];
+  }
+  return true;
+}
+
+template <typename T>
+T* dev_upload(pn_system_s* s, const T* h, size_t n, int* err) {
+  if (n == 0) n = 1;
+  void* p = nullptr;
+  if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *err = PN_ENOMEM;
+    return nullptr;
+  }
+  s->allocs.push_back(p);
+  if (h && cudaMemcpy(p, h, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    *err = PN_EDEVICE;
+    return nullptr;
+  }
+  return (T*)p;
+}
+
+void free_all(pn_system_s* s) {
+  for (void* p : s->allocs) cudaFree(p);
+  s->allocs.clear();
+  if (s->work_mem) cudaFree(s->work_mem);
+  s->work_mem = nullptr;
+  if (s->tape_mem) cudaFree(s->tape_mem);
+  s->tape_mem = nullptr;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- workspace
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t pn_work_bytes(const DevSys& s, int Wc, int T, int elem) {
+  size_t W = Wc, N = s.N;
+  size_t ldH = std::max(s.Zd, s.D), ldZ = std::max(3 * s.Zd, s.D);
+  size_t b = 0;
+  b += align_up(W * N * 3 * 8);                      // r
+  b += align_up(W * s.Ppair * 4 * 8);                // geo
+  b += align_up(W * N * s.n_orb * 5 * 8);            // phi
+  b += align_up(W * s.Ppair * 3 * s.K * elem);       // efeat (lives after wjet)
+  b += align_up(W * s.Ppair * 3 * s.Zd * elem);      // wjet
+  b += align_up(W * N * T * s.D * elem);             // X
+  b += align_up(W * N * T * ldH * elem);             // H
+  b += align_up(W * N * T * ldZ * elem);             // Zb
+  b += 3 * align_up(W * T * s.D * elem);             // Xs, As, Bs
+  b += align_up(W * N * T * s.n_orb * elem);         // F
+  b += align_up(W * T * elem);                       // Jj
+  b += align_up(W * s.n_det * 2 * (3 + 3 * N) * 8);  // det
+  b += 3 * align_up(W * 8) + align_up(W * 4);        // outputs
+  b += align_up(8);                                  // n_acc
+  b += align_up(W * N * 3 * 8) + align_up(W * 8);    // proposals
+  return b;
+}
+
+template <typename R>
+Work<R> pn_carve_work(const DevSys& s, int Wc, int T, void* base) {
+  Work<R> w;
+  char* p = (char*)base;
+  size_t W = Wc, N = s.N;
+  size_t ldH = std::max(s.Zd, s.D), ldZ = std::max(3 * s.Zd, s.D);
+  size_t elem = sizeof(R);
+  auto take = [&](size_t bytes) { char* q = p; p += align_up(bytes); return (void*)q; };
+  w.Wc = Wc;
+  w.T = T;
+  w.r = (double*)take(W * N * 3 * 8);
+  w.geo = (double*)take(W * s.Ppair * 4 * 8);
+  w.phi = (double*)take(W * N * s.n_orb * 5 * 8);
+  w.efeat = (R*)take(W * s.Ppair * 3 * s.K * elem);
+  w.wjet = (R*)take(W * s.Ppair * 3 * s.Zd * elem);
+  w.X = (R*)take(W * N * T * s.D * elem);
+  w.H = (R*)take(W * N * T * ldH * elem);
+  w.Zb = (R*)take(W * N * T * ldZ * elem);
+  w.Xs = (R*)take(W * T * s.D * elem);
+  w.As = (R*)take(W * T * s.D * elem);
+  w.Bs = (R*)take(W * T * s.D * elem);
+  w.F = (R*)take(W * N * T * s.n_orb * elem);
+  w.Jj = (R*)take(W * T * elem);
+  w.det = (double*)take(W * s.n_det * 2 * (3 + 3 * N) * 8);
+  w.out_logabs = (double*)take(W * 8);
+  w.out_sign = (double*)take(W * 8);
+  w.out_eloc = (double*)take(W * 8);
+  w.out_status = (int*)take(W * 4);
+  w.n_acc = (unsigned long long*)take(8);
+  w.r_prop = (double*)take(W * N * 3 * 8);
+  w.lp_prop = (double*)take(W * 8);
+  w.ldH = (int)ldH;
+  w.ldZ = (int)ldZ;
+  w.end = p;
+  return w;
+}
+template Work<double> pn_carve_work<double>(const DevSys&, int, int, void*);
+template Work<float> pn_carve_work<float>(const DevSys&, int, int, void*);
+
+// ----------------------------------------------------------- parameters
+static int upload_params(pn_system_s* s, const double* hp) {
+  const DevSys& d = s->ds;
+  const NetOff& o = s->off;
+  s->h_params.assign(hp, hp + o.total);
+  PN_CUDA(cudaMemcpy(s->p64, hp, o.total * 8, cudaMemcpyHostToDevice));
+  std::vector<float> p32(hp, hp + o.total);
+  PN_CUDA(cudaMemcpy(s->p32, p32.data(), o.total * 4, cudaMemcpyHostToDevice));
+  // stacked receiving maps and summed biases per layer
+  size_t gsz = (size_t)3 * d.Zd * d.D;
+  std::vector<double> G((size_t)std::max(d.L, 1) * gsz), Gb((size_t)std::max(d.L, 1) * d.D);
+  for (int n = 0; n < d.L; ++n) {
+    for (int c = 0; c < 3; ++c)
+      for (int z = 0; z < d.Zd; ++z)
+        for (int k = 0; k < d.D; ++k)
+          G[n * gsz + ((size_t)c * d.Zd + z) * d.D + k] = hp[o.GW[n][c] + (int64_t)z * d.D + k];
+    for (int k = 0; k < d.D; ++k)
+      Gb[(size_t)n * d.D + k] = hp[o.Gb[n][0] + k] + hp[o.Gb[n][1] + k] + hp[o.Gb[n][2] + k];
+  }
+  PN_CUDA(cudaMemcpy(s->Gcat64, G.data(), G.size() * 8, cudaMemcpyHostToDevice));
+  PN_CUDA(cudaMemcpy(s->Gb64, Gb.data(), Gb.size() * 8, cudaMemcpyHostToDevice));
+  std::vector<float> G32(G.begin(), G.end()), Gb32(Gb.begin(), Gb.end());
+  PN_CUDA(cudaMemcpy(s->Gcat32, G32.data(), G32.size() * 4, cudaMemcpyHostToDevice));
+  PN_CUDA(cudaMemcpy(s->Gb32, Gb32.data(), Gb32.size() * 4, cudaMemcpyHostToDevice));
+  return PN_OK;
+}
+
+template <>
+DevNet<double> pn_devnet<double>(pn_system_s* s) {
+  DevNet<double> n;
+  n.p = s->p64; n.Gcat = s->Gcat64; n.Gb = s->Gb64; n.off = s->off;
+  return n;
+}
+template <>
+DevNet<float> pn_devnet<float>(pn_system_s* s) {
+  DevNet<float> n;
+  n.p = s->p32; n.Gcat = s->Gcat32; n.Gb = s->Gb32; n.off = s->off;
+  return n;
+}
+
+// --------------------------------------------------------------- init
+extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
+  if (!d || !out) { pn_set_error("null argument"); return PN_EINVAL; }
+  *out = nullptr;
+  const int N = d->n_up + d->n_dn;
+  if (d->M < 1 || d->M > PN_MAX_NUCLEI) { pn_set_error("M=%d outside 1..%d", d->M, PN_MAX_NUCLEI); return PN_EINVAL; }
+  if (N < 1 || N > PN_MAX_ELECTRONS) { pn_set_error("N=%d outside 1..%d", N, PN_MAX_ELECTRONS); return PN_EINVAL; }
+  if (d->n_up < 0 || d->n_dn < 0 || d->n_up > PN_MAX_SPIN || d->n_dn > PN_MAX_SPIN || d->n_up < d->n_dn) {
+    pn_set_error("spin counts n_up=%d n_dn=%d invalid (need n_dn <= n_up <= %d)", d->n_up, d->n_dn, PN_MAX_SPIN);
+    return PN_EINVAL;
+  }
+  if (d->n_orb < 1 || d->n_orb > PN_MAX_ORBITALS) { pn_set_error("n_orb=%d outside 1..%d", d->n_orb, PN_MAX_ORBITALS); return PN_EINVAL; }
+  if (d->n_det < 1 || d->n_det > PN_MAX_DETS) { pn_set_error("n_det=%d outside 1..%d", d->n_det, PN_MAX_DETS); return PN_EINVAL; }
+  if (d->L < 0 || d->L > PN_MAX_LAYERS) { pn_set_error("L=%d outside 0..%d", d->L, PN_MAX_LAYERS); return PN_EINVAL; }
+  if (d->D < 1 || d->D > PN_MAX_DIM || d->Zd < 1 || d->Zd > PN_MAX_DIM || d->K < 1 || d->K > 64) {
+    pn_set_error("network sizes D=%d Zd=%d K=%d out of range", d->D, d->Zd, d->K);
+    return PN_EINVAL;
+  }
+  if (std::max(d->K, d->Zd) > 128) { pn_set_error("filter hidden width max(K,Zd) > 128"); return PN_EINVAL; }
+  if (d->n_shells < 1 || !d->Z || !d->R || !d->shell_center || !d->shell_l || !d->shell_nprim ||
+      !d->prim_exp || !d->prim_coef || !d->mo_coeffs || !d->ci || !d->params ||
+      (d->n_up > 0 && !d->occ_up) || (d->n_dn > 0 && !d->occ_dn)) {
+    pn_set_error("missing array in system description");
+    return PN_EINVAL;
+  }
+  if (d->precision != PN_FP64 && d->precision != PN_MIXED) { pn_set_error("precision %d unknown", d->precision); return PN_EINVAL; }
+  NetOff off = pn_net_offsets(d->D, d->Zd, d->K, d->L, d->M, d->n_orb);
+  if (d->n_params != off.total) {
+    pn_set_error("n_params=%lld, layout needs %lld", (long long)d->n_params, (long long)off.total);
+    return PN_EINVAL;
+  }
+  HostSys h;
+  h.M = d->M; h.N = N; h.n_up = d->n_up; h.n_dn = d->n_dn; h.n_orb = d->n_orb; h.n_det = d->n_det;
+  h.n_shells = d->n_shells;
+  h.Z.assign(d->Z, d->Z + d->M);
+  h.R.assign(d->R, d->R + 3 * d->M);
+  int nprim_tot = 0, nb = 0;
+  for (int s = 0; s < d->n_shells; ++s) {
+    int l = d->shell_l[s], c = d->shell_center[s], np = d->shell_nprim[s];
+    if (l < -1 || l > 2 || c < 0 || c >= d->M || np < 1 || np > 16 || (l == -1 && np != 1)) {
+      pn_set_error("shell %d invalid (center %d, l %d, nprim %d)", s, c, l, np);
+      return PN_EINVAL;
+    }
+    h.sc.push_back(c); h.sl.push_back(l); h.sn.push_back(np);
+    h.spo.push_back(nprim_tot); h.sbo.push_back(nb);
+    nprim_tot += np;
+    nb += ncart(l);
+  }
+  h.n_b = nb;
+  h.pe.assign(d->prim_exp, d->prim_exp + nprim_tot);
+  h.pc.assign(d->prim_coef, d->prim_coef + nprim_tot);
+  h.mo.assign(d->mo_coeffs, d->mo_coeffs + (size_t)nb * d->n_orb);
+  for (int I = 0; I < d->M; ++I)
+    if (!(d->Z[I] > 0)) { pn_set_error("nuclear charge %d not positive", I); return PN_EINVAL; }
+  std::vector<int> occ((size_t)d->n_det * N);
+  for (int p = 0; p < d->n_det; ++p) {
+    for (int k = 0; k < d->n_up; ++k) occ[(size_t)p * N + k] = d->occ_up[p * d->n_up + k];
+    for (int k = 0; k < d->n_dn; ++k) occ[(size_t)p * N + d->n_up + k] = d->occ_dn[p * d->n_dn + k];
+  }
+  for (int v : occ)
+    if (v < 0 || v >= d->n_orb) { pn_set_error("orbital index %d outside 0..%d", v, d->n_orb - 1); return PN_EINVAL; }
+
+  // --- nuclear cusp splice coefficients (Ma et al., value at nucleus free)
+  std::vector<double> crc(d->M, 0.0), cC((size_t)d->M * d->n_orb, 0.0), cS((size_t)d->M * d->n_orb, 1.0),
+      cA((size_t)d->M * d->n_orb * 5, 0.0);
+  std::vector<int> con((size_t)d->M * d->n_orb, 0);
+  if (d->use_cusp) {
+    for (int I = 0; I < d->M; ++I) {
+      double rc = 0.5 / d->Z[I];
+      crc[I] = rc;
+      bool has_s = false;
+      for (int s = 0; s < d->n_shells; ++s) has_s |= (h.sl[s] == 0 && h.sc[s] == I);
+      if (!has_s) continue;
+      std::vector<double> full;
+      host_orbitals(h, &h.R[3 * I], full);
+      for (int mu = 0; mu < d->n_orb; ++mu) {
+        double gmin = 1e300, gmax = -1e300, scale = 0;
+        double f0 = 0, f1, f2, fend = 0;
+        for (int g = 0; g < 64; ++g) {
+          double rr = rc * g / 63.0;
+          double f;
+          host_s_part(h, I, mu, rr, &f, &f1, &f2);
+          if (g == 0) f0 = f;
+          if (g == 63) fend = f;
+          gmin = std::min(gmin, f);
+          gmax = std::max(gmax, f);
+          scale = std::max(scale, fabs(f));
+        }
+        if (scale < 1e-14) continue;
+        double C = 0;
+        if (gmin < 0 && gmax > 0) C = (fend > 0) ? gmin - 0.1 * scale : gmax + 0.1 * scale;
+        double fr, fr1, fr2;
+        host_s_part(h, I, mu, rc, &fr, &fr1, &fr2);
+        double sg = (fr - C > 0) ? 1.0 : -1.0;
+        double phi0 = d->cusp_phi0 ? d->cusp_phi0[(size_t)mu * d->M + I] : f0;
+        if ((phi0 - C) * sg <= 0) {
+          pn_set_error("cusp: phi0 - C has the wrong sign for orbital %d at nucleus %d", mu, I);
+          return PN_EINVAL;
+        }
+        double eta0 = full[mu] - f0;
+        double a0 = log(fabs(phi0 - C));
+        double a1 = -d->Z[I] * (phi0 + eta0) / (phi0 - C);
+        double X1 = log(fabs(fr - C));
+        double X2 = fr1 / (fr - C);
+        double X3 = fr2 / (fr - C) - X2 * X2;
+        double A[3][3] = {{rc * rc, rc * rc * rc, rc * rc * rc * rc},
+                          {2 * rc, 3 * rc * rc, 4 * rc * rc * rc},
+                          {2.0, 6 * rc, 12 * rc * rc}};
+        double b[3] = {X1 - a0 - a1 * rc, X2 - a1, X3}, x[3];
+        if (!solve3(A, b, x)) { pn_set_error("cusp: singular matching system"); return PN_EINVAL; }
+        size_t k = (size_t)I * d->n_orb + mu;
+        con[k] = 1;
+        cC[k] = C;
+        cS[k] = sg;
+        cA[k * 5 + 0] = a0; cA[k * 5 + 1] = a1;
+        cA[k * 5 + 2] = x[0]; cA[k * 5 + 3] = x[1]; cA[k * 5 + 4] = x[2];
+      }
+    }
+  }
+
+  pn_system_s* s = new pn_system_s();
+  s->work_mem = nullptr;
+  s->tape_mem = nullptr;
+  s->tape_bytes = 0;
+  cudaGetDevice(&s->device);
+  s->off = off;
+  s->precision = d->precision;
+  DevSys& ds = s->ds;
+  ds.N = N; ds.n_up = d->n_up; ds.n_dn = d->n_dn; ds.M = d->M; ds.n_b = nb; ds.n_orb = d->n_orb;
+  ds.n_det = d->n_det; ds.n_shells = d->n_shells;
+  ds.D = d->D; ds.Zd = d->Zd; ds.K = d->K; ds.L = d->L; ds.Hw = std::max(d->K, d->Zd);
+  ds.Pee = N * (N - 1) / 2; ds.Pen = N * d->M; ds.Ppair = ds.Pee + ds.Pen;
+  ds.r_c = d->r_c; ds.use_cusp = d->use_cusp; ds.use_gamma = d->use_gamma;
+  double Vnn = 0;
+  for (int I = 0; I < d->M; ++I)
+    for (int J = I + 1; J < d->M; ++J) {
+      double dx = d->R[3 * I] - d->R[3 * J], dy = d->R[3 * I + 1] - d->R[3 * J + 1], dz = d->R[3 * I + 2] - d->R[3 * J + 2];
+      Vnn += d->Z[I] * d->Z[J] / sqrt(dx * dx + dy * dy + dz * dz);
+    }
+  ds.Vnn = Vnn;
+  std::vector<double> fmu(d->K), fis(d->K);
+  for (int k = 0; k < d->K; ++k) {
+    double q = (double)(k + 1) / (d->K + 1);
+    double sig = (1.0 + d->r_c * q) / 7.0;
+    fmu[k] = d->r_c * q * q;
+    fis[k] = 1.0 / (sig * sig);
+  }
+  int err = PN_OK;
+  ds.Z = dev_upload(s, d->Z, d->M, &err);
+  ds.R = dev_upload(s, d->R, 3 * d->M, &err);
+  ds.sh_center = dev_upload(s, h.sc.data(), h.sc.size(), &err);
+  ds.sh_l = dev_upload(s, h.sl.data(), h.sl.size(), &err);
+  ds.sh_nprim = dev_upload(s, h.sn.data(), h.sn.size(), &err);
+  ds.sh_poff = dev_upload(s, h.spo.data(), h.spo.size(), &err);
+  ds.sh_boff = dev_upload(s, h.sbo.data(), h.sbo.size(), &err);
+  ds.pexp = dev_upload(s, h.pe.data(), h.pe.size(), &err);
+  ds.pcoef = dev_upload(s, h.pc.data(), h.pc.size(), &err);
+  ds.mo = dev_upload(s, h.mo.data(), h.mo.size(), &err);
+  ds.occ = dev_upload(s, occ.data(), occ.size(), &err);
+  ds.ci = dev_upload(s, d->ci, d->n_det, &err);
+  ds.cusp_rc = dev_upload(s, crc.data(), crc.size(), &err);
+  ds.cusp_on = dev_upload(s, con.data(), con.size(), &err);
+  ds.cusp_C = dev_upload(s, cC.data(), cC.size(), &err);
+  ds.cusp_s = dev_upload(s, cS.data(), cS.size(), &err);
+  ds.cusp_a = dev_upload(s, cA.data(), cA.size(), &err);
+  ds.feat_mu = dev_upload(s, fmu.data(), fmu.size(), &err);
+  ds.feat_isig2 = dev_upload(s, fis.data(), fis.size(), &err);
+  s->p64 = dev_upload<double>(s, nullptr, off.total, &err);
+  s->p32 = dev_upload<float>(s, nullptr, off.total, &err);
+  size_t gsz = (size_t)std::max(d->L, 1) * 3 * d->Zd * d->D;
+  s->Gcat64 = dev_upload<double>(s, nullptr, gsz, &err);
+  s->Gb64 = dev_upload<double>(s, nullptr, (size_t)std::max(d->L, 1) * d->D, &err);
+  s->Gcat32 = dev_upload<float>(s, nullptr, gsz, &err);
+  s->Gb32 = dev_upload<float>(s, nullptr, (size_t)std::max(d->L, 1) * d->D, &err);
+  if (err != PN_OK) {
+    pn_set_error("device allocation/upload failed during init");
+    free_all(s);
+    delete s;
+    return err;
+  }
+  if (int e = upload_params(s, d->params)) { free_all(s); delete s; return e; }
+  // workspace
+  s->Wc = std::max(1, d->max_walkers);
+  s->Tjet = 3 * N + 2;
+  int elem = d->precision == PN_FP64 ? 8 : 4;
+  s->work_bytes = pn_work_bytes(ds, s->Wc, s->Tjet, elem);
+  if (cudaMalloc(&s->work_mem, s->work_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    pn_set_error("workspace of %zu bytes for %d walkers does not fit", s->work_bytes, s->Wc);
+    s->work_mem = nullptr;
+    free_all(s);
+    delete s;
+    return PN_ENOMEM;
+  }
+  char* end;
+  if (d->precision == PN_FP64) {
+    s->w64 = pn_carve_work<double>(ds, s->Wc, s->Tjet, s->work_mem);
+    end = s->w64.end;
+  } else {
+    s->w32 = pn_carve_work<float>(ds, s->Wc, s->Tjet, s->work_mem);
+    end = s->w32.end;
+  }
+  if (end > (char*)s->work_mem + s->work_bytes) {
+    pn_set_error("workspace layout exceeds its allocation");
+    free_all(s);
+    delete s;
+    return PN_EINVAL;
+  }
+  *out = s;
+  return PN_OK;
+}
+
+extern "C" int pn_destroy_system(pn_system_t s) {
+  if (!s) return PN_OK;
+  free_all(s);
+  delete s;
+  return PN_OK;
+}
+
+extern "C" int pn_set_params(pn_system_t s, const double* params, int64_t n) {
+  if (!s || !params) { pn_set_error("null argument"); return PN_EINVAL; }
+  if (n != s->off.total) { pn_set_error("n_params=%lld, expected %lld", (long long)n, (long long)s->off.total); return PN_EINVAL; }
+  std::vector<double> hp(n);
+  if (pn_is_device_ptr(params)) {
+    PN_CUDA(cudaMemcpy(hp.data(), params, n * 8, cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(hp.data(), params, n * 8);
+  }
+  PN_CUDA(cudaDeviceSynchronize());
+  return upload_params(s, hp.data());
+}
+
+extern "C" int64_t pn_num_params(pn_system_t s) { return s ? s->off.total : -1; }
+extern "C" size_t pn_workspace_bytes(pn_system_t s) { return s ? s->work_bytes : 0; }
