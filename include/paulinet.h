@@ -160,6 +160,25 @@ int pn_eval_local_energy(pn_system_t sys, const double* r, int W, double* eloc,
 int pn_eval_components(pn_system_t sys, const double* r, int W, double* phi,
                        double* J, double* f, double* ld, void* stream);
 
+/* ln|psi| and sign(psi) like pn_eval_logpsi, for callers that cannot
+ * allocate device memory while they evaluate (a thread capturing a CUDA
+ * graph, a latency-bound loop that must not wait on the allocator, a process
+ * that reserves its memory once at start-up).  The paper has no counterpart:
+ * this is a deployment variant of the value pass.  The call allocates
+ * nothing: its intermediates live in one fixed 16 MiB file-scope device
+ * array that every GPU loading the library holds until the process exits.
+ * All buffers must be device pointers, and the handle's device must be
+ * current.  W is limited by that array (about 600 walkers of a
+ * four-electron, D = 64 system in PN_FP64); a larger W returns PN_EINVAL
+ * with the limit in pn_last_error() and launches nothing.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call shares the one
+ * array, so calls that overlap on the GPU (other streams, other threads)
+ * race: serialise them.  No part of the array has to start at zero. */
+int pn_eval_logpsi_static(pn_system_t sys, const double* r, int W,
+                          double* logabs, double* sign, int* status,
+                          void* stream);
+
 /* n_steps Metropolis steps for each walker (Methods, ansatz optimisation:
  * sampling of |psi|^2; Gaussian all-electron proposal of width sigma):
  * r' = r + sigma xi, accept iff u < exp(2 (ln|psi(r')| - ln|psi(r)|)).
