@@ -173,6 +173,60 @@ def cpu_baseline_sample(n_walkers=96):
             "seconds": dt}
 
 
+def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384, load=0.7):
+    """Poisson stream of seeded molecules through the serving loop, mixed and
+    plain FP64 servers.  The arrival rate is set to `load` times the mixed
+    server's measured capacity (a closed-loop calibration burst first)."""
+    import torch
+    from paper_1909_08423_gb300 import binding, synth
+    stream = synth.serving_stream(n_jobs, seed, rate_per_s=1.0, wmax=wmax)
+    sys_cache = {}
+    out = {}
+    for prec_name, prec in (("mixed", binding.PN_MIXED), ("fp64", binding.PN_FP64)):
+        systems = [binding.System(synth.serving_system(j["seed"]), precision=prec, max_walkers=1) for j in stream]
+        srv = binding.Server(budget_gb << 30, n_slots=slots, chunk_walkers=chunk)
+        # calibration: all jobs of a prefix at once -> walker-E_loc/s and jobs/s capacity
+        ncal = min(len(stream), 24)
+        t0 = time.perf_counter()
+        ids = [srv.submit(systems[k], binding.PN_JOB_SWEEP if stream[k]["kind"] == "sweep" else binding.PN_JOB_ELOC,
+                          stream[k]["W"], n_steps=stream[k]["n_steps"], sigma=0.2, seed=stream[k]["seed"])
+               for k in range(ncal)]
+        for i in ids:
+            srv.poll(i, timeout_us=-1)
+        cap_jobs = ncal / (time.perf_counter() - t0)
+        if prec_name == "mixed":
+            rate = load * cap_jobs
+        # open-loop Poisson arrivals at `rate`
+        arr = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, size=n_jobs))
+        ids = []
+        t0 = time.perf_counter()
+        for k, j in enumerate(stream):
+            while time.perf_counter() - t0 < arr[k]:
+                time.sleep(min(0.0005, max(0.0, arr[k] - (time.perf_counter() - t0))))
+            ids.append(srv.submit(systems[k], binding.PN_JOB_SWEEP if j["kind"] == "sweep" else binding.PN_JOB_ELOC,
+                                  j["W"], n_steps=j["n_steps"], sigma=0.2, seed=j["seed"]))
+        lat = []
+        walkers = 0
+        for k, i in enumerate(ids):
+            res = srv.poll(i, timeout_us=-1)
+            lat.append(res.queue_ms + res.run_ms)
+            walkers += res.W
+        span = time.perf_counter() - t0
+        srv.close()
+        lat = np.array(lat)
+        out[prec_name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                          "walker_eloc_per_s": walkers / span, "jobs_per_s": n_jobs / span,
+                          "calibrated_capacity_jobs_per_s": cap_jobs}
+        for s_ in systems:
+            s_.close()
+    out["arrival_rate_jobs_per_s"] = rate
+    out["jobs"] = n_jobs
+    out["stream"] = (f"{n_jobs} Poisson jobs, seeded neutral molecules of 1-6 nuclei, Z 1-10, 2-30 electrons, "
+                     f"1-32 determinants, 256-{wmax} walkers log-uniform, E_loc or 10-step sweep 50/50; "
+                     f"{slots} slots, load {load} of calibrated mixed capacity")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,6 +237,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=60)
+    ap.add_argument("--serve-only", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -190,6 +246,11 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_1909_08423_gb300 import binding, synth
+
+    if args.serve_only:
+        torch.cuda.set_device(0)
+        print(json.dumps({"serve": run_serving(args.serve_jobs)}), flush=True)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -382,6 +443,8 @@ def main():
             "clocks": clocks, "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
+    if rank == 0 and args.serve_jobs > 0:
+        line["serve"] = run_serving(args.serve_jobs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

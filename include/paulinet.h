@@ -200,7 +200,8 @@ int pn_init_walkers(pn_system_t sys, double* r, int W, uint64_t seed, void* stre
 /* grad[P] = sum_w cotangent[w] d ln|psi(r_w)| / d theta over the network
  * parameters (layout above) -- the backward pass needed by Eq. (trainig).
  * The value pass is recomputed chunk by chunk so that the stored activations
- * stay within mem_budget_bytes (0: the handle's workspace chunk). */
+ * stay within mem_budget_bytes (0: room for max(max_walkers, 256) walkers).
+ * A budget below one walker's tape returns PN_EINVAL. */
 int pn_grad_logpsi(pn_system_t sys, const double* r, int W, const double* cotangent,
                    double* grad, size_t mem_budget_bytes, void* stream);
 
@@ -222,7 +223,10 @@ typedef struct pn_server_s* pn_server_t;
 typedef struct pn_server_cfg {
   size_t hbm_budget_bytes;   /* total device memory the server may hold */
   int n_slots;               /* concurrent jobs (one stream each)       */
-  int chunk_walkers;         /* walkers per workspace chunk per slot    */
+  int chunk_walkers;         /* walkers per workspace chunk per job     */
+  int debug_fail_nth;        /* test hook: the n-th admitted job fails on
+                                the host before it launches anything
+                                (result status PN_EDEVICE); 0 = off     */
 } pn_server_cfg;
 
 enum { PN_JOB_ELOC = 0, PN_JOB_SWEEP = 1 };
@@ -255,9 +259,11 @@ int pn_server_create(const pn_server_cfg* cfg, pn_server_t* out);
 int pn_server_destroy(pn_server_t srv);
 /* Queue a job.  PN_EBUDGET at once if its footprint can never fit. */
 int pn_submit(pn_server_t srv, pn_system_t sys, const pn_job* job, uint64_t* job_id);
-/* PN_OK with *res filled once done (the job is then forgotten),
- * PN_ENOTREADY if timeout_us == 0 and not done, PN_ETIMEOUT if it did not
- * finish within timeout_us (> 0), PN_EINVAL for an unknown id. */
+/* PN_OK with *res filled once done (the job is then forgotten; res->status
+ * says how it ended: PN_OK, PN_ECANCELLED or an error), PN_ENOTREADY if
+ * timeout_us == 0 and not done, PN_ETIMEOUT if it did not finish within
+ * timeout_us (> 0), PN_EINVAL for an unknown id.  A negative timeout waits
+ * until the job ends. */
 int pn_poll(pn_server_t srv, uint64_t job_id, pn_result* res, int64_t timeout_us);
 /* Cancel a queued job (PN_OK) -- running jobs complete (PN_ENOTREADY). */
 int pn_cancel(pn_server_t srv, uint64_t job_id);

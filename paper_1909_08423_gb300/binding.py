@@ -44,7 +44,8 @@ class SystemDesc(C.Structure):
 
 
 class ServerCfg(C.Structure):
-    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("n_slots", C.c_int), ("chunk_walkers", C.c_int)]
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("n_slots", C.c_int), ("chunk_walkers", C.c_int),
+                ("debug_fail_nth", C.c_int)]
 
 
 class Job(C.Structure):
@@ -238,6 +239,52 @@ class System:
     def grad_logpsi(self, r, cot, grad, mem_budget_bytes=0):
         check(load().pn_grad_logpsi(self.h, _ptr(r), r.shape[0], _ptr(cot), _ptr(grad), int(mem_budget_bytes),
                                     _stream(r)))
+
+
+class Server:
+    """The serving loop: submit jobs for any resident system, poll results."""
+
+    def __init__(self, hbm_budget_bytes, n_slots=4, chunk_walkers=4096, debug_fail_nth=0):
+        cfg = ServerCfg(int(hbm_budget_bytes), int(n_slots), int(chunk_walkers), int(debug_fail_nth))
+        h = C.c_void_p()
+        check(load().pn_server_create(C.byref(cfg), C.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, system, kind, W, n_steps=0, sigma=0.2, seed=0, r_init=None, eloc_out=None, r_out=None):
+        j = Job(kind, int(W), int(n_steps), float(sigma), int(seed), _ptr(r_init), _ptr(eloc_out), _ptr(r_out))
+        jid = C.c_uint64()
+        check(load().pn_submit(self.h, system.h, C.byref(j), C.byref(jid)))
+        self._keep[jid.value] = (r_init, eloc_out, r_out)
+        return jid.value
+
+    def poll(self, job_id, timeout_us=-1):
+        """Returns a Result, or None when not ready / timed out."""
+        res = Result()
+        rc = load().pn_poll(self.h, C.c_uint64(job_id), C.byref(res), int(timeout_us))
+        if rc in (4, 5):
+            return None
+        check(rc)
+        self._keep.pop(job_id, None)
+        return res
+
+    def cancel(self, job_id):
+        return load().pn_cancel(self.h, C.c_uint64(job_id))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pn_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def job_footprint(system, W, chunk_walkers):
+    return load().pn_job_footprint(system.h, int(W), int(chunk_walkers))
 
 
 def clip_local_energy(eloc, out, cot=None, q=5.0):

@@ -152,27 +152,7 @@ int set_device(pn_system_s* s) {
 template <typename R>
 int eval_impl(pn_system_s* s, const double* r, int W, int jet, double* eloc, double* logabs, double* sign, int* status,
               cudaStream_t st) {
-  Work<R>& w = work_of<R>(s);
-  const DevNet<R> net = pn_devnet<R>(s);
-  const DevSys& ds = s->ds;
-  const int N = ds.N;
-  const bool rdev = pn_is_device_ptr(r);
-  const bool sync = !rdev || is_host(eloc) || is_host(logabs) || is_host(sign) || is_host(status);
-  for (int c0 = 0; c0 < W; c0 += s->Wc) {
-    const int Wn = std::min(s->Wc, W - c0);
-    const double* rc = r + (size_t)c0 * N * 3;
-    if (!rdev) {
-      PN_CUDA(cudaMemcpyAsync(w.r, rc, (size_t)Wn * N * 3 * 8, cudaMemcpyHostToDevice, st));
-      rc = w.r;
-    }
-    if (int e = pn_forward_chunk<R>(ds, net, w, rc, Wn, jet, st)) return e;
-    if (eloc && jet) PN_CUDA(cudaMemcpyAsync(eloc + c0, w.out_eloc, Wn * 8, cudaMemcpyDefault, st));
-    if (logabs) PN_CUDA(cudaMemcpyAsync(logabs + c0, w.out_logabs, Wn * 8, cudaMemcpyDefault, st));
-    if (sign) PN_CUDA(cudaMemcpyAsync(sign + c0, w.out_sign, Wn * 8, cudaMemcpyDefault, st));
-    if (status) PN_CUDA(cudaMemcpyAsync(status + c0, w.out_status, Wn * 4, cudaMemcpyDefault, st));
-  }
-  if (sync) PN_CUDA(cudaStreamSynchronize(st));
-  return PN_OK;
+  return pn_run_eval<R>(s->ds, pn_devnet<R>(s), work_of<R>(s), s->Wc, r, W, jet, eloc, logabs, sign, status, st);
 }
 
 template <typename R>
@@ -217,14 +197,49 @@ int components_impl(pn_system_s* s, const double* r, int W, double* phi, double*
 template <typename R>
 int metropolis_impl(pn_system_s* s, double* r, double* logabs, int W, int n_steps, double sigma,
                     unsigned long long seed, unsigned long long step0, int64_t* n_accept, cudaStream_t st) {
-  Work<R>& w = work_of<R>(s);
-  const DevNet<R> net = pn_devnet<R>(s);
-  const DevSys& ds = s->ds;
+  return pn_run_metropolis<R>(s->ds, pn_devnet<R>(s), work_of<R>(s), s->Wc, r, logabs, W, n_steps, sigma, seed, step0,
+                              n_accept, st);
+}
+
+}  // namespace
+
+// ------------------------------------------------------ drivers with explicit workspace
+template <typename R>
+int pn_run_eval(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, const double* r, int W, int jet,
+                double* eloc, double* logabs, double* sign, int* status, cudaStream_t st) {
+  const int N = ds.N;
+  const bool rdev = pn_is_device_ptr(r);
+  const bool sync = !rdev || is_host(eloc) || is_host(logabs) || is_host(sign) || is_host(status);
+  for (int c0 = 0; c0 < W; c0 += Wc) {
+    const int Wn = std::min(Wc, W - c0);
+    const double* rc = r + (size_t)c0 * N * 3;
+    if (!rdev) {
+      PN_CUDA(cudaMemcpyAsync(w.r, rc, (size_t)Wn * N * 3 * 8, cudaMemcpyHostToDevice, st));
+      rc = w.r;
+    }
+    if (int e = pn_forward_chunk<R>(ds, net, w, rc, Wn, jet, st)) return e;
+    if (eloc && jet) PN_CUDA(cudaMemcpyAsync(eloc + c0, w.out_eloc, Wn * 8, cudaMemcpyDefault, st));
+    if (logabs) PN_CUDA(cudaMemcpyAsync(logabs + c0, w.out_logabs, Wn * 8, cudaMemcpyDefault, st));
+    if (sign) PN_CUDA(cudaMemcpyAsync(sign + c0, w.out_sign, Wn * 8, cudaMemcpyDefault, st));
+    if (status) PN_CUDA(cudaMemcpyAsync(status + c0, w.out_status, Wn * 4, cudaMemcpyDefault, st));
+  }
+  if (sync) PN_CUDA(cudaStreamSynchronize(st));
+  return PN_OK;
+}
+template int pn_run_eval<double>(const DevSys&, const DevNet<double>&, Work<double>&, int, const double*, int, int,
+                                 double*, double*, double*, int*, cudaStream_t);
+template int pn_run_eval<float>(const DevSys&, const DevNet<float>&, Work<float>&, int, const double*, int, int,
+                                double*, double*, double*, int*, cudaStream_t);
+
+template <typename R>
+int pn_run_metropolis(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, double* r, double* logabs, int W,
+                      int n_steps, double sigma, unsigned long long seed, unsigned long long step0, int64_t* n_accept,
+                      cudaStream_t st) {
   const int N = ds.N;
   const bool rdev = pn_is_device_ptr(r), ldev = pn_is_device_ptr(logabs);
   PN_CUDA(cudaMemsetAsync(w.n_acc, 0, 8, st));
-  for (int c0 = 0; c0 < W; c0 += s->Wc) {
-    const int Wn = std::min(s->Wc, W - c0);
+  for (int c0 = 0; c0 < W; c0 += Wc) {
+    const int Wn = std::min(Wc, W - c0);
     double* rc = r + (size_t)c0 * N * 3;
     double* lc = logabs + c0;
     if (!rdev) {
@@ -248,8 +263,15 @@ int metropolis_impl(pn_system_s* s, double* r, double* logabs, int W, int n_step
   if (!rdev || !ldev || is_host(n_accept)) PN_CUDA(cudaStreamSynchronize(st));
   return PN_OK;
 }
+template int pn_run_metropolis<double>(const DevSys&, const DevNet<double>&, Work<double>&, int, double*, double*, int,
+                                       int, double, unsigned long long, unsigned long long, int64_t*, cudaStream_t);
+template int pn_run_metropolis<float>(const DevSys&, const DevNet<float>&, Work<float>&, int, double*, double*, int,
+                                      int, double, unsigned long long, unsigned long long, int64_t*, cudaStream_t);
 
-}  // namespace
+int pn_run_init_walkers(const DevSys& ds, double* r, int W, unsigned long long seed, cudaStream_t st) {
+  PN_LAUNCH("k_init_walkers", st, k_init_walkers<<<nblk(W, 128), 128, 0, st>>>(ds, ds.nuc, r, W, seed));
+  return PN_OK;
+}
 
 // ------------------------------------------------------------------- C ABI
 #define PN_SYS_CHECK(s)                                   \
@@ -314,29 +336,14 @@ extern "C" int pn_init_walkers(pn_system_t s, double* r, int W, uint64_t seed, v
   if (W == 0) return PN_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const DevSys& ds = s->ds;
-  // nucleus per electron: nuclei repeated Z_I times; up k -> 2k, down k -> 2k+1
-  std::vector<double> Z(ds.M);
-  PN_CUDA(cudaMemcpy(Z.data(), ds.Z, ds.M * 8, cudaMemcpyDeviceToHost));
-  std::vector<int> lst;
-  for (int I = 0; I < ds.M; ++I)
-    for (int k = 0; k < (int)llround(Z[I]); ++k) lst.push_back(I);
-  if (lst.empty()) lst.push_back(0);
-  std::vector<int> nuc(ds.N);
-  for (int k = 0; k < ds.n_up; ++k) nuc[k] = lst[(2 * k) % lst.size()];
-  for (int k = 0; k < ds.n_dn; ++k) nuc[ds.n_up + k] = lst[(2 * k + 1) % lst.size()];
-  int* dnuc = nullptr;
-  // the nucleus table is tiny; keep one per call in the workspace's n_acc slot area is not enough, so allocate
-  PN_CUDA(cudaMallocAsync((void**)&dnuc, ds.N * sizeof(int), st));
-  PN_CUDA(cudaMemcpyAsync(dnuc, nuc.data(), ds.N * sizeof(int), cudaMemcpyHostToDevice, st));
   const bool rdev = pn_is_device_ptr(r);
   double* rd = r;
   if (!rdev) PN_CUDA(cudaMallocAsync((void**)&rd, (size_t)W * ds.N * 3 * 8, st));
-  PN_LAUNCH("k_init_walkers", st, k_init_walkers<<<nblk(W, 128), 128, 0, st>>>(ds, dnuc, rd, W, seed));
+  if (int e = pn_run_init_walkers(ds, rd, W, seed, st)) return e;
   if (!rdev) {
     PN_CUDA(cudaMemcpyAsync(r, rd, (size_t)W * ds.N * 3 * 8, cudaMemcpyDeviceToHost, st));
     PN_CUDA(cudaFreeAsync(rd, st));
   }
-  PN_CUDA(cudaFreeAsync(dnuc, st));
   PN_CUDA(cudaStreamSynchronize(st));
   return PN_OK;
 }

@@ -316,38 +316,42 @@ __global__ void k_filter_bwd(DevSys s, DevNet<R> net, int n, const R* __restrict
 }
 
 // ------------------------------------------------------------ weight grads
-// part[split][ka][nb] = sum over this split's rows r (whose pair channel is
-// `ch`, or all rows if ch < 0) of A[r][ka] * B[r][nb]; A == nullptr means a
-// column of ones (bias gradient, Ka = 1).  32x32 tile per block.
+// part[split][ka][nb] = sum over this split's rows r of A[r][ka] * B[r][nb];
+// A == nullptr means a column of ones (bias gradient, Ka = 1).  With a pair
+// map, logical row r is walker r / cnt, pair map[r % cnt] (the pairs of one
+// filter channel), i.e. storage row (r / cnt) * P + map[r % cnt].  Each block
+// sums its rows in R, then writes one float64 partial tile (32 x 32).
 template <typename R>
 __global__ void k_wgrad(const R* __restrict__ A, int lda, const R* __restrict__ B, int ldb, int rows, int Ka, int Nb,
-                        int rows_per_split, DevSys s, int ch, double* __restrict__ part) {
+                        int rows_per_split, const int* __restrict__ map, int cnt, int P, double* __restrict__ part) {
   __shared__ R As[32][33];
   __shared__ R Bs[32][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
   const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
   const int r_begin = blockIdx.z * rows_per_split;
   const int r_end = min(rows, r_begin + rows_per_split);
-  double acc[4] = {0, 0, 0, 0};
+  R acc[4] = {0, 0, 0, 0};
   for (int r0 = r_begin; r0 < r_end; r0 += 32) {
     for (int q = ty; q < 32; q += 8) {
       const int r = r0 + q;
-      bool ok = r < r_end;
-      if (ok && ch >= 0) ok = pair_channel(s, r % s.Ppair) == ch;
-      As[q][tx] = (ok && k0 + tx < Ka) ? (A ? A[(size_t)r * lda + k0 + tx] : R(1)) : R(0);
-      Bs[q][tx] = (ok && n0 + tx < Nb) ? B[(size_t)r * ldb + n0 + tx] : R(0);
+      const bool ok = r < r_end;
+      size_t row = r;
+      if (ok && map) row = (size_t)(r / cnt) * P + map[r % cnt];
+      As[q][tx] = (ok && k0 + tx < Ka) ? (A ? A[row * lda + k0 + tx] : R(1)) : R(0);
+      Bs[q][tx] = (ok && n0 + tx < Nb) ? B[row * ldb + n0 + tx] : R(0);
     }
     __syncthreads();
+#pragma unroll 8
     for (int q = 0; q < 32; ++q) {
-      const double b = (double)Bs[q][tx];
+      const R b = Bs[q][tx];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc[e] += (double)As[q][ty + 8 * e] * b;
+      for (int e = 0; e < 4; ++e) acc[e] += As[q][ty + 8 * e] * b;
     }
     __syncthreads();
   }
   for (int e = 0; e < 4; ++e) {
     const int k = k0 + ty + 8 * e, nn = n0 + tx;
-    if (k < Ka && nn < Nb) part[((size_t)blockIdx.z * Ka + k) * Nb + nn] = acc[e];
+    if (k < Ka && nn < Nb) part[((size_t)blockIdx.z * Ka + k) * Nb + nn] = (double)acc[e];
   }
 }
 
@@ -508,13 +512,21 @@ Tape<R> carve_tape(const DevSys& s, int Wb, void* base, size_t part_elems) {
 template <typename R>
 int wgrad(Tape<R>& t, const R* A, int lda, const R* B, int ldb, int rows, int Ka, int Nb, const DevSys& s, int ch,
           double* grad, int64_t base, int64_t stride_c, int rows_per_c, cudaStream_t st) {
+  const int* map = nullptr;
+  int cnt = 0;
+  if (ch >= 0) {
+    // rows of one filter channel only: Wn * (pairs of that channel)
+    cnt = s.ch_off[ch + 1] - s.ch_off[ch];
+    map = s.ch_pairs + s.ch_off[ch];
+    rows = (rows / s.Ppair) * cnt;
+  }
   if (rows <= 0) return PN_OK;
   const size_t tile = (size_t)Ka * Nb;
-  int nsplit = std::max(1, std::min<int>((rows + 1023) / 1024, (int)(t.part_elems / tile)));
-  nsplit = std::min(nsplit, 1024);
+  constexpr int kRowsPerBlock = 256;
+  int nsplit = std::max(1, std::min<int>((rows + kRowsPerBlock - 1) / kRowsPerBlock, (int)(t.part_elems / tile)));
   const int rps = (rows + nsplit - 1) / nsplit;
   dim3 grid((Nb + 31) / 32, (Ka + 31) / 32, nsplit);
-  PN_LAUNCH("k_wgrad", st, k_wgrad<R><<<grid, 256, 0, st>>>(A, lda, B, ldb, rows, Ka, Nb, rps, s, ch, t.part));
+  PN_LAUNCH("k_wgrad", st, k_wgrad<R><<<grid, 256, 0, st>>>(A, lda, B, ldb, rows, Ka, Nb, rps, map, cnt, s.Ppair, t.part));
   PN_LAUNCH("k_reduce_part", st, k_reduce_part<<<nblk(tile, 256), 256, 0, st>>>(t.part, nsplit, Ka, Nb, grad, base, stride_c, rows_per_c));
   return PN_OK;
 }
@@ -643,12 +655,13 @@ static int grad_impl(pn_system_s* sys, const double* r, int W, const double* cot
   const DevNet<R> net = pn_devnet<R>(sys);
   const int N = s.N;
   const size_t per = tape_bytes_per_walker<R>(s);
-  if (budget == 0) budget = sys->work_bytes;
-  // partial tiles: enough for the largest weight block times 64 splits
+  // partial tiles: enough for the largest weight block times 256 splits
   size_t maxKN = std::max<size_t>({(size_t)s.D * s.D, (size_t)3 * s.Zd * s.D, (size_t)s.K * s.Hw,
                                    (size_t)s.Hw * s.Zd, (size_t)s.D * s.n_orb, (size_t)s.M * s.Zd, 1});
-  const size_t part_elems = maxKN * 64;
+  const size_t part_elems = maxKN * 256;
   const size_t fixed = part_elems * 8 + 4096 * 64;
+  // default: room for one workspace chunk (at least 256 walkers)
+  if (budget == 0) budget = fixed + per * (size_t)std::min(W, std::max(sys->Wc, 256)) + 65536;
   if (budget <= fixed + per) {
     pn_set_error("grad: memory budget %zu below one walker's tape (%zu bytes)", budget, fixed + per);
     return PN_EINVAL;

@@ -79,6 +79,9 @@ struct DevSys {
   const double* cusp_a;   // [M][n_orb][5]
   const double* feat_mu;  // [K]
   const double* feat_isig2;  // [K] 1/sigma^2
+  const int* nuc;         // [N] nucleus each electron starts near (walker init)
+  const int* ch_pairs;    // [Ppair] pair indices grouped by filter channel
+  int ch_off[4];          // channel c owns ch_pairs[ch_off[c] .. ch_off[c+1])
 };
 
 // Pair indexing: unordered electron pair (a<b) -> a*N - a*(a+1)/2 + (b-a-1)
@@ -165,6 +168,17 @@ int pn_forward_chunk(const DevSys& s, const DevNet<R>& net, Work<R>& w,
 
 template <typename R>
 DevNet<R> pn_devnet(pn_system_s* sys);
+
+// Chunked drivers over an explicit workspace (used by the C ABI with the
+// handle's workspace and by the serving loop with per-job workspaces).
+template <typename R>
+int pn_run_eval(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, const double* r, int W, int jet,
+                double* eloc, double* logabs, double* sign, int* status, cudaStream_t st);
+template <typename R>
+int pn_run_metropolis(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, double* r, double* logabs, int W,
+                      int n_steps, double sigma, unsigned long long seed, unsigned long long step0, int64_t* n_accept,
+                      cudaStream_t st);
+int pn_run_init_walkers(const DevSys& ds, double* r, int W, unsigned long long seed, cudaStream_t st);
 
 // Host/device pointer check.
 bool pn_is_device_ptr(const void* p);

@@ -466,6 +466,33 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   ds.cusp_C = dev_upload(s, cC.data(), cC.size(), &err);
   ds.cusp_s = dev_upload(s, cS.data(), cS.size(), &err);
   ds.cusp_a = dev_upload(s, cA.data(), cA.size(), &err);
+  {
+    // pairs grouped by filter channel: same spin, opposite spin, nucleus
+    std::vector<int> chp;
+    for (int c = 0; c < 3; ++c) {
+      ds.ch_off[c] = (int)chp.size();
+      for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b) {
+          const int ch = ((a < d->n_up) == (b < d->n_up)) ? 0 : 1;
+          if (ch == c) chp.push_back(pn_pair_index(a, b, N));
+        }
+      if (c == 2)
+        for (int q = 0; q < N * d->M; ++q) chp.push_back(ds.Pee + q);
+    }
+    ds.ch_off[3] = (int)chp.size();
+    ds.ch_pairs = dev_upload(s, chp.data(), chp.size(), &err);
+  }
+  {
+    // nucleus per electron for walker initialisation: the nuclei repeated
+    // Z_I times; up electron k takes entry 2k, down electron k entry 2k + 1
+    std::vector<int> lst, nuc(N);
+    for (int I = 0; I < d->M; ++I)
+      for (int k = 0; k < (int)llround(d->Z[I]); ++k) lst.push_back(I);
+    if (lst.empty()) lst.push_back(0);
+    for (int k = 0; k < d->n_up; ++k) nuc[k] = lst[(2 * k) % lst.size()];
+    for (int k = 0; k < d->n_dn; ++k) nuc[d->n_up + k] = lst[(2 * k + 1) % lst.size()];
+    ds.nuc = dev_upload(s, nuc.data(), nuc.size(), &err);
+  }
   ds.feat_mu = dev_upload(s, fmu.data(), fmu.size(), &err);
   ds.feat_isig2 = dev_upload(s, fis.data(), fis.size(), &err);
   s->p64 = dev_upload<double>(s, nullptr, off.total, &err);

@@ -32,7 +32,7 @@ def test_grad_chunking_by_memory_budget(lib):
     cot = torch.as_tensor(np.random.default_rng(0).normal(size=300), device="cuda")
     s = lib.System(sysd, precision=lib.PN_FP64, max_walkers=512)
     outs = []
-    for budget in (0, 40 << 20, 12 << 20):
+    for budget in (0, 30 << 20, 16 << 20):
         g = torch.empty(s.n_params, dtype=torch.float64, device="cuda")
         s.grad_logpsi(r, cot, g, budget)
         outs.append(g.cpu().numpy())

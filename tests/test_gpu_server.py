@@ -1,0 +1,112 @@
+"""Serving loop: continuous batching of jobs for molecules of different
+sizes, admission by device-memory footprint, bounded polling, cancellation,
+host-injected failures, and results that are the same alone and in a mix."""
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1909_08423_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GB = 1 << 30
+
+
+def _systems(lib):
+    mk = [synth.h2(), synth.be(), synth.h10(), synth.serving_system(3), synth.serving_system(11)]
+    return [lib.System(s, precision=lib.PN_MIXED, max_walkers=1) for s in mk]
+
+
+def _run(lib, server, jobs):
+    ids = [server.submit(**j) for j in jobs]
+    return [server.poll(i, timeout_us=-1) for i in ids]
+
+
+def _job(system, kind, W, seed, out=True):
+    e = torch.full((W,), np.nan, dtype=torch.float64, device="cuda") if out else None
+    r = torch.full((W, system.N, 3), np.nan, dtype=torch.float64, device="cuda") if out else None
+    return dict(system=system, kind=kind, W=W, n_steps=5 if kind == 1 else 0, sigma=0.2, seed=seed,
+                eloc_out=e, r_out=r)
+
+
+def test_eloc_job_matches_direct_call(lib):
+    sysd = synth.be()
+    s = lib.System(sysd, precision=lib.PN_MIXED, max_walkers=512)
+    r = torch.as_tensor(synth.random_walkers(sysd, 700, 3), device="cuda")
+    E = torch.empty(700, dtype=torch.float64, device="cuda")
+    s.eval_local_energy(r, E)
+    srv = lib.Server(4 * GB, n_slots=2, chunk_walkers=512)
+    out = torch.empty_like(E)
+    jid = srv.submit(s, lib.PN_JOB_ELOC, 700, r_init=r, eloc_out=out)
+    res = srv.poll(jid, timeout_us=-1)
+    torch.cuda.synchronize()
+    assert res.status == 0 and res.W == 700
+    np.testing.assert_array_equal(out.cpu().numpy(), E.cpu().numpy())
+    En = E.cpu().numpy()
+    assert abs(res.e_mean - En.mean()) < 1e-10 * abs(En.mean())
+    assert abs(res.e_stderr - En.std(ddof=1) / np.sqrt(700)) < 1e-8
+    srv.close()
+
+
+def test_results_same_alone_and_in_a_mix(lib):
+    systems = _systems(lib)
+    srv = lib.Server(8 * GB, n_slots=4, chunk_walkers=1024)
+    probe = [_job(systems[1], lib.PN_JOB_SWEEP, 777, 5), _job(systems[3], lib.PN_JOB_ELOC, 300, 6)]
+    alone = []
+    for j in probe:
+        res = _run(lib, srv, [j])[0]
+        torch.cuda.synchronize()
+        alone.append((res, j["eloc_out"].cpu().numpy().copy(), j["r_out"].cpu().numpy().copy()))
+    rng = np.random.default_rng(0)
+    mix = []
+    for k in range(14):
+        s = systems[k % len(systems)]
+        mix.append(_job(s, int(rng.integers(0, 2)), int(rng.integers(64, 2048)), 100 + k))
+    again = [_job(systems[1], lib.PN_JOB_SWEEP, 777, 5), _job(systems[3], lib.PN_JOB_ELOC, 300, 6)]
+    jobs = mix[:5] + [again[0]] + mix[5:10] + [again[1]] + mix[10:]
+    results = _run(lib, srv, jobs)
+    torch.cuda.synchronize()
+    assert all(r.status == 0 for r in results)
+    for (res_a, e_a, r_a), j in zip(alone, again):
+        np.testing.assert_array_equal(j["eloc_out"].cpu().numpy(), e_a)
+        np.testing.assert_array_equal(j["r_out"].cpu().numpy(), r_a)
+    # the mix overlapped: some job was admitted while another was running
+    assert any(r.queue_ms > 0 for r in results)
+    srv.close()
+
+
+def test_budget_rejects_and_serialises(lib):
+    systems = _systems(lib)
+    from paper_1909_08423_gb300 import binding
+    s = systems[2]
+    fp = binding.job_footprint(s, 4096, 1024)
+    srv = lib.Server(int(fp * 1.5), n_slots=4, chunk_walkers=1024)
+    with pytest.raises(binding.PNError) as e:
+        srv.submit(s, lib.PN_JOB_ELOC, 50_000_000)
+    assert e.value.code == 3  # PN_EBUDGET
+    res = _run(lib, srv, [_job(s, lib.PN_JOB_ELOC, 4096, k) for k in range(3)])
+    assert all(r.status == 0 for r in res)
+    # only one job fits at a time: the later ones waited for admission
+    assert sorted(r.queue_ms for r in res)[-1] > 0
+    srv.close()
+
+
+def test_cancel_timeout_and_injected_failure(lib):
+    systems = _systems(lib)
+    srv = lib.Server(8 * GB, n_slots=1, chunk_walkers=2048, debug_fail_nth=2)
+    long_job = srv.submit(systems[2], lib.PN_JOB_SWEEP, 8192, n_steps=20, seed=1)
+    failing = srv.submit(systems[0], lib.PN_JOB_ELOC, 128, seed=2)
+    cancelled = srv.submit(systems[1], lib.PN_JOB_ELOC, 128, seed=3)
+    assert srv.cancel(cancelled) == 0
+    assert srv.poll(long_job, timeout_us=1) is None  # still running: bounded wait expires
+    r0 = srv.poll(long_job, timeout_us=-1)
+    r1 = srv.poll(failing, timeout_us=-1)
+    r2 = srv.poll(cancelled, timeout_us=-1)
+    assert r0.status == 0
+    assert r1.status == 6  # PN_EDEVICE, injected on the host before any launch
+    assert r2.status == 7  # PN_ECANCELLED
+    # the server keeps serving after the failure
+    r3 = _run(lib, srv, [_job(systems[0], lib.PN_JOB_ELOC, 64, 9)])[0]
+    assert r3.status == 0
+    srv.close()
