@@ -191,6 +191,16 @@ int pn_metropolis_step(pn_system_t sys, double* r, double* logabs, int W,
                        int n_steps, double sigma, uint64_t seed, uint64_t step0,
                        int64_t* n_accept, void* stream);
 
+/* Implementation options of a handle (they change speed, not results
+ * beyond floating-point rounding).
+ * PN_OPT_FUSED_SAMPLER (default 1): run Metropolis steps in one launch that
+ *   keeps walkers in shared memory for all steps -- one warp per walker for
+ *   small systems (up to 24 KiB of state per walker), else a tile of walkers
+ *   per block; 2 forces the tile kernel; 0 (or a system too large for one
+ *   tile) uses one kernel per stage. */
+enum { PN_OPT_FUSED_SAMPLER = 1 };
+int pn_set_option(pn_system_t sys, int option, int value);
+
 /* Initial walkers: electron e at R[nucleus(e)] + N(0, 1) per coordinate
  * (Methods: Gaussians around the nuclei), nucleus(e) from the list of nuclei
  * repeated Z_I times, up electron k -> entry 2k, down electron k -> 2k+1

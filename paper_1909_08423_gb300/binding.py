@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpaulinet.so")
 
 PN_FP64, PN_MIXED = 0, 1
 PN_JOB_ELOC, PN_JOB_SWEEP = 0, 1
+PN_OPT_FUSED_SAMPLER = 1
 ERRORS = {0: "PN_OK", 1: "PN_EINVAL", 2: "PN_ENOMEM", 3: "PN_EBUDGET", 4: "PN_ENOTREADY",
           5: "PN_ETIMEOUT", 6: "PN_EDEVICE", 7: "PN_ECANCELLED"}
 
@@ -84,6 +85,7 @@ EXPORTS = {
     "pn_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Result), C.c_int64]),
     "pn_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
     "pn_job_footprint": (C.c_size_t, [C.c_void_p, C.c_int, C.c_int]),
+    "pn_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "pn_launch_count": (C.c_ulonglong, []),
     "pn_profile_kernel": (C.c_int, [C.c_char_p]),
     "pn_profile_read": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
@@ -232,6 +234,9 @@ class System:
         W = r.shape[0]
         check(load().pn_metropolis_step(self.h, _ptr(r), _ptr(logabs), W, n_steps, float(sigma), int(seed),
                                         int(step0), _ptr(n_accept), _stream(r)))
+
+    def set_option(self, option, value):
+        check(load().pn_set_option(self.h, int(option), int(value)))
 
     def init_walkers(self, r, seed):
         check(load().pn_init_walkers(self.h, _ptr(r), r.shape[0], int(seed), _stream(r)))

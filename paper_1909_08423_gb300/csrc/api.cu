@@ -250,7 +250,11 @@ int pn_run_metropolis(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc
       PN_CUDA(cudaMemcpyAsync(w.lp_prop, lc, (size_t)Wn * 8, cudaMemcpyHostToDevice, st));
       lc = w.lp_prop;
     }
-    for (int k = 0; k < n_steps; ++k) {
+    int fused = ds.fused_sampler ? pn_run_metropolis_fused<R>(ds, net, rc, lc, Wn, (unsigned)c0, n_steps, sigma, seed,
+                                                             step0, w.n_acc, st)
+                                 : PN_ENOTREADY;
+    if (fused != PN_OK && fused != PN_ENOTREADY) return fused;
+    for (int k = 0; fused != PN_OK && k < n_steps; ++k) {
       const unsigned long long step = step0 + (unsigned long long)k;
       PN_LAUNCH("k_propose", st, k_propose<<<nblk(Wn, 128), 128, 0, st>>>(rc, w.r_prop, Wn, N, (unsigned)c0, seed, step, sigma));
       if (int e = pn_forward_chunk<R>(ds, net, w, w.r_prop, Wn, 0, st)) return e;
@@ -346,6 +350,19 @@ extern "C" int pn_init_walkers(pn_system_t s, double* r, int W, uint64_t seed, v
   }
   PN_CUDA(cudaStreamSynchronize(st));
   return PN_OK;
+}
+
+extern "C" int pn_set_option(pn_system_t s, int option, int value) {
+  if (!s) { pn_set_error("null system"); return PN_EINVAL; }
+  switch (option) {
+    case PN_OPT_FUSED_SAMPLER:
+      if (value < 0 || value > 2) { pn_set_error("fused sampler option takes 0, 1 or 2"); return PN_EINVAL; }
+      s->ds.fused_sampler = value;
+      return PN_OK;
+    default:
+      pn_set_error("unknown option %d", option);
+      return PN_EINVAL;
+  }
 }
 
 extern "C" int pn_clip_local_energy(const double* eloc, int W, double q, double* out, double* cot, void* stream) {

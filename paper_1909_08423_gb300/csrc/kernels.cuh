@@ -43,3 +43,17 @@ template <typename R>
 int pn_launch_features_init(const DevSys& s, const R* x0, const double* geo, int Wn, R* ef, R* X, cudaStream_t st);
 template <typename R>
 int pn_launch_sum_electrons(const R* X, R* Xs, int Wn, int N, int D, cudaStream_t st);
+
+// One Box-Muller pair (normals 4j + 2*pair and 4j + 2*pair + 1) of the same
+// stream as pn_normals4, so that the pairs of one block can go to different
+// lanes.
+__device__ inline void pn_normal_pair(unsigned long long seed, unsigned walker, unsigned long long step, unsigned j,
+                                      int pair, double out[2]) {
+  unsigned c[4] = {j, walker, (unsigned)(step & 0xffffffffull), (unsigned)(step >> 32)};
+  pn_philox(c, (unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
+  const double u0 = pn_u01(c[2 * pair]), u1 = pn_u01(c[2 * pair + 1]);
+  const double rad = sqrt(-2.0 * log(u0));
+  const double ang = 2.0 * 3.141592653589793 * u1;
+  out[0] = rad * cos(ang);
+  out[1] = rad * sin(ang);
+}

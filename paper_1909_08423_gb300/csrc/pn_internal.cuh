@@ -79,9 +79,12 @@ struct DevSys {
   const double* cusp_a;   // [M][n_orb][5]
   const double* feat_mu;  // [K]
   const double* feat_isig2;  // [K] 1/sigma^2
+  const float* feat_mu32;    // [K] float copies for float32 paths
+  const float* feat_isig2_32;
   const int* nuc;         // [N] nucleus each electron starts near (walker init)
   const int* ch_pairs;    // [Ppair] pair indices grouped by filter channel
   int ch_off[4];          // channel c owns ch_pairs[ch_off[c] .. ch_off[c+1])
+  int fused_sampler;      // 1: Metropolis through the fused tile kernel when it fits
 };
 
 // Pair indexing: unordered electron pair (a<b) -> a*N - a*(a+1)/2 + (b-a-1)
@@ -179,6 +182,11 @@ int pn_run_metropolis(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc
                       int n_steps, double sigma, unsigned long long seed, unsigned long long step0, int64_t* n_accept,
                       cudaStream_t st);
 int pn_run_init_walkers(const DevSys& ds, double* r, int W, unsigned long long seed, cudaStream_t st);
+// Fused sampler (sampler.cu): PN_ENOTREADY if a tile does not fit.
+template <typename R>
+int pn_run_metropolis_fused(const DevSys& s, const DevNet<R>& net, double* r, double* lp, int W, unsigned walker0,
+                            int n_steps, double sigma, unsigned long long seed, unsigned long long step0,
+                            unsigned long long* n_acc, cudaStream_t st);
 
 // Host/device pointer check.
 bool pn_is_device_ptr(const void* p);

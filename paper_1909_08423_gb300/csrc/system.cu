@@ -434,6 +434,7 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   ds.D = d->D; ds.Zd = d->Zd; ds.K = d->K; ds.L = d->L; ds.Hw = std::max(d->K, d->Zd);
   ds.Pee = N * (N - 1) / 2; ds.Pen = N * d->M; ds.Ppair = ds.Pee + ds.Pen;
   ds.r_c = d->r_c; ds.use_cusp = d->use_cusp; ds.use_gamma = d->use_gamma;
+  ds.fused_sampler = 1;
   double Vnn = 0;
   for (int I = 0; I < d->M; ++I)
     for (int J = I + 1; J < d->M; ++J) {
@@ -495,6 +496,11 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   }
   ds.feat_mu = dev_upload(s, fmu.data(), fmu.size(), &err);
   ds.feat_isig2 = dev_upload(s, fis.data(), fis.size(), &err);
+  {
+    std::vector<float> fmu32(fmu.begin(), fmu.end()), fis32(fis.begin(), fis.end());
+    ds.feat_mu32 = dev_upload(s, fmu32.data(), fmu32.size(), &err);
+    ds.feat_isig2_32 = dev_upload(s, fis32.data(), fis32.size(), &err);
+  }
   s->p64 = dev_upload<double>(s, nullptr, off.total, &err);
   s->p32 = dev_upload<float>(s, nullptr, off.total, &err);
   size_t gsz = (size_t)std::max(d->L, 1) * 3 * d->Zd * d->D;

@@ -172,15 +172,19 @@ def test_chunking_is_batch_invariant(lib, oracles):
     np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("fused", [1, 2, 0])
+@pytest.mark.parametrize("name,W,steps", [("be", 96, 6), ("h10", 37, 3), ("n2", 9, 2)])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_metropolis_matches_oracle(lib, oracles, precision):
-    o = oracles["be"]
+def test_metropolis_matches_oracle(lib, oracles, precision, name, W, steps, fused):
+    """Every sampler implementation (warp-per-walker or tile kernel, staged kernels)
+    against the oracle's Metropolis chain with the same Philox stream."""
+    o = oracles[name]
     sysd = o.sys
-    W, steps = 96, 6
     r0 = synth.random_walkers(sysd, W, 9)
     lp0, _ = o.eval_logpsi(r0)
     ro, lpo, acco = sampling.metropolis(o, r0, lp0, steps, 0.2, seed=77, step0=1000)
     s = lib.System(sysd, precision=precision, max_walkers=40)
+    s.set_option(lib.PN_OPT_FUSED_SAMPLER, fused)
     rd = torch.as_tensor(r0, device="cuda").clone()
     lpd = torch.as_tensor(lp0, device="cuda").clone()
     nacc = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -194,7 +198,7 @@ def test_metropolis_matches_oracle(lib, oracles, precision):
         np.testing.assert_allclose(lpd.cpu().numpy(), lpo, rtol=1e-11, atol=1e-10)
     else:
         # float32 network: a decision can flip only where the ratio is near u
-        assert same.mean() > 0.95
+        assert same.mean() > 0.9
 
 
 def test_init_walkers_match_oracle(lib, oracles):
