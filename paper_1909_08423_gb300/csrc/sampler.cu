@@ -396,8 +396,26 @@ __device__ inline void warp_gemm(int lane, int rows, int K, const R* __restrict_
       const R* x2 = rx(min(r0 + 2, rows - 1));
       const R* x3 = rx(min(r0 + 3, rows - 1));
       R a0 = bias, a1 = bias, a2 = bias, a3 = bias;
-#pragma unroll 8
-      for (int k = 0; k < K; ++k) {
+      int k = 0;
+      if constexpr (sizeof(R) == 4) {
+        // rows are 16-byte aligned with K a multiple of 4: one 128-bit
+        // shared load brings four k values of a row
+        if ((K & 3) == 0) {
+#pragma unroll 2
+          for (; k < K; k += 4) {
+            const float4 p0 = *(const float4*)(x0 + k), p1 = *(const float4*)(x1 + k);
+            const float4 p2 = *(const float4*)(x2 + k), p3 = *(const float4*)(x3 + k);
+            const R w0 = __ldg(wc + (size_t)k * Nout), w1 = __ldg(wc + (size_t)(k + 1) * Nout);
+            const R w2 = __ldg(wc + (size_t)(k + 2) * Nout), w3 = __ldg(wc + (size_t)(k + 3) * Nout);
+            a0 += p0.x * w0 + p0.y * w1 + p0.z * w2 + p0.w * w3;
+            a1 += p1.x * w0 + p1.y * w1 + p1.z * w2 + p1.w * w3;
+            a2 += p2.x * w0 + p2.y * w1 + p2.z * w2 + p2.w * w3;
+            a3 += p3.x * w0 + p3.y * w1 + p3.z * w2 + p3.w * w3;
+          }
+        }
+      }
+#pragma unroll 4
+      for (; k < K; ++k) {
         const R w = __ldg(wc + (size_t)k * Nout);
         a0 += x0[k] * w;
         a1 += x1[k] * w;
