@@ -330,7 +330,7 @@ def main():
         step(mixed)
     candidates = ["k_linear", "k_filter", "k_message", "k_slater", "k_orbitals", "k_combine", "k_features",
                   "k_ssp_jet", "k_wgrad", "k_slater_bwd", "k_propose", "k_accept", "k_geometry",
-                  "k_metropolis_warp", "k_metropolis_fused"]
+                  "k_metropolis_warp", "k_metropolis_fused", "k_linear_tc"]
     share = {}
     for kname in candidates:
         lib.pn_profile_kernel(kname.encode())

@@ -197,9 +197,23 @@ int pn_metropolis_step(pn_system_t sys, double* r, double* logabs, int W,
  *   keeps walkers in shared memory for all steps -- one warp per walker for
  *   small systems (up to 24 KiB of state per walker), else a tile of walkers
  *   per block; 2 forces the tile kernel; 0 (or a system too large for one
- *   tile) uses one kernel per stage. */
-enum { PN_OPT_FUSED_SAMPLER = 1 };
+ *   tile) uses one kernel per stage.
+ * PN_OPT_TENSOR_CORES (PN_MIXED only; default 0): a mask of the float32
+ *   linear layers that run on tcgen05 with each operand split into three
+ *   bf16 pieces (six products, float32 accumulation in tensor memory):
+ *   1 = interaction layers of the local-energy jet, 2 = its heads, 4 =
+ *   value passes (ln|psi| and the gradient's recomputation).  The tensor
+ *   core's float32 accumulation is coarser than CUDA-core float32, so the
+ *   mask is a per-system choice: enable a group only where the E_loc error
+ *   against PN_FP64 stays within the required bound (the Python helper
+ *   paper_1909_08423_gb300.precision.calibrate measures this). */
+enum { PN_OPT_FUSED_SAMPLER = 1, PN_OPT_TENSOR_CORES = 2 };
 int pn_set_option(pn_system_t sys, int option, int value);
+
+/* Synchronises the device and reports whether any of the handle's kernels
+ * gave up a bounded wait since the last check (PN_ETIMEOUT; the affected
+ * outputs are invalid) -- PN_OK otherwise. */
+int pn_device_status(pn_system_t sys);
 
 /* Initial walkers: electron e at R[nucleus(e)] + N(0, 1) per coordinate
  * (Methods: Gaussians around the nuclei), nucleus(e) from the list of nuclei
@@ -279,6 +293,16 @@ int pn_poll(pn_server_t srv, uint64_t job_id, pn_result* res, int64_t timeout_us
 int pn_cancel(pn_server_t srv, uint64_t job_id);
 /* Device bytes a job of this size would hold. */
 size_t pn_job_footprint(pn_system_t sys, int W, int chunk_walkers);
+
+/* Self-test of the tensor-core linear layer used by the mixed path (no
+ * counterpart in the paper): Y (=|+=) X W + b on device float32 buffers,
+ * X [rows][K] (row stride ldx), W [K][Nout] (row stride ldw), Y [rows][Nout]
+ * (row stride ldy), bias added on rows with row % T == 0; Nout <= 256.
+ * Runs on `stream` and synchronises it; PN_ETIMEOUT if the kernel's bounded
+ * wait for the tensor cores expired. */
+int pn_test_linear_tc(const float* X, int ldx, const float* W, int ldw,
+                      const float* b, float* Y, int ldy, int rows, int K,
+                      int Nout, int T, int accumulate, void* stream);
 
 /* ---------------------------------------------------------------------
  * Measurement hooks (no counterpart in the paper).

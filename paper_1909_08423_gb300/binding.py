@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpaulinet.so")
 
 PN_FP64, PN_MIXED = 0, 1
 PN_JOB_ELOC, PN_JOB_SWEEP = 0, 1
-PN_OPT_FUSED_SAMPLER = 1
+PN_OPT_FUSED_SAMPLER, PN_OPT_TENSOR_CORES = 1, 2
 ERRORS = {0: "PN_OK", 1: "PN_EINVAL", 2: "PN_ENOMEM", 3: "PN_EBUDGET", 4: "PN_ENOTREADY",
           5: "PN_ETIMEOUT", 6: "PN_EDEVICE", 7: "PN_ECANCELLED"}
 
@@ -86,6 +86,9 @@ EXPORTS = {
     "pn_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
     "pn_job_footprint": (C.c_size_t, [C.c_void_p, C.c_int, C.c_int]),
     "pn_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "pn_device_status": (C.c_int, [C.c_void_p]),
+    "pn_test_linear_tc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                    C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "pn_launch_count": (C.c_ulonglong, []),
     "pn_profile_kernel": (C.c_int, [C.c_char_p]),
     "pn_profile_read": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
@@ -234,6 +237,9 @@ class System:
         W = r.shape[0]
         check(load().pn_metropolis_step(self.h, _ptr(r), _ptr(logabs), W, n_steps, float(sigma), int(seed),
                                         int(step0), _ptr(n_accept), _stream(r)))
+
+    def device_status(self):
+        check(load().pn_device_status(self.h))
 
     def set_option(self, option, value):
         check(load().pn_set_option(self.h, int(option), int(value)))

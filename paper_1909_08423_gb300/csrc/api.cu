@@ -359,10 +359,28 @@ extern "C" int pn_set_option(pn_system_t s, int option, int value) {
       if (value < 0 || value > 2) { pn_set_error("fused sampler option takes 0, 1 or 2"); return PN_EINVAL; }
       s->ds.fused_sampler = value;
       return PN_OK;
+    case PN_OPT_TENSOR_CORES:
+      if (value < 0 || value > 7) { pn_set_error("tensor-core option takes a mask 0..7"); return PN_EINVAL; }
+      s->ds.tensor_cores = value;
+      return PN_OK;
     default:
       pn_set_error("unknown option %d", option);
       return PN_EINVAL;
   }
+}
+
+extern "C" int pn_device_status(pn_system_t s) {
+  if (!s) { pn_set_error("null system"); return PN_EINVAL; }
+  PN_CUDA(cudaDeviceSynchronize());
+  int h = 0;
+  PN_CUDA(cudaMemcpy(&h, s->ds.dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    const int zero = 0;
+    PN_CUDA(cudaMemcpy(s->ds.dev_err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    pn_set_error("a bounded device wait expired (tensor-core completion)");
+    return PN_ETIMEOUT;
+  }
+  return PN_OK;
 }
 
 extern "C" int pn_clip_local_energy(const double* eloc, int W, double q, double* out, double* cot, void* stream) {

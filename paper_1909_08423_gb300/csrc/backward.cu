@@ -561,26 +561,26 @@ static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const d
     R* Zn = t.Z + (size_t)n * rows * 3 * Zd;
     R* Ahn = t.Ah + (size_t)n * Wn * P * Hw;
     R* wn = t.wv + (size_t)n * Wn * P * Zd;
-    if (int e = pn_linear<R>(Xn, D, net.p + o.hW[n], Zd, net.p + o.hb[n], Hn, Zd, rows, D, Zd, 1, 0, st)) return e;
+    if (int e = pn_linear<R>(&s, PN_TC_VALUE, Xn, D, net.p + o.hW[n], Zd, net.p + o.hb[n], Hn, Zd, rows, D, Zd, 1, 0, st)) return e;
     PN_LAUNCH("k_filter_tape", st, k_filter_tape<R><<<nblk((size_t)Wn * P, 8), 256, 0, st>>>(s, net, n, t.ef, Wn, Ahn, wn));
     PN_LAUNCH("k_message_value", st, k_message_value<R><<<nblk((size_t)rows * Zd, 256), 256, 0, st>>>(s, net.p + o.Y, wn, Hn, Wn, Zn));
     PN_CUDA(cudaMemcpyAsync(Xn1, Xn, WND * sizeof(R), cudaMemcpyDeviceToDevice, st));
-    if (int e = pn_linear<R>(Zn, 3 * Zd, net.Gcat + (size_t)n * 3 * Zd * D, D, net.Gb + (size_t)n * D, Xn1, D, rows,
+    if (int e = pn_linear<R>(&s, PN_TC_VALUE, Zn, 3 * Zd, net.Gcat + (size_t)n * 3 * Zd * D, D, net.Gb + (size_t)n * D, Xn1, D, rows,
                              3 * Zd, D, 1, 1, st))
       return e;
   }
   R* XL = t.X + (size_t)L * WND;
   // kappa
-  if (int e = pn_linear<R>(XL, D, net.p + o.kW[0], D, net.p + o.kb[0], t.kA1, D, rows, D, D, 1, 0, st)) return e;
+  if (int e = pn_linear<R>(&s, PN_TC_VALUE, XL, D, net.p + o.kW[0], D, net.p + o.kb[0], t.kA1, D, rows, D, D, 1, 0, st)) return e;
   PN_LAUNCH("k_ssp_copy", st, k_ssp_copy<R><<<nblk(WND, 256), 256, 0, st>>>(t.kA1, t.kS1, WND));
-  if (int e = pn_linear<R>(t.kS1, D, net.p + o.kW[1], D, net.p + o.kb[1], t.kA2, D, rows, D, D, 1, 0, st)) return e;
+  if (int e = pn_linear<R>(&s, PN_TC_VALUE, t.kS1, D, net.p + o.kW[1], D, net.p + o.kb[1], t.kA2, D, rows, D, D, 1, 0, st)) return e;
   PN_LAUNCH("k_ssp_copy", st, k_ssp_copy<R><<<nblk(WND, 256), 256, 0, st>>>(t.kA2, t.kS2, WND));
-  if (int e = pn_linear<R>(t.kS2, D, net.p + o.kW[2], no, net.p + o.kb[2], t.F, no, rows, D, no, 1, 0, st)) return e;
+  if (int e = pn_linear<R>(&s, PN_TC_VALUE, t.kS2, D, net.p + o.kW[2], no, net.p + o.kb[2], t.F, no, rows, D, no, 1, 0, st)) return e;
   // eta
   if (int e = pn_launch_sum_electrons<R>(XL, t.Xs, Wn, N, D, st)) return e;
-  if (int e = pn_linear<R>(t.Xs, D, net.p + o.eW[0], D, net.p + o.eb[0], t.eA1, D, Wn, D, D, 1, 0, st)) return e;
+  if (int e = pn_linear<R>(&s, PN_TC_VALUE, t.Xs, D, net.p + o.eW[0], D, net.p + o.eb[0], t.eA1, D, Wn, D, D, 1, 0, st)) return e;
   PN_LAUNCH("k_ssp_copy", st, k_ssp_copy<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.eA1, t.eS1, (size_t)Wn * D));
-  if (int e = pn_linear<R>(t.eS1, D, net.p + o.eW[1], D, net.p + o.eb[1], t.eA2, D, Wn, D, D, 1, 0, st)) return e;
+  if (int e = pn_linear<R>(&s, PN_TC_VALUE, t.eS1, D, net.p + o.eW[1], D, net.p + o.eb[1], t.eA2, D, Wn, D, D, 1, 0, st)) return e;
   PN_LAUNCH("k_ssp_copy", st, k_ssp_copy<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.eA2, t.eS2, (size_t)Wn * D));
 
   // ---------------- backward

@@ -562,15 +562,24 @@ using namespace pnk;
 static inline unsigned nblk(size_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 template <typename R>
-int pn_linear(const R* X, int ldx, const R* W, int ldw, const R* b, R* Y, int ldy, int rows, int Kd, int Nout, int T,
-              int acc, cudaStream_t st) {
+int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw, const R* b, R* Y, int ldy, int rows,
+              int Kd, int Nout, int T, int acc, cudaStream_t st) {
   if (rows <= 0) return PN_OK;
+  if constexpr (sizeof(R) == 4) {
+    // value passes (T == 1) use the PN_TC_VALUE bit, jet passes the group bit
+    const int bit = T == 1 ? PN_TC_VALUE : grp;
+    if (s && (s->tensor_cores & bit) && pn_tc_supported(Nout))
+      return pn_linear_tc((const float*)X, ldx, (const float*)W, ldw, (const float*)b, (float*)Y, ldy, rows, Kd, Nout,
+                          T, acc, s->dev_err, st);
+  }
   dim3 grid((Nout + 63) / 64, (rows + 63) / 64);
   PN_LAUNCH("k_linear", st, k_linear<R><<<grid, 256, 0, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, Kd, Nout, T, acc));
   return PN_OK;
 }
-template int pn_linear<double>(const double*, int, const double*, int, const double*, double*, int, int, int, int, int, int, cudaStream_t);
-template int pn_linear<float>(const float*, int, const float*, int, const float*, float*, int, int, int, int, int, int, cudaStream_t);
+template int pn_linear<double>(const DevSys*, int, const double*, int, const double*, int, const double*, double*, int,
+                               int, int, int, int, int, cudaStream_t);
+template int pn_linear<float>(const DevSys*, int, const float*, int, const float*, int, const float*, float*, int, int,
+                              int, int, int, int, cudaStream_t);
 
 template <typename R>
 int pn_ssp_jet(R* A, int ld, size_t groups, int T, int dim, cudaStream_t st) {
@@ -585,13 +594,13 @@ int pn_network_layers(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn,
   PN_LAUNCH("k_features", st, k_features<R><<<nblk((size_t)Wn * s.Ppair * s.K, 256), 256, 0, st>>>(s, w.geo, Wn, jet, w.efeat));
   PN_LAUNCH("k_init_x", st, k_init_x<R><<<nblk(groups * T * s.D, 256), 256, 0, st>>>(net.p + net.off.x0, w.X, groups, T, s.D));
   for (int n = 0; n < s.L; ++n) {
-    if (int e = pn_linear<R>(w.X, s.D, net.p + net.off.hW[n], s.Zd, net.p + net.off.hb[n], w.H, w.ldH, rows, s.D,
+    if (int e = pn_linear<R>(&s, PN_TC_LAYERS, w.X, s.D, net.p + net.off.hW[n], s.Zd, net.p + net.off.hb[n], w.H, w.ldH, rows, s.D,
                              s.Zd, T, 0, st))
       return e;
     PN_LAUNCH("k_filter", st, k_filter<R><<<nblk((size_t)Wn * s.Ppair, FW), FW * 32, 0, st>>>(s, net, n, w.efeat, Wn, jet, w.wjet));
     PN_LAUNCH("k_message", st, k_message<R><<<nblk((size_t)rows * s.Zd, 256), 256, 0, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H, w.ldH, Wn,
                                                                   T, w.Zb, w.ldZ));
-    if (int e = pn_linear<R>(w.Zb, w.ldZ, net.Gcat + (size_t)n * 3 * s.Zd * s.D, s.D, net.Gb + (size_t)n * s.D, w.X,
+    if (int e = pn_linear<R>(&s, PN_TC_LAYERS, w.Zb, w.ldZ, net.Gcat + (size_t)n * 3 * s.Zd * s.D, s.D, net.Gb + (size_t)n * s.D, w.X,
                              s.D, rows, 3 * s.Zd, s.D, T, 1, st))
       return e;
   }
@@ -605,20 +614,20 @@ int pn_heads(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn, int T, c
   const NetOff& o = net.off;
   const int D = s.D;
   // backflow head kappa on every electron
-  if (int e = pn_linear<R>(w.X, D, net.p + o.kW[0], D, net.p + o.kb[0], w.Zb, w.ldZ, rows, D, D, T, 0, st)) return e;
+  if (int e = pn_linear<R>(&s, PN_TC_HEADS, w.X, D, net.p + o.kW[0], D, net.p + o.kb[0], w.Zb, w.ldZ, rows, D, D, T, 0, st)) return e;
   if (int e = pn_ssp_jet<R>(w.Zb, w.ldZ, groups, T, D, st)) return e;
-  if (int e = pn_linear<R>(w.Zb, w.ldZ, net.p + o.kW[1], D, net.p + o.kb[1], w.H, w.ldH, rows, D, D, T, 0, st)) return e;
+  if (int e = pn_linear<R>(&s, PN_TC_HEADS, w.Zb, w.ldZ, net.p + o.kW[1], D, net.p + o.kb[1], w.H, w.ldH, rows, D, D, T, 0, st)) return e;
   if (int e = pn_ssp_jet<R>(w.H, w.ldH, groups, T, D, st)) return e;
-  if (int e = pn_linear<R>(w.H, w.ldH, net.p + o.kW[2], s.n_orb, net.p + o.kb[2], w.F, s.n_orb, rows, D, s.n_orb, T, 0, st))
+  if (int e = pn_linear<R>(&s, PN_TC_HEADS, w.H, w.ldH, net.p + o.kW[2], s.n_orb, net.p + o.kb[2], w.F, s.n_orb, rows, D, s.n_orb, T, 0, st))
     return e;
   // Jastrow head eta on the electron sum
   PN_LAUNCH("k_sum_electrons", st, k_sum_electrons<R><<<nblk((size_t)Wn * T * D, 256), 256, 0, st>>>(w.X, w.Xs, Wn, s.N, T, D));
   const int rs = Wn * T;
-  if (int e = pn_linear<R>(w.Xs, D, net.p + o.eW[0], D, net.p + o.eb[0], w.As, D, rs, D, D, T, 0, st)) return e;
+  if (int e = pn_linear<R>(&s, PN_TC_HEADS, w.Xs, D, net.p + o.eW[0], D, net.p + o.eb[0], w.As, D, rs, D, D, T, 0, st)) return e;
   if (int e = pn_ssp_jet<R>(w.As, D, (size_t)Wn, T, D, st)) return e;
-  if (int e = pn_linear<R>(w.As, D, net.p + o.eW[1], D, net.p + o.eb[1], w.Bs, D, rs, D, D, T, 0, st)) return e;
+  if (int e = pn_linear<R>(&s, PN_TC_HEADS, w.As, D, net.p + o.eW[1], D, net.p + o.eb[1], w.Bs, D, rs, D, D, T, 0, st)) return e;
   if (int e = pn_ssp_jet<R>(w.Bs, D, (size_t)Wn, T, D, st)) return e;
-  if (int e = pn_linear<R>(w.Bs, D, net.p + o.eW[2], 1, net.p + o.eb[2], w.Jj, 1, rs, D, 1, T, 0, st)) return e;
+  if (int e = pn_linear<R>(&s, PN_TC_HEADS, w.Bs, D, net.p + o.eW[2], 1, net.p + o.eb[2], w.Jj, 1, rs, D, 1, T, 0, st)) return e;
   return PN_OK;
 }
 

@@ -3,9 +3,13 @@
 
 #include "pn_internal.cuh"
 
+// Y (=|+=) X W + b on value rows; float32 layers of group `grp` (a
+// PN_TC_* bit) go to the tensor cores when the system enables that group
+// (s may be null: CUDA cores).
+enum { PN_TC_LAYERS = 1, PN_TC_HEADS = 2, PN_TC_VALUE = 4 };
 template <typename R>
-int pn_linear(const R* X, int ldx, const R* W, int ldw, const R* b, R* Y, int ldy, int rows, int Kd, int Nout, int T,
-              int acc, cudaStream_t st);
+int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw, const R* b, R* Y, int ldy, int rows,
+              int Kd, int Nout, int T, int acc, cudaStream_t st);
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of the multiply-xor
 // bijection with the key bumped by the Weyl constants between rounds.

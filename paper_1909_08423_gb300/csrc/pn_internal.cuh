@@ -81,10 +81,21 @@ struct DevSys {
   const double* feat_isig2;  // [K] 1/sigma^2
   const float* feat_mu32;    // [K] float copies for float32 paths
   const float* feat_isig2_32;
+  // float copies of the orbital tables for the mixed sampler
+  const float* R32;
+  const float* pexp32;
+  const float* pcoef32;
+  const float* mo32;
+  const float* cusp_rc32;
+  const float* cusp_C32;
+  const float* cusp_s32;
+  const float* cusp_a32;
   const int* nuc;         // [N] nucleus each electron starts near (walker init)
   const int* ch_pairs;    // [Ppair] pair indices grouped by filter channel
   int ch_off[4];          // channel c owns ch_pairs[ch_off[c] .. ch_off[c+1])
   int fused_sampler;      // 1: Metropolis through the fused tile kernel when it fits
+  int tensor_cores;       // 1: float32 linear layers on tcgen05 (split tf32)
+  int* dev_err;           // device word: set when a bounded wait expired
 };
 
 // Pair indexing: unordered electron pair (a<b) -> a*N - a*(a+1)/2 + (b-a-1)
@@ -171,6 +182,11 @@ int pn_forward_chunk(const DevSys& s, const DevNet<R>& net, Work<R>& w,
 
 template <typename R>
 DevNet<R> pn_devnet(pn_system_s* sys);
+
+// Tensor-core linear layer (tc_gemm.cu).
+bool pn_tc_supported(int Nout);
+int pn_linear_tc(const float* X, int ldx, const float* W, int ldw, const float* b, float* Y, int ldy, int rows, int K,
+                 int Nout, int T, int acc, int* err, cudaStream_t st);
 
 // Chunked drivers over an explicit workspace (used by the C ABI with the
 // handle's workspace and by the serving loop with per-job workspaces).

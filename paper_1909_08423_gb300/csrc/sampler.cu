@@ -35,6 +35,22 @@ __device__ inline const double* feat_is_of<double>(const DevSys& s) { return s.f
 template <>
 __device__ inline const float* feat_is_of<float>(const DevSys& s) { return s.feat_isig2_32; }
 
+// Orbital tables in the sampler's orbital precision C.
+template <typename C>
+struct OrbTab {
+  const C *R, *pexp, *pcoef, *mo, *rc, *cC, *cs, *ca;
+};
+template <typename C>
+__device__ inline OrbTab<C> orb_tab(const DevSys& s);
+template <>
+__device__ inline OrbTab<double> orb_tab<double>(const DevSys& s) {
+  return {s.R, s.pexp, s.pcoef, s.mo, s.cusp_rc, s.cusp_C, s.cusp_s, s.cusp_a};
+}
+template <>
+__device__ inline OrbTab<float> orb_tab<float>(const DevSys& s) {
+  return {s.R32, s.pexp32, s.pcoef32, s.mo32, s.cusp_rc32, s.cusp_C32, s.cusp_s32, s.cusp_a32};
+}
+
 template <typename R>
 __device__ inline R ssp_(R x) {
   return (x > R(0) ? x : R(0)) + log1p(exp(-fabs(x))) - R(0.69314718055994530942);
@@ -346,7 +362,7 @@ __global__ void __launch_bounds__(256) k_metropolis_fused(DevSys s, DevNet<R> ne
 
 // Per-warp shared-memory layout (bytes).
 struct WLayout {
-  size_t r, rp, d, dr, phi, rad, ic, det, x, h, z, wv, hid, e, F, xs, a1s, a2s, J, bytes;
+  size_t r, rp, rpf, dr, phi, rad, ic, det, x, h, z, wv, hid, e, F, xs, a1s, a2s, J, bytes;
   int G;  // largest pair group of one filter channel
 };
 
@@ -362,10 +378,10 @@ __host__ __device__ inline WLayout make_wlayout(const DevSys& s) {
   const size_t r = sizeof(R);
   L.r = put(N * 3 * 8);
   L.rp = put(N * 3 * 8);
-  L.d = put(P * 8);
+  L.rpf = put(N * 3 * r);
   L.dr = put(P * r);
-  L.phi = put(N * no * 8);
-  L.rad = put(N * (size_t)s.n_shells * 8);
+  L.phi = put(N * no * r);
+  L.rad = put(N * (size_t)s.n_shells * r);
   L.ic = put(N * 4);
   L.det = put((size_t)s.n_det * 4 * 8);
   L.x = put(N * D * r);
@@ -437,30 +453,35 @@ __device__ inline void warp_gemm(int lane, int rows, int K, const R* __restrict_
 
 // Value of every cusp-spliced orbital at every electron, spread over the
 // warp: lanes first take (electron, shell) radial parts, then (electron,
-// orbital) contractions, so that each float64 instruction does up to 32
-// lanes of work.  rad: [N][n_shells] scratch, ic: [N] cusp nucleus or -1.
-__device__ inline void warp_orbitals(const DevSys& s, int lane, const double* __restrict__ rp, double* __restrict__ phi,
-                                     double* __restrict__ rad, int* __restrict__ ic) {
+// orbital) contractions, so that each instruction does up to 32 lanes of
+// work (this matters most in float64, whose warp instructions cost the same
+// on GB300 whatever the active lane count).  Arithmetic in C (double in
+// PN_FP64, float in PN_MIXED, where only the acceptance ratio needs it).
+// rp: [N][3] positions in C; rad: [N][n_shells] scratch; ic: [N].
+template <typename C>
+__device__ inline void warp_orbitals(const DevSys& s, int lane, const C* __restrict__ rp, C* __restrict__ phi,
+                                     C* __restrict__ rad, int* __restrict__ ic) {
+  const OrbTab<C> t = orb_tab<C>(s);
   const int N = s.N, ns = s.n_shells, no = s.n_orb;
   for (int i = lane; i < N; i += 32) {
     int Ic = -1;
     if (s.use_cusp)
       for (int I = 0; I < s.M; ++I) {
-        const double v0 = rp[3 * i] - s.R[3 * I], v1 = rp[3 * i + 1] - s.R[3 * I + 1], v2 = rp[3 * i + 2] - s.R[3 * I + 2];
-        if (v0 * v0 + v1 * v1 + v2 * v2 < s.cusp_rc[I] * s.cusp_rc[I]) Ic = I;
+        const C v0 = rp[3 * i] - t.R[3 * I], v1 = rp[3 * i + 1] - t.R[3 * I + 1], v2 = rp[3 * i + 2] - t.R[3 * I + 2];
+        if (v0 * v0 + v1 * v1 + v2 * v2 < t.rc[I] * t.rc[I]) Ic = I;
       }
     ic[i] = Ic;
   }
   for (int q = lane; q < N * ns; q += 32) {
     const int i = q / ns, sh = q % ns;
     const int c = s.sh_center[sh], np = s.sh_nprim[sh], po = s.sh_poff[sh];
-    const double v0 = rp[3 * i] - s.R[3 * c], v1 = rp[3 * i + 1] - s.R[3 * c + 1], v2 = rp[3 * i + 2] - s.R[3 * c + 2];
-    const double r2 = v0 * v0 + v1 * v1 + v2 * v2;
-    double e = 0;
+    const C v0 = rp[3 * i] - t.R[3 * c], v1 = rp[3 * i + 1] - t.R[3 * c + 1], v2 = rp[3 * i + 2] - t.R[3 * c + 2];
+    const C r2 = v0 * v0 + v1 * v1 + v2 * v2;
+    C e = 0;
     if (s.sh_l[sh] == -1) {
-      e = s.pcoef[po] * exp(-s.pexp[po] * sqrt(r2));
+      e = t.pcoef[po] * exp(-t.pexp[po] * sqrt(r2));
     } else {
-      for (int k = 0; k < np; ++k) e += s.pcoef[po + k] * exp(-s.pexp[po + k] * r2);
+      for (int k = 0; k < np; ++k) e += t.pcoef[po + k] * exp(-t.pexp[po + k] * r2);
     }
     rad[q] = e;
   }
@@ -468,17 +489,17 @@ __device__ inline void warp_orbitals(const DevSys& s, int lane, const double* __
   for (int q = lane; q < N * no; q += 32) {
     const int i = q / no, mu = q % no;
     const int Ic = ic[i];
-    double acc = 0;
+    C acc = 0;
     for (int sh = 0; sh < ns; ++sh) {
       const int c = s.sh_center[sh], l = s.sh_l[sh], bo = s.sh_boff[sh];
-      const double e = rad[i * ns + sh];
+      const C e = rad[i * ns + sh];
       if (l <= 0) {
         if (l == 0 && c == Ic && s.cusp_on[Ic * no + mu]) continue;  // replaced inside the cusp sphere
-        acc += s.mo[(size_t)bo * no + mu] * e;
+        acc += t.mo[(size_t)bo * no + mu] * e;
         continue;
       }
-      const double v0 = rp[3 * i] - s.R[3 * c], v1 = rp[3 * i + 1] - s.R[3 * c + 1], v2 = rp[3 * i + 2] - s.R[3 * c + 2];
-      const double* m = s.mo + (size_t)bo * no + mu;
+      const C v0 = rp[3 * i] - t.R[3 * c], v1 = rp[3 * i + 1] - t.R[3 * c + 1], v2 = rp[3 * i + 2] - t.R[3 * c + 2];
+      const C* m = t.mo + (size_t)bo * no + mu;
       if (l == 1) {
         acc += e * (m[0] * v0 + m[no] * v1 + m[2 * no] * v2);
       } else {
@@ -487,16 +508,35 @@ __device__ inline void warp_orbitals(const DevSys& s, int lane, const double* __
       }
     }
     if (Ic >= 0 && s.cusp_on[Ic * no + mu]) {
-      const double v0 = rp[3 * i] - s.R[3 * Ic], v1 = rp[3 * i + 1] - s.R[3 * Ic + 1], v2 = rp[3 * i + 2] - s.R[3 * Ic + 2];
-      const double d = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+      const C v0 = rp[3 * i] - t.R[3 * Ic], v1 = rp[3 * i + 1] - t.R[3 * Ic + 1], v2 = rp[3 * i + 2] - t.R[3 * Ic + 2];
+      const C d = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
       const int k = Ic * no + mu;
-      const double* a = s.cusp_a + (size_t)k * 5;
-      const double p = a[0] + d * (a[1] + d * (a[2] + d * (a[3] + d * a[4])));
-      acc += s.cusp_C[k] + s.cusp_s[k] * exp(p);
+      const C* a = t.ca + (size_t)k * 5;
+      const C p = a[0] + d * (a[1] + d * (a[2] + d * (a[3] + d * a[4])));
+      acc += t.cC[k] + t.cs[k] * exp(p);
     }
     phi[q] = acc;
   }
   __syncwarp();
+}
+
+// One Box-Muller pair in C precision from the shared Philox stream.
+template <typename C>
+__device__ inline void normal_pair(unsigned long long seed, unsigned walker, unsigned long long step, unsigned j,
+                                   int pair, C out[2]) {
+  if constexpr (sizeof(C) == 8) {
+    pn_normal_pair(seed, walker, step, j, pair, out);
+  } else {
+    unsigned c[4] = {j, walker, (unsigned)(step & 0xffffffffull), (unsigned)(step >> 32)};
+    pn_philox(c, (unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
+    const float u0 = ((float)c[2 * pair] + 0.5f) * 2.3283064365386963e-10f;
+    const float u1 = ((float)c[2 * pair + 1] + 0.5f) * 2.3283064365386963e-10f;
+    const float rad = sqrtf(-2.0f * logf(u0));
+    float sn, cs;
+    sincospif(2.0f * u1, &sn, &cs);
+    out[0] = rad * cs;
+    out[1] = rad * sn;
+  }
 }
 
 template <typename R>
@@ -512,10 +552,10 @@ __global__ void __launch_bounds__(256) k_metropolis_warp(DevSys s, DevNet<R> net
   unsigned char* base = smem + (size_t)wid * L.bytes;
   double* sr = (double*)(base + L.r);
   double* srp = (double*)(base + L.rp);
-  double* sd = (double*)(base + L.d);
+  R* srpf = (R*)(base + L.rpf);
   R* sdr = (R*)(base + L.dr);
-  double* sphi = (double*)(base + L.phi);
-  double* srad = (double*)(base + L.rad);
+  R* sphi = (R*)(base + L.phi);
+  R* srad = (R*)(base + L.rad);
   int* sic = (int*)(base + L.ic);
   double* sdet = (double*)(base + L.det);
   R* sx = (R*)(base + L.x);
@@ -539,31 +579,36 @@ __global__ void __launch_bounds__(256) k_metropolis_warp(DevSys s, DevNet<R> net
   __syncwarp();
   for (int k = 0; k < n_steps; ++k) {
     const unsigned long long step = step0 + (unsigned long long)k;
+    // proposal; positions stay float64, the value pass reads an R copy
     for (int q = lane; q < 2 * nblk4; q += 32) {
       const int j = q >> 1, pr = q & 1;
       if (4 * j + 2 * pr >= n3) continue;
-      double zz[2];
-      pn_normal_pair(seed, wid_g, step, j, pr, zz);
-      for (int t = 0; t < 2; ++t)
-        if (4 * j + 2 * pr + t < n3) srp[4 * j + 2 * pr + t] = sr[4 * j + 2 * pr + t] + sigma * zz[t];
+      R zz[2];
+      normal_pair<R>(seed, wid_g, step, j, pr, zz);
+      for (int t = 0; t < 2; ++t) {
+        const int m = 4 * j + 2 * pr + t;
+        if (m < n3) {
+          srp[m] = sr[m] + sigma * (double)zz[t];
+          srpf[m] = (R)srp[m];
+        }
+      }
     }
     __syncwarp();
+    const OrbTab<R> tab = orb_tab<R>(s);
     for (int p = lane; p < P; p += 32) {
-      double v[3];
+      R v[3];
       if (p < s.Pee) {
         int a = 0, rem = p;
         while (rem >= N - 1 - a) { rem -= N - 1 - a; ++a; }
         const int bb = a + 1 + rem;
-        for (int x = 0; x < 3; ++x) v[x] = srp[3 * a + x] - srp[3 * bb + x];
+        for (int x = 0; x < 3; ++x) v[x] = srpf[3 * a + x] - srpf[3 * bb + x];
       } else {
         const int q = p - s.Pee, i = q / s.M, I = q % s.M;
-        for (int x = 0; x < 3; ++x) v[x] = srp[3 * i + x] - s.R[3 * I + x];
+        for (int x = 0; x < 3; ++x) v[x] = srpf[3 * i + x] - tab.R[3 * I + x];
       }
-      const double dd = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-      sd[p] = dd;
-      sdr[p] = (R)dd;
+      sdr[p] = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     }
-    warp_orbitals(s, lane, srp, sphi, srad, sic);
+    warp_orbitals<R>(s, lane, srpf, sphi, srad, sic);
     for (int q = lane; q < N * D; q += 32) sx[q] = net.p[o.x0 + q % D];
     __syncwarp();
     for (int n = 0; n < s.L; ++n) {
@@ -653,7 +698,7 @@ __global__ void __launch_bounds__(256) k_metropolis_warp(DevSys s, DevNet<R> net
         for (int a = 0; a < ns; ++a)
           for (int bb = 0; bb < ns; ++bb) {
             const int i = e0 + a, mu = occ[bb];
-            A[a * ns + bb] = sphi[(size_t)i * no + mu] * (1.0 + (double)sF[(size_t)i * no + mu]);
+            A[a * ns + bb] = (double)sphi[(size_t)i * no + mu] * (1.0 + (double)sF[(size_t)i * no + mu]);
           }
         pn_slogdet(A, ns, &ld, &sg);
       }
@@ -668,7 +713,8 @@ __global__ void __launch_bounds__(256) k_metropolis_warp(DevSys s, DevNet<R> net
       if (s.ci[p] != 0.0 && sg != 0.0) m = fmax(m, sdet[4 * p] + sdet[4 * p + 2]);
     }
     for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-    double S = 0, gam = 0;
+    double S = 0;
+    R gam = 0;
     if (m > -INFINITY)
       for (int p = lane; p < nd; p += 32) {
         const double sg = sdet[4 * p + 1] * sdet[4 * p + 3];
@@ -679,18 +725,22 @@ __global__ void __launch_bounds__(256) k_metropolis_warp(DevSys s, DevNet<R> net
         int a = 0, rem = p;
         while (rem >= N - 1 - a) { rem -= N - 1 - a; ++a; }
         const int bb = a + 1 + rem;
-        const double c = ((a < s.n_up) == (bb < s.n_up)) ? 0.25 : 0.5;
-        gam -= c / (1.0 + sd[p]);
+        const R c = ((a < s.n_up) == (bb < s.n_up)) ? R(0.25) : R(0.5);
+        gam -= c / (R(1) + sdr[p]);
       }
     for (int off = 16; off > 0; off >>= 1) {
       S += __shfl_xor_sync(0xffffffffu, S, off);
       gam += __shfl_xor_sync(0xffffffffu, gam, off);
     }
-    const double lpn = gam + (double)sJ[0] + m + log(fabs(S));
+    const double lpn = (double)gam + (double)sJ[0] + m + log(fabs(S));
     unsigned c4[4] = {(unsigned)nblk4, wid_g, (unsigned)(step & 0xffffffffull), (unsigned)(step >> 32)};
     pn_philox(c4, (unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
-    const double u = pn_u01(c4[0]);
-    const bool accept = u < exp(2.0 * (lpn - lpw));
+    bool accept;
+    if constexpr (sizeof(R) == 8) {
+      accept = pn_u01(c4[0]) < exp(2.0 * (lpn - lpw));
+    } else {
+      accept = ((float)c4[0] + 0.5f) * 2.3283064365386963e-10f < expf((float)(2.0 * (lpn - lpw)));
+    }
     if (accept) {
       for (int q = lane; q < n3; q += 32) sr[q] = srp[q];
       lpw = lpn;

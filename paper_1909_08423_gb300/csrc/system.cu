@@ -435,6 +435,7 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   ds.Pee = N * (N - 1) / 2; ds.Pen = N * d->M; ds.Ppair = ds.Pee + ds.Pen;
   ds.r_c = d->r_c; ds.use_cusp = d->use_cusp; ds.use_gamma = d->use_gamma;
   ds.fused_sampler = 1;
+  ds.tensor_cores = 0;  // set per system after calibration (PN_OPT_TENSOR_CORES)
   double Vnn = 0;
   for (int I = 0; I < d->M; ++I)
     for (int J = I + 1; J < d->M; ++J) {
@@ -494,8 +495,26 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
     for (int k = 0; k < d->n_dn; ++k) nuc[d->n_up + k] = lst[(2 * k + 1) % lst.size()];
     ds.nuc = dev_upload(s, nuc.data(), nuc.size(), &err);
   }
+  {
+    int zero = 0;
+    ds.dev_err = dev_upload(s, &zero, 1, &err);
+  }
   ds.feat_mu = dev_upload(s, fmu.data(), fmu.size(), &err);
   ds.feat_isig2 = dev_upload(s, fis.data(), fis.size(), &err);
+  {
+    auto f32 = [&](const double* src, size_t n) {
+      std::vector<float> v(src, src + n);
+      return dev_upload(s, v.data(), v.size(), &err);
+    };
+    ds.R32 = f32(d->R, 3 * (size_t)d->M);
+    ds.pexp32 = f32(h.pe.data(), h.pe.size());
+    ds.pcoef32 = f32(h.pc.data(), h.pc.size());
+    ds.mo32 = f32(h.mo.data(), h.mo.size());
+    ds.cusp_rc32 = f32(crc.data(), crc.size());
+    ds.cusp_C32 = f32(cC.data(), cC.size());
+    ds.cusp_s32 = f32(cS.data(), cS.size());
+    ds.cusp_a32 = f32(cA.data(), cA.size());
+  }
   {
     std::vector<float> fmu32(fmu.begin(), fmu.end()), fis32(fis.begin(), fis.end());
     ds.feat_mu32 = dev_upload(s, fmu32.data(), fmu32.size(), &err);
