@@ -65,6 +65,10 @@ def algorithmic_flops(sysd, kernel, mode):
         # value: 2 per partner; derivative rows 4; Laplacian row ~ 20
         per_row = 2 if T == 1 else (2 + 4 * (T - 2) + 20) / T
         return L * N * T * Zd * (N - 1 + M) * per_row
+    if kernel in ("k_metropolis_warp", "k_metropolis_fused"):
+        # one value pass of the network per walker-step (float32 work):
+        # filters, h and receiving maps, messages, both heads
+        return sum(algorithmic_flops(sysd, k, "value") for k in ("k_filter", "k_linear", "k_message"))
     if kernel == "k_slater":
         nsig = [sysd["n_up"], sysd["n_dn"]]
         f = 0
@@ -239,6 +243,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=60)
     ap.add_argument("--serve-only", action="store_true")
+    ap.add_argument("--case", choices=["sampler", "jet_tc"], default=None,
+                    help="run one small kernel case (for ncu captures) and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -246,6 +252,25 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_1909_08423_gb300 import binding, synth
+
+    if args.case:
+        torch.cuda.set_device(0)
+        sysd = synth.be()
+        s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=W_PER_RANK)
+        r = torch.empty(W_PER_RANK, s.N, 3, dtype=torch.float64, device="cuda")
+        s.init_walkers(r, 1)
+        if args.case == "sampler":  # 5 Metropolis steps of the Be workload
+            lp = torch.empty(W_PER_RANK, dtype=torch.float64, device="cuda")
+            sg = torch.empty_like(lp)
+            s.eval_logpsi(r, lp, sg)
+            s.metropolis_step(r, lp, 5, SIGMA, 3, 0)
+        else:  # one local-energy pass with every layer group on tcgen05
+            s.set_option(binding.PN_OPT_TENSOR_CORES, 7)
+            E = torch.empty(W_PER_RANK, dtype=torch.float64, device="cuda")
+            s.eval_local_energy(r, E)
+        s.device_status()
+        print("case ok", flush=True)
+        return
 
     if args.serve_only:
         torch.cuda.set_device(0)
@@ -415,6 +440,8 @@ def main():
         if dom in ("k_filter", "k_linear", "k_message", "k_slater"):
             per_step_flops = W * (N_METROPOLIS * algorithmic_flops(sysd, dom, "value") +
                                   algorithmic_flops(sysd, dom, "jet"))
+        elif dom in ("k_metropolis_warp", "k_metropolis_fused"):
+            per_step_flops = W * N_METROPOLIS * algorithmic_flops(sysd, dom, "value")
         kern_ms_per_step = kern[1] / args.steps
         if per_step_flops:
             achieved = per_step_flops / (kern_ms_per_step / 1e3) / 1e12
@@ -423,7 +450,10 @@ def main():
             roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": achieved / fp32_peak, "traffic": None,
                     "launches_per_step": kern[0] / args.steps, "kernel_ms_per_step": kern_ms_per_step,
-                    "peak_source": "fp32 CUDA-core nominal from unit counts and max clock"}
+                    "peak_source": "fp32 CUDA-core nominal from unit counts and max clock",
+                    "flops_per_step": per_step_flops,
+                    "note": "algorithmic float32 network FLOPs of the launches timed; the sampler also "
+                            "runs float64 determinants and log-sums"}
         else:
             roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
                     "traffic": None, "kernel_ms_per_step": kern_ms_per_step}

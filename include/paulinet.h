@@ -195,9 +195,12 @@ int pn_metropolis_step(pn_system_t sys, double* r, double* logabs, int W,
  * beyond floating-point rounding).
  * PN_OPT_FUSED_SAMPLER (default 1): run Metropolis steps in one launch that
  *   keeps walkers in shared memory for all steps -- one warp per walker for
- *   small systems (up to 24 KiB of state per walker), else a tile of walkers
- *   per block; 2 forces the tile kernel; 0 (or a system too large for one
- *   tile) uses one kernel per stage.
+ *   small systems (up to 24 KiB of state per walker; weights read through
+ *   L1/L2), else a tile of walkers per block; 2 forces the tile kernel; 3
+ *   the warp kernel with its block's warps walking the layers in lockstep
+ *   and each weight block bulk-copied (TMA) into shared memory one stage
+ *   ahead; 0 (or a system too large for one tile) uses one kernel per
+ *   stage.
  * PN_OPT_TENSOR_CORES (PN_MIXED only; default 0): a mask of the float32
  *   linear layers that run on tcgen05 with each operand split into three
  *   bf16 pieces (six products, float32 accumulation in tensor memory):

@@ -356,7 +356,7 @@ extern "C" int pn_set_option(pn_system_t s, int option, int value) {
   if (!s) { pn_set_error("null system"); return PN_EINVAL; }
   switch (option) {
     case PN_OPT_FUSED_SAMPLER:
-      if (value < 0 || value > 2) { pn_set_error("fused sampler option takes 0, 1 or 2"); return PN_EINVAL; }
+      if (value < 0 || value > 3) { pn_set_error("fused sampler option takes 0..3"); return PN_EINVAL; }
       s->ds.fused_sampler = value;
       return PN_OK;
     case PN_OPT_TENSOR_CORES:

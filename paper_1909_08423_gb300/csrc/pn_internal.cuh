@@ -136,13 +136,28 @@ struct Work {
 
 size_t pn_work_bytes(const DevSys& s, int Wc, int T, int elem);
 
+// Weight blocks of the fused sampler in the order it consumes them: per
+// layer h, (W1, W2) for the three filter channels, stacked receiving maps;
+// then kappa 1..3 and eta 1..3.  Each block starts 16-byte aligned in a
+// packed copy of the weights so that it can be bulk-copied (TMA) into
+// shared memory.
+constexpr int PN_MAX_STAGES = 8 * PN_MAX_LAYERS + 6;
+struct StageTab {
+  int n;                        // stages per Metropolis step
+  int max_bytes;                // largest block
+  int64_t off[PN_MAX_STAGES];   // element offset in the packed weights
+  int bytes[PN_MAX_STAGES];     // block size in bytes (multiple of 16)
+};
+
 // Per-precision parameters on the device.
 template <typename R>
 struct DevNet {
-  const R* p;     // flat parameter vector in R
-  const R* Gcat;  // [L][3 Zd][D]  same, anti, nuc receiving maps stacked
-  const R* Gb;    // [L][D]        sum of the three receiving biases
+  const R* p;      // flat parameter vector in R
+  const R* Gcat;   // [L][3 Zd][D]  same, anti, nuc receiving maps stacked
+  const R* Gb;     // [L][D]        sum of the three receiving biases
+  const R* wpack;  // sampler weight blocks, 16-byte aligned (see StageTab)
   NetOff off;
+  StageTab stab;
 };
 
 struct pn_system_s {
@@ -161,6 +176,9 @@ struct pn_system_s {
   float* Gb32;
   void* work_mem;
   size_t work_bytes;
+  StageTab stab64, stab32;  // packed sampler weights per precision
+  double* wpack64;
+  float* wpack32;
   void* tape_mem;          // backward tape (grown on demand)
   size_t tape_bytes;
   Work<double> w64;

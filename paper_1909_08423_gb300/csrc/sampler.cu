@@ -400,9 +400,10 @@ __host__ __device__ inline WLayout make_wlayout(const DevSys& s) {
 }
 
 // Y[q] (=|+=) act(X[q] W + b), q < rows; lanes over output columns.
-template <typename R, bool SSP, bool ACC, class RX, class RY>
+template <typename R, bool SSP, bool ACC, bool LDG = true, class RX, class RY>
 __device__ inline void warp_gemm(int lane, int rows, int K, const R* __restrict__ W, int Nout, const R* __restrict__ b,
                                  RX rx, RY ry) {
+  auto ldw = [&](const R* p) { return LDG ? __ldg(p) : *p; };
   for (int col = lane; col < Nout; col += 32) {
     const R bias = b ? __ldg(b + col) : R(0);
     const R* wc = W + col;
@@ -421,8 +422,8 @@ __device__ inline void warp_gemm(int lane, int rows, int K, const R* __restrict_
           for (; k < K; k += 4) {
             const float4 p0 = *(const float4*)(x0 + k), p1 = *(const float4*)(x1 + k);
             const float4 p2 = *(const float4*)(x2 + k), p3 = *(const float4*)(x3 + k);
-            const R w0 = __ldg(wc + (size_t)k * Nout), w1 = __ldg(wc + (size_t)(k + 1) * Nout);
-            const R w2 = __ldg(wc + (size_t)(k + 2) * Nout), w3 = __ldg(wc + (size_t)(k + 3) * Nout);
+            const R w0 = ldw(wc + (size_t)k * Nout), w1 = ldw(wc + (size_t)(k + 1) * Nout);
+            const R w2 = ldw(wc + (size_t)(k + 2) * Nout), w3 = ldw(wc + (size_t)(k + 3) * Nout);
             a0 += p0.x * w0 + p0.y * w1 + p0.z * w2 + p0.w * w3;
             a1 += p1.x * w0 + p1.y * w1 + p1.z * w2 + p1.w * w3;
             a2 += p2.x * w0 + p2.y * w1 + p2.z * w2 + p2.w * w3;
@@ -432,7 +433,7 @@ __device__ inline void warp_gemm(int lane, int rows, int K, const R* __restrict_
       }
 #pragma unroll 4
       for (; k < K; ++k) {
-        const R w = __ldg(wc + (size_t)k * Nout);
+        const R w = ldw(wc + (size_t)k * Nout);
         a0 += x0[k] * w;
         a1 += x1[k] * w;
         a2 += x2[k] * w;
@@ -539,16 +540,42 @@ __device__ inline void normal_pair(unsigned long long seed, unsigned walker, uns
   }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256) k_metropolis_warp(DevSys s, DevNet<R> net, WLayout L, double* __restrict__ r,
-                                                         double* __restrict__ lp, int W, unsigned walker0, int n_steps,
-                                                         double sigma, unsigned long long seed,
-                                                         unsigned long long step0,
+__device__ inline uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline bool bar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ inline bool bar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (bar_try(bar, parity)) return true;
+  return false;
+}
+
+// STAGED: the warps of a block walk the network in lockstep and each
+// weight block is bulk-copied (cp.async.bulk, completion on an mbarrier)
+// from the packed weights into one of two shared buffers, one stage ahead
+// of its use.  Otherwise each warp reads the packed weights through L1.
+template <typename R, bool STAGED>
+__global__ void __launch_bounds__(256) k_metropolis_warp(DevSys s, DevNet<R> net, WLayout L, StageTab st,
+                                                         const R* __restrict__ wpack, int wbuf_off, int wbuf_bytes,
+                                                         double* __restrict__ r, double* __restrict__ lp, int W,
+                                                         unsigned walker0, int n_steps, double sigma,
+                                                         unsigned long long seed, unsigned long long step0,
                                                          unsigned long long* __restrict__ n_acc) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ __align__(8) uint64_t wbar[2];
+  __shared__ int abort_flag;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, tid = threadIdx.x;
   const int w = blockIdx.x * (blockDim.x >> 5) + wid;
-  if (w >= W) return;  // whole warps only; no block-wide barrier below
+  const bool active = w < W;
+  if (!STAGED && !active) return;  // without block barriers idle warps can leave
   unsigned char* base = smem + (size_t)wid * L.bytes;
   double* sr = (double*)(base + L.r);
   double* srp = (double*)(base + L.rp);
@@ -569,189 +596,310 @@ __global__ void __launch_bounds__(256) k_metropolis_warp(DevSys s, DevNet<R> net
   R* sa1 = (R*)(base + L.a1s);
   R* sa2 = (R*)(base + L.a2s);
   R* sJ = (R*)(base + L.J);
+  R* wbuf[2] = {(R*)(smem + wbuf_off), (R*)(smem + wbuf_off + wbuf_bytes)};
   const int N = s.N, P = s.Ppair, D = s.D, Zd = s.Zd, K = s.K, Hw = s.Hw, no = s.n_orb, nd = s.n_det;
   const int n3 = 3 * N, nblk4 = (n3 + 3) / 4;
   const NetOff& o = net.off;
   const unsigned wid_g = walker0 + (unsigned)w;
-  for (int i = lane; i < n3; i += 32) sr[i] = r[(size_t)w * n3 + i];
-  double lpw = lp[w];
+
+  // -- weight stages
+  const long total = (long)n_steps * st.n;
+  long g = 0;  // stage counter over all steps
+  auto issue = [&](long q) {
+    if (q >= total) return;
+    const int j = (int)(q % st.n), b = (int)(q & 1);
+    const uint32_t bar = smem_addr(&wbar[b]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(st.bytes[j]) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(wbuf[b])),
+                 "l"(wpack + st.off[j]), "r"(st.bytes[j]), "r"(bar)
+                 : "memory");
+  };
+  auto acquire = [&]() -> const R* {
+    const int j = (int)(g % st.n);
+    if (!STAGED) return wpack + st.off[j];
+    const int b = (int)(g & 1);
+    if (!bar_wait(smem_addr(&wbar[b]), (uint32_t)((g >> 1) & 1))) abort_flag = 1;
+    return wbuf[b];
+  };
+  auto release = [&]() {
+    if (STAGED) {
+      __syncthreads();  // every warp is done with this buffer
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(g + 2);
+      }
+    }
+    ++g;
+  };
+  if (STAGED) {
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&wbar[0])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&wbar[1])));
+      asm volatile("fence.mbarrier_init.release.cluster;");
+      abort_flag = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      issue(0);
+      issue(1);
+    }
+  }
+
+  double lpw = 0;
   unsigned naccw = 0;
+  if (active) {
+    for (int i = lane; i < n3; i += 32) sr[i] = r[(size_t)w * n3 + i];
+    lpw = lp[w];
+  }
   __syncwarp();
   for (int k = 0; k < n_steps; ++k) {
     const unsigned long long step = step0 + (unsigned long long)k;
-    // proposal; positions stay float64, the value pass reads an R copy
-    for (int q = lane; q < 2 * nblk4; q += 32) {
-      const int j = q >> 1, pr = q & 1;
-      if (4 * j + 2 * pr >= n3) continue;
-      R zz[2];
-      normal_pair<R>(seed, wid_g, step, j, pr, zz);
-      for (int t = 0; t < 2; ++t) {
-        const int m = 4 * j + 2 * pr + t;
-        if (m < n3) {
-          srp[m] = sr[m] + sigma * (double)zz[t];
-          srpf[m] = (R)srp[m];
+    if (active) {
+      // proposal; positions stay float64, the value pass reads an R copy
+      for (int q = lane; q < 2 * nblk4; q += 32) {
+        const int j = q >> 1, pr = q & 1;
+        if (4 * j + 2 * pr >= n3) continue;
+        R zz[2];
+        normal_pair<R>(seed, wid_g, step, j, pr, zz);
+        for (int t = 0; t < 2; ++t) {
+          const int m = 4 * j + 2 * pr + t;
+          if (m < n3) {
+            srp[m] = sr[m] + sigma * (double)zz[t];
+            srpf[m] = (R)srp[m];
+          }
         }
       }
-    }
-    __syncwarp();
-    const OrbTab<R> tab = orb_tab<R>(s);
-    for (int p = lane; p < P; p += 32) {
-      R v[3];
-      if (p < s.Pee) {
-        int a = 0, rem = p;
-        while (rem >= N - 1 - a) { rem -= N - 1 - a; ++a; }
-        const int bb = a + 1 + rem;
-        for (int x = 0; x < 3; ++x) v[x] = srpf[3 * a + x] - srpf[3 * bb + x];
-      } else {
-        const int q = p - s.Pee, i = q / s.M, I = q % s.M;
-        for (int x = 0; x < 3; ++x) v[x] = srpf[3 * i + x] - tab.R[3 * I + x];
+      __syncwarp();
+      const OrbTab<R> tab = orb_tab<R>(s);
+      for (int p = lane; p < P; p += 32) {
+        R v[3];
+        if (p < s.Pee) {
+          int a = 0, rem = p;
+          while (rem >= N - 1 - a) { rem -= N - 1 - a; ++a; }
+          const int bb = a + 1 + rem;
+          for (int x = 0; x < 3; ++x) v[x] = srpf[3 * a + x] - srpf[3 * bb + x];
+        } else {
+          const int q = p - s.Pee, i = q / s.M, I = q % s.M;
+          for (int x = 0; x < 3; ++x) v[x] = srpf[3 * i + x] - tab.R[3 * I + x];
+        }
+        sdr[p] = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
       }
-      sdr[p] = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      warp_orbitals<R>(s, lane, srpf, sphi, srad, sic);
+      for (int q = lane; q < N * D; q += 32) sx[q] = net.p[o.x0 + q % D];
+      __syncwarp();
     }
-    warp_orbitals<R>(s, lane, srpf, sphi, srad, sic);
-    for (int q = lane; q < N * D; q += 32) sx[q] = net.p[o.x0 + q % D];
-    __syncwarp();
     for (int n = 0; n < s.L; ++n) {
-      warp_gemm<R, false, false>(
-          lane, N, D, net.p + o.hW[n], Zd, net.p + o.hb[n], [&](int q) { return (const R*)(sx + (size_t)q * D); },
-          [&](int q) { return sh + (size_t)q * Zd; });
+      {
+        const R* Wt = acquire();
+        if (active)
+          warp_gemm<R, false, false, !STAGED>(
+              lane, N, D, Wt, Zd, net.p + o.hb[n], [&](int q) { return (const R*)(sx + (size_t)q * D); },
+              [&](int q) { return sh + (size_t)q * Zd; });
+        release();
+      }
       for (int c = 0; c < 3; ++c) {
         const int cnt = s.ch_off[c + 1] - s.ch_off[c];
-        if (cnt == 0) continue;
         const int* pl = s.ch_pairs + s.ch_off[c];
-        // distance features of this channel's pairs
-        const R* fm = feat_mu_of<R>(s);
-        const R* fi = feat_is_of<R>(s);
-        for (int q = lane; q < cnt * K; q += 32) {
-          const int g = q / K, kk = q % K;
-          const R d = sdr[pl[g]];
-          const R dm = d - fm[kk];
-          se[q] = d * d * exp(-d - dm * dm * fi[kk]);
-        }
-        __syncwarp();
-        warp_gemm<R, true, false>(
-            lane, cnt, K, net.p + o.W1[n][c], Hw, net.p + o.b1[n][c],
-            [&](int q) { return (const R*)(se + (size_t)q * K); }, [&](int q) { return shid + (size_t)q * Hw; });
-        __syncwarp();
-        warp_gemm<R, false, false>(
-            lane, cnt, Hw, net.p + o.W2[n][c], Zd, net.p + o.b2[n][c],
-            [&](int q) { return (const R*)(shid + (size_t)q * Hw); }, [&](int q) { return swv + (size_t)pl[q] * Zd; });
-        __syncwarp();
-      }
-      for (int q = lane; q < N * Zd; q += 32) {
-        const int z = q % Zd, i = q / Zd;
-        R zs = 0, za = 0, zn = 0;
-        const bool si = i < s.n_up;
-        for (int j = 0; j < N; ++j) {
-          if (j == i) continue;
-          const int p = i < j ? pn_pair_index(i, j, N) : pn_pair_index(j, i, N);
-          const R v = swv[(size_t)p * Zd + z] * sh[(size_t)j * Zd + z];
-          if ((j < s.n_up) == si) zs += v; else za += v;
-        }
-        for (int I = 0; I < s.M; ++I) zn += swv[(size_t)(s.Pee + i * s.M + I) * Zd + z] * net.p[o.Y + I * Zd + z];
-        R* zo = sz + (size_t)i * 3 * Zd;
-        zo[z] = zs;
-        zo[Zd + z] = za;
-        zo[2 * Zd + z] = zn;
-      }
-      __syncwarp();
-      warp_gemm<R, false, true>(
-          lane, N, 3 * Zd, net.Gcat + (size_t)n * 3 * Zd * D, D, net.Gb + (size_t)n * D,
-          [&](int q) { return (const R*)(sz + (size_t)q * 3 * Zd); }, [&](int q) { return sx + (size_t)q * D; });
-      __syncwarp();
-    }
-    // heads
-    for (int dd = lane; dd < D; dd += 32) {
-      R acc = 0;
-      for (int i = 0; i < N; ++i) acc += sx[(size_t)i * D + dd];
-      sxs[dd] = acc;
-    }
-    warp_gemm<R, true, false>(
-        lane, N, D, net.p + o.kW[0], D, net.p + o.kb[0], [&](int q) { return (const R*)(sx + (size_t)q * D); },
-        [&](int q) { return sz + (size_t)q * D; });
-    __syncwarp();
-    warp_gemm<R, true, false>(
-        lane, N, D, net.p + o.kW[1], D, net.p + o.kb[1], [&](int q) { return (const R*)(sz + (size_t)q * D); },
-        [&](int q) { return swv + (size_t)q * D; });
-    warp_gemm<R, true, false>(
-        lane, 1, D, net.p + o.eW[0], D, net.p + o.eb[0], [&](int q) { return (const R*)sxs; },
-        [&](int q) { return sa1; });
-    __syncwarp();
-    warp_gemm<R, false, false>(
-        lane, N, D, net.p + o.kW[2], no, net.p + o.kb[2], [&](int q) { return (const R*)(swv + (size_t)q * D); },
-        [&](int q) { return sF + (size_t)q * no; });
-    warp_gemm<R, true, false>(
-        lane, 1, D, net.p + o.eW[1], D, net.p + o.eb[1], [&](int q) { return (const R*)sa1; },
-        [&](int q) { return sa2; });
-    __syncwarp();
-    warp_gemm<R, false, false>(
-        lane, 1, D, net.p + o.eW[2], 1, net.p + o.eb[2], [&](int q) { return (const R*)sa2; },
-        [&](int q) { return sJ; });
-    // determinants: one lane per (determinant, spin)
-    for (int q = lane; q < nd * 2; q += 32) {
-      const int sp = q & 1, p = q >> 1;
-      const int ns = sp ? s.n_dn : s.n_up, e0 = sp ? s.n_up : 0;
-      double ld = 0, sg = 1;
-      if (ns > 0) {
-        double A[PN_MAX_SPIN * PN_MAX_SPIN];
-        const int* occ = s.occ + p * N + e0;
-        for (int a = 0; a < ns; ++a)
-          for (int bb = 0; bb < ns; ++bb) {
-            const int i = e0 + a, mu = occ[bb];
-            A[a * ns + bb] = (double)sphi[(size_t)i * no + mu] * (1.0 + (double)sF[(size_t)i * no + mu]);
+        {
+          const R* Wt = acquire();
+          if (active && cnt > 0) {
+            // distance features of this channel's pairs
+            const R* fm = feat_mu_of<R>(s);
+            const R* fi = feat_is_of<R>(s);
+            for (int q = lane; q < cnt * K; q += 32) {
+              const int gg = q / K, kk = q % K;
+              const R d = sdr[pl[gg]];
+              const R dm = d - fm[kk];
+              se[q] = d * d * exp(-d - dm * dm * fi[kk]);
+            }
+            __syncwarp();
+            warp_gemm<R, true, false, !STAGED>(
+                lane, cnt, K, Wt, Hw, net.p + o.b1[n][c], [&](int q) { return (const R*)(se + (size_t)q * K); },
+                [&](int q) { return shid + (size_t)q * Hw; });
+            __syncwarp();
           }
-        pn_slogdet(A, ns, &ld, &sg);
+          release();
+        }
+        {
+          const R* Wt = acquire();
+          if (active && cnt > 0) {
+            warp_gemm<R, false, false, !STAGED>(
+                lane, cnt, Hw, Wt, Zd, net.p + o.b2[n][c], [&](int q) { return (const R*)(shid + (size_t)q * Hw); },
+                [&](int q) { return swv + (size_t)pl[q] * Zd; });
+            __syncwarp();
+          }
+          release();
+        }
       }
-      sdet[2 * q] = ld;
-      sdet[2 * q + 1] = sg;
+      {
+        const R* Wt = acquire();
+        if (active) {
+          for (int q = lane; q < N * Zd; q += 32) {
+            const int z = q % Zd, i = q / Zd;
+            R zs = 0, za = 0, zn = 0;
+            const bool si = i < s.n_up;
+            for (int j = 0; j < N; ++j) {
+              if (j == i) continue;
+              const int p = i < j ? pn_pair_index(i, j, N) : pn_pair_index(j, i, N);
+              const R v = swv[(size_t)p * Zd + z] * sh[(size_t)j * Zd + z];
+              if ((j < s.n_up) == si) zs += v; else za += v;
+            }
+            for (int I = 0; I < s.M; ++I) zn += swv[(size_t)(s.Pee + i * s.M + I) * Zd + z] * net.p[o.Y + I * Zd + z];
+            R* zo = sz + (size_t)i * 3 * Zd;
+            zo[z] = zs;
+            zo[Zd + z] = za;
+            zo[2 * Zd + z] = zn;
+          }
+          __syncwarp();
+          warp_gemm<R, false, true, !STAGED>(
+              lane, N, 3 * Zd, Wt, D, net.Gb + (size_t)n * D,
+              [&](int q) { return (const R*)(sz + (size_t)q * 3 * Zd); }, [&](int q) { return sx + (size_t)q * D; });
+          __syncwarp();
+        }
+        release();
+      }
     }
-    __syncwarp();
-    // signed log-sum over determinants and gamma, reduced across lanes
-    double m = -INFINITY;
-    for (int p = lane; p < nd; p += 32) {
-      const double sg = sdet[4 * p + 1] * sdet[4 * p + 3];
-      if (s.ci[p] != 0.0 && sg != 0.0) m = fmax(m, sdet[4 * p] + sdet[4 * p + 2]);
+    // heads: kappa on every electron, eta on the electron sum
+    {
+      const R* Wt = acquire();
+      if (active) {
+        for (int dd = lane; dd < D; dd += 32) {
+          R acc = 0;
+          for (int i = 0; i < N; ++i) acc += sx[(size_t)i * D + dd];
+          sxs[dd] = acc;
+        }
+        warp_gemm<R, true, false, !STAGED>(
+            lane, N, D, Wt, D, net.p + o.kb[0], [&](int q) { return (const R*)(sx + (size_t)q * D); },
+            [&](int q) { return sz + (size_t)q * D; });
+        __syncwarp();
+      }
+      release();
     }
-    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-    double S = 0;
-    R gam = 0;
-    if (m > -INFINITY)
+    {
+      const R* Wt = acquire();
+      if (active) {
+        warp_gemm<R, true, false, !STAGED>(
+            lane, N, D, Wt, D, net.p + o.kb[1], [&](int q) { return (const R*)(sz + (size_t)q * D); },
+            [&](int q) { return swv + (size_t)q * D; });
+        __syncwarp();
+      }
+      release();
+    }
+    {
+      const R* Wt = acquire();
+      if (active) {
+        warp_gemm<R, false, false, !STAGED>(
+            lane, N, D, Wt, no, net.p + o.kb[2], [&](int q) { return (const R*)(swv + (size_t)q * D); },
+            [&](int q) { return sF + (size_t)q * no; });
+        __syncwarp();
+      }
+      release();
+    }
+    {
+      const R* Wt = acquire();
+      if (active) {
+        warp_gemm<R, true, false, !STAGED>(
+            lane, 1, D, Wt, D, net.p + o.eb[0], [&](int q) { return (const R*)sxs; }, [&](int q) { return sa1; });
+        __syncwarp();
+      }
+      release();
+    }
+    {
+      const R* Wt = acquire();
+      if (active) {
+        warp_gemm<R, true, false, !STAGED>(
+            lane, 1, D, Wt, D, net.p + o.eb[1], [&](int q) { return (const R*)sa1; }, [&](int q) { return sa2; });
+        __syncwarp();
+      }
+      release();
+    }
+    {
+      const R* Wt = acquire();
+      if (active) {
+        warp_gemm<R, false, false, !STAGED>(
+            lane, 1, D, Wt, 1, net.p + o.eb[2], [&](int q) { return (const R*)sa2; }, [&](int q) { return sJ; });
+        __syncwarp();
+      }
+      release();
+    }
+    if (active) {
+      // determinants: one lane per (determinant, spin)
+      for (int q = lane; q < nd * 2; q += 32) {
+        const int sp = q & 1, p = q >> 1;
+        const int ns = sp ? s.n_dn : s.n_up, e0 = sp ? s.n_up : 0;
+        double ld = 0, sg = 1;
+        if (ns > 0) {
+          double A[PN_MAX_SPIN * PN_MAX_SPIN];
+          const int* occ = s.occ + p * N + e0;
+          for (int a = 0; a < ns; ++a)
+            for (int bb = 0; bb < ns; ++bb) {
+              const int i = e0 + a, mu = occ[bb];
+              A[a * ns + bb] = (double)sphi[(size_t)i * no + mu] * (1.0 + (double)sF[(size_t)i * no + mu]);
+            }
+          pn_slogdet(A, ns, &ld, &sg);
+        }
+        sdet[2 * q] = ld;
+        sdet[2 * q + 1] = sg;
+      }
+      __syncwarp();
+      // signed log-sum over determinants and gamma, reduced across lanes
+      double m = -INFINITY;
       for (int p = lane; p < nd; p += 32) {
         const double sg = sdet[4 * p + 1] * sdet[4 * p + 3];
-        if (sg != 0.0) S += s.ci[p] * sg * exp(sdet[4 * p] + sdet[4 * p + 2] - m);
+        if (s.ci[p] != 0.0 && sg != 0.0) m = fmax(m, sdet[4 * p] + sdet[4 * p + 2]);
       }
-    if (s.use_gamma)
-      for (int p = lane; p < s.Pee; p += 32) {
-        int a = 0, rem = p;
-        while (rem >= N - 1 - a) { rem -= N - 1 - a; ++a; }
-        const int bb = a + 1 + rem;
-        const R c = ((a < s.n_up) == (bb < s.n_up)) ? R(0.25) : R(0.5);
-        gam -= c / (R(1) + sdr[p]);
+      for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+      double S = 0;
+      R gam = 0;
+      if (m > -INFINITY)
+        for (int p = lane; p < nd; p += 32) {
+          const double sg = sdet[4 * p + 1] * sdet[4 * p + 3];
+          if (sg != 0.0) S += s.ci[p] * sg * exp(sdet[4 * p] + sdet[4 * p + 2] - m);
+        }
+      if (s.use_gamma)
+        for (int p = lane; p < s.Pee; p += 32) {
+          int a = 0, rem = p;
+          while (rem >= N - 1 - a) { rem -= N - 1 - a; ++a; }
+          const int bb = a + 1 + rem;
+          const R c = ((a < s.n_up) == (bb < s.n_up)) ? R(0.25) : R(0.5);
+          gam -= c / (R(1) + sdr[p]);
+        }
+      for (int off = 16; off > 0; off >>= 1) {
+        S += __shfl_xor_sync(0xffffffffu, S, off);
+        gam += __shfl_xor_sync(0xffffffffu, gam, off);
       }
-    for (int off = 16; off > 0; off >>= 1) {
-      S += __shfl_xor_sync(0xffffffffu, S, off);
-      gam += __shfl_xor_sync(0xffffffffu, gam, off);
+      const double lpn = (double)gam + (double)sJ[0] + m + log(fabs(S));
+      unsigned c4[4] = {(unsigned)nblk4, wid_g, (unsigned)(step & 0xffffffffull), (unsigned)(step >> 32)};
+      pn_philox(c4, (unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
+      bool accept;
+      if constexpr (sizeof(R) == 8) {
+        accept = pn_u01(c4[0]) < exp(2.0 * (lpn - lpw));
+      } else {
+        accept = ((float)c4[0] + 0.5f) * 2.3283064365386963e-10f < expf((float)(2.0 * (lpn - lpw)));
+      }
+      if (accept) {
+        for (int q = lane; q < n3; q += 32) sr[q] = srp[q];
+        lpw = lpn;
+        ++naccw;
+      }
+      __syncwarp();
     }
-    const double lpn = (double)gam + (double)sJ[0] + m + log(fabs(S));
-    unsigned c4[4] = {(unsigned)nblk4, wid_g, (unsigned)(step & 0xffffffffull), (unsigned)(step >> 32)};
-    pn_philox(c4, (unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
-    bool accept;
-    if constexpr (sizeof(R) == 8) {
-      accept = pn_u01(c4[0]) < exp(2.0 * (lpn - lpw));
-    } else {
-      accept = ((float)c4[0] + 0.5f) * 2.3283064365386963e-10f < expf((float)(2.0 * (lpn - lpw)));
-    }
-    if (accept) {
-      for (int q = lane; q < n3; q += 32) sr[q] = srp[q];
-      lpw = lpn;
-      ++naccw;
-    }
-    __syncwarp();
+    if (STAGED && abort_flag) break;  // uniform: read after the last release's barrier
   }
-  for (int i = lane; i < n3; i += 32) r[(size_t)w * n3 + i] = sr[i];
-  if (lane == 0) {
-    lp[w] = lpw;
-    if (n_acc && naccw) atomicAdd(n_acc, (unsigned long long)naccw);
+  if (STAGED && abort_flag) {
+    // a weight copy did not arrive in time: flag it, give the copies in
+    // flight a last bounded wait and leave the walkers at their last state
+    if (tid == 0) atomicExch(s.dev_err, 2);
+    bar_wait(smem_addr(&wbar[g & 1]), (uint32_t)((g >> 1) & 1));
+    bar_wait(smem_addr(&wbar[(g + 1) & 1]), (uint32_t)(((g + 1) >> 1) & 1));
+  }
+  if (active) {
+    for (int i = lane; i < n3; i += 32) r[(size_t)w * n3 + i] = sr[i];
+    if (lane == 0) {
+      lp[w] = lpw;
+      if (n_acc && naccw) atomicAdd(n_acc, (unsigned long long)naccw);
+    }
   }
 }
 
@@ -781,13 +929,31 @@ int pn_run_metropolis_fused(const DevSys& s, const DevNet<R>& net, double* r, do
   // small systems: one warp per walker when a walker's state is small
   const WLayout WL = make_wlayout<R>(s);
   if (s.fused_sampler != 2 && WL.bytes <= 24 * 1024) {
-    const int warps = (int)std::min<size_t>(8, (200 * 1024) / WL.bytes);
-    const int smem = (int)(WL.bytes * warps);
-    PN_CUDA(cudaFuncSetAttribute(k_metropolis_warp<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const StageTab& stt = net.stab;
+    const R* wp = net.wpack;
+    int warps = (int)std::min<size_t>(8, (200 * 1024) / WL.bytes);
+    // lockstep with shared weight buffers when two of the largest block fit beside the warps' state
+    int wbuf_bytes = (stt.max_bytes + 127) / 128 * 128;
+    const size_t cap = 220 * 1024;
+    // TMA-fed lockstep only on request: measured slower on the Be workload
+    // (its 128 registers per thread halve the resident warps)
+    bool staged = s.fused_sampler == 3;
+    while (staged && warps > 1 && WL.bytes * warps + 2 * (size_t)wbuf_bytes > cap) --warps;
+    if (WL.bytes * warps + 2 * (size_t)wbuf_bytes > cap) staged = false;
+    const int wbuf_off = (int)((WL.bytes * warps + 127) / 128 * 128);
+    const int smem = staged ? wbuf_off + 2 * wbuf_bytes : (int)(WL.bytes * warps);
     const int blocks = (W + warps - 1) / warps;
-    PN_LAUNCH("k_metropolis_warp", st,
-              k_metropolis_warp<R><<<blocks, warps * 32, smem, st>>>(s, net, WL, r, lp, W, walker0, n_steps, sigma,
-                                                                     seed, step0, n_acc));
+    if (staged) {
+      PN_CUDA(cudaFuncSetAttribute(k_metropolis_warp<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      PN_LAUNCH("k_metropolis_warp", st,
+                k_metropolis_warp<R, true><<<blocks, warps * 32, smem, st>>>(
+                    s, net, WL, stt, wp, wbuf_off, wbuf_bytes, r, lp, W, walker0, n_steps, sigma, seed, step0, n_acc));
+    } else {
+      PN_CUDA(cudaFuncSetAttribute(k_metropolis_warp<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      PN_LAUNCH("k_metropolis_warp", st,
+                k_metropolis_warp<R, false><<<blocks, warps * 32, smem, st>>>(
+                    s, net, WL, stt, wp, 0, 0, r, lp, W, walker0, n_steps, sigma, seed, step0, n_acc));
+    }
     return PN_OK;
   }
   int smem = 0;

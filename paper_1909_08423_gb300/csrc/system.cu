@@ -285,19 +285,71 @@ static int upload_params(pn_system_s* s, const double* hp) {
   std::vector<float> G32(G.begin(), G.end()), Gb32(Gb.begin(), Gb.end());
   PN_CUDA(cudaMemcpy(s->Gcat32, G32.data(), G32.size() * 4, cudaMemcpyHostToDevice));
   PN_CUDA(cudaMemcpy(s->Gb32, Gb32.data(), Gb32.size() * 4, cudaMemcpyHostToDevice));
+  // packed sampler weights (same block order in both precisions)
+  std::vector<std::pair<const double*, size_t>> blocks;
+  for (int n = 0; n < d.L; ++n) {
+    blocks.push_back({hp + o.hW[n], (size_t)d.D * d.Zd});
+    for (int c = 0; c < 3; ++c) {
+      blocks.push_back({hp + o.W1[n][c], (size_t)d.K * d.Hw});
+      blocks.push_back({hp + o.W2[n][c], (size_t)d.Hw * d.Zd});
+    }
+    blocks.push_back({G.data() + n * gsz, gsz});
+  }
+  const size_t outs[6] = {(size_t)d.D, (size_t)d.D, (size_t)d.n_orb, (size_t)d.D, (size_t)d.D, 1};
+  const int64_t srcs[6] = {o.kW[0], o.kW[1], o.kW[2], o.eW[0], o.eW[1], o.eW[2]};
+  for (int k = 0; k < 6; ++k) blocks.push_back({hp + srcs[k], (size_t)d.D * outs[k]});
+  for (int prec = 0; prec < 2; ++prec) {
+    const size_t el = prec == 0 ? 8 : 4, align = 16 / el;
+    StageTab& t = prec == 0 ? s->stab64 : s->stab32;
+    t.n = (int)blocks.size();
+    t.max_bytes = 0;
+    size_t tot = 0;
+    for (int b = 0; b < t.n; ++b) {
+      const size_t padded = (blocks[b].second + align - 1) / align * align;
+      t.off[b] = (int64_t)tot;
+      t.bytes[b] = (int)(padded * el);
+      t.max_bytes = std::max(t.max_bytes, t.bytes[b]);
+      tot += padded;
+    }
+    if (prec == 0) {
+      std::vector<double> pk(tot, 0.0);
+      for (int b = 0; b < t.n; ++b) std::copy(blocks[b].first, blocks[b].first + blocks[b].second, pk.begin() + t.off[b]);
+      PN_CUDA(cudaMemcpy(s->wpack64, pk.data(), tot * 8, cudaMemcpyHostToDevice));
+    } else {
+      std::vector<float> pk(tot, 0.0f);
+      for (int b = 0; b < t.n; ++b) std::copy(blocks[b].first, blocks[b].first + blocks[b].second, pk.begin() + t.off[b]);
+      PN_CUDA(cudaMemcpy(s->wpack32, pk.data(), tot * 4, cudaMemcpyHostToDevice));
+    }
+  }
   return PN_OK;
+}
+
+// Elements of the packed sampler weights (upper bound, for allocation).
+static size_t wpack_elems(const DevSys& d) {
+  size_t tot = 0;
+  auto add = [&](size_t n) { tot += (n + 3) / 4 * 4; };
+  for (int n = 0; n < d.L; ++n) {
+    add((size_t)d.D * d.Zd);
+    for (int c = 0; c < 3; ++c) { add((size_t)d.K * d.Hw); add((size_t)d.Hw * d.Zd); }
+    add((size_t)3 * d.Zd * d.D);
+  }
+  add((size_t)d.D * d.D); add((size_t)d.D * d.D); add((size_t)d.D * d.n_orb);
+  add((size_t)d.D * d.D); add((size_t)d.D * d.D); add((size_t)d.D);
+  return tot;
 }
 
 template <>
 DevNet<double> pn_devnet<double>(pn_system_s* s) {
   DevNet<double> n;
   n.p = s->p64; n.Gcat = s->Gcat64; n.Gb = s->Gb64; n.off = s->off;
+  n.wpack = s->wpack64; n.stab = s->stab64;
   return n;
 }
 template <>
 DevNet<float> pn_devnet<float>(pn_system_s* s) {
   DevNet<float> n;
   n.p = s->p32; n.Gcat = s->Gcat32; n.Gb = s->Gb32; n.off = s->off;
+  n.wpack = s->wpack32; n.stab = s->stab32;
   return n;
 }
 
@@ -527,6 +579,8 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   s->Gb64 = dev_upload<double>(s, nullptr, (size_t)std::max(d->L, 1) * d->D, &err);
   s->Gcat32 = dev_upload<float>(s, nullptr, gsz, &err);
   s->Gb32 = dev_upload<float>(s, nullptr, (size_t)std::max(d->L, 1) * d->D, &err);
+  s->wpack64 = dev_upload<double>(s, nullptr, wpack_elems(ds), &err);
+  s->wpack32 = dev_upload<float>(s, nullptr, wpack_elems(ds), &err);
   if (err != PN_OK) {
     pn_set_error("device allocation/upload failed during init");
     free_all(s);
