@@ -65,7 +65,7 @@ def algorithmic_flops(sysd, kernel, mode):
         # value: 2 per partner; derivative rows 4; Laplacian row ~ 20
         per_row = 2 if T == 1 else (2 + 4 * (T - 2) + 20) / T
         return L * N * T * Zd * (N - 1 + M) * per_row
-    if kernel in ("k_metropolis_warp", "k_metropolis_fused"):
+    if kernel in ("k_metropolis_warp", "k_metropolis_fused", "k_metropolis_tc"):
         # one value pass of the network per walker-step (float32 work):
         # filters, h and receiving maps, messages, both heads
         return sum(algorithmic_flops(sysd, k, "value") for k in ("k_filter", "k_linear", "k_message"))
@@ -243,6 +243,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=60)
     ap.add_argument("--serve-only", action="store_true")
+    ap.add_argument("--sampler", type=int, default=None,
+                    help="PN_OPT_FUSED_SAMPLER for the timed mixed path (library default if absent)")
     ap.add_argument("--case", choices=["sampler", "jet_tc"], default=None,
                     help="run one small kernel case (for ncu captures) and exit")
     args = ap.parse_args()
@@ -259,6 +261,8 @@ def main():
         s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=W_PER_RANK)
         r = torch.empty(W_PER_RANK, s.N, 3, dtype=torch.float64, device="cuda")
         s.init_walkers(r, 1)
+        if args.sampler is not None:
+            s.set_option(binding.PN_OPT_FUSED_SAMPLER, args.sampler)
         if args.case == "sampler":  # 5 Metropolis steps of the Be workload
             lp = torch.empty(W_PER_RANK, dtype=torch.float64, device="cuda")
             sg = torch.empty_like(lp)
@@ -297,6 +301,8 @@ def main():
 
     def make_state(precision):
         s = binding.System(sysd, precision=precision, max_walkers=W)
+        if args.sampler is not None and precision == binding.PN_MIXED:
+            s.set_option(binding.PN_OPT_FUSED_SAMPLER, args.sampler)
         r = torch.empty(W, s.N, 3, dtype=torch.float64, device=dev)
         s.init_walkers(r, 1000 + rank)
         lp = torch.empty(W, dtype=torch.float64, device=dev)
@@ -355,7 +361,7 @@ def main():
         step(mixed)
     candidates = ["k_linear", "k_filter", "k_message", "k_slater", "k_orbitals", "k_combine", "k_features",
                   "k_ssp_jet", "k_wgrad", "k_slater_bwd", "k_propose", "k_accept", "k_geometry",
-                  "k_metropolis_warp", "k_metropolis_fused", "k_linear_tc"]
+                  "k_metropolis_warp", "k_metropolis_fused", "k_metropolis_tc", "k_linear_tc"]
     share = {}
     for kname in candidates:
         lib.pn_profile_kernel(kname.encode())
@@ -440,7 +446,7 @@ def main():
         if dom in ("k_filter", "k_linear", "k_message", "k_slater"):
             per_step_flops = W * (N_METROPOLIS * algorithmic_flops(sysd, dom, "value") +
                                   algorithmic_flops(sysd, dom, "jet"))
-        elif dom in ("k_metropolis_warp", "k_metropolis_fused"):
+        elif dom in ("k_metropolis_warp", "k_metropolis_fused", "k_metropolis_tc"):
             per_step_flops = W * N_METROPOLIS * algorithmic_flops(sysd, dom, "value")
         kern_ms_per_step = kern[1] / args.steps
         if per_step_flops:

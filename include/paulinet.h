@@ -193,13 +193,18 @@ int pn_metropolis_step(pn_system_t sys, double* r, double* logabs, int W,
 
 /* Implementation options of a handle (they change speed, not results
  * beyond floating-point rounding).
- * PN_OPT_FUSED_SAMPLER (default 1): run Metropolis steps in one launch that
+ * PN_OPT_FUSED_SAMPLER (default 4 for PN_MIXED, 1 for PN_FP64): run
+ *   Metropolis steps in one launch that
  *   keeps walkers in shared memory for all steps -- one warp per walker for
  *   small systems (up to 24 KiB of state per walker; weights read through
  *   L1/L2), else a tile of walkers per block; 2 forces the tile kernel; 3
  *   the warp kernel with its block's warps walking the layers in lockstep
  *   and each weight block bulk-copied (TMA) into shared memory one stage
- *   ahead; 0 (or a system too large for one tile) uses one kernel per
+ *   ahead; 4 (PN_MIXED) the tensor-core sampler -- a block per tile of
+ *   walkers whose electrons and pairs fill 128-row tcgen05 tiles, every
+ *   linear map one MMA group with three-piece bf16 operands and weights
+ *   bulk-copied (TMA) one stage ahead -- falling back to 1 where the tiles
+ *   do not fit; 0 (or a system too large for one tile) uses one kernel per
  *   stage.
  * PN_OPT_TENSOR_CORES (PN_MIXED only; default 0): a mask of the float32
  *   linear layers that run on tcgen05 with each operand split into three

@@ -250,9 +250,13 @@ int pn_run_metropolis(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc
       PN_CUDA(cudaMemcpyAsync(w.lp_prop, lc, (size_t)Wn * 8, cudaMemcpyHostToDevice, st));
       lc = w.lp_prop;
     }
-    int fused = ds.fused_sampler ? pn_run_metropolis_fused<R>(ds, net, rc, lc, Wn, (unsigned)c0, n_steps, sigma, seed,
-                                                             step0, w.n_acc, st)
-                                 : PN_ENOTREADY;
+    int fused = PN_ENOTREADY;
+    if constexpr (sizeof(R) == 4) {
+      if (ds.fused_sampler == 4)
+        fused = pn_run_metropolis_tc(ds, net, rc, lc, Wn, (unsigned)c0, n_steps, sigma, seed, step0, w.n_acc, st);
+    }
+    if (fused == PN_ENOTREADY && ds.fused_sampler)
+      fused = pn_run_metropolis_fused<R>(ds, net, rc, lc, Wn, (unsigned)c0, n_steps, sigma, seed, step0, w.n_acc, st);
     if (fused != PN_OK && fused != PN_ENOTREADY) return fused;
     for (int k = 0; fused != PN_OK && k < n_steps; ++k) {
       const unsigned long long step = step0 + (unsigned long long)k;
@@ -356,7 +360,7 @@ extern "C" int pn_set_option(pn_system_t s, int option, int value) {
   if (!s) { pn_set_error("null system"); return PN_EINVAL; }
   switch (option) {
     case PN_OPT_FUSED_SAMPLER:
-      if (value < 0 || value > 3) { pn_set_error("fused sampler option takes 0..3"); return PN_EINVAL; }
+      if (value < 0 || value > 4) { pn_set_error("fused sampler option takes 0..4"); return PN_EINVAL; }
       s->ds.fused_sampler = value;
       return PN_OK;
     case PN_OPT_TENSOR_CORES:

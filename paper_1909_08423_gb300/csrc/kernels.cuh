@@ -61,3 +61,40 @@ __device__ inline void pn_normal_pair(unsigned long long seed, unsigned walker, 
   out[0] = rad * cos(ang);
   out[1] = rad * sin(ang);
 }
+
+// Orbital tables in the sampler's orbital precision C.
+template <typename C>
+struct OrbTab {
+  const C *R, *pexp, *pcoef, *mo, *rc, *cC, *cs, *ca;
+};
+template <typename C>
+__device__ inline OrbTab<C> orb_tab(const DevSys& s);
+template <>
+__device__ inline OrbTab<double> orb_tab<double>(const DevSys& s) {
+  return {s.R, s.pexp, s.pcoef, s.mo, s.cusp_rc, s.cusp_C, s.cusp_s, s.cusp_a};
+}
+template <>
+__device__ inline OrbTab<float> orb_tab<float>(const DevSys& s) {
+  return {s.R32, s.pexp32, s.pcoef32, s.mo32, s.cusp_rc32, s.cusp_C32, s.cusp_s32, s.cusp_a32};
+}
+
+
+// One Box-Muller pair in C precision from the shared Philox stream.
+template <typename C>
+__device__ inline void normal_pair(unsigned long long seed, unsigned walker, unsigned long long step, unsigned j,
+                                   int pair, C out[2]) {
+  if constexpr (sizeof(C) == 8) {
+    pn_normal_pair(seed, walker, step, j, pair, out);
+  } else {
+    unsigned c[4] = {j, walker, (unsigned)(step & 0xffffffffull), (unsigned)(step >> 32)};
+    pn_philox(c, (unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
+    const float u0 = ((float)c[2 * pair] + 0.5f) * 2.3283064365386963e-10f;
+    const float u1 = ((float)c[2 * pair + 1] + 0.5f) * 2.3283064365386963e-10f;
+    const float rad = sqrtf(-2.0f * logf(u0));
+    float sn, cs;
+    sincospif(2.0f * u1, &sn, &cs);
+    out[0] = rad * cs;
+    out[1] = rad * sn;
+  }
+}
+

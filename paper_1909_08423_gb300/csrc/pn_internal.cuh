@@ -93,6 +93,7 @@ struct DevSys {
   const int* nuc;         // [N] nucleus each electron starts near (walker init)
   const int* ch_pairs;    // [Ppair] pair indices grouped by filter channel
   int ch_off[4];          // channel c owns ch_pairs[ch_off[c] .. ch_off[c+1])
+  const int* ch_pos;      // [Ppair] position of each pair inside its channel's list
   int fused_sampler;      // 1: Metropolis through the fused tile kernel when it fits
   int tensor_cores;       // 1: float32 linear layers on tcgen05 (split tf32)
   int* dev_err;           // device word: set when a bounded wait expired
@@ -149,6 +150,21 @@ struct StageTab {
   int bytes[PN_MAX_STAGES];     // block size in bytes (multiple of 16)
 };
 
+// Weight blocks of the tensor-core sampler, in consumption order: per layer
+// h, then for every non-empty filter channel (W1, W2, receiving-map slice);
+// then kappa 1..3 and eta 1..3.  Each block is stored as three bf16 pieces
+// of the transposed weight (rows = outputs padded to 16, columns = inputs)
+// in the canonical K-major tile layout of tcgen05 (8 x 16-byte core
+// matrices), so that one bulk copy lands it ready for the MMA.
+struct TcStages {
+  int n;                       // stages per Metropolis step (0: not eligible)
+  int max_bytes;
+  int64_t off[PN_MAX_STAGES];  // bf16 element offset in the packed blocks
+  int bytes[PN_MAX_STAGES];    // bytes (three pieces)
+  int K[PN_MAX_STAGES];        // inputs
+  int Np[PN_MAX_STAGES];       // outputs padded to 16
+};
+
 // Per-precision parameters on the device.
 template <typename R>
 struct DevNet {
@@ -158,6 +174,9 @@ struct DevNet {
   const R* wpack;  // sampler weight blocks, 16-byte aligned (see StageTab)
   NetOff off;
   StageTab stab;
+  const unsigned short* tcpack;  // tensor-core sampler blocks (float path only)
+  const TcStages* tcst;          // their table, in device memory
+  int tc_n, tc_max_bytes;        // host copies of its size fields
 };
 
 struct pn_system_s {
@@ -177,6 +196,9 @@ struct pn_system_s {
   void* work_mem;
   size_t work_bytes;
   StageTab stab64, stab32;  // packed sampler weights per precision
+  TcStages tcst;            // tensor-core sampler weight blocks
+  TcStages* tcst_dev;       // the same table in device memory
+  unsigned short* tcpack;   // [tcst total] bf16 pieces
   double* wpack64;
   float* wpack32;
   void* tape_mem;          // backward tape (grown on demand)
@@ -216,6 +238,10 @@ int pn_run_metropolis(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc
                       int n_steps, double sigma, unsigned long long seed, unsigned long long step0, int64_t* n_accept,
                       cudaStream_t st);
 int pn_run_init_walkers(const DevSys& ds, double* r, int W, unsigned long long seed, cudaStream_t st);
+// Tensor-core sampler (sampler_tc.cu): PN_ENOTREADY if the system's tiles do not fit.
+int pn_run_metropolis_tc(const DevSys& s, const DevNet<float>& net, double* r, double* lp, int W, unsigned walker0,
+                         int n_steps, double sigma, unsigned long long seed, unsigned long long step0,
+                         unsigned long long* n_acc, cudaStream_t st);
 // Fused sampler (sampler.cu): PN_ENOTREADY if a tile does not fit.
 template <typename R>
 int pn_run_metropolis_fused(const DevSys& s, const DevNet<R>& net, double* r, double* lp, int W, unsigned walker0,

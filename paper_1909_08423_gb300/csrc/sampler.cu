@@ -35,22 +35,6 @@ __device__ inline const double* feat_is_of<double>(const DevSys& s) { return s.f
 template <>
 __device__ inline const float* feat_is_of<float>(const DevSys& s) { return s.feat_isig2_32; }
 
-// Orbital tables in the sampler's orbital precision C.
-template <typename C>
-struct OrbTab {
-  const C *R, *pexp, *pcoef, *mo, *rc, *cC, *cs, *ca;
-};
-template <typename C>
-__device__ inline OrbTab<C> orb_tab(const DevSys& s);
-template <>
-__device__ inline OrbTab<double> orb_tab<double>(const DevSys& s) {
-  return {s.R, s.pexp, s.pcoef, s.mo, s.cusp_rc, s.cusp_C, s.cusp_s, s.cusp_a};
-}
-template <>
-__device__ inline OrbTab<float> orb_tab<float>(const DevSys& s) {
-  return {s.R32, s.pexp32, s.pcoef32, s.mo32, s.cusp_rc32, s.cusp_C32, s.cusp_s32, s.cusp_a32};
-}
-
 template <typename R>
 __device__ inline R ssp_(R x) {
   return (x > R(0) ? x : R(0)) + log1p(exp(-fabs(x))) - R(0.69314718055994530942);
@@ -521,25 +505,6 @@ __device__ inline void warp_orbitals(const DevSys& s, int lane, const C* __restr
   __syncwarp();
 }
 
-// One Box-Muller pair in C precision from the shared Philox stream.
-template <typename C>
-__device__ inline void normal_pair(unsigned long long seed, unsigned walker, unsigned long long step, unsigned j,
-                                   int pair, C out[2]) {
-  if constexpr (sizeof(C) == 8) {
-    pn_normal_pair(seed, walker, step, j, pair, out);
-  } else {
-    unsigned c[4] = {j, walker, (unsigned)(step & 0xffffffffull), (unsigned)(step >> 32)};
-    pn_philox(c, (unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
-    const float u0 = ((float)c[2 * pair] + 0.5f) * 2.3283064365386963e-10f;
-    const float u1 = ((float)c[2 * pair + 1] + 0.5f) * 2.3283064365386963e-10f;
-    const float rad = sqrtf(-2.0f * logf(u0));
-    float sn, cs;
-    sincospif(2.0f * u1, &sn, &cs);
-    out[0] = rad * cs;
-    out[1] = rad * sn;
-  }
-}
-
 __device__ inline uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ inline bool bar_try(uint32_t bar, uint32_t parity) {
@@ -928,7 +893,7 @@ int pn_run_metropolis_fused(const DevSys& s, const DevNet<R>& net, double* r, do
                             unsigned long long* n_acc, cudaStream_t st) {
   // small systems: one warp per walker when a walker's state is small
   const WLayout WL = make_wlayout<R>(s);
-  if (s.fused_sampler != 2 && WL.bytes <= 24 * 1024) {
+  if (s.fused_sampler != 2 && WL.bytes <= 24 * 1024) {  // 1, 3 (and 4 when the tensor-core tiles do not fit)
     const StageTab& stt = net.stab;
     const R* wp = net.wpack;
     int warps = (int)std::min<size_t>(8, (200 * 1024) / WL.bytes);

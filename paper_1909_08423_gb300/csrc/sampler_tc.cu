@@ -1,0 +1,670 @@
+// Metropolis sampler with the network on the 5th-generation tensor cores.
+//
+// One CTA (eight warps) owns a tile of WT walkers, so that its electrons
+// (WT * N <= 128) and the pairs of each filter channel (WT * count <= 128)
+// each fill one 128-row tcgen05 tile.  Every linear map of every step is
+// one or a few tcgen05.mma groups over the whole tile:
+//  - activations are written by the CUDA cores into shared memory as three
+//    bf16 pieces in the canonical K-major layout (8 x 16-byte core
+//    matrices), weights arrive the same way by a TMA bulk copy of a block
+//    prepared at parameter upload, double-buffered one stage ahead;
+//  - one thread issues the six piece products (a0b0 ... a1b1, float32
+//    accumulation in tensor memory) and commits to an mbarrier;
+//  - warps w and w + 4 read TMEM lanes 32(w % 4)..+31 (their 32 rows),
+//    alternate 16-column chunks each, with tcgen05.ld and apply bias and
+//    activation, writing the next operand or float state.
+// Geometry, orbitals (float32), features, messages, determinants (float64
+// LU and log-sum) and the accept test run on the CUDA cores between the MMA
+// stages.  Every wait is bounded: on expiry the CTA raises the device error
+// word, drains what it started (bounded) and frees its TMEM.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "ansatz_dev.cuh"
+#include "kernels.cuh"
+#include "pn_internal.cuh"
+
+namespace {
+
+constexpr int TM = 128;  // tile rows
+constexpr int NT = 256;  // threads: two warps per TMEM lane quadrant
+
+__device__ inline uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// K-major canonical layout: 8-row groups SBO = K/8 * 128 bytes apart, core
+// matrices along K 128 bytes apart.
+__device__ inline uint32_t t_off(int row, int k, int K) {
+  return (uint32_t)(row >> 3) * (uint32_t)(K >> 3) * 128u + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u +
+         (uint32_t)(k & 7) * 2u;
+}
+
+__device__ inline uint64_t sdesc(uint32_t addr, int K) {
+  const uint32_t sbo = (uint32_t)(K >> 3) * 128u;
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__device__ inline uint32_t idesc_bf16(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ inline void put3(unsigned char* A, int piece_bytes, int row, int k, int K, float a) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(a);
+  const float r1 = a - __bfloat162float(h0);
+  const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+  const __nv_bfloat16 h2 = __float2bfloat16_rn(r1 - __bfloat162float(h1));
+  const uint32_t off = t_off(row, k, K);
+  *(__nv_bfloat16*)(A + off) = h0;
+  *(__nv_bfloat16*)(A + piece_bytes + off) = h1;
+  *(__nv_bfloat16*)(A + 2 * piece_bytes + off) = h2;
+}
+
+// Eight consecutive k of one row -> one 16-byte store per bf16 piece (one
+// row of a core matrix).  k8 is a multiple of 8.
+__device__ inline void put3x8(unsigned char* A, int piece_bytes, int row, int k8, int K, const float v[8]) {
+  uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    uint32_t h0[2], h1[2], h2[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const float a = v[2 * j + t];
+      const __nv_bfloat16 b0 = __float2bfloat16_rn(a);
+      const float r1 = a - __bfloat162float(b0);
+      const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+      const __nv_bfloat16 b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
+      h0[t] = __bfloat16_as_ushort(b0);
+      h1[t] = __bfloat16_as_ushort(b1);
+      h2[t] = __bfloat16_as_ushort(b2);
+    }
+    w0[j] = h0[0] | (h0[1] << 16);
+    w1[j] = h1[0] | (h1[1] << 16);
+    w2[j] = h2[0] | (h2[1] << 16);
+  }
+  const uint32_t off = t_off(row, k8, K);
+  *(uint4*)(A + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+  *(uint4*)(A + piece_bytes + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+  *(uint4*)(A + 2 * piece_bytes + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+}
+
+__device__ inline bool try_bar(uint32_t bar, uint32_t par) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(par)
+      : "memory");
+  return ok != 0;
+}
+__device__ inline bool wait_bar(uint32_t bar, uint32_t par) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (try_bar(bar, par)) return true;
+  return false;
+}
+
+__device__ inline float sspf(float x) { return fmaxf(x, 0.f) + log1pf(expf(-fabsf(x))) - 0.69314718055994530942f; }
+
+__device__ inline void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t u[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
+        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(u[j]);
+}
+
+struct TcLayout {
+  int WT;
+  int a_bytes;  // one piece of the A tile region (128 rows x Kmax bf16)
+  int b_bytes;  // one weight buffer
+  size_t A, B0, B1, x, h, wv, r, rp, rpf, d, phi, rad, ic, det, F, J, lp, bytes;
+};
+
+__host__ __device__ inline size_t a16(size_t x) { return (x + 127) & ~(size_t)127; }
+
+inline TcLayout tc_layout(const DevSys& s, int max_bytes, int WT) {
+  TcLayout L;
+  L.WT = WT;
+  const int Kmax = std::max(std::max(s.D, s.K), std::max(s.Hw, s.Zd));
+  L.a_bytes = TM * Kmax * 2;
+  L.b_bytes = (int)a16(max_bytes);
+  size_t o = 0;
+  auto put = [&](size_t b) { size_t q = o; o += a16(b); return q; };
+  const size_t N = s.N, P = s.Ppair, no = s.n_orb;
+  L.A = put(3 * (size_t)L.a_bytes);
+  L.B0 = put(L.b_bytes);
+  L.B1 = put(L.b_bytes);
+  // float state rows padded by 4 floats: lanes run over rows, so an unpadded
+  // power-of-two stride would put every lane in the same bank
+  L.x = put((size_t)TM * (s.D + 4) * 4);
+  L.h = put((size_t)TM * (s.Zd + 4) * 4);
+  L.wv = put((size_t)TM * (s.Zd + 4) * 4);
+  L.r = put(WT * N * 3 * 8);
+  L.rp = put(WT * N * 3 * 8);
+  L.rpf = put(WT * N * 3 * 4);
+  L.d = put(WT * P * 4);
+  L.phi = put(WT * N * no * 4);
+  L.rad = put(WT * N * (size_t)s.n_shells * 4);
+  L.ic = put(WT * N * 4);
+  L.det = put((size_t)WT * s.n_det * 4 * 8);
+  L.F = put(WT * N * no * 4);
+  L.J = put(WT * 4);
+  L.lp = put(WT * 8);
+  L.bytes = o;
+  return L;
+}
+
+__global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float> net,
+                                                         const TcStages* __restrict__ tsp,
+                                                         const unsigned short* __restrict__ tcpack, TcLayout L,
+                                                         double* __restrict__ r, double* __restrict__ lp, int W,
+                                                         unsigned walker0, int n_steps, double sigma,
+                                                         unsigned long long seed, unsigned long long step0,
+                                                         unsigned long long* __restrict__ n_acc, uint32_t tmem_cols) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar_w[2];
+  __shared__ __align__(8) uint64_t bar_m;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  __shared__ unsigned acc_count;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = s.N, P = s.Ppair, D = s.D, Zd = s.Zd, K = s.K, Hw = s.Hw, no = s.n_orb, nd = s.n_det;
+  const int n3 = 3 * N, nblk4 = (n3 + 3) / 4;
+  const NetOff& o = net.off;
+  const TcStages& ts = *tsp;
+  const int w0 = blockIdx.x * L.WT;
+  const int WTt = min(L.WT, W - w0);
+  const int rowsN = WTt * N;
+  const int LX = D + 4, LH = Zd + 4;  // padded row strides of x and of h / w
+  unsigned char* sA = smem + L.A;
+  unsigned char* sB[2] = {smem + L.B0, smem + L.B1};
+  float* sx = (float*)(smem + L.x);
+  float* sh = (float*)(smem + L.h);
+  float* swv = (float*)(smem + L.wv);
+  double* sr = (double*)(smem + L.r);
+  double* srp = (double*)(smem + L.rp);
+  float* srpf = (float*)(smem + L.rpf);
+  float* sd = (float*)(smem + L.d);
+  float* sphi = (float*)(smem + L.phi);
+  float* srad = (float*)(smem + L.rad);
+  int* sic = (int*)(smem + L.ic);
+  double* sdet = (double*)(smem + L.det);
+  float* sF = (float*)(smem + L.F);
+  float* sJ = (float*)(smem + L.J);
+  double* slp = (double*)(smem + L.lp);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar_w[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar_w[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar_m)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+    acc_count = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const uint32_t col_g = (uint32_t)(tmem_cols / 2);  // receiving-map accumulator columns
+
+  // ---- weight stages (TMA, one ahead) and MMA completion phases
+  const long total = (long)n_steps * ts.n;
+  long g = 0;
+  uint32_t mma_phase = 0;
+  auto issue = [&](long q) {
+    if (q >= total) return;
+    const int j = (int)(q % ts.n), b = (int)(q & 1);
+    const uint32_t bar = saddr(&bar_w[b]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(ts.bytes[j]) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     saddr(sB[b])),
+                 "l"(tcpack + ts.off[j]), "r"(ts.bytes[j]), "r"(bar)
+                 : "memory");
+  };
+  if (tid == 0) {
+    issue(0);
+    issue(1);
+  }
+  // One GEMM stage: the A tile (K columns) is in sA, written and fenced by
+  // every thread before the barrier that precedes this call.  Accumulates
+  // into TMEM columns [col, col + Np); acc_first says whether the first
+  // product adds to what the columns hold.
+  auto gemm = [&](uint32_t col, bool acc_first) {
+    const int j = (int)(g % ts.n), b = (int)(g & 1);
+    const int Kg = ts.K[j], Np = ts.Np[j];
+    if (!wait_bar(saddr(&bar_w[b]), (uint32_t)((g >> 1) & 1))) abort_flag = 1;
+    if (tid == 0 && !abort_flag) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a0 = saddr(sA), b0 = saddr(sB[b]);
+      const uint32_t bp = (uint32_t)Np * (uint32_t)Kg * 2u;  // one weight piece
+      const uint32_t idesc = idesc_bf16(Np);
+      // descriptors of the three pieces, built once; a k-step of 16 bf16
+      // (256 bytes) advances only the start-address field (addr >> 4)
+      const uint64_t dA[3] = {sdesc(a0, Kg), sdesc(a0 + (uint32_t)L.a_bytes, Kg), sdesc(a0 + 2u * (uint32_t)L.a_bytes, Kg)};
+      const uint64_t dB[3] = {sdesc(b0, Kg), sdesc(b0 + bp, Kg), sdesc(b0 + 2u * bp, Kg)};
+      const uint32_t dcol = tmem + col;
+      for (int st = 0; st < Kg / 16; ++st) {
+        const uint64_t adv = (uint64_t)(st * 16);
+        // (A piece, B piece), smallest weight first: a1b1 a2b0 a0b2 a1b0 a0b1 a0b0
+        const uint32_t first = (st == 0) ? (acc_first ? 1u : 0u) : 1u;
+        asm volatile(
+            "{\n\t.reg .pred pf, pt;\n\t"
+            "setp.ne.b32 pf, %13, 0;\n\t"
+            "setp.eq.b32 pt, %13, %13;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %12, pf;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %4, %12, pt;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %12, pt;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %7, %8, %12, pt;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %9, %10, %12, pt;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %11, %14, %12, pt;\n\t}" ::"r"(dcol),
+            "l"(dA[1] + adv), "l"(dB[1] + adv), "l"(dA[2] + adv), "l"(dB[0] + adv), "l"(dA[0] + adv),
+            "l"(dB[2] + adv), "l"(dA[1] + adv), "l"(dB[0] + adv), "l"(dA[0] + adv), "l"(dB[1] + adv),
+            "l"(dA[0] + adv), "r"(idesc), "r"(first), "l"(dB[0] + adv));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(&bar_m))
+                   : "memory");
+    }
+    if (!abort_flag && !wait_bar(saddr(&bar_m), mma_phase)) abort_flag = 1;
+    mma_phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // the weight buffer is free once the MMAs completed
+    if (tid == 0) issue(g + 2);
+    ++g;
+  };
+  // End of an epilogue that wrote the next A tile: make the generic-proxy
+  // stores visible to the tensor core, then meet at the barrier.
+  auto fence_sync = [&]() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  };
+  // warp w reads TMEM lane quadrant w % 4 (tile rows 32 (w % 4) + lane);
+  // the two warps of a quadrant take alternate 16-column chunks
+  const int quad = warp & 3, half = warp >> 2;
+  const int arow = quad * 32 + lane;
+  const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
+
+  // ---- walker state
+  for (int i = tid; i < WTt * n3; i += NT) sr[i] = r[(size_t)w0 * n3 + i];
+  for (int i = tid; i < WTt; i += NT) slp[i] = lp[w0 + i];
+  unsigned nacc = 0;
+  __syncthreads();
+  const OrbTab<float> tab = orb_tab<float>(s);
+
+  for (int kstep = 0; kstep < n_steps && !abort_flag; ++kstep) {
+    const unsigned long long step = step0 + (unsigned long long)kstep;
+    // proposals (float32 normals, float64 positions)
+    for (int q = tid; q < WTt * 2 * nblk4; q += NT) {
+      const int w = q / (2 * nblk4), jj = (q % (2 * nblk4)) >> 1, pr = q & 1;
+      if (4 * jj + 2 * pr >= n3) continue;
+      float zz[2];
+      normal_pair<float>(seed, walker0 + (unsigned)(w0 + w), step, jj, pr, zz);
+      for (int t = 0; t < 2; ++t) {
+        const int m = 4 * jj + 2 * pr + t;
+        if (m < n3) {
+          srp[w * n3 + m] = sr[w * n3 + m] + sigma * (double)zz[t];
+          srpf[w * n3 + m] = (float)srp[w * n3 + m];
+        }
+      }
+    }
+    __syncthreads();
+    // pair distances
+    for (int q = tid; q < WTt * P; q += NT) {
+      const int w = q / P, p = q % P;
+      const float* rw = srpf + w * n3;
+      float v[3];
+      if (p < s.Pee) {
+        int a = 0, rem = p;
+        while (rem >= N - 1 - a) { rem -= N - 1 - a; ++a; }
+        const int bb = a + 1 + rem;
+        for (int x = 0; x < 3; ++x) v[x] = rw[3 * a + x] - rw[3 * bb + x];
+      } else {
+        const int qq = p - s.Pee, i = qq / s.M, I = qq % s.M;
+        for (int x = 0; x < 3; ++x) v[x] = rw[3 * i + x] - tab.R[3 * I + x];
+      }
+      sd[q] = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    }
+    // orbitals: cusp sphere, radial parts, contractions (float32)
+    for (int e = tid; e < rowsN; e += NT) {
+      int Ic = -1;
+      if (s.use_cusp)
+        for (int I = 0; I < s.M; ++I) {
+          const float v0 = srpf[3 * e] - tab.R[3 * I], v1 = srpf[3 * e + 1] - tab.R[3 * I + 1],
+                      v2 = srpf[3 * e + 2] - tab.R[3 * I + 2];
+          if (v0 * v0 + v1 * v1 + v2 * v2 < tab.rc[I] * tab.rc[I]) Ic = I;
+        }
+      sic[e] = Ic;
+    }
+    for (int q = tid; q < rowsN * s.n_shells; q += NT) {
+      const int e = q / s.n_shells, sh_ = q % s.n_shells;
+      const int c = s.sh_center[sh_], np_ = s.sh_nprim[sh_], po = s.sh_poff[sh_];
+      const float v0 = srpf[3 * e] - tab.R[3 * c], v1 = srpf[3 * e + 1] - tab.R[3 * c + 1],
+                  v2 = srpf[3 * e + 2] - tab.R[3 * c + 2];
+      const float r2 = v0 * v0 + v1 * v1 + v2 * v2;
+      float ev = 0;
+      if (s.sh_l[sh_] == -1)
+        ev = tab.pcoef[po] * expf(-tab.pexp[po] * sqrtf(r2));
+      else
+        for (int k = 0; k < np_; ++k) ev += tab.pcoef[po + k] * expf(-tab.pexp[po + k] * r2);
+      srad[q] = ev;
+    }
+    // x^(0) on real rows, zero elsewhere
+    for (int q = tid; q < TM * D; q += NT) sx[(q / D) * LX + q % D] = (q / D) < rowsN ? net.p[o.x0 + q % D] : 0.f;
+    __syncthreads();
+    for (int q = tid; q < rowsN * no; q += NT) {
+      const int e = q / no, mu = q % no;
+      const int Ic = sic[e];
+      float acc = 0;
+      for (int sh_ = 0; sh_ < s.n_shells; ++sh_) {
+        const int c = s.sh_center[sh_], l = s.sh_l[sh_], bo = s.sh_boff[sh_];
+        const float ev = srad[e * s.n_shells + sh_];
+        if (l <= 0) {
+          if (l == 0 && c == Ic && s.cusp_on[Ic * no + mu]) continue;
+          acc += tab.mo[(size_t)bo * no + mu] * ev;
+          continue;
+        }
+        const float v0 = srpf[3 * e] - tab.R[3 * c], v1 = srpf[3 * e + 1] - tab.R[3 * c + 1],
+                    v2 = srpf[3 * e + 2] - tab.R[3 * c + 2];
+        const float* m = tab.mo + (size_t)bo * no + mu;
+        if (l == 1)
+          acc += ev * (m[0] * v0 + m[no] * v1 + m[2 * no] * v2);
+        else
+          acc += ev * (m[0] * v0 * v0 + m[no] * v0 * v1 + m[2 * no] * v0 * v2 + m[3 * no] * v1 * v1 +
+                       m[4 * no] * v1 * v2 + m[5 * no] * v2 * v2);
+      }
+      if (Ic >= 0 && s.cusp_on[Ic * no + mu]) {
+        const float v0 = srpf[3 * e] - tab.R[3 * Ic], v1 = srpf[3 * e + 1] - tab.R[3 * Ic + 1],
+                    v2 = srpf[3 * e + 2] - tab.R[3 * Ic + 2];
+        const float dd = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
+        const int k = Ic * no + mu;
+        const float* a = tab.ca + (size_t)k * 5;
+        acc += tab.cC[k] + tab.cs[k] * expf(a[0] + dd * (a[1] + dd * (a[2] + dd * (a[3] + dd * a[4]))));
+      }
+      sphi[q] = acc;
+    }
+    // ---- interaction layers
+    for (int n = 0; n < s.L && !abort_flag; ++n) {
+      // A <- x (K = D); h = x Wh + bh
+      for (int q = tid; q < TM * (D / 8); q += NT) {
+        const int row = q % TM, k8 = (q / TM) * 8;
+        float v[8];
+        const float4 p0 = *(const float4*)(sx + row * LX + k8), p1 = *(const float4*)(sx + row * LX + k8 + 4);
+        v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w; v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
+        put3x8(sA, L.a_bytes, row, k8, D, v);
+      }
+      fence_sync();
+      gemm(0, false);
+      for (int c0 = half * 16; c0 < Zd; c0 += 32) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)c0, v);
+        for (int jj = 0; jj < 16; jj += 4)
+          *(float4*)(sh + arow * LH + c0 + jj) =
+              make_float4(v[jj] + net.p[o.hb[n] + c0 + jj], v[jj + 1] + net.p[o.hb[n] + c0 + jj + 1],
+                          v[jj + 2] + net.p[o.hb[n] + c0 + jj + 2], v[jj + 3] + net.p[o.hb[n] + c0 + jj + 3]);
+      }
+      bool g_started = false;
+      for (int c = 0; c < 3; ++c) {
+        const int cnt = s.ch_off[c + 1] - s.ch_off[c];
+        if (cnt == 0) continue;
+        const int* pl = s.ch_pairs + s.ch_off[c];
+        const int rowsP = WTt * cnt;
+        // A <- distance features of this channel's pairs (K = s.K)
+        __syncthreads();  // A is free (the previous MMA completed) and sh is written
+        const float* fm = s.feat_mu32;
+        const float* fi = s.feat_isig2_32;
+        for (int q = tid; q < TM * (K / 8); q += NT) {
+          const int row = q % TM, k8 = (q / TM) * 8;
+          float v[8];
+          const float dd = row < rowsP ? sd[(row / cnt) * P + pl[row % cnt]] : 0.f;
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const float dm = dd - fm[k8 + t];
+            v[t] = row < rowsP ? dd * dd * expf(-dd - dm * dm * fi[k8 + t]) : 0.f;
+          }
+          put3x8(sA, L.a_bytes, row, k8, K, v);
+        }
+        fence_sync();
+        gemm(0, false);  // hidden = e W1
+        for (int c0 = half * 16; c0 < Hw; c0 += 32) {
+          float v[16];
+          tmem_ld16(trow + (uint32_t)c0, v);
+          for (int jj = 0; jj < 16; ++jj) v[jj] = arow < rowsP ? sspf(v[jj] + net.p[o.b1[n][c] + c0 + jj]) : 0.f;
+          put3x8(sA, L.a_bytes, arow, c0, Hw, v);
+          put3x8(sA, L.a_bytes, arow, c0 + 8, Hw, v + 8);
+        }
+        fence_sync();
+        gemm(0, false);  // w = hidden W2
+        for (int c0 = half * 16; c0 < Zd; c0 += 32) {
+          float v[16];
+          tmem_ld16(trow + (uint32_t)c0, v);
+          const float* b2 = net.p + o.b2[n][c] + c0;
+          for (int jj = 0; jj < 16; jj += 4)
+            *(float4*)(swv + arow * LH + c0 + jj) =
+                make_float4(v[jj] + b2[jj], v[jj + 1] + b2[jj + 1], v[jj + 2] + b2[jj + 2], v[jj + 3] + b2[jj + 3]);
+        }
+        __syncthreads();
+        // A <- z_c: messages of this channel for every electron (K = Zd)
+        for (int q = tid; q < TM * (Zd / 8); q += NT) {
+          const int e = q % TM, z8 = (q / TM) * 8;
+          float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+          if (e < rowsN) {
+            const int w = e / N, i = e % N;
+            if (c < 2) {
+              const bool si = i < s.n_up;
+              for (int jn = 0; jn < N; ++jn) {
+                if (jn == i || (((jn < s.n_up) == si) != (c == 0))) continue;
+                const int p = i < jn ? pn_pair_index(i, jn, N) : pn_pair_index(jn, i, N);
+                const float* wr = swv + (w * cnt + s.ch_pos[p]) * LH + z8;
+                const float* hr = sh + (w * N + jn) * LH + z8;
+                const float4 w0 = *(const float4*)wr, w1 = *(const float4*)(wr + 4);
+                const float4 h0 = *(const float4*)hr, h1 = *(const float4*)(hr + 4);
+                acc[0] += w0.x * h0.x; acc[1] += w0.y * h0.y; acc[2] += w0.z * h0.z; acc[3] += w0.w * h0.w;
+                acc[4] += w1.x * h1.x; acc[5] += w1.y * h1.y; acc[6] += w1.z * h1.z; acc[7] += w1.w * h1.w;
+              }
+            } else {
+              for (int I = 0; I < s.M; ++I) {
+                const float* wr = swv + (w * cnt + s.ch_pos[s.Pee + i * s.M + I]) * LH + z8;
+                const float4 w0 = *(const float4*)wr, w1 = *(const float4*)(wr + 4);
+                const float* y = net.p + o.Y + I * Zd + z8;
+                acc[0] += w0.x * y[0]; acc[1] += w0.y * y[1]; acc[2] += w0.z * y[2]; acc[3] += w0.w * y[3];
+                acc[4] += w1.x * y[4]; acc[5] += w1.y * y[5]; acc[6] += w1.z * y[6]; acc[7] += w1.w * y[7];
+              }
+            }
+          }
+          put3x8(sA, L.a_bytes, e, z8, Zd, acc);
+        }
+        fence_sync();
+        gemm(col_g, g_started);  // x update += z_c G_c
+        g_started = true;
+      }
+      // x += accumulated update + receiving biases
+      for (int c0 = half * 16; c0 < D; c0 += 32) {
+        float v[16];
+        tmem_ld16(trow + col_g + (uint32_t)c0, v);
+        if (arow < rowsN) {
+          const float* gb = net.Gb + (size_t)n * D + c0;
+          for (int jj = 0; jj < 16; jj += 4) {
+            float4 xv = *(float4*)(sx + arow * LX + c0 + jj);
+            xv.x += v[jj] + gb[jj];
+            xv.y += v[jj + 1] + gb[jj + 1];
+            xv.z += v[jj + 2] + gb[jj + 2];
+            xv.w += v[jj + 3] + gb[jj + 3];
+            *(float4*)(sx + arow * LX + c0 + jj) = xv;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (abort_flag) break;
+    // ---- backflow head kappa: three maps on every electron row
+    for (int q = tid; q < TM * (D / 8); q += NT) {
+      const int row = q % TM, k8 = (q / TM) * 8;
+      float v[8];
+      const float4 p0 = *(const float4*)(sx + row * LX + k8), p1 = *(const float4*)(sx + row * LX + k8 + 4);
+      v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w; v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
+      put3x8(sA, L.a_bytes, row, k8, D, v);
+    }
+    fence_sync();
+    for (int layer = 0; layer < 2; ++layer) {
+      gemm(0, false);
+      for (int c0 = half * 16; c0 < D; c0 += 32) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)c0, v);
+        for (int jj = 0; jj < 16; ++jj) v[jj] = arow < rowsN ? sspf(v[jj] + net.p[o.kb[layer] + c0 + jj]) : 0.f;
+        put3x8(sA, L.a_bytes, arow, c0, D, v);
+        put3x8(sA, L.a_bytes, arow, c0 + 8, D, v + 8);
+      }
+      fence_sync();
+    }
+    gemm(0, false);
+    for (int c0 = half * 16; c0 < no; c0 += 32) {
+      float v[16];
+      tmem_ld16(trow + (uint32_t)c0, v);
+      if (arow < rowsN)
+        for (int jj = 0; jj < 16 && c0 + jj < no; ++jj) sF[arow * no + c0 + jj] = v[jj] + net.p[o.kb[2] + c0 + jj];
+    }
+    __syncthreads();
+    // ---- Jastrow head eta on the electron sums (rows = walkers)
+    for (int q = tid; q < TM * (D / 8); q += NT) {
+      const int w = q % TM, d8 = (q / TM) * 8;
+      float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (w < WTt)
+        for (int i = 0; i < N; ++i) {
+          const float4 p0 = *(const float4*)(sx + (w * N + i) * LX + d8), p1 = *(const float4*)(sx + (w * N + i) * LX + d8 + 4);
+          acc[0] += p0.x; acc[1] += p0.y; acc[2] += p0.z; acc[3] += p0.w;
+          acc[4] += p1.x; acc[5] += p1.y; acc[6] += p1.z; acc[7] += p1.w;
+        }
+      put3x8(sA, L.a_bytes, w, d8, D, acc);
+    }
+    fence_sync();
+    for (int layer = 0; layer < 2; ++layer) {
+      gemm(0, false);
+      for (int c0 = half * 16; c0 < D; c0 += 32) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)c0, v);
+        for (int jj = 0; jj < 16; ++jj) v[jj] = arow < WTt ? sspf(v[jj] + net.p[o.eb[layer] + c0 + jj]) : 0.f;
+        put3x8(sA, L.a_bytes, arow, c0, D, v);
+        put3x8(sA, L.a_bytes, arow, c0 + 8, D, v + 8);
+      }
+      fence_sync();
+    }
+    gemm(0, false);
+    if (half == 0) {
+      float v[16];
+      tmem_ld16(trow, v);
+      if (arow < WTt) sJ[arow] = v[0] + net.p[o.eb[2]];
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    // ---- determinants (float64 LU), one thread per (walker, det, spin)
+    for (int q = tid; q < WTt * nd * 2; q += NT) {
+      const int sp = q & 1, p = (q >> 1) % nd, w = (q >> 1) / nd;
+      const int ns = sp ? s.n_dn : s.n_up, e0 = sp ? s.n_up : 0;
+      double ld = 0, sg = 1;
+      if (ns > 0) {
+        double A[PN_MAX_SPIN * PN_MAX_SPIN];
+        const int* occ = s.occ + p * N + e0;
+        for (int a = 0; a < ns; ++a)
+          for (int bb = 0; bb < ns; ++bb) {
+            const int e = w * N + e0 + a, mu = occ[bb];
+            A[a * ns + bb] = (double)sphi[e * no + mu] * (1.0 + (double)sF[e * no + mu]);
+          }
+        pn_slogdet(A, ns, &ld, &sg);
+      }
+      sdet[2 * q] = ld;
+      sdet[2 * q + 1] = sg;
+    }
+    __syncthreads();
+    // ---- ln|psi'| (float64 log-sum over determinants) and the accept test
+    for (int w = tid; w < WTt; w += NT) {
+      const double* dw = sdet + (size_t)w * nd * 4;
+      double m = -INFINITY;
+      for (int p = 0; p < nd; ++p) {
+        const double sg = dw[4 * p + 1] * dw[4 * p + 3];
+        if (s.ci[p] != 0.0 && sg != 0.0) m = fmax(m, dw[4 * p] + dw[4 * p + 2]);
+      }
+      double S = 0;
+      if (m > -INFINITY)
+        for (int p = 0; p < nd; ++p) {
+          const double sg = dw[4 * p + 1] * dw[4 * p + 3];
+          if (sg != 0.0) S += s.ci[p] * sg * exp(dw[4 * p] + dw[4 * p + 2] - m);
+        }
+      float gam = 0.f;
+      if (s.use_gamma)
+        for (int a = 0; a < N; ++a)
+          for (int bb = a + 1; bb < N; ++bb) {
+            const float c = ((a < s.n_up) == (bb < s.n_up)) ? 0.25f : 0.5f;
+            gam -= c / (1.f + sd[w * P + pn_pair_index(a, bb, N)]);
+          }
+      const double lpn = (double)gam + (double)sJ[w] + m + log(fabs(S));
+      unsigned c4[4] = {(unsigned)nblk4, walker0 + (unsigned)(w0 + w), (unsigned)(step & 0xffffffffull),
+                        (unsigned)(step >> 32)};
+      pn_philox(c4, (unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
+      const float u = ((float)c4[0] + 0.5f) * 2.3283064365386963e-10f;
+      if (u < expf((float)(2.0 * (lpn - slp[w])))) {
+        for (int q = 0; q < n3; ++q) sr[w * n3 + q] = srp[w * n3 + q];
+        slp[w] = lpn;
+        ++nacc;
+      }
+    }
+    __syncthreads();
+  }
+  if (abort_flag) {
+    if (tid == 0) atomicExch(s.dev_err, 3);
+    // drain: the weight copies and the MMA group this CTA may have in flight
+    wait_bar(saddr(&bar_w[g & 1]), (uint32_t)((g >> 1) & 1));
+    wait_bar(saddr(&bar_w[(g + 1) & 1]), (uint32_t)(((g + 1) >> 1) & 1));
+    wait_bar(saddr(&bar_m), mma_phase);
+  }
+  for (int i = tid; i < WTt * n3; i += NT) r[(size_t)w0 * n3 + i] = sr[i];
+  for (int i = tid; i < WTt; i += NT) lp[w0 + i] = slp[i];
+  if (nacc) atomicAdd(&acc_count, nacc);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && n_acc && acc_count) atomicAdd(n_acc, (unsigned long long)acc_count);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+}
+
+}  // namespace
+
+// Launch the tensor-core sampler; PN_ENOTREADY if the system's tiles do not fit.
+int pn_run_metropolis_tc(const DevSys& s, const DevNet<float>& net, double* r, double* lp, int W, unsigned walker0,
+                         int n_steps, double sigma, unsigned long long seed, unsigned long long step0,
+                         unsigned long long* n_acc, cudaStream_t st) {
+  if (net.tc_n == 0 || !net.tcpack || !net.tcst || W <= 0) return PN_ENOTREADY;
+  int maxcnt = 1;
+  for (int c = 0; c < 3; ++c) maxcnt = std::max(maxcnt, s.ch_off[c + 1] - s.ch_off[c]);
+  int dev = 0, sms = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int WT = std::min(TM / s.N, TM / maxcnt);
+  WT = std::min(WT, std::max(1, (W + sms - 1) / sms));
+  if (WT < 1) return PN_ENOTREADY;
+  const TcLayout L = tc_layout(s, net.tc_max_bytes, WT);
+  if (L.bytes + 1024 > (size_t)maxsm) return PN_ENOTREADY;
+  const uint32_t cols = s.D > 64 ? 256u : 128u;
+  PN_CUDA(cudaFuncSetAttribute(k_metropolis_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes));
+  const int blocks = (W + WT - 1) / WT;
+  PN_LAUNCH("k_metropolis_tc", st,
+            k_metropolis_tc<<<blocks, NT, L.bytes, st>>>(s, net, net.tcst, net.tcpack, L, r, lp, W, walker0, n_steps,
+                                                         sigma, seed, step0, n_acc, cols));
+  return PN_OK;
+}

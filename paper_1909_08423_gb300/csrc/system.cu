@@ -321,7 +321,78 @@ static int upload_params(pn_system_s* s, const double* hp) {
       PN_CUDA(cudaMemcpy(s->wpack32, pk.data(), tot * 4, cudaMemcpyHostToDevice));
     }
   }
+  // tensor-core sampler blocks (only for shapes its tiles take)
+  if (s->tcpack) {
+    TcStages& t = s->tcst;
+    t.n = 0;
+    t.max_bytes = 0;
+    std::vector<unsigned short> pk;
+    // one block: W[k][n] (row stride ldw, K x Nout) -> three bf16 pieces of
+    // W^T in the canonical layout (rows n padded to 16, K columns)
+    auto add = [&](const double* W, int K, int Nout, int ldw) {
+      const int Np = (Nout + 15) / 16 * 16;
+      const size_t piece = (size_t)Np * K;
+      const size_t base = pk.size();
+      pk.resize(base + 3 * piece, 0);
+      const size_t sbo = (size_t)K / 8 * 64;  // elements between 8-row groups
+      for (int n = 0; n < Nout; ++n)
+        for (int k = 0; k < K; ++k) {
+          float a = (float)W[(size_t)k * ldw + n];
+          unsigned short pc[3];
+          for (int q = 0; q < 3; ++q) {
+            uint32_t bits;
+            memcpy(&bits, &a, 4);
+            // round to nearest even bf16
+            const uint32_t lsb = (bits >> 16) & 1u;
+            bits += 0x7FFFu + lsb;
+            pc[q] = (unsigned short)(bits >> 16);
+            uint32_t hb = (uint32_t)pc[q] << 16;
+            float hf;
+            memcpy(&hf, &hb, 4);
+            a = a - hf;
+          }
+          const size_t off = (size_t)(n / 8) * sbo + (size_t)(k / 8) * 64 + (size_t)(n % 8) * 8 + (k % 8);
+          for (int q = 0; q < 3; ++q) pk[base + q * piece + off] = pc[q];
+        }
+      t.off[t.n] = (int64_t)base;
+      t.bytes[t.n] = (int)(3 * piece * 2);
+      t.K[t.n] = K;
+      t.Np[t.n] = Np;
+      t.max_bytes = std::max(t.max_bytes, t.bytes[t.n]);
+      ++t.n;
+    };
+    for (int n = 0; n < d.L; ++n) {
+      add(hp + o.hW[n], d.D, d.Zd, d.Zd);
+      for (int c = 0; c < 3; ++c) {
+        if (d.ch_off[c + 1] == d.ch_off[c]) continue;
+        add(hp + o.W1[n][c], d.K, d.Hw, d.Hw);
+        add(hp + o.W2[n][c], d.Hw, d.Zd, d.Zd);
+        add(hp + o.GW[n][c], d.Zd, d.D, d.D);
+      }
+    }
+    add(hp + o.kW[0], d.D, d.D, d.D);
+    add(hp + o.kW[1], d.D, d.D, d.D);
+    add(hp + o.kW[2], d.D, d.n_orb, d.n_orb);
+    add(hp + o.eW[0], d.D, d.D, d.D);
+    add(hp + o.eW[1], d.D, d.D, d.D);
+    add(hp + o.eW[2], d.D, 1, 1);
+    PN_CUDA(cudaMemcpy(s->tcpack, pk.data(), pk.size() * 2, cudaMemcpyHostToDevice));
+    PN_CUDA(cudaMemcpy(s->tcst_dev, &t, sizeof(TcStages), cudaMemcpyHostToDevice));
+  }
   return PN_OK;
+}
+
+// bf16 elements of the tensor-core sampler blocks; 0 if the shapes do not fit its tiles.
+static size_t tcpack_elems(const DevSys& d) {
+  if (d.D % 16 || d.Zd % 16 || d.K % 16 || d.Hw % 16 || d.D > 128) return 0;
+  auto np = [](int n) { return (size_t)((n + 15) / 16 * 16); };
+  size_t tot = 0;
+  for (int n = 0; n < d.L; ++n) {
+    tot += 3 * np(d.Zd) * d.D;
+    for (int c = 0; c < 3; ++c) tot += 3 * (np(d.Hw) * d.K + np(d.Zd) * d.Hw + np(d.D) * d.Zd);
+  }
+  tot += 3 * d.D * (np(d.D) * 4 + np(d.n_orb) + np(1));
+  return tot;
 }
 
 // Elements of the packed sampler weights (upper bound, for allocation).
@@ -343,6 +414,7 @@ DevNet<double> pn_devnet<double>(pn_system_s* s) {
   DevNet<double> n;
   n.p = s->p64; n.Gcat = s->Gcat64; n.Gb = s->Gb64; n.off = s->off;
   n.wpack = s->wpack64; n.stab = s->stab64;
+  n.tcpack = nullptr; n.tcst = nullptr; n.tc_n = 0; n.tc_max_bytes = 0;
   return n;
 }
 template <>
@@ -350,6 +422,7 @@ DevNet<float> pn_devnet<float>(pn_system_s* s) {
   DevNet<float> n;
   n.p = s->p32; n.Gcat = s->Gcat32; n.Gb = s->Gb32; n.off = s->off;
   n.wpack = s->wpack32; n.stab = s->stab32;
+  n.tcpack = s->tcpack; n.tcst = s->tcst_dev; n.tc_n = s->tcst.n; n.tc_max_bytes = s->tcst.max_bytes;
   return n;
 }
 
@@ -486,7 +559,8 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   ds.D = d->D; ds.Zd = d->Zd; ds.K = d->K; ds.L = d->L; ds.Hw = std::max(d->K, d->Zd);
   ds.Pee = N * (N - 1) / 2; ds.Pen = N * d->M; ds.Ppair = ds.Pee + ds.Pen;
   ds.r_c = d->r_c; ds.use_cusp = d->use_cusp; ds.use_gamma = d->use_gamma;
-  ds.fused_sampler = 1;
+  // mixed path: the tensor-core sampler where its tiles fit (else the warp kernel)
+  ds.fused_sampler = d->precision == PN_MIXED ? 4 : 1;
   ds.tensor_cores = 0;  // set per system after calibration (PN_OPT_TENSOR_CORES)
   double Vnn = 0;
   for (int I = 0; I < d->M; ++I)
@@ -535,6 +609,10 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
     }
     ds.ch_off[3] = (int)chp.size();
     ds.ch_pairs = dev_upload(s, chp.data(), chp.size(), &err);
+    std::vector<int> pos(chp.size());
+    for (int c = 0; c < 3; ++c)
+      for (int q = ds.ch_off[c]; q < ds.ch_off[c + 1]; ++q) pos[chp[q]] = q - ds.ch_off[c];
+    ds.ch_pos = dev_upload(s, pos.data(), pos.size(), &err);
   }
   {
     // nucleus per electron for walker initialisation: the nuclei repeated
@@ -581,6 +659,13 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   s->Gb32 = dev_upload<float>(s, nullptr, (size_t)std::max(d->L, 1) * d->D, &err);
   s->wpack64 = dev_upload<double>(s, nullptr, wpack_elems(ds), &err);
   s->wpack32 = dev_upload<float>(s, nullptr, wpack_elems(ds), &err);
+  s->tcst.n = 0;
+  s->tcpack = nullptr;
+  s->tcst_dev = nullptr;
+  if (size_t te = tcpack_elems(ds)) {
+    s->tcpack = dev_upload<unsigned short>(s, nullptr, te, &err);
+    s->tcst_dev = (TcStages*)dev_upload<unsigned char>(s, nullptr, sizeof(TcStages), &err);
+  }
   if (err != PN_OK) {
     pn_set_error("device allocation/upload failed during init");
     free_all(s);

@@ -205,7 +205,7 @@ def test_chunking_is_batch_invariant(lib, oracles):
     np.testing.assert_array_equal(a, b)
 
 
-@pytest.mark.parametrize("fused", [1, 2, 3, 0])
+@pytest.mark.parametrize("fused", [1, 2, 3, 4, 0])
 @pytest.mark.parametrize("name,W,steps", [("be", 96, 6), ("h10", 37, 3), ("n2", 9, 2)])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_metropolis_matches_oracle(lib, oracles, precision, name, W, steps, fused):
