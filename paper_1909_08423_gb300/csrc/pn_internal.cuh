@@ -156,13 +156,14 @@ struct StageTab {
 // of the transposed weight (rows = outputs padded to 16, columns = inputs)
 // in the canonical K-major tile layout of tcgen05 (8 x 16-byte core
 // matrices), so that one bulk copy lands it ready for the MMA.
+constexpr int PN_MAX_TC_STAGES = 10 * PN_MAX_LAYERS + 6;  // h + 3 x (W1, W2, G) per layer, 6 head maps
 struct TcStages {
-  int n;                       // stages per Metropolis step (0: not eligible)
+  int n;                          // stages per Metropolis step (0: not eligible)
   int max_bytes;
-  int64_t off[PN_MAX_STAGES];  // bf16 element offset in the packed blocks
-  int bytes[PN_MAX_STAGES];    // bytes (three pieces)
-  int K[PN_MAX_STAGES];        // inputs
-  int Np[PN_MAX_STAGES];       // outputs padded to 16
+  int64_t off[PN_MAX_TC_STAGES];  // bf16 element offset in the packed blocks
+  int bytes[PN_MAX_TC_STAGES];    // bytes (three pieces)
+  int K[PN_MAX_TC_STAGES];        // inputs
+  int Np[PN_MAX_TC_STAGES];       // outputs padded to 16
 };
 
 // Per-precision parameters on the device.

@@ -1,6 +1,6 @@
 // Metropolis sampler with the network on the 5th-generation tensor cores.
 //
-// One CTA (eight warps) owns a tile of WT walkers, so that its electrons
+// One CTA (sixteen warps) owns a tile of WT walkers, so that its electrons
 // (WT * N <= 128) and the pairs of each filter channel (WT * count <= 128)
 // each fill one 128-row tcgen05 tile.  Every linear map of every step is
 // one or a few tcgen05.mma groups over the whole tile:
@@ -10,18 +10,20 @@
 //    prepared at parameter upload, double-buffered one stage ahead;
 //  - one thread issues the six piece products (a0b0 ... a1b1, float32
 //    accumulation in tensor memory) and commits to an mbarrier;
-//  - warps w and w + 4 read TMEM lanes 32(w % 4)..+31 (their 32 rows),
-//    alternate 16-column chunks each, with tcgen05.ld and apply bias and
-//    activation, writing the next operand or float state.
+//  - warps w, w + 4, w + 8, w + 12 read TMEM lanes 32(w % 4)..+31 (their
+//    32 rows), taking every fourth 8-column chunk, with tcgen05.ld and
+//    apply bias and activation, writing the next operand or float state.
 // Geometry, orbitals (float32), features, messages, determinants (float64
-// LU and log-sum) and the accept test run on the CUDA cores between the MMA
-// stages.  Every wait is bounded: on expiry the CTA raises the device error
+// LU; each determinant kept as mantissa x 2^exponent so that the signed sum
+// over determinants needs one logarithm per walker) and the accept test run
+// on the CUDA cores between the MMA stages.  Every wait is bounded: on expiry the CTA raises the device error
 // word, drains what it started (bounded) and frees its TMEM.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "ansatz_dev.cuh"
 #include "kernels.cuh"
@@ -30,7 +32,8 @@
 namespace {
 
 constexpr int TM = 128;  // tile rows
-constexpr int NT = 256;  // threads: two warps per TMEM lane quadrant
+constexpr int NT = 512;        // threads
+constexpr int WPQ = NT / 128;  // warps per TMEM lane quadrant
 
 __device__ inline uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -55,38 +58,22 @@ __device__ inline uint32_t idesc_bf16(int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
-__device__ inline void put3(unsigned char* A, int piece_bytes, int row, int k, int K, float a) {
-  const __nv_bfloat16 h0 = __float2bfloat16_rn(a);
-  const float r1 = a - __bfloat162float(h0);
-  const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
-  const __nv_bfloat16 h2 = __float2bfloat16_rn(r1 - __bfloat162float(h1));
-  const uint32_t off = t_off(row, k, K);
-  *(__nv_bfloat16*)(A + off) = h0;
-  *(__nv_bfloat16*)(A + piece_bytes + off) = h1;
-  *(__nv_bfloat16*)(A + 2 * piece_bytes + off) = h2;
-}
-
 // Eight consecutive k of one row -> one 16-byte store per bf16 piece (one
-// row of a core matrix).  k8 is a multiple of 8.
+// row of a core matrix).  k8 is a multiple of 8.  Pairs convert together
+// (low half = even k).
+__device__ inline uint32_t bf2u(__nv_bfloat162 h) { return *reinterpret_cast<const uint32_t*>(&h); }
 __device__ inline void put3x8(unsigned char* A, int piece_bytes, int row, int k8, int K, const float v[8]) {
   uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    uint32_t h0[2], h1[2], h2[2];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const float a = v[2 * j + t];
-      const __nv_bfloat16 b0 = __float2bfloat16_rn(a);
-      const float r1 = a - __bfloat162float(b0);
-      const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
-      const __nv_bfloat16 b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
-      h0[t] = __bfloat16_as_ushort(b0);
-      h1[t] = __bfloat16_as_ushort(b1);
-      h2[t] = __bfloat16_as_ushort(b2);
-    }
-    w0[j] = h0[0] | (h0[1] << 16);
-    w1[j] = h1[0] | (h1[1] << 16);
-    w2[j] = h2[0] | (h2[1] << 16);
+    const float a = v[2 * j], b = v[2 * j + 1];
+    const __nv_bfloat162 p0 = __floats2bfloat162_rn(a, b);
+    const float ra = a - __low2float(p0), rb = b - __high2float(p0);
+    const __nv_bfloat162 p1 = __floats2bfloat162_rn(ra, rb);
+    const __nv_bfloat162 p2 = __floats2bfloat162_rn(ra - __low2float(p1), rb - __high2float(p1));
+    w0[j] = bf2u(p0);
+    w1[j] = bf2u(p1);
+    w2[j] = bf2u(p2);
   }
   const uint32_t off = t_off(row, k8, K);
   *(uint4*)(A + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
@@ -109,19 +96,70 @@ __device__ inline bool wait_bar(uint32_t bar, uint32_t par) {
   return false;
 }
 
-__device__ inline float sspf(float x) { return fmaxf(x, 0.f) + log1pf(expf(-fabsf(x))) - 0.69314718055994530942f; }
+// Shifted softplus ln(1 + e^x) - ln 2 = max(x, 0) + log1p(e^-|x|) - ln 2, with
+// log1p(t) = 2 artanh(t / (2 + t)) summed as the Taylor series of artanh:
+// s = t / (2 + t) <= 1/3 on t in (0, 1], and the terms up to s^13 / 13 leave
+// a relative remainder below 2e-8.
+__device__ inline float sspf(float x) {
+  const float t = __expf(-fabsf(x));
+  const float s = __fdividef(t, 2.f + t);
+  const float s2 = s * s;
+  float q = 1.f / 13.f;
+  q = fmaf(q, s2, 1.f / 11.f);
+  q = fmaf(q, s2, 1.f / 9.f);
+  q = fmaf(q, s2, 1.f / 7.f);
+  q = fmaf(q, s2, 1.f / 5.f);
+  q = fmaf(q, s2, 1.f / 3.f);
+  q = fmaf(q, s2, 1.f);
+  return fmaxf(x, 0.f) + 2.f * s * q - 0.69314718055994530942f;
+}
 
-__device__ inline void tmem_ld16(uint32_t taddr, float v[16]) {
-  uint32_t u[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-      "[%16];"
-      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
-        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
-      : "r"(taddr));
+// Eight consecutive fp32 columns of this thread's TMEM lane.
+__device__ inline void tmem_ld8(uint32_t taddr, float v[8]) {
+  uint32_t u[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
+               : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(u[j]);
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(u[j]);
+}
+
+// LU with partial pivoting in float64 of an ns x ns matrix (row-major,
+// overwritten); det(A) = mant * 2^ex with the sign in mant, rescaled after
+// every pivot so that products of small orbital values do not underflow.
+// mant = 0 for a singular matrix.
+__device__ inline void det_scaled(double* A, int ns, double* mant, int* ex) {
+  double m = 1.0;
+  int e = 0;
+  for (int c = 0; c < ns; ++c) {
+    int best = c;
+    double bv = fabs(A[c * ns + c]);
+    for (int rr = c + 1; rr < ns; ++rr) {
+      const double v = fabs(A[rr * ns + c]);
+      if (v > bv) { bv = v; best = rr; }
+    }
+    if (!(bv > 0.0)) { *mant = 0.0; *ex = 0; return; }
+    if (best != c) {
+      for (int k = 0; k < ns; ++k) {
+        const double t0 = A[c * ns + k];
+        A[c * ns + k] = A[best * ns + k];
+        A[best * ns + k] = t0;
+      }
+      m = -m;
+    }
+    const double piv = A[c * ns + c];
+    int pe;
+    m = frexp(m * piv, &pe);
+    e += pe;
+    const double ip = 1.0 / piv;
+    for (int rr = c + 1; rr < ns; ++rr) {
+      const double f = A[rr * ns + c] * ip;
+      for (int k = c + 1; k < ns; ++k) A[rr * ns + k] -= f * A[c * ns + k];
+    }
+  }
+  *mant = m;
+  *ex = e;
 }
 
 struct TcLayout {
@@ -178,11 +216,19 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   __shared__ unsigned acc_count;
+  __shared__ int st_K[PN_MAX_TC_STAGES], st_Np[PN_MAX_TC_STAGES], st_bytes[PN_MAX_TC_STAGES];
+  __shared__ long long st_off[PN_MAX_TC_STAGES];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = s.N, P = s.Ppair, D = s.D, Zd = s.Zd, K = s.K, Hw = s.Hw, no = s.n_orb, nd = s.n_det;
   const int n3 = 3 * N, nblk4 = (n3 + 3) / 4;
   const NetOff& o = net.off;
-  const TcStages& ts = *tsp;
+  const int nst = tsp->n;
+  for (int i = tid; i < nst; i += NT) {
+    st_K[i] = tsp->K[i];
+    st_Np[i] = tsp->Np[i];
+    st_bytes[i] = tsp->bytes[i];
+    st_off[i] = tsp->off[i];
+  }
   const int w0 = blockIdx.x * L.WT;
   const int WTt = min(L.WT, W - w0);
   const int rowsN = WTt * N;
@@ -224,17 +270,17 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
   const uint32_t col_g = (uint32_t)(tmem_cols / 2);  // receiving-map accumulator columns
 
   // ---- weight stages (TMA, one ahead) and MMA completion phases
-  const long total = (long)n_steps * ts.n;
+  const long total = (long)n_steps * nst;
   long g = 0;
   uint32_t mma_phase = 0;
   auto issue = [&](long q) {
     if (q >= total) return;
-    const int j = (int)(q % ts.n), b = (int)(q & 1);
+    const int j = (int)(q % nst), b = (int)(q & 1);
     const uint32_t bar = saddr(&bar_w[b]);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(ts.bytes[j]) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(st_bytes[j]) : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      saddr(sB[b])),
-                 "l"(tcpack + ts.off[j]), "r"(ts.bytes[j]), "r"(bar)
+                 "l"(tcpack + st_off[j]), "r"(st_bytes[j]), "r"(bar)
                  : "memory");
   };
   if (tid == 0) {
@@ -246,8 +292,8 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
   // into TMEM columns [col, col + Np); acc_first says whether the first
   // product adds to what the columns hold.
   auto gemm = [&](uint32_t col, bool acc_first) {
-    const int j = (int)(g % ts.n), b = (int)(g & 1);
-    const int Kg = ts.K[j], Np = ts.Np[j];
+    const int j = (int)(g % nst), b = (int)(g & 1);
+    const int Kg = st_K[j], Np = st_Np[j];
     if (!wait_bar(saddr(&bar_w[b]), (uint32_t)((g >> 1) & 1))) abort_flag = 1;
     if (tid == 0 && !abort_flag) {
       asm volatile("tcgen05.fence::after_thread_sync;");
@@ -296,8 +342,8 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
     asm volatile("tcgen05.fence::after_thread_sync;");
   };
   // warp w reads TMEM lane quadrant w % 4 (tile rows 32 (w % 4) + lane);
-  // the two warps of a quadrant take alternate 16-column chunks
-  const int quad = warp & 3, half = warp >> 2;
+  // the WPQ warps of a quadrant take every WPQ-th 8-column chunk
+  const int quad = warp & 3, sub = warp >> 2;
   const int arow = quad * 32 + lane;
   const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
 
@@ -411,13 +457,13 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
       }
       fence_sync();
       gemm(0, false);
-      for (int c0 = half * 16; c0 < Zd; c0 += 32) {
-        float v[16];
-        tmem_ld16(trow + (uint32_t)c0, v);
-        for (int jj = 0; jj < 16; jj += 4)
+      for (int c0 = sub * 8; c0 < Zd; c0 += WPQ * 8) {
+        float v[8];
+        tmem_ld8(trow + (uint32_t)c0, v);
+        const float* hb = net.p + o.hb[n] + c0;
+        for (int jj = 0; jj < 8; jj += 4)
           *(float4*)(sh + arow * LH + c0 + jj) =
-              make_float4(v[jj] + net.p[o.hb[n] + c0 + jj], v[jj + 1] + net.p[o.hb[n] + c0 + jj + 1],
-                          v[jj + 2] + net.p[o.hb[n] + c0 + jj + 2], v[jj + 3] + net.p[o.hb[n] + c0 + jj + 3]);
+              make_float4(v[jj] + hb[jj], v[jj + 1] + hb[jj + 1], v[jj + 2] + hb[jj + 2], v[jj + 3] + hb[jj + 3]);
       }
       bool g_started = false;
       for (int c = 0; c < 3; ++c) {
@@ -442,20 +488,20 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
         }
         fence_sync();
         gemm(0, false);  // hidden = e W1
-        for (int c0 = half * 16; c0 < Hw; c0 += 32) {
-          float v[16];
-          tmem_ld16(trow + (uint32_t)c0, v);
-          for (int jj = 0; jj < 16; ++jj) v[jj] = arow < rowsP ? sspf(v[jj] + net.p[o.b1[n][c] + c0 + jj]) : 0.f;
+        for (int c0 = sub * 8; c0 < Hw; c0 += WPQ * 8) {
+          float v[8];
+          tmem_ld8(trow + (uint32_t)c0, v);
+          const float* b1 = net.p + o.b1[n][c] + c0;
+          for (int jj = 0; jj < 8; ++jj) v[jj] = arow < rowsP ? sspf(v[jj] + b1[jj]) : 0.f;
           put3x8(sA, L.a_bytes, arow, c0, Hw, v);
-          put3x8(sA, L.a_bytes, arow, c0 + 8, Hw, v + 8);
         }
         fence_sync();
         gemm(0, false);  // w = hidden W2
-        for (int c0 = half * 16; c0 < Zd; c0 += 32) {
-          float v[16];
-          tmem_ld16(trow + (uint32_t)c0, v);
+        for (int c0 = sub * 8; c0 < Zd; c0 += WPQ * 8) {
+          float v[8];
+          tmem_ld8(trow + (uint32_t)c0, v);
           const float* b2 = net.p + o.b2[n][c] + c0;
-          for (int jj = 0; jj < 16; jj += 4)
+          for (int jj = 0; jj < 8; jj += 4)
             *(float4*)(swv + arow * LH + c0 + jj) =
                 make_float4(v[jj] + b2[jj], v[jj + 1] + b2[jj + 1], v[jj + 2] + b2[jj + 2], v[jj + 3] + b2[jj + 3]);
         }
@@ -495,12 +541,12 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
         g_started = true;
       }
       // x += accumulated update + receiving biases
-      for (int c0 = half * 16; c0 < D; c0 += 32) {
-        float v[16];
-        tmem_ld16(trow + col_g + (uint32_t)c0, v);
+      for (int c0 = sub * 8; c0 < D; c0 += WPQ * 8) {
+        float v[8];
+        tmem_ld8(trow + col_g + (uint32_t)c0, v);
         if (arow < rowsN) {
           const float* gb = net.Gb + (size_t)n * D + c0;
-          for (int jj = 0; jj < 16; jj += 4) {
+          for (int jj = 0; jj < 8; jj += 4) {
             float4 xv = *(float4*)(sx + arow * LX + c0 + jj);
             xv.x += v[jj] + gb[jj];
             xv.y += v[jj + 1] + gb[jj + 1];
@@ -524,21 +570,21 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
     fence_sync();
     for (int layer = 0; layer < 2; ++layer) {
       gemm(0, false);
-      for (int c0 = half * 16; c0 < D; c0 += 32) {
-        float v[16];
-        tmem_ld16(trow + (uint32_t)c0, v);
-        for (int jj = 0; jj < 16; ++jj) v[jj] = arow < rowsN ? sspf(v[jj] + net.p[o.kb[layer] + c0 + jj]) : 0.f;
+      for (int c0 = sub * 8; c0 < D; c0 += WPQ * 8) {
+        float v[8];
+        tmem_ld8(trow + (uint32_t)c0, v);
+        const float* kb = net.p + o.kb[layer] + c0;
+        for (int jj = 0; jj < 8; ++jj) v[jj] = arow < rowsN ? sspf(v[jj] + kb[jj]) : 0.f;
         put3x8(sA, L.a_bytes, arow, c0, D, v);
-        put3x8(sA, L.a_bytes, arow, c0 + 8, D, v + 8);
       }
       fence_sync();
     }
     gemm(0, false);
-    for (int c0 = half * 16; c0 < no; c0 += 32) {
-      float v[16];
-      tmem_ld16(trow + (uint32_t)c0, v);
+    for (int c0 = sub * 8; c0 < no; c0 += WPQ * 8) {
+      float v[8];
+      tmem_ld8(trow + (uint32_t)c0, v);
       if (arow < rowsN)
-        for (int jj = 0; jj < 16 && c0 + jj < no; ++jj) sF[arow * no + c0 + jj] = v[jj] + net.p[o.kb[2] + c0 + jj];
+        for (int jj = 0; jj < 8 && c0 + jj < no; ++jj) sF[arow * no + c0 + jj] = v[jj] + net.p[o.kb[2] + c0 + jj];
     }
     __syncthreads();
     // ---- Jastrow head eta on the electron sums (rows = walkers)
@@ -556,19 +602,19 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
     fence_sync();
     for (int layer = 0; layer < 2; ++layer) {
       gemm(0, false);
-      for (int c0 = half * 16; c0 < D; c0 += 32) {
-        float v[16];
-        tmem_ld16(trow + (uint32_t)c0, v);
-        for (int jj = 0; jj < 16; ++jj) v[jj] = arow < WTt ? sspf(v[jj] + net.p[o.eb[layer] + c0 + jj]) : 0.f;
+      for (int c0 = sub * 8; c0 < D; c0 += WPQ * 8) {
+        float v[8];
+        tmem_ld8(trow + (uint32_t)c0, v);
+        const float* eb = net.p + o.eb[layer] + c0;
+        for (int jj = 0; jj < 8; ++jj) v[jj] = arow < WTt ? sspf(v[jj] + eb[jj]) : 0.f;
         put3x8(sA, L.a_bytes, arow, c0, D, v);
-        put3x8(sA, L.a_bytes, arow, c0 + 8, D, v + 8);
       }
       fence_sync();
     }
     gemm(0, false);
-    if (half == 0) {
-      float v[16];
-      tmem_ld16(trow, v);
+    if (sub == 0) {
+      float v[8];
+      tmem_ld8(trow, v);
       if (arow < WTt) sJ[arow] = v[0] + net.p[o.eb[2]];
     }
     __syncthreads();
@@ -577,7 +623,8 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
     for (int q = tid; q < WTt * nd * 2; q += NT) {
       const int sp = q & 1, p = (q >> 1) % nd, w = (q >> 1) / nd;
       const int ns = sp ? s.n_dn : s.n_up, e0 = sp ? s.n_up : 0;
-      double ld = 0, sg = 1;
+      double mant = 1.0;
+      int ex = 0;
       if (ns > 0) {
         double A[PN_MAX_SPIN * PN_MAX_SPIN];
         const int* occ = s.occ + p * N + e0;
@@ -586,26 +633,27 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
             const int e = w * N + e0 + a, mu = occ[bb];
             A[a * ns + bb] = (double)sphi[e * no + mu] * (1.0 + (double)sF[e * no + mu]);
           }
-        pn_slogdet(A, ns, &ld, &sg);
+        det_scaled(A, ns, &mant, &ex);
       }
-      sdet[2 * q] = ld;
-      sdet[2 * q + 1] = sg;
+      sdet[2 * q] = mant;
+      sdet[2 * q + 1] = (double)ex;
     }
     __syncthreads();
-    // ---- ln|psi'| (float64 log-sum over determinants) and the accept test
+    // ---- ln|psi'| = gamma + J + ln|sum_p c_p det_up,p det_dn,p| (float64
+    // sum of the determinant products scaled by the largest power of two)
+    // and the accept test
     for (int w = tid; w < WTt; w += NT) {
       const double* dw = sdet + (size_t)w * nd * 4;
-      double m = -INFINITY;
-      for (int p = 0; p < nd; ++p) {
-        const double sg = dw[4 * p + 1] * dw[4 * p + 3];
-        if (s.ci[p] != 0.0 && sg != 0.0) m = fmax(m, dw[4 * p] + dw[4 * p + 2]);
-      }
+      int emax = INT_MIN;
+      for (int p = 0; p < nd; ++p)
+        if (s.ci[p] != 0.0 && dw[4 * p] * dw[4 * p + 2] != 0.0) emax = max(emax, (int)(dw[4 * p + 1] + dw[4 * p + 3]));
       double S = 0;
-      if (m > -INFINITY)
+      if (emax != INT_MIN)
         for (int p = 0; p < nd; ++p) {
-          const double sg = dw[4 * p + 1] * dw[4 * p + 3];
-          if (sg != 0.0) S += s.ci[p] * sg * exp(dw[4 * p] + dw[4 * p + 2] - m);
+          const double pr = dw[4 * p] * dw[4 * p + 2];
+          if (pr != 0.0) S += s.ci[p] * ldexp(pr, (int)(dw[4 * p + 1] + dw[4 * p + 3]) - emax);
         }
+      const double m = emax == INT_MIN ? -INFINITY : (double)emax * 0.69314718055994530942;
       float gam = 0.f;
       if (s.use_gamma)
         for (int a = 0; a < N; ++a)
@@ -659,7 +707,7 @@ int pn_run_metropolis_tc(const DevSys& s, const DevNet<float>& net, double* r, d
   WT = std::min(WT, std::max(1, (W + sms - 1) / sms));
   if (WT < 1) return PN_ENOTREADY;
   const TcLayout L = tc_layout(s, net.tc_max_bytes, WT);
-  if (L.bytes + 1024 > (size_t)maxsm) return PN_ENOTREADY;
+  if (L.bytes + 4096 > (size_t)maxsm) return PN_ENOTREADY;  // + static shared memory
   const uint32_t cols = s.D > 64 ? 256u : 128u;
   PN_CUDA(cudaFuncSetAttribute(k_metropolis_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes));
   const int blocks = (W + WT - 1) / WT;

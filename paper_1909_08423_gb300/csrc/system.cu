@@ -354,6 +354,7 @@ static int upload_params(pn_system_s* s, const double* hp) {
           const size_t off = (size_t)(n / 8) * sbo + (size_t)(k / 8) * 64 + (size_t)(n % 8) * 8 + (k % 8);
           for (int q = 0; q < 3; ++q) pk[base + q * piece + off] = pc[q];
         }
+      if (t.n >= PN_MAX_TC_STAGES) return;  // cannot happen within PN_MAX_LAYERS; checked below
       t.off[t.n] = (int64_t)base;
       t.bytes[t.n] = (int)(3 * piece * 2);
       t.K[t.n] = K;
@@ -376,6 +377,9 @@ static int upload_params(pn_system_s* s, const double* hp) {
     add(hp + o.eW[0], d.D, d.D, d.D);
     add(hp + o.eW[1], d.D, d.D, d.D);
     add(hp + o.eW[2], d.D, 1, 1);
+    int live = 0;
+    for (int c = 0; c < 3; ++c) live += d.ch_off[c + 1] != d.ch_off[c];
+    if (t.n != d.L * (1 + 3 * live) + 6) { pn_set_error("tensor-core stage table overflow"); return PN_EINVAL; }
     PN_CUDA(cudaMemcpy(s->tcpack, pk.data(), pk.size() * 2, cudaMemcpyHostToDevice));
     PN_CUDA(cudaMemcpy(s->tcst_dev, &t, sizeof(TcStages), cudaMemcpyHostToDevice));
   }

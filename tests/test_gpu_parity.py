@@ -235,6 +235,59 @@ def test_metropolis_matches_oracle(lib, oracles, precision, name, W, steps, fuse
         assert same.mean() > 0.9
 
 
+def _be_eight_layers():
+    """Be with eight interaction layers: the longest stage list the
+    tensor-core sampler takes (8 x (h + 3 x (W1, W2, G)) + 6 head maps)."""
+    return synth.make_system([4.0], [[0, 0, 0]], lambda z: {0: 4, 1: 2}, n_det=4, D=64, K=32, L=8, seed=3)
+
+
+@pytest.mark.parametrize("fused", [1, 2, 4])
+@pytest.mark.parametrize("name,W,steps", [("be", 96, 6), ("h10", 37, 4), ("n2", 9, 3), ("be8", 40, 3)])
+def test_mixed_metropolis_moves_are_valid(lib, oracles, name, W, steps, fused):
+    """Float32-network samplers, one step at a time from their own state:
+    every walker either stays or moves to the oracle's proposal r + sigma xi
+    (same Philox stream), its stored ln|psi| is the oracle's at its position
+    to float32 accuracy, and wherever its accept decision differs from the
+    oracle's, the oracle's log-ratio 2 (ln|psi'| - ln|psi|) lies within 1e-3
+    of ln u, i.e. the flip is a rounding-level tie, not a wrong test."""
+    from oracle import philox
+    o = Oracle(_be_eight_layers()) if name == "be8" else oracles[name]
+    sysd = o.sys
+    N = o.N
+    r = synth.random_walkers(sysd, W, 9)
+    lp0, _ = o.eval_logpsi(r)
+    r, _ = sampling.metropolis(o, r, lp0, 20, 0.2, seed=5, step0=0)[:2]  # leave the tails
+    lp, _ = o.eval_logpsi(r)
+    s = lib.System(sysd, precision=lib.PN_MIXED, max_walkers=40)
+    s.set_option(lib.PN_OPT_FUSED_SAMPLER, fused)
+    rd = torch.as_tensor(r, device="cuda").clone()
+    lpd = torch.as_tensor(lp, device="cuda").clone()
+    walkers = np.arange(W)
+    flips = 0
+    for k in range(steps):
+        step = 1000 + k
+        r_old = rd.cpu().numpy()
+        lp_old_oracle, _ = o.eval_logpsi(r_old)
+        s.metropolis_step(rd, lpd, 1, 0.2, 77, step)
+        torch.cuda.synchronize()
+        r_new = rd.cpu().numpy()
+        xi = philox.normals(77, walkers, step, 3 * N).reshape(W, N, 3)
+        prop = r_old + 0.2 * xi
+        stay = np.all(np.abs(r_new - r_old) == 0, axis=(1, 2))
+        moved = np.all(np.abs(r_new - prop) < 1e-5, axis=(1, 2))
+        assert np.all(stay | moved), "a walker left both r and r + sigma xi"
+        lp_prop, _ = o.eval_logpsi(prop)
+        u = philox.accept_uniform(77, walkers, step, 3 * N)
+        margin = 2.0 * (lp_prop - lp_old_oracle) - np.log(u)
+        acc_oracle = margin > 0
+        differ = moved != acc_oracle
+        assert np.all(np.abs(margin[differ]) < 1e-3), margin[differ]
+        flips += int(differ.sum())
+        lp_ref, _ = o.eval_logpsi(r_new)
+        np.testing.assert_allclose(lpd.cpu().numpy(), lp_ref, rtol=0, atol=2e-4 * (1 + np.abs(lp_ref)).max())
+    assert flips <= max(1, W * steps // 20)
+
+
 def test_init_walkers_match_oracle(lib, oracles):
     sysd = oracles["n2"].sys
     s = lib.System(sysd, precision=lib.PN_FP64, max_walkers=16)
