@@ -7,12 +7,19 @@
 //  - activations are written by the CUDA cores into shared memory as three
 //    bf16 pieces in the canonical K-major layout (8 x 16-byte core
 //    matrices), weights arrive the same way by a TMA bulk copy of a block
-//    prepared at parameter upload, double-buffered one stage ahead;
-//  - one thread issues the six piece products (a0b0 ... a1b1, float32
-//    accumulation in tensor memory) and commits to an mbarrier;
+//    prepared at parameter upload, triple-buffered two stages ahead;
+//  - the weight pieces of a block lie one after another, which is itself a
+//    canonical tile of 3 Np rows, so one thread issues per 16-wide k-step
+//    three MMAs, a0 [b0; b1; b2], a1 [b0; b1] and a2 b0, accumulating the
+//    products with b0, b1, b2 in three float32 column blocks of tensor
+//    memory (the six products of the split, three instructions), and
+//    commits to an mbarrier (an MMA costs about the same whatever its N);
 //  - warps w, w + 4, w + 8, w + 12 read TMEM lanes 32(w % 4)..+31 (their
-//    32 rows), taking every fourth 8-column chunk, with tcgen05.ld and
-//    apply bias and activation, writing the next operand or float state.
+//    32 rows), taking every fourth 8-column chunk, sum the three column
+//    blocks (smallest first) and apply bias and activation, writing the
+//    next operand or float state.
+// h of the first layer is one row for every electron (x^(0) is shared), so
+// it is formed once per launch and its GEMM is not in the stage list.
 // Geometry, orbitals (float32), features, messages, determinants (float64
 // LU; each determinant kept as mantissa x 2^exponent so that the signed sum
 // over determinants needs one logarithm per walker) and the accept test run
@@ -114,6 +121,25 @@ __device__ inline float sspf(float x) {
   return fmaxf(x, 0.f) + 2.f * s * q - 0.69314718055994530942f;
 }
 
+// Eight consecutive fp32 columns of this thread's TMEM lane, summed over the
+// three product blocks at taddr, taddr + np, taddr + 2 np (b2 + b1 + b0).
+__device__ inline void tmem_ld8x3(uint32_t taddr, uint32_t np, float v[8]) {
+  uint32_t u0[8], u1[8], u2[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(u0[0]), "=r"(u0[1]), "=r"(u0[2]), "=r"(u0[3]), "=r"(u0[4]), "=r"(u0[5]), "=r"(u0[6]), "=r"(u0[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(u1[0]), "=r"(u1[1]), "=r"(u1[2]), "=r"(u1[3]), "=r"(u1[4]), "=r"(u1[5]), "=r"(u1[6]), "=r"(u1[7])
+               : "r"(taddr + np));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(u2[0]), "=r"(u2[1]), "=r"(u2[2]), "=r"(u2[3]), "=r"(u2[4]), "=r"(u2[5]), "=r"(u2[6]), "=r"(u2[7])
+               : "r"(taddr + 2u * np));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    v[j] = (__uint_as_float(u2[j]) + __uint_as_float(u1[j])) + __uint_as_float(u0[j]);
+}
+
 // Eight consecutive fp32 columns of this thread's TMEM lane.
 __device__ inline void tmem_ld8(uint32_t taddr, float v[8]) {
   uint32_t u[8];
@@ -166,7 +192,7 @@ struct TcLayout {
   int WT;
   int a_bytes;  // one piece of the A tile region (128 rows x Kmax bf16)
   int b_bytes;  // one weight buffer
-  size_t A, B0, B1, x, h, wv, r, rp, rpf, d, phi, rad, ic, det, F, J, lp, bytes;
+  size_t A, B[3], x, h, wv, h0, r, rp, rpf, d, phi, rad, ic, det, F, J, lp, bytes;
 };
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 127) & ~(size_t)127; }
@@ -181,13 +207,13 @@ inline TcLayout tc_layout(const DevSys& s, int max_bytes, int WT) {
   auto put = [&](size_t b) { size_t q = o; o += a16(b); return q; };
   const size_t N = s.N, P = s.Ppair, no = s.n_orb;
   L.A = put(3 * (size_t)L.a_bytes);
-  L.B0 = put(L.b_bytes);
-  L.B1 = put(L.b_bytes);
+  for (int b = 0; b < 3; ++b) L.B[b] = put(L.b_bytes);
   // float state rows padded by 4 floats: lanes run over rows, so an unpadded
   // power-of-two stride would put every lane in the same bank
   L.x = put((size_t)TM * (s.D + 4) * 4);
   L.h = put((size_t)TM * (s.Zd + 4) * 4);
   L.wv = put((size_t)TM * (s.Zd + 4) * 4);
+  L.h0 = put((size_t)s.Zd * 4);
   L.r = put(WT * N * 3 * 8);
   L.rp = put(WT * N * 3 * 8);
   L.rpf = put(WT * N * 3 * 4);
@@ -211,7 +237,8 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
                                                          unsigned long long seed, unsigned long long step0,
                                                          unsigned long long* __restrict__ n_acc, uint32_t tmem_cols) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar_w[2];
+  __shared__ __align__(8) uint64_t bar_w[3];
+  __shared__ long issued;  // weight copies issued (thread 0 writes)
   __shared__ __align__(8) uint64_t bar_m;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
@@ -234,7 +261,8 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
   const int rowsN = WTt * N;
   const int LX = D + 4, LH = Zd + 4;  // padded row strides of x and of h / w
   unsigned char* sA = smem + L.A;
-  unsigned char* sB[2] = {smem + L.B0, smem + L.B1};
+  unsigned char* sB[3] = {smem + L.B[0], smem + L.B[1], smem + L.B[2]};
+  float* sh0 = (float*)(smem + L.h0);
   float* sx = (float*)(smem + L.x);
   float* sh = (float*)(smem + L.h);
   float* swv = (float*)(smem + L.wv);
@@ -256,8 +284,8 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar_w[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar_w[1])));
+    for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar_w[b])));
+    issued = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar_m)));
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
@@ -267,16 +295,19 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t col_g = (uint32_t)(tmem_cols / 2);  // receiving-map accumulator columns
+  const uint32_t col_g = (uint32_t)(tmem_cols / 2);  // receiving-map accumulator (3 blocks of D columns)
 
-  // ---- weight stages (TMA, one ahead) and MMA completion phases
+  // ---- weight stages (TMA, two ahead) and MMA completion phases
   const long total = (long)n_steps * nst;
   long g = 0;
   uint32_t mma_phase = 0;
+  bool mma_pending = false;  // thread 0: a committed MMA group not yet waited for
+  uint32_t pend_phase = 0;
   auto issue = [&](long q) {
     if (q >= total) return;
-    const int j = (int)(q % nst), b = (int)(q & 1);
+    const int j = (int)(q % nst), b = (int)(q % 3);
     const uint32_t bar = saddr(&bar_w[b]);
+    issued = q + 1;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(st_bytes[j]) : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      saddr(sB[b])),
@@ -286,52 +317,55 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
   if (tid == 0) {
     issue(0);
     issue(1);
+    issue(2);
   }
   // One GEMM stage: the A tile (K columns) is in sA, written and fenced by
   // every thread before the barrier that precedes this call.  Accumulates
-  // into TMEM columns [col, col + Np); acc_first says whether the first
-  // product adds to what the columns hold.
-  auto gemm = [&](uint32_t col, bool acc_first) {
-    const int j = (int)(g % nst), b = (int)(g & 1);
+  // the b0, b1, b2 products into TMEM column blocks [col + q Np, +Np),
+  // q = 0, 1, 2; acc_first says whether the first product adds to what the
+  // columns hold.  Returns Np, the block width the epilogue reads.
+  auto gemm = [&](uint32_t col, bool acc_first) -> uint32_t {
+    const int j = (int)(g % nst), b = (int)(g % 3);
     const int Kg = st_K[j], Np = st_Np[j];
-    if (!wait_bar(saddr(&bar_w[b]), (uint32_t)((g >> 1) & 1))) abort_flag = 1;
+    if (!abort_flag && !wait_bar(saddr(&bar_w[b]), (uint32_t)((g / 3) & 1))) abort_flag = 1;
     if (tid == 0 && !abort_flag) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t a0 = saddr(sA), b0 = saddr(sB[b]);
-      const uint32_t bp = (uint32_t)Np * (uint32_t)Kg * 2u;  // one weight piece
-      const uint32_t idesc = idesc_bf16(Np);
-      // descriptors of the three pieces, built once; a k-step of 16 bf16
-      // (256 bytes) advances only the start-address field (addr >> 4)
-      const uint64_t dA[3] = {sdesc(a0, Kg), sdesc(a0 + (uint32_t)L.a_bytes, Kg), sdesc(a0 + 2u * (uint32_t)L.a_bytes, Kg)};
-      const uint64_t dB[3] = {sdesc(b0, Kg), sdesc(b0 + bp, Kg), sdesc(b0 + 2u * bp, Kg)};
+      const uint32_t i3 = idesc_bf16(3 * Np), i2 = idesc_bf16(2 * Np), i1 = idesc_bf16(Np);
+      // descriptors built once; a k-step of 16 bf16 (256 bytes) advances
+      // only the start-address field (addr >> 4)
+      const uint64_t dA0 = sdesc(a0, Kg), dA1 = sdesc(a0 + (uint32_t)L.a_bytes, Kg),
+                     dA2 = sdesc(a0 + 2u * (uint32_t)L.a_bytes, Kg), dB = sdesc(b0, Kg);
       const uint32_t dcol = tmem + col;
       for (int st = 0; st < Kg / 16; ++st) {
         const uint64_t adv = (uint64_t)(st * 16);
-        // (A piece, B piece), smallest weight first: a1b1 a2b0 a0b2 a1b0 a0b1 a0b0
         const uint32_t first = (st == 0) ? (acc_first ? 1u : 0u) : 1u;
         asm volatile(
             "{\n\t.reg .pred pf, pt;\n\t"
-            "setp.ne.b32 pf, %13, 0;\n\t"
-            "setp.eq.b32 pt, %13, %13;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %12, pf;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %4, %12, pt;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %12, pt;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %7, %8, %12, pt;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %9, %10, %12, pt;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %11, %14, %12, pt;\n\t}" ::"r"(dcol),
-            "l"(dA[1] + adv), "l"(dB[1] + adv), "l"(dA[2] + adv), "l"(dB[0] + adv), "l"(dA[0] + adv),
-            "l"(dB[2] + adv), "l"(dA[1] + adv), "l"(dB[0] + adv), "l"(dA[0] + adv), "l"(dB[1] + adv),
-            "l"(dA[0] + adv), "r"(idesc), "r"(first), "l"(dB[0] + adv));
+            "setp.ne.b32 pf, %8, 0;\n\t"
+            "setp.eq.b32 pt, %8, %8;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %4, %5, pf;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %4, %6, pt;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %4, %7, pt;\n\t}" ::"r"(dcol),
+            "l"(dA0 + adv), "l"(dA1 + adv), "l"(dA2 + adv), "l"(dB + adv), "r"(i3), "r"(i2), "r"(i1), "r"(first));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(&bar_m))
                    : "memory");
+      mma_pending = true;
+      pend_phase = mma_phase;
     }
-    if (!abort_flag && !wait_bar(saddr(&bar_m), mma_phase)) abort_flag = 1;
+    if (!abort_flag) {
+      if (wait_bar(saddr(&bar_m), mma_phase))
+        mma_pending = false;
+      else
+        abort_flag = 1;
+    }
     mma_phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
     // the weight buffer is free once the MMAs completed
-    if (tid == 0) issue(g + 2);
+    if (tid == 0 && !abort_flag) issue(g + 3);
     ++g;
+    return (uint32_t)Np;
   };
   // End of an epilogue that wrote the next A tile: make the generic-proxy
   // stores visible to the tensor core, then meet at the barrier.
@@ -350,11 +384,19 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
   // ---- walker state
   for (int i = tid; i < WTt * n3; i += NT) sr[i] = r[(size_t)w0 * n3 + i];
   for (int i = tid; i < WTt; i += NT) slp[i] = lp[w0 + i];
+  for (int z = tid; z < Zd; z += NT) {  // h^(0) row (float32, in input order)
+    float acc = net.p[o.hb[0] + z];
+    for (int d = 0; d < D; ++d) acc = fmaf(net.p[o.x0 + d], net.p[o.hW[0] + (size_t)d * Zd + z], acc);
+    sh0[z] = acc;
+  }
   unsigned nacc = 0;
   __syncthreads();
   const OrbTab<float> tab = orb_tab<float>(s);
 
-  for (int kstep = 0; kstep < n_steps && !abort_flag; ++kstep) {
+  // abort decisions are taken at barriers (__syncthreads_or) so that every
+  // thread leaves the loops at the same point
+  for (int kstep = 0; kstep < n_steps; ++kstep) {
+    bool stop = false;
     const unsigned long long step = step0 + (unsigned long long)kstep;
     // proposals (float32 normals, float64 positions)
     for (int q = tid; q < WTt * 2 * nblk4; q += NT) {
@@ -446,7 +488,13 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
       sphi[q] = acc;
     }
     // ---- interaction layers
-    for (int n = 0; n < s.L && !abort_flag; ++n) {
+    for (int n = 0; n < s.L; ++n) {
+      if (n == 0) {  // h^(0) = x^(0) Wh + bh, the same row for every electron
+        for (int q = tid; q < TM * (Zd / 4); q += NT) {
+          const int row = q / (Zd / 4), z4 = (q % (Zd / 4)) * 4;
+          *(float4*)(sh + row * LH + z4) = *(const float4*)(sh0 + z4);
+        }
+      } else {
       // A <- x (K = D); h = x Wh + bh
       for (int q = tid; q < TM * (D / 8); q += NT) {
         const int row = q % TM, k8 = (q / TM) * 8;
@@ -456,14 +504,15 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
         put3x8(sA, L.a_bytes, row, k8, D, v);
       }
       fence_sync();
-      gemm(0, false);
+      const uint32_t np = gemm(0, false);
       for (int c0 = sub * 8; c0 < Zd; c0 += WPQ * 8) {
         float v[8];
-        tmem_ld8(trow + (uint32_t)c0, v);
+        tmem_ld8x3(trow + (uint32_t)c0, np, v);
         const float* hb = net.p + o.hb[n] + c0;
         for (int jj = 0; jj < 8; jj += 4)
           *(float4*)(sh + arow * LH + c0 + jj) =
               make_float4(v[jj] + hb[jj], v[jj + 1] + hb[jj + 1], v[jj + 2] + hb[jj + 2], v[jj + 3] + hb[jj + 3]);
+      }
       }
       bool g_started = false;
       for (int c = 0; c < 3; ++c) {
@@ -487,19 +536,19 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
           put3x8(sA, L.a_bytes, row, k8, K, v);
         }
         fence_sync();
-        gemm(0, false);  // hidden = e W1
+        uint32_t np = gemm(0, false);  // hidden = e W1
         for (int c0 = sub * 8; c0 < Hw; c0 += WPQ * 8) {
           float v[8];
-          tmem_ld8(trow + (uint32_t)c0, v);
+          tmem_ld8x3(trow + (uint32_t)c0, np, v);
           const float* b1 = net.p + o.b1[n][c] + c0;
           for (int jj = 0; jj < 8; ++jj) v[jj] = arow < rowsP ? sspf(v[jj] + b1[jj]) : 0.f;
           put3x8(sA, L.a_bytes, arow, c0, Hw, v);
         }
         fence_sync();
-        gemm(0, false);  // w = hidden W2
+        np = gemm(0, false);  // w = hidden W2
         for (int c0 = sub * 8; c0 < Zd; c0 += WPQ * 8) {
           float v[8];
-          tmem_ld8(trow + (uint32_t)c0, v);
+          tmem_ld8x3(trow + (uint32_t)c0, np, v);
           const float* b2 = net.p + o.b2[n][c] + c0;
           for (int jj = 0; jj < 8; jj += 4)
             *(float4*)(swv + arow * LH + c0 + jj) =
@@ -537,13 +586,13 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
           put3x8(sA, L.a_bytes, e, z8, Zd, acc);
         }
         fence_sync();
-        gemm(col_g, g_started);  // x update += z_c G_c
+        gemm(col_g, g_started);  // x update += z_c G_c (blocks of D columns)
         g_started = true;
       }
       // x += accumulated update + receiving biases
       for (int c0 = sub * 8; c0 < D; c0 += WPQ * 8) {
         float v[8];
-        tmem_ld8(trow + col_g + (uint32_t)c0, v);
+        tmem_ld8x3(trow + col_g + (uint32_t)c0, (uint32_t)D, v);
         if (arow < rowsN) {
           const float* gb = net.Gb + (size_t)n * D + c0;
           for (int jj = 0; jj < 8; jj += 4) {
@@ -556,9 +605,12 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
           }
         }
       }
-      __syncthreads();
+      if (__syncthreads_or(abort_flag)) {
+        stop = true;
+        break;
+      }
     }
-    if (abort_flag) break;
+    if (stop) break;
     // ---- backflow head kappa: three maps on every electron row
     for (int q = tid; q < TM * (D / 8); q += NT) {
       const int row = q % TM, k8 = (q / TM) * 8;
@@ -569,20 +621,20 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
     }
     fence_sync();
     for (int layer = 0; layer < 2; ++layer) {
-      gemm(0, false);
+      const uint32_t np = gemm(0, false);
       for (int c0 = sub * 8; c0 < D; c0 += WPQ * 8) {
         float v[8];
-        tmem_ld8(trow + (uint32_t)c0, v);
+        tmem_ld8x3(trow + (uint32_t)c0, np, v);
         const float* kb = net.p + o.kb[layer] + c0;
         for (int jj = 0; jj < 8; ++jj) v[jj] = arow < rowsN ? sspf(v[jj] + kb[jj]) : 0.f;
         put3x8(sA, L.a_bytes, arow, c0, D, v);
       }
       fence_sync();
     }
-    gemm(0, false);
+    uint32_t np = gemm(0, false);
     for (int c0 = sub * 8; c0 < no; c0 += WPQ * 8) {
       float v[8];
-      tmem_ld8(trow + (uint32_t)c0, v);
+      tmem_ld8x3(trow + (uint32_t)c0, np, v);
       if (arow < rowsN)
         for (int jj = 0; jj < 8 && c0 + jj < no; ++jj) sF[arow * no + c0 + jj] = v[jj] + net.p[o.kb[2] + c0 + jj];
     }
@@ -601,24 +653,23 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
     }
     fence_sync();
     for (int layer = 0; layer < 2; ++layer) {
-      gemm(0, false);
+      const uint32_t npl = gemm(0, false);
       for (int c0 = sub * 8; c0 < D; c0 += WPQ * 8) {
         float v[8];
-        tmem_ld8(trow + (uint32_t)c0, v);
+        tmem_ld8x3(trow + (uint32_t)c0, npl, v);
         const float* eb = net.p + o.eb[layer] + c0;
         for (int jj = 0; jj < 8; ++jj) v[jj] = arow < WTt ? sspf(v[jj] + eb[jj]) : 0.f;
         put3x8(sA, L.a_bytes, arow, c0, D, v);
       }
       fence_sync();
     }
-    gemm(0, false);
+    np = gemm(0, false);
     if (sub == 0) {
       float v[8];
-      tmem_ld8(trow, v);
+      tmem_ld8x3(trow, np, v);
       if (arow < WTt) sJ[arow] = v[0] + net.p[o.eb[2]];
     }
-    __syncthreads();
-    if (abort_flag) break;
+    if (__syncthreads_or(abort_flag)) break;
     // ---- determinants (float64 LU), one thread per (walker, det, spin)
     for (int q = tid; q < WTt * nd * 2; q += NT) {
       const int sp = q & 1, p = (q >> 1) % nd, w = (q >> 1) / nd;
@@ -672,14 +723,15 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
         ++nacc;
       }
     }
-    __syncthreads();
+    if (__syncthreads_or(abort_flag)) break;
   }
-  if (abort_flag) {
-    if (tid == 0) atomicExch(s.dev_err, 3);
-    // drain: the weight copies and the MMA group this CTA may have in flight
-    wait_bar(saddr(&bar_w[g & 1]), (uint32_t)((g >> 1) & 1));
-    wait_bar(saddr(&bar_w[(g + 1) & 1]), (uint32_t)(((g + 1) >> 1) & 1));
-    wait_bar(saddr(&bar_m), mma_phase);
+  if (abort_flag && tid == 0) {
+    atomicExch(s.dev_err, 3);
+    // drain what this CTA may have in flight: the weight copies (at most
+    // three outstanding; thread 0 issued them) and the last MMA group
+    for (long q = issued - 3 < 0 ? 0 : issued - 3; q < issued; ++q)
+      wait_bar(saddr(&bar_w[q % 3]), (uint32_t)((q / 3) & 1));
+    if (mma_pending) wait_bar(saddr(&bar_m), pend_phase);
   }
   for (int i = tid; i < WTt * n3; i += NT) r[(size_t)w0 * n3 + i] = sr[i];
   for (int i = tid; i < WTt; i += NT) lp[w0 + i] = slp[i];
@@ -708,7 +760,11 @@ int pn_run_metropolis_tc(const DevSys& s, const DevNet<float>& net, double* r, d
   if (WT < 1) return PN_ENOTREADY;
   const TcLayout L = tc_layout(s, net.tc_max_bytes, WT);
   if (L.bytes + 4096 > (size_t)maxsm) return PN_ENOTREADY;  // + static shared memory
-  const uint32_t cols = s.D > 64 ? 256u : 128u;
+  // TMEM: three column blocks of the widest map at 0, three blocks of D for
+  // the receiving-map accumulator at 256
+  const int widest = std::max(std::max(s.D, s.Hw), std::max(s.Zd, (s.n_orb + 15) / 16 * 16));
+  if (3 * widest > 256) return PN_ENOTREADY;
+  const uint32_t cols = 512u;
   PN_CUDA(cudaFuncSetAttribute(k_metropolis_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes));
   const int blocks = (W + WT - 1) / WT;
   PN_LAUNCH("k_metropolis_tc", st,

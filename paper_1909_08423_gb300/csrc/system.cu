@@ -363,7 +363,7 @@ static int upload_params(pn_system_s* s, const double* hp) {
       ++t.n;
     };
     for (int n = 0; n < d.L; ++n) {
-      add(hp + o.hW[n], d.D, d.Zd, d.Zd);
+      if (n > 0) add(hp + o.hW[n], d.D, d.Zd, d.Zd);  // h of layer 0 is one shared row
       for (int c = 0; c < 3; ++c) {
         if (d.ch_off[c + 1] == d.ch_off[c]) continue;
         add(hp + o.W1[n][c], d.K, d.Hw, d.Hw);
@@ -379,7 +379,7 @@ static int upload_params(pn_system_s* s, const double* hp) {
     add(hp + o.eW[2], d.D, 1, 1);
     int live = 0;
     for (int c = 0; c < 3; ++c) live += d.ch_off[c + 1] != d.ch_off[c];
-    if (t.n != d.L * (1 + 3 * live) + 6) { pn_set_error("tensor-core stage table overflow"); return PN_EINVAL; }
+    if (t.n != d.L * (1 + 3 * live) - 1 + 6) { pn_set_error("tensor-core stage table overflow"); return PN_EINVAL; }
     PN_CUDA(cudaMemcpy(s->tcpack, pk.data(), pk.size() * 2, cudaMemcpyHostToDevice));
     PN_CUDA(cudaMemcpy(s->tcst_dev, &t, sizeof(TcStages), cudaMemcpyHostToDevice));
   }
