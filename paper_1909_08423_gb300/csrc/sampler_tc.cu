@@ -66,21 +66,22 @@ __device__ inline uint32_t idesc_bf16(int N) {
 }
 
 // Eight consecutive k of one row -> one 16-byte store per bf16 piece (one
-// row of a core matrix).  k8 is a multiple of 8.  Pairs convert together
-// (low half = even k).
-__device__ inline uint32_t bf2u(__nv_bfloat162 h) { return *reinterpret_cast<const uint32_t*>(&h); }
+// row of a core matrix).  k8 is a multiple of 8.  The split truncates: the
+// high 16 bits of a float are a bf16 (8 significant bits), the remainder
+// a - hi is exact and has at most 16 significant bits, and so on, so that
+// a = a0 + a1 + a2 exactly for every normal float.  Pairs are packed with
+// the even k in the low half.
 __device__ inline void put3x8(unsigned char* A, int piece_bytes, int row, int k8, int K, const float v[8]) {
   uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const float a = v[2 * j], b = v[2 * j + 1];
-    const __nv_bfloat162 p0 = __floats2bfloat162_rn(a, b);
-    const float ra = a - __low2float(p0), rb = b - __high2float(p0);
-    const __nv_bfloat162 p1 = __floats2bfloat162_rn(ra, rb);
-    const __nv_bfloat162 p2 = __floats2bfloat162_rn(ra - __low2float(p1), rb - __high2float(p1));
-    w0[j] = bf2u(p0);
-    w1[j] = bf2u(p1);
-    w2[j] = bf2u(p2);
+    const uint32_t ua = __float_as_uint(v[2 * j]), ub = __float_as_uint(v[2 * j + 1]);
+    const float ra = v[2 * j] - __uint_as_float(ua & 0xFFFF0000u), rb = v[2 * j + 1] - __uint_as_float(ub & 0xFFFF0000u);
+    const uint32_t ura = __float_as_uint(ra), urb = __float_as_uint(rb);
+    const float qa = ra - __uint_as_float(ura & 0xFFFF0000u), qb = rb - __uint_as_float(urb & 0xFFFF0000u);
+    w0[j] = __byte_perm(ua, ub, 0x7632);
+    w1[j] = __byte_perm(ura, urb, 0x7632);
+    w2[j] = __byte_perm(__float_as_uint(qa), __float_as_uint(qb), 0x7632);
   }
   const uint32_t off = t_off(row, k8, K);
   *(uint4*)(A + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
@@ -192,7 +193,8 @@ struct TcLayout {
   int WT;
   int a_bytes;  // one piece of the A tile region (128 rows x Kmax bf16)
   int b_bytes;  // one weight buffer
-  size_t A, B[3], x, h, wv, h0, r, rp, rpf, d, phi, rad, ic, det, F, J, lp, bytes;
+  size_t A, B[3], x, h, wv, h0, Y, msg, r, rp, rpf, d, phi, rad, ic, det, dex, F, J, lp, bytes;
+  int E;  // partner slots per (channel, electron): N - 1 + M
 };
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 127) & ~(size_t)127; }
@@ -214,6 +216,9 @@ inline TcLayout tc_layout(const DevSys& s, int max_bytes, int WT) {
   L.h = put((size_t)TM * (s.Zd + 4) * 4);
   L.wv = put((size_t)TM * (s.Zd + 4) * 4);
   L.h0 = put((size_t)s.Zd * 4);
+  L.Y = put((size_t)s.M * s.Zd * 4);
+  L.E = s.N - 1 + s.M;
+  L.msg = put((size_t)3 * s.N * (L.E + 1) * 4);
   L.r = put(WT * N * 3 * 8);
   L.rp = put(WT * N * 3 * 8);
   L.rpf = put(WT * N * 3 * 4);
@@ -221,7 +226,8 @@ inline TcLayout tc_layout(const DevSys& s, int max_bytes, int WT) {
   L.phi = put(WT * N * no * 4);
   L.rad = put(WT * N * (size_t)s.n_shells * 4);
   L.ic = put(WT * N * 4);
-  L.det = put((size_t)WT * s.n_det * 4 * 8);
+  L.det = put((size_t)WT * s.n_det * 2 * 8);
+  L.dex = put((size_t)WT * s.n_det * 2 * 4);
   L.F = put(WT * N * no * 4);
   L.J = put(WT * 4);
   L.lp = put(WT * 8);
@@ -263,6 +269,8 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
   unsigned char* sA = smem + L.A;
   unsigned char* sB[3] = {smem + L.B[0], smem + L.B[1], smem + L.B[2]};
   float* sh0 = (float*)(smem + L.h0);
+  float* sY = (float*)(smem + L.Y);
+  int* smsg = (int*)(smem + L.msg);  // [3][N][1 + E]: count, then (pos << 16 | partner)
   float* sx = (float*)(smem + L.x);
   float* sh = (float*)(smem + L.h);
   float* swv = (float*)(smem + L.wv);
@@ -274,6 +282,7 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
   float* srad = (float*)(smem + L.rad);
   int* sic = (int*)(smem + L.ic);
   double* sdet = (double*)(smem + L.det);
+  int* sdex = (int*)(smem + L.dex);
   float* sF = (float*)(smem + L.F);
   float* sJ = (float*)(smem + L.J);
   double* slp = (double*)(smem + L.lp);
@@ -299,25 +308,30 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
 
   // ---- weight stages (TMA, two ahead) and MMA completion phases
   const long total = (long)n_steps * nst;
-  long g = 0;
   uint32_t mma_phase = 0;
   bool mma_pending = false;  // thread 0: a committed MMA group not yet waited for
   uint32_t pend_phase = 0;
-  auto issue = [&](long q) {
-    if (q >= total) return;
-    const int j = (int)(q % nst), b = (int)(q % 3);
-    const uint32_t bar = saddr(&bar_w[b]);
-    issued = q + 1;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(st_bytes[j]) : "memory");
+  // ring positions: producer (thread 0) and consumer stage / buffer / phase
+  long n_issued = 0;
+  int pj = 0, pb = 0;
+  int cj = 0, cb = 0;
+  uint32_t cpar = 0;
+  auto issue = [&]() {
+    if (n_issued >= total) return;
+    const uint32_t bar = saddr(&bar_w[pb]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(st_bytes[pj]) : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     saddr(sB[b])),
-                 "l"(tcpack + st_off[j]), "r"(st_bytes[j]), "r"(bar)
+                     saddr(sB[pb])),
+                 "l"(tcpack + st_off[pj]), "r"(st_bytes[pj]), "r"(bar)
                  : "memory");
+    issued = ++n_issued;
+    pj = pj + 1 == nst ? 0 : pj + 1;
+    pb = pb == 2 ? 0 : pb + 1;
   };
   if (tid == 0) {
-    issue(0);
-    issue(1);
-    issue(2);
+    issue();
+    issue();
+    issue();
   }
   // One GEMM stage: the A tile (K columns) is in sA, written and fenced by
   // every thread before the barrier that precedes this call.  Accumulates
@@ -325,9 +339,9 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
   // q = 0, 1, 2; acc_first says whether the first product adds to what the
   // columns hold.  Returns Np, the block width the epilogue reads.
   auto gemm = [&](uint32_t col, bool acc_first) -> uint32_t {
-    const int j = (int)(g % nst), b = (int)(g % 3);
-    const int Kg = st_K[j], Np = st_Np[j];
-    if (!abort_flag && !wait_bar(saddr(&bar_w[b]), (uint32_t)((g / 3) & 1))) abort_flag = 1;
+    const int b = cb;
+    const int Kg = st_K[cj], Np = st_Np[cj];
+    if (!abort_flag && !wait_bar(saddr(&bar_w[b]), cpar)) abort_flag = 1;
     if (tid == 0 && !abort_flag) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t a0 = saddr(sA), b0 = saddr(sB[b]);
@@ -363,8 +377,12 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
     mma_phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
     // the weight buffer is free once the MMAs completed
-    if (tid == 0 && !abort_flag) issue(g + 3);
-    ++g;
+    if (tid == 0 && !abort_flag) issue();
+    cj = cj + 1 == nst ? 0 : cj + 1;
+    if (++cb == 3) {
+      cb = 0;
+      cpar ^= 1u;
+    }
     return (uint32_t)Np;
   };
   // End of an epilogue that wrote the next A tile: make the generic-proxy
@@ -384,6 +402,30 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
   // ---- walker state
   for (int i = tid; i < WTt * n3; i += NT) sr[i] = r[(size_t)w0 * n3 + i];
   for (int i = tid; i < WTt; i += NT) slp[i] = lp[w0 + i];
+  for (int q = tid; q < s.M * Zd; q += NT) sY[q] = net.p[o.Y + q];
+  // message partners: for channel c and electron i, the positions k of the
+  // channel's pairs that contain i and the other particle (electron or
+  // nucleus) of each
+  for (int q = tid; q < 3 * N; q += NT) {
+    const int c = q / N, i = q % N;
+    int* ent = smsg + q * (L.E + 1);
+    int cntp = 0;
+    const int* pl = s.ch_pairs + s.ch_off[c];
+    for (int k = 0; k < s.ch_off[c + 1] - s.ch_off[c]; ++k) {
+      const int p = pl[k];
+      int other = -1;
+      if (p < s.Pee) {
+        int a = 0, rem = p;
+        while (rem >= N - 1 - a) { rem -= N - 1 - a; ++a; }
+        const int bb = a + 1 + rem;
+        other = a == i ? bb : (bb == i ? a : -1);
+      } else if ((p - s.Pee) / s.M == i) {
+        other = (p - s.Pee) % s.M;
+      }
+      if (other >= 0) ent[1 + cntp++] = (k << 16) | other;
+    }
+    ent[0] = cntp;
+  }
   for (int z = tid; z < Zd; z += NT) {  // h^(0) row (float32, in input order)
     float acc = net.p[o.hb[0] + z];
     for (int d = 0; d < D; ++d) acc = fmaf(net.p[o.x0 + d], net.p[o.hW[0] + (size_t)d * Zd + z], acc);
@@ -496,8 +538,8 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
         }
       } else {
       // A <- x (K = D); h = x Wh + bh
-      for (int q = tid; q < TM * (D / 8); q += NT) {
-        const int row = q % TM, k8 = (q / TM) * 8;
+      for (int q = tid; q < rowsN * (D / 8); q += NT) {
+        const int row = q % rowsN, k8 = (q / rowsN) * 8;
         float v[8];
         const float4 p0 = *(const float4*)(sx + row * LX + k8), p1 = *(const float4*)(sx + row * LX + k8 + 4);
         v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w; v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
@@ -505,6 +547,7 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
       }
       fence_sync();
       const uint32_t np = gemm(0, false);
+      if (quad * 32 < rowsN)
       for (int c0 = sub * 8; c0 < Zd; c0 += WPQ * 8) {
         float v[8];
         tmem_ld8x3(trow + (uint32_t)c0, np, v);
@@ -524,28 +567,33 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
         __syncthreads();  // A is free (the previous MMA completed) and sh is written
         const float* fm = s.feat_mu32;
         const float* fi = s.feat_isig2_32;
-        for (int q = tid; q < TM * (K / 8); q += NT) {
-          const int row = q % TM, k8 = (q / TM) * 8;
+        // (rows of the tile past the real ones are left as they are: a row
+        // of the product depends only on the same row of A, and those rows
+        // are never read back)
+        for (int q = tid; q < rowsP * (K / 8); q += NT) {
+          const int row = q % rowsP, k8 = (q / rowsP) * 8;
           float v[8];
-          const float dd = row < rowsP ? sd[(row / cnt) * P + pl[row % cnt]] : 0.f;
+          const float dd = sd[(row / cnt) * P + pl[row % cnt]];
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
             const float dm = dd - fm[k8 + t];
-            v[t] = row < rowsP ? dd * dd * expf(-dd - dm * dm * fi[k8 + t]) : 0.f;
+            v[t] = dd * dd * __expf(-dd - dm * dm * fi[k8 + t]);
           }
           put3x8(sA, L.a_bytes, row, k8, K, v);
         }
         fence_sync();
         uint32_t np = gemm(0, false);  // hidden = e W1
-        for (int c0 = sub * 8; c0 < Hw; c0 += WPQ * 8) {
-          float v[8];
-          tmem_ld8x3(trow + (uint32_t)c0, np, v);
-          const float* b1 = net.p + o.b1[n][c] + c0;
-          for (int jj = 0; jj < 8; ++jj) v[jj] = arow < rowsP ? sspf(v[jj] + b1[jj]) : 0.f;
-          put3x8(sA, L.a_bytes, arow, c0, Hw, v);
-        }
+        if (quad * 32 < rowsP)
+          for (int c0 = sub * 8; c0 < Hw; c0 += WPQ * 8) {
+            float v[8];
+            tmem_ld8x3(trow + (uint32_t)c0, np, v);
+            const float* b1 = net.p + o.b1[n][c] + c0;
+            for (int jj = 0; jj < 8; ++jj) v[jj] = sspf(v[jj] + b1[jj]);
+            put3x8(sA, L.a_bytes, arow, c0, Hw, v);
+          }
         fence_sync();
         np = gemm(0, false);  // w = hidden W2
+        if (quad * 32 < rowsP)
         for (int c0 = sub * 8; c0 < Zd; c0 += WPQ * 8) {
           float v[8];
           tmem_ld8x3(trow + (uint32_t)c0, np, v);
@@ -556,32 +604,19 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
         }
         __syncthreads();
         // A <- z_c: messages of this channel for every electron (K = Zd)
-        for (int q = tid; q < TM * (Zd / 8); q += NT) {
-          const int e = q % TM, z8 = (q / TM) * 8;
+        for (int q = tid; q < rowsN * (Zd / 8); q += NT) {
+          const int e = q % rowsN, z8 = (q / rowsN) * 8;
+          const int w = e / N, i = e % N;
+          const int* ent = smsg + (c * N + i) * (L.E + 1);
           float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-          if (e < rowsN) {
-            const int w = e / N, i = e % N;
-            if (c < 2) {
-              const bool si = i < s.n_up;
-              for (int jn = 0; jn < N; ++jn) {
-                if (jn == i || (((jn < s.n_up) == si) != (c == 0))) continue;
-                const int p = i < jn ? pn_pair_index(i, jn, N) : pn_pair_index(jn, i, N);
-                const float* wr = swv + (w * cnt + s.ch_pos[p]) * LH + z8;
-                const float* hr = sh + (w * N + jn) * LH + z8;
-                const float4 w0 = *(const float4*)wr, w1 = *(const float4*)(wr + 4);
-                const float4 h0 = *(const float4*)hr, h1 = *(const float4*)(hr + 4);
-                acc[0] += w0.x * h0.x; acc[1] += w0.y * h0.y; acc[2] += w0.z * h0.z; acc[3] += w0.w * h0.w;
-                acc[4] += w1.x * h1.x; acc[5] += w1.y * h1.y; acc[6] += w1.z * h1.z; acc[7] += w1.w * h1.w;
-              }
-            } else {
-              for (int I = 0; I < s.M; ++I) {
-                const float* wr = swv + (w * cnt + s.ch_pos[s.Pee + i * s.M + I]) * LH + z8;
-                const float4 w0 = *(const float4*)wr, w1 = *(const float4*)(wr + 4);
-                const float* y = net.p + o.Y + I * Zd + z8;
-                acc[0] += w0.x * y[0]; acc[1] += w0.y * y[1]; acc[2] += w0.z * y[2]; acc[3] += w0.w * y[3];
-                acc[4] += w1.x * y[4]; acc[5] += w1.y * y[5]; acc[6] += w1.z * y[6]; acc[7] += w1.w * y[7];
-              }
-            }
+          for (int u = 1; u <= ent[0]; ++u) {
+            const int k = ent[u] >> 16, src = ent[u] & 0xFFFF;
+            const float* wr = swv + (w * cnt + k) * LH + z8;
+            const float* hr = c < 2 ? sh + (w * N + src) * LH + z8 : sY + src * Zd + z8;
+            const float4 w0 = *(const float4*)wr, w1 = *(const float4*)(wr + 4);
+            const float4 h0 = *(const float4*)hr, h1 = *(const float4*)(hr + 4);
+            acc[0] += w0.x * h0.x; acc[1] += w0.y * h0.y; acc[2] += w0.z * h0.z; acc[3] += w0.w * h0.w;
+            acc[4] += w1.x * h1.x; acc[5] += w1.y * h1.y; acc[6] += w1.z * h1.z; acc[7] += w1.w * h1.w;
           }
           put3x8(sA, L.a_bytes, e, z8, Zd, acc);
         }
@@ -590,6 +625,7 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
         g_started = true;
       }
       // x += accumulated update + receiving biases
+      if (quad * 32 < rowsN)
       for (int c0 = sub * 8; c0 < D; c0 += WPQ * 8) {
         float v[8];
         tmem_ld8x3(trow + col_g + (uint32_t)c0, (uint32_t)D, v);
@@ -612,8 +648,8 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
     }
     if (stop) break;
     // ---- backflow head kappa: three maps on every electron row
-    for (int q = tid; q < TM * (D / 8); q += NT) {
-      const int row = q % TM, k8 = (q / TM) * 8;
+    for (int q = tid; q < rowsN * (D / 8); q += NT) {
+      const int row = q % rowsN, k8 = (q / rowsN) * 8;
       float v[8];
       const float4 p0 = *(const float4*)(sx + row * LX + k8), p1 = *(const float4*)(sx + row * LX + k8 + 4);
       v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w; v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
@@ -622,16 +658,18 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
     fence_sync();
     for (int layer = 0; layer < 2; ++layer) {
       const uint32_t np = gemm(0, false);
+      if (quad * 32 < rowsN)
       for (int c0 = sub * 8; c0 < D; c0 += WPQ * 8) {
         float v[8];
         tmem_ld8x3(trow + (uint32_t)c0, np, v);
         const float* kb = net.p + o.kb[layer] + c0;
-        for (int jj = 0; jj < 8; ++jj) v[jj] = arow < rowsN ? sspf(v[jj] + kb[jj]) : 0.f;
+        for (int jj = 0; jj < 8; ++jj) v[jj] = sspf(v[jj] + kb[jj]);
         put3x8(sA, L.a_bytes, arow, c0, D, v);
       }
       fence_sync();
     }
     uint32_t np = gemm(0, false);
+    if (quad * 32 < rowsN)
     for (int c0 = sub * 8; c0 < no; c0 += WPQ * 8) {
       float v[8];
       tmem_ld8x3(trow + (uint32_t)c0, np, v);
@@ -640,11 +678,10 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
     }
     __syncthreads();
     // ---- Jastrow head eta on the electron sums (rows = walkers)
-    for (int q = tid; q < TM * (D / 8); q += NT) {
-      const int w = q % TM, d8 = (q / TM) * 8;
+    for (int q = tid; q < WTt * (D / 8); q += NT) {
+      const int w = q % WTt, d8 = (q / WTt) * 8;
       float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (w < WTt)
-        for (int i = 0; i < N; ++i) {
+      for (int i = 0; i < N; ++i) {
           const float4 p0 = *(const float4*)(sx + (w * N + i) * LX + d8), p1 = *(const float4*)(sx + (w * N + i) * LX + d8 + 4);
           acc[0] += p0.x; acc[1] += p0.y; acc[2] += p0.z; acc[3] += p0.w;
           acc[4] += p1.x; acc[5] += p1.y; acc[6] += p1.z; acc[7] += p1.w;
@@ -654,17 +691,18 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
     fence_sync();
     for (int layer = 0; layer < 2; ++layer) {
       const uint32_t npl = gemm(0, false);
+      if (quad * 32 < WTt)
       for (int c0 = sub * 8; c0 < D; c0 += WPQ * 8) {
         float v[8];
         tmem_ld8x3(trow + (uint32_t)c0, npl, v);
         const float* eb = net.p + o.eb[layer] + c0;
-        for (int jj = 0; jj < 8; ++jj) v[jj] = arow < WTt ? sspf(v[jj] + eb[jj]) : 0.f;
+        for (int jj = 0; jj < 8; ++jj) v[jj] = sspf(v[jj] + eb[jj]);
         put3x8(sA, L.a_bytes, arow, c0, D, v);
       }
       fence_sync();
     }
     np = gemm(0, false);
-    if (sub == 0) {
+    if (sub == 0 && quad * 32 < WTt) {
       float v[8];
       tmem_ld8x3(trow, np, v);
       if (arow < WTt) sJ[arow] = v[0] + net.p[o.eb[2]];
@@ -686,23 +724,25 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
           }
         det_scaled(A, ns, &mant, &ex);
       }
-      sdet[2 * q] = mant;
-      sdet[2 * q + 1] = (double)ex;
+      sdet[q] = mant;
+      sdex[q] = ex;
     }
     __syncthreads();
     // ---- ln|psi'| = gamma + J + ln|sum_p c_p det_up,p det_dn,p| (float64
     // sum of the determinant products scaled by the largest power of two)
     // and the accept test
     for (int w = tid; w < WTt; w += NT) {
-      const double* dw = sdet + (size_t)w * nd * 4;
+      const double* dm = sdet + (size_t)w * nd * 2;
+      const int* de = sdex + (size_t)w * nd * 2;
       int emax = INT_MIN;
       for (int p = 0; p < nd; ++p)
-        if (s.ci[p] != 0.0 && dw[4 * p] * dw[4 * p + 2] != 0.0) emax = max(emax, (int)(dw[4 * p + 1] + dw[4 * p + 3]));
+        if (s.ci[p] != 0.0 && dm[2 * p] != 0.0 && dm[2 * p + 1] != 0.0) emax = max(emax, de[2 * p] + de[2 * p + 1]);
       double S = 0;
       if (emax != INT_MIN)
         for (int p = 0; p < nd; ++p) {
-          const double pr = dw[4 * p] * dw[4 * p + 2];
-          if (pr != 0.0) S += s.ci[p] * ldexp(pr, (int)(dw[4 * p + 1] + dw[4 * p + 3]) - emax);
+          const int sh = de[2 * p] + de[2 * p + 1] - emax;  // <= 0
+          if (sh > -1022 && dm[2 * p] != 0.0 && dm[2 * p + 1] != 0.0)
+            S += s.ci[p] * (dm[2 * p] * dm[2 * p + 1]) * __longlong_as_double((long long)(1023 + sh) << 52);
         }
       const double m = emax == INT_MIN ? -INFINITY : (double)emax * 0.69314718055994530942;
       float gam = 0.f;
