@@ -317,28 +317,55 @@ __global__ void k_filter_bwd(DevSys s, DevNet<R> net, int n, const R* __restrict
 
 // ------------------------------------------------------------ weight grads
 // part[split][ka][nb] = sum over this split's rows r of A[r][ka] * B[r][nb];
-// A == nullptr means a column of ones (bias gradient, Ka = 1).  With a pair
-// map, logical row r is walker r / cnt, pair map[r % cnt] (the pairs of one
-// filter channel), i.e. storage row (r / cnt) * P + map[r % cnt].  Each block
-// sums its rows in R, then writes one float64 partial tile (32 x 32).
+// Weight gradients grad[block] += sum_rows A^T B, many parameter blocks per
+// launch.  A == nullptr means a column of ones (bias gradient, Ka = 1).
+// With a pair map, logical row r is walker r / cnt, pair map[r % cnt] (the
+// pairs of one filter channel), i.e. storage row (r / cnt) * P + map[r % cnt].
+// Rows per block are at most about 256; each block sums its rows of one
+// 32 x 32 tile in R and writes a float64 partial; the last block of a tile
+// to finish (counted with an atomic) adds the partials of all blocks in
+// split order and updates the gradient, so the result does not depend on
+// block scheduling.  rows_per_c > 0 splits the K rows over three parameter
+// blocks stride_c apart (stacked receiving maps).
+constexpr int kWgMaxJobs = 24;
+constexpr int kWgMaxCtr = 4096;  // 32 x 32 tiles in one group
 template <typename R>
-__global__ void k_wgrad(const R* __restrict__ A, int lda, const R* __restrict__ B, int ldb, int rows, int Ka, int Nb,
-                        int rows_per_split, const int* __restrict__ map, int cnt, int P, double* __restrict__ part) {
+struct WgJob {
+  const R* A;
+  const R* B;
+  const int* map;
+  int64_t part0, base, stride_c;
+  int lda, ldb, rows, Ka, Nb, cnt, rps, nsplit, tn, tk, blk0, ctr0, rows_per_c;
+};
+template <typename R>
+struct WgGroup {
+  int n, P;
+  WgJob<R> j[kWgMaxJobs];
+};
+
+template <typename R>
+__global__ void k_wgrad(const __grid_constant__ WgGroup<R> G, double* __restrict__ part, unsigned* __restrict__ ctr, double* __restrict__ grad) {
   __shared__ R As[32][33];
   __shared__ R Bs[32][33];
+  __shared__ bool last;
+  int ji = 0;
+  while (ji + 1 < G.n && (int)blockIdx.x >= G.j[ji + 1].blk0) ++ji;
+  const WgJob<R>& J = G.j[ji];
+  const int local = (int)blockIdx.x - J.blk0;
+  const int ntile = J.tn * J.tk, split = local / ntile, tile = local % ntile;
+  const int k0 = (tile / J.tn) * 32, n0 = (tile % J.tn) * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
-  const int r_begin = blockIdx.z * rows_per_split;
-  const int r_end = min(rows, r_begin + rows_per_split);
+  const int r_begin = split * J.rps;
+  const int r_end = min(J.rows, r_begin + J.rps);
   R acc[4] = {0, 0, 0, 0};
   for (int r0 = r_begin; r0 < r_end; r0 += 32) {
     for (int q = ty; q < 32; q += 8) {
       const int r = r0 + q;
       const bool ok = r < r_end;
       size_t row = r;
-      if (ok && map) row = (size_t)(r / cnt) * P + map[r % cnt];
-      As[q][tx] = (ok && k0 + tx < Ka) ? (A ? A[row * lda + k0 + tx] : R(1)) : R(0);
-      Bs[q][tx] = (ok && n0 + tx < Nb) ? B[row * ldb + n0 + tx] : R(0);
+      if (ok && J.map) row = (size_t)(r / J.cnt) * G.P + J.map[r % J.cnt];
+      As[q][tx] = (ok && k0 + tx < J.Ka) ? (J.A ? J.A[row * J.lda + k0 + tx] : R(1)) : R(0);
+      Bs[q][tx] = (ok && n0 + tx < J.Nb) ? J.B[row * J.ldb + n0 + tx] : R(0);
     }
     __syncthreads();
 #pragma unroll 8
@@ -349,29 +376,30 @@ __global__ void k_wgrad(const R* __restrict__ A, int lda, const R* __restrict__ 
     }
     __syncthreads();
   }
+  double* pj = part + J.part0;
   for (int e = 0; e < 4; ++e) {
     const int k = k0 + ty + 8 * e, nn = n0 + tx;
-    if (k < Ka && nn < Nb) part[((size_t)blockIdx.z * Ka + k) * Nb + nn] = (double)acc[e];
+    if (k < J.Ka && nn < J.Nb) pj[((size_t)split * J.Ka + k) * J.Nb + nn] = (double)acc[e];
   }
-}
-
-// grad[dst(k, n)] += sum_split part[split][k][n].  dst = base + k*Nb + n, or
-// for the stacked receiving maps the (channel, z) row split into three.
-__global__ void k_reduce_part(const double* __restrict__ part, int nsplit, int Ka, int Nb, double* __restrict__ grad,
-                              int64_t base, int64_t stride_c, int rows_per_c) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (size_t)Ka * Nb) return;
-  double acc = 0;
-  for (int sp = 0; sp < nsplit; ++sp) acc += part[(size_t)sp * Ka * Nb + i];
-  const int k = i / Nb, n = i % Nb;
-  int64_t dst;
-  if (rows_per_c > 0) {
-    const int c = k / rows_per_c, kk = k % rows_per_c;
-    dst = base + c * stride_c + (int64_t)kk * Nb + n;
-  } else {
-    dst = base + (int64_t)k * Nb + n;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&ctr[J.ctr0 + tile], 1u) == (unsigned)(J.nsplit - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int e = 0; e < 4; ++e) {
+    const int k = k0 + ty + 8 * e, nn = n0 + tx;
+    if (k >= J.Ka || nn >= J.Nb) continue;
+    double sum = 0;
+    for (int sp = 0; sp < J.nsplit; ++sp) sum += __ldcg(pj + ((size_t)sp * J.Ka + k) * J.Nb + nn);
+    int64_t dst;
+    if (J.rows_per_c > 0)
+      dst = J.base + (int64_t)(k / J.rows_per_c) * J.stride_c + (int64_t)(k % J.rows_per_c) * J.Nb + nn;
+    else
+      dst = J.base + (int64_t)k * J.Nb + nn;
+    grad[dst] += sum;
   }
-  grad[dst] += acc;
+  if (threadIdx.x == 0) ctr[J.ctr0 + tile] = 0u;  // ready for the next launch
 }
 
 __global__ void k_add_to(double* __restrict__ grad, int64_t off, const double* __restrict__ v, int n) {
@@ -440,6 +468,7 @@ struct Tape {
   R *dX, *dX2, *dH, *dZ, *dw, *dAh, *Sh, *dYr, *dF, *dJ, *dA, *dB, *dXs, *dAs, *dBs;
   double* part;
   size_t part_elems;
+  unsigned* ctr;  // per-tile completion counters of k_wgrad (kept at zero between launches)
   double* bias_tmp;
   char* end;  // one past the last carved byte
 };
@@ -501,35 +530,79 @@ Tape<R> carve_tape(const DevSys& s, int Wb, void* base, size_t part_elems) {
   t.dBs = (R*)take(W * D * r);
   t.part = (double*)take(part_elems * 8);
   t.part_elems = part_elems;
+  t.ctr = (unsigned*)take(kWgMaxCtr * 4);
   t.bias_tmp = nullptr;
   t.end = p;
   return t;
 }
 
-// grad += sum_rows A^T B (or column sums of B when A is null) into the
-// parameter block at `base`; rows_per_c > 0 splits the K rows over three
-// parameter blocks stride_c apart (stacked receiving maps).
+// Collects the weight-gradient blocks of one dependency group (their A and
+// B stay valid until flush) and runs them as one k_wgrad launch.
 template <typename R>
-int wgrad(Tape<R>& t, const R* A, int lda, const R* B, int ldb, int rows, int Ka, int Nb, const DevSys& s, int ch,
-          double* grad, int64_t base, int64_t stride_c, int rows_per_c, cudaStream_t st) {
-  const int* map = nullptr;
-  int cnt = 0;
-  if (ch >= 0) {
-    // rows of one filter channel only: Wn * (pairs of that channel)
-    cnt = s.ch_off[ch + 1] - s.ch_off[ch];
-    map = s.ch_pairs + s.ch_off[ch];
-    rows = (rows / s.Ppair) * cnt;
+struct WgBatch {
+  const DevSys* s;
+  Tape<R>* t;
+  double* grad;
+  WgGroup<R> G;
+  int64_t rows_total[kWgMaxJobs];
+  void reset() { G.n = 0; G.P = s->Ppair; }
+  // grad += sum_rows A^T B (or column sums of B when A is null) into the
+  // parameter block at `base`; ch >= 0 restricts the rows to the pairs of
+  // filter channel ch (rows then count walkers x pairs)
+  int add(const R* A, int lda, const R* B, int ldb, int rows, int Ka, int Nb, int ch, int64_t base,
+          int64_t stride_c, int rows_per_c) {
+    const int* map = nullptr;
+    int cnt = 0;
+    if (ch >= 0) {
+      cnt = s->ch_off[ch + 1] - s->ch_off[ch];
+      map = s->ch_pairs + s->ch_off[ch];
+      rows = (rows / s->Ppair) * cnt;
+    }
+    if (rows <= 0) return PN_OK;
+    if (G.n == kWgMaxJobs) {
+      pn_set_error("internal: weight-gradient group full");
+      return PN_EINVAL;
+    }
+    WgJob<R>& J = G.j[G.n++];
+    J.A = A; J.B = B; J.map = map; J.cnt = cnt;
+    J.lda = lda; J.ldb = ldb; J.rows = rows; J.Ka = Ka; J.Nb = Nb;
+    J.base = base; J.stride_c = stride_c; J.rows_per_c = rows_per_c;
+    J.tn = (Nb + 31) / 32;
+    J.tk = (Ka + 31) / 32;
+    return PN_OK;
   }
-  if (rows <= 0) return PN_OK;
-  const size_t tile = (size_t)Ka * Nb;
-  constexpr int kRowsPerBlock = 256;
-  int nsplit = std::max(1, std::min<int>((rows + kRowsPerBlock - 1) / kRowsPerBlock, (int)(t.part_elems / tile)));
-  const int rps = (rows + nsplit - 1) / nsplit;
-  dim3 grid((Nb + 31) / 32, (Ka + 31) / 32, nsplit);
-  PN_LAUNCH("k_wgrad", st, k_wgrad<R><<<grid, 256, 0, st>>>(A, lda, B, ldb, rows, Ka, Nb, rps, map, cnt, s.Ppair, t.part));
-  PN_LAUNCH("k_reduce_part", st, k_reduce_part<<<nblk(tile, 256), 256, 0, st>>>(t.part, nsplit, Ka, Nb, grad, base, stride_c, rows_per_c));
-  return PN_OK;
-}
+  int flush(cudaStream_t st) {
+    if (G.n == 0) return PN_OK;
+    constexpr int kRowsPerBlock = 256;
+    // splits of about 256 rows, fewer if the partial buffer would overflow
+    size_t need = 0;
+    for (int i = 0; i < G.n; ++i)
+      need += (size_t)G.j[i].Ka * G.j[i].Nb * ((G.j[i].rows + kRowsPerBlock - 1) / kRowsPerBlock);
+    const double scale = need > t->part_elems ? (double)t->part_elems / (double)need : 1.0;
+    int64_t part0 = 0;
+    int blk = 0, ctr0 = 0;
+    for (int i = 0; i < G.n; ++i) {
+      WgJob<R>& J = G.j[i];
+      const int want = (J.rows + kRowsPerBlock - 1) / kRowsPerBlock;
+      J.nsplit = std::max(1, std::min(want, (int)(want * scale)));
+      J.rps = (J.rows + J.nsplit - 1) / J.nsplit;
+      J.nsplit = (J.rows + J.rps - 1) / J.rps;
+      J.part0 = part0;
+      J.blk0 = blk;
+      J.ctr0 = ctr0;
+      part0 += (int64_t)J.nsplit * J.Ka * J.Nb;
+      blk += J.nsplit * J.tn * J.tk;
+      ctr0 += J.tn * J.tk;
+    }
+    if ((size_t)part0 > t->part_elems || ctr0 > kWgMaxCtr) {
+      pn_set_error("internal: weight-gradient partials exceed their buffer");
+      return PN_EINVAL;
+    }
+    PN_LAUNCH("k_wgrad", st, k_wgrad<R><<<blk, 256, 0, st>>>(G, t->part, t->ctr, grad));
+    reset();
+    return PN_OK;
+  }
+};
 
 template <typename R>
 int linear_bt(const R* X, int ldx, const R* W, int ldw, R* Y, int ldy, int rows, int Kd, int Nout, int acc,
@@ -584,31 +657,37 @@ static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const d
   PN_LAUNCH("k_ssp_copy", st, k_ssp_copy<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.eA2, t.eS2, (size_t)Wn * D));
 
   // ---------------- backward
+  WgBatch<R> wg;
+  wg.s = &s;
+  wg.t = &t;
+  wg.grad = grad;
+  wg.reset();
   PN_LAUNCH("k_slater_bwd", st, k_slater_bwd<R><<<nblk(Wn, 32), 32, 0, st>>>(s, t.phi, t.F, u, Wn, t.dF, t.dJ));
   // kappa head
-  if (int e = wgrad<R>(t, t.kS2, D, t.dF, no, rows, D, no, s, -1, grad, o.kW[2], 0, 0, st)) return e;
-  if (int e = wgrad<R>(t, nullptr, 0, t.dF, no, rows, 1, no, s, -1, grad, o.kb[2], 0, 0, st)) return e;
+  if (int e = wg.add(t.kS2, D, t.dF, no, rows, D, no, -1, o.kW[2], 0, 0)) return e;
+  if (int e = wg.add(nullptr, 0, t.dF, no, rows, 1, no, -1, o.kb[2], 0, 0)) return e;
   if (int e = linear_bt<R>(t.dF, no, net.p + o.kW[2], no, t.dA, D, rows, no, D, 0, st)) return e;
   PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dA, t.kA2, t.dA, WND));
-  if (int e = wgrad<R>(t, t.kS1, D, t.dA, D, rows, D, D, s, -1, grad, o.kW[1], 0, 0, st)) return e;
-  if (int e = wgrad<R>(t, nullptr, 0, t.dA, D, rows, 1, D, s, -1, grad, o.kb[1], 0, 0, st)) return e;
+  if (int e = wg.add(t.kS1, D, t.dA, D, rows, D, D, -1, o.kW[1], 0, 0)) return e;
+  if (int e = wg.add(nullptr, 0, t.dA, D, rows, 1, D, -1, o.kb[1], 0, 0)) return e;
   if (int e = linear_bt<R>(t.dA, D, net.p + o.kW[1], D, t.dB, D, rows, D, D, 0, st)) return e;
   PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dB, t.kA1, t.dB, WND));
-  if (int e = wgrad<R>(t, XL, D, t.dB, D, rows, D, D, s, -1, grad, o.kW[0], 0, 0, st)) return e;
-  if (int e = wgrad<R>(t, nullptr, 0, t.dB, D, rows, 1, D, s, -1, grad, o.kb[0], 0, 0, st)) return e;
+  if (int e = wg.add(XL, D, t.dB, D, rows, D, D, -1, o.kW[0], 0, 0)) return e;
+  if (int e = wg.add(nullptr, 0, t.dB, D, rows, 1, D, -1, o.kb[0], 0, 0)) return e;
   if (int e = linear_bt<R>(t.dB, D, net.p + o.kW[0], D, t.dX, D, rows, D, D, 0, st)) return e;
   // eta head (J = eta(sum_i x_i); dJ/d out = u)
-  if (int e = wgrad<R>(t, t.eS2, D, t.dJ, 1, Wn, D, 1, s, -1, grad, o.eW[2], 0, 0, st)) return e;
-  if (int e = wgrad<R>(t, nullptr, 0, t.dJ, 1, Wn, 1, 1, s, -1, grad, o.eb[2], 0, 0, st)) return e;
+  if (int e = wg.add(t.eS2, D, t.dJ, 1, Wn, D, 1, -1, o.eW[2], 0, 0)) return e;
+  if (int e = wg.add(nullptr, 0, t.dJ, 1, Wn, 1, 1, -1, o.eb[2], 0, 0)) return e;
   PN_LAUNCH("k_outer_row", st, k_outer_row<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dJ, net.p + o.eW[2], t.dAs, Wn, D));
   PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dAs, t.eA2, t.dAs, (size_t)Wn * D));
-  if (int e = wgrad<R>(t, t.eS1, D, t.dAs, D, Wn, D, D, s, -1, grad, o.eW[1], 0, 0, st)) return e;
-  if (int e = wgrad<R>(t, nullptr, 0, t.dAs, D, Wn, 1, D, s, -1, grad, o.eb[1], 0, 0, st)) return e;
+  if (int e = wg.add(t.eS1, D, t.dAs, D, Wn, D, D, -1, o.eW[1], 0, 0)) return e;
+  if (int e = wg.add(nullptr, 0, t.dAs, D, Wn, 1, D, -1, o.eb[1], 0, 0)) return e;
   if (int e = linear_bt<R>(t.dAs, D, net.p + o.eW[1], D, t.dBs, D, Wn, D, D, 0, st)) return e;
   PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dBs, t.eA1, t.dBs, (size_t)Wn * D));
-  if (int e = wgrad<R>(t, t.Xs, D, t.dBs, D, Wn, D, D, s, -1, grad, o.eW[0], 0, 0, st)) return e;
-  if (int e = wgrad<R>(t, nullptr, 0, t.dBs, D, Wn, 1, D, s, -1, grad, o.eb[0], 0, 0, st)) return e;
+  if (int e = wg.add(t.Xs, D, t.dBs, D, Wn, D, D, -1, o.eW[0], 0, 0)) return e;
+  if (int e = wg.add(nullptr, 0, t.dBs, D, Wn, 1, D, -1, o.eb[0], 0, 0)) return e;
   if (int e = linear_bt<R>(t.dBs, D, net.p + o.eW[0], D, t.dXs, D, Wn, D, D, 0, st)) return e;
+  if (int e = wg.flush(st)) return e;  // both heads' weight gradients
   PN_LAUNCH("k_bcast_add", st, k_bcast_add<R><<<nblk(WND, 256), 256, 0, st>>>(t.dX, t.dXs, Wn, N, D));
   // interaction layers, last to first; t.dX holds d/dX^(n+1)
   for (int n = L - 1; n >= 0; --n) {
@@ -618,34 +697,34 @@ static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const d
     R* Ahn = t.Ah + (size_t)n * Wn * P * Hw;
     R* wn = t.wv + (size_t)n * Wn * P * Zd;
     // receiving maps: X^(n+1) = X^(n) + [z_same z_anti z_nuc] Gcat + sum of biases
-    if (int e = wgrad<R>(t, Zn, 3 * Zd, t.dX, D, rows, 3 * Zd, D, s, -1, grad, o.GW[n][0], o.GW[n][1] - o.GW[n][0], Zd,
-                         st))
+    if (int e = wg.add(Zn, 3 * Zd, t.dX, D, rows, 3 * Zd, D, -1, o.GW[n][0], o.GW[n][1] - o.GW[n][0], Zd))
       return e;
     for (int c = 0; c < 3; ++c)
-      if (int e = wgrad<R>(t, nullptr, 0, t.dX, D, rows, 1, D, s, -1, grad, o.Gb[n][c], 0, 0, st)) return e;
+      if (int e = wg.add(nullptr, 0, t.dX, D, rows, 1, D, -1, o.Gb[n][c], 0, 0)) return e;
     if (int e = linear_bt<R>(t.dX, D, net.Gcat + (size_t)n * 3 * Zd * D, D, t.dZ, 3 * Zd, rows, D, 3 * Zd, 0, st))
       return e;
     // messages
     PN_LAUNCH("k_msg_bwd_w", st, k_msg_bwd_w<R><<<nblk((size_t)Wn * P * Zd, 256), 256, 0, st>>>(s, net.p + o.Y, Hn, t.dZ, Wn, t.dw));
     PN_LAUNCH("k_msg_bwd_h", st, k_msg_bwd_h<R><<<nblk((size_t)rows * Zd, 256), 256, 0, st>>>(s, wn, t.dZ, Wn, t.dH, t.dYr));
-    if (int e = wgrad<R>(t, nullptr, 0, t.dYr, s.M * Zd, rows, 1, s.M * Zd, s, -1, grad, o.Y, 0, 0, st)) return e;
+    if (int e = wg.add(nullptr, 0, t.dYr, s.M * Zd, rows, 1, s.M * Zd, -1, o.Y, 0, 0)) return e;
     // filters, per channel
     PN_LAUNCH("k_filter_bwd", st, k_filter_bwd<R><<<nblk((size_t)Wn * P, 8), 256, 0, st>>>(s, net, n, Ahn, t.dw, Wn, t.dAh, t.Sh));
     for (int c = 0; c < 3; ++c) {
-      if (int e = wgrad<R>(t, t.Sh, Hw, t.dw, Zd, Wn * P, Hw, Zd, s, c, grad, o.W2[n][c], 0, 0, st)) return e;
-      if (int e = wgrad<R>(t, nullptr, 0, t.dw, Zd, Wn * P, 1, Zd, s, c, grad, o.b2[n][c], 0, 0, st)) return e;
-      if (int e = wgrad<R>(t, t.ef, 3 * K, t.dAh, Hw, Wn * P, K, Hw, s, c, grad, o.W1[n][c], 0, 0, st)) return e;
-      if (int e = wgrad<R>(t, nullptr, 0, t.dAh, Hw, Wn * P, 1, Hw, s, c, grad, o.b1[n][c], 0, 0, st)) return e;
+      if (int e = wg.add(t.Sh, Hw, t.dw, Zd, Wn * P, Hw, Zd, c, o.W2[n][c], 0, 0)) return e;
+      if (int e = wg.add(nullptr, 0, t.dw, Zd, Wn * P, 1, Zd, c, o.b2[n][c], 0, 0)) return e;
+      if (int e = wg.add(t.ef, 3 * K, t.dAh, Hw, Wn * P, K, Hw, c, o.W1[n][c], 0, 0)) return e;
+      if (int e = wg.add(nullptr, 0, t.dAh, Hw, Wn * P, 1, Hw, c, o.b1[n][c], 0, 0)) return e;
     }
     // input map h
-    if (int e = wgrad<R>(t, Xn, D, t.dH, Zd, rows, D, Zd, s, -1, grad, o.hW[n], 0, 0, st)) return e;
-    if (int e = wgrad<R>(t, nullptr, 0, t.dH, Zd, rows, 1, Zd, s, -1, grad, o.hb[n], 0, 0, st)) return e;
+    if (int e = wg.add(Xn, D, t.dH, Zd, rows, D, Zd, -1, o.hW[n], 0, 0)) return e;
+    if (int e = wg.add(nullptr, 0, t.dH, Zd, rows, 1, Zd, -1, o.hb[n], 0, 0)) return e;
+    if (int e = wg.flush(st)) return e;  // this layer's weight gradients, before dX changes
     // d/dX^(n) = d/dX^(n+1) + dH Wh^T
     if (int e = linear_bt<R>(t.dH, Zd, net.p + o.hW[n], Zd, t.dX, D, rows, Zd, D, 1, st)) return e;
   }
   // shared electron embedding
-  if (int e = wgrad<R>(t, nullptr, 0, t.dX, D, rows, 1, D, s, -1, grad, o.x0, 0, 0, st)) return e;
-  return PN_OK;
+  if (int e = wg.add(nullptr, 0, t.dX, D, rows, 1, D, -1, o.x0, 0, 0)) return e;
+  return wg.flush(st);
 }
 
 template <typename R>
@@ -659,7 +738,7 @@ static int grad_impl(pn_system_s* sys, const double* r, int W, const double* cot
   size_t maxKN = std::max<size_t>({(size_t)s.D * s.D, (size_t)3 * s.Zd * s.D, (size_t)s.K * s.Hw,
                                    (size_t)s.Hw * s.Zd, (size_t)s.D * s.n_orb, (size_t)s.M * s.Zd, 1});
   const size_t part_elems = maxKN * 256;
-  const size_t fixed = part_elems * 8 + 4096 * 64;
+  const size_t fixed = part_elems * 8 + kWgMaxCtr * 4 + 4096 * 64;
   // default: room for one workspace chunk (at least 256 walkers)
   if (budget == 0) budget = fixed + per * (size_t)std::min(W, std::max(sys->Wc, 256)) + 65536;
   if (budget <= fixed + per) {
@@ -686,6 +765,7 @@ static int grad_impl(pn_system_s* sys, const double* r, int W, const double* cot
                  sys->tape_bytes);
     return PN_EINVAL;
   }
+  PN_CUDA(cudaMemsetAsync(t.ctr, 0, kWgMaxCtr * 4, st));
   const bool rdev = pn_is_device_ptr(r), udev = pn_is_device_ptr(cot), gdev = pn_is_device_ptr(grad);
   double* gd = grad;
   if (!gdev) {
