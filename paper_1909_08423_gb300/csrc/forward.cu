@@ -7,6 +7,8 @@
 // electron k, 3N + 1 Laplacian (sum over all 3N second derivatives).
 #include <math.h>
 
+#include <algorithm>
+
 #include "ansatz_dev.cuh"
 #include "kernels.cuh"
 #include "pn_internal.cuh"
@@ -210,6 +212,84 @@ __global__ void __launch_bounds__(256) k_linear(const R* __restrict__ X, int ldx
   }
 }
 
+// Float32 Y (+)= X W + b (bias on value rows only), 128 x 64 output tiles,
+// 8 x 4 outputs per thread, float4 loads from global and shared memory.
+// Requires ldx, ldw, ldy, Kd and Nout multiples of 4 and 16-byte aligned X,
+// W and Y (the caller checks).
+__global__ void __launch_bounds__(256) k_linear_v4(const float* __restrict__ X, int ldx, const float* __restrict__ W,
+                                                   int ldw, const float* __restrict__ bias, float* __restrict__ Y,
+                                                   int ldy, int rows, int Kd, int Nout, int T, int accumulate) {
+  __shared__ __align__(16) float As[16][128 + 4];
+  __shared__ __align__(16) float Bs[16][64];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int row0 = blockIdx.y * 128, col0 = blockIdx.x * 64;
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < Kd; k0 += 16) {
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      const int e = tid + l * 256;
+      const int rr = e >> 2, k4 = (e & 3) * 4;
+      const int gr = row0 + rr, gk = k0 + k4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gr < rows && gk < Kd) v = *(const float4*)(X + (size_t)gr * ldx + gk);
+      As[k4][rr] = v.x;
+      As[k4 + 1][rr] = v.y;
+      As[k4 + 2][rr] = v.z;
+      As[k4 + 3][rr] = v.w;
+    }
+    {
+      const int kb = tid >> 4, c4 = (tid & 15) * 4;
+      const int gk = k0 + kb, gc = col0 + c4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gk < Kd && gc < Nout) v = *(const float4*)(W + (size_t)gk * ldw + gc);
+      *(float4*)&Bs[kb][c4] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const float4 a0 = *(const float4*)&As[kk][ty * 8], a1 = *(const float4*)&As[kk][ty * 8 + 4];
+      const float4 b = *(const float4*)&Bs[kk][tx * 4];
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  const int gc = col0 + tx * 4;
+  if (gc >= Nout) return;
+  float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (bias) bv = make_float4(bias[gc], bias[gc + 1], bias[gc + 2], bias[gc + 3]);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gr = row0 + ty * 8 + i;
+    if (gr >= rows) break;
+    const bool val = (gr % T) == 0;
+    float4 v = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    if (val) {
+      v.x += bv.x;
+      v.y += bv.y;
+      v.z += bv.z;
+      v.w += bv.w;
+    }
+    float4* y = (float4*)(Y + (size_t)gr * ldy + gc);
+    if (accumulate) {
+      const float4 o = *y;
+      v.x += o.x;
+      v.y += o.y;
+      v.z += o.z;
+      v.w += o.w;
+    }
+    *y = v;
+  }
+}
+
 // x^(0): the shared electron embedding on value rows, zero derivatives.
 template <typename R>
 __global__ void k_init_x(const R* __restrict__ x0, R* __restrict__ X, size_t groups, int T, int D) {
@@ -224,73 +304,88 @@ __global__ void k_init_x(const R* __restrict__ x0, R* __restrict__ X, size_t gro
 // z_i^{same|anti} = sum_j w_ij * h_j, z_i^nuc = sum_I w_iI * Y_I with the
 // product rule through the jet.  Zb[w][i][t][c*Zd + z].
 template <typename R>
-__global__ void k_message(DevSys s, const R* __restrict__ Y, const double* __restrict__ geo, const R* __restrict__ wj,
-                          const R* __restrict__ H, int ldH, int Wn, int T, R* __restrict__ Zb, int ldZ) {
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int Zd = s.Zd, N = s.N;
-  if (idx >= (size_t)Wn * N * T * Zd) return;
-  const int z = idx % Zd;
-  size_t q = idx / Zd;
-  const int t = q % T;
-  q /= T;
-  const int i = q % N;
-  const int w = q / N;
-  const int lap = T - 1;
-  int tk = -1, ta = 0;
-  if (t > 0 && t < lap) { tk = (t - 1) / 3; ta = (t - 1) % 3; }
-  const bool si = i < s.n_up;
-  R zs = 0, za = 0, zn = 0;
-  const R* Hw_ = H + (size_t)w * N * T * ldH;
-  const double* gw = geo + (size_t)w * s.Ppair * 4;
-  const R* ww = wj + (size_t)w * s.Ppair * 3 * Zd;
-  for (int j = 0; j < N; ++j) {
-    if (j == i) continue;
+__global__ void __launch_bounds__(256) k_message(DevSys s, const R* __restrict__ Y, const double* __restrict__ geo,
+                                                 const R* __restrict__ wj, const R* __restrict__ H, int ldH, int Wn,
+                                                 int T, R* __restrict__ Zb, int ldZ) {
+  // one block per (walker, electron i); the geometry of i's partners
+  // (electrons j != i, then nuclei) is read once and kept in R as
+  // (d, 1/d, unit vector from the partner to i)
+  extern __shared__ __align__(16) unsigned char msg_smem[];
+  R* gsh = (R*)msg_smem;
+  const int Zd = s.Zd, N = s.N, M = s.M;
+  const int w = blockIdx.x / N, i = blockIdx.x % N;
+  const int npart = N - 1 + M;
+  for (int k = threadIdx.x; k < npart; k += blockDim.x) {
     int p;
-    double sgn;
-    if (i < j) { p = pn_pair_index(i, j, N); sgn = 1.0; }
-    else { p = pn_pair_index(j, i, N); sgn = -1.0; }
-    const double* g = gw + p * 4;
-    const R w0 = ww[(size_t)p * 3 * Zd + z];
-    const R* hj = Hw_ + (size_t)j * T * ldH;
-    const R h0 = hj[z];
-    R v;
-    if (t == 0) {
-      v = w0 * h0;
-    } else if (t < lap) {
-      const R w1 = ww[(size_t)p * 3 * Zd + Zd + z];
-      // unit vector u = (r_i - r_j)/d
-      const R u = (R)(sgn * g[1 + ta]);
-      const R dd = (tk == i) ? u : ((tk == j) ? -u : R(0));
-      v = w1 * dd * h0 + w0 * hj[(size_t)t * ldH + z];
+    double sgn = 1.0;
+    if (k < N - 1) {
+      const int j = k < i ? k : k + 1;
+      if (i < j) p = pn_pair_index(i, j, N);
+      else { p = pn_pair_index(j, i, N); sgn = -1.0; }
     } else {
-      const R w1 = ww[(size_t)p * 3 * Zd + Zd + z];
-      const R w2 = ww[(size_t)p * 3 * Zd + 2 * Zd + z];
-      const R d = (R)g[0];
-      R cross = 0;
-      for (int a = 0; a < 3; ++a) {
-        const R u = (R)(sgn * g[1 + a]);
-        cross += u * (hj[(size_t)(1 + 3 * i + a) * ldH + z] - hj[(size_t)(1 + 3 * j + a) * ldH + z]);
+      p = s.Pee + i * M + (k - (N - 1));
+    }
+    const double* g = geo + ((size_t)w * s.Ppair + p) * 4;
+    R* o = gsh + k * 5;
+    o[0] = (R)g[0];
+    o[1] = (R)(1.0 / g[0]);
+    o[2] = (R)(sgn * g[1]);
+    o[3] = (R)(sgn * g[2]);
+    o[4] = (R)(sgn * g[3]);
+  }
+  __syncthreads();
+  const int lap = T - 1;
+  const bool si = i < s.n_up;
+  const R* Hw_ = H + (size_t)w * N * T * ldH;
+  const R* ww = wj + (size_t)w * s.Ppair * 3 * Zd;
+  R* ob = Zb + (size_t)(w * N + i) * T * ldZ;
+  for (int q = threadIdx.x; q < T * Zd; q += blockDim.x) {
+    const int t = q / Zd, z = q % Zd;
+    int tk = -1, ta = 0;
+    if (t > 0 && t < lap) { tk = (t - 1) / 3; ta = (t - 1) % 3; }
+    R zs = 0, za = 0, zn = 0;
+    for (int k = 0; k < N - 1; ++k) {
+      const int j = k < i ? k : k + 1;
+      const int p = i < j ? pn_pair_index(i, j, N) : pn_pair_index(j, i, N);
+      const R* gk = gsh + k * 5;
+      const R w0 = ww[(size_t)p * 3 * Zd + z];
+      const R* hj = Hw_ + (size_t)j * T * ldH;
+      const R h0 = hj[z];
+      R v;
+      if (t == 0) {
+        v = w0 * h0;
+      } else if (t < lap) {
+        const R w1 = ww[(size_t)p * 3 * Zd + Zd + z];
+        const R u = gk[2 + ta];
+        const R dd = (tk == i) ? u : ((tk == j) ? -u : R(0));
+        v = w1 * dd * h0 + w0 * hj[(size_t)t * ldH + z];
+      } else {
+        const R w1 = ww[(size_t)p * 3 * Zd + Zd + z];
+        const R w2 = ww[(size_t)p * 3 * Zd + 2 * Zd + z];
+        R cross = 0;
+        for (int a = 0; a < 3; ++a)
+          cross += gk[2 + a] * (hj[(size_t)(1 + 3 * i + a) * ldH + z] - hj[(size_t)(1 + 3 * j + a) * ldH + z]);
+        v = (R(2) * w2 + R(4) * w1 * gk[1]) * h0 + w0 * hj[(size_t)lap * ldH + z] + R(2) * w1 * cross;
       }
-      v = (R(2) * w2 + R(4) * w1 / d) * h0 + w0 * hj[(size_t)lap * ldH + z] + R(2) * w1 * cross;
+      if ((j < s.n_up) == si) zs += v; else za += v;
     }
-    if ((j < s.n_up) == si) zs += v; else za += v;
-  }
-  for (int I = 0; I < s.M; ++I) {
-    const int p = s.Pee + i * s.M + I;
-    const double* g = gw + p * 4;
-    const R y = Y[I * Zd + z];
-    const R* wp = ww + (size_t)p * 3 * Zd;
-    if (t == 0) zn += wp[z] * y;
-    else if (t < lap) {
-      if (tk == i) zn += wp[Zd + z] * (R)g[1 + ta] * y;
-    } else {
-      zn += (wp[2 * Zd + z] + R(2) * wp[Zd + z] / (R)g[0]) * y;
+    for (int I = 0; I < M; ++I) {
+      const int p = s.Pee + i * M + I;
+      const R* gk = gsh + (N - 1 + I) * 5;
+      const R y = Y[I * Zd + z];
+      const R* wp = ww + (size_t)p * 3 * Zd;
+      if (t == 0) zn += wp[z] * y;
+      else if (t < lap) {
+        if (tk == i) zn += wp[Zd + z] * gk[2 + ta] * y;
+      } else {
+        zn += (wp[2 * Zd + z] + R(2) * wp[Zd + z] * gk[1]) * y;
+      }
     }
+    R* o = ob + (size_t)t * ldZ;
+    o[z] = zs;
+    o[Zd + z] = za;
+    o[2 * Zd + z] = zn;
   }
-  R* o = Zb + ((size_t)(w * N + i) * T + t) * ldZ;
-  o[z] = zs;
-  o[Zd + z] = za;
-  o[2 * Zd + z] = zn;
 }
 
 // ---------------------------------------------------- activation on a jet
@@ -572,6 +667,17 @@ int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw
       return pn_linear_tc((const float*)X, ldx, (const float*)W, ldw, (const float*)b, (float*)Y, ldy, rows, Kd, Nout,
                           T, acc, s->dev_err, st);
   }
+  if constexpr (sizeof(R) == 4) {
+    const bool v4 = ldx % 4 == 0 && ldw % 4 == 0 && ldy % 4 == 0 && Kd % 4 == 0 && Nout % 4 == 0 &&
+                    ((uintptr_t)X & 15) == 0 && ((uintptr_t)W & 15) == 0 && ((uintptr_t)Y & 15) == 0;
+    if (v4) {
+      dim3 grid((Nout + 63) / 64, (rows + 127) / 128);
+      PN_LAUNCH("k_linear", st,
+                k_linear_v4<<<grid, 256, 0, st>>>((const float*)X, ldx, (const float*)W, ldw, (const float*)b,
+                                                  (float*)Y, ldy, rows, Kd, Nout, T, acc));
+      return PN_OK;
+    }
+  }
   dim3 grid((Nout + 63) / 64, (rows + 63) / 64);
   PN_LAUNCH("k_linear", st, k_linear<R><<<grid, 256, 0, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, Kd, Nout, T, acc));
   return PN_OK;
@@ -598,8 +704,10 @@ int pn_network_layers(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn,
                              s.Zd, T, 0, st))
       return e;
     PN_LAUNCH("k_filter", st, k_filter<R><<<nblk((size_t)Wn * s.Ppair, FW), FW * 32, 0, st>>>(s, net, n, w.efeat, Wn, jet, w.wjet));
-    PN_LAUNCH("k_message", st, k_message<R><<<nblk((size_t)rows * s.Zd, 256), 256, 0, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H, w.ldH, Wn,
-                                                                  T, w.Zb, w.ldZ));
+    PN_LAUNCH("k_message", st,
+              k_message<R><<<(unsigned)((size_t)Wn * s.N), std::min(256, (T * s.Zd + 31) / 32 * 32),
+                             (size_t)(s.N - 1 + s.M) * 5 * sizeof(R), st>>>(
+                  s, net.p + net.off.Y, w.geo, w.wjet, w.H, w.ldH, Wn, T, w.Zb, w.ldZ));
     if (int e = pn_linear<R>(&s, PN_TC_LAYERS, w.Zb, w.ldZ, net.Gcat + (size_t)n * 3 * s.Zd * s.D, s.D, net.Gb + (size_t)n * s.D, w.X,
                              s.D, rows, 3 * s.Zd, s.D, T, 1, st))
       return e;
