@@ -93,13 +93,23 @@ __global__ void k_components(DevSys s, const double* __restrict__ phi, const R* 
 // ---------------------------------------------------------------- clipping
 // One block: bitonic sort of the batch in shared memory for the median,
 // mean absolute deviation, logarithmic clipping, then the loss weights.
+// The sort runs on order-preserving 64-bit integer keys of the doubles
+// (sign bit set for non-negatives, all bits flipped for negatives), so that
+// its compares stay off the float64 pipe; padding takes the largest key.
+__device__ inline unsigned long long clip_key(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ inline double clip_unkey(unsigned long long k) {
+  return __longlong_as_double((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k));
+}
 __global__ void k_clip(const double* __restrict__ E, int W, double q, double* __restrict__ out,
                        double* __restrict__ cot) {
-  extern __shared__ double sh[];
+  extern __shared__ unsigned long long skey[];
   __shared__ double red[32];
   int n = 1;
   while (n < W) n <<= 1;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) sh[i] = i < W ? E[i] : INFINITY;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) skey[i] = i < W ? clip_key(E[i]) : ~0ull;
   __syncthreads();
   for (int k = 2; k <= n; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
@@ -107,13 +117,13 @@ __global__ void k_clip(const double* __restrict__ E, int W, double q, double* __
         const int l = i ^ j;
         if (l > i) {
           const bool up = (i & k) == 0;
-          const double a = sh[i], b = sh[l];
-          if ((a > b) == up) { sh[i] = b; sh[l] = a; }
+          const unsigned long long a = skey[i], b = skey[l];
+          if ((a > b) == up) { skey[i] = b; skey[l] = a; }
         }
       }
       __syncthreads();
     }
-  const double m = 0.5 * (sh[(W - 1) / 2] + sh[W / 2]);
+  const double m = 0.5 * (clip_unkey(skey[(W - 1) / 2]) + clip_unkey(skey[W / 2]));
   auto block_sum = [&](double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __syncthreads();

@@ -385,6 +385,16 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
     }
     return (uint32_t)Np;
   };
+  // A stage this thread does not take part in: advance the ring as gemm()
+  // does, without waiting.
+  auto skip_stage = [&]() {
+    mma_phase ^= 1u;
+    cj = cj + 1 == nst ? 0 : cj + 1;
+    if (++cb == 3) {
+      cb = 0;
+      cpar ^= 1u;
+    }
+  };
   // End of an epilogue that wrote the next A tile: make the generic-proxy
   // stores visible to the tensor core, then meet at the barrier.
   auto fence_sync = [&]() {
@@ -677,57 +687,78 @@ __global__ void __launch_bounds__(NT, 1) k_metropolis_tc(DevSys s, DevNet<float>
         for (int jj = 0; jj < 8 && c0 + jj < no; ++jj) sF[arow * no + c0 + jj] = v[jj] + net.p[o.kb[2] + c0 + jj];
     }
     __syncthreads();
-    // ---- Jastrow head eta on the electron sums (rows = walkers)
-    for (int q = tid; q < WTt * (D / 8); q += NT) {
-      const int w = q % WTt, d8 = (q / WTt) * 8;
-      float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      for (int i = 0; i < N; ++i) {
+    // ---- Jastrow head eta on the electron sums (rows = walkers), and the
+    // determinants.  When the walkers fit one TMEM lane quadrant (WTt <= 32)
+    // the four warps of quadrant 0 run the eta maps while the other twelve
+    // warps form the determinants (float64 LU), meeting at the next barrier.
+    const bool split = WTt <= 32;
+    const bool in_e = !split || quad == 0;
+    if (in_e) {
+      const int ge = split ? sub * 32 + lane : tid, ne = split ? 128 : NT;
+      auto esync = [&]() {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        if (split)
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+        else
+          __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+      };
+      for (int q = ge; q < WTt * (D / 8); q += ne) {
+        const int w = q % WTt, d8 = (q / WTt) * 8;
+        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < N; ++i) {
           const float4 p0 = *(const float4*)(sx + (w * N + i) * LX + d8), p1 = *(const float4*)(sx + (w * N + i) * LX + d8 + 4);
           acc[0] += p0.x; acc[1] += p0.y; acc[2] += p0.z; acc[3] += p0.w;
           acc[4] += p1.x; acc[5] += p1.y; acc[6] += p1.z; acc[7] += p1.w;
         }
-      put3x8(sA, L.a_bytes, w, d8, D, acc);
-    }
-    fence_sync();
-    for (int layer = 0; layer < 2; ++layer) {
-      const uint32_t npl = gemm(0, false);
-      if (quad * 32 < WTt)
-      for (int c0 = sub * 8; c0 < D; c0 += WPQ * 8) {
-        float v[8];
-        tmem_ld8x3(trow + (uint32_t)c0, npl, v);
-        const float* eb = net.p + o.eb[layer] + c0;
-        for (int jj = 0; jj < 8; ++jj) v[jj] = sspf(v[jj] + eb[jj]);
-        put3x8(sA, L.a_bytes, arow, c0, D, v);
+        put3x8(sA, L.a_bytes, w, d8, D, acc);
       }
-      fence_sync();
+      esync();
+      for (int layer = 0; layer < 2; ++layer) {
+        const uint32_t npl = gemm(0, false);
+        if (quad * 32 < WTt)
+          for (int c0 = sub * 8; c0 < D; c0 += WPQ * 8) {
+            float v[8];
+            tmem_ld8x3(trow + (uint32_t)c0, npl, v);
+            const float* eb = net.p + o.eb[layer] + c0;
+            for (int jj = 0; jj < 8; ++jj) v[jj] = sspf(v[jj] + eb[jj]);
+            put3x8(sA, L.a_bytes, arow, c0, D, v);
+          }
+        esync();
+      }
+      np = gemm(0, false);
+      if (sub == 0 && quad * 32 < WTt) {
+        float v[8];
+        tmem_ld8x3(trow, np, v);
+        if (arow < WTt) sJ[arow] = v[0] + net.p[o.eb[2]];
+      }
+    } else {
+      for (int k = 0; k < 3; ++k) skip_stage();  // keep the stage ring in step with quadrant 0
     }
-    np = gemm(0, false);
-    if (sub == 0 && quad * 32 < WTt) {
-      float v[8];
-      tmem_ld8x3(trow, np, v);
-      if (arow < WTt) sJ[arow] = v[0] + net.p[o.eb[2]];
+    if (!split || !in_e) {
+      // one thread per (walker, det, spin)
+      const int gd = split ? ((sub * 3 + quad - 1) * 32 + lane) : tid, nthr = split ? NT - 128 : NT;
+      for (int q = gd; q < WTt * nd * 2; q += nthr) {
+        const int sp = q & 1, p = (q >> 1) % nd, w = (q >> 1) / nd;
+        const int ns = sp ? s.n_dn : s.n_up, e0 = sp ? s.n_up : 0;
+        double mant = 1.0;
+        int ex = 0;
+        if (ns > 0) {
+          double A[PN_MAX_SPIN * PN_MAX_SPIN];
+          const int* occ = s.occ + p * N + e0;
+          for (int a = 0; a < ns; ++a)
+            for (int bb = 0; bb < ns; ++bb) {
+              const int e = w * N + e0 + a, mu = occ[bb];
+              A[a * ns + bb] = (double)sphi[e * no + mu] * (1.0 + (double)sF[e * no + mu]);
+            }
+          det_scaled(A, ns, &mant, &ex);
+        }
+        sdet[q] = mant;
+        sdex[q] = ex;
+      }
     }
     if (__syncthreads_or(abort_flag)) break;
-    // ---- determinants (float64 LU), one thread per (walker, det, spin)
-    for (int q = tid; q < WTt * nd * 2; q += NT) {
-      const int sp = q & 1, p = (q >> 1) % nd, w = (q >> 1) / nd;
-      const int ns = sp ? s.n_dn : s.n_up, e0 = sp ? s.n_up : 0;
-      double mant = 1.0;
-      int ex = 0;
-      if (ns > 0) {
-        double A[PN_MAX_SPIN * PN_MAX_SPIN];
-        const int* occ = s.occ + p * N + e0;
-        for (int a = 0; a < ns; ++a)
-          for (int bb = 0; bb < ns; ++bb) {
-            const int e = w * N + e0 + a, mu = occ[bb];
-            A[a * ns + bb] = (double)sphi[e * no + mu] * (1.0 + (double)sF[e * no + mu]);
-          }
-        det_scaled(A, ns, &mant, &ex);
-      }
-      sdet[q] = mant;
-      sdex[q] = ex;
-    }
-    __syncthreads();
     // ---- ln|psi'| = gamma + J + ln|sum_p c_p det_up,p det_dn,p| (float64
     // sum of the determinant products scaled by the largest power of two)
     // and the accept test
