@@ -45,6 +45,28 @@ def _peaks():
 
 # Algorithmic floating-point work per launch class (multiply-add = 2), per
 # walker, for the value pass (T = 1) and the jet pass (T = 3N + 2).
+def tc_sampler_executed_flops(sysd, W, n_sms=152):
+    """bf16 tensor-core FLOPs the tcgen05 sampler executes per Metropolis step
+    over all CTAs: every stage is a 128-row tile with six piece products per
+    float32 product (K x Np per product, Np padded to 16), the first layer's h
+    excluded; CTAs hold WT walkers as the launcher sizes them."""
+    N = sysd["n_up"] + sysd["n_dn"]
+    M = len(sysd["Z"])
+    D, Zd, K, L = sysd["D"], sysd["Zd"], sysd["K"], sysd["L"]
+    Hw = max(K, Zd)
+    no = sysd["mo_coeffs"].shape[1]
+    pad = lambda x: (x + 15) // 16 * 16
+    nup, ndn = sysd["n_up"], sysd["n_dn"]
+    cnts = [nup * (nup - 1) // 2 + ndn * (ndn - 1) // 2, nup * ndn, N * M]
+    live = sum(1 for c in cnts if c > 0)
+    stages = [(D, Zd)] * (L - 1) + [(K, Hw), (Hw, Zd), (Zd, D)] * (L * live)
+    stages += [(D, D), (D, D), (D, pad(no)), (D, D), (D, D), (D, 16)]
+    macs_tile = sum(6 * k * n * 128 for k, n in stages)
+    WT = min(128 // N, 128 // max(cnts), -(-W // n_sms))
+    ctas = -(-W // WT)
+    return 2 * macs_tile * ctas
+
+
 def algorithmic_flops(sysd, kernel, mode):
     N = sysd["n_up"] + sysd["n_dn"]
     M = len(sysd["Z"])
@@ -87,15 +109,30 @@ def _clock_sampler(path):
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     try:
-        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+        proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "20"],
                                 stdout=open(path, "w"), stderr=subprocess.DEVNULL)
     except Exception:
         return None
-
-
-def _clock_summary(path, dev_index):
+    # start timing only once the sampler is writing, so that its samples fall
+    # inside the timed region; the lines before it are dropped from the summary
+    t0 = time.time()
+    while time.time() - t0 < 10.0 and proc.poll() is None:
+        try:
+            if os.path.getsize(path) > 0:
+                break
+        except OSError:
+            pass
+        time.sleep(0.01)
     try:
-        rows = [l.strip().split(", ") for l in open(path) if l.strip()]
+        proc.skip = sum(1 for l in open(path) if l.strip())
+    except OSError:
+        proc.skip = 0
+    return proc
+
+
+def _clock_summary(path, dev_index, skip=0):
+    try:
+        rows = [l.strip().split(", ") for l in open(path) if l.strip()][skip:]
     except Exception:
         return None
     rows = [r for r in rows if len(r) >= 9 and r[0] == str(dev_index)]
@@ -172,21 +209,40 @@ def cpu_baseline_sample(n_walkers=96):
     Ec = oclip.clip_local_energy(E)
     o.grad_logpsi(r, oclip.loss_cotangent(Ec))
     dt = time.perf_counter() - t0
-    return {"value": n_walkers / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+    cores = torch.get_num_threads()
+    # the same step on one core, on a smaller sample of the same walkers
+    n1 = max(2, n_walkers // 8)
+    torch.set_num_threads(1)
+    try:
+        r1 = sampling.init_walkers(sysd, n1, 1)
+        lp1, _ = o.eval_logpsi(r1)
+        t1 = time.perf_counter()
+        r1, lp1, _ = sampling.metropolis(o, r1, lp1, N_METROPOLIS, SIGMA, seed=1, step0=0)
+        E1, _, _ = o.local_energy(r1)
+        o.grad_logpsi(r1, oclip.loss_cotangent(oclip.clip_local_energy(E1)))
+        dt1 = time.perf_counter() - t1
+    finally:
+        torch.set_num_threads(cores)
+    return {"value": n_walkers / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_walkers} walkers: {N_METROPOLIS} Metropolis steps + E_loc + clip + grad (one step)",
-            "seconds": dt}
+            "seconds": dt, "value_1core": n1 / dt1, "sample_1core": f"{n1} walkers, same step, 1 thread"}
 
 
-def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384, load=0.7):
+def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384, load=0.7,
+                precisions=("mixed", "fp64"), sweep=()):
     """Poisson stream of seeded molecules through the serving loop, mixed and
     plain FP64 servers.  The arrival rate is set to `load` times the mixed
-    server's measured capacity (a closed-loop calibration burst first)."""
+    server's measured capacity (a closed-loop calibration burst first).
+    `sweep` lists further loads at which the mixed server is measured again
+    on the same stream (the latency-load curve)."""
     import torch
     from paper_1909_08423_gb300 import binding, synth
     stream = synth.serving_stream(n_jobs, seed, rate_per_s=1.0, wmax=wmax)
-    sys_cache = {}
     out = {}
-    for prec_name, prec in (("mixed", binding.PN_MIXED), ("fp64", binding.PN_FP64)):
+    rate = cap_mixed = None
+    runs = [(p_, load) for p_ in precisions] + [("mixed", l_) for l_ in sweep]
+    for prec_name, run_load in runs:
+        prec = binding.PN_MIXED if prec_name == "mixed" else binding.PN_FP64
         systems = [binding.System(synth.serving_system(j["seed"]), precision=prec, max_walkers=1) for j in stream]
         srv = binding.Server(budget_gb << 30, n_slots=slots, chunk_walkers=chunk)
         # calibration: all jobs of a prefix at once -> walker-E_loc/s and jobs/s capacity
@@ -198,10 +254,13 @@ def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384
         for i in ids:
             srv.poll(i, timeout_us=-1)
         cap_jobs = ncal / (time.perf_counter() - t0)
-        if prec_name == "mixed":
+        if prec_name == "mixed" and cap_mixed is None:
+            cap_mixed = cap_jobs
+        if rate is None:  # every server sees the arrival rate set by the first calibration
             rate = load * cap_jobs
+        this_rate = run_load * cap_mixed if (prec_name == "mixed" and run_load != load) else rate
         # open-loop Poisson arrivals at `rate`
-        arr = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, size=n_jobs))
+        arr = np.cumsum(np.random.default_rng(seed).exponential(1.0 / this_rate, size=n_jobs))
         ids = []
         t0 = time.perf_counter()
         for k, j in enumerate(stream):
@@ -218,9 +277,13 @@ def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384
         span = time.perf_counter() - t0
         srv.close()
         lat = np.array(lat)
-        out[prec_name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                          "walker_eloc_per_s": walkers / span, "jobs_per_s": n_jobs / span,
-                          "calibrated_capacity_jobs_per_s": cap_jobs}
+        rec = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+               "walker_eloc_per_s": walkers / span, "jobs_per_s": n_jobs / span,
+               "calibrated_capacity_jobs_per_s": cap_jobs}
+        if run_load == load and prec_name not in out:
+            out[prec_name] = rec
+        else:
+            out.setdefault("load_sweep", []).append(dict(rec, load=run_load, arrival_rate_jobs_per_s=this_rate))
         for s_ in systems:
             s_.close()
     out["arrival_rate_jobs_per_s"] = rate
@@ -243,6 +306,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=60)
     ap.add_argument("--serve-only", action="store_true")
+    ap.add_argument("--serve-load", type=float, default=0.7, help="offered load, fraction of calibrated mixed capacity")
+    ap.add_argument("--serve-precisions", default="mixed,fp64")
+    ap.add_argument("--serve-sweep", default="", help="further loads for the mixed server, e.g. 0.5,0.9")
     ap.add_argument("--sampler", type=int, default=None,
                     help="PN_OPT_FUSED_SAMPLER for the timed mixed path (library default if absent)")
     ap.add_argument("--case", choices=["sampler", "jet_tc"], default=None,
@@ -278,7 +344,10 @@ def main():
 
     if args.serve_only:
         torch.cuda.set_device(0)
-        print(json.dumps({"serve": run_serving(args.serve_jobs)}), flush=True)
+        sweep = tuple(float(x) for x in args.serve_sweep.split(",") if x)
+        print(json.dumps({"serve": run_serving(args.serve_jobs, load=args.serve_load,
+                                               precisions=tuple(args.serve_precisions.split(",")), sweep=sweep)}),
+              flush=True)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -380,7 +449,7 @@ def main():
     if sampler:
         sampler.terminate()
         sampler.wait()
-    clocks = _clock_summary(clk_path, local)
+    clocks = _clock_summary(clk_path, local, getattr(sampler, "skip", 0))
     t = torch.tensor([ms], device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -460,6 +529,14 @@ def main():
                     "flops_per_step": per_step_flops,
                     "note": "algorithmic float32 network FLOPs of the launches timed; the sampler also "
                             "runs float64 determinants and log-sums"}
+            if dom == "k_metropolis_tc":
+                ex = tc_sampler_executed_flops(sysd, W) * N_METROPOLIS
+                ex_tf = ex / (kern_ms_per_step / 1e3) / 1e12
+                bf16 = peaks.get("bf16_tflops", 1900.0)
+                roof["tensor_view"] = {
+                    "executed_tflops": ex_tf, "peak": bf16, "frac": ex_tf / bf16, "unit": "TFLOP/s",
+                    "note": "bf16 tcgen05 work actually issued (six piece products per float32 product, "
+                            "128-row tiles incl. padding) against the bf16 peak (" + peak_src + ")"}
         else:
             roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
                     "traffic": None, "kernel_ms_per_step": kern_ms_per_step}

@@ -50,25 +50,29 @@ def test_eloc_job_matches_direct_call(lib):
 
 
 def test_results_same_alone_and_in_a_mix(lib):
+    """Twenty sampled jobs (five molecules, both kinds, 64-900 walkers) run
+    alone, then again inside a mix of forty jobs on four slots: energies and
+    final positions are bitwise equal (per-walker work does not depend on
+    the batch, and the random stream is keyed by job seed, walker and step)."""
     systems = _systems(lib)
     srv = lib.Server(8 * GB, n_slots=4, chunk_walkers=1024)
-    probe = [_job(systems[1], lib.PN_JOB_SWEEP, 777, 5), _job(systems[3], lib.PN_JOB_ELOC, 300, 6)]
+    rng = np.random.default_rng(0)
+    spec = [(k % len(systems), int(rng.integers(0, 2)), int(rng.integers(64, 900)), 500 + k) for k in range(20)]
     alone = []
-    for j in probe:
+    for si, kind, W, seed in spec:
+        j = _job(systems[si], kind, W, seed)
         res = _run(lib, srv, [j])[0]
         torch.cuda.synchronize()
-        alone.append((res, j["eloc_out"].cpu().numpy().copy(), j["r_out"].cpu().numpy().copy()))
-    rng = np.random.default_rng(0)
-    mix = []
-    for k in range(14):
-        s = systems[k % len(systems)]
-        mix.append(_job(s, int(rng.integers(0, 2)), int(rng.integers(64, 2048)), 100 + k))
-    again = [_job(systems[1], lib.PN_JOB_SWEEP, 777, 5), _job(systems[3], lib.PN_JOB_ELOC, 300, 6)]
-    jobs = mix[:5] + [again[0]] + mix[5:10] + [again[1]] + mix[10:]
+        assert res.status == 0
+        alone.append((j["eloc_out"].cpu().numpy().copy(), j["r_out"].cpu().numpy().copy()))
+    again = [_job(systems[si], kind, W, seed) for si, kind, W, seed in spec]
+    filler = [_job(systems[k % len(systems)], int(rng.integers(0, 2)), int(rng.integers(64, 2048)), 100 + k)
+              for k in range(20)]
+    jobs = [x for pair in zip(filler, again) for x in pair]
     results = _run(lib, srv, jobs)
     torch.cuda.synchronize()
     assert all(r.status == 0 for r in results)
-    for (res_a, e_a, r_a), j in zip(alone, again):
+    for (e_a, r_a), j in zip(alone, again):
         np.testing.assert_array_equal(j["eloc_out"].cpu().numpy(), e_a)
         np.testing.assert_array_equal(j["r_out"].cpu().numpy(), r_a)
     # the mix overlapped: some job was admitted while another was running
