@@ -297,6 +297,14 @@ class Oracle(Model):
                 lap = lap + gi[:, i, a]
         return lp.detach().numpy(), s.detach().numpy(), g.detach().numpy(), lap.detach().numpy()
 
+    def value_and_grad(self, r):
+        """ln|psi|, sign and grad_r ln|psi| [W,N,3] (one reverse-mode gradient);
+        the drift of the Langevin sampler."""
+        r = _t(r).clone().requires_grad_(True)
+        lp, s = self.logpsi(r)
+        g = torch.autograd.grad(lp.sum(), r)[0]
+        return lp.detach().numpy(), s.detach().numpy(), g.numpy()
+
     def local_energy(self, r):
         """E_loc = -1/2 (lap ln|psi| + |grad ln|psi||^2) + V, plus ln|psi| and sign."""
         lp, s, g, lap = self.derivatives(r)

@@ -346,6 +346,80 @@ def test_metropolis_samples_hydrogen_density():
     assert abs((rs ** 2).mean() - 3.0) < 0.15
 
 
+def _langevin_chain(S, W, tau, seed, burn, blocks):
+    o = Oracle(S)
+    r = sampling.init_walkers(S, W, seed=seed)
+    lp, _, g = o.value_and_grad(r)
+    r, lp, g, _ = sampling.langevin(o, r, lp, g, burn, tau, seed=seed, step0=0)
+    rs, acc = [], []
+    for k in range(blocks):
+        r, lp, g, a = sampling.langevin(o, r, lp, g, 10, tau, seed=seed, step0=burn + 10 * k)
+        rs.append(np.linalg.norm(r[:, 0], axis=-1))
+        acc.append(a.mean() / 10)
+    return np.concatenate(rs), float(np.mean(acc))
+
+
+@pytest.mark.parametrize("tau", [0.3, 1.0])
+def test_langevin_samples_gaussian_density(tau):
+    """psi = exp(-alpha r^2): |psi|^2 is a Gaussian of variance 1/(4 alpha)
+    per axis, so <r> = sqrt(2 / (pi alpha)) and <r^2> = 3 / (4 alpha).  With
+    tau = 1 the drift step 2 alpha tau r is longer than r, so the clipping
+    at the nucleus acts on every move and the Hastings ratio must carry it."""
+    alpha = 0.7
+    rs, _ = _langevin_chain(synth.single_gto(1.0, alpha), 2048, tau, 5, 40, 6)
+    assert abs(rs.mean() - np.sqrt(2 / (np.pi * alpha))) < 0.02
+    assert abs((rs ** 2).mean() - 3 / (4 * alpha)) < 0.04
+
+
+def test_langevin_samples_hydrogen_density():
+    """|psi|^2 = exp(-2r): <r> = 3/2, <r^2> = 3 under the Langevin chain."""
+    rs, acc = _langevin_chain(synth.hydrogen_like_sto(1.0, 1.0), 2048, 0.1, 6, 40, 6)
+    assert abs(rs.mean() - 1.5) < 0.04
+    assert abs((rs ** 2).mean() - 3.0) < 0.15
+    assert acc > 0.95
+
+
+def test_langevin_drift_direction_raises_acceptance():
+    """With the drift along +grad ln|psi| the proposal nearly follows |psi|^2
+    (acceptance 1 - O(tau^3/2)); the same chain with the drift reversed,
+    planted here in the oracle, still samples correctly but accepts far less.
+    Pins the sign of the drift, which the moments alone cannot see."""
+    S = synth.hydrogen_like_sto(1.0, 1.0)
+    _, acc = _langevin_chain(S, 1024, 0.1, 6, 20, 1)
+    orig = sampling.clipped_drift
+    sampling.clipped_drift = lambda s_, r_, g_, t_: -orig(s_, r_, g_, t_)
+    try:
+        _, acc_rev = _langevin_chain(S, 1024, 0.1, 6, 20, 1)
+    finally:
+        sampling.clipped_drift = orig
+    assert acc > 0.97 and acc_rev < 0.8
+
+
+def test_langevin_small_step_always_accepts():
+    """As tau -> 0 the Hastings ratio tends to 1: every move is accepted."""
+    S = synth.be()
+    o = Oracle(S)
+    r = sampling.init_walkers(S, 16, seed=3)
+    lp, _, g = o.value_and_grad(r)
+    _, _, _, acc = sampling.langevin(o, r, lp, g, 2, 1e-6, seed=3, step0=0)
+    assert np.all(acc == 2)
+
+
+def test_clipped_drift_never_passes_a_nucleus():
+    """The drift displacement is never longer than the distance from the
+    electron to its nearest nucleus, and is unchanged where it is shorter."""
+    S = synth.h10()
+    rng = np.random.default_rng(8)
+    r = sampling.init_walkers(S, 64, seed=8)
+    g = rng.normal(0, 5.0, r.shape)
+    c = sampling.clipped_drift(S, r, g, 0.5)
+    d = np.linalg.norm(r[:, :, None, :] - np.asarray(S["R"])[None, None], axis=-1).min(-1)
+    lc = np.linalg.norm(c, axis=-1)
+    assert np.all(lc <= d * (1 + 1e-12))
+    short = np.linalg.norm(0.5 * g, axis=-1) <= d
+    np.testing.assert_allclose(c[short], 0.5 * g[short], rtol=0, atol=0)
+
+
 # ----------------------------------------------------------------- clipping
 
 def test_clipping_window_and_smoothness():
