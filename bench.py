@@ -228,6 +228,49 @@ def cpu_baseline_sample(n_walkers=96):
             "seconds": dt, "value_1core": n1 / dt1, "sample_1core": f"{n1} walkers, same step, 1 thread"}
 
 
+def run_langevin(sysd, W, target=0.57, steps=10):
+    """The paper's Langevin sampler on the bench workload: tau bisected (on
+    log tau, short runs) to the 57 % target acceptance, then `steps` steps
+    timed with CUDA events (mixed path)."""
+    import torch
+    from paper_1909_08423_gb300 import binding
+    s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=W)
+    r = torch.empty(W, s.N, 3, dtype=torch.float64, device="cuda")
+    s.init_walkers(r, 7)
+    lp = torch.empty(W, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(r)
+    s.eval_drift(r, g, lp)
+    s.langevin_step(r, lp, g, 20, 0.05, 7, 0)  # leave the initial Gaussian cloud
+    nacc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    lo, hi = np.log(1e-3), np.log(2.0)
+    step0 = 100
+    for _ in range(7):
+        tau = float(np.exp(0.5 * (lo + hi)))
+        s.langevin_step(r, lp, g, 5, tau, 7, step0, nacc)
+        step0 += 5
+        acc = int(nacc.item()) / (5 * W)
+        if acc > target:
+            lo = np.log(tau)
+        else:
+            hi = np.log(tau)
+    tau = float(np.exp(0.5 * (lo + hi)))
+    s.langevin_step(r, lp, g, 2, tau, 7, step0)
+    step0 += 2
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.langevin_step(r, lp, g, steps, tau, 7, step0, nacc)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = {"tau": tau, "accept_rate": int(nacc.item()) / (steps * W), "ms_per_step": ms,
+           "walker_steps_per_s": W / (ms / 1e3), "walkers": W, "steps_timed": steps,
+           "note": "all-electron drift-diffusion proposal with the drift clipped at the nearest nucleus; "
+                   "tau bisected to the 57 % target acceptance; staged kernels with one jet pass per step"}
+    s.close()
+    return out
+
+
 def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384, load=0.7,
                 precisions=("mixed", "fp64"), sweep=()):
     """Poisson stream of seeded molecules through the serving loop, mixed and
@@ -304,6 +347,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-langevin", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=60)
     ap.add_argument("--serve-only", action="store_true")
     ap.add_argument("--serve-load", type=float, default=0.7, help="offered load, fraction of calibrated mixed capacity")
@@ -557,6 +601,8 @@ def main():
             "clocks": clocks, "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
+    if rank == 0 and not args.no_langevin:
+        line["langevin"] = run_langevin(sysd, W)
     if rank == 0 and args.serve_jobs > 0:
         line["serve"] = run_serving(args.serve_jobs)
     if rank == 0:

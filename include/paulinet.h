@@ -191,6 +191,33 @@ int pn_metropolis_step(pn_system_t sys, double* r, double* logabs, int W,
                        int n_steps, double sigma, uint64_t seed, uint64_t step0,
                        int64_t* n_accept, void* stream);
 
+/* ln|psi| and its gradient with respect to the electron positions,
+ * drift [W][N][3] = grad_r ln|psi| (the quantity the Langevin proposal
+ * follows; Methods, ansatz optimisation, sampling), from the same jet pass
+ * as pn_eval_local_energy.  logabs may be NULL.  Host or device buffers; a
+ * call with a host buffer returns after the results are written. */
+int pn_eval_drift(pn_system_t sys, const double* r, int W, double* logabs,
+                  double* drift, void* stream);
+
+/* n_steps Langevin (drift-diffusion) Metropolis-Hastings steps for each
+ * walker (Methods, ansatz optimisation: Langevin Monte Carlo after Umrigar
+ * et al., its radial proposal replaced by clipping the step length at the
+ * nearest nucleus).  All electrons move at once:
+ *   r' = r + c(r) + sqrt(tau) xi,  c_e = tau drift_e, shortened to the
+ *        distance from r_e to its nearest nucleus when it is longer,
+ *   accept iff u < |psi(r')/psi(r)|^2 T(r' -> r) / T(r -> r'),
+ *   T(x -> y) = exp(-|y - x - c(x)|^2 / (2 tau)).
+ * xi and u come from the same Philox4x32-10 stream layout as
+ * pn_metropolis_step.  r [W][N][3], logabs [W] and drift [W][N][3] must be
+ * DEVICE buffers holding ln|psi(r)| and grad ln|psi(r)| on entry
+ * (pn_eval_drift); they are updated in place.  n_accept (one int64, host or
+ * device, may be NULL) receives the accepted moves over walkers and steps.
+ * tau > 0 is the time step; the paper tunes it for 57 % acceptance, which is
+ * left to the caller.  PN_EINVAL for host buffers or tau <= 0. */
+int pn_langevin_step(pn_system_t sys, double* r, double* logabs, double* drift,
+                     int W, int n_steps, double tau, uint64_t seed,
+                     uint64_t step0, int64_t* n_accept, void* stream);
+
 /* Implementation options of a handle (they change speed, not results
  * beyond floating-point rounding).
  * PN_OPT_FUSED_SAMPLER (default 4 for PN_MIXED, 1 for PN_FP64): run

@@ -76,6 +76,9 @@ EXPORTS = {
     "pn_metropolis_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
                                      C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]),
     "pn_init_walkers": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_uint64, C.c_void_p]),
+    "pn_eval_drift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pn_langevin_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
+                                   C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]),
     "pn_grad_logpsi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t,
                                  C.c_void_p]),
     "pn_clip_local_energy": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -237,6 +240,13 @@ class System:
         W = r.shape[0]
         check(load().pn_metropolis_step(self.h, _ptr(r), _ptr(logabs), W, n_steps, float(sigma), int(seed),
                                         int(step0), _ptr(n_accept), _stream(r)))
+
+    def eval_drift(self, r, drift, logabs=None):
+        check(load().pn_eval_drift(self.h, _ptr(r), r.shape[0], _ptr(logabs), _ptr(drift), _stream(r)))
+
+    def langevin_step(self, r, logabs, drift, n_steps, tau, seed, step0, n_accept=None):
+        check(load().pn_langevin_step(self.h, _ptr(r), _ptr(logabs), _ptr(drift), r.shape[0], n_steps, float(tau),
+                                      int(seed), int(step0), _ptr(n_accept), _stream(r)))
 
     def device_status(self):
         check(load().pn_device_status(self.h))

@@ -53,6 +53,90 @@ __global__ void k_accept(double* __restrict__ r, double* __restrict__ lp, const 
   }
 }
 
+// ---------------------------------------------------------- Langevin moves
+// Drift displacement of electron e: c = tau * grad_e ln|psi|, shortened to
+// the distance from r_e to the nearest nucleus when longer, so that the
+// drift cannot carry the electron past a nucleus.
+__device__ inline void langevin_drift(const DevSys& s, const double* re, const double* ge, double tau, double c[3]) {
+  double dmin = INFINITY;
+  for (int I = 0; I < s.M; ++I) {
+    const double a = re[0] - s.R[3 * I], b = re[1] - s.R[3 * I + 1], d = re[2] - s.R[3 * I + 2];
+    dmin = fmin(dmin, sqrt(a * a + b * b + d * d));
+  }
+  for (int x = 0; x < 3; ++x) c[x] = tau * ge[x];
+  const double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+  if (len > dmin) {
+    const double f = dmin / len;
+    for (int x = 0; x < 3; ++x) c[x] *= f;
+  }
+}
+
+// r' = r + c(r) + sqrt(tau) xi (normals from the same Philox layout as the
+// Gaussian proposal); keeps |xi|^2 / 2, the forward term of the proposal
+// density ratio.
+__global__ void k_langevin_propose(DevSys s, const double* __restrict__ r, const double* __restrict__ drift,
+                                   double* __restrict__ rp, double* __restrict__ half_xi2, int Wn, unsigned walker0,
+                                   unsigned long long seed, unsigned long long step, double tau) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= Wn) return;
+  const int N = s.N, n3 = 3 * N;
+  const double st = sqrt(tau);
+  double x2 = 0;
+  for (int e = 0; e < N; ++e) {
+    double c[3];
+    langevin_drift(s, r + (size_t)w * n3 + 3 * e, drift + (size_t)w * n3 + 3 * e, tau, c);
+    for (int x = 0; x < 3; ++x) rp[(size_t)w * n3 + 3 * e + x] = r[(size_t)w * n3 + 3 * e + x] + c[x];
+  }
+  for (int j = 0; j * 4 < n3; ++j) {
+    double z[4];
+    pn_normals4(seed, walker0 + w, step, j, z);
+    for (int k = 0; k < 4; ++k) {
+      const int m = 4 * j + k;
+      if (m < n3) {
+        rp[(size_t)w * n3 + m] += st * z[k];
+        x2 += z[k] * z[k];
+      }
+    }
+  }
+  half_xi2[w] = 0.5 * x2;
+}
+
+// Metropolis-Hastings test u < |psi'/psi|^2 T(r' -> r) / T(r -> r') with
+// T(x -> y) = exp(-|y - x - c(x)|^2 / (2 tau)); u is word 0 of block
+// ceil(3N/4) as for the Gaussian proposal.  On accept r, ln|psi| and the
+// drift take the proposal's values.
+__global__ void k_langevin_accept(DevSys s, double* __restrict__ r, double* __restrict__ lp,
+                                  double* __restrict__ drift, const double* __restrict__ rp,
+                                  const double* __restrict__ lpp, const double* __restrict__ gp,
+                                  const double* __restrict__ half_xi2, int Wn, unsigned walker0,
+                                  unsigned long long seed, unsigned long long step, double tau,
+                                  unsigned long long* n_acc) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= Wn) return;
+  const int N = s.N, n3 = 3 * N;
+  double back2 = 0;
+  for (int e = 0; e < N; ++e) {
+    double c[3];
+    langevin_drift(s, rp + (size_t)w * n3 + 3 * e, gp + (size_t)w * n3 + 3 * e, tau, c);
+    for (int x = 0; x < 3; ++x) {
+      const double b = r[(size_t)w * n3 + 3 * e + x] - rp[(size_t)w * n3 + 3 * e + x] - c[x];
+      back2 += b * b;
+    }
+  }
+  const double log_ratio = 2.0 * (lpp[w] - lp[w]) + half_xi2[w] - back2 / (2.0 * tau);
+  unsigned cc[4] = {(unsigned)((n3 + 3) / 4), walker0 + w, (unsigned)(step & 0xffffffffull), (unsigned)(step >> 32)};
+  pn_philox(cc, (unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
+  const double u = pn_u01(cc[0]);
+  if (u < exp(log_ratio)) {
+    for (int m = 0; m < n3; ++m) {
+      r[(size_t)w * n3 + m] = rp[(size_t)w * n3 + m];
+      drift[(size_t)w * n3 + m] = gp[(size_t)w * n3 + m];
+    }
+    lp[w] = lpp[w];
+    atomicAdd(n_acc, 1ull);
+  }
+}
+
 // electron e at R[nuc(e)] + normal, normals at step 2^64 - 1.
 __global__ void k_init_walkers(DevSys s, const int* __restrict__ nuc, double* __restrict__ r, int W,
                                unsigned long long seed) {
@@ -286,6 +370,67 @@ template int pn_run_metropolis<double>(const DevSys&, const DevNet<double>&, Wor
 template int pn_run_metropolis<float>(const DevSys&, const DevNet<float>&, Work<float>&, int, double*, double*, int,
                                       int, double, unsigned long long, unsigned long long, int64_t*, cudaStream_t);
 
+// ln|psi| and grad_r ln|psi| (the Langevin drift) by the jet pass.
+template <typename R>
+int pn_run_drift(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, const double* r, int W, double* logabs,
+                 double* drift, cudaStream_t st) {
+  const int N = ds.N;
+  const bool rdev = pn_is_device_ptr(r);
+  for (int c0 = 0; c0 < W; c0 += Wc) {
+    const int Wn = std::min(Wc, W - c0);
+    const double* rc = r + (size_t)c0 * N * 3;
+    if (!rdev) {
+      PN_CUDA(cudaMemcpyAsync(w.r, rc, (size_t)Wn * N * 3 * 8, cudaMemcpyHostToDevice, st));
+      rc = w.r;
+    }
+    if (int e = pn_forward_chunk<R>(ds, net, w, rc, Wn, 1, st)) return e;
+    if (logabs) PN_CUDA(cudaMemcpyAsync(logabs + c0, w.out_logabs, Wn * 8, cudaMemcpyDefault, st));
+    PN_CUDA(cudaMemcpyAsync(drift + (size_t)c0 * N * 3, w.out_grad, (size_t)Wn * N * 3 * 8, cudaMemcpyDefault, st));
+  }
+  if (!rdev || is_host(logabs) || is_host(drift)) PN_CUDA(cudaStreamSynchronize(st));
+  return PN_OK;
+}
+template int pn_run_drift<double>(const DevSys&, const DevNet<double>&, Work<double>&, int, const double*, int, double*,
+                                  double*, cudaStream_t);
+template int pn_run_drift<float>(const DevSys&, const DevNet<float>&, Work<float>&, int, const double*, int, double*,
+                                 double*, cudaStream_t);
+
+// Langevin Metropolis-Hastings steps, staged per workspace chunk: propose,
+// jet pass at the proposals (ln|psi'| and its gradient), accept.  r,
+// logabs and drift are device buffers, updated in place.
+template <typename R>
+int pn_run_langevin(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, double* r, double* logabs,
+                    double* drift, int W, int n_steps, double tau, unsigned long long seed, unsigned long long step0,
+                    int64_t* n_accept, cudaStream_t st) {
+  const int N = ds.N;
+  PN_CUDA(cudaMemsetAsync(w.n_acc, 0, 8, st));
+  for (int c0 = 0; c0 < W; c0 += Wc) {
+    const int Wn = std::min(Wc, W - c0);
+    double* rc = r + (size_t)c0 * N * 3;
+    double* lc = logabs + c0;
+    double* dc = drift + (size_t)c0 * N * 3;
+    for (int k = 0; k < n_steps; ++k) {
+      const unsigned long long step = step0 + (unsigned long long)k;
+      PN_LAUNCH("k_langevin_propose", st,
+                k_langevin_propose<<<nblk(Wn, 128), 128, 0, st>>>(ds, rc, dc, w.r_prop, w.lp_prop, Wn, (unsigned)c0,
+                                                                  seed, step, tau));
+      if (int e = pn_forward_chunk<R>(ds, net, w, w.r_prop, Wn, 1, st)) return e;
+      PN_LAUNCH("k_langevin_accept", st,
+                k_langevin_accept<<<nblk(Wn, 128), 128, 0, st>>>(ds, rc, lc, dc, w.r_prop, w.out_logabs, w.out_grad,
+                                                                 w.lp_prop, Wn, (unsigned)c0, seed, step, tau,
+                                                                 w.n_acc));
+    }
+  }
+  if (n_accept) PN_CUDA(cudaMemcpyAsync(n_accept, w.n_acc, 8, cudaMemcpyDefault, st));
+  if (is_host(n_accept)) PN_CUDA(cudaStreamSynchronize(st));
+  return PN_OK;
+}
+template int pn_run_langevin<double>(const DevSys&, const DevNet<double>&, Work<double>&, int, double*, double*,
+                                     double*, int, int, double, unsigned long long, unsigned long long, int64_t*,
+                                     cudaStream_t);
+template int pn_run_langevin<float>(const DevSys&, const DevNet<float>&, Work<float>&, int, double*, double*, double*,
+                                    int, int, double, unsigned long long, unsigned long long, int64_t*, cudaStream_t);
+
 int pn_run_init_walkers(const DevSys& ds, double* r, int W, unsigned long long seed, cudaStream_t st) {
   PN_LAUNCH("k_init_walkers", st, k_init_walkers<<<nblk(W, 128), 128, 0, st>>>(ds, ds.nuc, r, W, seed));
   return PN_OK;
@@ -346,6 +491,46 @@ extern "C" int pn_metropolis_step(pn_system_t s, double* r, double* logabs, int 
   }
   return s->precision == PN_FP64 ? metropolis_impl<double>(s, r, logabs, W, n_steps, sigma, seed, step0, n_accept, st)
                                  : metropolis_impl<float>(s, r, logabs, W, n_steps, sigma, seed, step0, n_accept, st);
+}
+
+extern "C" int pn_eval_drift(pn_system_t s, const double* r, int W, double* logabs, double* drift, void* stream) {
+  PN_SYS_CHECK(s);
+  if (W < 0 || (W > 0 && (!r || !drift))) {
+    pn_set_error("bad arguments");
+    return PN_EINVAL;
+  }
+  if (W == 0) return PN_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  return s->precision == PN_FP64
+             ? pn_run_drift<double>(s->ds, pn_devnet<double>(s), work_of<double>(s), s->Wc, r, W, logabs, drift, st)
+             : pn_run_drift<float>(s->ds, pn_devnet<float>(s), work_of<float>(s), s->Wc, r, W, logabs, drift, st);
+}
+
+extern "C" int pn_langevin_step(pn_system_t s, double* r, double* logabs, double* drift, int W, int n_steps,
+                                double tau, uint64_t seed, uint64_t step0, int64_t* n_accept, void* stream) {
+  PN_SYS_CHECK(s);
+  if (W < 0 || n_steps < 0 || !(tau > 0) || (W > 0 && (!r || !logabs || !drift))) {
+    pn_set_error("bad arguments");
+    return PN_EINVAL;
+  }
+  if (W > 0 && (!pn_is_device_ptr(r) || !pn_is_device_ptr(logabs) || !pn_is_device_ptr(drift))) {
+    pn_set_error("pn_langevin_step takes device buffers for r, logabs and drift");
+    return PN_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (W == 0 || n_steps == 0) {
+    if (n_accept) {
+      int64_t z = 0;
+      PN_CUDA(cudaMemcpyAsync(n_accept, &z, 8, cudaMemcpyDefault, st));
+      PN_CUDA(cudaStreamSynchronize(st));
+    }
+    return PN_OK;
+  }
+  return s->precision == PN_FP64
+             ? pn_run_langevin<double>(s->ds, pn_devnet<double>(s), work_of<double>(s), s->Wc, r, logabs, drift, W,
+                                       n_steps, tau, seed, step0, n_accept, st)
+             : pn_run_langevin<float>(s->ds, pn_devnet<float>(s), work_of<float>(s), s->Wc, r, logabs, drift, W,
+                                      n_steps, tau, seed, step0, n_accept, st);
 }
 
 extern "C" int pn_init_walkers(pn_system_t s, double* r, int W, uint64_t seed, void* stream) {

@@ -560,7 +560,8 @@ __global__ void k_slater(DevSys s, const double* __restrict__ phi, const R* __re
 template <typename R>
 __global__ void k_combine(DevSys s, const double* __restrict__ geo, const double* __restrict__ det,
                           const R* __restrict__ Jj, int Wn, int T, int jet, double* __restrict__ logabs,
-                          double* __restrict__ sign, double* __restrict__ eloc, int* __restrict__ status) {
+                          double* __restrict__ sign, double* __restrict__ eloc, int* __restrict__ status,
+                          double* __restrict__ grad_out) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= Wn) return;
   const int N = s.N, nd = s.n_det, stride = 3 + 3 * N;
@@ -643,6 +644,8 @@ __global__ void k_combine(DevSys s, const double* __restrict__ geo, const double
   }
   double gn = 0;
   for (int t = 0; t < n3; ++t) gn += g[t] * g[t];
+  if (grad_out)
+    for (int t = 0; t < n3; ++t) grad_out[(size_t)w * n3 + t] = g[t];
   const double E = -0.5 * (lap + gn) + V;
   eloc[w] = E;
   if (st == PN_WALKER_OK && !(isfinite(E) && isfinite(la))) st = PN_WALKER_NONFINITE;
@@ -750,7 +753,7 @@ int pn_forward_chunk(const DevSys& s, const DevNet<R>& net, Work<R>& w, const do
   if (int e = pn_heads<R>(s, net, w, Wn, T, st)) return e;
   PN_LAUNCH("k_slater", st, k_slater<R><<<nblk((size_t)Wn * s.n_det * 2, 64), 64, 0, st>>>(s, w.phi, w.F, Wn, T, jet, w.det));
   PN_LAUNCH("k_combine", st, k_combine<R><<<nblk(Wn, 64), 64, 0, st>>>(s, w.geo, w.det, w.Jj, Wn, T, jet, w.out_logabs, w.out_sign, w.out_eloc,
-                                            w.out_status));
+                                            w.out_status, w.out_grad));
   return PN_OK;
 }
 

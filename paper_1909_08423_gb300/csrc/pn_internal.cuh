@@ -127,6 +127,7 @@ struct Work {
   double* out_logabs;     // [Wc]
   double* out_sign;       // [Wc]
   double* out_eloc;       // [Wc]
+  double* out_grad;       // [Wc][3N]  grad_r ln|psi| of the jet pass
   int* out_status;        // [Wc]
   unsigned long long* n_acc;  // [1]
   double* r_prop;         // [Wc][N][3]

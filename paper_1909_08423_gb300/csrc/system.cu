@@ -217,6 +217,7 @@ size_t pn_work_bytes(const DevSys& s, int Wc, int T, int elem) {
   b += align_up(W * T * elem);                       // Jj
   b += align_up(W * s.n_det * 2 * (3 + 3 * N) * 8);  // det
   b += 3 * align_up(W * 8) + align_up(W * 4);        // outputs
+  b += align_up(W * N * 3 * 8);                      // grad ln|psi|
   b += align_up(8);                                  // n_acc
   b += align_up(W * N * 3 * 8) + align_up(W * 8);    // proposals
   return b;
@@ -250,6 +251,7 @@ Work<R> pn_carve_work(const DevSys& s, int Wc, int T, void* base) {
   w.out_sign = (double*)take(W * 8);
   w.out_eloc = (double*)take(W * 8);
   w.out_status = (int*)take(W * 4);
+  w.out_grad = (double*)take(W * N * 3 * 8);
   w.n_acc = (unsigned long long*)take(8);
   w.r_prop = (double*)take(W * N * 3 * 8);
   w.lp_prop = (double*)take(W * 8);
