@@ -294,8 +294,48 @@ __global__ void k_msg_bwd_h(DevSys s, const R* __restrict__ wv, const R* __restr
 
 // Filter backward through the hidden layer: dAh = (dw W2^T) * sigmoid(Ah),
 // Sh = ssp(Ah) kept for the W2 gradient.  One warp per pair row.
+constexpr int FB_ROWS = 8;  // pair rows per warp in k_filter_bwd
 template <typename R>
-__global__ void k_filter_bwd(DevSys s, DevNet<R> net, int n, const R* __restrict__ Ah, const R* __restrict__ dw, int Wn,
+__global__ void __launch_bounds__(256) k_filter_bwd(DevSys s, DevNet<R> net, int n, const R* __restrict__ Ah,
+                                                    const R* __restrict__ dw, int Wn, R* __restrict__ dAh,
+                                                    R* __restrict__ Sh) {
+  // the three channels' W2 [Hw][Zd] in shared memory, rows padded by one so
+  // that lanes running over h hit distinct banks; one warp per pair row,
+  // FB_ROWS rows per warp
+  extern __shared__ __align__(16) unsigned char fb_smem[];
+  const int Hw = s.Hw, Zd = s.Zd, LZ = Zd + 1;
+  R* W2s = (R*)fb_smem;                 // [3][Hw][LZ]
+  R* dsh = W2s + (size_t)3 * Hw * LZ;   // [8][Zd]
+  for (int q = threadIdx.x; q < 3 * Hw * Zd; q += blockDim.x) {
+    const int c = q / (Hw * Zd), h = (q / Zd) % Hw, z = q % Zd;
+    W2s[((size_t)c * Hw + h) * LZ + z] = net.p[net.off.W2[n][c] + (size_t)h * Zd + z];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  R* dv = dsh + wid * Zd;
+  const size_t rows = (size_t)Wn * s.Ppair;
+  for (int k = 0; k < FB_ROWS; ++k) {
+    const size_t row = ((size_t)blockIdx.x * 8 + wid) * FB_ROWS + k;
+    if (row >= rows) break;
+    const int ch = pair_channel(s, row % s.Ppair);
+    const R* W2 = W2s + (size_t)ch * Hw * LZ;
+    for (int z = lane; z < Zd; z += 32) dv[z] = dw[row * Zd + z];
+    __syncwarp();
+    for (int h = lane; h < Hw; h += 32) {
+      R acc = 0;
+      for (int z = 0; z < Zd; ++z) acc += dv[z] * W2[h * LZ + z];
+      const R a = Ah[row * Hw + h];
+      dAh[row * Hw + h] = acc * sigm_(a);
+      Sh[row * Hw + h] = ssp_(a);
+    }
+    __syncwarp();
+  }
+}
+
+// Same, reading W2 from global memory: for filter widths whose weights do not
+// fit in shared memory.
+template <typename R>
+__global__ void k_filter_bwd_global(DevSys s, DevNet<R> net, int n, const R* __restrict__ Ah, const R* __restrict__ dw, int Wn,
                              R* __restrict__ dAh, R* __restrict__ Sh) {
   __shared__ R sh_d[8][128];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -387,17 +427,31 @@ __global__ void k_wgrad(const __grid_constant__ WgGroup<R> G, double* __restrict
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // each element summed over the splits in split order; the four elements of
+  // a thread are interleaved so that their loads overlap
+  const int nn = n0 + tx;
+  bool ok[4];
+  double sum[4];
+#pragma unroll
   for (int e = 0; e < 4; ++e) {
-    const int k = k0 + ty + 8 * e, nn = n0 + tx;
-    if (k >= J.Ka || nn >= J.Nb) continue;
-    double sum = 0;
-    for (int sp = 0; sp < J.nsplit; ++sp) sum += __ldcg(pj + ((size_t)sp * J.Ka + k) * J.Nb + nn);
+    ok[e] = k0 + ty + 8 * e < J.Ka && nn < J.Nb;
+    sum[e] = 0;
+  }
+#pragma unroll 4
+  for (int sp = 0; sp < J.nsplit; ++sp)
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (ok[e]) sum[e] += __ldcg(pj + ((size_t)sp * J.Ka + (k0 + ty + 8 * e)) * J.Nb + nn);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (!ok[e]) continue;
+    const int k = k0 + ty + 8 * e;
     int64_t dst;
     if (J.rows_per_c > 0)
       dst = J.base + (int64_t)(k / J.rows_per_c) * J.stride_c + (int64_t)(k % J.rows_per_c) * J.Nb + nn;
     else
       dst = J.base + (int64_t)k * J.Nb + nn;
-    grad[dst] += sum;
+    grad[dst] += sum[e];
   }
   if (threadIdx.x == 0) ctr[J.ctr0 + tile] = 0u;  // ready for the next launch
 }
@@ -708,7 +762,23 @@ static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const d
     PN_LAUNCH("k_msg_bwd_h", st, k_msg_bwd_h<R><<<nblk((size_t)rows * Zd, 256), 256, 0, st>>>(s, wn, t.dZ, Wn, t.dH, t.dYr));
     if (int e = wg.add(nullptr, 0, t.dYr, s.M * Zd, rows, 1, s.M * Zd, -1, o.Y, 0, 0)) return e;
     // filters, per channel
-    PN_LAUNCH("k_filter_bwd", st, k_filter_bwd<R><<<nblk((size_t)Wn * P, 8), 256, 0, st>>>(s, net, n, Ahn, t.dw, Wn, t.dAh, t.Sh));
+    {
+      const size_t fb = ((size_t)3 * Hw * (Zd + 1) + 8 * Zd) * sizeof(R);
+      int dev = 0, maxsm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if (fb <= (size_t)maxsm) {
+        if (fb > 48 * 1024)
+          PN_CUDA(cudaFuncSetAttribute(k_filter_bwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb));
+        PN_LAUNCH("k_filter_bwd", st,
+                  k_filter_bwd<R><<<nblk((size_t)Wn * P, 8 * FB_ROWS), 256, fb, st>>>(s, net, n, Ahn, t.dw, Wn,
+                                                                                     t.dAh, t.Sh));
+      } else {
+        PN_LAUNCH("k_filter_bwd", st,
+                  k_filter_bwd_global<R><<<nblk((size_t)Wn * P, 8), 256, 0, st>>>(s, net, n, Ahn, t.dw, Wn, t.dAh,
+                                                                                  t.Sh));
+      }
+    }
     for (int c = 0; c < 3; ++c) {
       if (int e = wg.add(t.Sh, Hw, t.dw, Zd, Wn * P, Hw, Zd, c, o.W2[n][c], 0, 0)) return e;
       if (int e = wg.add(nullptr, 0, t.dw, Zd, Wn * P, 1, Zd, c, o.b2[n][c], 0, 0)) return e;
