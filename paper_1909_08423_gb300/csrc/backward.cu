@@ -374,8 +374,8 @@ struct WgJob {
   const R* A;
   const R* B;
   const int* map;
-  int64_t part0, base, stride_c;
-  int lda, ldb, rows, Ka, Nb, cnt, rps, nsplit, tn, tk, blk0, ctr0, rows_per_c;
+  int64_t part0, base, stride_c, dst_stride;
+  int lda, ldb, rows, Ka, Nb, cnt, rps, nsplit, tn, tk, blk0, ctr0, rows_per_c, ndst;
 };
 template <typename R>
 struct WgGroup {
@@ -384,9 +384,25 @@ struct WgGroup {
 };
 
 template <typename R>
-__global__ void k_wgrad(const __grid_constant__ WgGroup<R> G, double* __restrict__ part, unsigned* __restrict__ ctr, double* __restrict__ grad) {
-  __shared__ R As[32][33];
-  __shared__ R Bs[32][33];
+__device__ inline void wg_load4(const R* p, R v[4]) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 q = *(const float4*)p;
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+    const double2 q0 = *(const double2*)p, q1 = *(const double2*)(p + 2);
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+  }
+}
+
+// One block = one (job, split, 32 x 32 tile); 128 threads, each 2 rows (k)
+// x 4 columns (n) of the tile.  The storage rows of each 32-row chunk are
+// resolved once into shared memory.
+template <typename R>
+__global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ WgGroup<R> G, double* __restrict__ part,
+                                               unsigned* __restrict__ ctr, double* __restrict__ grad) {
+  __shared__ __align__(16) R As[32][32 + 4];
+  __shared__ __align__(16) R Bs[32][32 + 4];
+  __shared__ long long srow[32];
   __shared__ bool last;
   int ji = 0;
   while (ji + 1 < G.n && (int)blockIdx.x >= G.j[ji + 1].blk0) ++ji;
@@ -394,66 +410,106 @@ __global__ void k_wgrad(const __grid_constant__ WgGroup<R> G, double* __restrict
   const int local = (int)blockIdx.x - J.blk0;
   const int ntile = J.tn * J.tk, split = local / ntile, tile = local % ntile;
   const int k0 = (tile / J.tn) * 32, n0 = (tile % J.tn) * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;  // 4 columns x 2 rows each
   const int r_begin = split * J.rps;
   const int r_end = min(J.rows, r_begin + J.rps);
-  R acc[4] = {0, 0, 0, 0};
-  for (int r0 = r_begin; r0 < r_end; r0 += 32) {
-    for (int q = ty; q < 32; q += 8) {
-      const int r = r0 + q;
-      const bool ok = r < r_end;
-      size_t row = r;
-      if (ok && J.map) row = (size_t)(r / J.cnt) * G.P + J.map[r % J.cnt];
-      As[q][tx] = (ok && k0 + tx < J.Ka) ? (J.A ? J.A[row * J.lda + k0 + tx] : R(1)) : R(0);
-      Bs[q][tx] = (ok && n0 + tx < J.Nb) ? J.B[row * J.ldb + n0 + tx] : R(0);
+  R acc[2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  if (!J.A) {
+    // bias gradient (Ka = 1): column sums of B; thread = (column, row group)
+    const int c = tid & 31, grp = tid >> 5;
+    R cs = 0;
+    if (n0 + c < J.Nb)
+      for (int r = r_begin + grp; r < r_end; r += 4) {
+        const long long row = J.map ? (long long)(r / J.cnt) * G.P + J.map[r % J.cnt] : (long long)r;
+        cs += J.B[row * J.ldb + n0 + c];
+      }
+    As[grp][c] = cs;
+    __syncthreads();
+    // thread (tx, ty = 0) holds columns 4 tx .. 4 tx + 3 of row k = 0
+    if (ty == 0)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        acc[0][j] = ((As[0][4 * tx + j] + As[1][4 * tx + j]) + As[2][4 * tx + j]) + As[3][4 * tx + j];
+  }
+  for (int r0 = r_begin; J.A && r0 < r_end; r0 += 32) {
+    if (tid < 32) {
+      const int r = r0 + tid;
+      long long row = -1;
+      if (r < r_end) row = J.map ? (long long)(r / J.cnt) * G.P + J.map[r % J.cnt] : (long long)r;
+      srow[tid] = row;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const int e = tid + 128 * l, q = e >> 5, c = e & 31;
+      const long long row = srow[q];
+      As[q][c] = (row >= 0 && k0 + c < J.Ka) ? (J.A ? J.A[row * J.lda + k0 + c] : R(1)) : R(0);
+      Bs[q][c] = (row >= 0 && n0 + c < J.Nb) ? J.B[row * J.ldb + n0 + c] : R(0);
     }
     __syncthreads();
 #pragma unroll 8
     for (int q = 0; q < 32; ++q) {
-      const R b = Bs[q][tx];
+      const R a0 = As[q][2 * ty], a1 = As[q][2 * ty + 1];
+      R b[4];
+      wg_load4(&Bs[q][4 * tx], b);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc[e] += As[q][ty + 8 * e] * b;
+      for (int j = 0; j < 4; ++j) {
+        acc[0][j] += a0 * b[j];
+        acc[1][j] += a1 * b[j];
+      }
     }
     __syncthreads();
   }
   double* pj = part + J.part0;
-  for (int e = 0; e < 4; ++e) {
-    const int k = k0 + ty + 8 * e, nn = n0 + tx;
-    if (k < J.Ka && nn < J.Nb) pj[((size_t)split * J.Ka + k) * J.Nb + nn] = (double)acc[e];
-  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = k0 + 2 * ty + i, nn = n0 + 4 * tx + j;
+      if (k < J.Ka && nn < J.Nb) pj[((size_t)split * J.Ka + k) * J.Nb + nn] = (double)acc[i][j];
+    }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&ctr[J.ctr0 + tile], 1u) == (unsigned)(J.nsplit - 1);
+  if (tid == 0) last = atomicAdd(&ctr[J.ctr0 + tile], 1u) == (unsigned)(J.nsplit - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // each element summed over the splits in split order; the four elements of
-  // a thread are interleaved so that their loads overlap
-  const int nn = n0 + tx;
-  bool ok[4];
-  double sum[4];
+  // each element summed over the splits in split order; a thread's eight
+  // elements are interleaved so that their loads overlap
+  double sum[2][4];
+  bool ok[2][4];
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    ok[e] = k0 + ty + 8 * e < J.Ka && nn < J.Nb;
-    sum[e] = 0;
-  }
-#pragma unroll 4
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      ok[i][j] = k0 + 2 * ty + i < J.Ka && n0 + 4 * tx + j < J.Nb;
+      sum[i][j] = 0;
+    }
+#pragma unroll 2
   for (int sp = 0; sp < J.nsplit; ++sp)
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
-      if (ok[e]) sum[e] += __ldcg(pj + ((size_t)sp * J.Ka + (k0 + ty + 8 * e)) * J.Nb + nn);
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    if (!ok[e]) continue;
-    const int k = k0 + ty + 8 * e;
-    int64_t dst;
-    if (J.rows_per_c > 0)
-      dst = J.base + (int64_t)(k / J.rows_per_c) * J.stride_c + (int64_t)(k % J.rows_per_c) * J.Nb + nn;
-    else
-      dst = J.base + (int64_t)k * J.Nb + nn;
-    grad[dst] += sum[e];
-  }
-  if (threadIdx.x == 0) ctr[J.ctr0 + tile] = 0u;  // ready for the next launch
+      for (int j = 0; j < 4; ++j)
+        if (ok[i][j]) sum[i][j] += __ldcg(pj + ((size_t)sp * J.Ka + (k0 + 2 * ty + i)) * J.Nb + n0 + 4 * tx + j);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!ok[i][j]) continue;
+      const int k = k0 + 2 * ty + i, nn = n0 + 4 * tx + j;
+      int64_t dst;
+      if (J.rows_per_c > 0)
+        dst = J.base + (int64_t)(k / J.rows_per_c) * J.stride_c + (int64_t)(k % J.rows_per_c) * J.Nb + nn;
+      else
+        dst = J.base + (int64_t)k * J.Nb + nn;
+      for (int d = 0; d < J.ndst; ++d) grad[dst + d * J.dst_stride] += sum[i][j];
+    }
+  if (tid == 0) ctr[J.ctr0 + tile] = 0u;  // ready for the next launch
 }
 
 __global__ void k_add_to(double* __restrict__ grad, int64_t off, const double* __restrict__ v, int n) {
@@ -604,7 +660,7 @@ struct WgBatch {
   // parameter block at `base`; ch >= 0 restricts the rows to the pairs of
   // filter channel ch (rows then count walkers x pairs)
   int add(const R* A, int lda, const R* B, int ldb, int rows, int Ka, int Nb, int ch, int64_t base,
-          int64_t stride_c, int rows_per_c) {
+          int64_t stride_c, int rows_per_c, int ndst = 1, int64_t dst_stride = 0) {
     const int* map = nullptr;
     int cnt = 0;
     if (ch >= 0) {
@@ -621,6 +677,7 @@ struct WgBatch {
     J.A = A; J.B = B; J.map = map; J.cnt = cnt;
     J.lda = lda; J.ldb = ldb; J.rows = rows; J.Ka = Ka; J.Nb = Nb;
     J.base = base; J.stride_c = stride_c; J.rows_per_c = rows_per_c;
+    J.ndst = ndst; J.dst_stride = dst_stride;
     J.tn = (Nb + 31) / 32;
     J.tk = (Ka + 31) / 32;
     return PN_OK;
@@ -652,7 +709,7 @@ struct WgBatch {
       pn_set_error("internal: weight-gradient partials exceed their buffer");
       return PN_EINVAL;
     }
-    PN_LAUNCH("k_wgrad", st, k_wgrad<R><<<blk, 256, 0, st>>>(G, t->part, t->ctr, grad));
+    PN_LAUNCH("k_wgrad", st, k_wgrad<R><<<blk, 128, 0, st>>>(G, t->part, t->ctr, grad));
     reset();
     return PN_OK;
   }
@@ -753,8 +810,8 @@ static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const d
     // receiving maps: X^(n+1) = X^(n) + [z_same z_anti z_nuc] Gcat + sum of biases
     if (int e = wg.add(Zn, 3 * Zd, t.dX, D, rows, 3 * Zd, D, -1, o.GW[n][0], o.GW[n][1] - o.GW[n][0], Zd))
       return e;
-    for (int c = 0; c < 3; ++c)
-      if (int e = wg.add(nullptr, 0, t.dX, D, rows, 1, D, -1, o.Gb[n][c], 0, 0)) return e;
+    // the three receiving-map biases share one gradient, the column sums of dX
+    if (int e = wg.add(nullptr, 0, t.dX, D, rows, 1, D, -1, o.Gb[n][0], 0, 0, 3, o.Gb[n][1] - o.Gb[n][0])) return e;
     if (int e = linear_bt<R>(t.dX, D, net.Gcat + (size_t)n * 3 * Zd * D, D, t.dZ, 3 * Zd, rows, D, 3 * Zd, 0, st))
       return e;
     // messages
