@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ WgGroup<R
                                                unsigned* __restrict__ ctr, double* __restrict__ grad) {
   __shared__ __align__(16) R As[32][32 + 4];
   __shared__ __align__(16) R Bs[32][32 + 4];
-  __shared__ long long srow[32];
+  __shared__ long long srow[256];
   __shared__ bool last;
   int ji = 0;
   while (ji + 1 < G.n && (int)blockIdx.x >= G.j[ji + 1].blk0) ++ji;
@@ -435,34 +435,50 @@ __global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ WgGroup<R
       for (int j = 0; j < 4; ++j)
         acc[0][j] = ((As[0][4 * tx + j] + As[1][4 * tx + j]) + As[2][4 * tx + j]) + As[3][4 * tx + j];
   }
-  for (int r0 = r_begin; J.A && r0 < r_end; r0 += 32) {
-    if (tid < 32) {
-      const int r = r0 + tid;
-      long long row = -1;
-      if (r < r_end) row = J.map ? (long long)(r / J.cnt) * G.P + J.map[r % J.cnt] : (long long)r;
-      srow[tid] = row;
+  // matrix jobs: rows in segments of 256 (their storage rows resolved once),
+  // each segment in 32-row chunks with the next chunk's loads in flight
+  // while the current one is summed
+  for (int s0 = r_begin; J.A && s0 < r_end; s0 += 256) {
+    const int s1 = min(r_end, s0 + 256);
+    __syncthreads();  // srow of the previous segment no longer read
+    for (int q = tid; q < 256; q += 128) {
+      const int r = s0 + q;
+      srow[q] = r < s1 ? (J.map ? (long long)(r / J.cnt) * G.P + J.map[r % J.cnt] : (long long)r) : -1;
     }
     __syncthreads();
+    R va[8], vb[8];
+    auto fetch = [&](int c0) {
 #pragma unroll
-    for (int l = 0; l < 8; ++l) {
-      const int e = tid + 128 * l, q = e >> 5, c = e & 31;
-      const long long row = srow[q];
-      As[q][c] = (row >= 0 && k0 + c < J.Ka) ? (J.A ? J.A[row * J.lda + k0 + c] : R(1)) : R(0);
-      Bs[q][c] = (row >= 0 && n0 + c < J.Nb) ? J.B[row * J.ldb + n0 + c] : R(0);
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int q = 0; q < 32; ++q) {
-      const R a0 = As[q][2 * ty], a1 = As[q][2 * ty + 1];
-      R b[4];
-      wg_load4(&Bs[q][4 * tx], b);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        acc[0][j] += a0 * b[j];
-        acc[1][j] += a1 * b[j];
+      for (int l = 0; l < 8; ++l) {
+        const int e = tid + 128 * l, q = e >> 5, c = e & 31;
+        const long long row = c0 + q < 256 ? srow[c0 + q] : -1;
+        va[l] = (row >= 0 && k0 + c < J.Ka) ? J.A[row * J.lda + k0 + c] : R(0);
+        vb[l] = (row >= 0 && n0 + c < J.Nb) ? J.B[row * J.ldb + n0 + c] : R(0);
       }
+    };
+    fetch(0);
+    for (int c0 = 0; c0 < s1 - s0; c0 += 32) {
+#pragma unroll
+      for (int l = 0; l < 8; ++l) {
+        const int e = tid + 128 * l, q = e >> 5, c = e & 31;
+        As[q][c] = va[l];
+        Bs[q][c] = vb[l];
+      }
+      __syncthreads();
+      if (c0 + 32 < s1 - s0) fetch(c0 + 32);
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) {
+        const R a0 = As[q][2 * ty], a1 = As[q][2 * ty + 1];
+        R b[4];
+        wg_load4(&Bs[q][4 * tx], b);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[0][j] += a0 * b[j];
+          acc[1][j] += a1 * b[j];
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   double* pj = part + J.part0;
 #pragma unroll
