@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(256) k_linear_bt(const R* __restrict__ X, int 
   __shared__ R As[16][64 + 1];
   __shared__ R Bs[16][64 + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+  const int row0 = blockIdx.x * 64, col0 = blockIdx.y * 64;  // row tiles in x: no 65535 limit
   R acc[4][4];
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) acc[i][j] = 0;
@@ -735,7 +735,7 @@ template <typename R>
 int linear_bt(const R* X, int ldx, const R* W, int ldw, R* Y, int ldy, int rows, int Kd, int Nout, int acc,
               cudaStream_t st) {
   if (rows <= 0) return PN_OK;
-  dim3 grid((Nout + 63) / 64, (rows + 63) / 64);
+  dim3 grid((rows + 63) / 64, (Nout + 63) / 64);
   PN_LAUNCH("k_linear_bt", st, k_linear_bt<R><<<grid, 256, 0, st>>>(X, ldx, W, ldw, Y, ldy, rows, Kd, Nout, acc));
   return PN_OK;
 }

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) k_linear(const R* __restrict__ X, int ldx
   __shared__ R As[16][64 + 1];
   __shared__ R Bs[16][64];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+  const int row0 = blockIdx.x * 64, col0 = blockIdx.y * 64;  // row tiles in x: no 65535 limit
   R acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256) k_linear_v4(const float* __restrict__ X, 
   __shared__ __align__(16) float As[16][128 + 4];
   __shared__ __align__(16) float Bs[16][64];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int row0 = blockIdx.y * 128, col0 = blockIdx.x * 64;
+  const int row0 = blockIdx.x * 128, col0 = blockIdx.y * 64;  // row tiles in x: no 65535 limit
   float acc[8][4];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
@@ -674,14 +674,14 @@ int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw
     const bool v4 = ldx % 4 == 0 && ldw % 4 == 0 && ldy % 4 == 0 && Kd % 4 == 0 && Nout % 4 == 0 &&
                     ((uintptr_t)X & 15) == 0 && ((uintptr_t)W & 15) == 0 && ((uintptr_t)Y & 15) == 0;
     if (v4) {
-      dim3 grid((Nout + 63) / 64, (rows + 127) / 128);
+      dim3 grid((rows + 127) / 128, (Nout + 63) / 64);
       PN_LAUNCH("k_linear", st,
                 k_linear_v4<<<grid, 256, 0, st>>>((const float*)X, ldx, (const float*)W, ldw, (const float*)b,
                                                   (float*)Y, ldy, rows, Kd, Nout, T, acc));
       return PN_OK;
     }
   }
-  dim3 grid((Nout + 63) / 64, (rows + 63) / 64);
+  dim3 grid((rows + 63) / 64, (Nout + 63) / 64);
   PN_LAUNCH("k_linear", st, k_linear<R><<<grid, 256, 0, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, Kd, Nout, T, acc));
   return PN_OK;
 }

@@ -1,0 +1,161 @@
+"""Full-size workloads in the launch configuration the bench times, checked
+against the oracle on sampled walkers it can compute one by one.
+
+Sizes: H2 1024 walkers (FP64 E_loc), Be 4096 walkers (100 Metropolis steps,
+E_loc, clipping and the parameter gradient, mixed and FP64 samplers), H10
+8192 walkers (mixed E_loc and gradient), N2-shaped 16384 walkers (one
+Metropolis sweep, E_loc and gradient, mixed).  The gradient is a sum over
+walkers, so a cotangent that is non-zero only on the sampled walkers makes
+the full-size backward comparable with the oracle's gradient over those
+walkers alone.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import sampling
+from oracle.ansatz import Oracle
+from paper_1909_08423_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SIGMA = 0.2
+
+
+def _sample(W, n, seed):
+    return np.sort(np.random.default_rng(seed).choice(W, size=n, replace=False))
+
+
+def _grad_on_sample(s, r, idx, scale=1.0):
+    """Full-batch gradient with a cotangent non-zero on idx only."""
+    W = r.shape[0]
+    cot = torch.zeros(W, dtype=torch.float64, device="cuda")
+    cot[torch.as_tensor(idx, device="cuda")] = scale
+    g = torch.empty(s.n_params, dtype=torch.float64, device="cuda")
+    s.grad_logpsi(r, cot, g)
+    torch.cuda.synchronize()
+    return g.cpu().numpy()
+
+
+def test_h2_fp64_local_energy_full_batch(lib):
+    sysd = synth.h2()
+    o = Oracle(sysd)
+    W = 1024
+    s = lib.System(sysd, precision=lib.PN_FP64, max_walkers=W)
+    r = torch.empty(W, s.N, 3, dtype=torch.float64, device="cuda")
+    s.init_walkers(r, 1)
+    E = torch.empty(W, dtype=torch.float64, device="cuda")
+    s.eval_local_energy(r, E)
+    torch.cuda.synchronize()
+    idx = _sample(W, 64, 0)
+    Eo, _, _ = o.local_energy(r.cpu().numpy()[idx])
+    np.testing.assert_allclose(E.cpu().numpy()[idx], Eo, rtol=0, atol=1e-8 * (1 + np.abs(Eo)).max())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_be_bench_step_full_size(lib, precision):
+    """4096 Be walkers: 100 Metropolis steps (sigma 0.2), E_loc and the
+    gradient, each launch over the whole batch as in the bench.  FP64: the
+    sampled walkers' chains equal the oracle's exactly.  Mixed (tensor-core
+    sampler): E_loc and ln|psi| of the final walkers within the mixed bound,
+    and at least 90 % of the sampled chains identical to the oracle's."""
+    sysd = synth.be()
+    o = Oracle(sysd)
+    W = 4096
+    s = lib.System(sysd, precision=precision, max_walkers=W)
+    r = torch.empty(W, s.N, 3, dtype=torch.float64, device="cuda")
+    s.init_walkers(r, 1)
+    lp = torch.empty(W, dtype=torch.float64, device="cuda")
+    sg = torch.empty_like(lp)
+    s.eval_logpsi(r, lp, sg)
+    r0, lp0 = r.cpu().numpy().copy(), lp.cpu().numpy().copy()
+    s.metropolis_step(r, lp, 100, SIGMA, 3, 0)
+    E = torch.empty(W, dtype=torch.float64, device="cuda")
+    s.eval_local_energy(r, E)
+    torch.cuda.synchronize()
+    rg, lpg, Eg = r.cpu().numpy(), lp.cpu().numpy(), E.cpu().numpy()
+    idx = _sample(W, 12, 5)
+    same = []
+    for w in idx:
+        ro, lpo, _ = sampling.metropolis(o, r0[w:w + 1], lp0[w:w + 1], 100, SIGMA, seed=3, step0=0, walker0=int(w))
+        same.append(np.all(np.abs(rg[w] - ro[0]) < (1e-9 if precision == 0 else 1e-5)))
+        if precision == 0:
+            np.testing.assert_allclose(rg[w], ro[0], rtol=0, atol=1e-9)
+            np.testing.assert_allclose(lpg[w], lpo[0], rtol=1e-11, atol=1e-10)
+    if precision == 1:
+        assert np.mean(same) >= 0.9
+    Eo, lpo, _ = o.local_energy(rg[idx])
+    tol = 1e-8 * (1 + np.abs(Eo)) if precision == 0 else 1e-4 * np.ones_like(Eo)
+    assert np.all(np.abs(Eg[idx] - Eo) <= tol), np.abs(Eg[idx] - Eo)
+    # gradient over the sampled walkers through the full-size backward
+    gi = _grad_on_sample(s, r, idx)
+    go = o.grad_logpsi(rg[idx], np.ones(len(idx)))
+    if precision == 0:
+        assert np.max(np.abs(gi - go)) <= 1e-9 * np.abs(go).max()
+    else:
+        assert np.linalg.norm(gi - go) / np.linalg.norm(go) < 1e-4
+
+
+def test_h10_mixed_local_energy_and_gradient_full_size(lib):
+    sysd = synth.h10()
+    o = Oracle(sysd)
+    W = 8192
+    s = lib.System(sysd, precision=lib.PN_MIXED, max_walkers=W)
+    r = torch.empty(W, s.N, 3, dtype=torch.float64, device="cuda")
+    s.init_walkers(r, 2)
+    lp = torch.empty(W, dtype=torch.float64, device="cuda")
+    sg = torch.empty_like(lp)
+    s.eval_logpsi(r, lp, sg)
+    s.metropolis_step(r, lp, 60, SIGMA, 4, 0)  # leave the initial cloud
+    E = torch.empty(W, dtype=torch.float64, device="cuda")
+    s.eval_local_energy(r, E)
+    torch.cuda.synchronize()
+    rg, Eg = r.cpu().numpy(), E.cpu().numpy()
+    idx = _sample(W, 10, 6)
+    Eo, _, _ = o.local_energy(rg[idx])
+    err = np.abs(Eg[idx] - Eo)
+    assert err.max() < 1e-3 and np.median(err) < 1e-4, err
+    gi = _grad_on_sample(s, r, idx)
+    go = o.grad_logpsi(rg[idx], np.ones(len(idx)))
+    assert np.linalg.norm(gi - go) / np.linalg.norm(go) < 1e-4
+
+
+def test_n2_mixed_vmc_step_full_size(lib):
+    """16384 N2-shaped walkers, after 30 burn-in sweeps: one Metropolis sweep,
+    E_loc, clipping and the backward, each over the whole batch; sampled
+    walkers against the oracle."""
+    sysd = synth.n2()
+    o = Oracle(sysd)
+    W = 16384
+    s = lib.System(sysd, precision=lib.PN_MIXED, max_walkers=W)
+    r = torch.empty(W, s.N, 3, dtype=torch.float64, device="cuda")
+    s.init_walkers(r, 3)
+    lp = torch.empty(W, dtype=torch.float64, device="cuda")
+    sg = torch.empty_like(lp)
+    s.eval_logpsi(r, lp, sg)
+    s.metropolis_step(r, lp, 30, SIGMA, 5, 1000)
+    torch.cuda.synchronize()
+    r0, lp0 = r.cpu().numpy().copy(), lp.cpu().numpy().copy()
+    s.metropolis_step(r, lp, 1, SIGMA, 5, 0)
+    E = torch.empty(W, dtype=torch.float64, device="cuda")
+    s.eval_local_energy(r, E)
+    Ec = torch.empty_like(E)
+    cot = torch.empty_like(E)
+    from paper_1909_08423_gb300 import binding
+    binding.clip_local_energy(E, Ec, cot)
+    torch.cuda.synchronize()
+    rg, Eg = r.cpu().numpy(), E.cpu().numpy()
+    idx = _sample(W, 3, 7)
+    # the sweep: each sampled walker's move as the oracle makes it
+    moved_same = 0
+    for w in idx:
+        ro, _, _ = sampling.metropolis(o, r0[w:w + 1], lp0[w:w + 1], 1, SIGMA, seed=5, step0=0, walker0=int(w))
+        moved_same += int(np.all(np.abs(rg[w] - ro[0]) < 1e-5))
+    assert moved_same >= len(idx) - 1
+    Eo, _, _ = o.local_energy(rg[idx])
+    assert np.all(np.abs(Eg[idx] - Eo) < 1e-3), np.abs(Eg[idx] - Eo)
+    assert np.all(np.isfinite(Ec.cpu().numpy()))
+    gi = _grad_on_sample(s, r, idx[:2])
+    go = o.grad_logpsi(rg[idx[:2]], np.ones(2))
+    assert np.linalg.norm(gi - go) / np.linalg.norm(go) < 1e-4
