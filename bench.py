@@ -271,6 +271,32 @@ def run_langevin(sysd, W, target=0.57, steps=10):
     return out
 
 
+def run_line_scan(npts=4096):
+    """E_loc along the LiH line scan through both nuclei and both fixed
+    electrons (mixed path), timed with CUDA events."""
+    import torch
+    from paper_1909_08423_gb300 import binding, synth
+    sysd = synth.lih()
+    r0, e, d, t0, t1 = synth.lih_scan()
+    s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=npts)
+    r0d = torch.as_tensor(r0, device="cuda")
+    E = torch.empty(npts, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        s.eval_line_scan(r0d, e, d, t0, t1, npts, E)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.eval_line_scan(r0d, e, d, t0, t1, npts, E)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    En = E.cpu().numpy()
+    s.close()
+    return {"points": npts, "ms": ms, "points_per_s": npts / (ms / 1e3), "system": "LiH-shaped, 4 e, 4 dets",
+            "finite_fraction": float(np.isfinite(En).mean()),
+            "note": "one electron moved along the molecular axis through both nuclei and both fixed electrons"}
+
+
 def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384, load=0.7,
                 precisions=("mixed", "fp64"), sweep=()):
     """Poisson stream of seeded molecules through the serving loop, mixed and
@@ -603,6 +629,7 @@ def main():
         line["cpu_baseline"] = cpu_baseline_sample()
     if rank == 0 and not args.no_langevin:
         line["langevin"] = run_langevin(sysd, W)
+        line["line_scan"] = run_line_scan()
     if rank == 0 and args.serve_jobs > 0:
         line["serve"] = run_serving(args.serve_jobs)
     if rank == 0:

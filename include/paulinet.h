@@ -199,6 +199,21 @@ int pn_metropolis_step(pn_system_t sys, double* r, double* logabs, int W,
 int pn_eval_drift(pn_system_t sys, const double* r, int W, double* logabs,
                   double* drift, void* stream);
 
+/* E_loc, ln|psi| and sign along a line through configuration space
+ * (Results, the one-dimensional scan of the wave function and its local
+ * energy in LiH): point k of npts is the configuration r0 [N][3] with
+ * electron `electron` at r0[electron] + t_k dir, t_k = t0 + k (t1 - t0) /
+ * (npts - 1).  Passing the line through a nucleus or another electron shows
+ * the cusps: with the cusp splice and gamma, E_loc stays finite at the
+ * coalescence points.  r0 is host or device; dir is a HOST array of three
+ * doubles; eloc [npts] (required), logabs, sign [npts] and status [npts]
+ * (may be NULL) are host or device.  Uses the handle's workspace in chunks;
+ * allocates nothing. */
+int pn_eval_line_scan(pn_system_t sys, const double* r0, int electron,
+                      const double* dir, double t0, double t1, int npts,
+                      double* eloc, double* logabs, double* sign, int* status,
+                      void* stream);
+
 /* n_steps Langevin (drift-diffusion) Metropolis-Hastings steps for each
  * walker (Methods, ansatz optimisation: Langevin Monte Carlo after Umrigar
  * et al., its radial proposal replaced by clipping the step length at the
@@ -288,11 +303,14 @@ typedef struct pn_server_cfg {
                                 (result status PN_EDEVICE); 0 = off     */
 } pn_server_cfg;
 
-enum { PN_JOB_ELOC = 0, PN_JOB_SWEEP = 1 };
+enum { PN_JOB_ELOC = 0, PN_JOB_SWEEP = 1, PN_JOB_SCAN = 2 };
 
 typedef struct pn_job {
   int kind;          /* PN_JOB_ELOC: E_loc of the walkers; PN_JOB_SWEEP:
-                        n_steps Metropolis steps, then E_loc            */
+                        n_steps Metropolis steps, then E_loc;
+                        PN_JOB_SCAN: E_loc at W points of a line scan
+                        (pn_eval_line_scan) of the base configuration
+                        r_init [N][3] (required), r_out unused           */
   int W;
   int n_steps;
   double sigma;
@@ -300,6 +318,9 @@ typedef struct pn_job {
   const double* r_init;  /* [W][N][3] host or device, or NULL -> pn_init_walkers */
   double* eloc_out;      /* [W] host or device, or NULL                 */
   double* r_out;         /* [W][N][3] host or device, or NULL           */
+  int scan_electron;     /* PN_JOB_SCAN: the moving electron            */
+  double scan_dir[3];    /* PN_JOB_SCAN: direction of the line          */
+  double scan_t0, scan_t1;  /* PN_JOB_SCAN: first and last parameter  */
 } pn_job;
 
 typedef struct pn_result {

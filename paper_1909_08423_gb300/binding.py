@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libpaulinet.so")
 
 PN_FP64, PN_MIXED = 0, 1
-PN_JOB_ELOC, PN_JOB_SWEEP = 0, 1
+PN_JOB_ELOC, PN_JOB_SWEEP, PN_JOB_SCAN = 0, 1, 2
 PN_OPT_FUSED_SAMPLER, PN_OPT_TENSOR_CORES = 1, 2
 ERRORS = {0: "PN_OK", 1: "PN_EINVAL", 2: "PN_ENOMEM", 3: "PN_EBUDGET", 4: "PN_ENOTREADY",
           5: "PN_ETIMEOUT", 6: "PN_EDEVICE", 7: "PN_ECANCELLED"}
@@ -52,7 +52,8 @@ class ServerCfg(C.Structure):
 class Job(C.Structure):
     _fields_ = [("kind", C.c_int), ("W", C.c_int), ("n_steps", C.c_int), ("sigma", C.c_double),
                 ("seed", C.c_uint64), ("r_init", C.c_void_p), ("eloc_out", C.c_void_p),
-                ("r_out", C.c_void_p)]
+                ("r_out", C.c_void_p), ("scan_electron", C.c_int), ("scan_dir", C.c_double * 3),
+                ("scan_t0", C.c_double), ("scan_t1", C.c_double)]
 
 
 class Result(C.Structure):
@@ -77,6 +78,8 @@ EXPORTS = {
                                      C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]),
     "pn_init_walkers": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_uint64, C.c_void_p]),
     "pn_eval_drift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pn_eval_line_scan": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.c_double, C.c_int,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pn_langevin_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
                                    C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]),
     "pn_grad_logpsi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t,
@@ -244,6 +247,11 @@ class System:
     def eval_drift(self, r, drift, logabs=None):
         check(load().pn_eval_drift(self.h, _ptr(r), r.shape[0], _ptr(logabs), _ptr(drift), _stream(r)))
 
+    def eval_line_scan(self, r0, electron, direction, t0, t1, npts, eloc, logabs=None, sign=None, status=None):
+        d = np.ascontiguousarray(np.asarray(direction, dtype=np.float64).reshape(3))
+        check(load().pn_eval_line_scan(self.h, _ptr(r0), int(electron), d.ctypes.data, float(t0), float(t1),
+                                       int(npts), _ptr(eloc), _ptr(logabs), _ptr(sign), _ptr(status), _stream(eloc)))
+
     def langevin_step(self, r, logabs, drift, n_steps, tau, seed, step0, n_accept=None):
         check(load().pn_langevin_step(self.h, _ptr(r), _ptr(logabs), _ptr(drift), r.shape[0], n_steps, float(tau),
                                       int(seed), int(step0), _ptr(n_accept), _stream(r)))
@@ -272,8 +280,10 @@ class Server:
         self.h = h
         self._keep = {}
 
-    def submit(self, system, kind, W, n_steps=0, sigma=0.2, seed=0, r_init=None, eloc_out=None, r_out=None):
-        j = Job(kind, int(W), int(n_steps), float(sigma), int(seed), _ptr(r_init), _ptr(eloc_out), _ptr(r_out))
+    def submit(self, system, kind, W, n_steps=0, sigma=0.2, seed=0, r_init=None, eloc_out=None, r_out=None,
+               scan_electron=0, scan_dir=(1.0, 0.0, 0.0), scan_t0=0.0, scan_t1=1.0):
+        j = Job(kind, int(W), int(n_steps), float(sigma), int(seed), _ptr(r_init), _ptr(eloc_out), _ptr(r_out),
+                int(scan_electron), (C.c_double * 3)(*[float(x) for x in scan_dir]), float(scan_t0), float(scan_t1))
         jid = C.c_uint64()
         check(load().pn_submit(self.h, system.h, C.byref(j), C.byref(jid)))
         self._keep[jid.value] = (r_init, eloc_out, r_out)

@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "kernels.cuh"
 #include "pn_internal.cuh"
@@ -135,6 +136,19 @@ __global__ void k_langevin_accept(DevSys s, double* __restrict__ r, double* __re
     lp[w] = lpp[w];
     atomicAdd(n_acc, 1ull);
   }
+}
+
+// Configurations of a line scan: every point is the base configuration r0
+// [N][3] with electron e moved to r0[e] + (t0 + (k0 + k) dt) dir.
+__global__ void k_line_positions(const double* __restrict__ r0, int N, int e, double dx, double dy, double dz, double t0,
+                                 double dt, int k0, int n, double* __restrict__ r) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double tk = t0 + (double)(k0 + k) * dt;
+  for (int m = 0; m < 3 * N; ++m) r[(size_t)k * 3 * N + m] = r0[m];
+  r[(size_t)k * 3 * N + 3 * e] = r0[3 * e] + tk * dx;
+  r[(size_t)k * 3 * N + 3 * e + 1] = r0[3 * e + 1] + tk * dy;
+  r[(size_t)k * 3 * N + 3 * e + 2] = r0[3 * e + 2] + tk * dz;
 }
 
 // electron e at R[nuc(e)] + normal, normals at step 2^64 - 1.
@@ -431,6 +445,38 @@ template int pn_run_langevin<double>(const DevSys&, const DevNet<double>&, Work<
 template int pn_run_langevin<float>(const DevSys&, const DevNet<float>&, Work<float>&, int, double*, double*, double*,
                                     int, int, double, unsigned long long, unsigned long long, int64_t*, cudaStream_t);
 
+// E_loc, ln|psi| and sign along a line: npts points t0 .. t1 (inclusive) of
+// electron e's position r0[e] + t dir, in workspace chunks.  r0 is staged in
+// the workspace's proposal buffer, so nothing is allocated.
+template <typename R>
+int pn_run_line_scan(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, const double* r0, int e,
+                     const double dir[3], double t0, double t1, int npts, double* eloc, double* logabs, double* sign,
+                     int* status, cudaStream_t st) {
+  const int N = ds.N;
+  PN_CUDA(cudaMemcpyAsync(w.r_prop, r0, (size_t)N * 3 * 8, cudaMemcpyDefault, st));
+  const double dt = npts > 1 ? (t1 - t0) / (double)(npts - 1) : 0.0;
+  for (int c0 = 0; c0 < npts; c0 += Wc) {
+    const int Wn = std::min(Wc, npts - c0);
+    PN_LAUNCH("k_line_positions", st,
+              k_line_positions<<<nblk(Wn, 128), 128, 0, st>>>(w.r_prop, N, e, dir[0], dir[1], dir[2], t0, dt, c0, Wn,
+                                                              w.r));
+    if (int er = pn_forward_chunk<R>(ds, net, w, w.r, Wn, 1, st)) return er;
+    if (eloc) PN_CUDA(cudaMemcpyAsync(eloc + c0, w.out_eloc, Wn * 8, cudaMemcpyDefault, st));
+    if (logabs) PN_CUDA(cudaMemcpyAsync(logabs + c0, w.out_logabs, Wn * 8, cudaMemcpyDefault, st));
+    if (sign) PN_CUDA(cudaMemcpyAsync(sign + c0, w.out_sign, Wn * 8, cudaMemcpyDefault, st));
+    if (status) PN_CUDA(cudaMemcpyAsync(status + c0, w.out_status, Wn * 4, cudaMemcpyDefault, st));
+  }
+  if (is_host(eloc) || is_host(logabs) || is_host(sign) || is_host(status) || !pn_is_device_ptr(r0))
+    PN_CUDA(cudaStreamSynchronize(st));
+  return PN_OK;
+}
+template int pn_run_line_scan<double>(const DevSys&, const DevNet<double>&, Work<double>&, int, const double*, int,
+                                      const double[3], double, double, int, double*, double*, double*, int*,
+                                      cudaStream_t);
+template int pn_run_line_scan<float>(const DevSys&, const DevNet<float>&, Work<float>&, int, const double*, int,
+                                     const double[3], double, double, int, double*, double*, double*, int*,
+                                     cudaStream_t);
+
 int pn_run_init_walkers(const DevSys& ds, double* r, int W, unsigned long long seed, cudaStream_t st) {
   PN_LAUNCH("k_init_walkers", st, k_init_walkers<<<nblk(W, 128), 128, 0, st>>>(ds, ds.nuc, r, W, seed));
   return PN_OK;
@@ -531,6 +577,25 @@ extern "C" int pn_langevin_step(pn_system_t s, double* r, double* logabs, double
                                        n_steps, tau, seed, step0, n_accept, st)
              : pn_run_langevin<float>(s->ds, pn_devnet<float>(s), work_of<float>(s), s->Wc, r, logabs, drift, W,
                                       n_steps, tau, seed, step0, n_accept, st);
+}
+
+extern "C" int pn_eval_line_scan(pn_system_t s, const double* r0, int electron, const double* dir, double t0,
+                                 double t1, int npts, double* eloc, double* logabs, double* sign, int* status,
+                                 void* stream) {
+  PN_SYS_CHECK(s);
+  if (npts < 0 || (npts > 0 && (!r0 || !dir || !eloc)) || electron < 0 || electron >= s->ds.N ||
+      !std::isfinite(t0) || !std::isfinite(t1)) {
+    pn_set_error("bad arguments");
+    return PN_EINVAL;
+  }
+  if (npts == 0) return PN_OK;
+  double d[3] = {dir[0], dir[1], dir[2]};  // dir is a host array
+  cudaStream_t st = (cudaStream_t)stream;
+  return s->precision == PN_FP64
+             ? pn_run_line_scan<double>(s->ds, pn_devnet<double>(s), work_of<double>(s), s->Wc, r0, electron, d, t0,
+                                        t1, npts, eloc, logabs, sign, status, st)
+             : pn_run_line_scan<float>(s->ds, pn_devnet<float>(s), work_of<float>(s), s->Wc, r0, electron, d, t0, t1,
+                                       npts, eloc, logabs, sign, status, st);
 }
 
 extern "C" int pn_init_walkers(pn_system_t s, double* r, int W, uint64_t seed, void* stream) {

@@ -239,6 +239,10 @@ template <typename R>
 int pn_run_metropolis(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, double* r, double* logabs, int W,
                       int n_steps, double sigma, unsigned long long seed, unsigned long long step0, int64_t* n_accept,
                       cudaStream_t st);
+template <typename R>
+int pn_run_line_scan(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, const double* r0, int e,
+                     const double dir[3], double t0, double t1, int npts, double* eloc, double* logabs, double* sign,
+                     int* status, cudaStream_t st);
 int pn_run_init_walkers(const DevSys& ds, double* r, int W, unsigned long long seed, cudaStream_t st);
 // Tensor-core sampler (sampler_tc.cu): PN_ENOTREADY if the system's tiles do not fit.
 int pn_run_metropolis_tc(const DevSys& s, const DevNet<float>& net, double* r, double* lp, int W, unsigned walker0,

@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -140,6 +141,19 @@ static int launch_job(pn_server_s* srv, Slot& sl, JobRec& j) {
   int* stat = (int*)p; p += align256((size_t)W * 4);
   double* stats = (double*)p;
   const DevNet<R> net = pn_devnet<R>(s);
+  if (j.job.kind == PN_JOB_SCAN) {
+    // E_loc along the line; the configurations live only in the workspace
+    if (int e = pn_run_line_scan<R>(ds, net, w, Wc, j.job.r_init, j.job.scan_electron, j.job.scan_dir, j.job.scan_t0,
+                                    j.job.scan_t1, W, E, nullptr, nullptr, stat, st))
+      return e;
+    PN_LAUNCH("k_job_stats", st, k_job_stats<<<1, 256, 0, st>>>(E, stat, W, nullptr, stats));
+    PN_CUDA(cudaMemcpyAsync(sl.stats_host, stats, 4 * 8, cudaMemcpyDeviceToHost, st));
+    if (j.job.eloc_out) PN_CUDA(cudaMemcpyAsync(j.job.eloc_out, E, (size_t)W * 8, cudaMemcpyDefault, st));
+    PN_CUDA(cudaFreeAsync(j.mem, st));
+    j.mem = nullptr;
+    PN_CUDA(cudaEventRecord(sl.done, st));
+    return PN_OK;
+  }
   if (j.job.r_init)
     PN_CUDA(cudaMemcpyAsync(r, j.job.r_init, (size_t)W * ds.N * 3 * 8, cudaMemcpyDefault, st));
   else if (int e = pn_run_init_walkers(ds, r, W, j.job.seed, st))
@@ -304,7 +318,10 @@ extern "C" int pn_server_destroy(pn_server_t srv) {
 
 extern "C" int pn_submit(pn_server_t srv, pn_system_t sys, const pn_job* job, uint64_t* job_id) {
   if (!srv || !sys || !job || !job_id || job->W < 1 || job->n_steps < 0 ||
-      (job->kind != PN_JOB_ELOC && job->kind != PN_JOB_SWEEP) || (job->kind == PN_JOB_SWEEP && !(job->sigma > 0))) {
+      (job->kind != PN_JOB_ELOC && job->kind != PN_JOB_SWEEP && job->kind != PN_JOB_SCAN) ||
+      (job->kind == PN_JOB_SWEEP && !(job->sigma > 0)) ||
+      (job->kind == PN_JOB_SCAN && (!job->r_init || job->scan_electron < 0 || job->scan_electron >= sys->ds.N ||
+                                    !std::isfinite(job->scan_t0) || !std::isfinite(job->scan_t1)))) {
     pn_set_error("submit: bad job");
     return PN_EINVAL;
   }

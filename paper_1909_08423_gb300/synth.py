@@ -253,6 +253,24 @@ def n2(seed=0):
                        lambda z: {0: 4, 1: 4, 2: 2}, n_det=32, D=128, K=32, L=4, seed=seed)
 
 
+def lih(seed=0, use_cusp=1, use_gamma=1):
+    """LiH-shaped: Li (Z=3) at the origin and H at 3.015 bohr on the x axis,
+    2 up 2 down electrons, 4 determinants; Li 4s2p shells, H 3 s shells; D=64,
+    L=3, K=32."""
+    return make_system([3.0, 1.0], [[0, 0, 0], [3.015, 0, 0]], lambda z: {0: 4, 1: 2} if z >= 3 else _spec_h(z),
+                       n_det=4, D=64, K=32, L=3, seed=seed, use_cusp=use_cusp, use_gamma=use_gamma)
+
+
+def lih_scan():
+    """The one-dimensional scan of the LiH results: on the x axis, from the
+    left, the Li nucleus, a spin-up electron (x = 1.0), a spin-down electron
+    (x = 2.0) and the H nucleus; the second spin-down electron off the axis;
+    the second spin-up electron (index 1, electrons are ordered up first) moves
+    along x.  Returns (r0 [4][3], electron, direction, t0, t1)."""
+    r0 = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 0.0], [2.0, 0.0, 0.0], [1.1, 1.3, 0.6]])
+    return r0, 1, np.array([1.0, 0.0, 0.0]), -1.5, 4.5
+
+
 WORKLOADS = {
     "h2": dict(make=h2, W=1024),
     "be": dict(make=be, W=4096, n_steps=100, sigma=0.2),

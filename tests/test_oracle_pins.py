@@ -420,6 +420,35 @@ def test_clipped_drift_never_passes_a_nucleus():
     np.testing.assert_allclose(c[short], 0.5 * g[short], rtol=0, atol=0)
 
 
+def _lih_scan_eloc(o, xs):
+    r0, e, d, _, _ = synth.lih_scan()
+    r = np.repeat(r0[None], len(xs), 0).copy()
+    r[:, e, :] = r0[e] + np.asarray(xs, dtype=float)[:, None] * d
+    return o.local_energy(r)[0]
+
+
+def test_lih_scan_local_energy_through_coalescences():
+    """The LiH scan (Results, one-dimensional scan): with the nuclear cusp
+    splice and the electronic cusp factor gamma, E_loc of the moving electron
+    converges at the Li nucleus and at the opposite-spin electron.  Without
+    the splice it diverges like -Z/delta at the nucleus, and without gamma like
+    +1/delta at the electron: the cusps, not the network, remove those poles."""
+    deltas = np.array([1e-2, 1e-3, 1e-4])
+    on = Oracle(synth.lih())
+    for centre in (0.0, 2.0):
+        for side in (1.0, -1.0):
+            E = _lih_scan_eloc(on, centre + side * deltas)
+            assert np.all(np.isfinite(E))
+            assert abs(E[2] - E[1]) < abs(E[1] - E[0]) + 1e-9  # contracting: a limit exists
+            assert abs(E[2] - E[1]) < 0.1 * max(1.0, abs(E[1]))
+    no_cusp = Oracle(synth.lih(use_cusp=0))
+    E = _lih_scan_eloc(no_cusp, deltas)
+    assert abs(E[2] * deltas[2] + 3.0) < 0.01  # E_loc ~ -Z / delta, Z = 3
+    no_gamma = Oracle(synth.lih(use_gamma=0))
+    E = _lih_scan_eloc(no_gamma, 2.0 + deltas)
+    assert abs(E[2] * deltas[2] - 1.0) < 0.01  # E_loc ~ +1 / delta
+
+
 # ----------------------------------------------------------------- clipping
 
 def test_clipping_window_and_smoothness():
