@@ -18,6 +18,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -512,8 +513,10 @@ def main():
     lib.pn_profile_kernel(None)
     dom = max(share, key=lambda k: share[k][1])
 
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/pn_clocks_{rank}.csv"
+    # nvidia-smi samples of the timed region: PN_CLOCK_LOG names the file to
+    # keep them in (rank appended), else a temporary file
+    clk_path = os.environ.get("PN_CLOCK_LOG")
+    clk_path = f"{clk_path}.rank{rank}" if clk_path else os.path.join(tempfile.gettempdir(), f"pn_clocks_{rank}.csv")
     sampler = _clock_sampler(clk_path)
     ms, launches, kern = timed(mixed, args.steps, 0, prof_kernel=dom)
     if sampler:

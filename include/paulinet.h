@@ -123,6 +123,12 @@ typedef struct pn_system_desc {
   int use_cusp, use_gamma;
   int precision;             /* PN_FP64 | PN_MIXED */
   int max_walkers;           /* workspace chunk (walkers) */
+  /* Ablation variants of the ansatz (Results, the comparison of single and
+   * multiple determinants with and without backflow): no_jastrow = 1 removes
+   * the Jastrow factor (J = 0), no_backflow = 1 the backflow (f = 1).  The
+   * removed head's parameters stay in the layout; its last map is held at
+   * zero on the device and its gradient entries are returned as zero. */
+  int no_jastrow, no_backflow;
 } pn_system_desc;
 
 /* Number of network parameters for the given sizes (layout above). */

@@ -13,7 +13,7 @@ walkers only:
   E_loc = -1/2 (lap ln|psi| + |grad ln|psi||^2) + V      Eq. (monte-carlo)
   grad_theta L = 2 E[(E_loc - L) grad_theta ln|psi|]     Eq. (trainig)
 
-Readings of points the paper leaves open (all recorded in the design doc):
+Readings of points the paper leaves open:
 q_k = k/(K+1) (open interval); shifted softplus activation; hidden widths
 max(d_in, d_out); biases on every linear map; no activation after a last
 layer; f = 1 + kappa(x); one x0 for all electrons; c_ij = 1/4 same spin,
@@ -198,10 +198,16 @@ def network(sys, P, r):
                          (P[f"w{n}.nuc.W2"], P[f"w{n}.nuc.b2"])])          # [W,N,M,Zd]
         z["nuc"] = (wn * P["Y"][None, None]).sum(2)
         x = x + sum(z[c] @ P[f"g{n}.{c}.W"] + P[f"g{n}.{c}.b"] for c in ("same", "anti", "nuc"))
+    # ablation variants (Results, single/multiple determinants with and
+    # without backflow): a removed head is J = 0 or f = 1
     J = _mlp(x.sum(1), [(P["eta.W1"], P["eta.b1"]), (P["eta.W2"], P["eta.b2"]),
                         (P["eta.W3"], P["eta.b3"])])[..., 0]
     f = 1.0 + _mlp(x, [(P["kappa.W1"], P["kappa.b1"]), (P["kappa.W2"], P["kappa.b2"]),
                        (P["kappa.W3"], P["kappa.b3"])])
+    if sys.get("no_jastrow", 0):
+        J = torch.zeros_like(J)
+    if sys.get("no_backflow", 0):
+        f = torch.ones_like(f)
     return J, f
 
 
@@ -317,7 +323,8 @@ class Oracle(Model):
         layout of ``synth.param_shapes``."""
         P = params_to_torch(self.sys, requires_grad=True)
         lp, _ = self.logpsi(_t(r), P)
-        (lp * _t(cot)).sum().backward()
+        if lp.requires_grad:  # else no parameter enters psi (every head removed, gamma off)
+            (lp * _t(cot)).sum().backward()
         shapes = synth.param_shapes(self.sys["D"], self.sys["Zd"], self.sys["K"], self.sys["L"],
                                     len(self.sys["Z"]), self.sys["mo_coeffs"].shape[1])
         # parameters that do not enter (e.g. same-spin filters with one

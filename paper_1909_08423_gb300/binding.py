@@ -41,6 +41,7 @@ class SystemDesc(C.Structure):
         ("cusp_phi0", C.c_void_p),
         ("use_cusp", C.c_int), ("use_gamma", C.c_int),
         ("precision", C.c_int), ("max_walkers", C.c_int),
+        ("no_jastrow", C.c_int), ("no_backflow", C.c_int),
     ]
 
 
@@ -200,6 +201,7 @@ class System:
         d.params, d.n_params = k["params"].ctypes.data, len(k["params"])
         d.cusp_phi0 = None if k["phi0"] is None else k["phi0"].ctypes.data
         d.use_cusp, d.use_gamma = int(sysd["use_cusp"]), int(sysd["use_gamma"])
+        d.no_jastrow, d.no_backflow = int(sysd.get("no_jastrow", 0)), int(sysd.get("no_backflow", 0))
         d.precision, d.max_walkers = precision, max_walkers
         self._desc = d
         h = C.c_void_p()

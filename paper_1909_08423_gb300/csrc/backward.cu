@@ -928,6 +928,11 @@ static int grad_impl(pn_system_s* sys, const double* r, int W, const double* cot
     PN_CUDA(cudaMemcpyAsync(t.u, cot + c0, (size_t)Wn * 8, udev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     if (int e = grad_chunk<R>(s, net, t, rc, t.u, Wn, gd, st)) return e;
   }
+  // ablation variants: a removed head is not part of the model
+  const NetOff& o = sys->off;
+  if (sys->no_jastrow) PN_CUDA(cudaMemsetAsync(gd + o.eW[0], 0, (size_t)(o.eb[2] + 1 - o.eW[0]) * 8, st));
+  if (sys->no_backflow)
+    PN_CUDA(cudaMemsetAsync(gd + o.kW[0], 0, (size_t)(o.kb[2] + s.n_orb - o.kW[0]) * 8, st));
   if (!gdev) {
     PN_CUDA(cudaMemcpyAsync(grad, gd, (size_t)sys->off.total * 8, cudaMemcpyDeviceToHost, st));
     PN_CUDA(cudaFreeAsync(gd, st));

@@ -185,6 +185,7 @@ struct pn_system_s {
   DevSys ds;
   NetOff off;
   int precision;
+  int no_jastrow, no_backflow;  // ablation variants: head removed
   int Wc;
   int Tjet;
   // device allocations

@@ -264,10 +264,16 @@ template Work<double> pn_carve_work<double>(const DevSys&, int, int, void*);
 template Work<float> pn_carve_work<float>(const DevSys&, int, int, void*);
 
 // ----------------------------------------------------------- parameters
-static int upload_params(pn_system_s* s, const double* hp) {
+static int upload_params(pn_system_s* s, const double* hp_user) {
   const DevSys& d = s->ds;
   const NetOff& o = s->off;
-  s->h_params.assign(hp, hp + o.total);
+  s->h_params.assign(hp_user, hp_user + o.total);
+  // ablation variants: the removed head's last map is zero, so that every
+  // kernel computes J = 0 or f = 1 exactly
+  std::vector<double> masked(hp_user, hp_user + o.total);
+  if (s->no_jastrow) std::fill(masked.begin() + o.eW[2], masked.begin() + o.eb[2] + 1, 0.0);
+  if (s->no_backflow) std::fill(masked.begin() + o.kW[2], masked.begin() + o.kb[2] + d.n_orb, 0.0);
+  const double* hp = masked.data();
   PN_CUDA(cudaMemcpy(s->p64, hp, o.total * 8, cudaMemcpyHostToDevice));
   std::vector<float> p32(hp, hp + o.total);
   PN_CUDA(cudaMemcpy(s->p32, p32.data(), o.total * 4, cudaMemcpyHostToDevice));
@@ -559,6 +565,8 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   cudaGetDevice(&s->device);
   s->off = off;
   s->precision = d->precision;
+  s->no_jastrow = d->no_jastrow ? 1 : 0;
+  s->no_backflow = d->no_backflow ? 1 : 0;
   DevSys& ds = s->ds;
   ds.N = N; ds.n_up = d->n_up; ds.n_dn = d->n_dn; ds.M = d->M; ds.n_b = nb; ds.n_orb = d->n_orb;
   ds.n_det = d->n_det; ds.n_shells = d->n_shells;

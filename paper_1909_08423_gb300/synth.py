@@ -17,6 +17,7 @@ A system is a plain dict of numpy arrays:
   n_up, n_dn, occ_up [n_det, n_up] i32, occ_dn [n_det, n_dn] i32, ci [n_det] f64
   net: D, Zd, K, L, r_c                  network sizes (Table 2 of the paper)
   params: dict name -> array             network weights (see ``param_shapes``)
+  no_jastrow, no_backflow                ablation switches (J = 0 / f = 1)
   use_cusp, use_gamma                    switches for the nuclear cusp correction
                                          and the electronic cusp factor
 
@@ -168,7 +169,7 @@ def _determinants(rng, n_det, n_up, n_dn, n_orb):
 
 
 def make_system(Z, R, atom_spec, n_det, D, K, L, seed, r_c=10.0, Zd=None,
-                n_orb=None, n_up=None, n_dn=None, use_cusp=1, use_gamma=1):
+                n_orb=None, n_up=None, n_dn=None, use_cusp=1, use_gamma=1, no_jastrow=0, no_backflow=0):
     """Seeded neutral system.  atom_spec(Z_I) -> {l: n_shells}."""
     rng = np.random.default_rng(seed)
     Z = np.asarray(Z, dtype=np.float64)
@@ -189,7 +190,7 @@ def make_system(Z, R, atom_spec, n_det, D, K, L, seed, r_c=10.0, Zd=None,
     occ_up, occ_dn, ci = _determinants(rng, n_det, n_up, n_dn, n_orb)
     sysd.update(n_up=n_up, n_dn=n_dn, occ_up=occ_up, occ_dn=occ_dn, ci=ci,
                 D=D, Zd=Zd, K=K, L=L, r_c=float(r_c), use_cusp=int(use_cusp),
-                use_gamma=int(use_gamma), cusp_phi0=None)
+                use_gamma=int(use_gamma), cusp_phi0=None, no_jastrow=int(no_jastrow), no_backflow=int(no_backflow))
     sysd["params"] = random_params(rng, D, Zd, K, L, len(Z), n_orb)
     return sysd
 

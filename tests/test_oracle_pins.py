@@ -449,6 +449,36 @@ def test_lih_scan_local_energy_through_coalescences():
     assert abs(E[2] * deltas[2] - 1.0) < 0.01  # E_loc ~ +1 / delta
 
 
+def test_ablation_without_jastrow_and_backflow_is_the_determinant_sum():
+    """no_jastrow and no_backflow with gamma off leave
+    psi = sum_p c_p det[phi(r_up)]_p det[phi(r_dn)]_p (Eq. ansatz with J = 0,
+    f = 1), checked against numpy determinants of the orbital matrices; the
+    removed heads get zero gradient."""
+    S = synth.make_system([4.0], [[0, 0, 0]], lambda z: {0: 4, 1: 2}, n_det=4, D=32, K=16, L=2, seed=7,
+                          use_gamma=0, no_jastrow=1, no_backflow=1)
+    o = Oracle(S)
+    r = _pts(16, 4, seed=8)
+    lp, sg = o.eval_logpsi(r)
+    import torch as _torch
+    phi = o.orbitals(_torch.as_tensor(r)).numpy()
+    nu = S["n_up"]
+    psi = np.zeros(len(r))
+    for p, c in enumerate(S["ci"]):
+        du = np.linalg.det(phi[:, :nu][:, :, S["occ_up"][p]])
+        dd = np.linalg.det(phi[:, nu:][:, :, S["occ_dn"][p]])
+        psi += c * du * dd
+    np.testing.assert_allclose(lp, np.log(np.abs(psi)), rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(sg, np.sign(psi))
+    g = o.grad_logpsi(r, np.ones(len(r)))
+    sh = synth.param_shapes(S["D"], S["Zd"], S["K"], S["L"], len(S["Z"]), S["mo_coeffs"].shape[1])
+    off = 0
+    for name, shape in sh:
+        n = int(np.prod(shape))
+        if name.startswith("eta.") or name.startswith("kappa."):
+            assert np.all(g[off:off + n] == 0), name
+        off += n
+
+
 # ----------------------------------------------------------------- clipping
 
 def test_clipping_window_and_smoothness():
