@@ -479,6 +479,26 @@ def test_ablation_without_jastrow_and_backflow_is_the_determinant_sum():
         off += n
 
 
+def test_adamw_closed_forms():
+    """With zero moments the first AdamW step moves every parameter by
+    lr (g / (|g| + eps) + wd theta); with a constant gradient the bias
+    corrections make every later step the same size.  Weight decay alone
+    (g = 0) shrinks theta by the factor 1 - lr wd."""
+    from oracle import optim
+    rng = np.random.default_rng(3)
+    th, g = rng.normal(size=50), rng.normal(size=50)
+    lr, wd, eps = 0.01, 0.05, 1e-8
+    m = v = np.zeros(50)
+    x = th
+    for t in range(1, 6):
+        xn, m, v = optim.adamw_step(x, g, m, v, t, lr, wd=wd, eps=eps)
+        np.testing.assert_allclose(xn, x - lr * (g / (np.abs(g) + eps) + wd * x), rtol=1e-12, atol=1e-15)
+        x = xn
+    xz, _, _ = optim.adamw_step(th, np.zeros(50), np.zeros(50), np.zeros(50), 1, lr, wd=wd, eps=eps)
+    np.testing.assert_allclose(xz, th * (1 - lr * wd), rtol=1e-15)
+    assert optim.learning_rate(200, 0.01, 200) == 0.005
+
+
 # ----------------------------------------------------------------- clipping
 
 def test_clipping_window_and_smoothness():
