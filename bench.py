@@ -298,6 +298,33 @@ def run_line_scan(npts=4096):
             "note": "one electron moved along the molecular axis through both nuclei and both fixed electrons"}
 
 
+def run_vmc_train(sysd, steps=10):
+    """The paper's training configuration (batch 10000, 2000 walkers, pool
+    refilled every 100 steps after 50 discarded steps) on the bench system:
+    one optimisation step (clipped loss gradient on the batch, AdamW, new
+    parameters uploaded) and one pool refill, timed separately."""
+    import torch
+    from paper_1909_08423_gb300 import binding, synth
+    from paper_1909_08423_gb300.vmc import VMCTrainer
+    s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=10000)
+    tr = VMCTrainer(s, synth.flatten_params(sysd), walkers=2000, batch=10000, resample_period=100, n_discard=50,
+                    n_decorr=1, seed=11)
+    tr.step()  # first pool and one step
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = [tr.step() for _ in range(steps)]
+    torch.cuda.synchronize()
+    step_ms = (time.perf_counter() - t0) * 1e3 / steps
+    t0 = time.perf_counter()
+    tr.resample()
+    torch.cuda.synchronize()
+    refill_ms = (time.perf_counter() - t0) * 1e3
+    s.close()
+    return {"batch": 10000, "walkers": 2000, "train_step_ms": step_ms, "pool_refill_ms": refill_ms,
+            "amortized_step_ms": step_ms + refill_ms / 100, "e_mean_last": hist[-1]["e_mean"],
+            "note": "host-timed (the parameter upload synchronises); refill = 50 + 500 Metropolis steps of 2000 walkers"}
+
+
 def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384, load=0.7,
                 precisions=("mixed", "fp64"), sweep=()):
     """Poisson stream of seeded molecules through the serving loop, mixed and
@@ -633,6 +660,7 @@ def main():
     if rank == 0 and not args.no_langevin:
         line["langevin"] = run_langevin(sysd, W)
         line["line_scan"] = run_line_scan()
+        line["vmc_train"] = run_vmc_train(sysd)
     if rank == 0 and args.serve_jobs > 0:
         line["serve"] = run_serving(args.serve_jobs)
     if rank == 0:

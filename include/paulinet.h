@@ -300,6 +300,19 @@ int pn_clip_local_energy(const double* eloc, int W, double q, double* out,
  */
 typedef struct pn_server_s* pn_server_t;
 
+/* One AdamW step for VMC training (Methods, ansatz optimisation: Adam with
+ * decoupled weight decay after Loshchilov and Hutter, the total energy as
+ * the loss, Eq. trainig for its gradient):
+ *   m <- b1 m + (1 - b1) g;  v <- b2 v + (1 - b2) g^2;
+ *   theta <- theta - lr (m / (1 - b1^t) / (sqrt(v / (1 - b2^t)) + eps)
+ *                        + weight_decay theta).
+ * theta, grad, m, v: n float64 DEVICE buffers (m and v start at zero and
+ * are updated in place); t >= 1 is the step count.  Asynchronous on the
+ * stream; PN_EINVAL for host buffers or out-of-range hyperparameters. */
+int pn_adamw_step(double* theta, const double* grad, double* m, double* v,
+                  int64_t n, double lr, double beta1, double beta2, double eps,
+                  double weight_decay, int64_t t, void* stream);
+
 typedef struct pn_server_cfg {
   size_t hbm_budget_bytes;   /* total device memory the server may hold */
   int n_slots;               /* concurrent jobs (one stream each)       */

@@ -78,6 +78,8 @@ EXPORTS = {
     "pn_metropolis_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
                                      C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]),
     "pn_init_walkers": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_uint64, C.c_void_p]),
+    "pn_adamw_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_double,
+                                C.c_double, C.c_double, C.c_double, C.c_int64, C.c_void_p]),
     "pn_eval_drift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pn_eval_line_scan": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.c_double, C.c_int,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -318,6 +320,12 @@ class Server:
 
 def job_footprint(system, W, chunk_walkers):
     return load().pn_job_footprint(system.h, int(W), int(chunk_walkers))
+
+
+def adamw_step(theta, grad, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.01):
+    """One AdamW step on device float64 tensors (pn_adamw_step)."""
+    check(load().pn_adamw_step(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), int(theta.numel()), float(lr), float(beta1),
+                               float(beta2), float(eps), float(weight_decay), int(t), _stream(theta)))
 
 
 def clip_local_energy(eloc, out, cot=None, q=5.0):
