@@ -131,3 +131,27 @@ def test_descriptions_beyond_a_maximum_are_rejected(lib, what):
         binding.System(sysd)
     assert e.value.code == 1
     assert "outside" in str(e.value) or "range" in str(e.value), str(e.value)
+
+
+@pytest.mark.parametrize("fused", [4, 1])
+def test_one_electron_sampler_density(lib, fused):
+    """The mixed samplers (tensor-core and warp kernels) on the hydrogen atom,
+    one electron and no electron pairs: 16384 walkers reproduce the moments
+    <r> = 3/2 and <r^2> = 3 of |psi|^2 = exp(-2r)."""
+    S = synth.hydrogen_like_sto(1.0, 1.0)
+    s = lib.System(S, precision=lib.PN_MIXED, max_walkers=16384)
+    s.set_option(lib.PN_OPT_FUSED_SAMPLER, fused)
+    W = 16384
+    r = torch.empty(W, 1, 3, dtype=torch.float64, device="cuda")
+    s.init_walkers(r, 5)
+    lp = torch.empty(W, dtype=torch.float64, device="cuda")
+    sg = torch.empty_like(lp)
+    s.eval_logpsi(r, lp, sg)
+    s.metropolis_step(r, lp, 100, 0.5, 5, 0)
+    rs = []
+    for b in range(4):
+        s.metropolis_step(r, lp, 10, 0.5, 5, 100 + 10 * b)
+        rs.append(torch.linalg.norm(r[:, 0], dim=-1).cpu().numpy())
+    rs = np.concatenate(rs)
+    assert abs(rs.mean() - 1.5) < 0.02
+    assert abs((rs ** 2).mean() - 3.0) < 0.08
