@@ -630,6 +630,14 @@ def main():
                     "note": "algorithmic float32 network FLOPs of the launches timed; the sampler also "
                             "runs float64 determinants and log-sums"}
             if dom == "k_metropolis_tc":
+                # DRAM bytes of one launch over these 4096 walkers, from an ncu
+                # capture (dram__bytes_read.sum + dram__bytes_write.sum, 5-step
+                # launch): positions, log-amplitudes and the first read of the
+                # weights; it does not grow with the step count (the weights
+                # stay in L2, the walker state in shared memory)
+                roof["traffic"] = 1.13e6
+                roof["traffic_note"] = ("ncu, one k_metropolis_tc launch on the same 4096 walkers (5 steps); "
+                                        "independent of the step count")
                 ex = tc_sampler_executed_flops(sysd, W) * N_METROPOLIS
                 ex_tf = ex / (kern_ms_per_step / 1e3) / 1e12
                 bf16 = peaks.get("bf16_tflops", 1900.0)

@@ -213,9 +213,12 @@ __global__ void __launch_bounds__(256) k_linear(const R* __restrict__ X, int ldx
 }
 
 // Float32 Y (+)= X W + b (bias on value rows only), 128 x 64 output tiles,
-// 8 x 4 outputs per thread, float4 loads from global and shared memory.
-// Requires ldx, ldw, ldy, Kd and Nout multiples of 4 and 16-byte aligned X,
-// W and Y (the caller checks).
+// 8 x 4 outputs per thread, float4 loads of X and of shared memory.
+// Requires ldx and Kd multiples of 4 and a 16-byte aligned X (the caller
+// checks).  VEC_W: float4 loads of W (ldw, Nout multiples of 4, W aligned),
+// else element loads; VEC_Y: float4 stores of Y (ldy, Nout multiples of 4,
+// Y aligned), else element stores.
+template <bool VEC_W, bool VEC_Y>
 __global__ void __launch_bounds__(256) k_linear_v4(const float* __restrict__ X, int ldx, const float* __restrict__ W,
                                                    int ldw, const float* __restrict__ bias, float* __restrict__ Y,
                                                    int ldy, int rows, int Kd, int Nout, int T, int accumulate) {
@@ -241,12 +244,20 @@ __global__ void __launch_bounds__(256) k_linear_v4(const float* __restrict__ X, 
       As[k4 + 2][rr] = v.z;
       As[k4 + 3][rr] = v.w;
     }
-    {
+    if constexpr (VEC_W) {
       const int kb = tid >> 4, c4 = (tid & 15) * 4;
       const int gk = k0 + kb, gc = col0 + c4;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (gk < Kd && gc < Nout) v = *(const float4*)(W + (size_t)gk * ldw + gc);
       *(float4*)&Bs[kb][c4] = v;
+    } else {
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int e = tid + l * 256;
+        const int kb = e >> 6, cb = e & 63;
+        const int gk = k0 + kb, gc = col0 + cb;
+        Bs[kb][cb] = (gk < Kd && gc < Nout) ? W[(size_t)gk * ldw + gc] : 0.f;
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -264,29 +275,32 @@ __global__ void __launch_bounds__(256) k_linear_v4(const float* __restrict__ X, 
   }
   const int gc = col0 + tx * 4;
   if (gc >= Nout) return;
-  float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (bias) bv = make_float4(bias[gc], bias[gc + 1], bias[gc + 2], bias[gc + 3]);
+  float bv[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) bv[j] = (bias && gc + j < Nout) ? bias[gc + j] : 0.f;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int gr = row0 + ty * 8 + i;
     if (gr >= rows) break;
     const bool val = (gr % T) == 0;
-    float4 v = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-    if (val) {
-      v.x += bv.x;
-      v.y += bv.y;
-      v.z += bv.z;
-      v.w += bv.w;
+    float v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = acc[i][j] + (val ? bv[j] : 0.f);
+    float* y = Y + (size_t)gr * ldy + gc;
+    if constexpr (VEC_Y) {
+      if (accumulate) {
+        const float4 o = *(const float4*)y;
+        v[0] += o.x;
+        v[1] += o.y;
+        v[2] += o.z;
+        v[3] += o.w;
+      }
+      *(float4*)y = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (gc + j < Nout) y[j] = accumulate ? y[j] + v[j] : v[j];
     }
-    float4* y = (float4*)(Y + (size_t)gr * ldy + gc);
-    if (accumulate) {
-      const float4 o = *y;
-      v.x += o.x;
-      v.y += o.y;
-      v.z += o.z;
-      v.w += o.w;
-    }
-    *y = v;
   }
 }
 
@@ -671,13 +685,18 @@ int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw
                           T, acc, s->dev_err, st);
   }
   if constexpr (sizeof(R) == 4) {
-    const bool v4 = ldx % 4 == 0 && ldw % 4 == 0 && ldy % 4 == 0 && Kd % 4 == 0 && Nout % 4 == 0 &&
-                    ((uintptr_t)X & 15) == 0 && ((uintptr_t)W & 15) == 0 && ((uintptr_t)Y & 15) == 0;
-    if (v4) {
+    if (ldx % 4 == 0 && Kd % 4 == 0 && ((uintptr_t)X & 15) == 0) {
+      const bool vw = ldw % 4 == 0 && Nout % 4 == 0 && ((uintptr_t)W & 15) == 0;
+      const bool vy = ldy % 4 == 0 && Nout % 4 == 0 && ((uintptr_t)Y & 15) == 0;
       dim3 grid((rows + 127) / 128, (Nout + 63) / 64);
-      PN_LAUNCH("k_linear", st,
-                k_linear_v4<<<grid, 256, 0, st>>>((const float*)X, ldx, (const float*)W, ldw, (const float*)b,
-                                                  (float*)Y, ldy, rows, Kd, Nout, T, acc));
+      const float *xf = (const float*)X, *wf = (const float*)W, *bf = (const float*)b;
+      float* yf = (float*)Y;
+      if (vw && vy)
+        PN_LAUNCH("k_linear", st, (k_linear_v4<true, true><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));
+      else if (vy)
+        PN_LAUNCH("k_linear", st, (k_linear_v4<false, true><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));
+      else
+        PN_LAUNCH("k_linear", st, (k_linear_v4<false, false><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));
       return PN_OK;
     }
   }
