@@ -258,16 +258,28 @@ def run_langevin(sysd, W, target=0.57, steps=10):
     s.langevin_step(r, lp, g, 2, tau, 7, step0)
     step0 += 2
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    s.langevin_step(r, lp, g, steps, tau, 7, step0, nacc)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    out = {"tau": tau, "accept_rate": int(nacc.item()) / (steps * W), "ms_per_step": ms,
+
+    def timed(k0):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.langevin_step(r, lp, g, steps, tau, 7, k0, nacc)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ms = timed(step0)
+    acc = int(nacc.item()) / (steps * W)
+    # the same steps with the drift from the forward jet pass, for comparison
+    s.set_option(binding.PN_OPT_DRIFT, 0)
+    s.langevin_step(r, lp, g, 2, tau, 7, step0 + steps)
+    ms_jet = timed(step0 + steps + 2)
+    s.set_option(binding.PN_OPT_DRIFT, 1)
+    out = {"tau": tau, "accept_rate": acc, "ms_per_step": ms,
            "walker_steps_per_s": W / (ms / 1e3), "walkers": W, "steps_timed": steps,
+           "ms_per_step_jet_drift": ms_jet,
            "note": "all-electron drift-diffusion proposal with the drift clipped at the nearest nucleus; "
-                   "tau bisected to the 57 % target acceptance; staged kernels with one jet pass per step"}
+                   "tau bisected to the 57 % target acceptance; staged kernels, the drift at each proposal "
+                   "by reverse mode (ms_per_step_jet_drift: the same steps with the forward jet pass)"}
     s.close()
     return out
 
@@ -573,17 +585,25 @@ def main():
     err = (E_m - E_d).abs().cpu().numpy()
     mixed_err = {"max": float(err.max()), "p999": float(np.quantile(err, 0.999)), "mean": float(err.mean())}
 
-    # end to end through the C ABI with host buffers (copies inside the region)
+    # end to end through the C ABI with host buffers in pinned (page-locked)
+    # memory; every call copies its inputs in and its results out inside the
+    # timed region
     e2e = None
     if not args.no_e2e:
         s = mixed["s"]
-        rh = mixed["r"].cpu().numpy().copy()
-        lph = mixed["lp"].cpu().numpy().copy()
-        Eh = np.empty(W)
-        Ech = np.empty(W)
-        coth = np.empty(W)
-        gh = np.empty(s.n_params)
-        nah = np.zeros(1, dtype=np.int64)
+
+        def pinned(shape, dtype=torch.float64):
+            return torch.zeros(shape, dtype=dtype).pin_memory().numpy()
+
+        rh = pinned(tuple(mixed["r"].shape))
+        rh[...] = mixed["r"].cpu().numpy()
+        lph = pinned((W,))
+        lph[...] = mixed["lp"].cpu().numpy()
+        Eh = pinned((W,))
+        Ech = pinned((W,))
+        coth = pinned((W,))
+        gh = pinned((s.n_params,))
+        nah = pinned((1,), torch.int64)
 
         def host_step(k):
             s.metropolis_step(rh, lph, N_METROPOLIS, SIGMA, 11 + rank, k * N_METROPOLIS, nah)

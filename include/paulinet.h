@@ -199,9 +199,13 @@ int pn_metropolis_step(pn_system_t sys, double* r, double* logabs, int W,
 
 /* ln|psi| and its gradient with respect to the electron positions,
  * drift [W][N][3] = grad_r ln|psi| (the quantity the Langevin proposal
- * follows; Methods, ansatz optimisation, sampling), from the same jet pass
- * as pn_eval_local_energy.  logabs may be NULL.  Host or device buffers; a
- * call with a host buffer returns after the results are written. */
+ * follows; Methods, ansatz optimisation, sampling).  By default it is formed
+ * in reverse mode (one value pass kept on the handle's tape, then the chain
+ * back from ln|psi| to the pair distances and orbitals; the tape is
+ * allocated on first use and kept); PN_OPT_DRIFT = 0 selects the jet pass
+ * of pn_eval_local_energy instead.  logabs may be NULL.  Host or device
+ * buffers; a call with a host buffer returns after the results are
+ * written. */
 int pn_eval_drift(pn_system_t sys, const double* r, int W, double* logabs,
                   double* drift, void* stream);
 
@@ -231,10 +235,11 @@ int pn_eval_line_scan(pn_system_t sys, const double* r0, int electron,
  * xi and u come from the same Philox4x32-10 stream layout as
  * pn_metropolis_step.  r [W][N][3], logabs [W] and drift [W][N][3] must be
  * DEVICE buffers holding ln|psi(r)| and grad ln|psi(r)| on entry
- * (pn_eval_drift); they are updated in place.  n_accept (one int64, host or
- * device, may be NULL) receives the accepted moves over walkers and steps.
- * tau > 0 is the time step; the paper tunes it for 57 % acceptance, which is
- * left to the caller.  PN_EINVAL for host buffers or tau <= 0. */
+ * (pn_eval_drift); they are updated in place.  The drift at each proposal
+ * is formed as in pn_eval_drift (PN_OPT_DRIFT).  n_accept (one int64, host
+ * or device, may be NULL) receives the accepted moves over walkers and
+ * steps.  tau > 0 is the time step; the paper tunes it for 57 % acceptance,
+ * which is left to the caller.  PN_EINVAL for host buffers or tau <= 0. */
 int pn_langevin_step(pn_system_t sys, double* r, double* logabs, double* drift,
                      int W, int n_steps, double tau, uint64_t seed,
                      uint64_t step0, int64_t* n_accept, void* stream);
@@ -262,8 +267,11 @@ int pn_langevin_step(pn_system_t sys, double* r, double* logabs, double* drift,
  *   core's float32 accumulation is coarser than CUDA-core float32, so the
  *   mask is a per-system choice: enable a group only where the E_loc error
  *   against PN_FP64 stays within the required bound (the Python helper
- *   paper_1909_08423_gb300.precision.calibrate measures this). */
-enum { PN_OPT_FUSED_SAMPLER = 1, PN_OPT_TENSOR_CORES = 2 };
+ *   paper_1909_08423_gb300.precision.calibrate measures this).
+ * PN_OPT_DRIFT (default 1): how pn_eval_drift and pn_langevin_step form
+ *   grad_r ln|psi| -- 1 reverse mode (work linear in the electron count),
+ *   0 the forward jet pass (3N + 2 rows per electron). */
+enum { PN_OPT_FUSED_SAMPLER = 1, PN_OPT_TENSOR_CORES = 2, PN_OPT_DRIFT = 3 };
 int pn_set_option(pn_system_t sys, int option, int value);
 
 /* Synchronises the device and reports whether any of the handle's kernels

@@ -384,10 +384,19 @@ template int pn_run_metropolis<double>(const DevSys&, const DevNet<double>&, Wor
 template int pn_run_metropolis<float>(const DevSys&, const DevNet<float>&, Work<float>&, int, double*, double*, int,
                                       int, double, unsigned long long, unsigned long long, int64_t*, cudaStream_t);
 
-// ln|psi| and grad_r ln|psi| (the Langevin drift) by the jet pass.
+// ln|psi| and grad_r ln|psi| (the Langevin drift) of a workspace chunk:
+// by reverse mode on the system's tape when rev is given, else by the jet
+// pass (which also forms E_loc).  Results land in w.out_logabs, w.out_grad.
 template <typename R>
-int pn_run_drift(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, const double* r, int W, double* logabs,
-                 double* drift, cudaStream_t st) {
+static int drift_of_chunk(pn_system_s* rev, const DevSys& ds, const DevNet<R>& net, Work<R>& w, const double* r,
+                          int Wn, cudaStream_t st) {
+  if (rev) return pn_drift_reverse<R>(rev, r, Wn, w.out_logabs, w.out_grad, st);
+  return pn_forward_chunk<R>(ds, net, w, r, Wn, 1, st);
+}
+
+template <typename R>
+int pn_run_drift(pn_system_s* rev, const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, const double* r, int W,
+                 double* logabs, double* drift, cudaStream_t st) {
   const int N = ds.N;
   const bool rdev = pn_is_device_ptr(r);
   for (int c0 = 0; c0 < W; c0 += Wc) {
@@ -397,23 +406,24 @@ int pn_run_drift(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, con
       PN_CUDA(cudaMemcpyAsync(w.r, rc, (size_t)Wn * N * 3 * 8, cudaMemcpyHostToDevice, st));
       rc = w.r;
     }
-    if (int e = pn_forward_chunk<R>(ds, net, w, rc, Wn, 1, st)) return e;
+    if (int e = drift_of_chunk<R>(rev, ds, net, w, rc, Wn, st)) return e;
     if (logabs) PN_CUDA(cudaMemcpyAsync(logabs + c0, w.out_logabs, Wn * 8, cudaMemcpyDefault, st));
     PN_CUDA(cudaMemcpyAsync(drift + (size_t)c0 * N * 3, w.out_grad, (size_t)Wn * N * 3 * 8, cudaMemcpyDefault, st));
   }
   if (!rdev || is_host(logabs) || is_host(drift)) PN_CUDA(cudaStreamSynchronize(st));
   return PN_OK;
 }
-template int pn_run_drift<double>(const DevSys&, const DevNet<double>&, Work<double>&, int, const double*, int, double*,
-                                  double*, cudaStream_t);
-template int pn_run_drift<float>(const DevSys&, const DevNet<float>&, Work<float>&, int, const double*, int, double*,
-                                 double*, cudaStream_t);
+template int pn_run_drift<double>(pn_system_s*, const DevSys&, const DevNet<double>&, Work<double>&, int, const double*,
+                                  int, double*, double*, cudaStream_t);
+template int pn_run_drift<float>(pn_system_s*, const DevSys&, const DevNet<float>&, Work<float>&, int, const double*, int,
+                                 double*, double*, cudaStream_t);
 
 // Langevin Metropolis-Hastings steps, staged per workspace chunk: propose,
-// jet pass at the proposals (ln|psi'| and its gradient), accept.  r,
-// logabs and drift are device buffers, updated in place.
+// ln|psi'| and its gradient at the proposals (reverse mode when rev is
+// given, else the jet pass), accept.  r, logabs and drift are device
+// buffers, updated in place.
 template <typename R>
-int pn_run_langevin(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, double* r, double* logabs,
+int pn_run_langevin(pn_system_s* rev, const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, double* r, double* logabs,
                     double* drift, int W, int n_steps, double tau, unsigned long long seed, unsigned long long step0,
                     int64_t* n_accept, cudaStream_t st) {
   const int N = ds.N;
@@ -428,7 +438,7 @@ int pn_run_langevin(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, 
       PN_LAUNCH("k_langevin_propose", st,
                 k_langevin_propose<<<nblk(Wn, 128), 128, 0, st>>>(ds, rc, dc, w.r_prop, w.lp_prop, Wn, (unsigned)c0,
                                                                   seed, step, tau));
-      if (int e = pn_forward_chunk<R>(ds, net, w, w.r_prop, Wn, 1, st)) return e;
+      if (int e = drift_of_chunk<R>(rev, ds, net, w, w.r_prop, Wn, st)) return e;
       PN_LAUNCH("k_langevin_accept", st,
                 k_langevin_accept<<<nblk(Wn, 128), 128, 0, st>>>(ds, rc, lc, dc, w.r_prop, w.out_logabs, w.out_grad,
                                                                  w.lp_prop, Wn, (unsigned)c0, seed, step, tau,
@@ -439,10 +449,10 @@ int pn_run_langevin(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, 
   if (is_host(n_accept)) PN_CUDA(cudaStreamSynchronize(st));
   return PN_OK;
 }
-template int pn_run_langevin<double>(const DevSys&, const DevNet<double>&, Work<double>&, int, double*, double*,
+template int pn_run_langevin<double>(pn_system_s*, const DevSys&, const DevNet<double>&, Work<double>&, int, double*, double*,
                                      double*, int, int, double, unsigned long long, unsigned long long, int64_t*,
                                      cudaStream_t);
-template int pn_run_langevin<float>(const DevSys&, const DevNet<float>&, Work<float>&, int, double*, double*, double*,
+template int pn_run_langevin<float>(pn_system_s*, const DevSys&, const DevNet<float>&, Work<float>&, int, double*, double*, double*,
                                     int, int, double, unsigned long long, unsigned long long, int64_t*, cudaStream_t);
 
 // E_loc, ln|psi| and sign along a line: npts points t0 .. t1 (inclusive) of
@@ -547,9 +557,10 @@ extern "C" int pn_eval_drift(pn_system_t s, const double* r, int W, double* loga
   }
   if (W == 0) return PN_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  pn_system_s* rev = s->drift_mode ? s : nullptr;
   return s->precision == PN_FP64
-             ? pn_run_drift<double>(s->ds, pn_devnet<double>(s), work_of<double>(s), s->Wc, r, W, logabs, drift, st)
-             : pn_run_drift<float>(s->ds, pn_devnet<float>(s), work_of<float>(s), s->Wc, r, W, logabs, drift, st);
+             ? pn_run_drift<double>(rev, s->ds, pn_devnet<double>(s), work_of<double>(s), s->Wc, r, W, logabs, drift, st)
+             : pn_run_drift<float>(rev, s->ds, pn_devnet<float>(s), work_of<float>(s), s->Wc, r, W, logabs, drift, st);
 }
 
 extern "C" int pn_langevin_step(pn_system_t s, double* r, double* logabs, double* drift, int W, int n_steps,
@@ -572,10 +583,11 @@ extern "C" int pn_langevin_step(pn_system_t s, double* r, double* logabs, double
     }
     return PN_OK;
   }
+  pn_system_s* rev = s->drift_mode ? s : nullptr;
   return s->precision == PN_FP64
-             ? pn_run_langevin<double>(s->ds, pn_devnet<double>(s), work_of<double>(s), s->Wc, r, logabs, drift, W,
+             ? pn_run_langevin<double>(rev, s->ds, pn_devnet<double>(s), work_of<double>(s), s->Wc, r, logabs, drift, W,
                                        n_steps, tau, seed, step0, n_accept, st)
-             : pn_run_langevin<float>(s->ds, pn_devnet<float>(s), work_of<float>(s), s->Wc, r, logabs, drift, W,
+             : pn_run_langevin<float>(rev, s->ds, pn_devnet<float>(s), work_of<float>(s), s->Wc, r, logabs, drift, W,
                                       n_steps, tau, seed, step0, n_accept, st);
 }
 
@@ -622,6 +634,10 @@ extern "C" int pn_set_option(pn_system_t s, int option, int value) {
     case PN_OPT_FUSED_SAMPLER:
       if (value < 0 || value > 4) { pn_set_error("fused sampler option takes 0..4"); return PN_EINVAL; }
       s->ds.fused_sampler = value;
+      return PN_OK;
+    case PN_OPT_DRIFT:
+      if (value < 0 || value > 1) { pn_set_error("drift option takes 0 (jet pass) or 1 (reverse mode)"); return PN_EINVAL; }
+      s->drift_mode = value;
       return PN_OK;
     case PN_OPT_TENSOR_CORES:
       if (value < 0 || value > 7) { pn_set_error("tensor-core option takes a mask 0..7"); return PN_EINVAL; }

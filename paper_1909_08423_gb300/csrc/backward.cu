@@ -104,115 +104,171 @@ __global__ void k_ssp_copy(const R* __restrict__ A, R* __restrict__ S, size_t n)
 
 // ---------------------------------------------------------- backward kernels
 // Determinant part: d ln|psi| / d F[w][i][mu] (f = 1 + F) for weight u_w,
-// with omega_p = c_p s_p e^{ld_p} / S and d ln|det A| / dA = A^{-T}.
-// Also writes the walker's J cotangent (= u_w).  One thread per walker.
+// with omega_p = c_p s_p e^{ld_p} / S and d ln|det A| / dA = A^{-T}, in three
+// passes so that every (walker, determinant, spin) block gets a thread:
+// k_slater_lu forms ln|det| and the sign of each block, k_slater_inv the
+// weighted inverse omega_p A^{-T} of each block, k_slater_gather sums the
+// blocks for each electron row in determinant order (a fixed order, so the
+// result is deterministic).
+
+// LU factorisation with partial pivoting of spin block sp of determinant p:
+// A[a][b] = phi_{occ_b}(r_{e0+a}) (1 + F_{e0+a, occ_b}).  Returns false for
+// a singular block; perm (optional) receives the row permutation.
 template <typename R>
-__global__ void k_slater_bwd(DevSys s, const double* __restrict__ phi, const R* __restrict__ F, const double* __restrict__ u,
-                             int Wn, R* __restrict__ dF, R* __restrict__ dJ) {
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= Wn) return;
-  const int N = s.N, no = s.n_orb, nd = s.n_det;
-  constexpr int NS = PN_MAX_SPIN;
-  const double* phw = phi + (size_t)w * N * no * 5;
-  const R* Fw = F + (size_t)w * N * no;
-  double ld[PN_MAX_DETS], sg[PN_MAX_DETS];
-  // pass 1: ln|det| and signs
-  for (int p = 0; p < nd; ++p) {
-    double l = 0, sgn = 1;
-    for (int sp = 0; sp < 2; ++sp) {
-      const int ns = sp ? s.n_dn : s.n_up, e0 = sp ? s.n_up : 0;
-      if (ns == 0) continue;
-      const int* occ = s.occ + p * N + e0;
-      double LU[NS * NS];
-      for (int a = 0; a < ns; ++a)
-        for (int b = 0; b < ns; ++b)
-          LU[a * ns + b] = phw[((e0 + a) * no + occ[b]) * 5] * (1.0 + (double)Fw[(e0 + a) * no + occ[b]]);
-      for (int c = 0; c < ns; ++c) {
-        int best = c;
-        double bv = fabs(LU[c * ns + c]);
-        for (int rr = c + 1; rr < ns; ++rr)
-          if (fabs(LU[rr * ns + c]) > bv) { bv = fabs(LU[rr * ns + c]); best = rr; }
-        if (!(bv > 0.0)) { sgn = 0; break; }
-        if (best != c) {
-          for (int k = 0; k < ns; ++k) { double t = LU[c * ns + k]; LU[c * ns + k] = LU[best * ns + k]; LU[best * ns + k] = t; }
-          sgn = -sgn;
-        }
-        const double piv = LU[c * ns + c];
-        if (piv < 0) sgn = -sgn;
-        l += log(fabs(piv));
-        for (int rr = c + 1; rr < ns; ++rr) {
-          const double f = LU[rr * ns + c] / piv;
-          LU[rr * ns + c] = f;
-          for (int k = c + 1; k < ns; ++k) LU[rr * ns + k] -= f * LU[c * ns + k];
-        }
-      }
-      if (sgn == 0) break;
+__device__ inline bool slater_block_lu(const DevSys& s, const double* phw, const R* Fw, int p, int sp, double* LU,
+                                       int* perm, double& ld, double& sgn) {
+  const int no = s.n_orb, ns = sp ? s.n_dn : s.n_up, e0 = sp ? s.n_up : 0;
+  const int* occ = s.occ + p * s.N + e0;
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b < ns; ++b)
+      LU[a * ns + b] = phw[((e0 + a) * no + occ[b]) * 5] * (1.0 + (double)Fw[(e0 + a) * no + occ[b]]);
+  if (perm)
+    for (int c = 0; c < ns; ++c) perm[c] = c;
+  ld = 0;
+  sgn = 1;
+  for (int c = 0; c < ns; ++c) {
+    int best = c;
+    double bv = fabs(LU[c * ns + c]);
+    for (int rr = c + 1; rr < ns; ++rr)
+      if (fabs(LU[rr * ns + c]) > bv) { bv = fabs(LU[rr * ns + c]); best = rr; }
+    if (!(bv > 0.0)) { sgn = 0; return false; }
+    if (best != c) {
+      for (int k = 0; k < ns; ++k) { double t = LU[c * ns + k]; LU[c * ns + k] = LU[best * ns + k]; LU[best * ns + k] = t; }
+      if (perm) { int t = perm[c]; perm[c] = perm[best]; perm[best] = t; }
+      sgn = -sgn;
     }
-    ld[p] = l;
-    sg[p] = sgn;
-  }
-  double m = -INFINITY;
-  for (int p = 0; p < nd; ++p)
-    if (s.ci[p] != 0.0 && sg[p] != 0.0) m = fmax(m, ld[p]);
-  double S = 0;
-  for (int p = 0; p < nd; ++p)
-    if (sg[p] != 0.0) S += s.ci[p] * sg[p] * exp(ld[p] - m);
-  const double uw = u[w];
-  dJ[w] = (R)uw;
-  double dphit[PN_MAX_ELECTRONS * PN_MAX_ORBITALS];
-  for (int k = 0; k < N * no; ++k) dphit[k] = 0;
-  if (S != 0.0 && m > -INFINITY) {
-    for (int p = 0; p < nd; ++p) {
-      if (sg[p] == 0.0) continue;
-      const double om = uw * s.ci[p] * sg[p] * exp(ld[p] - m) / S;
-      for (int sp = 0; sp < 2; ++sp) {
-        const int ns = sp ? s.n_dn : s.n_up, e0 = sp ? s.n_up : 0;
-        if (ns == 0) continue;
-        const int* occ = s.occ + p * N + e0;
-        double LU[NS * NS];
-        int perm[NS];
-        for (int a = 0; a < ns; ++a)
-          for (int b = 0; b < ns; ++b)
-            LU[a * ns + b] = phw[((e0 + a) * no + occ[b]) * 5] * (1.0 + (double)Fw[(e0 + a) * no + occ[b]]);
-        for (int c = 0; c < ns; ++c) perm[c] = c;
-        for (int c = 0; c < ns; ++c) {
-          int best = c;
-          double bv = fabs(LU[c * ns + c]);
-          for (int rr = c + 1; rr < ns; ++rr)
-            if (fabs(LU[rr * ns + c]) > bv) { bv = fabs(LU[rr * ns + c]); best = rr; }
-          if (best != c) {
-            for (int k = 0; k < ns; ++k) { double t = LU[c * ns + k]; LU[c * ns + k] = LU[best * ns + k]; LU[best * ns + k] = t; }
-            int t = perm[c]; perm[c] = perm[best]; perm[best] = t;
-          }
-          const double piv = LU[c * ns + c];
-          for (int rr = c + 1; rr < ns; ++rr) {
-            const double f = LU[rr * ns + c] / piv;
-            LU[rr * ns + c] = f;
-            for (int k = c + 1; k < ns; ++k) LU[rr * ns + k] -= f * LU[c * ns + k];
-          }
-        }
-        // column `col` of A^{-1}; d ln|det| / dA[a][b] = Ainv[b][a]
-        for (int col = 0; col < ns; ++col) {
-          double y[NS];
-          for (int rr = 0; rr < ns; ++rr) {
-            double v = (perm[rr] == col) ? 1.0 : 0.0;
-            for (int k = 0; k < rr; ++k) v -= LU[rr * ns + k] * y[k];
-            y[rr] = v;
-          }
-          for (int rr = ns - 1; rr >= 0; --rr) {
-            double v = y[rr];
-            for (int k = rr + 1; k < ns; ++k) v -= LU[rr * ns + k] * y[k];
-            y[rr] = v / LU[rr * ns + rr];
-          }
-          // y = Ainv[:, col]; entry Ainv[b][col] pairs with A[col][b]
-          for (int b = 0; b < ns; ++b) dphit[(e0 + col) * no + occ[b]] += om * y[b];
-        }
-      }
+    const double piv = LU[c * ns + c];
+    if (piv < 0) sgn = -sgn;
+    ld += log(fabs(piv));
+    for (int rr = c + 1; rr < ns; ++rr) {
+      const double f = LU[rr * ns + c] / piv;
+      LU[rr * ns + c] = f;
+      for (int k = c + 1; k < ns; ++k) LU[rr * ns + k] -= f * LU[c * ns + k];
     }
   }
-  for (int i = 0; i < N; ++i)
-    for (int mu = 0; mu < no; ++mu)
-      dF[((size_t)w * N + i) * no + mu] = (R)(dphit[i * no + mu] * phw[(i * no + mu) * 5]);
+  return true;
+}
+
+// lds[w][p][sp] = (ln|det|, sign); one thread per (walker, determinant, spin).
+template <typename R>
+__global__ void k_slater_lu(DevSys s, const double* __restrict__ phi, const R* __restrict__ F, int Wn,
+                            double* __restrict__ lds) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)Wn * s.n_det * 2) return;
+  const int sp = idx & 1, p = (idx >> 1) % s.n_det;
+  const size_t w = (idx >> 1) / s.n_det;
+  double* o = lds + idx * 2;
+  if ((sp ? s.n_dn : s.n_up) == 0) { o[0] = 0; o[1] = 1; return; }
+  double LU[PN_MAX_SPIN * PN_MAX_SPIN];
+  double ld, sg;
+  slater_block_lu<R>(s, phi + w * s.N * s.n_orb * 5, F + w * s.N * s.n_orb, p, sp, LU, nullptr, ld, sg);
+  o[0] = ld;
+  o[1] = sg;
+}
+
+// Walker-level log-sum of the determinants from the block table:
+// m = max ln|det_p| over live determinants, S = sum_p c_p s_p e^{ld_p - m}.
+__device__ inline void slater_logsum(const DevSys& s, const double* lw, double& m, double& S) {
+  m = -INFINITY;
+  for (int p = 0; p < s.n_det; ++p) {
+    const double* q = lw + p * 4;
+    if (s.ci[p] != 0.0 && q[1] != 0.0 && q[3] != 0.0) m = fmax(m, q[0] + q[2]);
+  }
+  S = 0;
+  for (int p = 0; p < s.n_det; ++p) {
+    const double* q = lw + p * 4;
+    const double sg = q[1] * q[3];
+    if (sg != 0.0) S += s.ci[p] * sg * exp(q[0] + q[2] - m);
+  }
+}
+
+// inv[w][p][sp][a][b] = u_w omega_p (A^{-1})[b][a] = d ln|psi| / dA[a][b]
+// contributed by block (p, sp); zero where the block or the walker is
+// singular.  One thread per (walker, determinant, spin).
+template <typename R>
+__global__ void k_slater_inv(DevSys s, const double* __restrict__ phi, const R* __restrict__ F,
+                             const double* __restrict__ u, const double* __restrict__ lds, int Wn, int inv_stride,
+                             double* __restrict__ inv) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)Wn * s.n_det * 2) return;
+  const int sp = idx & 1, p = (idx >> 1) % s.n_det;
+  const size_t w = (idx >> 1) / s.n_det;
+  const int ns = sp ? s.n_dn : s.n_up;
+  if (ns == 0) return;
+  double* o = inv + w * inv_stride + (size_t)p * (s.n_up * s.n_up + s.n_dn * s.n_dn) + (sp ? s.n_up * s.n_up : 0);
+  const double* lw = lds + w * s.n_det * 4;
+  double m, S;
+  slater_logsum(s, lw, m, S);
+  const double sg = lw[p * 4 + 1] * lw[p * 4 + 3];
+  if (!(S != 0.0) || !(m > -INFINITY) || sg == 0.0) {
+    for (int k = 0; k < ns * ns; ++k) o[k] = 0;
+    return;
+  }
+  const double om = (u ? u[w] : 1.0) * s.ci[p] * sg * exp(lw[p * 4] + lw[p * 4 + 2] - m) / S;
+  double LU[PN_MAX_SPIN * PN_MAX_SPIN];
+  int perm[PN_MAX_SPIN];
+  double ld, sgb;
+  slater_block_lu<R>(s, phi + w * s.N * s.n_orb * 5, F + w * s.N * s.n_orb, p, sp, LU, perm, ld, sgb);
+  // column `col` of A^{-1}: entry (b, col) pairs with A[col][b]
+  for (int col = 0; col < ns; ++col) {
+    double y[PN_MAX_SPIN];
+    for (int rr = 0; rr < ns; ++rr) {
+      double v = (perm[rr] == col) ? 1.0 : 0.0;
+      for (int k = 0; k < rr; ++k) v -= LU[rr * ns + k] * y[k];
+      y[rr] = v;
+    }
+    for (int rr = ns - 1; rr >= 0; --rr) {
+      double v = y[rr];
+      for (int k = rr + 1; k < ns; ++k) v -= LU[rr * ns + k] * y[k];
+      y[rr] = v / LU[rr * ns + rr];
+    }
+    for (int b = 0; b < ns; ++b) o[col * ns + b] = om * y[b];
+  }
+}
+
+// Per electron row i: dphit[mu] = sum_p sum_{b: occ_b = mu} inv[p][i][b]
+// (determinant order), then dF = dphit phi and, with gr, the orbital part
+// of grad_r ln|psi|, sum_mu dphit (1 + F) grad phi_mu(r_i).  Row 0 also
+// writes the walker's J cotangent u_w and, with lse, ln|sum_p c_p det_p|.
+// One thread per (walker, electron).
+template <typename R>
+__global__ void k_slater_gather(DevSys s, const double* __restrict__ phi, const R* __restrict__ F,
+                                const double* __restrict__ u, const double* __restrict__ lds,
+                                const double* __restrict__ inv, int Wn, int inv_stride, R* __restrict__ dF,
+                                R* __restrict__ dJ, double* __restrict__ gr, double* __restrict__ lse) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)Wn * s.N) return;
+  const int N = s.N, no = s.n_orb, i = idx % N;
+  const size_t w = idx / N;
+  const int sp = i < s.n_up ? 0 : 1, ns = sp ? s.n_dn : s.n_up, e0 = sp ? s.n_up : 0, a = i - e0;
+  const int blk = s.n_up * s.n_up + s.n_dn * s.n_dn, off = sp ? s.n_up * s.n_up : 0;
+  double dphit[PN_MAX_ORBITALS];
+  for (int mu = 0; mu < no; ++mu) dphit[mu] = 0;
+  const double* iw = inv + w * inv_stride;
+  for (int p = 0; p < s.n_det; ++p) {
+    const int* occ = s.occ + p * N + e0;
+    const double* q = iw + (size_t)p * blk + off + a * ns;
+    for (int b = 0; b < ns; ++b) dphit[occ[b]] += q[b];
+  }
+  const double* ph = phi + idx * no * 5;
+  const R* Fi = F + idx * no;
+  for (int mu = 0; mu < no; ++mu) dF[idx * no + mu] = (R)(dphit[mu] * ph[mu * 5]);
+  if (gr) {
+    double g[3] = {0, 0, 0};
+    for (int mu = 0; mu < no; ++mu) {
+      const double c = dphit[mu] * (1.0 + (double)Fi[mu]);
+      for (int x = 0; x < 3; ++x) g[x] += c * ph[mu * 5 + 1 + x];
+    }
+    for (int x = 0; x < 3; ++x) gr[idx * 3 + x] = g[x];
+  }
+  if (i == 0) {
+    dJ[w] = (R)(u ? u[w] : 1.0);
+    if (lse) {
+      double m, S;
+      slater_logsum(s, lds + w * s.n_det * 4, m, S);
+      lse[w] = (S != 0.0 && m > -INFINITY) ? m + log(fabs(S)) : -INFINITY;
+    }
+  }
 }
 
 // out = d * sigmoid(a)
@@ -287,9 +343,10 @@ __global__ void k_msg_bwd_h(DevSys s, const R* __restrict__ wv, const R* __restr
     acc += ww[(size_t)p * Zd + z] * dZw[(size_t)i * 3 * Zd + c * Zd + z];
   }
   dH[idx] = acc;
-  for (int I = 0; I < s.M; ++I)
+  if (dYr)
+    for (int I = 0; I < s.M; ++I)
     dYr[(((size_t)w * N + j) * s.M + I) * Zd + z] =
-        ww[(size_t)(s.Pee + j * s.M + I) * Zd + z] * dZw[(size_t)j * 3 * Zd + 2 * Zd + z];
+          ww[(size_t)(s.Pee + j * s.M + I) * Zd + z] * dZw[(size_t)j * 3 * Zd + 2 * Zd + z];
 }
 
 // Filter backward through the hidden layer: dAh = (dw W2^T) * sigmoid(Ah),
@@ -353,6 +410,96 @@ __global__ void k_filter_bwd_global(DevSys s, DevNet<R> net, int n, const R* __r
     dAh[row * Hw + h] = acc * sigm_(a);
     Sh[row * Hw + h] = ssp_(a);
   }
+}
+
+// Filter backward towards the pair distance, for grad_r ln|psi|: the hidden
+// cotangent dAh = (dw W2^T) * sigmoid(Ah) of pair row p meets the distance
+// derivative of the hidden pre-activation, q = e'(d_p) W1, and
+// dd[p] += sum_h dAh q.  One warp per pair row, FB_ROWS rows per warp; with
+// SW the three channels' W2 sit in shared memory (rows padded by one).
+template <typename R, bool SW>
+__global__ void __launch_bounds__(256) k_filter_bwd_dist(DevSys s, DevNet<R> net, int n, const R* __restrict__ Ah,
+                                                         const R* __restrict__ ef, const R* __restrict__ dw, int Wn,
+                                                         double* __restrict__ dd) {
+  extern __shared__ __align__(16) unsigned char fd_smem[];
+  const int Hw = s.Hw, Zd = s.Zd, K = s.K, LZ = SW ? Zd + 1 : Zd;
+  R* W2s = (R*)fd_smem;                               // [3][Hw][LZ] (SW only)
+  R* dsh = W2s + (SW ? (size_t)3 * Hw * LZ : 0);      // [8][Zd]
+  R* esh = dsh + 8 * Zd;                              // [8][K]
+  if (SW) {
+    for (int q = threadIdx.x; q < 3 * Hw * Zd; q += blockDim.x) {
+      const int c = q / (Hw * Zd), h = (q / Zd) % Hw, z = q % Zd;
+      W2s[((size_t)c * Hw + h) * LZ + z] = net.p[net.off.W2[n][c] + (size_t)h * Zd + z];
+    }
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  R* dv = dsh + wid * Zd;
+  R* ev = esh + wid * K;
+  const size_t rows = (size_t)Wn * s.Ppair;
+  for (int k = 0; k < FB_ROWS; ++k) {
+    const size_t row = ((size_t)blockIdx.x * 8 + wid) * FB_ROWS + k;
+    if (row >= rows) break;
+    const int ch = pair_channel(s, row % s.Ppair);
+    const R* W2 = SW ? W2s + (size_t)ch * Hw * LZ : net.p + net.off.W2[n][ch];
+    const R* W1 = net.p + net.off.W1[n][ch];
+    for (int z = lane; z < Zd; z += 32) dv[z] = dw[row * Zd + z];
+    for (int q = lane; q < K; q += 32) ev[q] = ef[row * 3 * K + K + q];
+    __syncwarp();
+    double part = 0;
+    for (int h = lane; h < Hw; h += 32) {
+      R acc = 0;
+      for (int z = 0; z < Zd; ++z) acc += dv[z] * W2[h * LZ + z];
+      R q = 0;
+      for (int kk = 0; kk < K; ++kk) q += ev[kk] * W1[kk * Hw + h];
+      part += (double)(acc * sigm_(Ah[row * Hw + h])) * (double)q;
+    }
+    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) dd[row] += part;
+    __syncwarp();
+  }
+}
+
+// ln|psi| = gamma + J + ln|sum_p c_p det_p| and
+// grad_r ln|psi| = orbital part + sum over pairs of (d ln|psi| / d d_p) grad_r d_p,
+// the distance cotangent collecting the filters of every layer and the
+// electronic cusp factor gamma.  One thread per walker.
+template <typename R>
+__global__ void k_drift_combine(DevSys s, const double* __restrict__ geo, const double* __restrict__ lse,
+                                const R* __restrict__ J, const double* __restrict__ gr, const double* __restrict__ dd,
+                                int Wn, double* __restrict__ logabs, double* __restrict__ grad) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= Wn) return;
+  const int N = s.N, n3 = 3 * N, P = s.Ppair;
+  double g[3 * PN_MAX_ELECTRONS];
+  for (int t = 0; t < n3; ++t) g[t] = gr[(size_t)w * n3 + t];
+  const double* gw = geo + (size_t)w * P * 4;
+  const double* dw = dd + (size_t)w * P;
+  double gam = 0;
+  for (int a = 0; a < N; ++a)
+    for (int b = a + 1; b < N; ++b) {
+      const int p = pn_pair_index(a, b, N);
+      const double* u = gw + p * 4;
+      double c = dw[p];
+      if (s.use_gamma) {
+        const double cc = ((a < s.n_up) == (b < s.n_up)) ? 0.25 : 0.5;
+        const double e = 1.0 / (1.0 + u[0]);
+        gam -= cc * e;
+        c += cc * e * e;
+      }
+      for (int x = 0; x < 3; ++x) {
+        g[3 * a + x] += c * u[1 + x];
+        g[3 * b + x] -= c * u[1 + x];
+      }
+    }
+  for (int q = 0; q < s.Pen; ++q) {
+    const int i = q / s.M;
+    const double* u = gw + (s.Pee + q) * 4;
+    const double c = dw[s.Pee + q];
+    for (int x = 0; x < 3; ++x) g[3 * i + x] += c * u[1 + x];
+  }
+  logabs[w] = gam + (double)J[w] + lse[w];
+  for (int t = 0; t < n3; ++t) grad[(size_t)w * n3 + t] = g[t];
 }
 
 // ------------------------------------------------------------ weight grads
@@ -592,6 +739,8 @@ struct Tape {
   R *kA1, *kS1, *kA2, *kS2, *F;           // kappa
   R *Xs, *eA1, *eS1, *eA2, *eS2, *J;      // eta
   R *dX, *dX2, *dH, *dZ, *dw, *dAh, *Sh, *dYr, *dF, *dJ, *dA, *dB, *dXs, *dAs, *dBs;
+  double *lds, *inv;      // determinant blocks: (ln|det|, sign) per spin, weighted inverses
+  double *dd, *gr, *lse;  // position gradient: distance cotangents, orbital part, determinant log-sum
   double* part;
   size_t part_elems;
   unsigned* ctr;  // per-tile completion counters of k_wgrad (kept at zero between launches)
@@ -608,7 +757,8 @@ size_t tape_bytes_per_walker(const DevSys& s) {
   e += P * 3 * s.K + (L + 1) * N * D + L * N * Zd + L * N * 3 * Zd + L * P * Hw + L * P * Zd;
   e += 4 * N * D + N * no + 5 * D + 1;
   e += 2 * N * D + N * Zd + N * 3 * Zd + P * Zd + 2 * P * Hw + N * s.M * Zd + N * no + 1 + 2 * N * D + 3 * D;
-  return e * sizeof(R) + (P * 4 + N * no * 5 + 1) * 8 + 64 * 24;
+  const size_t blocks = (size_t)s.n_det * (4 + s.n_up * s.n_up + s.n_dn * s.n_dn);
+  return e * sizeof(R) + (P * 4 + N * no * 5 + 1 + P + 3 * N + 1 + blocks) * 8 + 64 * 29;
 }
 
 template <typename R>
@@ -654,6 +804,11 @@ Tape<R> carve_tape(const DevSys& s, int Wb, void* base, size_t part_elems) {
   t.dXs = (R*)take(W * D * r);
   t.dAs = (R*)take(W * D * r);
   t.dBs = (R*)take(W * D * r);
+  t.lds = (double*)take(W * s.n_det * 4 * 8);
+  t.inv = (double*)take(W * s.n_det * (s.n_up * s.n_up + s.n_dn * s.n_dn) * 8);
+  t.dd = (double*)take(W * P * 8);
+  t.gr = (double*)take(W * N * 3 * 8);
+  t.lse = (double*)take(W * 8);
   t.part = (double*)take(part_elems * 8);
   t.part_elems = part_elems;
   t.ctr = (unsigned*)take(kWgMaxCtr * 4);
@@ -731,6 +886,20 @@ struct WgBatch {
   }
 };
 
+// The three determinant passes; gr and lse may be null.
+template <typename R>
+int slater_bwd(const DevSys& s, Tape<R>& t, const double* u, int Wn, double* gr, double* lse, cudaStream_t st) {
+  const size_t nb = (size_t)Wn * s.n_det * 2;
+  const int inv_stride = s.n_det * (s.n_up * s.n_up + s.n_dn * s.n_dn);
+  PN_LAUNCH("k_slater_bwd", st, k_slater_lu<R><<<nblk(nb, 64), 64, 0, st>>>(s, t.phi, t.F, Wn, t.lds));
+  PN_LAUNCH("k_slater_bwd", st,
+            k_slater_inv<R><<<nblk(nb, 64), 64, 0, st>>>(s, t.phi, t.F, u, t.lds, Wn, inv_stride, t.inv));
+  PN_LAUNCH("k_slater_bwd", st,
+            k_slater_gather<R><<<nblk((size_t)Wn * s.N, 64), 64, 0, st>>>(s, t.phi, t.F, u, t.lds, t.inv, Wn,
+                                                                          inv_stride, t.dF, t.dJ, gr, lse));
+  return PN_OK;
+}
+
 template <typename R>
 int linear_bt(const R* X, int ldx, const R* W, int ldw, R* Y, int ldy, int rows, int Kd, int Nout, int acc,
               cudaStream_t st) {
@@ -744,16 +913,18 @@ int linear_bt(const R* X, int ldx, const R* W, int ldw, R* Y, int ldy, int rows,
 
 
 
+// Value pass keeping every activation on the tape.  With `drift` the
+// features also carry their distance derivatives and the Jastrow factor J
+// itself is formed (the parameter gradient needs neither).
 template <typename R>
-static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const double* r, const double* u, int Wn,
-                      double* grad, cudaStream_t st) {
-  const int N = s.N, D = s.D, Zd = s.Zd, L = s.L, P = s.Ppair, Hw = s.Hw, no = s.n_orb, K = s.K;
+static int tape_value_pass(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const double* r, int Wn, bool drift,
+                           cudaStream_t st) {
+  const int N = s.N, D = s.D, Zd = s.Zd, L = s.L, P = s.Ppair, Hw = s.Hw, no = s.n_orb;
   const NetOff& o = net.off;
   const int rows = Wn * N;
   const size_t WND = (size_t)Wn * N * D;
-  // ---------------- value pass with the tape
   if (int e = pn_launch_geometry_orbitals(s, r, Wn, t.geo, t.phi, st)) return e;
-  if (int e = pn_launch_features_init<R>(s, net.p + o.x0, t.geo, Wn, t.ef, t.X, st)) return e;
+  if (int e = pn_launch_features_init<R>(s, net.p + o.x0, t.geo, Wn, drift ? 1 : 0, t.ef, t.X, st)) return e;
   for (int n = 0; n < L; ++n) {
     R* Xn = t.X + (size_t)n * WND;
     R* Xn1 = t.X + (size_t)(n + 1) * WND;
@@ -782,6 +953,89 @@ static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const d
   PN_LAUNCH("k_ssp_copy", st, k_ssp_copy<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.eA1, t.eS1, (size_t)Wn * D));
   if (int e = pn_linear<R>(&s, PN_TC_VALUE, t.eS1, D, net.p + o.eW[1], D, net.p + o.eb[1], t.eA2, D, Wn, D, D, 1, 0, st)) return e;
   PN_LAUNCH("k_ssp_copy", st, k_ssp_copy<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.eA2, t.eS2, (size_t)Wn * D));
+  if (drift)
+    if (int e = pn_linear<R>(&s, PN_TC_VALUE, t.eS2, D, net.p + o.eW[2], 1, net.p + o.eb[2], t.J, 1, Wn, D, 1, 1, 0, st))
+      return e;
+  return PN_OK;
+}
+
+// Filter backward towards the distances for layer n (shared-memory W2 when it fits).
+template <typename R>
+static int filter_bwd_dist(const DevSys& s, const DevNet<R>& net, int n, const R* Ah, const R* ef, const R* dw, int Wn,
+                           double* dd, cudaStream_t st) {
+  const size_t tail = (size_t)8 * (s.Zd + s.K) * sizeof(R);
+  const size_t fb = (size_t)3 * s.Hw * (s.Zd + 1) * sizeof(R) + tail;
+  int dev = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const unsigned grid = nblk((size_t)Wn * s.Ppair, 8 * FB_ROWS);
+  if (fb <= (size_t)maxsm) {
+    if (fb > 48 * 1024)
+      PN_CUDA(cudaFuncSetAttribute(k_filter_bwd_dist<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb));
+    PN_LAUNCH("k_filter_bwd_dist", st,
+              (k_filter_bwd_dist<R, true><<<grid, 256, fb, st>>>(s, net, n, Ah, ef, dw, Wn, dd)));
+  } else {
+    PN_LAUNCH("k_filter_bwd_dist", st,
+              (k_filter_bwd_dist<R, false><<<grid, 256, tail, st>>>(s, net, n, Ah, ef, dw, Wn, dd)));
+  }
+  return PN_OK;
+}
+
+// ln|psi| and grad_r ln|psi| of Wn walkers by reverse mode: the value pass
+// on the tape, then the chain back from ln|psi| (weight 1 per walker)
+// through the determinants, both heads and the interaction layers to the
+// pair distances and the orbitals, with no weight gradients formed.
+template <typename R>
+static int drift_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const double* r, int Wn, double* logabs,
+                       double* grad, cudaStream_t st) {
+  const int N = s.N, D = s.D, Zd = s.Zd, L = s.L, P = s.Ppair, Hw = s.Hw, no = s.n_orb;
+  const NetOff& o = net.off;
+  const int rows = Wn * N;
+  const size_t WND = (size_t)Wn * N * D;
+  if (int e = tape_value_pass<R>(s, net, t, r, Wn, true, st)) return e;
+  PN_CUDA(cudaMemsetAsync(t.dd, 0, (size_t)Wn * P * 8, st));
+  if (int e = slater_bwd<R>(s, t, nullptr, Wn, t.gr, t.lse, st)) return e;
+  // kappa head
+  if (int e = linear_bt<R>(t.dF, no, net.p + o.kW[2], no, t.dA, D, rows, no, D, 0, st)) return e;
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dA, t.kA2, t.dA, WND));
+  if (int e = linear_bt<R>(t.dA, D, net.p + o.kW[1], D, t.dB, D, rows, D, D, 0, st)) return e;
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dB, t.kA1, t.dB, WND));
+  if (int e = linear_bt<R>(t.dB, D, net.p + o.kW[0], D, t.dX, D, rows, D, D, 0, st)) return e;
+  // eta head
+  PN_LAUNCH("k_outer_row", st, k_outer_row<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dJ, net.p + o.eW[2], t.dAs, Wn, D));
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dAs, t.eA2, t.dAs, (size_t)Wn * D));
+  if (int e = linear_bt<R>(t.dAs, D, net.p + o.eW[1], D, t.dBs, D, Wn, D, D, 0, st)) return e;
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dBs, t.eA1, t.dBs, (size_t)Wn * D));
+  if (int e = linear_bt<R>(t.dBs, D, net.p + o.eW[0], D, t.dXs, D, Wn, D, D, 0, st)) return e;
+  PN_LAUNCH("k_bcast_add", st, k_bcast_add<R><<<nblk(WND, 256), 256, 0, st>>>(t.dX, t.dXs, Wn, N, D));
+  // interaction layers, last to first; t.dX holds d/dX^(n+1)
+  for (int n = L - 1; n >= 0; --n) {
+    R* Hn = t.H + (size_t)n * rows * Zd;
+    R* Ahn = t.Ah + (size_t)n * Wn * P * Hw;
+    R* wn = t.wv + (size_t)n * Wn * P * Zd;
+    if (int e = linear_bt<R>(t.dX, D, net.Gcat + (size_t)n * 3 * Zd * D, D, t.dZ, 3 * Zd, rows, D, 3 * Zd, 0, st))
+      return e;
+    PN_LAUNCH("k_msg_bwd_w", st, k_msg_bwd_w<R><<<nblk((size_t)Wn * P * Zd, 256), 256, 0, st>>>(s, net.p + o.Y, Hn, t.dZ, Wn, t.dw));
+    PN_LAUNCH("k_msg_bwd_h", st,
+              k_msg_bwd_h<R><<<nblk((size_t)rows * Zd, 256), 256, 0, st>>>(s, wn, t.dZ, Wn, t.dH, (R*)nullptr));
+    if (int e = filter_bwd_dist<R>(s, net, n, Ahn, t.ef, t.dw, Wn, t.dd, st)) return e;
+    if (n > 0)  // x^(0) is the constant embedding
+      if (int e = linear_bt<R>(t.dH, Zd, net.p + o.hW[n], Zd, t.dX, D, rows, Zd, D, 1, st)) return e;
+  }
+  PN_LAUNCH("k_drift_combine", st,
+            k_drift_combine<R><<<nblk(Wn, 64), 64, 0, st>>>(s, t.geo, t.lse, t.J, t.gr, t.dd, Wn, logabs, grad));
+  return PN_OK;
+}
+
+template <typename R>
+static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const double* r, const double* u, int Wn,
+                      double* grad, cudaStream_t st) {
+  const int N = s.N, D = s.D, Zd = s.Zd, L = s.L, P = s.Ppair, Hw = s.Hw, no = s.n_orb, K = s.K;
+  const NetOff& o = net.off;
+  const int rows = Wn * N;
+  const size_t WND = (size_t)Wn * N * D;
+  R* XL = t.X + (size_t)L * WND;
+  if (int e = tape_value_pass<R>(s, net, t, r, Wn, false, st)) return e;
 
   // ---------------- backward
   WgBatch<R> wg;
@@ -789,7 +1043,7 @@ static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const d
   wg.t = &t;
   wg.grad = grad;
   wg.reset();
-  PN_LAUNCH("k_slater_bwd", st, k_slater_bwd<R><<<nblk(Wn, 32), 32, 0, st>>>(s, t.phi, t.F, u, Wn, t.dF, t.dJ));
+  if (int e = slater_bwd<R>(s, t, u, Wn, nullptr, nullptr, st)) return e;
   // kappa head
   if (int e = wg.add(t.kS2, D, t.dF, no, rows, D, no, -1, o.kW[2], 0, 0)) return e;
   if (int e = wg.add(nullptr, 0, t.dF, no, rows, 1, no, -1, o.kb[2], 0, 0)) return e;
@@ -870,6 +1124,21 @@ static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const d
   return wg.flush(st);
 }
 
+// Grows the system's tape allocation to at least `bytes` (never shrinks it).
+static int ensure_tape(pn_system_s* sys, size_t bytes) {
+  if (bytes <= sys->tape_bytes) return PN_OK;
+  if (sys->tape_mem) cudaFree(sys->tape_mem);
+  sys->tape_mem = nullptr;
+  sys->tape_bytes = 0;
+  if (cudaMalloc(&sys->tape_mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    pn_set_error("cannot allocate %zu bytes of tape", bytes);
+    return PN_ENOMEM;
+  }
+  sys->tape_bytes = bytes;
+  return PN_OK;
+}
+
 template <typename R>
 static int grad_impl(pn_system_s* sys, const double* r, int W, const double* cot, double* grad, size_t budget,
                      cudaStream_t st) {
@@ -891,17 +1160,7 @@ static int grad_impl(pn_system_s* sys, const double* r, int W, const double* cot
   int Wb = (int)std::min<size_t>((size_t)W, (budget - fixed) / per);
   Wb = std::max(1, Wb);
   const size_t bytes = fixed + per * Wb + 65536;
-  if (bytes > sys->tape_bytes) {
-    if (sys->tape_mem) cudaFree(sys->tape_mem);
-    sys->tape_mem = nullptr;
-    sys->tape_bytes = 0;
-    if (cudaMalloc(&sys->tape_mem, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      pn_set_error("grad: cannot allocate %zu bytes of tape", bytes);
-      return PN_ENOMEM;
-    }
-    sys->tape_bytes = bytes;
-  }
+  if (int e = ensure_tape(sys, bytes)) return e;
   Tape<R> t = carve_tape<R>(s, Wb, sys->tape_mem, part_elems);
   if (t.end > (char*)sys->tape_mem + sys->tape_bytes) {
     pn_set_error("grad: tape layout (%zu bytes) exceeds its allocation (%zu)", (size_t)(t.end - (char*)sys->tape_mem),
@@ -941,6 +1200,25 @@ static int grad_impl(pn_system_s* sys, const double* r, int W, const double* cot
   if (!rdev || !udev || !gdev) PN_CUDA(cudaStreamSynchronize(st));
   return PN_OK;
 }
+
+template <typename R>
+int pn_drift_reverse(pn_system_s* sys, const double* r, int Wn, double* logabs, double* grad, cudaStream_t st) {
+  if (Wn <= 0) return PN_OK;
+  const DevSys& s = sys->ds;
+  // the tape is sized for a whole workspace chunk so that it is carved once
+  const int Wb = std::max(Wn, sys->Wc);
+  const size_t bytes = tape_bytes_per_walker<R>(s) * (size_t)Wb + 4096 * 64 + 65536;
+  if (int e = ensure_tape(sys, bytes)) return e;
+  Tape<R> t = carve_tape<R>(s, Wb, sys->tape_mem, 0);
+  if (t.end > (char*)sys->tape_mem + sys->tape_bytes) {
+    pn_set_error("drift: tape layout (%zu bytes) exceeds its allocation (%zu)", (size_t)(t.end - (char*)sys->tape_mem),
+                 sys->tape_bytes);
+    return PN_EINVAL;
+  }
+  return drift_chunk<R>(s, pn_devnet<R>(sys), t, r, Wn, logabs, grad, st);
+}
+template int pn_drift_reverse<double>(pn_system_s*, const double*, int, double*, double*, cudaStream_t);
+template int pn_drift_reverse<float>(pn_system_s*, const double*, int, double*, double*, cudaStream_t);
 
 extern "C" int pn_grad_logpsi(pn_system_t s, const double* r, int W, const double* cot, double* grad, size_t budget,
                               void* stream) {

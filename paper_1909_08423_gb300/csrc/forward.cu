@@ -58,6 +58,9 @@ __global__ void k_orbitals(DevSys s, const double* __restrict__ r, int Wn, doubl
 // ------------------------------------------------------------- features
 // e_k(d) = d^2 exp(-d - (d - mu_k)^2 / sigma_k^2) and its first two
 // derivatives in d, for every pair: efeat[w][p][c][k], c = value, d/dd, d2/dd2.
+// Evaluated in the network's precision R: a float32 network consumes float32
+// features, and float64 exponentials run at a small fraction of the float32
+// rate on this GPU.
 template <typename R>
 __global__ void k_features(DevSys s, const double* __restrict__ geo, int Wn, int jet, R* __restrict__ ef) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -65,15 +68,16 @@ __global__ void k_features(DevSys s, const double* __restrict__ geo, int Wn, int
   if (idx >= total) return;
   const int k = idx % s.K;
   const size_t wp = idx / s.K;
-  const double d = geo[wp * 4];
-  const double mu = s.feat_mu[k], is2 = s.feat_isig2[k];
-  const double E = exp(-d - (d - mu) * (d - mu) * is2);
+  const R d = (R)geo[wp * 4];
+  const R mu = sizeof(R) == 4 ? (R)s.feat_mu32[k] : (R)s.feat_mu[k];
+  const R is2 = sizeof(R) == 4 ? (R)s.feat_isig2_32[k] : (R)s.feat_isig2[k];
+  const R E = exp(-d - (d - mu) * (d - mu) * is2);
   R* o = ef + wp * 3 * s.K;
-  o[k] = (R)(d * d * E);
+  o[k] = d * d * E;
   if (jet) {
-    const double q = -1.0 - 2.0 * (d - mu) * is2;  // derivative of the exponent
-    o[s.K + k] = (R)(E * (2.0 * d + d * d * q));
-    o[2 * s.K + k] = (R)(E * (2.0 + 4.0 * d * q + d * d * (q * q - 2.0 * is2)));
+    const R q = R(-1) - R(2) * (d - mu) * is2;  // derivative of the exponent
+    o[s.K + k] = E * (R(2) * d + d * d * q);
+    o[2 * s.K + k] = E * (R(2) + R(4) * d * q + d * d * (q * q - R(2) * is2));
   }
 }
 
@@ -789,13 +793,16 @@ int pn_launch_geometry_orbitals(const DevSys& s, const double* r, int Wn, double
 }
 
 template <typename R>
-int pn_launch_features_init(const DevSys& s, const R* x0, const double* geo, int Wn, R* ef, R* X, cudaStream_t st) {
-  PN_LAUNCH("k_features", st, k_features<R><<<nblk((size_t)Wn * s.Ppair * s.K, 256), 256, 0, st>>>(s, geo, Wn, 0, ef));
+int pn_launch_features_init(const DevSys& s, const R* x0, const double* geo, int Wn, int deriv, R* ef, R* X,
+                            cudaStream_t st) {
+  PN_LAUNCH("k_features", st, k_features<R><<<nblk((size_t)Wn * s.Ppair * s.K, 256), 256, 0, st>>>(s, geo, Wn, deriv, ef));
   PN_LAUNCH("k_init_x", st, k_init_x<R><<<nblk((size_t)Wn * s.N * s.D, 256), 256, 0, st>>>(x0, X, (size_t)Wn * s.N, 1, s.D));
   return PN_OK;
 }
-template int pn_launch_features_init<double>(const DevSys&, const double*, const double*, int, double*, double*, cudaStream_t);
-template int pn_launch_features_init<float>(const DevSys&, const float*, const double*, int, float*, float*, cudaStream_t);
+template int pn_launch_features_init<double>(const DevSys&, const double*, const double*, int, int, double*, double*,
+                                             cudaStream_t);
+template int pn_launch_features_init<float>(const DevSys&, const float*, const double*, int, int, float*, float*,
+                                            cudaStream_t);
 
 template <typename R>
 int pn_launch_sum_electrons(const R* X, R* Xs, int Wn, int N, int D, cudaStream_t st) {

@@ -44,7 +44,9 @@ __device__ inline void pn_normals4(unsigned long long seed, unsigned walker, uns
 
 int pn_launch_geometry_orbitals(const DevSys& s, const double* r, int Wn, double* geo, double* phi, cudaStream_t st);
 template <typename R>
-int pn_launch_features_init(const DevSys& s, const R* x0, const double* geo, int Wn, R* ef, R* X, cudaStream_t st);
+// deriv = 1 also writes the first and second distance derivatives of the features
+int pn_launch_features_init(const DevSys& s, const R* x0, const double* geo, int Wn, int deriv, R* ef, R* X,
+                            cudaStream_t st);
 template <typename R>
 int pn_launch_sum_electrons(const R* X, R* Xs, int Wn, int N, int D, cudaStream_t st);
 

@@ -186,6 +186,7 @@ struct pn_system_s {
   NetOff off;
   int precision;
   int no_jastrow, no_backflow;  // ablation variants: head removed
+  int drift_mode;               // grad_r ln|psi| for Langevin moves: 0 jet pass, 1 reverse mode
   int Wc;
   int Tjet;
   // device allocations
@@ -254,6 +255,12 @@ template <typename R>
 int pn_run_metropolis_fused(const DevSys& s, const DevNet<R>& net, double* r, double* lp, int W, unsigned walker0,
                             int n_steps, double sigma, unsigned long long seed, unsigned long long step0,
                             unsigned long long* n_acc, cudaStream_t st);
+
+// ln|psi| and grad_r ln|psi| of Wn <= max(Wc, Wn) walkers at device
+// positions r by reverse mode (backward.cu), on the system's tape (grown on
+// demand); logabs [Wn] and grad [Wn][N][3] are device buffers.
+template <typename R>
+int pn_drift_reverse(pn_system_s* sys, const double* r, int Wn, double* logabs, double* grad, cudaStream_t st);
 
 // Host/device pointer check.
 bool pn_is_device_ptr(const void* p);

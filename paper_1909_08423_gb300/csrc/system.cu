@@ -567,6 +567,7 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   s->precision = d->precision;
   s->no_jastrow = d->no_jastrow ? 1 : 0;
   s->no_backflow = d->no_backflow ? 1 : 0;
+  s->drift_mode = 1;
   DevSys& ds = s->ds;
   ds.N = N; ds.n_up = d->n_up; ds.n_dn = d->n_dn; ds.M = d->M; ds.n_b = nb; ds.n_orb = d->n_orb;
   ds.n_det = d->n_det; ds.n_shells = d->n_shells;

@@ -1,6 +1,7 @@
 """Langevin (drift-diffusion) sampler through the C ABI against the oracle.
 
-The drift grad ln|psi| of the FP64 path matches the oracle's reverse-mode
+The drift grad ln|psi| of the FP64 path, formed both in reverse mode (the
+default) and by the forward jet pass, matches the oracle's reverse-mode
 gradient to rounding; the FP64 chain reproduces the oracle's chain (same
 Philox stream, same clipping of the drift at the nearest nucleus); the
 mixed chain makes only moves the oracle would propose from the same state,
@@ -33,13 +34,15 @@ def _equilibrated(o, W, seed):
     return r
 
 
+@pytest.mark.parametrize("mode", [1, 0], ids=["reverse", "jet"])
 @pytest.mark.parametrize("name,W", [("be", 64), ("h10", 16), ("n2", 6)])
-def test_drift_matches_oracle(lib, oracles, name, W):
+def test_drift_matches_oracle(lib, oracles, name, W, mode):
     o = oracles[name]
     r = _equilibrated(o, W, 3)
     lp_o, _, g_o = o.value_and_grad(r)
     for prec, tol in ((0, 1e-8), (1, 2e-3)):
         s = lib.System(o.sys, precision=prec, max_walkers=32)
+        s.set_option(lib.PN_OPT_DRIFT, mode)
         rd = torch.as_tensor(r, device="cuda")
         g = torch.empty_like(rd)
         lp = torch.empty(W, dtype=torch.float64, device="cuda")
@@ -59,13 +62,15 @@ def test_drift_matches_oracle(lib, oracles, name, W):
         np.testing.assert_array_equal(gh, gn)
 
 
+@pytest.mark.parametrize("mode", [1, 0], ids=["reverse", "jet"])
 @pytest.mark.parametrize("name,W,steps,tau", [("be", 48, 4, 0.1), ("h10", 12, 2, 0.1), ("n2", 4, 2, 0.05)])
-def test_langevin_fp64_matches_oracle(lib, oracles, name, W, steps, tau):
+def test_langevin_fp64_matches_oracle(lib, oracles, name, W, steps, tau, mode):
     o = oracles[name]
     r0 = _equilibrated(o, W, 5)
     lp0, _, g0 = o.value_and_grad(r0)
     ro, lpo, go, acco = sampling.langevin(o, r0, lp0, g0, steps, tau, seed=11, step0=300)
     s = lib.System(o.sys, precision=lib.PN_FP64, max_walkers=32)
+    s.set_option(lib.PN_OPT_DRIFT, mode)
     rd = torch.as_tensor(r0, device="cuda").clone()
     lpd = torch.as_tensor(lp0, device="cuda").clone()
     gd = torch.as_tensor(g0, device="cuda").clone()
@@ -118,6 +123,49 @@ def test_langevin_mixed_moves_are_valid(lib, oracles, name, W, steps):
         assert np.all(np.abs(margin[differ]) < 1e-3), margin[differ]
         flips += int(differ.sum())
     assert flips <= max(1, W * steps // 20)
+
+
+_VARIANTS = {
+    # the ablation variants, a system without the cusp corrections and LiH
+    "be_no_heads": lambda: synth.make_system([4.0], [[0, 0, 0]], lambda z: {0: 4, 1: 2}, n_det=4, D=64, K=32, L=3,
+                                             seed=0, no_jastrow=1, no_backflow=1),
+    "be_no_backflow": lambda: synth.make_system([4.0], [[0, 0, 0]], lambda z: {0: 4, 1: 2}, n_det=1, D=64, K=32, L=3,
+                                                seed=0, no_backflow=1),
+    "lih_plain": lambda: synth.lih(use_cusp=False, use_gamma=False),
+    "lih": synth.lih,
+}
+
+
+@pytest.mark.parametrize("name", list(_VARIANTS))
+def test_reverse_drift_equals_jet_drift(lib, name):
+    """Both ways of forming grad_r ln|psi| give the same numbers: to rounding
+    on the FP64 path, to float32 accuracy on the mixed path; chunked (W above
+    the workspace) and host buffers included."""
+    sysd = _VARIANTS[name]()
+    W = 72
+    r = synth.random_walkers(sysd, W, 8)
+    for prec, tol in ((0, 1e-9), (1, 2e-3)):
+        s = lib.System(sysd, precision=prec, max_walkers=32)
+        out = {}
+        for mode in (0, 1):
+            s.set_option(lib.PN_OPT_DRIFT, mode)
+            g = np.empty(r.shape)
+            lp = np.empty(W)
+            s.eval_drift(np.ascontiguousarray(r), g, lp)
+            out[mode] = (g, lp)
+        (g0, l0), (g1, l1) = out[0], out[1]
+        fin = np.isfinite(l0)
+        assert fin.mean() > 0.9
+        np.testing.assert_array_equal(np.isfinite(l1), fin)
+        np.testing.assert_allclose(l1[fin], l0[fin], rtol=0, atol=1e-10 if prec == 0 else 1e-4)
+        err = np.abs(g1[fin] - g0[fin]) / (1.0 + np.abs(g0[fin]))
+        assert err.max() < tol, (prec, err.max())
+
+
+def test_drift_option_rejects_bad_values(lib):
+    s = lib.System(synth.be(), precision=lib.PN_FP64, max_walkers=8)
+    with pytest.raises(lib.PNError):
+        s.set_option(lib.PN_OPT_DRIFT, 2)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
