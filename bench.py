@@ -337,6 +337,48 @@ def run_vmc_train(sysd, steps=10):
             "note": "host-timed (the parameter upload synchronises); refill = 50 + 500 Metropolis steps of 2000 walkers"}
 
 
+def run_ablation(W=4096, steps=3):
+    """The paper's ablation variants on the bench atom (single or four
+    determinants, with or without backflow, and both heads removed): the
+    bench step (100 Metropolis steps + E_loc + clipping + backward) of W
+    walkers per variant, mixed path, CUDA events."""
+    import torch
+    from paper_1909_08423_gb300 import binding, synth
+    variants = {"SD-SJ": (1, 0, 1), "SD-BF": (1, 0, 0), "MD-SJ": (4, 0, 1), "MD-BF": (4, 0, 0), "MD-none": (4, 1, 1)}
+    out = {}
+    for name, (nd, nj, nb) in variants.items():
+        sysd = synth.make_system([4.0], [[0, 0, 0]], lambda z: {0: 4, 1: 2}, n_det=nd, D=64, K=32, L=3, seed=0,
+                                 no_jastrow=nj, no_backflow=nb)
+        s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=W)
+        r = torch.empty(W, s.N, 3, dtype=torch.float64, device="cuda")
+        s.init_walkers(r, 5)
+        lp = torch.empty(W, dtype=torch.float64, device="cuda")
+        sg = torch.empty_like(lp)
+        s.eval_logpsi(r, lp, sg)
+        E, Ec, cot = torch.empty_like(lp), torch.empty_like(lp), torch.empty_like(lp)
+        g = torch.empty(s.n_params, dtype=torch.float64, device="cuda")
+
+        def step(k):
+            s.metropolis_step(r, lp, N_METROPOLIS, SIGMA, 5, k * N_METROPOLIS)
+            s.eval_local_energy(r, E)
+            binding.clip_local_energy(E, Ec, cot)
+            s.grad_logpsi(r, cot, g)
+
+        step(0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(steps):
+            step(1 + k)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"n_det": nd, "jastrow": not nj, "backflow": not nb, "ms_per_step": ms,
+                     "walker_eloc_per_s": W / (ms / 1e3), "e_mean": float(Ec.mean())}
+        s.close()
+    return out
+
+
 def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384, load=0.7,
                 precisions=("mixed", "fp64"), sweep=()):
     """Poisson stream of seeded molecules through the serving loop, mixed and
@@ -421,7 +463,7 @@ def main():
     ap.add_argument("--serve-sweep", default="", help="further loads for the mixed server, e.g. 0.5,0.9")
     ap.add_argument("--sampler", type=int, default=None,
                     help="PN_OPT_FUSED_SAMPLER for the timed mixed path (library default if absent)")
-    ap.add_argument("--case", choices=["sampler", "jet_tc"], default=None,
+    ap.add_argument("--case", choices=["sampler", "jet_tc", "langevin"], default=None,
                     help="run one small kernel case (for ncu captures) and exit")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -444,6 +486,11 @@ def main():
             sg = torch.empty_like(lp)
             s.eval_logpsi(r, lp, sg)
             s.metropolis_step(r, lp, 5, SIGMA, 3, 0)
+        elif args.case == "langevin":  # initial drift + 3 Langevin steps of the Be workload
+            lp = torch.empty(W_PER_RANK, dtype=torch.float64, device="cuda")
+            g = torch.empty_like(r)
+            s.eval_drift(r, g, lp)
+            s.langevin_step(r, lp, g, 3, 0.1, 3, 0)
         else:  # one local-energy pass with every layer group on tcgen05
             s.set_option(binding.PN_OPT_TENSOR_CORES, 7)
             E = torch.empty(W_PER_RANK, dtype=torch.float64, device="cuda")
@@ -689,6 +736,7 @@ def main():
         line["langevin"] = run_langevin(sysd, W)
         line["line_scan"] = run_line_scan()
         line["vmc_train"] = run_vmc_train(sysd)
+        line["ablation"] = run_ablation(W)
     if rank == 0 and args.serve_jobs > 0:
         line["serve"] = run_serving(args.serve_jobs)
     if rank == 0:
