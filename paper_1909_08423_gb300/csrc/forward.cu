@@ -406,6 +406,119 @@ __global__ void __launch_bounds__(256) k_message(DevSys s, const R* __restrict__
   }
 }
 
+// Same messages, one thread per (walker, row chunk, electron i, column z):
+// chunk c < ceil(N/2) holds the tangent rows of electrons 2c and 2c + 1
+// (t = 1 + 3k + a), the last chunk the value row and the Laplacian row.
+// Each partner's filter jet, geometry and value row are read once per
+// chunk, and the product-rule factor d d_ij / d r_{k,a} is resolved per
+// electron k, so a row costs one h load and two multiply-adds per partner.
+// Arithmetic per row is that of k_message.
+template <typename R>
+__global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict__ Y, const double* __restrict__ geo,
+                                                   const R* __restrict__ wj, const R* __restrict__ H, int ldH, int Wn,
+                                                   int T, R* __restrict__ Zb, int ldZ) {
+  const int Zd = s.Zd, N = s.N, M = s.M;
+  const int nTan = (N + 1) / 2, nC = nTan + 1;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)Wn * nC * N * Zd) return;
+  const int z = idx % Zd;
+  const int i = (idx / Zd) % N;
+  const int c = (idx / ((size_t)Zd * N)) % nC;
+  const int w = idx / ((size_t)Zd * N * nC);
+  const int lap = T - 1;
+  const bool si = i < s.n_up;
+  const R* Hw_ = H + (size_t)w * N * T * ldH + z;
+  const R* ww = wj + (size_t)w * s.Ppair * 3 * Zd + z;
+  const double* gw = geo + (size_t)w * s.Ppair * 4;
+  R* ob = Zb + (size_t)(w * N + i) * T * ldZ + z;
+  if (c < nTan) {
+    const int k0 = 2 * c, nk = (k0 + 1 < N) ? 2 : 1;
+    R zs[6], za[6], zq[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) zs[q] = za[q] = zq[q] = 0;
+    for (int j = 0; j < N; ++j) {
+      if (j == i) continue;
+      const int p = i < j ? pn_pair_index(i, j, N) : pn_pair_index(j, i, N);
+      const double* g = gw + p * 4;
+      const R sg = i < j ? R(1) : R(-1);  // unit vector from j to i
+      const R u[3] = {sg * (R)g[1], sg * (R)g[2], sg * (R)g[3]};
+      const R w0 = ww[(size_t)p * 3 * Zd], w1 = ww[(size_t)p * 3 * Zd + Zd];
+      const R* hj = Hw_ + (size_t)j * T * ldH;
+      const R h0 = hj[0];
+      const bool same = (j < s.n_up) == si;
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        if (kk >= nk) break;
+        const int k = k0 + kk;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const R dd = (k == i) ? u[a] : ((k == j) ? -u[a] : R(0));
+          const R v = w1 * dd * h0 + w0 * hj[(size_t)(1 + 3 * k + a) * ldH];
+          if (same) zs[3 * kk + a] += v; else za[3 * kk + a] += v;
+        }
+      }
+    }
+    for (int I = 0; I < M; ++I) {
+      const int p = s.Pee + i * M + I;
+      const double* g = gw + p * 4;
+      const R y = Y[I * Zd + z];
+      const R w1 = ww[(size_t)p * 3 * Zd + Zd];
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        if (kk >= nk) break;
+        if (k0 + kk == i)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) zq[3 * kk + a] += w1 * (R)g[1 + a] * y;
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      if (kk >= nk) break;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        R* o = ob + (size_t)(1 + 3 * (k0 + kk) + a) * ldZ;
+        o[0] = zs[3 * kk + a];
+        o[Zd] = za[3 * kk + a];
+        o[2 * Zd] = zq[3 * kk + a];
+      }
+    }
+    return;
+  }
+  // value row and Laplacian row
+  R vs = 0, va = 0, vq = 0, ls = 0, la = 0, lq = 0;
+  for (int j = 0; j < N; ++j) {
+    if (j == i) continue;
+    const int p = i < j ? pn_pair_index(i, j, N) : pn_pair_index(j, i, N);
+    const double* g = gw + p * 4;
+    const R sg = i < j ? R(1) : R(-1);
+    const R id = R(1) / (R)g[0];
+    const R w0 = ww[(size_t)p * 3 * Zd], w1 = ww[(size_t)p * 3 * Zd + Zd], w2 = ww[(size_t)p * 3 * Zd + 2 * Zd];
+    const R* hj = Hw_ + (size_t)j * T * ldH;
+    const R h0 = hj[0];
+    R cross = 0;
+    for (int a = 0; a < 3; ++a)
+      cross += sg * (R)g[1 + a] * (hj[(size_t)(1 + 3 * i + a) * ldH] - hj[(size_t)(1 + 3 * j + a) * ldH]);
+    const R v0 = w0 * h0;
+    const R vl = (R(2) * w2 + R(4) * w1 * id) * h0 + w0 * hj[(size_t)lap * ldH] + R(2) * w1 * cross;
+    if ((j < s.n_up) == si) { vs += v0; ls += vl; } else { va += v0; la += vl; }
+  }
+  for (int I = 0; I < M; ++I) {
+    const int p = s.Pee + i * M + I;
+    const double* g = gw + p * 4;
+    const R y = Y[I * Zd + z];
+    const R* wp = ww + (size_t)p * 3 * Zd;
+    vq += wp[0] * y;
+    lq += (wp[2 * Zd] + R(2) * wp[Zd] * (R(1) / (R)g[0])) * y;
+  }
+  ob[0] = vs;
+  ob[Zd] = va;
+  ob[2 * Zd] = vq;
+  R* ol = ob + (size_t)lap * ldZ;
+  ol[0] = ls;
+  ol[Zd] = la;
+  ol[2 * Zd] = lq;
+}
+
 // ---------------------------------------------------- activation on a jet
 // s = ssp(a): s_t = sigma(a) a_t, lap s = sigma(a) lap a + sigma'(a) sum_t a_t^2.
 template <typename R>
@@ -730,10 +843,17 @@ int pn_network_layers(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn,
                              s.Zd, T, 0, st))
       return e;
     PN_LAUNCH("k_filter", st, k_filter<R><<<nblk((size_t)Wn * s.Ppair, FW), FW * 32, 0, st>>>(s, net, n, w.efeat, Wn, jet, w.wjet));
-    PN_LAUNCH("k_message", st,
-              k_message<R><<<(unsigned)((size_t)Wn * s.N), std::min(256, (T * s.Zd + 31) / 32 * 32),
-                             (size_t)(s.N - 1 + s.M) * 5 * sizeof(R), st>>>(
-                  s, net.p + net.off.Y, w.geo, w.wjet, w.H, w.ldH, Wn, T, w.Zb, w.ldZ));
+    if (jet) {
+      const size_t nthr = (size_t)Wn * ((s.N + 1) / 2 + 1) * s.N * s.Zd;
+      PN_LAUNCH("k_message", st,
+                k_message_c<R><<<nblk(nthr, 256), 256, 0, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H, w.ldH, Wn,
+                                                                 T, w.Zb, w.ldZ));
+    } else {
+      PN_LAUNCH("k_message", st,
+                k_message<R><<<(unsigned)((size_t)Wn * s.N), std::min(256, (T * s.Zd + 31) / 32 * 32),
+                               (size_t)(s.N - 1 + s.M) * 5 * sizeof(R), st>>>(
+                    s, net.p + net.off.Y, w.geo, w.wjet, w.H, w.ldH, Wn, T, w.Zb, w.ldZ));
+    }
     if (int e = pn_linear<R>(&s, PN_TC_LAYERS, w.Zb, w.ldZ, net.Gcat + (size_t)n * 3 * s.Zd * s.D, s.D, net.Gb + (size_t)n * s.D, w.X,
                              s.D, rows, 3 * s.Zd, s.D, T, 1, st))
       return e;
