@@ -933,7 +933,12 @@ static int tape_value_pass(const DevSys& s, const DevNet<R>& net, Tape<R>& t, co
     R* Ahn = t.Ah + (size_t)n * Wn * P * Hw;
     R* wn = t.wv + (size_t)n * Wn * P * Zd;
     if (int e = pn_linear<R>(&s, PN_TC_VALUE, Xn, D, net.p + o.hW[n], Zd, net.p + o.hb[n], Hn, Zd, rows, D, Zd, 1, 0, st)) return e;
-    PN_LAUNCH("k_filter_tape", st, k_filter_tape<R><<<nblk((size_t)Wn * P, 8), 256, 0, st>>>(s, net, n, t.ef, Wn, Ahn, wn));
+    int fe = PN_ENOTREADY;
+    if constexpr (sizeof(R) == 4)
+      fe = pn_filter_tile_value(s, net, n, (const float*)t.ef, Wn, (float*)Ahn, (float*)wn, st);
+    if (fe != PN_OK && fe != PN_ENOTREADY) return fe;
+    if (fe == PN_ENOTREADY)
+      PN_LAUNCH("k_filter_tape", st, k_filter_tape<R><<<nblk((size_t)Wn * P, 8), 256, 0, st>>>(s, net, n, t.ef, Wn, Ahn, wn));
     PN_LAUNCH("k_message_value", st, k_message_value<R><<<nblk((size_t)rows * Zd, 256), 256, 0, st>>>(s, net.p + o.Y, wn, Hn, Wn, Zn));
     PN_CUDA(cudaMemcpyAsync(Xn1, Xn, WND * sizeof(R), cudaMemcpyDeviceToDevice, st));
     if (int e = pn_linear<R>(&s, PN_TC_VALUE, Zn, 3 * Zd, net.Gcat + (size_t)n * 3 * Zd * D, D, net.Gb + (size_t)n * D, Xn1, D, rows,
@@ -963,6 +968,10 @@ static int tape_value_pass(const DevSys& s, const DevNet<R>& net, Tape<R>& t, co
 template <typename R>
 static int filter_bwd_dist(const DevSys& s, const DevNet<R>& net, int n, const R* Ah, const R* ef, const R* dw, int Wn,
                            double* dd, cudaStream_t st) {
+  if constexpr (sizeof(R) == 4) {
+    const int fe = pn_filter_tile_dist(s, net, n, (const float*)Ah, (const float*)ef, (const float*)dw, Wn, dd, st);
+    if (fe != PN_ENOTREADY) return fe;
+  }
   const size_t tail = (size_t)8 * (s.Zd + s.K) * sizeof(R);
   const size_t fb = (size_t)3 * s.Hw * (s.Zd + 1) * sizeof(R) + tail;
   int dev = 0, maxsm = 0;
@@ -1089,7 +1098,11 @@ static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const d
     PN_LAUNCH("k_msg_bwd_h", st, k_msg_bwd_h<R><<<nblk((size_t)rows * Zd, 256), 256, 0, st>>>(s, wn, t.dZ, Wn, t.dH, t.dYr));
     if (int e = wg.add(nullptr, 0, t.dYr, s.M * Zd, rows, 1, s.M * Zd, -1, o.Y, 0, 0)) return e;
     // filters, per channel
-    {
+    int fe = PN_ENOTREADY;
+    if constexpr (sizeof(R) == 4)
+      fe = pn_filter_tile_bwd(s, net, n, (const float*)Ahn, (const float*)t.dw, Wn, (float*)t.dAh, (float*)t.Sh, st);
+    if (fe != PN_OK && fe != PN_ENOTREADY) return fe;
+    if (fe == PN_ENOTREADY) {
       const size_t fb = ((size_t)3 * Hw * (Zd + 1) + 8 * Zd) * sizeof(R);
       int dev = 0, maxsm = 0;
       cudaGetDevice(&dev);

@@ -216,94 +216,149 @@ __global__ void __launch_bounds__(256) k_linear(const R* __restrict__ X, int ldx
   }
 }
 
-// Float32 Y (+)= X W + b (bias on value rows only), 128 x 64 output tiles,
-// 8 x 4 outputs per thread, float4 loads of X and of shared memory.
-// Requires ldx and Kd multiples of 4 and a 16-byte aligned X (the caller
-// checks).  VEC_W: float4 loads of W (ldw, Nout multiples of 4, W aligned),
-// else element loads; VEC_Y: float4 stores of Y (ldy, Nout multiples of 4,
-// Y aligned), else element stores.
-template <bool VEC_W, bool VEC_Y>
-__global__ void __launch_bounds__(256) k_linear_v4(const float* __restrict__ X, int ldx, const float* __restrict__ W,
-                                                   int ldw, const float* __restrict__ bias, float* __restrict__ Y,
-                                                   int ldy, int rows, int Kd, int Nout, int T, int accumulate) {
-  __shared__ __align__(16) float As[16][128 + 4];
-  __shared__ __align__(16) float Bs[16][64];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int row0 = blockIdx.x * 128, col0 = blockIdx.y * 64;  // row tiles in x: no 65535 limit
-  float acc[8][4];
+// Float32 Y (+)= X W + b (bias on value rows only): BM x BN output tiles,
+// 8 x TN outputs per thread -- 256 x 32 (TN 4) for maps at most 32 wide so
+// that no half-empty tiles are computed, 128 x 64 (TN 4) up to 64, 128 x 128
+// (TN 8, the thread's columns in two float4 groups 64 apart) beyond.  16-deep
+// k slices are double-buffered in shared memory: the next slice's global
+// loads are issued before the current slice's multiply-adds and stored
+// after them, one barrier per slice.  Requires ldx and Kd multiples of 4 and
+// a 16-byte aligned X (the caller checks).  VEC_W: float4 loads of W (ldw,
+// Nout multiples of 4, W aligned), else element loads; VEC_Y: float4 stores
+// of Y (ldy, Nout multiples of 4, Y aligned), else element stores.
+template <int BM, int BN, int TN, bool VEC_W, bool VEC_Y>
+__global__ void __launch_bounds__(256, TN == 8 ? 2 : 3)
+    k_linear_v4(const float* __restrict__ X, int ldx, const float* __restrict__ W, int ldw,
+                const float* __restrict__ bias, float* __restrict__ Y, int ldy, int rows, int Kd, int Nout, int T,
+                int accumulate) {
+  static_assert((BM / 8) * (BN / TN) == 256 && (TN == 4 || TN == 8), "256 threads x 8 x TN outputs");
+  constexpr int TX = BN / TN;            // threads across the columns
+  constexpr int CG = TN / 4;             // float4 column groups per thread
+  constexpr int CS = BN / CG;            // distance between a thread's column groups
+  constexpr int AL = BM / 64;            // float4 loads of an A slice per thread
+  constexpr int BL = (4 * BN + 255) / 256;  // float4 loads of a B slice per thread
+  constexpr int BS = 16 * BN / 256;      // element loads of a B slice per thread
+  __shared__ __align__(16) float As[2][16][BM + 4];
+  __shared__ __align__(16) float Bs[2][16][BN];
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;  // row tiles in x: no 65535 limit
+  float acc[8][TN];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int k0 = 0; k0 < Kd; k0 += 16) {
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+  float4 ra[AL];
+  float4 rb4[BL];
+  float rbs[BS > 0 ? BS : 1];
+  auto load = [&](int k0) {
 #pragma unroll
-    for (int l = 0; l < 2; ++l) {
+    for (int l = 0; l < AL; ++l) {
       const int e = tid + l * 256;
-      const int rr = e >> 2, k4 = (e & 3) * 4;
-      const int gr = row0 + rr, gk = k0 + k4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gr < rows && gk < Kd) v = *(const float4*)(X + (size_t)gr * ldx + gk);
-      As[k4][rr] = v.x;
-      As[k4 + 1][rr] = v.y;
-      As[k4 + 2][rr] = v.z;
-      As[k4 + 3][rr] = v.w;
+      const int gr = row0 + (e >> 2), gk = k0 + (e & 3) * 4;
+      ra[l] = (gr < rows && gk < Kd) ? *(const float4*)(X + (size_t)gr * ldx + gk) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if constexpr (VEC_W) {
-      const int kb = tid >> 4, c4 = (tid & 15) * 4;
-      const int gk = k0 + kb, gc = col0 + c4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gk < Kd && gc < Nout) v = *(const float4*)(W + (size_t)gk * ldw + gc);
-      *(float4*)&Bs[kb][c4] = v;
+#pragma unroll
+      for (int l = 0; l < BL; ++l) {
+        const int e = tid + l * 256;
+        if (e < 4 * BN) {
+          const int gk = k0 + e / (BN / 4), gc = col0 + (e % (BN / 4)) * 4;
+          rb4[l] = (gk < Kd && gc < Nout) ? *(const float4*)(W + (size_t)gk * ldw + gc)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
     } else {
 #pragma unroll
-      for (int l = 0; l < 4; ++l) {
+      for (int l = 0; l < BS; ++l) {
         const int e = tid + l * 256;
-        const int kb = e >> 6, cb = e & 63;
-        const int gk = k0 + kb, gc = col0 + cb;
-        Bs[kb][cb] = (gk < Kd && gc < Nout) ? W[(size_t)gk * ldw + gc] : 0.f;
+        const int gk = k0 + e / BN, gc = col0 + e % BN;
+        rbs[l] = (gk < Kd && gc < Nout) ? W[(size_t)gk * ldw + gc] : 0.f;
       }
     }
-    __syncthreads();
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int l = 0; l < AL; ++l) {
+      const int e = tid + l * 256;
+      const int rr = e >> 2, k4 = (e & 3) * 4;
+      As[buf][k4][rr] = ra[l].x;
+      As[buf][k4 + 1][rr] = ra[l].y;
+      As[buf][k4 + 2][rr] = ra[l].z;
+      As[buf][k4 + 3][rr] = ra[l].w;
+    }
+    if constexpr (VEC_W) {
+#pragma unroll
+      for (int l = 0; l < BL; ++l) {
+        const int e = tid + l * 256;
+        if (e < 4 * BN) *(float4*)&Bs[buf][e / (BN / 4)][(e % (BN / 4)) * 4] = rb4[l];
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < BS; ++l) {
+        const int e = tid + l * 256;
+        Bs[buf][e / BN][e % BN] = rbs[l];
+      }
+    }
+  };
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < Kd; k0 += 16) {
+    const bool more = k0 + 16 < Kd;
+    if (more) load(k0 + 16);
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      const float4 a0 = *(const float4*)&As[kk][ty * 8], a1 = *(const float4*)&As[kk][ty * 8 + 4];
-      const float4 b = *(const float4*)&Bs[kk][tx * 4];
+      const float4 a0 = *(const float4*)&As[buf][kk][ty * 8], a1 = *(const float4*)&As[buf][kk][ty * 8 + 4];
       const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bb[4] = {b.x, b.y, b.z, b.w};
+      float bb[TN];
+#pragma unroll
+      for (int g = 0; g < CG; ++g) {
+        const float4 b = *(const float4*)&Bs[buf][kk][g * CS + tx * 4];
+        bb[4 * g] = b.x;
+        bb[4 * g + 1] = b.y;
+        bb[4 * g + 2] = b.z;
+        bb[4 * g + 3] = b.w;
+      }
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
     }
+    if (more) store(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
-  const int gc = col0 + tx * 4;
-  if (gc >= Nout) return;
-  float bv[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) bv[j] = (bias && gc + j < Nout) ? bias[gc + j] : 0.f;
+  for (int g = 0; g < CG; ++g) {
+    const int gc = col0 + g * CS + tx * 4;
+    if (gc >= Nout) continue;
+    float bv[4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int gr = row0 + ty * 8 + i;
-    if (gr >= rows) break;
-    const bool val = (gr % T) == 0;
-    float v[4];
+    for (int j = 0; j < 4; ++j) bv[j] = (bias && gc + j < Nout) ? bias[gc + j] : 0.f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = acc[i][j] + (val ? bv[j] : 0.f);
-    float* y = Y + (size_t)gr * ldy + gc;
-    if constexpr (VEC_Y) {
-      if (accumulate) {
-        const float4 o = *(const float4*)y;
-        v[0] += o.x;
-        v[1] += o.y;
-        v[2] += o.z;
-        v[3] += o.w;
+    for (int i = 0; i < 8; ++i) {
+      const int gr = row0 + ty * 8 + i;
+      if (gr >= rows) break;
+      const bool val = (gr % T) == 0;
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = acc[i][4 * g + j] + (val ? bv[j] : 0.f);
+      float* y = Y + (size_t)gr * ldy + gc;
+      if constexpr (VEC_Y) {
+        if (accumulate) {
+          const float4 o = *(const float4*)y;
+          v[0] += o.x;
+          v[1] += o.y;
+          v[2] += o.z;
+          v[3] += o.w;
+        }
+        *(float4*)y = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (gc + j < Nout) y[j] = accumulate ? y[j] + v[j] : v[j];
       }
-      *(float4*)y = make_float4(v[0], v[1], v[2], v[3]);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (gc + j < Nout) y[j] = accumulate ? y[j] + v[j] : v[j];
     }
   }
 }
@@ -805,15 +860,22 @@ int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw
     if (ldx % 4 == 0 && Kd % 4 == 0 && ((uintptr_t)X & 15) == 0) {
       const bool vw = ldw % 4 == 0 && Nout % 4 == 0 && ((uintptr_t)W & 15) == 0;
       const bool vy = ldy % 4 == 0 && Nout % 4 == 0 && ((uintptr_t)Y & 15) == 0;
-      dim3 grid((rows + 127) / 128, (Nout + 63) / 64);
       const float *xf = (const float*)X, *wf = (const float*)W, *bf = (const float*)b;
       float* yf = (float*)Y;
-      if (vw && vy)
-        PN_LAUNCH("k_linear", st, (k_linear_v4<true, true><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));
-      else if (vy)
-        PN_LAUNCH("k_linear", st, (k_linear_v4<false, true><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));
-      else
-        PN_LAUNCH("k_linear", st, (k_linear_v4<false, false><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));
+#define PN_LIN(BM, BN, TN)                                                                                    \
+  do {                                                                                                        \
+    dim3 grid((rows + BM - 1) / BM, (Nout + BN - 1) / BN);                                                    \
+    if (vw && vy)                                                                                             \
+      PN_LAUNCH("k_linear", st, (k_linear_v4<BM, BN, TN, true, true><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));   \
+    else if (vy)                                                                                              \
+      PN_LAUNCH("k_linear", st, (k_linear_v4<BM, BN, TN, false, true><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));  \
+    else                                                                                                      \
+      PN_LAUNCH("k_linear", st, (k_linear_v4<BM, BN, TN, false, false><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc))); \
+  } while (0)
+      if (Nout <= 32) PN_LIN(256, 32, 4);        // narrow maps
+      else if (Nout <= 64) PN_LIN(128, 64, 4);
+      else PN_LIN(128, 128, 8);
+#undef PN_LIN
       return PN_OK;
     }
   }
@@ -842,7 +904,16 @@ int pn_network_layers(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn,
     if (int e = pn_linear<R>(&s, PN_TC_LAYERS, w.X, s.D, net.p + net.off.hW[n], s.Zd, net.p + net.off.hb[n], w.H, w.ldH, rows, s.D,
                              s.Zd, T, 0, st))
       return e;
-    PN_LAUNCH("k_filter", st, k_filter<R><<<nblk((size_t)Wn * s.Ppair, FW), FW * 32, 0, st>>>(s, net, n, w.efeat, Wn, jet, w.wjet));
+    // jet filters on pair-row tiles for large batches; below about 128 k pair
+    // rows the per-row kernel's many small blocks hide latency better (Be,
+    // 4096 walkers x 10 pairs: 0.154 ms per pass per-row, 0.174 ms tiled)
+    int fe = PN_ENOTREADY;
+    if constexpr (sizeof(R) == 4)
+      if (jet && (size_t)Wn * s.Ppair >= ((size_t)1 << 17))
+        fe = pn_filter_tile_jet(s, net, n, (const float*)w.efeat, Wn, (float*)w.wjet, st);
+    if (fe != PN_OK && fe != PN_ENOTREADY) return fe;
+    if (fe == PN_ENOTREADY)
+      PN_LAUNCH("k_filter", st, k_filter<R><<<nblk((size_t)Wn * s.Ppair, FW), FW * 32, 0, st>>>(s, net, n, w.efeat, Wn, jet, w.wjet));
     if (jet) {
       const size_t nthr = (size_t)Wn * ((s.N + 1) / 2 + 1) * s.N * s.Zd;
       PN_LAUNCH("k_message", st,

@@ -43,12 +43,26 @@ __device__ inline void pn_normals4(unsigned long long seed, unsigned walker, uns
 }
 
 int pn_launch_geometry_orbitals(const DevSys& s, const double* r, int Wn, double* geo, double* phi, cudaStream_t st);
-template <typename R>
 // deriv = 1 also writes the first and second distance derivatives of the features
+template <typename R>
 int pn_launch_features_init(const DevSys& s, const R* x0, const double* geo, int Wn, int deriv, R* ef, R* X,
                             cudaStream_t st);
 template <typename R>
 int pn_launch_sum_electrons(const R* X, R* Xs, int Wn, int N, int D, cudaStream_t st);
+
+// Filter networks of layer n on tiles of 64 pair rows of one channel
+// (filter_tiles.cu, float32): value pass with the tape (Ah, w), jet pass
+// (w and its two distance derivatives, [row][3][Zd]), backward for the
+// weight gradients (dAh, ssp(Ah)) and backward to the pair distances
+// (dd += ...).  PN_ENOTREADY when a tile does not fit in shared memory.
+int pn_filter_tile_value(const DevSys& s, const DevNet<float>& net, int n, const float* ef, int Wn, float* Ah,
+                         float* wv, cudaStream_t st);
+int pn_filter_tile_jet(const DevSys& s, const DevNet<float>& net, int n, const float* ef, int Wn, float* wj,
+                       cudaStream_t st);
+int pn_filter_tile_bwd(const DevSys& s, const DevNet<float>& net, int n, const float* Ah, const float* dw, int Wn,
+                       float* dAh, float* Sh, cudaStream_t st);
+int pn_filter_tile_dist(const DevSys& s, const DevNet<float>& net, int n, const float* Ah, const float* ef,
+                        const float* dw, int Wn, double* dd, cudaStream_t st);
 
 // One Box-Muller pair (normals 4j + 2*pair and 4j + 2*pair + 1) of the same
 // stream as pn_normals4, so that the pairs of one block can go to different
