@@ -904,6 +904,10 @@ template <typename R>
 int linear_bt(const R* X, int ldx, const R* W, int ldw, R* Y, int ldy, int rows, int Kd, int Nout, int acc,
               cudaStream_t st) {
   if (rows <= 0) return PN_OK;
+  if constexpr (sizeof(R) == 4) {
+    const int e = pn_linear_bt_f32((const float*)X, ldx, (const float*)W, ldw, (float*)Y, ldy, rows, Kd, Nout, acc, st);
+    if (e != PN_ENOTREADY) return e;
+  }
   dim3 grid((rows + 63) / 64, (Nout + 63) / 64);
   PN_LAUNCH("k_linear_bt", st, k_linear_bt<R><<<grid, 256, 0, st>>>(X, ldx, W, ldw, Y, ldy, rows, Kd, Nout, acc));
   return PN_OK;

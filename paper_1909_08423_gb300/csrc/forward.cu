@@ -225,8 +225,10 @@ __global__ void __launch_bounds__(256) k_linear(const R* __restrict__ X, int ldx
 // after them, one barrier per slice.  Requires ldx and Kd multiples of 4 and
 // a 16-byte aligned X (the caller checks).  VEC_W: float4 loads of W (ldw,
 // Nout multiples of 4, W aligned), else element loads; VEC_Y: float4 stores
-// of Y (ldy, Nout multiples of 4, Y aligned), else element stores.
-template <int BM, int BN, int TN, bool VEC_W, bool VEC_Y>
+// of Y (ldy, Nout multiples of 4, Y aligned), else element stores.  TB:
+// the weight is stored transposed, W[n][k] with row stride ldw (Y = X W^T,
+// the backward's maps); its float4 loads then run along k.
+template <int BM, int BN, int TN, bool VEC_W, bool VEC_Y, bool TB = false>
 __global__ void __launch_bounds__(256, TN == 8 ? 2 : 3)
     k_linear_v4(const float* __restrict__ X, int ldx, const float* __restrict__ W, int ldw,
                 const float* __restrict__ bias, float* __restrict__ Y, int ldy, int rows, int Kd, int Nout, int T,
@@ -257,7 +259,24 @@ __global__ void __launch_bounds__(256, TN == 8 ? 2 : 3)
       const int gr = row0 + (e >> 2), gk = k0 + (e & 3) * 4;
       ra[l] = (gr < rows && gk < Kd) ? *(const float4*)(X + (size_t)gr * ldx + gk) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if constexpr (VEC_W) {
+    if constexpr (TB && VEC_W) {  // float4 along k of row n of W
+#pragma unroll
+      for (int l = 0; l < BL; ++l) {
+        const int e = tid + l * 256;
+        if (e < 4 * BN) {
+          const int gc = col0 + (e >> 2), gk = k0 + (e & 3) * 4;
+          rb4[l] = (gk < Kd && gc < Nout) ? *(const float4*)(W + (size_t)gc * ldw + gk)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+    } else if constexpr (TB) {
+#pragma unroll
+      for (int l = 0; l < BS; ++l) {
+        const int e = tid + l * 256;
+        const int gk = k0 + (e & 15), gc = col0 + (e >> 4);
+        rbs[l] = (gk < Kd && gc < Nout) ? W[(size_t)gc * ldw + gk] : 0.f;
+      }
+    } else if constexpr (VEC_W) {
 #pragma unroll
       for (int l = 0; l < BL; ++l) {
         const int e = tid + l * 256;
@@ -286,7 +305,25 @@ __global__ void __launch_bounds__(256, TN == 8 ? 2 : 3)
       As[buf][k4 + 2][rr] = ra[l].z;
       As[buf][k4 + 3][rr] = ra[l].w;
     }
-    if constexpr (VEC_W) {
+    if constexpr (TB && VEC_W) {
+#pragma unroll
+      for (int l = 0; l < BL; ++l) {
+        const int e = tid + l * 256;
+        if (e < 4 * BN) {
+          const int n = e >> 2, k4 = (e & 3) * 4;
+          Bs[buf][k4][n] = rb4[l].x;
+          Bs[buf][k4 + 1][n] = rb4[l].y;
+          Bs[buf][k4 + 2][n] = rb4[l].z;
+          Bs[buf][k4 + 3][n] = rb4[l].w;
+        }
+      }
+    } else if constexpr (TB) {
+#pragma unroll
+      for (int l = 0; l < BS; ++l) {
+        const int e = tid + l * 256;
+        Bs[buf][e & 15][e >> 4] = rbs[l];
+      }
+    } else if constexpr (VEC_W) {
 #pragma unroll
       for (int l = 0; l < BL; ++l) {
         const int e = tid + l * 256;
@@ -845,6 +882,40 @@ using namespace pnk;
 
 static inline unsigned nblk(size_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// Tile shape by output width, then the load/store widths.
+template <bool TB>
+static int linear_v4_launch(const float* xf, int ldx, const float* wf, int ldw, const float* bf, float* yf, int ldy,
+                            int rows, int Kd, int Nout, int T, int acc, bool vw, bool vy, cudaStream_t st) {
+  const char* kname = TB ? "k_linear_bt" : "k_linear";
+#define PN_LIN(BM, BN, TN)                                                                                    \
+  do {                                                                                                        \
+    dim3 grid((rows + BM - 1) / BM, (Nout + BN - 1) / BN);                                                    \
+    if (vw && vy)                                                                                             \
+      PN_LAUNCH(kname, st, (k_linear_v4<BM, BN, TN, true, true, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));   \
+    else if (vy)                                                                                              \
+      PN_LAUNCH(kname, st, (k_linear_v4<BM, BN, TN, false, true, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));  \
+    else                                                                                                      \
+      PN_LAUNCH(kname, st, (k_linear_v4<BM, BN, TN, false, false, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc))); \
+  } while (0)
+  if (Nout <= 32) PN_LIN(256, 32, 4);  // narrow maps
+  else if (Nout <= 64) PN_LIN(128, 64, 4);
+  else PN_LIN(128, 128, 8);
+#undef PN_LIN
+  return PN_OK;
+}
+
+// Float32 Y (=|+=) X W^T with W stored [Nout][Kd] (row stride ldw): the
+// backward's products through transposed weights on the pipelined tiles.
+// PN_ENOTREADY when X is not float4-aligned (the caller's scalar kernel).
+int pn_linear_bt_f32(const float* X, int ldx, const float* W, int ldw, float* Y, int ldy, int rows, int Kd, int Nout,
+                     int acc, cudaStream_t st) {
+  if (ldx % 4 || Kd % 4 || ((uintptr_t)X & 15)) return PN_ENOTREADY;
+  if (rows <= 0) return PN_OK;
+  const bool vw = ldw % 4 == 0 && ((uintptr_t)W & 15) == 0;
+  const bool vy = ldy % 4 == 0 && Nout % 4 == 0 && ((uintptr_t)Y & 15) == 0;
+  return linear_v4_launch<true>(X, ldx, W, ldw, nullptr, Y, ldy, rows, Kd, Nout, 1, acc, vw, vy, st);
+}
+
 template <typename R>
 int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw, const R* b, R* Y, int ldy, int rows,
               int Kd, int Nout, int T, int acc, cudaStream_t st) {
@@ -862,21 +933,7 @@ int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw
       const bool vy = ldy % 4 == 0 && Nout % 4 == 0 && ((uintptr_t)Y & 15) == 0;
       const float *xf = (const float*)X, *wf = (const float*)W, *bf = (const float*)b;
       float* yf = (float*)Y;
-#define PN_LIN(BM, BN, TN)                                                                                    \
-  do {                                                                                                        \
-    dim3 grid((rows + BM - 1) / BM, (Nout + BN - 1) / BN);                                                    \
-    if (vw && vy)                                                                                             \
-      PN_LAUNCH("k_linear", st, (k_linear_v4<BM, BN, TN, true, true><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));   \
-    else if (vy)                                                                                              \
-      PN_LAUNCH("k_linear", st, (k_linear_v4<BM, BN, TN, false, true><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));  \
-    else                                                                                                      \
-      PN_LAUNCH("k_linear", st, (k_linear_v4<BM, BN, TN, false, false><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc))); \
-  } while (0)
-      if (Nout <= 32) PN_LIN(256, 32, 4);        // narrow maps
-      else if (Nout <= 64) PN_LIN(128, 64, 4);
-      else PN_LIN(128, 128, 8);
-#undef PN_LIN
-      return PN_OK;
+      return linear_v4_launch<false>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc, vw, vy, st);
     }
   }
   dim3 grid((rows + 63) / 64, (Nout + 63) / 64);

@@ -11,6 +11,11 @@ template <typename R>
 int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw, const R* b, R* Y, int ldy, int rows,
               int Kd, int Nout, int T, int acc, cudaStream_t st);
 
+// Float32 Y (=|+=) X W^T, W stored [Nout][Kd] with row stride ldw, on the
+// pipelined GEMM tiles; PN_ENOTREADY when X is not float4-aligned.
+int pn_linear_bt_f32(const float* X, int ldx, const float* W, int ldw, float* Y, int ldy, int rows, int Kd, int Nout,
+                     int acc, cudaStream_t st);
+
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of the multiply-xor
 // bijection with the key bumped by the Weyl constants between rounds.
 __device__ inline void pn_philox(unsigned c[4], unsigned k0, unsigned k1) {
