@@ -463,7 +463,7 @@ def main():
     ap.add_argument("--serve-sweep", default="", help="further loads for the mixed server, e.g. 0.5,0.9")
     ap.add_argument("--sampler", type=int, default=None,
                     help="PN_OPT_FUSED_SAMPLER for the timed mixed path (library default if absent)")
-    ap.add_argument("--case", choices=["sampler", "jet_tc", "langevin"], default=None,
+    ap.add_argument("--case", choices=["sampler", "jet_tc", "langevin", "drift_n2"], default=None,
                     help="run one small kernel case (for ncu captures) and exit")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -473,6 +473,20 @@ def main():
     import torch.distributed as dist
     from paper_1909_08423_gb300 import binding, synth
 
+    if args.case == "drift_n2":  # reverse-mode drift of 2048 N2-shaped walkers (inputs larger than L2)
+        torch.cuda.set_device(0)
+        sysd = synth.n2()
+        W = 2048
+        s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=W)
+        r = torch.empty(W, s.N, 3, dtype=torch.float64, device="cuda")
+        s.init_walkers(r, 1)
+        lp = torch.empty(W, dtype=torch.float64, device="cuda")
+        g = torch.empty_like(r)
+        for _ in range(2):
+            s.eval_drift(r, g, lp)
+        s.device_status()
+        print("case ok", flush=True)
+        return
     if args.case:
         torch.cuda.set_device(0)
         sysd = synth.be()

@@ -499,18 +499,21 @@ __global__ void __launch_bounds__(256) k_message(DevSys s, const R* __restrict__
 }
 
 // Same messages, one thread per (walker, row chunk, electron i, column z):
-// chunk c < ceil(N/2) holds the tangent rows of electrons 2c and 2c + 1
-// (t = 1 + 3k + a), the last chunk the value row and the Laplacian row.
+// chunk c < ceil(N/KC) holds the tangent rows of electrons KC c .. KC c +
+// KC - 1 (t = 1 + 3k + a), the last chunk the value row and the Laplacian
+// row.
 // Each partner's filter jet, geometry and value row are read once per
 // chunk, and the product-rule factor d d_ij / d r_{k,a} is resolved per
 // electron k, so a row costs one h load and two multiply-adds per partner.
 // Arithmetic per row is that of k_message.
+constexpr int MSG_KC = 2;  // electrons per tangent-row chunk of k_message_c
 template <typename R>
 __global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict__ Y, const double* __restrict__ geo,
                                                    const R* __restrict__ wj, const R* __restrict__ H, int ldH, int Wn,
                                                    int T, R* __restrict__ Zb, int ldZ) {
+  constexpr int KC = MSG_KC;
   const int Zd = s.Zd, N = s.N, M = s.M;
-  const int nTan = (N + 1) / 2, nC = nTan + 1;
+  const int nTan = (N + KC - 1) / KC, nC = nTan + 1;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)Wn * nC * N * Zd) return;
   const int z = idx % Zd;
@@ -524,10 +527,10 @@ __global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict
   const double* gw = geo + (size_t)w * s.Ppair * 4;
   R* ob = Zb + (size_t)(w * N + i) * T * ldZ + z;
   if (c < nTan) {
-    const int k0 = 2 * c, nk = (k0 + 1 < N) ? 2 : 1;
-    R zs[6], za[6], zq[6];
+    const int k0 = KC * c, nk = min(KC, N - k0);
+    R zs[3 * KC], za[3 * KC], zq[3 * KC];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) zs[q] = za[q] = zq[q] = 0;
+    for (int q = 0; q < 3 * KC; ++q) zs[q] = za[q] = zq[q] = 0;
     for (int j = 0; j < N; ++j) {
       if (j == i) continue;
       const int p = i < j ? pn_pair_index(i, j, N) : pn_pair_index(j, i, N);
@@ -539,7 +542,7 @@ __global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict
       const R h0 = hj[0];
       const bool same = (j < s.n_up) == si;
 #pragma unroll
-      for (int kk = 0; kk < 2; ++kk) {
+      for (int kk = 0; kk < KC; ++kk) {
         if (kk >= nk) break;
         const int k = k0 + kk;
 #pragma unroll
@@ -550,21 +553,23 @@ __global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict
         }
       }
     }
-    for (int I = 0; I < M; ++I) {
-      const int p = s.Pee + i * M + I;
-      const double* g = gw + p * 4;
-      const R y = Y[I * Zd + z];
-      const R w1 = ww[(size_t)p * 3 * Zd + Zd];
+    // nuclei move no electron but i: their terms sit in i's rows only
+    if (i >= k0 && i < k0 + nk)
+      for (int I = 0; I < M; ++I) {
+        const int p = s.Pee + i * M + I;
+        const double* g = gw + p * 4;
+        const R y = Y[I * Zd + z];
+        const R w1 = ww[(size_t)p * 3 * Zd + Zd];
 #pragma unroll
-      for (int kk = 0; kk < 2; ++kk) {
-        if (kk >= nk) break;
-        if (k0 + kk == i)
+        for (int kk = 0; kk < KC; ++kk) {
+          if (kk >= nk) break;
+          if (k0 + kk == i)
 #pragma unroll
-          for (int a = 0; a < 3; ++a) zq[3 * kk + a] += w1 * (R)g[1 + a] * y;
+            for (int a = 0; a < 3; ++a) zq[3 * kk + a] += w1 * (R)g[1 + a] * y;
+        }
       }
-    }
 #pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
+    for (int kk = 0; kk < KC; ++kk) {
       if (kk >= nk) break;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -972,7 +977,7 @@ int pn_network_layers(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn,
     if (fe == PN_ENOTREADY)
       PN_LAUNCH("k_filter", st, k_filter<R><<<nblk((size_t)Wn * s.Ppair, FW), FW * 32, 0, st>>>(s, net, n, w.efeat, Wn, jet, w.wjet));
     if (jet) {
-      const size_t nthr = (size_t)Wn * ((s.N + 1) / 2 + 1) * s.N * s.Zd;
+      const size_t nthr = (size_t)Wn * ((s.N + MSG_KC - 1) / MSG_KC + 1) * s.N * s.Zd;
       PN_LAUNCH("k_message", st,
                 k_message_c<R><<<nblk(nthr, 256), 256, 0, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H, w.ldH, Wn,
                                                                  T, w.Zb, w.ldZ));
