@@ -271,11 +271,11 @@ __global__ void k_slater_gather(DevSys s, const double* __restrict__ phi, const 
   }
 }
 
-// out = d * sigmoid(a)
+// d *= sigmoid(a), in place
 template <typename R>
-__global__ void k_mul_sigmoid(const R* __restrict__ d, const R* __restrict__ a, R* __restrict__ out, size_t n) {
+__global__ void k_mul_sigmoid(R* __restrict__ d, const R* __restrict__ a, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = d[i] * sigm_(a[i]);
+  if (i < n) d[i] *= sigm_(a[i]);
 }
 
 // dJ [Wn] times eta.W3^T -> dS2s [Wn][D]
@@ -1010,15 +1010,15 @@ static int drift_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const 
   if (int e = slater_bwd<R>(s, t, nullptr, Wn, t.gr, t.lse, st)) return e;
   // kappa head
   if (int e = linear_bt<R>(t.dF, no, net.p + o.kW[2], no, t.dA, D, rows, no, D, 0, st)) return e;
-  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dA, t.kA2, t.dA, WND));
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dA, t.kA2, WND));
   if (int e = linear_bt<R>(t.dA, D, net.p + o.kW[1], D, t.dB, D, rows, D, D, 0, st)) return e;
-  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dB, t.kA1, t.dB, WND));
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dB, t.kA1, WND));
   if (int e = linear_bt<R>(t.dB, D, net.p + o.kW[0], D, t.dX, D, rows, D, D, 0, st)) return e;
   // eta head
   PN_LAUNCH("k_outer_row", st, k_outer_row<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dJ, net.p + o.eW[2], t.dAs, Wn, D));
-  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dAs, t.eA2, t.dAs, (size_t)Wn * D));
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dAs, t.eA2, (size_t)Wn * D));
   if (int e = linear_bt<R>(t.dAs, D, net.p + o.eW[1], D, t.dBs, D, Wn, D, D, 0, st)) return e;
-  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dBs, t.eA1, t.dBs, (size_t)Wn * D));
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dBs, t.eA1, (size_t)Wn * D));
   if (int e = linear_bt<R>(t.dBs, D, net.p + o.eW[0], D, t.dXs, D, Wn, D, D, 0, st)) return e;
   PN_LAUNCH("k_bcast_add", st, k_bcast_add<R><<<nblk(WND, 256), 256, 0, st>>>(t.dX, t.dXs, Wn, N, D));
   // interaction layers, last to first; t.dX holds d/dX^(n+1)
@@ -1061,11 +1061,11 @@ static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const d
   if (int e = wg.add(t.kS2, D, t.dF, no, rows, D, no, -1, o.kW[2], 0, 0)) return e;
   if (int e = wg.add(nullptr, 0, t.dF, no, rows, 1, no, -1, o.kb[2], 0, 0)) return e;
   if (int e = linear_bt<R>(t.dF, no, net.p + o.kW[2], no, t.dA, D, rows, no, D, 0, st)) return e;
-  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dA, t.kA2, t.dA, WND));
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dA, t.kA2, WND));
   if (int e = wg.add(t.kS1, D, t.dA, D, rows, D, D, -1, o.kW[1], 0, 0)) return e;
   if (int e = wg.add(nullptr, 0, t.dA, D, rows, 1, D, -1, o.kb[1], 0, 0)) return e;
   if (int e = linear_bt<R>(t.dA, D, net.p + o.kW[1], D, t.dB, D, rows, D, D, 0, st)) return e;
-  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dB, t.kA1, t.dB, WND));
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk(WND, 256), 256, 0, st>>>(t.dB, t.kA1, WND));
   if (int e = wg.add(XL, D, t.dB, D, rows, D, D, -1, o.kW[0], 0, 0)) return e;
   if (int e = wg.add(nullptr, 0, t.dB, D, rows, 1, D, -1, o.kb[0], 0, 0)) return e;
   if (int e = linear_bt<R>(t.dB, D, net.p + o.kW[0], D, t.dX, D, rows, D, D, 0, st)) return e;
@@ -1073,11 +1073,11 @@ static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const d
   if (int e = wg.add(t.eS2, D, t.dJ, 1, Wn, D, 1, -1, o.eW[2], 0, 0)) return e;
   if (int e = wg.add(nullptr, 0, t.dJ, 1, Wn, 1, 1, -1, o.eb[2], 0, 0)) return e;
   PN_LAUNCH("k_outer_row", st, k_outer_row<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dJ, net.p + o.eW[2], t.dAs, Wn, D));
-  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dAs, t.eA2, t.dAs, (size_t)Wn * D));
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dAs, t.eA2, (size_t)Wn * D));
   if (int e = wg.add(t.eS1, D, t.dAs, D, Wn, D, D, -1, o.eW[1], 0, 0)) return e;
   if (int e = wg.add(nullptr, 0, t.dAs, D, Wn, 1, D, -1, o.eb[1], 0, 0)) return e;
   if (int e = linear_bt<R>(t.dAs, D, net.p + o.eW[1], D, t.dBs, D, Wn, D, D, 0, st)) return e;
-  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dBs, t.eA1, t.dBs, (size_t)Wn * D));
+  PN_LAUNCH("k_mul_sigmoid", st, k_mul_sigmoid<R><<<nblk((size_t)Wn * D, 256), 256, 0, st>>>(t.dBs, t.eA1, (size_t)Wn * D));
   if (int e = wg.add(t.Xs, D, t.dBs, D, Wn, D, D, -1, o.eW[0], 0, 0)) return e;
   if (int e = wg.add(nullptr, 0, t.dBs, D, Wn, 1, D, -1, o.eb[0], 0, 0)) return e;
   if (int e = linear_bt<R>(t.dBs, D, net.p + o.eW[0], D, t.dXs, D, Wn, D, D, 0, st)) return e;

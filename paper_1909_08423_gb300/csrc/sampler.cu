@@ -126,7 +126,6 @@ __global__ void __launch_bounds__(256) k_metropolis_fused(DevSys s, DevNet<R> ne
   double* sgeo = (double*)(smem + L.geo);
   double* sphi = (double*)(smem + L.phi);
   double* slp = (double*)(smem + L.lp);
-  double* slpp = (double*)(smem + L.lpp);
   double* sdet = (double*)(smem + L.det);
   R* sx = (R*)(smem + L.x);
   R* sh = (R*)(smem + L.h);

@@ -141,17 +141,6 @@ __device__ inline void tmem_ld8x3(uint32_t taddr, uint32_t np, float v[8]) {
     v[j] = (__uint_as_float(u2[j]) + __uint_as_float(u1[j])) + __uint_as_float(u0[j]);
 }
 
-// Eight consecutive fp32 columns of this thread's TMEM lane.
-__device__ inline void tmem_ld8(uint32_t taddr, float v[8]) {
-  uint32_t u[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(u[j]);
-}
-
 // LU with partial pivoting in float64 of an ns x ns matrix (row-major,
 // overwritten); det(A) = mant * 2^ex with the sign in mant, rescaled after
 // every pivot so that products of small orbital values do not underflow.

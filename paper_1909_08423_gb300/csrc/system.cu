@@ -142,7 +142,6 @@ void host_s_part(const HostSys& h, int I, int mu, double r, double* f, double* f
 
 bool solve3(double A[3][3], double b[3], double x[3]) {
   // Gaussian elimination with partial pivoting on a 3x3 system.
-  int piv[3] = {0, 1, 2};
   double M[3][4];
   for (int i = 0; i < 3; ++i) {
     for (int j = 0; j < 3; ++j) M[i][j] = A[i][j];
@@ -160,7 +159,6 @@ bool solve3(double A[3][3], double b[3], double x[3]) {
       for (int j = c; j < 4; ++j) M[r][j] -= f * M[c][j];
     }
   }
-  (void)piv;
   for (int i = 2; i >= 0; --i) {
     double acc = M[i][3];
     for (int j = i + 1; j < 3; ++j) acc -= M[i][j] * x[j];
