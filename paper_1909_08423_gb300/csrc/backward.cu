@@ -10,6 +10,12 @@
 // Weight gradients are sums over rows (walkers x electrons or pairs): each
 // is formed as per-block partial tiles in float64 and reduced in a fixed
 // order, so the result is deterministic.
+//
+// The same tape and chain with weight 1 per walker and no weight gradients
+// give grad_r ln|psi|, the drift of the Langevin proposal (Methods, ansatz
+// optimisation, sampling): the chain then ends at the pair distances
+// (through each layer's filter features and the cusp factor gamma) and at
+// the orbitals (through the backflowed determinant entries).
 #include <math.h>
 
 #include <algorithm>
@@ -886,7 +892,8 @@ struct WgBatch {
   }
 };
 
-// The three determinant passes; gr and lse may be null.
+// The three determinant passes (one profiling class, "k_slater_bwd"); gr
+// and lse may be null.
 template <typename R>
 int slater_bwd(const DevSys& s, Tape<R>& t, const double* u, int Wn, double* gr, double* lse, cudaStream_t st) {
   const size_t nb = (size_t)Wn * s.n_det * 2;
