@@ -284,6 +284,56 @@ def run_langevin(sysd, W, target=0.57, steps=10):
     return out
 
 
+def run_configs():
+    """The H10 chain (8192 walkers: E_loc + clipping + grad ln|psi|) and the
+    N2-shaped diatomic (16384 walkers in chunks of 4096: one Metropolis step
+    + E_loc + clipping + grad ln|psi|) at full size, mixed path, CUDA events
+    over two repetitions after one warm-up."""
+    import torch
+    from paper_1909_08423_gb300 import binding, synth
+
+    def timed(fn, n=2):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    out = {}
+    for name, make, W, chunk, sweep in (("h10", synth.h10, 8192, 8192, 0), ("n2", synth.n2, 16384, 4096, 1)):
+        sysd = make()
+        s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=chunk)
+        r = torch.empty(W, s.N, 3, dtype=torch.float64, device="cuda")
+        s.init_walkers(r, 3)
+        lp = torch.empty(W, dtype=torch.float64, device="cuda")
+        sg = torch.empty_like(lp)
+        s.eval_logpsi(r, lp, sg)
+        s.metropolis_step(r, lp, 20, SIGMA, 3, 0)
+        E, Ec, cot = torch.empty_like(lp), torch.empty_like(lp), torch.empty_like(lp)
+        g = torch.empty(s.n_params, dtype=torch.float64, device="cuda")
+        k = [100]
+
+        def step():
+            if sweep:
+                s.metropolis_step(r, lp, 1, SIGMA, 3, k[0])
+                k[0] += 1
+            s.eval_local_energy(r, E)
+            binding.clip_local_energy(E, Ec, cot)
+            s.grad_logpsi(r, cot, g)
+
+        ms_step = timed(step)
+        out[name] = {"walkers": W, "chunk": chunk, "ms_step": ms_step, "walker_eloc_per_s": W / (ms_step / 1e3),
+                     "ms_eloc": timed(lambda: s.eval_local_energy(r, E)),
+                     "ms_grad": timed(lambda: s.grad_logpsi(r, cot, g)),
+                     "ms_metropolis_step": timed(lambda: s.metropolis_step(r, lp, 1, SIGMA, 5, 10 ** 6)) if sweep else None}
+        s.close()
+    return out
+
+
 def run_line_scan(npts=4096):
     """E_loc along the LiH line scan through both nuclei and both fixed
     electrons (mixed path), timed with CUDA events."""
@@ -463,7 +513,7 @@ def main():
     ap.add_argument("--serve-sweep", default="", help="further loads for the mixed server, e.g. 0.5,0.9")
     ap.add_argument("--sampler", type=int, default=None,
                     help="PN_OPT_FUSED_SAMPLER for the timed mixed path (library default if absent)")
-    ap.add_argument("--case", choices=["sampler", "jet_tc", "langevin", "drift_n2"], default=None,
+    ap.add_argument("--case", choices=["sampler", "jet_tc", "langevin", "drift_n2", "configs"], default=None,
                     help="run one small kernel case (for ncu captures) and exit")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -473,6 +523,10 @@ def main():
     import torch.distributed as dist
     from paper_1909_08423_gb300 import binding, synth
 
+    if args.case == "configs":  # the H10 and N2-shaped configurations at full size
+        torch.cuda.set_device(0)
+        print(json.dumps(run_configs()), flush=True)
+        return
     if args.case == "drift_n2":  # reverse-mode drift of 2048 N2-shaped walkers (inputs larger than L2)
         torch.cuda.set_device(0)
         sysd = synth.n2()
