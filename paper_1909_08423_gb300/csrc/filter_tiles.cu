@@ -95,6 +95,18 @@ __device__ inline void tile_mm(const float* At, const float* Bs, int ldb, int Kc
   }
 }
 
+// acc[i][j] = bias[tx + 16 j] (zero past n): products start from the bias,
+// as the per-row kernels' sums do, so both give the same float32 rounding.
+template <int NJ>
+__device__ inline void bias_acc(float acc[4][NJ], const float* __restrict__ bias, int n, int tx) {
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const float b = tx + 16 * j < n ? bias[tx + 16 * j] : 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i][j] = b;
+  }
+}
+
 template <int NJ>
 __device__ inline void zero_acc(float acc[4][NJ]) {
 #pragma unroll
@@ -123,35 +135,31 @@ __global__ void __launch_bounds__(256) k_filter_tile_value(DevSys s, DevNet<floa
   __syncthreads();
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   float acc[4][NJ];
-  zero_acc<NJ>(acc);
+  bias_acc<NJ>(acc, net.p + net.off.b1[n][c], Hw, tx);
   tile_mm<NJ>(At, W1s, LW, K, ty, tx, acc);
-  const float* b1 = net.p + net.off.b1[n][c];
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     const int h = tx + 16 * j;
     if (h >= Hw) continue;
-    const float bb = b1[h];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int row = ty * 4 + i, g = sgr[row];
-      const float a = acc[i][j] + bb;
+      const float a = acc[i][j];
       if (g >= 0) Ah[(size_t)g * Hw + h] = a;
       Ht[h * LA + row] = sspf_(a);
     }
   }
   __syncthreads();
-  zero_acc<NJ>(acc);
+  bias_acc<NJ>(acc, net.p + net.off.b2[n][c], Zd, tx);
   tile_mm<NJ>(Ht, W2s, LW, Hw, ty, tx, acc);
-  const float* b2 = net.p + net.off.b2[n][c];
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     const int z = tx + 16 * j;
     if (z >= Zd) continue;
-    const float bb = b2[z];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int g = sgr[ty * 4 + i];
-      if (g >= 0) wv[(size_t)g * Zd + z] = acc[i][j] + bb;
+      if (g >= 0) wv[(size_t)g * Zd + z] = acc[i][j];
     }
   }
 }
@@ -178,16 +186,14 @@ __global__ void __launch_bounds__(256) k_filter_tile_jet(DevSys s, DevNet<float>
   float sg[4][NJ];
   {
     float acc[4][NJ];
-    zero_acc<NJ>(acc);
+    bias_acc<NJ>(acc, net.p + net.off.b1[n][c], Hw, tx);
     tile_mm<NJ>(At, W1s, LW, K, ty, tx, acc);
-    const float* b1 = net.p + net.off.b1[n][c];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
       const int h = tx + 16 * j;
-      const float bb = h < Hw ? b1[h] : 0.f;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const float a = acc[i][j] + bb;
+        const float a = acc[i][j];
         sg[i][j] = sigmf_(a);
         if (h < Hw) Ht[h * LA + ty * 4 + i] = sspf_(a);
       }
@@ -212,20 +218,21 @@ __global__ void __launch_bounds__(256) k_filter_tile_jet(DevSys s, DevNet<float>
     }
   }
   __syncthreads();
-  const float* b2 = net.p + net.off.b2[n][c];
   for (int d = 0; d < 3; ++d) {
     float acc[4][NJ];
-    zero_acc<NJ>(acc);
+    if (d == 0)
+      bias_acc<NJ>(acc, net.p + net.off.b2[n][c], Zd, tx);
+    else
+      zero_acc<NJ>(acc);
     tile_mm<NJ>(Ht + d * LW * LA, W2s, LW, Hw, ty, tx, acc);
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
       const int z = tx + 16 * j;
       if (z >= Zd) continue;
-      const float bb = d == 0 ? b2[z] : 0.f;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int g = sgr[ty * 4 + i];
-        if (g >= 0) wj[(size_t)g * 3 * Zd + d * Zd + z] = acc[i][j] + bb;
+        if (g >= 0) wj[(size_t)g * 3 * Zd + d * Zd + z] = acc[i][j];
       }
     }
   }
