@@ -49,3 +49,26 @@ def test_binding_loads_library_and_resolves_symbols(libpath):
     from paper_1909_08423_gb300 import synth
     s = synth.n2()
     assert lib.pn_num_params_for(128, 64, 32, 4, 2, 11) == synth.n_params(s)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback: without the compiled library the binding raises."""
+    import sys
+    code = ("from paper_1909_08423_gb300 import binding\n"
+            f"binding.load({str(tmp_path / 'libpaulinet.so')!r})\n")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert out.returncode != 0
+    assert "not built" in out.stderr
+
+
+def test_product_package_never_imports_the_oracle():
+    """The oracle is test infrastructure: no module of the package imports it."""
+    pkg = os.path.join(ROOT, "paper_1909_08423_gb300")
+    offenders = []
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith(".py"):
+                src = open(os.path.join(dirpath, f)).read()
+                if re.search(r"^\s*(from|import)\s+oracle\b", src, flags=re.M):
+                    offenders.append(f)
+    assert not offenders, offenders
