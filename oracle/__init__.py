@@ -20,7 +20,11 @@ Modules
   clip        smooth logarithmic clipping of local energies (Methods,
               "Ansatz optimization").
 
-Parity status of each function is listed in its docstring; the network's
-interior (filters, messages, heads) is pinned only through invariants,
-cusplessness and finite differences ("parity unpinned" beyond those).
+Parity status of each function is listed in its docstring.  The network's
+message passing and heads are also pinned by a special case: with constant
+filters every message is a partner count times a spin-class row, which fixes
+the channel assignment, the partner sums, the layer recursion and both heads.
+The distance dependence of the filter networks is pinned only through
+invariants, cusplessness and finite differences ("parity unpinned" beyond
+those).
 """

@@ -542,3 +542,50 @@ def test_parameter_gradient_matches_finite_differences(make):
             vals.append((Oracle(S2).eval_logpsi(r)[0] * cot).sum())
         fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(fd - g[k]) < 1e-6 * max(1.0, abs(g[k])), (k, fd, g[k])
+
+
+def test_network_with_constant_filters_reduces_to_partner_counts():
+    """With every filter's last map zeroed (W2 = 0, b2 = c) each filter is a
+    constant, so electron i's messages are counts of its partners times a
+    row shared by a spin class: x takes one row for up and one for down
+    electrons, J is one number for every configuration and f one row per
+    spin.  This pins the channel assignment (same spin, opposite spin,
+    nuclei), the exclusion of i from its own sums and the layer recursion
+    of the interaction layers (Methods, PauliNet extension of SchNet)."""
+    sysd = synth.make_system([3.0, 2.0], [[0, 0, 0], [0, 0, 1.5]], lambda z: {0: 2, 1: 1}, n_det=2, D=8, K=4,
+                             L=2, seed=11, Zd=4)
+    rng = np.random.default_rng(12)
+    P = {k: np.array(v, dtype=np.float64) for k, v in sysd["params"].items()}
+    for n in range(sysd["L"]):
+        for c in ("same", "anti", "nuc"):
+            P[f"w{n}.{c}.W2"] = np.zeros_like(P[f"w{n}.{c}.W2"])
+            P[f"w{n}.{c}.b2"] = rng.normal(0.0, 0.5, size=P[f"w{n}.{c}.b2"].shape)
+    sysd = dict(sysd)
+    sysd["params"] = P
+    comp = Oracle(sysd).components(synth.random_walkers(sysd, 12, 3))
+
+    def ssp(x):
+        return np.logaddexp(x, 0.0) - np.log(2.0)
+
+    def mlp(x, name):
+        for k in (1, 2, 3):
+            x = x @ P[f"{name}.W{k}"] + P[f"{name}.b{k}"]
+            if k < 3:
+                x = ssp(x)
+        return x
+
+    nu, nd = sysd["n_up"], sysd["n_dn"]
+    xu = xd = P["x0"]
+    for n in range(sysd["L"]):
+        hu, hd = xu @ P[f"h{n}.W"] + P[f"h{n}.b"], xd @ P[f"h{n}.W"] + P[f"h{n}.b"]
+        cs, ca, cn = (P[f"w{n}.{c}.b2"] for c in ("same", "anti", "nuc"))
+        g = lambda c, z: z @ P[f"g{n}.{c}.W"] + P[f"g{n}.{c}.b"]
+        zn = g("nuc", cn * P["Y"].sum(0))
+        xu, xd = (xu + g("same", cs * (nu - 1) * hu) + g("anti", ca * nd * hd) + zn,
+                  xd + g("same", cs * (nd - 1) * hd) + g("anti", ca * nu * hu) + zn)
+    J = mlp(nu * xu + nd * xd, "eta")[0]
+    fu, fd = 1.0 + mlp(xu, "kappa"), 1.0 + mlp(xd, "kappa")
+    np.testing.assert_allclose(comp["J"], J, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(comp["f"][:, :nu], np.broadcast_to(fu, comp["f"][:, :nu].shape), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(comp["f"][:, nu:], np.broadcast_to(fd, comp["f"][:, nu:].shape), rtol=1e-12, atol=1e-12)
+    assert abs(fu - fd).max() > 1e-6  # the spin classes differ far beyond the tolerance: a swapped channel shows
