@@ -350,6 +350,15 @@ def hydrogen_like_sto(Z=1.0, zeta=1.0):
                     [[0]], np.zeros((1, 0)), [1.0])
 
 
+def sto_beside_bare_nuclei(ZA=1.0, zeta=1.0, bare=((2.0, (0.0, 0.0, 1.7)),)):
+    """One electron in exp(-zeta r_A) on a nucleus A of charge ZA at the
+    origin, next to further nuclei (charge, position) that carry no basis
+    function; the network weights are zero."""
+    Z = [ZA] + [b[0] for b in bare]
+    R = [[0.0, 0.0, 0.0]] + [list(b[1]) for b in bare]
+    return _special(Z, R, [(0, -1, [zeta], [1.0])], 1, 0, np.ones((1, 1)), [[0]], np.zeros((1, 0)), [1.0])
+
+
 def single_gto(Z=1.0, alpha=0.7):
     """One electron in a single s Gaussian exp(-alpha r^2)."""
     return _special([Z], [[0, 0, 0]], [(0, 0, [alpha], [1.0])], 1, 0, np.ones((1, 1)),

@@ -161,6 +161,10 @@ def test_precision_calibration_picks_a_safe_mask(lib):
     assert table[0][0] <= 1e-4
 
 
+_BARE = ((2.0, (0.0, 0.0, 1.7)), (3.0, (1.1, -0.4, -1.2)))
+_VNN_BARE = (2.0 / 1.7 + 3.0 / np.linalg.norm([1.1, -0.4, -1.2])
+             + 6.0 / np.linalg.norm(np.array([1.1, -0.4, -1.2]) - np.array([0.0, 0.0, 1.7])))
+
 CLOSED = [
     ("H atom", lambda: synth.hydrogen_like_sto(1.0, 1.0), lambda r: -0.5 + 0 * r[:, 0, 0]),
     ("STO Z=3 zeta=2.2", lambda: synth.hydrogen_like_sto(3.0, 2.2),
@@ -170,6 +174,11 @@ CLOSED = [
     ("He product", lambda: synth.helium_like_product(2.0, 1.6875),
      lambda r: -1.6875 ** 2 + (1.6875 - 2) * (1 / np.linalg.norm(r[:, 0], axis=-1) + 1 / np.linalg.norm(r[:, 1], axis=-1))
      + 1 / np.linalg.norm(r[:, 0] - r[:, 1], axis=-1)),
+    # one electron on nucleus A beside two bare nuclei: every nucleus pair's
+    # repulsion enters V (Methods, the Hamiltonian)
+    ("STO + bare nuclei", lambda: synth.sto_beside_bare_nuclei(1.0, 1.3, _BARE),
+     lambda r: -1.3 ** 2 / 2 + 0.3 / np.linalg.norm(r[:, 0], axis=-1)
+     - sum(Z / np.linalg.norm(r[:, 0] - np.array(R), axis=-1) for Z, R in _BARE) + _VNN_BARE),
 ]
 
 

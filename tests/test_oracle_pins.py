@@ -65,6 +65,26 @@ def test_helium_like_product_closed_form():
     assert np.max(np.abs(E - (-zeta ** 2 + (zeta - Z) * (1 / r1 + 1 / r2) + 1 / r12))) < 1e-11
 
 
+@pytest.mark.parametrize("zeta", [1.0, 1.3])
+def test_nucleus_nucleus_repulsion_closed_form(zeta):
+    """exp(-zeta r_A) on nucleus A (Z_A = 1) beside bare nuclei B, C (no
+    basis functions): the kinetic part is that of the hydrogen-like atom and
+    V adds every electron-nucleus attraction and every nucleus pair's
+    repulsion (the Hamiltonian of the variational principle, Methods):
+    E_loc = -zeta^2/2 + (zeta - 1)/r_A - Z_B/r_B - Z_C/r_C
+            + Z_A Z_B/R_AB + Z_A Z_C/R_AC + Z_B Z_C/R_BC.
+    A dropped, doubled or once-counted nucleus pair fails it."""
+    bare = ((2.0, (0.0, 0.0, 1.7)), (3.0, (1.1, -0.4, -1.2)))
+    o = Oracle(synth.sto_beside_bare_nuclei(1.0, zeta, bare))
+    r = _pts(64, 1, seed=9)
+    E, _, _ = o.local_energy(r)
+    RA, (ZB, RB), (ZC, RC) = np.zeros(3), (bare[0][0], np.array(bare[0][1])), (bare[1][0], np.array(bare[1][1]))
+    dist = lambda a, b: np.linalg.norm(a - b, axis=-1)
+    exact = (-zeta ** 2 / 2 + (zeta - 1.0) / dist(r[:, 0], RA) - ZB / dist(r[:, 0], RB) - ZC / dist(r[:, 0], RC)
+             + ZB / dist(RA, RB) + ZC / dist(RA, RC) + ZB * ZC / dist(RB, RC))
+    assert np.max(np.abs(E - exact)) < 1e-11
+
+
 # ------------------------------------------------------------- determinants
 
 def _leibniz(A):
@@ -316,6 +336,61 @@ def test_cusp_splice_is_smooth_at_rc(make):
 
 
 # ----------------------------------------------------------------- sampling
+
+# Known-answer vectors of Philox4x32-10 published with the generator
+# (Salmon, Moraes, Dror & Shaw, SC'11; the Random123 distribution's test
+# vectors): counter (c0..c3), key (k0, k1) -> output words.
+PHILOX_KAT = [
+    ((0x00000000, 0x00000000, 0x00000000, 0x00000000), (0x00000000, 0x00000000),
+     (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+    ((0xffffffff, 0xffffffff, 0xffffffff, 0xffffffff), (0xffffffff, 0xffffffff),
+     (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+    ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+     (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1)),
+]
+
+
+@pytest.mark.parametrize("ctr,key,expect", PHILOX_KAT)
+def test_philox_known_answer_vectors(ctr, key, expect):
+    """A wrong round constant, Weyl increment, round count or word order
+    changes every output word."""
+    out = philox.philox4x32(*[np.array([c], dtype=np.uint64) for c in ctr], key[0], key[1])
+    assert tuple(int(w[0]) for w in out) == expect
+
+
+def _golden_features():
+    from fractions import Fraction
+    import os
+    rows = []
+    path = os.path.join(os.path.dirname(__file__), "golden", "features_k4_rc10.txt")
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        d, k, mu, sig, x, val = line.split()
+        rows.append((Fraction(d), int(k), Fraction(mu), Fraction(sig), Fraction(x), float(val)))
+    return rows
+
+
+def test_features_match_hand_worked_table():
+    """e_k(d) for K = 4, r_c = 10 against the table worked by hand from the
+    paper's e_k, mu_k and sigma_k (tests/golden/features_k4_rc10.txt).  The
+    table's own arithmetic is checked in exact fractions first; then the
+    oracle must reproduce every entry.  A wrong 1/7, a q_k instead of q_k^2,
+    a missing d^2 envelope or an endpoint-inclusive q grid fails it."""
+    from fractions import Fraction
+    rows = _golden_features()
+    assert len(rows) == 12
+    for d, k, mu, sig, x, val in rows:
+        q = Fraction(k, 5)
+        assert mu == 10 * q * q and sig == (1 + 10 * q) / 7
+        assert x == -d - (d - mu) ** 2 / sig ** 2
+        assert abs(float(d * d) * math.exp(float(x)) / val - 1) < 1e-15
+    sysd = {"K": 4, "r_c": 10.0}
+    ds = sorted({r[0] for r in rows})
+    e = features(sysd, torch.tensor([float(d) for d in ds], dtype=DT)).numpy()
+    for d, k, _, _, _, val in rows:
+        assert abs(e[ds.index(d), k - 1] / val - 1) < 1e-13, (d, k)
+
 
 def test_philox_normals_are_standard_and_reproducible():
     a = philox.normals(7, np.arange(20000), 3, 12)
