@@ -1,12 +1,17 @@
 """Benchmark: walker local energies per second on one GB300 (per rank).
 
-One step = one pass of the whole hot path over the Be-atom workload (seeded
-synthetic Be: Z=4, 2 up 2 down electrons, 4 determinants, 4s2p basis, D=64,
-L=3, K=32; 4096 walkers): 100 Metropolis steps (Gaussian proposal sigma =
-0.2 bohr), local energies of all walkers (forward Laplacian jet), clipping,
-and the hand-written backward of ln|psi| for the VMC loss gradient.
+One step = one pass of the whole hot path over the N2-shaped diatomic
+(seeded synthetic: two Z=7 nuclei 2.068 bohr apart, 7 up 7 down electrons,
+32 determinants, 4s4p2d Cartesian Gaussians per atom, D=128, Zd=64, K=32,
+L=4; 16384 walkers in workspace chunks of 4096): one Metropolis step of all
+walkers (Gaussian all-electron proposal, sigma = 0.2 bohr), local energies
+of all walkers (forward Laplacian jet, with the mixed path's local-energy
+guard), clipping, and the hand-written backward of ln|psi| for the VMC
+loss gradient (value pass recomputed per memory-budgeted chunk).
 value = walkers x ranks / step time.  The headline runs the mixed path; the
-same step is also timed on the plain FP64 path.
+same step is also timed on the plain FP64 path, and the Be-atom step (4096
+walkers, 100 Metropolis steps + E_loc + clip + grad) and the H10 chain
+(8192 walkers, E_loc + clip + grad) are reported beside it.
 
 --impl reference times the CPU oracle (the plain FP64 definition) on the
 host cores on a bounded sample of the same workload.
@@ -15,6 +20,7 @@ host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -27,12 +33,31 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "be"
-W_PER_RANK = 4096
-N_METROPOLIS = 100
+WORKLOAD = "n2"
+W_PER_RANK = 16384
+CHUNK = 4096
+N_METROPOLIS = 1
 SIGMA = 0.2
 METRIC = "walker local energies/s"
 UNIT = "walkers/s"
+WORKLOAD_DESC = ("N2-shaped diatomic (two Z=7 at 2.068 bohr, 14 e, 32 dets, 4s4p2d/atom, D=128 Zd=64 K=32 L=4), "
+                 "{W} walkers/GPU in chunks of {C}; step = 1 Metropolis step (sigma 0.2) + E_loc + clip + grad ln|psi|")
+
+# Kernel classes of the step and the unit that bounds each: "fp32" CUDA-core
+# float32 FMA, "fp64" float64 FMA, "tensor" tcgen05 (bf16 pieces), "hbm"
+# (the work the library reports for it is bytes).
+KERNEL_UNIT = {
+    "k_linear": "fp32", "k_linear_bt": "fp32", "k_filter": "fp32", "k_filter_tile": "fp32",
+    "k_metropolis_warp": "fp32", "k_metropolis_fused": "fp32", "k_metropolis_tc": "tensor",
+    "k_linear_tc": "tensor", "k_slater": "fp64", "k_message": "hbm",
+}
+KERNEL_CLASSES = ["k_linear", "k_linear_bt", "k_linear_tc", "k_filter", "k_message", "k_slater", "k_orbitals",
+                  "k_combine", "k_features", "k_ssp_jet", "k_sum_electrons", "k_init_x", "k_geometry", "k_wgrad",
+                  "k_slater_bwd", "k_filter_bwd", "k_filter_bwd_dist", "k_filter_tape", "k_msg_bwd_w",
+                  "k_msg_bwd_h", "k_mul_sigmoid", "k_ssp_copy", "k_outer_row", "k_bcast_add", "k_message_value",
+                  "k_metropolis_warp", "k_metropolis_fused", "k_metropolis_tc", "k_propose", "k_accept", "k_clip",
+                  "k_guard_flag", "k_guard_gather", "k_guard_scatter", "k_filter_tile_jet", "k_filter_tile_value",
+                  "k_filter_tile_bwd", "k_filter_tile_dist"]
 
 
 def _peaks():
@@ -44,65 +69,234 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# Algorithmic floating-point work per launch class (multiply-add = 2), per
-# walker, for the value pass (T = 1) and the jet pass (T = 3N + 2).
-def tc_sampler_executed_flops(sysd, W, n_sms=152):
-    """bf16 tensor-core FLOPs the tcgen05 sampler executes per Metropolis step
-    over all CTAs: every stage is a 128-row tile with six piece products per
-    float32 product (K x Np per product, Np padded to 16), the first layer's h
-    excluded; CTAs hold WT walkers as the launcher sizes them."""
-    N = sysd["n_up"] + sysd["n_dn"]
-    M = len(sysd["Z"])
-    D, Zd, K, L = sysd["D"], sysd["Zd"], sysd["K"], sysd["L"]
-    Hw = max(K, Zd)
-    no = sysd["mo_coeffs"].shape[1]
-    pad = lambda x: (x + 15) // 16 * 16
-    nup, ndn = sysd["n_up"], sysd["n_dn"]
-    cnts = [nup * (nup - 1) // 2 + ndn * (ndn - 1) // 2, nup * ndn, N * M]
-    live = sum(1 for c in cnts if c > 0)
-    stages = [(D, Zd)] * (L - 1) + [(K, Hw), (Hw, Zd), (Zd, D)] * (L * live)
-    stages += [(D, D), (D, D), (D, pad(no)), (D, D), (D, D), (D, 16)]
-    macs_tile = sum(6 * k * n * 128 for k, n in stages)
-    WT = min(128 // N, 128 // max(cnts), -(-W // n_sms))
-    ctas = -(-W // WT)
-    return 2 * macs_tile * ctas
+def _sha16(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def algorithmic_flops(sysd, kernel, mode):
-    N = sysd["n_up"] + sysd["n_dn"]
-    M = len(sysd["Z"])
-    D, Zd, K, L = sysd["D"], sysd["Zd"], sysd["K"], sysd["L"]
-    Hw = max(K, Zd)
-    no = sysd["mo_coeffs"].shape[1]
-    nd = len(sysd["ci"])
-    P = N * (N - 1) // 2 + N * M
-    T = 1 if mode == "value" else 3 * N + 2
-    jc = 1 if mode == "value" else 3
-    if kernel == "k_filter":
-        return L * P * jc * 2 * (K * Hw + Hw * Zd)
-    if kernel == "k_linear":
-        per_layer = N * T * 2 * (D * Zd + 3 * Zd * D)
-        heads = N * T * 2 * (D * D * 2 + D * no) + T * 2 * (2 * D * D + D)
-        return L * per_layer + heads
-    if kernel == "k_message":
-        # value: 2 per partner; derivative rows 4; Laplacian row ~ 20
-        per_row = 2 if T == 1 else (2 + 4 * (T - 2) + 20) / T
-        return L * N * T * Zd * (N - 1 + M) * per_row
-    if kernel in ("k_metropolis_warp", "k_metropolis_fused", "k_metropolis_tc"):
-        # one value pass of the network per walker-step (float32 work):
-        # filters, h and receiving maps, messages, both heads
-        return sum(algorithmic_flops(sysd, k, "value") for k in ("k_filter", "k_linear", "k_message"))
-    if kernel == "k_slater":
-        nsig = [sysd["n_up"], sysd["n_dn"]]
-        f = 0
-        for ns in nsig:
-            if ns == 0:
-                continue
-            f += 2 / 3 * ns ** 3 * 2
-            if T > 1:
-                f += 2 * ns ** 3 + 2 * ns ** 2 + 3 * N * (2 * ns ** 3 + 2 * ns ** 2 + 2 * ns ** 2)
-        return nd * f
-    return None
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def _traffic_per_work(kernel):
+    """DRAM bytes per unit of algorithmic work of a kernel class, from the
+    committed ncu capture summarised in profiles/traffic.json -- or None with
+    the reason, also when the kernel's source file changed since the capture
+    (its sha256 is recorded with the figures)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None, "no committed ncu capture"
+    rec = d.get(kernel)
+    if not rec:
+        return None, f"no committed ncu capture of {kernel}"
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src) or _sha16(src) != rec["source_sha16"]:
+        return None, f"{rec['source']} changed since the capture"
+    return rec["dram_bytes_per_work"], rec["note"]
+
+
+def _roofline(kernel, count, ms, work, peaks, peak_src, fp32, fp64):
+    """Roofline record of one kernel class: achieved = algorithmic work of its
+    launches / their summed CUDA-event time, against the peak of the unit
+    that bounds it."""
+    unit = KERNEL_UNIT.get(kernel)
+    rec = {"kernel": kernel, "launches": count, "kernel_ms": ms, "work": work}
+    if not unit or work <= 0 or ms <= 0:
+        rec.update(bound=None, achieved=None, peak=None, frac=None, unit=None,
+                   note="the library reports no algorithmic work for this class")
+        return rec
+    sec = ms / 1e3
+    if unit == "hbm":
+        ach, peak, u = work / sec / 1e9, peaks["hbm_gbs"], "GB/s"
+        rec.update(bound="hbm", peak_source=f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})")
+    elif unit == "tensor":
+        ach, peak, u = work / sec / 1e12, peaks["bf16_tflops"], "TFLOP/s"
+        rec.update(bound="tensor", peak_source=f"bf16_tflops (burst) of MEASURED_PEAKS.json ({peak_src}); "
+                                               "work counts each float32 product once")
+    else:
+        ach, u = work / sec / 1e12, "TFLOP/s"
+        peak = fp32 if unit == "fp32" else fp64
+        rec.update(bound="alu", peak_source=f"{unit} FMA issue rate measured by pn_measure_peak on this GPU")
+    rec.update(achieved=ach, peak=peak, unit=u, frac=ach / peak, work_per_launch=work / max(count, 1))
+    return rec
+
+
+# ---------------------------------------------------------------- oracle
+# The CPU oracle on a pool of processes, one per host core (spawned, so
+# that no worker inherits a CUDA context), each on its own walkers with one
+# torch thread.
+
+_ORACLE = {}
+
+
+def _oracle_of(name):
+    if name not in _ORACLE:
+        import torch
+        torch.set_num_threads(1)
+        from oracle.ansatz import Oracle
+        from paper_1909_08423_gb300 import synth
+        _ORACLE[name] = Oracle(synth.WORKLOADS[name]["make"]())
+    return _ORACLE[name]
+
+
+def _oracle_move_and_eloc(job):
+    """One walker chunk: n_metro Metropolis steps, then E_loc."""
+    from oracle import sampling
+    name, r, walker0, n_metro, seed, step0 = job
+    o = _oracle_of(name)
+    lp, _ = o.eval_logpsi(r)
+    if n_metro:
+        r, lp, _ = sampling.metropolis(o, r, lp, n_metro, SIGMA, seed=seed, step0=step0, walker0=walker0)
+    E, _, _ = o.local_energy(r)
+    return r, E
+
+
+def _oracle_grad(job):
+    name, r, cot = job
+    return _oracle_of(name).grad_logpsi(r, cot)
+
+
+class OraclePool:
+    """The oracle's VMC step on a sample of walkers over the host cores."""
+
+    def __init__(self, name, cores=None):
+        import multiprocessing as mp
+        self.name = name
+        self.cores = cores or len(os.sched_getaffinity(0))
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+
+    def step(self, r, k, n_metro):
+        from oracle import clip as oclip
+        parts = np.array_split(np.arange(len(r)), min(self.cores, len(r)))
+        jobs = [(self.name, r[p], int(p[0]), n_metro, 1, k * max(n_metro, 1)) for p in parts]
+        res = self.pool.map(_oracle_move_and_eloc, jobs)
+        r = np.concatenate([x[0] for x in res])
+        E = np.concatenate([x[1] for x in res])
+        cot = oclip.loss_cotangent(oclip.clip_local_energy(E))
+        self.pool.map(_oracle_grad, [(self.name, r[p], cot[p]) for p in parts])
+        return r
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _oracle_walkers(name, W, seed=1):
+    from oracle import sampling
+    from paper_1909_08423_gb300 import synth
+    return sampling.init_walkers(synth.WORKLOADS[name]["make"](), W, seed)
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pool = OraclePool(WORKLOAD)
+    Ws = args.ref_walkers or pool.cores
+    r = _oracle_walkers(WORKLOAD, Ws)
+    for k in range(args.warmup):
+        r = pool.step(r, k, N_METROPOLIS)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        r = pool.step(r, args.warmup + k, N_METROPOLIS)
+    dt = (time.perf_counter() - t0) / args.steps
+    pool.close()
+    v = Ws / dt
+    sample = (f"{Ws} walkers per step of the {W_PER_RANK}-walker N2-shaped workload (the same step: "
+              f"{N_METROPOLIS} Metropolis step + E_loc + clip + grad), over {pool.cores} processes of one thread")
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD_DESC.format(W=W_PER_RANK, C=CHUNK) + f"; sampled: {Ws} walkers per step",
+                       "walkers": Ws},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample(n_per_core=1):
+    """Oracle timing on the host cores for the cpu_baseline key: one VMC step
+    of the headline workload on a sample of walkers (n_per_core per core)."""
+    pool = OraclePool(WORKLOAD)
+    Ws = n_per_core * pool.cores
+    r = _oracle_walkers(WORKLOAD, Ws)
+    t0 = time.perf_counter()
+    pool.step(r, 0, N_METROPOLIS)
+    dt = time.perf_counter() - t0
+    pool.close()
+    return {"value": Ws / dt, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "sample": f"{Ws} walkers of the N2-shaped workload, one step ({N_METROPOLIS} Metropolis step + E_loc + "
+                      f"clip + grad), {pool.cores} processes of one thread", "seconds": dt}
+
+
+def run_be_step(W=4096, steps=3, n_metro=100):
+    """The Be-atom step: 100 Metropolis steps + E_loc + clip + grad, mixed."""
+    import torch
+    from paper_1909_08423_gb300 import binding, synth
+    s = binding.System(synth.be(), precision=binding.PN_MIXED, max_walkers=W)
+    r = torch.empty(W, s.N, 3, dtype=torch.float64, device="cuda")
+    s.init_walkers(r, 5)
+    lp = torch.empty(W, dtype=torch.float64, device="cuda")
+    sg = torch.empty_like(lp)
+    s.eval_logpsi(r, lp, sg)
+    E, Ec, cot = torch.empty_like(lp), torch.empty_like(lp), torch.empty_like(lp)
+    g = torch.empty(s.n_params, dtype=torch.float64, device="cuda")
+
+    def step(k):
+        s.metropolis_step(r, lp, n_metro, SIGMA, 5, k * n_metro)
+        s.eval_local_energy(r, E)
+        binding.clip_local_energy(E, Ec, cot)
+        s.grad_logpsi(r, cot, g)
+
+    step(0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(steps):
+        step(1 + k)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s.close()
+    return {"walkers": W, "ms_per_step": ms, "walker_eloc_per_s": W / (ms / 1e3), "steps": steps,
+            "step": f"{n_metro} Metropolis steps + E_loc + clip + grad, mixed, CUDA events"}
+
+
+def run_h10_step(W=8192, steps=3):
+    """The H10 chain: E_loc + clip + grad of 8192 walkers, mixed."""
+    import torch
+    from paper_1909_08423_gb300 import binding, synth
+    s = binding.System(synth.h10(), precision=binding.PN_MIXED, max_walkers=W)
+    r = torch.empty(W, s.N, 3, dtype=torch.float64, device="cuda")
+    s.init_walkers(r, 3)
+    lp = torch.empty(W, dtype=torch.float64, device="cuda")
+    sg = torch.empty_like(lp)
+    s.eval_logpsi(r, lp, sg)
+    s.metropolis_step(r, lp, 50, SIGMA, 3, 0)
+    E, Ec, cot = torch.empty_like(lp), torch.empty_like(lp), torch.empty_like(lp)
+    g = torch.empty(s.n_params, dtype=torch.float64, device="cuda")
+
+    def step():
+        s.eval_local_energy(r, E)
+        binding.clip_local_energy(E, Ec, cot)
+        s.grad_logpsi(r, cot, g)
+
+    step()
+    s.guard_count()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ng = s.guard_count()
+    s.close()
+    return {"walkers": W, "ms_per_step": ms, "walker_eloc_per_s": W / (ms / 1e3), "steps": steps,
+            "guard_reevaluated_per_step": ng / steps, "step": "E_loc + clip + grad, mixed, CUDA events"}
 
 
 def _clock_sampler(path):
@@ -131,6 +325,7 @@ def _clock_sampler(path):
     return proc
 
 
+
 def _clock_summary(path, dev_index, skip=0):
     try:
         rows = [l.strip().split(", ") for l in open(path) if l.strip()][skip:]
@@ -150,83 +345,6 @@ def _clock_summary(path, dev_index, skip=0):
     return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
             "reasons": sorted(reasons), "samples": len(rows)}
 
-
-def run_reference(args):
-    """The CPU oracle, as it stands, on a bounded sample of the workload."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    import torch
-    from oracle import clip as oclip
-    from oracle import sampling
-    from oracle.ansatz import Oracle
-    from paper_1909_08423_gb300 import synth
-    sysd = synth.WORKLOADS[WORKLOAD]["make"]()
-    o = Oracle(sysd)
-    Ws = args.ref_walkers
-    r = sampling.init_walkers(sysd, Ws, 1)
-    lp, _ = o.eval_logpsi(r)
-
-    def step(k):
-        nonlocal r, lp
-        r, lp, _ = sampling.metropolis(o, r, lp, N_METROPOLIS, SIGMA, seed=1, step0=k * N_METROPOLIS)
-        E, _, _ = o.local_energy(r)
-        Ec = oclip.clip_local_energy(E)
-        o.grad_logpsi(r, oclip.loss_cotangent(Ec))
-
-    for k in range(args.warmup):
-        step(k)
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        step(args.warmup + k)
-    dt = (time.perf_counter() - t0) / args.steps
-    v = Ws / dt
-    cores = torch.get_num_threads()
-    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"Be atom, {Ws} walkers sample of {W_PER_RANK}, {N_METROPOLIS} Metropolis steps "
-                                   "+ E_loc + clip + grad per step", "walkers": Ws},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{Ws} walkers per step of the {W_PER_RANK}-walker Be workload"},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
-def cpu_baseline_sample(n_walkers=96):
-    """Oracle timing on the host cores for the cpu_baseline key."""
-    import torch
-    from oracle import clip as oclip
-    from oracle import sampling
-    from oracle.ansatz import Oracle
-    from paper_1909_08423_gb300 import synth
-    sysd = synth.WORKLOADS[WORKLOAD]["make"]()
-    o = Oracle(sysd)
-    r = sampling.init_walkers(sysd, n_walkers, 1)
-    lp, _ = o.eval_logpsi(r)
-    t0 = time.perf_counter()
-    r, lp, _ = sampling.metropolis(o, r, lp, N_METROPOLIS, SIGMA, seed=1, step0=0)
-    E, _, _ = o.local_energy(r)
-    Ec = oclip.clip_local_energy(E)
-    o.grad_logpsi(r, oclip.loss_cotangent(Ec))
-    dt = time.perf_counter() - t0
-    cores = torch.get_num_threads()
-    # the same step on one core, on a smaller sample of the same walkers
-    n1 = max(2, n_walkers // 8)
-    torch.set_num_threads(1)
-    try:
-        r1 = sampling.init_walkers(sysd, n1, 1)
-        lp1, _ = o.eval_logpsi(r1)
-        t1 = time.perf_counter()
-        r1, lp1, _ = sampling.metropolis(o, r1, lp1, N_METROPOLIS, SIGMA, seed=1, step0=0)
-        E1, _, _ = o.local_energy(r1)
-        o.grad_logpsi(r1, oclip.loss_cotangent(oclip.clip_local_energy(E1)))
-        dt1 = time.perf_counter() - t1
-    finally:
-        torch.set_num_threads(cores)
-    return {"value": n_walkers / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n_walkers} walkers: {N_METROPOLIS} Metropolis steps + E_loc + clip + grad (one step)",
-            "seconds": dt, "value_1core": n1 / dt1, "sample_1core": f"{n1} walkers, same step, 1 thread"}
 
 
 def run_langevin(sysd, W, target=0.57, steps=10):
@@ -284,55 +402,6 @@ def run_langevin(sysd, W, target=0.57, steps=10):
     return out
 
 
-def run_configs():
-    """The H10 chain (8192 walkers: E_loc + clipping + grad ln|psi|) and the
-    N2-shaped diatomic (16384 walkers in chunks of 4096: one Metropolis step
-    + E_loc + clipping + grad ln|psi|) at full size, mixed path, CUDA events
-    over two repetitions after one warm-up."""
-    import torch
-    from paper_1909_08423_gb300 import binding, synth
-
-    def timed(fn, n=2):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(n):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / n
-
-    out = {}
-    for name, make, W, chunk, sweep in (("h10", synth.h10, 8192, 8192, 0), ("n2", synth.n2, 16384, 4096, 1)):
-        sysd = make()
-        s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=chunk)
-        r = torch.empty(W, s.N, 3, dtype=torch.float64, device="cuda")
-        s.init_walkers(r, 3)
-        lp = torch.empty(W, dtype=torch.float64, device="cuda")
-        sg = torch.empty_like(lp)
-        s.eval_logpsi(r, lp, sg)
-        s.metropolis_step(r, lp, 20, SIGMA, 3, 0)
-        E, Ec, cot = torch.empty_like(lp), torch.empty_like(lp), torch.empty_like(lp)
-        g = torch.empty(s.n_params, dtype=torch.float64, device="cuda")
-        k = [100]
-
-        def step():
-            if sweep:
-                s.metropolis_step(r, lp, 1, SIGMA, 3, k[0])
-                k[0] += 1
-            s.eval_local_energy(r, E)
-            binding.clip_local_energy(E, Ec, cot)
-            s.grad_logpsi(r, cot, g)
-
-        ms_step = timed(step)
-        out[name] = {"walkers": W, "chunk": chunk, "ms_step": ms_step, "walker_eloc_per_s": W / (ms_step / 1e3),
-                     "ms_eloc": timed(lambda: s.eval_local_energy(r, E)),
-                     "ms_grad": timed(lambda: s.grad_logpsi(r, cot, g)),
-                     "ms_metropolis_step": timed(lambda: s.metropolis_step(r, lp, 1, SIGMA, 5, 10 ** 6)) if sweep else None}
-        s.close()
-    return out
-
 
 def run_line_scan(npts=4096):
     """E_loc along the LiH line scan through both nuclei and both fixed
@@ -360,6 +429,7 @@ def run_line_scan(npts=4096):
             "note": "one electron moved along the molecular axis through both nuclei and both fixed electrons"}
 
 
+
 def run_vmc_train(sysd, steps=10):
     """The paper's training configuration (batch 10000, 2000 walkers, pool
     refilled every 100 steps after 50 discarded steps) on the bench system:
@@ -385,6 +455,7 @@ def run_vmc_train(sysd, steps=10):
     return {"batch": 10000, "walkers": 2000, "train_step_ms": step_ms, "pool_refill_ms": refill_ms,
             "amortized_step_ms": step_ms + refill_ms / 100, "e_mean_last": hist[-1]["e_mean"],
             "note": "host-timed (the parameter upload synchronises); refill = 50 + 500 Metropolis steps of 2000 walkers"}
+
 
 
 def run_ablation(W=4096, steps=3):
@@ -429,69 +500,79 @@ def run_ablation(W=4096, steps=3):
     return out
 
 
-def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384, load=0.7,
-                precisions=("mixed", "fp64"), sweep=()):
-    """Poisson stream of seeded molecules through the serving loop, mixed and
-    plain FP64 servers.  The arrival rate is set to `load` times the mixed
-    server's measured capacity (a closed-loop calibration burst first).
-    `sweep` lists further loads at which the mixed server is measured again
-    on the same stream (the latency-load curve)."""
+
+def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384, load=0.7, fp64_jobs=100,
+                sweep=()):
+    """Poisson stream of seeded molecules through the serving loop.  The
+    arrival rate is `load` times the mixed server's capacity, measured first
+    by a closed-loop burst of the stream's first jobs (also with one slot, to
+    show what running jobs side by side gains).  The mixed server serves the
+    whole stream; the plain FP64 server serves its first fp64_jobs jobs at the
+    same arrival rate.  `sweep` lists further loads at which the mixed server
+    is measured again (the latency-load curve)."""
     import torch
     from paper_1909_08423_gb300 import binding, synth
     stream = synth.serving_stream(n_jobs, seed, rate_per_s=1.0, wmax=wmax)
-    out = {}
-    rate = cap_mixed = None
-    runs = [(p_, load) for p_ in precisions] + [("mixed", l_) for l_ in sweep]
-    for prec_name, run_load in runs:
-        prec = binding.PN_MIXED if prec_name == "mixed" else binding.PN_FP64
-        systems = [binding.System(synth.serving_system(j["seed"]), precision=prec, max_walkers=1) for j in stream]
-        srv = binding.Server(budget_gb << 30, n_slots=slots, chunk_walkers=chunk)
-        # calibration: all jobs of a prefix at once -> walker-E_loc/s and jobs/s capacity
-        ncal = min(len(stream), 24)
+    kind = lambda j: binding.PN_JOB_SWEEP if j["kind"] == "sweep" else binding.PN_JOB_ELOC
+
+    def burst(systems, n, n_slots):
+        srv = binding.Server(budget_gb << 30, n_slots=n_slots, chunk_walkers=chunk)
         t0 = time.perf_counter()
-        ids = [srv.submit(systems[k], binding.PN_JOB_SWEEP if stream[k]["kind"] == "sweep" else binding.PN_JOB_ELOC,
-                          stream[k]["W"], n_steps=stream[k]["n_steps"], sigma=0.2, seed=stream[k]["seed"])
-               for k in range(ncal)]
-        for i in ids:
-            srv.poll(i, timeout_us=-1)
-        cap_jobs = ncal / (time.perf_counter() - t0)
-        if prec_name == "mixed" and cap_mixed is None:
-            cap_mixed = cap_jobs
-        if rate is None:  # every server sees the arrival rate set by the first calibration
-            rate = load * cap_jobs
-        this_rate = run_load * cap_mixed if (prec_name == "mixed" and run_load != load) else rate
-        # open-loop Poisson arrivals at `rate`
-        arr = np.cumsum(np.random.default_rng(seed).exponential(1.0 / this_rate, size=n_jobs))
+        ids = [srv.submit(systems[k], kind(stream[k]), stream[k]["W"], n_steps=stream[k]["n_steps"], sigma=0.2,
+                          seed=stream[k]["seed"]) for k in range(n)]
+        walkers = sum(srv.poll(i, timeout_us=-1).W for i in ids)
+        dt = time.perf_counter() - t0
+        srv.close()
+        return n / dt, walkers / dt
+
+    def open_loop(systems, n, rate):
+        srv = binding.Server(budget_gb << 30, n_slots=slots, chunk_walkers=chunk)
+        arr = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, size=n))
         ids = []
         t0 = time.perf_counter()
-        for k, j in enumerate(stream):
+        for k in range(n):
             while time.perf_counter() - t0 < arr[k]:
                 time.sleep(min(0.0005, max(0.0, arr[k] - (time.perf_counter() - t0))))
-            ids.append(srv.submit(systems[k], binding.PN_JOB_SWEEP if j["kind"] == "sweep" else binding.PN_JOB_ELOC,
-                                  j["W"], n_steps=j["n_steps"], sigma=0.2, seed=j["seed"]))
-        lat = []
-        walkers = 0
-        for k, i in enumerate(ids):
+            j = stream[k]
+            ids.append(srv.submit(systems[k], kind(j), j["W"], n_steps=j["n_steps"], sigma=0.2, seed=j["seed"]))
+        lat, walkers, over = [], 0, []
+        for i in ids:
             res = srv.poll(i, timeout_us=-1)
             lat.append(res.queue_ms + res.run_ms)
             walkers += res.W
         span = time.perf_counter() - t0
         srv.close()
         lat = np.array(lat)
-        rec = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-               "walker_eloc_per_s": walkers / span, "jobs_per_s": n_jobs / span,
-               "calibrated_capacity_jobs_per_s": cap_jobs}
-        if run_load == load and prec_name not in out:
-            out[prec_name] = rec
-        else:
-            out.setdefault("load_sweep", []).append(dict(rec, load=run_load, arrival_rate_jobs_per_s=this_rate))
-        for s_ in systems:
+        return {"jobs": n, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "walker_eloc_per_s": walkers / span, "jobs_per_s": n / span, "arrival_rate_jobs_per_s": rate}
+
+    out = {}
+    ncal = min(n_jobs, 24)
+    mixed_sys = [binding.System(synth.serving_system(j["seed"]), precision=binding.PN_MIXED, max_walkers=1)
+                 for j in stream]
+    cap_jobs, cap_walkers = burst(mixed_sys, ncal, slots)
+    cap1_jobs, cap1_walkers = burst(mixed_sys, ncal, 1)
+    rate = load * cap_jobs
+    out["mixed"] = open_loop(mixed_sys, n_jobs, rate)
+    out["mixed"].update(calibrated_capacity_jobs_per_s=cap_jobs, calibrated_walker_eloc_per_s=cap_walkers,
+                        one_slot_capacity_jobs_per_s=cap1_jobs, one_slot_walker_eloc_per_s=cap1_walkers)
+    for l_ in sweep:
+        out.setdefault("load_sweep", []).append(dict(open_loop(mixed_sys, n_jobs, l_ * cap_jobs), load=l_))
+    for s_ in mixed_sys:
+        s_.close()
+    if fp64_jobs > 0:
+        nf = min(fp64_jobs, n_jobs)
+        f64_sys = [binding.System(synth.serving_system(stream[k]["seed"]), precision=binding.PN_FP64, max_walkers=1)
+                   for k in range(nf)]
+        out["fp64"] = open_loop(f64_sys, nf, rate)
+        out["fp64"]["note"] = f"the stream's first {nf} jobs at the mixed server's arrival rate"
+        for s_ in f64_sys:
             s_.close()
     out["arrival_rate_jobs_per_s"] = rate
     out["jobs"] = n_jobs
     out["stream"] = (f"{n_jobs} Poisson jobs, seeded neutral molecules of 1-6 nuclei, Z 1-10, 2-30 electrons, "
                      f"1-32 determinants, 256-{wmax} walkers log-uniform, E_loc or 10-step sweep 50/50; "
-                     f"{slots} slots, load {load} of calibrated mixed capacity")
+                     f"{slots} slots, load {load} of the calibrated mixed capacity")
     return out
 
 
@@ -501,19 +582,22 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-walkers", type=int, default=32)
+    ap.add_argument("--ref-walkers", type=int, default=0, help="oracle walkers per step (default: one per core)")
+    ap.add_argument("--walkers", type=int, default=W_PER_RANK)
+    ap.add_argument("--chunk", type=int, default=CHUNK)
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--burn", type=int, default=200, help="Metropolis steps before timing (walkers sampled from |psi|^2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-langevin", action="store_true")
-    ap.add_argument("--serve-jobs", type=int, default=60)
+    ap.add_argument("--no-extras", action="store_true", help="skip the Be/H10 steps, Langevin, scan, training, ablation")
+    ap.add_argument("--serve-jobs", type=int, default=2000)
+    ap.add_argument("--serve-fp64-jobs", type=int, default=100)
     ap.add_argument("--serve-only", action="store_true")
     ap.add_argument("--serve-load", type=float, default=0.7, help="offered load, fraction of calibrated mixed capacity")
-    ap.add_argument("--serve-precisions", default="mixed,fp64")
     ap.add_argument("--serve-sweep", default="", help="further loads for the mixed server, e.g. 0.5,0.9")
     ap.add_argument("--sampler", type=int, default=None,
                     help="PN_OPT_FUSED_SAMPLER for the timed mixed path (library default if absent)")
-    ap.add_argument("--case", choices=["sampler", "jet_tc", "langevin", "drift_n2", "configs"], default=None,
+    ap.add_argument("--case", choices=["sampler", "jet_tc", "langevin", "drift_n2", "n2_small"], default=None,
                     help="run one small kernel case (for ncu captures) and exit")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -523,10 +607,6 @@ def main():
     import torch.distributed as dist
     from paper_1909_08423_gb300 import binding, synth
 
-    if args.case == "configs":  # the H10 and N2-shaped configurations at full size
-        torch.cuda.set_device(0)
-        print(json.dumps(run_configs()), flush=True)
-        return
     if args.case == "drift_n2":  # reverse-mode drift of 2048 N2-shaped walkers (inputs larger than L2)
         torch.cuda.set_device(0)
         sysd = synth.n2()
@@ -541,27 +621,60 @@ def main():
         s.device_status()
         print("case ok", flush=True)
         return
+    if args.case == "n2_small":  # the headline step on 1024 N2-shaped walkers, one chunk, work per class printed
+        torch.cuda.set_device(0)
+        sysd = synth.n2()
+        W = 1024
+        s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=W)
+        r = torch.empty(W, s.N, 3, dtype=torch.float64, device="cuda")
+        s.init_walkers(r, 1)
+        lp = torch.empty(W, dtype=torch.float64, device="cuda")
+        sg = torch.empty_like(lp)
+        s.eval_logpsi(r, lp, sg)
+        E, Ec, cot = torch.empty_like(lp), torch.empty_like(lp), torch.empty_like(lp)
+        g = torch.empty(s.n_params, dtype=torch.float64, device="cuda")
+
+        def step(k):
+            s.metropolis_step(r, lp, N_METROPOLIS, SIGMA, 7, k)
+            s.eval_local_energy(r, E)
+            binding.clip_local_energy(E, Ec, cot)
+            s.grad_logpsi(r, cot, g)
+
+        step(0)
+        work = {}
+        for kname in KERNEL_CLASSES:
+            binding.profile(kname)
+            step(1)
+            torch.cuda.synchronize()
+            n, ms, wk = binding.profile_read()
+            if n:
+                work[kname] = {"launches": n, "ms": ms, "work": wk}
+        binding.profile(None)
+        s.device_status()
+        print(json.dumps({"case": "n2_small", "walkers": W, "per_class_one_step": work}), flush=True)
+        print("case ok", flush=True)
+        return
     if args.case:
         torch.cuda.set_device(0)
         sysd = synth.be()
-        s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=W_PER_RANK)
-        r = torch.empty(W_PER_RANK, s.N, 3, dtype=torch.float64, device="cuda")
+        s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=4096)
+        r = torch.empty(4096, s.N, 3, dtype=torch.float64, device="cuda")
         s.init_walkers(r, 1)
         if args.sampler is not None:
             s.set_option(binding.PN_OPT_FUSED_SAMPLER, args.sampler)
         if args.case == "sampler":  # 5 Metropolis steps of the Be workload
-            lp = torch.empty(W_PER_RANK, dtype=torch.float64, device="cuda")
+            lp = torch.empty(4096, dtype=torch.float64, device="cuda")
             sg = torch.empty_like(lp)
             s.eval_logpsi(r, lp, sg)
             s.metropolis_step(r, lp, 5, SIGMA, 3, 0)
         elif args.case == "langevin":  # initial drift + 3 Langevin steps of the Be workload
-            lp = torch.empty(W_PER_RANK, dtype=torch.float64, device="cuda")
+            lp = torch.empty(4096, dtype=torch.float64, device="cuda")
             g = torch.empty_like(r)
             s.eval_drift(r, g, lp)
             s.langevin_step(r, lp, g, 3, 0.1, 3, 0)
         else:  # one local-energy pass with every layer group on tcgen05
             s.set_option(binding.PN_OPT_TENSOR_CORES, 7)
-            E = torch.empty(W_PER_RANK, dtype=torch.float64, device="cuda")
+            E = torch.empty(4096, dtype=torch.float64, device="cuda")
             s.eval_local_energy(r, E)
         s.device_status()
         print("case ok", flush=True)
@@ -570,9 +683,8 @@ def main():
     if args.serve_only:
         torch.cuda.set_device(0)
         sweep = tuple(float(x) for x in args.serve_sweep.split(",") if x)
-        print(json.dumps({"serve": run_serving(args.serve_jobs, load=args.serve_load,
-                                               precisions=tuple(args.serve_precisions.split(",")), sweep=sweep)}),
-              flush=True)
+        print(json.dumps({"serve": run_serving(args.serve_jobs, load=args.serve_load, fp64_jobs=args.serve_fp64_jobs,
+                                               sweep=sweep)}), flush=True)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -589,12 +701,17 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    peaks, peak_src = _peaks()
+    fp32_peak = binding.measure_peak(0)
+    fp64_peak = binding.measure_peak(1)
+
     sysd = synth.WORKLOADS[WORKLOAD]["make"]()
-    W = W_PER_RANK
+    W, chunk = args.walkers, args.chunk
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    def make_state(precision):
-        s = binding.System(sysd, precision=precision, max_walkers=W)
+    def make_state(precision, burn=None):
+        burn = args.burn if burn is None else burn
+        s = binding.System(sysd, precision=precision, max_walkers=chunk)
         if args.sampler is not None and precision == binding.PN_MIXED:
             s.set_option(binding.PN_OPT_FUSED_SAMPLER, args.sampler)
         r = torch.empty(W, s.N, 3, dtype=torch.float64, device=dev)
@@ -602,6 +719,8 @@ def main():
         lp = torch.empty(W, dtype=torch.float64, device=dev)
         sg = torch.empty_like(lp)
         s.eval_logpsi(r, lp, sg)
+        if burn:
+            s.metropolis_step(r, lp, burn, SIGMA, 999 + rank, 1 << 40)  # leave the initial Gaussian cloud
         st = dict(s=s, r=r, lp=lp, E=torch.empty_like(lp), Ec=torch.empty_like(lp), cot=torch.empty_like(lp),
                   g=torch.empty(s.n_params, dtype=torch.float64, device=dev),
                   nacc=torch.zeros(1, dtype=torch.int64, device=dev), k=0)
@@ -620,9 +739,10 @@ def main():
             step(st)
         barrier()
         if prof_kernel:
-            lib.pn_profile_kernel(prof_kernel.encode())
+            binding.profile(prof_kernel)
         n0 = lib.pn_launch_count()
         times = []
+        acc0 = 0
         for _ in range(steps):
             flush.zero_()
             a = torch.cuda.Event(enable_timing=True)
@@ -636,47 +756,38 @@ def main():
         ms = sum(a.elapsed_time(b) for a, b in times) / steps
         kern = None
         if prof_kernel:
-            cnt = C_int64()
-            tot = C_double()
-            binding.check(lib.pn_profile_read(ctypes.byref(cnt), ctypes.byref(tot)))
-            lib.pn_profile_kernel(None)
-            kern = (cnt.value, tot.value)
+            kern = binding.profile_read()
+            binding.profile(None)
         return ms, launches, kern
 
-    import ctypes
-    C_int64, C_double = ctypes.c_int64, ctypes.c_double
-    lib.pn_launch_count.restype = ctypes.c_ulonglong
-    lib.pn_profile_kernel.argtypes = [ctypes.c_char_p]
-    lib.pn_profile_read.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
-
     mixed = make_state(binding.PN_MIXED)
-    # find the dominant kernel class of the step (one profiled step each)
     for _ in range(max(1, args.warmup)):
         step(mixed)
-    candidates = ["k_linear", "k_filter", "k_message", "k_slater", "k_orbitals", "k_combine", "k_features",
-                  "k_ssp_jet", "k_wgrad", "k_slater_bwd", "k_propose", "k_accept", "k_geometry",
-                  "k_metropolis_warp", "k_metropolis_fused", "k_metropolis_tc", "k_linear_tc"]
+    # where the step's time goes: every kernel class timed over one step
     share = {}
-    for kname in candidates:
-        lib.pn_profile_kernel(kname.encode())
+    for kname in KERNEL_CLASSES:
+        binding.profile(kname)
         step(mixed)
         torch.cuda.synchronize()
-        cnt, tot = C_int64(), C_double()
-        binding.check(lib.pn_profile_read(ctypes.byref(cnt), ctypes.byref(tot)))
-        share[kname] = (cnt.value, tot.value)
-    lib.pn_profile_kernel(None)
+        n, ms_k, wk = binding.profile_read()
+        if n:
+            share[kname] = (n, ms_k, wk)
+    binding.profile(None)
     dom = max(share, key=lambda k: share[k][1])
+    mixed["s"].guard_count()
 
     # nvidia-smi samples of the timed region: PN_CLOCK_LOG names the file to
     # keep them in (rank appended), else a temporary file
     clk_path = os.environ.get("PN_CLOCK_LOG")
     clk_path = f"{clk_path}.rank{rank}" if clk_path else os.path.join(tempfile.gettempdir(), f"pn_clocks_{rank}.csv")
     sampler = _clock_sampler(clk_path)
+    mixed["nacc"].zero_()
     ms, launches, kern = timed(mixed, args.steps, 0, prof_kernel=dom)
     if sampler:
         sampler.terminate()
         sampler.wait()
     clocks = _clock_summary(clk_path, local, getattr(sampler, "skip", 0))
+    guard_n = mixed["s"].guard_count()
     t = torch.tensor([ms], device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -684,21 +795,35 @@ def main():
     value = W * world / (ms_max / 1e3)
     acc_rate = float(mixed["nacc"].item()) / (W * N_METROPOLIS)
 
-    # FP64 path, same step (fewer steps: it is the slow comparator)
-    f64 = make_state(binding.PN_FP64)
-    ms64, _, _ = timed(f64, args.fp64_steps, 1)
-    e64 = f64["E"].clone()
+    roof = _roofline(dom, kern[0], kern[1], kern[2], peaks, peak_src, fp32_peak, fp64_peak)
+    roof["kernel_ms_per_step"] = kern[1] / args.steps
+    tpw, tnote = _traffic_per_work(dom)
+    roof["traffic"] = tpw * roof["work_per_launch"] if (tpw is not None and roof.get("work_per_launch")) else None
+    roof["traffic_note"] = tnote
+    by_kernel = sorted((_roofline(k, v[0], v[1], v[2], peaks, peak_src, fp32_peak, fp64_peak)
+                        for k, v in share.items()), key=lambda x: -x["kernel_ms"])[:8]
 
-    # accuracy of the mixed path on the same sampled walkers
-    mixed_err = None
+    # accuracy of the mixed path on the sampled walkers, against the FP64 path
     E_m = torch.empty_like(mixed["E"])
     E_d = torch.empty_like(mixed["E"])
+    st_d = torch.empty(W, dtype=torch.int32, device=dev)
     mixed["s"].eval_local_energy(mixed["r"], E_m)
-    f64_check = binding.System(sysd, precision=binding.PN_FP64, max_walkers=W)
-    f64_check.eval_local_energy(mixed["r"], E_d)
+    g_err = mixed["s"].guard_count()
+    f64_check = binding.System(sysd, precision=binding.PN_FP64, max_walkers=chunk)
+    f64_check.eval_local_energy(mixed["r"], E_d, None, None, st_d)
     torch.cuda.synchronize()
-    err = (E_m - E_d).abs().cpu().numpy()
-    mixed_err = {"max": float(err.max()), "p999": float(np.quantile(err, 0.999)), "mean": float(err.mean())}
+    ok = (st_d == 0).cpu().numpy()
+    err = (E_m - E_d).abs().cpu().numpy()[ok]
+    mixed_err = {"max": float(err.max()), "p999": float(np.quantile(err, 0.999)), "mean": float(err.mean()),
+                 "walkers": int(ok.sum()), "guard_reevaluated": int(g_err),
+                 "note": "every walker of the timed state after the timed steps, mixed (guarded) vs float64 path"}
+    f64_check.close()
+
+    # FP64 path, same step (fewer steps: it is the slow comparator)
+    f64 = make_state(binding.PN_FP64, burn=0)
+    ms64, _, _ = timed(f64, args.fp64_steps, 1)
+    f64["s"].close()
+    del f64
 
     # end to end through the C ABI with host buffers in pinned (page-locked)
     # memory; every call copies its inputs in and its results out inside the
@@ -714,9 +839,7 @@ def main():
         rh[...] = mixed["r"].cpu().numpy()
         lph = pinned((W,))
         lph[...] = mixed["lp"].cpu().numpy()
-        Eh = pinned((W,))
-        Ech = pinned((W,))
-        coth = pinned((W,))
+        Eh, Ech, coth = pinned((W,)), pinned((W,)), pinned((W,))
         gh = pinned((s.n_params,))
         nah = pinned((1,), torch.int64)
 
@@ -735,78 +858,47 @@ def main():
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / n_e2e
         rb, lb = rh.nbytes, lph.nbytes
+        # in: r and ln|psi| (sampler), r (E_loc), E (clip), r and cotangent (grad);
+        # out: r, ln|psi|, accept count (sampler), E (E_loc), clipped E and
+        # cotangent (clip), gradient
         h2d = rb + lb + rb + W * 8 + rb + W * 8
         d2h = rb + lb + 8 + W * 8 + 2 * W * 8 + gh.nbytes
         e2e = {"value": W * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": dt * 1e3}
 
-    peaks, peak_src = _peaks()
-    roof = None
-    fl = algorithmic_flops(sysd, dom, "value")
-    if kern and kern[0] > 0:
-        # per step: value-pass launches dominate (Metropolis); count the
-        # algorithmic work of all timed launches of this class in the step
-        per_step_flops = None
-        if dom in ("k_filter", "k_linear", "k_message", "k_slater"):
-            per_step_flops = W * (N_METROPOLIS * algorithmic_flops(sysd, dom, "value") +
-                                  algorithmic_flops(sysd, dom, "jet"))
-        elif dom in ("k_metropolis_warp", "k_metropolis_fused", "k_metropolis_tc"):
-            per_step_flops = W * N_METROPOLIS * algorithmic_flops(sysd, dom, "value")
-        kern_ms_per_step = kern[1] / args.steps
-        if per_step_flops:
-            achieved = per_step_flops / (kern_ms_per_step / 1e3) / 1e12
-            # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
-            fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
-            roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp32_peak, "traffic": None,
-                    "launches_per_step": kern[0] / args.steps, "kernel_ms_per_step": kern_ms_per_step,
-                    "peak_source": "fp32 CUDA-core nominal from unit counts and max clock",
-                    "flops_per_step": per_step_flops,
-                    "note": "algorithmic float32 network FLOPs of the launches timed; the sampler also "
-                            "runs float64 determinants and log-sums"}
-            if dom == "k_metropolis_tc":
-                # DRAM bytes of one launch over these 4096 walkers, from an ncu
-                # capture (dram__bytes_read.sum + dram__bytes_write.sum, 5-step
-                # launch): positions, log-amplitudes and the first read of the
-                # weights; it does not grow with the step count (the weights
-                # stay in L2, the walker state in shared memory)
-                roof["traffic"] = 1.13e6
-                roof["traffic_note"] = ("ncu, one k_metropolis_tc launch on the same 4096 walkers (5 steps); "
-                                        "independent of the step count")
-                ex = tc_sampler_executed_flops(sysd, W) * N_METROPOLIS
-                ex_tf = ex / (kern_ms_per_step / 1e3) / 1e12
-                bf16 = peaks.get("bf16_tflops", 1900.0)
-                roof["tensor_view"] = {
-                    "executed_tflops": ex_tf, "peak": bf16, "frac": ex_tf / bf16, "unit": "TFLOP/s",
-                    "note": "bf16 tcgen05 work actually issued (six piece products per float32 product, "
-                            "128-row tiles incl. padding) against the bf16 peak (" + peak_src + ")"}
-        else:
-            roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
-                    "traffic": None, "kernel_ms_per_step": kern_ms_per_step}
-
+    cfg = {"workload": WORKLOAD_DESC.format(W=W, C=chunk), "walkers_per_gpu": W, "chunk": chunk,
+           "precision": "mixed: float32 network, float64 orbitals/determinants/sums/Coulomb; local-energy guard on "
+                        "(tau 2e-5 Ha)",
+           "l2": "flushed (256 MB write) between timed steps; the per-chunk intermediates (~14 GB) exceed L2",
+           "parallelism": f"replicas x{world} (walkers sharded, no data-path collective)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"Be atom (Z=4, 4 e, 4 dets, 4s2p, D=64 L=3 K=32), {W} walkers/GPU; step = "
-                                   f"{N_METROPOLIS} Metropolis steps (sigma {SIGMA}) + E_loc + clip + grad ln|psi|",
-                       "walkers_per_gpu": W, "precision": "mixed (float32 network, float64 orbitals/dets/sums)",
-                       "l2": "flushed (256 MB write) between timed steps",
-                       "parallelism": f"replicas x{world}"},
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": cfg,
+            "roofline": roof, "roofline_by_kernel": by_kernel,
+            "peaks": {"fp32_tflops": fp32_peak, "fp64_tflops": fp64_peak, "fp32_fp64_source": "pn_measure_peak",
+                      "hbm_gbs": peaks["hbm_gbs"], "bf16_tflops": peaks["bf16_tflops"],
+                      "hbm_bf16_source": f"MEASURED_PEAKS.json ({peak_src})"},
+            "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e,
             "fp64": {"value": W * world / (ms64 / 1e3), "ms_per_step": ms64, "steps": args.fp64_steps},
             "mixed_vs_fp64_eloc_err_ha": mixed_err,
+            "guard_reevaluated_per_step": guard_n / max(args.steps, 1),
             "accept_rate": acc_rate,
-            "kernel_share": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(share.items(), key=lambda x: -x[1][1])},
-            "roofline": roof, "peaks_source": peak_src, "gpu_launches": int(launches),
-            "clocks": clocks, "e2e": e2e}
+            "kernel_share": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(share.items(), key=lambda x: -x[1][1])}}
+    mixed["s"].close()
+    del mixed
+    torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
-    if rank == 0 and not args.no_langevin:
-        line["langevin"] = run_langevin(sysd, W)
+    if rank == 0 and not args.no_extras:
+        line["be"] = run_be_step()
+        line["h10"] = run_h10_step()
+        be = synth.be()
+        line["langevin"] = run_langevin(be, 4096)
         line["line_scan"] = run_line_scan()
-        line["vmc_train"] = run_vmc_train(sysd)
-        line["ablation"] = run_ablation(W)
+        line["vmc_train"] = run_vmc_train(be)
+        line["ablation"] = run_ablation(4096)
     if rank == 0 and args.serve_jobs > 0:
-        line["serve"] = run_serving(args.serve_jobs)
+        line["serve"] = run_serving(args.serve_jobs, load=args.serve_load, fp64_jobs=args.serve_fp64_jobs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

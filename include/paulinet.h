@@ -270,9 +270,42 @@ int pn_langevin_step(pn_system_t sys, double* r, double* logabs, double* drift,
  *   paper_1909_08423_gb300.precision.calibrate measures this).
  * PN_OPT_DRIFT (default 1): how pn_eval_drift and pn_langevin_step form
  *   grad_r ln|psi| -- 1 reverse mode (work linear in the electron count),
- *   0 the forward jet pass (3N + 2 rows per electron). */
-enum { PN_OPT_FUSED_SAMPLER = 1, PN_OPT_TENSOR_CORES = 2, PN_OPT_DRIFT = 3 };
+ *   0 the forward jet pass (3N + 2 rows per electron).
+ * PN_OPT_GUARD (PN_MIXED only; default 20): the local-energy guard of
+ *   pn_eval_local_energy, value = tau in micro-hartree, 0 = off.  The
+ *   float32 network's rounding reaches E_loc through the determinants and
+ *   the squared gradient, and a few walkers in ten thousand amplify it past
+ *   1e-4 Ha, with no cheap per-walker predictor of which.  With the guard on,
+ *   every workspace chunk's heads (the Jastrow and backflow maps) are
+ *   evaluated a second time on the other unit (tensor cores if they ran on
+ *   CUDA cores, and back), which changes only their rounding; the
+ *   determinants and E_loc are formed again from them, and every walker
+ *   whose two energies differ by more than tau, or not finitely, is
+ *   evaluated again in float64 and returned with its float64 E_loc, ln|psi|,
+ *   sign and status.  Each guarded chunk reads one count back to the host
+ *   (the call then synchronises its stream once per chunk).  Measured on
+ *   walkers sampled from |psi|^2 with tau = 2e-5 Ha: 0.2-0.5 % of walkers
+ *   re-evaluated and the largest remaining error below 7e-5 Ha on the
+ *   H10-chain and N2-shaped systems.  pn_guard_count reports how many
+ *   walkers were re-evaluated.
+ * PN_OPT_DET_TABLE (default 1): how the local-energy pass forms the
+ *   determinants' gradients and Laplacians -- 1 by the table method where
+ *   the system allows it (every determinant reached from determinant 0 by
+ *   at most 4 orbital replacements per spin, at most 8 electrons and 8
+ *   virtual orbitals per spin): det A_p = s_p det A_0 det(T[holes,
+ *   particles]) with T = A_0^-1 A, so that the 3N tangents and the
+ *   Laplacian of all determinants follow from those of determinant 0 and of
+ *   T; a walker whose determinant-0 block has a pivot ratio beyond 1e4 is
+ *   computed block by block; 0 block by block for every walker; 2 the table
+ *   kernel with every walker on its block-by-block path (a test of that
+ *   path). */
+enum { PN_OPT_FUSED_SAMPLER = 1, PN_OPT_TENSOR_CORES = 2, PN_OPT_DRIFT = 3, PN_OPT_GUARD = 4, PN_OPT_DET_TABLE = 5 };
 int pn_set_option(pn_system_t sys, int option, int value);
+
+/* Walkers the local-energy guard (PN_OPT_GUARD) re-evaluated in float64
+ * since the last call, summed over calls; resets the count.  Synchronises
+ * the device.  0 for PN_FP64 handles. */
+int pn_guard_count(pn_system_t sys, int64_t* n);
 
 /* Synchronises the device and reports whether any of the handle's kernels
  * gave up a bounded wait since the last check (PN_ETIMEOUT; the affected
@@ -304,7 +337,10 @@ int pn_clip_local_energy(const double* eloc, int W, double q, double* out,
 /* ---------------------------------------------------------------------
  * Serving loop: a persistent host thread that admits jobs by device-memory
  * footprint as slots free up and runs admitted jobs concurrently on
- * separate streams (continuous batching across molecules).
+ * separate streams, one host thread per slot (continuous batching across
+ * molecules).  Mixed jobs' local energies carry the guard of PN_OPT_GUARD
+ * with the system handle's tau (their footprint includes its float64
+ * workspace).
  */
 typedef struct pn_server_s* pn_server_t;
 
@@ -359,6 +395,11 @@ typedef struct pn_result {
   int64_t n_nonfinite;   /* walkers with status != PN_WALKER_OK        */
   double queue_ms;       /* submit -> admission                         */
   double run_ms;         /* admission -> completion                     */
+  double dev_start_ms;   /* the job's first device work, ms after the   */
+  double dev_end_ms;     /*   server's creation; and its last (CUDA
+                            events on the job's stream; 0 on failure)   */
+  int64_t n_guarded;     /* walkers the mixed local-energy guard
+                            re-evaluated in float64 (PN_OPT_GUARD)      */
 } pn_result;
 
 int pn_server_create(const pn_server_cfg* cfg, pn_server_t* out);
@@ -395,10 +436,22 @@ int pn_test_linear_tc(const float* X, int ldx, const float* W, int ldw,
  *   clears earlier records.
  * pn_profile_read: synchronises those events and returns how many launches
  *   were timed and their summed duration in ms.
+ * pn_profile_work: the algorithmic work of those launches, summed as their
+ *   launch sites report it -- floating-point operations (a multiply-add
+ *   counts 2) for compute kernels, bytes that must cross HBM for the
+ *   message kernels; 0 for kernel classes that report none.
+ * pn_measure_peak: the issue-rate ceiling of a CUDA-core unit on the
+ *   current device, measured by this library's own kernel (eight
+ *   independent multiply-add chains per thread, 8 blocks of 256 threads per
+ *   SM, best of two timed launches after one warm-up): kind 0 float32 FMA,
+ *   1 float64 FMA; *tflops in TFLOP/s.  Synchronises `stream`; changes no
+ *   device setting.
  */
 unsigned long long pn_launch_count(void);
 int pn_profile_kernel(const char* name);
 int pn_profile_read(int64_t* count, double* total_ms);
+int pn_profile_work(double* work);
+int pn_measure_peak(int kind, double* tflops, void* stream);
 
 const char* pn_last_error(void);
 

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpaulinet.so")
 
 PN_FP64, PN_MIXED = 0, 1
 PN_JOB_ELOC, PN_JOB_SWEEP, PN_JOB_SCAN = 0, 1, 2
-PN_OPT_FUSED_SAMPLER, PN_OPT_TENSOR_CORES, PN_OPT_DRIFT = 1, 2, 3
+PN_OPT_FUSED_SAMPLER, PN_OPT_TENSOR_CORES, PN_OPT_DRIFT, PN_OPT_GUARD, PN_OPT_DET_TABLE = 1, 2, 3, 4, 5
 ERRORS = {0: "PN_OK", 1: "PN_EINVAL", 2: "PN_ENOMEM", 3: "PN_EBUDGET", 4: "PN_ENOTREADY",
           5: "PN_ETIMEOUT", 6: "PN_EDEVICE", 7: "PN_ECANCELLED"}
 
@@ -60,7 +60,8 @@ class Job(C.Structure):
 class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("W", C.c_int), ("e_mean", C.c_double), ("e_stderr", C.c_double),
                 ("accept_rate", C.c_double), ("n_nonfinite", C.c_int64), ("queue_ms", C.c_double),
-                ("run_ms", C.c_double)]
+                ("run_ms", C.c_double), ("dev_start_ms", C.c_double), ("dev_end_ms", C.c_double),
+                ("n_guarded", C.c_int64)]
 
 
 EXPORTS = {
@@ -96,11 +97,14 @@ EXPORTS = {
     "pn_job_footprint": (C.c_size_t, [C.c_void_p, C.c_int, C.c_int]),
     "pn_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "pn_device_status": (C.c_int, [C.c_void_p]),
+    "pn_guard_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "pn_test_linear_tc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                     C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "pn_launch_count": (C.c_ulonglong, []),
     "pn_profile_kernel": (C.c_int, [C.c_char_p]),
     "pn_profile_read": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "pn_profile_work": (C.c_int, [C.POINTER(C.c_double)]),
+    "pn_measure_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "pn_last_error": (C.c_char_p, []),
 }
 
@@ -266,6 +270,13 @@ class System:
     def set_option(self, option, value):
         check(load().pn_set_option(self.h, int(option), int(value)))
 
+    def guard_count(self):
+        """Walkers the local-energy guard re-evaluated in float64 since the
+        last call (pn_guard_count)."""
+        n = C.c_int64()
+        check(load().pn_guard_count(self.h, C.byref(n)))
+        return n.value
+
     def init_walkers(self, r, seed):
         check(load().pn_init_walkers(self.h, _ptr(r), r.shape[0], int(seed), _stream(r)))
 
@@ -330,6 +341,27 @@ def adamw_step(theta, grad, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, weigh
 
 def clip_local_energy(eloc, out, cot=None, q=5.0):
     check(load().pn_clip_local_energy(_ptr(eloc), eloc.shape[0], float(q), _ptr(out), _ptr(cot), _stream(eloc)))
+
+
+def measure_peak(kind):
+    """TFLOP/s of the float32 (kind 0) or float64 (kind 1) FMA pipe, from the
+    library's own microbenchmark kernel (pn_measure_peak)."""
+    v = C.c_double()
+    check(load().pn_measure_peak(int(kind), C.byref(v), _stream()))
+    return v.value
+
+
+def profile(name):
+    """Start (name) or stop (None) CUDA-event timing of one kernel class."""
+    check(load().pn_profile_kernel(name.encode() if name else None))
+
+
+def profile_read():
+    """(launches, total ms, algorithmic work) of the timed kernel class."""
+    n, ms, wk = C.c_int64(), C.c_double(), C.c_double()
+    check(load().pn_profile_read(C.byref(n), C.byref(ms)))
+    check(load().pn_profile_work(C.byref(wk)))
+    return n.value, ms.value, wk.value
 
 
 def num_params_for(D, Zd, K, L, M, n_orb):

@@ -168,6 +168,45 @@ __global__ void k_init_walkers(DevSys s, const int* __restrict__ nuc, double* __
   }
 }
 
+// ------------------------------------------------------------------ guard
+// Walkers of a mixed chunk whose two evaluations differ by more than tau
+// (or give a non-finite difference) go to the list; singular walkers are
+// left alone (their E_loc is undefined in any precision).
+__global__ void k_guard_flag(const double* __restrict__ e1, const double* __restrict__ e2,
+                             const int* __restrict__ status, int Wn, double tau, int* __restrict__ list,
+                             int* __restrict__ count) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= Wn) return;
+  if (status[w] == PN_WALKER_SINGULAR) return;
+  if (!(fabs(e1[w] - e2[w]) <= tau)) list[atomicAdd(count, 1)] = w;
+}
+
+// Positions of flagged walkers k0 .. k0 + n - 1 into the float64 workspace.
+__global__ void k_guard_gather(const double* __restrict__ r, const int* __restrict__ list, int k0, int n, int N,
+                               double* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n * 3 * N) return;
+  const int k = q / (3 * N), m = q - k * 3 * N;
+  out[q] = r[(size_t)list[k0 + k] * 3 * N + m];
+}
+
+// Float64 results of the flagged walkers back into the chunk's outputs.
+__global__ void k_guard_scatter(const int* __restrict__ list, int k0, int n, int N, const double* __restrict__ e64,
+                                const double* __restrict__ l64, const double* __restrict__ s64,
+                                const int* __restrict__ st64, const double* __restrict__ g64, double* __restrict__ e,
+                                double* __restrict__ l, double* __restrict__ sg, int* __restrict__ st,
+                                double* __restrict__ g, int64_t* __restrict__ n_total) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int w = list[k0 + k];
+  e[w] = e64[k];
+  l[w] = l64[k];
+  sg[w] = s64[k];
+  st[w] = st64[k];
+  for (int m = 0; m < 3 * N; ++m) g[(size_t)w * 3 * N + m] = g64[(size_t)k * 3 * N + m];
+  if (k == 0) atomicAdd((unsigned long long*)n_total, (unsigned long long)n);
+}
+
 // Value-pass components for step-by-step checks.
 template <typename R>
 __global__ void k_components(DevSys s, const double* __restrict__ phi, const R* __restrict__ F,
@@ -260,7 +299,8 @@ int set_device(pn_system_s* s) {
 template <typename R>
 int eval_impl(pn_system_s* s, const double* r, int W, int jet, double* eloc, double* logabs, double* sign, int* status,
               cudaStream_t st) {
-  return pn_run_eval<R>(s->ds, pn_devnet<R>(s), work_of<R>(s), s->Wc, r, W, jet, eloc, logabs, sign, status, st);
+  const Guard* g = (s->guard_mem && s->guard.tau > 0) ? &s->guard : nullptr;
+  return pn_run_eval<R>(s->ds, pn_devnet<R>(s), work_of<R>(s), s->Wc, r, W, jet, eloc, logabs, sign, status, st, g);
 }
 
 template <typename R>
@@ -312,9 +352,36 @@ int metropolis_impl(pn_system_s* s, double* r, double* logabs, int W, int n_step
 }  // namespace
 
 // ------------------------------------------------------ drivers with explicit workspace
+// The guard of a mixed jet chunk (see Guard): second evaluation of the
+// heads, flags, float64 re-evaluation of the flagged walkers in pieces of
+// g.cap.  Reads the flag count back to the host (one synchronisation).
+static int guard_chunk(const DevSys& ds, const DevNet<float>& net, Work<float>& w, const Guard& g, const double* rc,
+                       int Wn, cudaStream_t st) {
+  const int N = ds.N;
+  if (int e = pn_probe_heads_chunk(ds, net, w, Wn, g.e_probe, st)) return e;
+  PN_CUDA(cudaMemsetAsync(g.count, 0, sizeof(int), st));
+  PN_LAUNCH("k_guard_flag", st, k_guard_flag<<<nblk(Wn, 128), 128, 0, st>>>(w.out_eloc, g.e_probe, w.out_status, Wn,
+                                                                            g.tau, g.list, g.count));
+  int nflag = 0;
+  PN_CUDA(cudaMemcpyAsync(&nflag, g.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PN_CUDA(cudaStreamSynchronize(st));
+  Work<double> w64 = g.w64;
+  for (int k0 = 0; k0 < nflag; k0 += g.cap) {
+    const int n = std::min(g.cap, nflag - k0);
+    PN_LAUNCH("k_guard_gather", st, k_guard_gather<<<nblk((size_t)n * 3 * N, 128), 128, 0, st>>>(rc, g.list, k0, n, N,
+                                                                                                  w64.r));
+    if (int e = pn_forward_chunk<double>(ds, g.net64, w64, w64.r, n, 1, st)) return e;
+    PN_LAUNCH("k_guard_scatter", st,
+              k_guard_scatter<<<nblk(n, 64), 64, 0, st>>>(g.list, k0, n, N, w64.out_eloc, w64.out_logabs, w64.out_sign,
+                                                           w64.out_status, w64.out_grad, w.out_eloc, w.out_logabs,
+                                                           w.out_sign, w.out_status, w.out_grad, g.n_total));
+  }
+  return PN_OK;
+}
+
 template <typename R>
 int pn_run_eval(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, const double* r, int W, int jet,
-                double* eloc, double* logabs, double* sign, int* status, cudaStream_t st) {
+                double* eloc, double* logabs, double* sign, int* status, cudaStream_t st, const Guard* g) {
   const int N = ds.N;
   const bool rdev = pn_is_device_ptr(r);
   const bool sync = !rdev || is_host(eloc) || is_host(logabs) || is_host(sign) || is_host(status);
@@ -326,6 +393,10 @@ int pn_run_eval(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, cons
       rc = w.r;
     }
     if (int e = pn_forward_chunk<R>(ds, net, w, rc, Wn, jet, st)) return e;
+    if constexpr (sizeof(R) == 4) {
+      if (jet && g && g->tau > 0)
+        if (int e = guard_chunk(ds, net, w, *g, rc, Wn, st)) return e;
+    }
     if (eloc && jet) PN_CUDA(cudaMemcpyAsync(eloc + c0, w.out_eloc, Wn * 8, cudaMemcpyDefault, st));
     if (logabs) PN_CUDA(cudaMemcpyAsync(logabs + c0, w.out_logabs, Wn * 8, cudaMemcpyDefault, st));
     if (sign) PN_CUDA(cudaMemcpyAsync(sign + c0, w.out_sign, Wn * 8, cudaMemcpyDefault, st));
@@ -335,9 +406,9 @@ int pn_run_eval(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, cons
   return PN_OK;
 }
 template int pn_run_eval<double>(const DevSys&, const DevNet<double>&, Work<double>&, int, const double*, int, int,
-                                 double*, double*, double*, int*, cudaStream_t);
+                                 double*, double*, double*, int*, cudaStream_t, const Guard*);
 template int pn_run_eval<float>(const DevSys&, const DevNet<float>&, Work<float>&, int, const double*, int, int,
-                                double*, double*, double*, int*, cudaStream_t);
+                                double*, double*, double*, int*, cudaStream_t, const Guard*);
 
 template <typename R>
 int pn_run_metropolis(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, double* r, double* logabs, int W,
@@ -639,6 +710,15 @@ extern "C" int pn_set_option(pn_system_t s, int option, int value) {
       if (value < 0 || value > 1) { pn_set_error("drift option takes 0 (jet pass) or 1 (reverse mode)"); return PN_EINVAL; }
       s->drift_mode = value;
       return PN_OK;
+    case PN_OPT_GUARD:
+      if (value < 0) { pn_set_error("guard option takes tau in micro-hartree, 0 = off"); return PN_EINVAL; }
+      if (value > 0 && !s->guard_mem) { pn_set_error("the local-energy guard exists for PN_MIXED handles only"); return PN_EINVAL; }
+      s->guard.tau = value * 1e-6;
+      return PN_OK;
+    case PN_OPT_DET_TABLE:
+      if (value < 0 || value > 2) { pn_set_error("determinant option takes 0..2"); return PN_EINVAL; }
+      s->ds.no_table = value == 1 ? 0 : (value == 0 ? 1 : 2);
+      return PN_OK;
     case PN_OPT_TENSOR_CORES:
       if (value < 0 || value > 7) { pn_set_error("tensor-core option takes a mask 0..7"); return PN_EINVAL; }
       s->ds.tensor_cores = value;
@@ -690,5 +770,16 @@ extern "C" int pn_clip_local_energy(const double* eloc, int W, double q, double*
     PN_CUDA(cudaFreeAsync(tmp, st));
     PN_CUDA(cudaStreamSynchronize(st));
   }
+  return PN_OK;
+}
+
+extern "C" int pn_guard_count(pn_system_t s, int64_t* n) {
+  if (!s || !n) { pn_set_error("bad arguments"); return PN_EINVAL; }
+  *n = 0;
+  if (!s->guard_mem) return PN_OK;
+  if (int e = set_device(s)) return e;
+  PN_CUDA(cudaDeviceSynchronize());
+  PN_CUDA(cudaMemcpy(n, s->guard.n_total, 8, cudaMemcpyDeviceToHost));
+  PN_CUDA(cudaMemset(s->guard.n_total, 0, 8));
   return PN_OK;
 }

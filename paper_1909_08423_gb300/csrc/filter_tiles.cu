@@ -347,6 +347,7 @@ int max_smem() {
 }
 
 // Launch kern<NJ> for the system's NJ with `bytes` of dynamic shared memory.
+// ft_work (algorithmic FLOPs of the launch) must be in scope.
 #define PN_FT_LAUNCH(NAME, KERN, BYTES_OF, ...)                                                       \
   do {                                                                                               \
     const int nj = nj_of(s);                                                                         \
@@ -359,17 +360,17 @@ int max_smem() {
       case 2:                                                                                        \
         if (bytes > 48 * 1024)                                                                       \
           PN_CUDA(cudaFuncSetAttribute(KERN<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)); \
-        PN_LAUNCH(NAME, st, (KERN<2><<<ft.t0[3], 256, bytes, st>>>(__VA_ARGS__)));                  \
+        PN_LAUNCH_W(NAME, st, ft_work, (KERN<2><<<ft.t0[3], 256, bytes, st>>>(__VA_ARGS__)));                  \
         break;                                                                                       \
       case 4:                                                                                        \
         if (bytes > 48 * 1024)                                                                       \
           PN_CUDA(cudaFuncSetAttribute(KERN<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)); \
-        PN_LAUNCH(NAME, st, (KERN<4><<<ft.t0[3], 256, bytes, st>>>(__VA_ARGS__)));                  \
+        PN_LAUNCH_W(NAME, st, ft_work, (KERN<4><<<ft.t0[3], 256, bytes, st>>>(__VA_ARGS__)));                  \
         break;                                                                                       \
       default:                                                                                       \
         if (bytes > 48 * 1024)                                                                       \
           PN_CUDA(cudaFuncSetAttribute(KERN<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)); \
-        PN_LAUNCH(NAME, st, (KERN<8><<<ft.t0[3], 256, bytes, st>>>(__VA_ARGS__)));                  \
+        PN_LAUNCH_W(NAME, st, ft_work, (KERN<8><<<ft.t0[3], 256, bytes, st>>>(__VA_ARGS__)));                  \
         break;                                                                                       \
     }                                                                                                \
     return PN_OK;                                                                                    \
@@ -380,6 +381,7 @@ int max_smem() {
 int pn_filter_tile_value(const DevSys& s, const DevNet<float>& net, int n, const float* ef, int Wn, float* Ah,
                          float* wv, cudaStream_t st) {
 #define BYTES(LW) ((size_t)s.K * (LW) + (size_t)s.Hw * (LW) + (size_t)s.K * LA + (size_t)(LW) * LA)
+  const double ft_work = 2.0 * Wn * s.Ppair * ((double)s.K * s.Hw + (double)s.Hw * s.Zd);
   PN_FT_LAUNCH("k_filter_tape", k_filter_tile_value, BYTES, s, net, n, ef, Wn, ft, Ah, wv);
 #undef BYTES
 }
@@ -387,6 +389,7 @@ int pn_filter_tile_value(const DevSys& s, const DevNet<float>& net, int n, const
 int pn_filter_tile_jet(const DevSys& s, const DevNet<float>& net, int n, const float* ef, int Wn, float* wj,
                        cudaStream_t st) {
 #define BYTES(LW) ((size_t)s.K * (LW) + (size_t)s.Hw * (LW) + (size_t)3 * s.K * LA + (size_t)3 * (LW) * LA)
+  const double ft_work = 6.0 * Wn * s.Ppair * ((double)s.K * s.Hw + (double)s.Hw * s.Zd);
   PN_FT_LAUNCH("k_filter", k_filter_tile_jet, BYTES, s, net, n, ef, Wn, ft, wj);
 #undef BYTES
 }
@@ -394,6 +397,7 @@ int pn_filter_tile_jet(const DevSys& s, const DevNet<float>& net, int n, const f
 int pn_filter_tile_bwd(const DevSys& s, const DevNet<float>& net, int n, const float* Ah, const float* dw, int Wn,
                        float* dAh, float* Sh, cudaStream_t st) {
 #define BYTES(LW) ((size_t)s.Zd * (LW) + (size_t)s.Zd * LA)
+  const double ft_work = 0;  // not reported
   PN_FT_LAUNCH("k_filter_bwd", k_filter_tile_bwd, BYTES, s, net, n, Ah, dw, Wn, ft, dAh, Sh);
 #undef BYTES
 }
@@ -401,6 +405,7 @@ int pn_filter_tile_bwd(const DevSys& s, const DevNet<float>& net, int n, const f
 int pn_filter_tile_dist(const DevSys& s, const DevNet<float>& net, int n, const float* Ah, const float* ef,
                         const float* dw, int Wn, double* dd, cudaStream_t st) {
 #define BYTES(LW) ((size_t)s.Zd * (LW) + (size_t)s.K * (LW) + (size_t)s.Zd * LA + (size_t)s.K * LA)
+  const double ft_work = 0;  // not reported
   PN_FT_LAUNCH("k_filter_bwd_dist", k_filter_tile_dist, BYTES, s, net, n, Ah, ef, dw, Wn, ft, dd);
 #undef BYTES
 }

@@ -10,6 +10,7 @@
 #include <algorithm>
 
 #include "ansatz_dev.cuh"
+#include "slater_dev.cuh"
 #include "kernels.cuh"
 #include "pn_internal.cuh"
 
@@ -652,10 +653,8 @@ __global__ void k_sum_electrons(const R* __restrict__ X, R* __restrict__ Xs, int
 }
 
 // ----------------------------------------------------------- determinants
-// One thread per (walker, determinant, spin).  A[a][b] = phi~(e0 + a, occ_b),
-// LU with partial pivoting; jet mode adds grad_t ln|det| = tr(A^-1 dA_t) and
-// lap ln|det| = tr(A^-1 lap A) - sum_t tr((A^-1 dA_t)^2).
-// det[w][p][s] = {ln|det|, sign, lap, grad[3N]}.
+// One thread per (walker, determinant, spin): the block computed directly
+// (pn_slater_block).  det[w][p][s] = {ln|det|, sign, lap, grad[3N]}.
 template <typename R>
 __global__ void k_slater(DevSys s, const double* __restrict__ phi, const R* __restrict__ F, int Wn, int T, int jet,
                          double* __restrict__ det) {
@@ -665,121 +664,8 @@ __global__ void k_slater(DevSys s, const double* __restrict__ phi, const R* __re
   const int p = (idx >> 1) % s.n_det;
   const int w = (idx >> 1) / s.n_det;
   const int N = s.N, no = s.n_orb;
-  const int ns = sg ? s.n_dn : s.n_up;
-  const int e0 = sg ? s.n_up : 0;
-  const int stride = 3 + 3 * N;
-  double* out = det + (size_t)idx * stride;
-  if (ns == 0) {
-    out[0] = 0; out[1] = 1; out[2] = 0;
-    if (jet) for (int t = 0; t < 3 * N; ++t) out[3 + t] = 0;
-    return;
-  }
-  const int* occ = s.occ + p * N + e0;
-  constexpr int NS = PN_MAX_SPIN;
-  double LU[NS * NS];
-  int perm[NS];
-  const double* phw = phi + (size_t)w * N * no * 5;
-  const R* Fw = F + (size_t)w * N * T * no;
-  for (int a = 0; a < ns; ++a)
-    for (int b = 0; b < ns; ++b) {
-      const int i = e0 + a, mu = occ[b];
-      LU[a * ns + b] = phw[(i * no + mu) * 5] * (1.0 + (double)Fw[(size_t)i * T * no + mu]);
-    }
-  double ld = 0, sign = 1;
-  bool sing = false;
-  for (int c = 0; c < ns; ++c) perm[c] = c;
-  for (int c = 0; c < ns; ++c) {
-    int best = c;
-    double bv = fabs(LU[c * ns + c]);
-    for (int rr = c + 1; rr < ns; ++rr) {
-      const double v = fabs(LU[rr * ns + c]);
-      if (v > bv) { bv = v; best = rr; }
-    }
-    if (!(bv > 0.0)) { sing = true; break; }
-    if (best != c) {
-      for (int k = 0; k < ns; ++k) {
-        const double t0 = LU[c * ns + k];
-        LU[c * ns + k] = LU[best * ns + k];
-        LU[best * ns + k] = t0;
-      }
-      const int tp = perm[c]; perm[c] = perm[best]; perm[best] = tp;
-      sign = -sign;
-    }
-    const double piv = LU[c * ns + c];
-    if (piv < 0) sign = -sign;
-    ld += log(fabs(piv));
-    for (int rr = c + 1; rr < ns; ++rr) {
-      const double f = LU[rr * ns + c] / piv;
-      LU[rr * ns + c] = f;
-      for (int k = c + 1; k < ns; ++k) LU[rr * ns + k] -= f * LU[c * ns + k];
-    }
-  }
-  if (sing) {
-    out[0] = -INFINITY; out[1] = 0; out[2] = 0;
-    if (jet) for (int t = 0; t < 3 * N; ++t) out[3 + t] = 0;
-    return;
-  }
-  out[0] = ld;
-  out[1] = sign;
-  if (!jet) return;
-  // inverse: solve A X = I with the factors (P A = L U)
-  double Ai[NS * NS];
-  for (int col = 0; col < ns; ++col) {
-    double y[NS];
-    for (int rr = 0; rr < ns; ++rr) {
-      double v = (perm[rr] == col) ? 1.0 : 0.0;
-      for (int k = 0; k < rr; ++k) v -= LU[rr * ns + k] * y[k];
-      y[rr] = v;
-    }
-    for (int rr = ns - 1; rr >= 0; --rr) {
-      double v = y[rr];
-      for (int k = rr + 1; k < ns; ++k) v -= LU[rr * ns + k] * y[k];
-      y[rr] = v / LU[rr * ns + rr];
-    }
-    for (int rr = 0; rr < ns; ++rr) Ai[rr * ns + col] = y[rr];
-  }
-  const int lap = T - 1;
-  // tr(A^-1 lap A)
-  double trl = 0;
-  for (int a = 0; a < ns; ++a)
-    for (int b = 0; b < ns; ++b) {
-      const int i = e0 + a, mu = occ[b];
-      const double* ph = phw + (i * no + mu) * 5;
-      const R* f = Fw + (size_t)i * T * no + mu;
-      const double f0 = 1.0 + (double)f[0];
-      double l = ph[4] * f0 + ph[0] * (double)f[(size_t)lap * no];
-      for (int x = 0; x < 3; ++x) l += 2.0 * ph[1 + x] * (double)f[(size_t)(1 + 3 * i + x) * no];
-      trl += Ai[b * ns + a] * l;
-    }
-  double lsum = trl;
-  for (int t = 1; t < lap; ++t) {
-    const int tk = (t - 1) / 3, ta = (t - 1) % 3;
-    double dA[NS * NS];
-    for (int a = 0; a < ns; ++a)
-      for (int b = 0; b < ns; ++b) {
-        const int i = e0 + a, mu = occ[b];
-        const double* ph = phw + (i * no + mu) * 5;
-        const R* f = Fw + (size_t)i * T * no + mu;
-        double v = ph[0] * (double)f[(size_t)t * no];
-        if (tk == i) v += ph[1 + ta] * (1.0 + (double)f[0]);
-        dA[a * ns + b] = v;
-      }
-    double B[NS * NS];
-    double tr = 0;
-    for (int a = 0; a < ns; ++a)
-      for (int b = 0; b < ns; ++b) {
-        double v = 0;
-        for (int c = 0; c < ns; ++c) v += Ai[a * ns + c] * dA[c * ns + b];
-        B[a * ns + b] = v;
-        if (a == b) tr += v;
-      }
-    double tr2 = 0;
-    for (int a = 0; a < ns; ++a)
-      for (int b = 0; b < ns; ++b) tr2 += B[a * ns + b] * B[b * ns + a];
-    out[3 + t - 1] = tr;
-    lsum -= tr2;
-  }
-  out[2] = lsum;
+  pn_slater_block<R, PN_MAX_SPIN>(s, phi + (size_t)w * N * no * 5, F + (size_t)w * N * T * no, p, sg, T, jet,
+                                  det + (size_t)idx * (3 + 3 * N));
 }
 
 // ------------------------------------------------------------ combination
@@ -896,11 +782,11 @@ static int linear_v4_launch(const float* xf, int ldx, const float* wf, int ldw, 
   do {                                                                                                        \
     dim3 grid((rows + BM - 1) / BM, (Nout + BN - 1) / BN);                                                    \
     if (vw && vy)                                                                                             \
-      PN_LAUNCH(kname, st, (k_linear_v4<BM, BN, TN, true, true, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));   \
+      PN_LAUNCH_W(kname, st, 2.0 * rows * Kd * Nout, (k_linear_v4<BM, BN, TN, true, true, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));   \
     else if (vy)                                                                                              \
-      PN_LAUNCH(kname, st, (k_linear_v4<BM, BN, TN, false, true, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));  \
+      PN_LAUNCH_W(kname, st, 2.0 * rows * Kd * Nout, (k_linear_v4<BM, BN, TN, false, true, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));  \
     else                                                                                                      \
-      PN_LAUNCH(kname, st, (k_linear_v4<BM, BN, TN, false, false, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc))); \
+      PN_LAUNCH_W(kname, st, 2.0 * rows * Kd * Nout, (k_linear_v4<BM, BN, TN, false, false, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc))); \
   } while (0)
   if (Nout <= 32) PN_LIN(256, 32, 4);  // narrow maps
   else if (Nout <= 64) PN_LIN(128, 64, 4);
@@ -942,7 +828,7 @@ int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw
     }
   }
   dim3 grid((rows + 63) / 64, (Nout + 63) / 64);
-  PN_LAUNCH("k_linear", st, k_linear<R><<<grid, 256, 0, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, Kd, Nout, T, acc));
+  PN_LAUNCH_W("k_linear", st, 2.0 * rows * Kd * Nout, k_linear<R><<<grid, 256, 0, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, Kd, Nout, T, acc));
   return PN_OK;
 }
 template int pn_linear<double>(const DevSys*, int, const double*, int, const double*, int, const double*, double*, int,
@@ -975,12 +861,16 @@ int pn_network_layers(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn,
         fe = pn_filter_tile_jet(s, net, n, (const float*)w.efeat, Wn, (float*)w.wjet, st);
     if (fe != PN_OK && fe != PN_ENOTREADY) return fe;
     if (fe == PN_ENOTREADY)
-      PN_LAUNCH("k_filter", st, k_filter<R><<<nblk((size_t)Wn * s.Ppair, FW), FW * 32, 0, st>>>(s, net, n, w.efeat, Wn, jet, w.wjet));
+      PN_LAUNCH_W("k_filter", st, 2.0 * (jet ? 3 : 1) * Wn * s.Ppair * (double)(s.K * s.Hw + s.Hw * s.Zd),
+                  k_filter<R><<<nblk((size_t)Wn * s.Ppair, FW), FW * 32, 0, st>>>(s, net, n, w.efeat, Wn, jet, w.wjet));
     if (jet) {
       const size_t nthr = (size_t)Wn * ((s.N + MSG_KC - 1) / MSG_KC + 1) * s.N * s.Zd;
-      PN_LAUNCH("k_message", st,
-                k_message_c<R><<<nblk(nthr, 256), 256, 0, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H, w.ldH, Wn,
-                                                                 T, w.Zb, w.ldZ));
+      // bytes that must cross HBM: the h rows and filter jets read once,
+      // the message rows written once
+      const double bytes = (double)sizeof(R) * Wn * ((double)s.N * T * s.Zd + 3.0 * s.Ppair * s.Zd + 3.0 * s.N * T * s.Zd);
+      PN_LAUNCH_W("k_message", st, bytes,
+                  k_message_c<R><<<nblk(nthr, 256), 256, 0, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H, w.ldH, Wn,
+                                                                   T, w.Zb, w.ldZ));
     } else {
       PN_LAUNCH("k_message", st,
                 k_message<R><<<(unsigned)((size_t)Wn * s.N), std::min(256, (T * s.Zd + 31) / 32 * 32),
@@ -1018,6 +908,35 @@ int pn_heads(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn, int T, c
   return PN_OK;
 }
 
+// Algorithmic float64 work of the determinants of one walker: per
+// (determinant, spin) block of size n the LU (2/3 n^3 multiply-adds); in jet
+// mode also the inverse (n^3), tr(A^-1 lap A) (n^2) and, per coordinate t,
+// A^-1 dA_t (n^3) and tr((A^-1 dA_t)^2) (n^2).
+static double pn_slater_flops(const DevSys& s, int jet) {
+  double f = 0;
+  for (int sg = 0; sg < 2; ++sg) {
+    const double n = sg ? s.n_dn : s.n_up;
+    if (n == 0) continue;
+    f += 2.0 * (2.0 / 3.0) * n * n * n;
+    if (jet) f += 2.0 * (n * n * n + n * n + 3.0 * s.N * (n * n * n + n * n));
+  }
+  return f * s.n_det;
+}
+
+// Determinant blocks: the table kernel for jet passes where the system has
+// a table, else one thread per block.
+template <typename R>
+static int pn_slater(const DevSys& s, const double* phi, const R* F, int Wn, int T, int jet, double* det,
+                     cudaStream_t st) {
+  if (jet && !s.no_table) {
+    const int e = pn_slater_table_launch<R>(s, phi, F, Wn, T, det, st);
+    if (e != PN_ENOTREADY) return e;
+  }
+  PN_LAUNCH_W("k_slater", st, Wn * pn_slater_flops(s, jet),
+              k_slater<R><<<nblk((size_t)Wn * s.n_det * 2, 64), 64, 0, st>>>(s, phi, F, Wn, T, jet, det));
+  return PN_OK;
+}
+
 template <typename R>
 int pn_forward_chunk(const DevSys& s, const DevNet<R>& net, Work<R>& w, const double* r, int Wn, int jet,
                      cudaStream_t st) {
@@ -1027,9 +946,27 @@ int pn_forward_chunk(const DevSys& s, const DevNet<R>& net, Work<R>& w, const do
   PN_LAUNCH("k_orbitals", st, k_orbitals<<<nblk((size_t)Wn * s.N, 64), 64, 0, st>>>(s, r, Wn, w.phi));
   if (int e = pn_network_layers<R>(s, net, w, Wn, T, jet, st)) return e;
   if (int e = pn_heads<R>(s, net, w, Wn, T, st)) return e;
-  PN_LAUNCH("k_slater", st, k_slater<R><<<nblk((size_t)Wn * s.n_det * 2, 64), 64, 0, st>>>(s, w.phi, w.F, Wn, T, jet, w.det));
+  if (int e = pn_slater<R>(s, w.phi, w.F, Wn, T, jet, w.det, st)) return e;
   PN_LAUNCH("k_combine", st, k_combine<R><<<nblk(Wn, 64), 64, 0, st>>>(s, w.geo, w.det, w.Jj, Wn, T, jet, w.out_logabs, w.out_sign, w.out_eloc,
                                             w.out_status, w.out_grad));
+  return PN_OK;
+}
+
+// Second evaluation of a guarded mixed chunk: the heads again with the
+// other unit for their linear maps (their rounding differs), the
+// determinants of the new backflow, and E_loc with the new Jastrow factor.
+// ln|psi| and sign of this pass go to scratch (the proposal buffers), E_loc
+// to e_probe; the first pass's outputs stay in w.
+int pn_probe_heads_chunk(const DevSys& s, const DevNet<float>& net, Work<float>& w, int Wn, double* e_probe,
+                         cudaStream_t st) {
+  if (Wn <= 0) return PN_OK;
+  const int T = 3 * s.N + 2;
+  DevSys s2 = s;
+  s2.tensor_cores ^= PN_TC_HEADS;
+  if (int e = pn_heads<float>(s2, net, w, Wn, T, st)) return e;
+  if (int e = pn_slater<float>(s, w.phi, w.F, Wn, T, 1, w.det, st)) return e;
+  PN_LAUNCH("k_combine", st, k_combine<float><<<nblk(Wn, 64), 64, 0, st>>>(s, w.geo, w.det, w.Jj, Wn, T, 1, w.lp_prop,
+                                                                          w.r_prop, e_probe, nullptr, nullptr));
   return PN_OK;
 }
 

@@ -47,6 +47,18 @@ __device__ inline void pn_normals4(unsigned long long seed, unsigned walker, uns
   }
 }
 
+// Algorithmic float32/float64 network work of one value pass of one walker
+// (multiply-add = 2): the filter networks of every pair and layer, the maps
+// h (none in the first layer, whose input is the one shared embedding) and
+// the stacked receiving maps, the messages, and both heads.
+inline double pn_value_pass_flops(const DevSys& s) {
+  const double N = s.N, M = s.M, D = s.D, Zd = s.Zd, K = s.K, Hw = s.Hw, L = s.L, P = s.Ppair;
+  const double filt = L * P * 2.0 * (K * Hw + Hw * Zd);
+  const double lin = N * 2.0 * ((L - 1) * D * Zd + L * 3.0 * Zd * D + 2.0 * D * D + D * s.n_orb) + 2.0 * (2.0 * D * D + D);
+  const double msg = L * N * Zd * (N - 1 + M) * 2.0;
+  return filt + lin + msg;
+}
+
 int pn_launch_geometry_orbitals(const DevSys& s, const double* r, int Wn, double* geo, double* phi, cudaStream_t st);
 // deriv = 1 also writes the first and second distance derivatives of the features
 template <typename R>

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -25,16 +26,34 @@ void pn_set_error(const char* fmt, ...);
   } while (0)
 
 // Launch bookkeeping (profile.cu): count, and optional event timing of one
-// kernel class.  PN_LAUNCH(name, stream, launch-expression).
+// kernel class.  PN_LAUNCH(name, stream, launch-expression).  Every launch
+// also sits in an NVTX range named by its class (a no-op unless a tool that
+// records NVTX is attached).
 void pn_prof_begin(const char* name, cudaStream_t st);
 void pn_note_launch(const char* name, cudaStream_t st);
+// Algorithmic work of the launch just made (FLOPs, or bytes for kernels
+// bound by memory traffic), summed while `name` is the timed class.
+void pn_prof_work(const char* name, double work);
 #define PN_CHECK_LAUNCH() PN_CUDA(cudaGetLastError())
 #define PN_LAUNCH(name, st, ...)        \
   do {                                  \
+    nvtxRangePushA(name);               \
     pn_prof_begin(name, st);            \
     __VA_ARGS__;                        \
     pn_note_launch(name, st);           \
+    nvtxRangePop();                     \
     PN_CHECK_LAUNCH();                  \
+  } while (0)
+// The same with the launch's algorithmic work (see pn_prof_work).
+#define PN_LAUNCH_W(name, st, work, ...) \
+  do {                                   \
+    nvtxRangePushA(name);                \
+    pn_prof_begin(name, st);             \
+    __VA_ARGS__;                         \
+    pn_note_launch(name, st);            \
+    pn_prof_work(name, (double)(work));  \
+    nvtxRangePop();                      \
+    PN_CHECK_LAUNCH();                   \
   } while (0)
 
 // ------------------------------------------------------------- parameters
@@ -94,10 +113,36 @@ struct DevSys {
   const int* ch_pairs;    // [Ppair] pair indices grouped by filter channel
   int ch_off[4];          // channel c owns ch_pairs[ch_off[c] .. ch_off[c+1])
   const int* ch_pos;      // [Ppair] position of each pair inside its channel's list
+  // Table of the determinant expansion relative to determinant 0 (jet
+  // determinants by the table method, slater_table.cu); null when a
+  // determinant is not reachable from determinant 0 by at most
+  // PN_TAB_KMAX replacements or a block exceeds PN_TAB_NMAX / PN_TAB_VMAX.
+  // Layout: per spin {n_virt, virtual orbitals [PN_MAX_ORBITALS]}, then per
+  // (determinant, spin) a record {k, sign, holes[KMAX], particles[KMAX]}
+  // (holes: positions in determinant 0's list; particles: indices into the
+  // spin's virtual orbitals).
+  const int* xtab;
+  int tab_wstride;        // doubles of shared memory per warp of the table kernel
+  int tab_nv[2];          // virtual orbitals per spin
+  int tab_k3[2];          // sum over determinants of k^3 per spin
+  int no_table;           // 1: jet determinants block by block even where a table exists;
+                          // 2: the table kernel with every walker on its direct fallback
   int fused_sampler;      // 1: Metropolis through the fused tile kernel when it fits
   int tensor_cores;       // 1: float32 linear layers on tcgen05 (split tf32)
   int* dev_err;           // device word: set when a bounded wait expired
 };
+
+#define PN_TAB_NMAX 8
+#define PN_TAB_VMAX 8
+#define PN_TAB_KMAX 4
+#define PN_TAB_REC (2 + 2 * PN_TAB_KMAX)
+
+// Jet determinants by the table method (slater_table.cu): PN_ENOTREADY when
+// the system has no table or the warp's matrices do not fit.
+template <typename R>
+int pn_slater_table_launch(const DevSys& s, const double* phi, const R* F, int Wn, int T, double* det,
+                           cudaStream_t st);
+double pn_slater_table_flops(const DevSys& s);
 
 // Pair indexing: unordered electron pair (a<b) -> a*N - a*(a+1)/2 + (b-a-1)
 __host__ __device__ inline int pn_pair_index(int a, int b, int N) {
@@ -181,8 +226,33 @@ struct DevNet {
   int tc_n, tc_max_bytes;        // host copies of its size fields
 };
 
+// Guard of the mixed-precision local energy.  The float32 network's
+// rounding reaches E_loc through the determinants and the squared gradient,
+// and a few walkers per ten thousand amplify it beyond 1e-4 Ha; no cheap
+// per-walker quantity predicts which.  So every mixed jet chunk is
+// evaluated twice: the heads run again on the other unit (tensor cores
+// instead of CUDA cores or back), which changes their rounding, and the
+// determinants and E_loc are formed from the second heads.  Walkers whose two
+// energies differ by more than tau (or are not finite) are evaluated again
+// in float64 and take the float64 results.  The float64 pass runs on its own
+// workspace of `cap` walkers.
+struct Guard {
+  double tau;            // hartree; <= 0 turns the guard off
+  int cap;               // walkers per float64 re-evaluation
+  Work<double> w64;      // float64 jet workspace for cap walkers
+  DevNet<double> net64;  // float64 parameters of the same system
+  double* e_probe;       // [Wc] E_loc of the second evaluation
+  int* list;             // [Wc] flagged walkers of the chunk
+  int* count;            // [2] device: flagged walkers, walkers re-evaluated so far
+  int64_t* n_total;      // [1] device: walkers re-evaluated since the last read
+};
+size_t pn_guard_bytes(const DevSys& s, int Wc, int cap);
+Guard pn_carve_guard(const DevSys& s, int Wc, int cap, void* base);
+
 struct pn_system_s {
   DevSys ds;
+  Guard guard;              // mixed handles: local-energy guard (tau 0: off)
+  void* guard_mem;
   NetOff off;
   int precision;
   int no_jastrow, no_backflow;  // ablation variants: head removed
@@ -232,11 +302,19 @@ bool pn_tc_supported(int Nout);
 int pn_linear_tc(const float* X, int ldx, const float* W, int ldw, const float* b, float* Y, int ldy, int rows, int K,
                  int Nout, int T, int acc, int* err, cudaStream_t st);
 
+
 // Chunked drivers over an explicit workspace (used by the C ABI with the
 // handle's workspace and by the serving loop with per-job workspaces).
+// g (mixed jet passes only; may be null) guards the local energies.
 template <typename R>
 int pn_run_eval(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, const double* r, int W, int jet,
-                double* eloc, double* logabs, double* sign, int* status, cudaStream_t st);
+                double* eloc, double* logabs, double* sign, int* status, cudaStream_t st,
+                const Guard* g = nullptr);
+// The second evaluation of a guarded chunk: heads on the other unit,
+// determinants, E_loc into e_probe (w.X, w.phi and w.geo hold the chunk's
+// first pass; w's other outputs are left as the first pass wrote them).
+int pn_probe_heads_chunk(const DevSys& s, const DevNet<float>& net, Work<float>& w, int Wn, double* e_probe,
+                         cudaStream_t st);
 template <typename R>
 int pn_run_metropolis(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, double* r, double* logabs, int W,
                       int n_steps, double sigma, unsigned long long seed, unsigned long long step0, int64_t* n_accept,

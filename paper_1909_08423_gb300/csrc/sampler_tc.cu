@@ -827,7 +827,7 @@ int pn_run_metropolis_tc(const DevSys& s, const DevNet<float>& net, double* r, d
   const uint32_t cols = 512u;
   PN_CUDA(cudaFuncSetAttribute(k_metropolis_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes));
   const int blocks = (W + WT - 1) / WT;
-  PN_LAUNCH("k_metropolis_tc", st,
+  PN_LAUNCH_W("k_metropolis_tc", st, (double)W * n_steps * pn_value_pass_flops(s),
             k_metropolis_tc<<<blocks, NT, L.bytes, st>>>(s, net, net.tcst, net.tcpack, L, r, lp, W, walker0, n_steps,
                                                          sigma, seed, step0, n_acc, cols));
   return PN_OK;

@@ -1,17 +1,21 @@
 // Serving loop: continuous batching of local-energy and sampling jobs for
 // molecules of different sizes.
 //
-// A host worker thread owns n_slots CUDA streams.  Jobs wait in a queue; a
-// job is admitted as soon as a slot is free and its device footprint fits
-// the remaining memory budget (jobs further back may be admitted past one
-// that does not fit yet).  An admitted job gets its own workspace, taken
-// from the stream-ordered allocator on its slot's stream, and all of its
-// work is enqueued there, so jobs on different slots overlap on the GPU.
-// A job's result depends only on its own inputs, seed and chunk size -- not
-// on which other jobs run beside it -- so a result is bitwise the same
-// alone and in a mix.  Completion is detected by polling CUDA events; every
-// host wait is bounded.
+// A scheduler thread admits queued jobs as soon as a slot is free and the
+// job's device footprint fits the remaining memory budget (jobs further back
+// may be admitted past one that does not fit yet).  Each slot has its own
+// CUDA stream and its own host thread: the slot thread takes the job's
+// workspace from the stream-ordered allocator on the slot's stream, enqueues
+// all of the job's work there, and waits for it, so jobs on different slots
+// overlap on the GPU and a wait inside one job (the mixed local-energy
+// guard reads one count per chunk) holds up no other slot.  A job's result
+// depends only on its own inputs, seed and chunk size -- not on which other
+// jobs run beside it -- so a result is the same alone and in a mix.  Each
+// job's first and last device work is bracketed by CUDA events, reported
+// relative to the server's creation, so that overlap is observable.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <cmath>
@@ -80,9 +84,10 @@ struct JobRec {
 
 struct Slot {
   cudaStream_t st = nullptr;
-  cudaEvent_t done = nullptr;
-  double* stats_host = nullptr;  // pinned [4]
-  std::shared_ptr<JobRec> job;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;  // the job's first and last device work
+  double* stats_host = nullptr;            // pinned [4]
+  std::shared_ptr<JobRec> job;             // assigned by the scheduler, cleared when done
+  std::thread thr;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -92,9 +97,10 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct pn_server_s {
   pn_server_cfg cfg;
   int device = 0;
+  cudaEvent_t t_ref = nullptr;  // recorded at creation: origin of the device times
   std::vector<Slot> slots;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_work, cv_done, cv_slot;
   std::deque<std::shared_ptr<JobRec>> queue;
   std::map<uint64_t, std::shared_ptr<JobRec>> jobs;
   size_t used = 0;
@@ -104,16 +110,22 @@ struct pn_server_s {
   std::thread worker;
 };
 
-static size_t job_bytes(pn_system_t s, int W, int chunk, size_t* work_bytes, int* Wc) {
+// Walkers per float64 re-evaluation of a serving job's local-energy guard.
+constexpr int kGuardCap = 64;
+
+static size_t job_bytes(pn_system_t s, int W, int chunk, size_t* work_bytes, int* Wc, size_t* guard_bytes = nullptr) {
   const DevSys& ds = s->ds;
   const int wc = std::max(1, std::min(W, chunk));
   const int elem = s->precision == PN_FP64 ? 8 : 4;
   const size_t wb = pn_work_bytes(ds, wc, 3 * ds.N + 2, elem);
+  // mixed jobs carry the local-energy guard of their own
+  const size_t gb = s->precision == PN_MIXED ? pn_guard_bytes(ds, wc, std::min(wc, kGuardCap)) : 0;
   if (work_bytes) *work_bytes = wb;
   if (Wc) *Wc = wc;
-  // workspace + positions, ln|psi|, E_loc, status, statistics
-  return align256(wb) + align256((size_t)W * ds.N * 3 * 8) + 2 * align256((size_t)W * 8) + align256((size_t)W * 4) +
-         align256(64) + 4096;
+  if (guard_bytes) *guard_bytes = gb;
+  // workspace + guard + positions, ln|psi|, E_loc, status, statistics
+  return align256(wb) + align256(gb) + align256((size_t)W * ds.N * 3 * 8) + 2 * align256((size_t)W * 8) +
+         align256((size_t)W * 4) + align256(64) + 4096;
 }
 
 extern "C" size_t pn_job_footprint(pn_system_t s, int W, int chunk_walkers) {
@@ -128,13 +140,24 @@ static int launch_job(pn_server_s* srv, Slot& sl, JobRec& j) {
   const DevSys& ds = s->ds;
   const int W = j.job.W;
   cudaStream_t st = sl.st;
-  size_t wb;
+  size_t wb, gb;
   int Wc;
-  const size_t total = job_bytes(s, W, srv->cfg.chunk_walkers, &wb, &Wc);
+  const size_t total = job_bytes(s, W, srv->cfg.chunk_walkers, &wb, &Wc, &gb);
+  PN_CUDA(cudaEventRecord(sl.t0, st));
   PN_CUDA(cudaMallocAsync(&j.mem, total, st));
   char* p = (char*)j.mem;
   Work<R> w = pn_carve_work<R>(ds, Wc, 3 * ds.N + 2, p);
   p += align256(wb);
+  Guard guard{};
+  const Guard* g = nullptr;
+  if (gb) {
+    guard = pn_carve_guard(ds, Wc, std::min(Wc, kGuardCap), p);
+    guard.net64 = pn_devnet<double>(s);
+    guard.tau = s->guard.tau;
+    PN_CUDA(cudaMemsetAsync(guard.n_total, 0, 8, st));
+    if (guard.tau > 0) g = &guard;
+  }
+  p += align256(gb);
   double* r = (double*)p; p += align256((size_t)W * ds.N * 3 * 8);
   double* lp = (double*)p; p += align256((size_t)W * 8);
   double* E = (double*)p; p += align256((size_t)W * 8);
@@ -151,7 +174,7 @@ static int launch_job(pn_server_s* srv, Slot& sl, JobRec& j) {
     if (j.job.eloc_out) PN_CUDA(cudaMemcpyAsync(j.job.eloc_out, E, (size_t)W * 8, cudaMemcpyDefault, st));
     PN_CUDA(cudaFreeAsync(j.mem, st));
     j.mem = nullptr;
-    PN_CUDA(cudaEventRecord(sl.done, st));
+    PN_CUDA(cudaEventRecord(sl.t1, st));
     return PN_OK;
   }
   if (j.job.r_init)
@@ -165,14 +188,15 @@ static int launch_job(pn_server_s* srv, Slot& sl, JobRec& j) {
       return e;
     acc = w.n_acc;
   }
-  if (int e = pn_run_eval<R>(ds, net, w, Wc, r, W, 1, E, nullptr, nullptr, stat, st)) return e;
+  if (int e = pn_run_eval<R>(ds, net, w, Wc, r, W, 1, E, nullptr, nullptr, stat, st, g)) return e;
   PN_LAUNCH("k_job_stats", st, k_job_stats<<<1, 256, 0, st>>>(E, stat, W, acc, stats));
   PN_CUDA(cudaMemcpyAsync(sl.stats_host, stats, 4 * 8, cudaMemcpyDeviceToHost, st));
   if (j.job.eloc_out) PN_CUDA(cudaMemcpyAsync(j.job.eloc_out, E, (size_t)W * 8, cudaMemcpyDefault, st));
   if (j.job.r_out) PN_CUDA(cudaMemcpyAsync(j.job.r_out, r, (size_t)W * ds.N * 3 * 8, cudaMemcpyDefault, st));
+  if (gb) PN_CUDA(cudaMemcpyAsync(&j.res.n_guarded, guard.n_total, 8, cudaMemcpyDeviceToHost, st));
   PN_CUDA(cudaFreeAsync(j.mem, st));
   j.mem = nullptr;
-  PN_CUDA(cudaEventRecord(sl.done, st));
+  PN_CUDA(cudaEventRecord(sl.t1, st));
   return PN_OK;
 }
 
@@ -180,6 +204,7 @@ static double ms_between(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
+// Results of the job on slot sl (called with srv->mu held).
 static void finish(pn_server_s* srv, Slot& sl, int status) {
   JobRec& j = *sl.job;
   j.t_done = Clock::now();
@@ -194,6 +219,13 @@ static void finish(pn_server_s* srv, Slot& sl, int status) {
     j.res.n_nonfinite = (int64_t)j.job.W - (int64_t)n;
     j.res.accept_rate =
         (j.job.kind == PN_JOB_SWEEP && j.job.n_steps > 0) ? h[3] / ((double)j.job.W * j.job.n_steps) : 0.0;
+    float a = 0, b = 0;
+    if (cudaEventElapsedTime(&a, srv->t_ref, sl.t0) == cudaSuccess &&
+        cudaEventElapsedTime(&b, srv->t_ref, sl.t1) == cudaSuccess) {
+      j.res.dev_start_ms = a;
+      j.res.dev_end_ms = b;
+    }
+    cudaGetLastError();
   }
   j.res.queue_ms = ms_between(j.t_submit, j.t_admit);
   j.res.run_ms = ms_between(j.t_admit, j.t_done);
@@ -202,72 +234,92 @@ static void finish(pn_server_s* srv, Slot& sl, int status) {
   sl.job.reset();
 }
 
+// One slot's host thread: launch the assigned job on the slot's stream,
+// wait for it, publish the result.
+static void slot_loop(pn_server_s* srv, int k) {
+  cudaSetDevice(srv->device);
+  Slot& sl = srv->slots[k];
+  std::unique_lock<std::mutex> lk(srv->mu);
+  while (true) {
+    srv->cv_slot.wait_for(lk, std::chrono::milliseconds(20), [&] { return srv->stop || (bool)sl.job; });
+    if (!sl.job) {
+      if (srv->stop) break;
+      continue;
+    }
+    auto j = sl.job;
+    lk.unlock();
+    int rc;
+    char tag[64];
+    snprintf(tag, sizeof tag, "pn_job %llu slot %d", (unsigned long long)j->id, k);
+    nvtxRangePushA(tag);
+    if (j->res.status == PN_EDEVICE) {
+      rc = PN_EDEVICE;  // injected host-side failure: nothing was launched
+    } else {
+      rc = j->sys->precision == PN_FP64 ? launch_job<double>(srv, sl, *j) : launch_job<float>(srv, sl, *j);
+    }
+    if (rc != PN_OK && j->mem) {
+      cudaFreeAsync(j->mem, sl.st);
+      j->mem = nullptr;
+    }
+    const cudaError_t e = cudaStreamSynchronize(sl.st);
+    if (rc == PN_OK && e != cudaSuccess) {
+      rc = PN_EDEVICE;
+      pn_set_error("job stream: %s", cudaGetErrorString(e));
+    }
+    if (rc != PN_OK) {
+      cudaGetLastError();
+      // PN_SERVER_LOG=1: failed jobs' messages on stderr (the message is
+      // thread-local to this slot's thread, so pn_last_error cannot show it)
+      const char* log = getenv("PN_SERVER_LOG");
+      if (log && log[0] == '1')
+        fprintf(stderr, "pn_server: job %llu (slot %d) ended with status %d: %s\n", (unsigned long long)j->id, k, rc,
+                pn_last_error());
+    }
+    nvtxRangePop();
+    lk.lock();
+    finish(srv, sl, rc);
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_all();
+  }
+}
+
+// Admission: first-come order, later jobs may pass one that does not fit
+// yet; a job goes to the first free slot.
 static void worker_loop(pn_server_s* srv) {
   cudaSetDevice(srv->device);
   std::unique_lock<std::mutex> lk(srv->mu);
   while (true) {
-    bool progressed = false;
-    // completions
-    for (auto& sl : srv->slots) {
-      if (!sl.job) continue;
-      const cudaError_t q = cudaEventQuery(sl.done);
-      if (q == cudaSuccess) {
-        finish(srv, sl, PN_OK);
-        progressed = true;
-      } else if (q != cudaErrorNotReady) {
-        cudaGetLastError();
-        finish(srv, sl, PN_EDEVICE);
-        progressed = true;
-      }
-    }
-    if (progressed) srv->cv_done.notify_all();
-    if (srv->stop && srv->queue.empty()) {
-      bool busy = false;
-      for (auto& sl : srv->slots) busy |= (bool)sl.job;
-      if (!busy) break;
-    }
-    // admissions: first-come order, later jobs may pass one that does not fit yet
+    if (srv->stop && srv->queue.empty()) break;
+    bool assigned = false;
+    nvtxRangePushA("pn_server tick");
     if (!srv->stop) {
       for (auto it = srv->queue.begin(); it != srv->queue.end();) {
         Slot* free_slot = nullptr;
-        for (auto& sl : srv->slots)
+        int k = 0;
+        for (auto& sl : srv->slots) {
           if (!sl.job) { free_slot = &sl; break; }
+          ++k;
+        }
         if (!free_slot) break;
         auto j = *it;
         if (srv->used + j->footprint > srv->cfg.hbm_budget_bytes) { ++it; continue; }
         it = srv->queue.erase(it);
         srv->used += j->footprint;
         j->state = RUNNING;
+        j->slot = k;
         j->t_admit = Clock::now();
-        free_slot->job = j;
         ++srv->admitted;
-        int rc;
         if (srv->cfg.debug_fail_nth > 0 && srv->admitted == srv->cfg.debug_fail_nth) {
-          rc = PN_EDEVICE;  // injected host-side failure: nothing was launched
+          j->res.status = PN_EDEVICE;
           pn_set_error("injected failure of admitted job %d", srv->admitted);
-        } else {
-          rc = j->sys->precision == PN_FP64 ? launch_job<double>(srv, *free_slot, *j)
-                                            : launch_job<float>(srv, *free_slot, *j);
         }
-        if (rc != PN_OK) {
-          if (j->mem) {
-            cudaFreeAsync(j->mem, free_slot->st);
-            j->mem = nullptr;
-          }
-          cudaStreamSynchronize(free_slot->st);
-          cudaGetLastError();
-          finish(srv, *free_slot, rc);
-          srv->cv_done.notify_all();
-        }
-        progressed = true;
+        free_slot->job = j;
+        assigned = true;
       }
     }
-    if (!progressed) {
-      bool busy = false;
-      for (auto& sl : srv->slots) busy |= (bool)sl.job;
-      // poll GPU completions every 50 us while jobs run, else sleep until work
-      srv->cv_work.wait_for(lk, busy ? std::chrono::microseconds(50) : std::chrono::milliseconds(20));
-    }
+    nvtxRangePop();
+    if (assigned) srv->cv_slot.notify_all();
+    srv->cv_work.wait_for(lk, std::chrono::milliseconds(20));
   }
 }
 
@@ -279,15 +331,30 @@ extern "C" int pn_server_create(const pn_server_cfg* cfg, pn_server_t* out) {
   auto* srv = new pn_server_s();
   srv->cfg = *cfg;
   cudaGetDevice(&srv->device);
+  // keep the job workspaces freed by finished jobs in the stream-ordered
+  // pool (up to the budget) instead of returning them to the driver at
+  // every synchronisation; a per-process attribute of this device's pool
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, srv->device) == cudaSuccess) {
+    uint64_t thr = cfg->hbm_budget_bytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  if (cudaEventCreate(&srv->t_ref) != cudaSuccess || cudaEventRecord(srv->t_ref, 0) != cudaSuccess ||
+      cudaEventSynchronize(srv->t_ref) != cudaSuccess) {
+    pn_set_error("server: reference event failed");
+    return PN_EDEVICE;
+  }
   srv->slots.resize(cfg->n_slots);
   for (auto& sl : srv->slots) {
     if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&sl.t0) != cudaSuccess || cudaEventCreate(&sl.t1) != cudaSuccess ||
         cudaMallocHost((void**)&sl.stats_host, 4 * 8) != cudaSuccess) {
       pn_set_error("server: stream/event/pinned buffer creation failed");
       return PN_EDEVICE;
     }
   }
+  for (int k = 0; k < cfg->n_slots; ++k) srv->slots[k].thr = std::thread(slot_loop, srv, k);
   srv->worker = std::thread(worker_loop, srv);
   *out = srv;
   return PN_OK;
@@ -306,12 +373,24 @@ extern "C" int pn_server_destroy(pn_server_t srv) {
   }
   srv->cv_work.notify_all();
   srv->worker.join();
+  // the slots finish their running jobs, then see the stop flag
+  while (true) {
+    std::unique_lock<std::mutex> lk(srv->mu);
+    bool busy = false;
+    for (auto& sl : srv->slots) busy |= (bool)sl.job;
+    if (!busy) break;
+    srv->cv_done.wait_for(lk, std::chrono::milliseconds(20));
+  }
+  srv->cv_slot.notify_all();
+  for (auto& sl : srv->slots) sl.thr.join();
   for (auto& sl : srv->slots) {
     cudaStreamSynchronize(sl.st);
-    cudaEventDestroy(sl.done);
+    cudaEventDestroy(sl.t0);
+    cudaEventDestroy(sl.t1);
     cudaStreamDestroy(sl.st);
     cudaFreeHost(sl.stats_host);
   }
+  cudaEventDestroy(srv->t_ref);
   delete srv;
   return PN_OK;
 }

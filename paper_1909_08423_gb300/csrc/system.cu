@@ -191,6 +191,8 @@ void free_all(pn_system_s* s) {
   s->work_mem = nullptr;
   if (s->tape_mem) cudaFree(s->tape_mem);
   s->tape_mem = nullptr;
+  if (s->guard_mem) cudaFree(s->guard_mem);
+  s->guard_mem = nullptr;
 }
 
 }  // namespace
@@ -260,6 +262,30 @@ Work<R> pn_carve_work(const DevSys& s, int Wc, int T, void* base) {
 }
 template Work<double> pn_carve_work<double>(const DevSys&, int, int, void*);
 template Work<float> pn_carve_work<float>(const DevSys&, int, int, void*);
+
+// Guard of the mixed local energy: a float64 jet workspace for cap walkers,
+// then the per-chunk probe energies, flag list and counters.
+size_t pn_guard_bytes(const DevSys& s, int Wc, int cap) {
+  return align_up(pn_work_bytes(s, cap, 3 * s.N + 2, 8)) + align_up((size_t)Wc * 8) + align_up((size_t)Wc * 4) +
+         align_up(2 * sizeof(int)) + align_up(8);
+}
+
+Guard pn_carve_guard(const DevSys& s, int Wc, int cap, void* base) {
+  Guard g;
+  g.tau = 0;
+  g.cap = cap;
+  char* p = (char*)base;
+  g.w64 = pn_carve_work<double>(s, cap, 3 * s.N + 2, p);
+  p += align_up(pn_work_bytes(s, cap, 3 * s.N + 2, 8));
+  g.e_probe = (double*)p;
+  p += align_up((size_t)Wc * 8);
+  g.list = (int*)p;
+  p += align_up((size_t)Wc * 4);
+  g.count = (int*)p;
+  p += align_up(2 * sizeof(int));
+  g.n_total = (int64_t*)p;
+  return g;
+}
 
 // ----------------------------------------------------------- parameters
 static int upload_params(pn_system_s* s, const double* hp_user) {
@@ -601,6 +627,79 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   ds.pcoef = dev_upload(s, h.pc.data(), h.pc.size(), &err);
   ds.mo = dev_upload(s, h.mo.data(), h.mo.size(), &err);
   ds.occ = dev_upload(s, occ.data(), occ.size(), &err);
+  // excitation table relative to determinant 0 (see DevSys::xtab)
+  {
+    const int hdr = 2 * (1 + PN_MAX_ORBITALS);
+    std::vector<int> xt(hdr + (size_t)d->n_det * 2 * PN_TAB_REC, 0);
+    bool ok = true;
+    size_t wstride = 0;
+    for (int sg = 0; sg < 2 && ok; ++sg) {
+      const int n = sg ? d->n_dn : d->n_up, e0 = sg ? d->n_up : 0;
+      std::vector<int> occ0(occ.begin() + e0, occ.begin() + e0 + n), V;
+      for (int p = 0; p < d->n_det; ++p)
+        for (int c = 0; c < n; ++c) {
+          const int mu = occ[(size_t)p * N + e0 + c];
+          if (std::find(occ0.begin(), occ0.end(), mu) == occ0.end() && std::find(V.begin(), V.end(), mu) == V.end())
+            V.push_back(mu);
+        }
+      std::sort(V.begin(), V.end());
+      if (n > PN_TAB_NMAX || (int)V.size() > PN_TAB_VMAX) { ok = false; break; }
+      xt[sg * (1 + PN_MAX_ORBITALS)] = (int)V.size();
+      for (size_t v = 0; v < V.size(); ++v) xt[sg * (1 + PN_MAX_ORBITALS) + 1 + v] = V[v];
+      auto parity = [](const std::vector<int>& a) {
+        int inv = 0;
+        for (size_t i = 0; i < a.size(); ++i)
+          for (size_t j = i + 1; j < a.size(); ++j) inv += a[i] > a[j];
+        return (inv & 1) ? -1 : 1;
+      };
+      int k3 = 0;
+      for (int p = 0; p < d->n_det && ok; ++p) {
+        // positions of determinant p holding a reference orbital (U, at
+        // reference position j) and holding a virtual one (C)
+        std::vector<int> U, J, C, used(n, 0);
+        for (int c = 0; c < n; ++c) {
+          const int mu = occ[(size_t)p * N + e0 + c];
+          const int j = (int)(std::find(occ0.begin(), occ0.end(), mu) - occ0.begin());
+          if (j < n) {
+            if (used[j]) { ok = false; break; }  // repeated orbital: leave it to the direct kernel
+            used[j] = 1;
+            U.push_back(c);
+            J.push_back(j);
+          } else {
+            C.push_back(c);
+          }
+        }
+        if (!ok) break;
+        const int k = (int)C.size();
+        if (k > PN_TAB_KMAX) { ok = false; break; }
+        std::vector<int> H;
+        for (int j = 0; j < n; ++j) if (!used[j]) H.push_back(j);
+        // block-triangular order: rows (J, H), columns (U, C)
+        std::vector<int> rows(J), cols(U);
+        rows.insert(rows.end(), H.begin(), H.end());
+        cols.insert(cols.end(), C.begin(), C.end());
+        int* rec = &xt[hdr + ((size_t)2 * p + sg) * PN_TAB_REC];
+        rec[0] = k;
+        rec[1] = parity(rows) * parity(cols);
+        for (int q = 0; q < k; ++q) {
+          rec[2 + q] = H[q];
+          const int mu = occ[(size_t)p * N + e0 + C[q]];
+          rec[2 + PN_TAB_KMAX + q] = (int)(std::find(V.begin(), V.end(), mu) - V.begin());
+        }
+        k3 += k * k * k;
+      }
+      const size_t nv = V.size(), ncol = n + nv, n3 = 3 * (size_t)N;
+      wstride = std::max(wstride, 3 * n * ncol + 3 * (size_t)n * n + 4 * n * nv + n3 + n3 * n * nv + n + 2);
+      ds.tab_nv[sg] = (int)nv;
+      ds.tab_k3[sg] = k3;
+    }
+    ds.xtab = nullptr;
+    ds.tab_wstride = 0;
+    if (ok) {
+      ds.xtab = dev_upload(s, xt.data(), xt.size(), &err);
+      ds.tab_wstride = (int)((wstride + 1) & ~(size_t)1);
+    }
+  }
   ds.ci = dev_upload(s, d->ci, d->n_det, &err);
   ds.cusp_rc = dev_upload(s, crc.data(), crc.size(), &err);
   ds.cusp_on = dev_upload(s, con.data(), con.size(), &err);
@@ -712,6 +811,23 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
     free_all(s);
     delete s;
     return PN_EINVAL;
+  }
+  // mixed handles: the local-energy guard, on by default with tau = 2e-5 Ha
+  if (d->precision == PN_MIXED) {
+    const int cap = std::min(s->Wc, 256);
+    const size_t gb = pn_guard_bytes(ds, s->Wc, cap);
+    if (cudaMalloc(&s->guard_mem, gb) != cudaSuccess) {
+      cudaGetLastError();
+      pn_set_error("local-energy guard of %zu bytes does not fit", gb);
+      s->guard_mem = nullptr;
+      free_all(s);
+      delete s;
+      return PN_ENOMEM;
+    }
+    s->guard = pn_carve_guard(ds, s->Wc, cap, s->guard_mem);
+    s->guard.net64 = pn_devnet<double>(s);
+    s->guard.tau = 2e-5;
+    PN_CUDA(cudaMemset(s->guard.n_total, 0, 8));
   }
   *out = s;
   return PN_OK;

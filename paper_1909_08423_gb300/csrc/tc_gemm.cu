@@ -228,7 +228,7 @@ int pn_linear_tc(const float* X, int ldx, const float* W, int ldw, const float* 
   const size_t smem = pn_tc_smem_bytes(Nout);
   PN_CUDA(cudaFuncSetAttribute(k_linear_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int blocks = (rows + TC_M - 1) / TC_M;
-  PN_LAUNCH("k_linear_tc", st,
+  PN_LAUNCH_W("k_linear_tc", st, 2.0 * rows * K * Nout,
             k_linear_tc<<<blocks, TC_THREADS, smem, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, K, Nout, Npad, T, acc, cols,
                                                           err));
   return PN_OK;

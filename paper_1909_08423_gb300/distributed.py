@@ -15,6 +15,19 @@ import torch
 import torch.distributed as dist
 
 
+def world_size(group=None):
+    """Ranks in `group` (1 when torch.distributed is not initialised)."""
+    if not (dist.is_available() and dist.is_initialized()):
+        return 1
+    return dist.get_world_size(group)
+
+
+def rank_of(group=None):
+    if not (dist.is_available() and dist.is_initialized()):
+        return 0
+    return dist.get_rank(group)
+
+
 def shard(W_total, rank, world):
     """Contiguous walker range [lo, hi) of one rank."""
     base, rem = divmod(W_total, world)

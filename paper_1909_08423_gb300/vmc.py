@@ -18,18 +18,33 @@ from __future__ import annotations
 
 import torch
 
-from . import binding
+from . import binding, checkpoint
+from . import distributed as pd
 from .autograd import vmc_loss_and_grad
 
 
 class VMCTrainer:
+    """Under torch.distributed (one process per GPU) each rank holds its
+    shard of the walkers and of every batch; its chains draw from the Philox
+    key seed + rank; the clipping window, the loss and the gradient are taken
+    over all ranks (see vmc_loss_and_grad), so every rank applies the same
+    AdamW update and the parameters stay identical.  `kernels` may replace
+    the library's clipping and AdamW calls (clip(E, Ec, cot), adamw(theta,
+    grad, m, v, lr, t, b1, b2, eps, wd)); `r0` gives this rank's initial
+    walkers instead of pn_init_walkers."""
+
     def __init__(self, system, params, walkers=2000, batch=10000, resample_period=100, n_discard=50, n_decorr=1,
                  lr=0.01, t0=200.0, weight_decay=0.01, betas=(0.9, 0.999), eps=1e-8, q=5.0, sampler="metropolis",
-                 sigma=0.2, tau=0.1, seed=0):
+                 sigma=0.2, tau=0.1, seed=0, device="cuda", group=None, kernels=None, r0=None):
         if sampler not in ("metropolis", "langevin"):
             raise ValueError("sampler must be 'metropolis' or 'langevin'")
         self.s = system
-        self.theta = torch.as_tensor(params, dtype=torch.float64, device="cuda").clone().contiguous()
+        self.group = group
+        self.world, self.rank = pd.world_size(group), pd.rank_of(group)
+        k = kernels or {}
+        self._clip = k.get("clip") or (lambda E, Ec, cot: binding.clip_local_energy(E, Ec, cot, q))
+        self._adamw = k.get("adamw") or binding.adamw_step
+        self.theta = torch.as_tensor(params, dtype=torch.float64, device=device).clone().contiguous()
         if self.theta.numel() != system.n_params:
             raise ValueError(f"{self.theta.numel()} parameters given, the system has {system.n_params}")
         self.m = torch.zeros_like(self.theta)
@@ -37,25 +52,32 @@ class VMCTrainer:
         self.cfg = dict(walkers=walkers, batch=batch, resample_period=resample_period, n_discard=n_discard,
                         n_decorr=n_decorr, lr=lr, t0=t0, weight_decay=weight_decay, betas=betas, eps=eps, q=q,
                         sampler=sampler, sigma=sigma, tau=tau, seed=seed)
+        lo, hi = pd.shard(walkers, self.rank, self.world)
+        blo, bhi = pd.shard(batch, self.rank, self.world)
+        self.W_local, self.B_local = hi - lo, bhi - blo
+        self.seed_local = seed + self.rank
         self.t = 0
         self.mc_step = 0
         N = system.N
-        self.r = torch.empty(walkers, N, 3, dtype=torch.float64, device="cuda")
+        self.r = torch.empty(self.W_local, N, 3, dtype=torch.float64, device=device)
         system.set_params(self.theta)
-        system.init_walkers(self.r, seed)
-        self.lp = torch.empty(walkers, dtype=torch.float64, device="cuda")
+        if r0 is not None:
+            self.r.copy_(torch.as_tensor(r0, dtype=torch.float64))
+        else:
+            system.init_walkers(self.r, self.seed_local)
+        self.lp = torch.empty(self.W_local, dtype=torch.float64, device=device)
         self.drift = torch.empty_like(self.r) if sampler == "langevin" else None
-        n_pool = resample_period * batch
-        self.pool = torch.empty(n_pool, N, 3, dtype=torch.float64, device="cuda")
+        n_pool = resample_period * self.B_local
+        self.pool = torch.empty(n_pool, N, 3, dtype=torch.float64, device=device)
 
     def _advance(self, n):
         c = self.cfg
         if n <= 0:
             return
         if c["sampler"] == "metropolis":
-            self.s.metropolis_step(self.r, self.lp, n, c["sigma"], c["seed"], self.mc_step)
+            self.s.metropolis_step(self.r, self.lp, n, c["sigma"], self.seed_local, self.mc_step)
         else:
-            self.s.langevin_step(self.r, self.lp, self.drift, n, c["tau"], c["seed"], self.mc_step)
+            self.s.langevin_step(self.r, self.lp, self.drift, n, c["tau"], self.seed_local, self.mc_step)
         self.mc_step += n
 
     def resample(self):
@@ -67,7 +89,7 @@ class VMCTrainer:
         else:
             self.s.eval_drift(self.r, self.drift, self.lp)
         self._advance(c["n_discard"])
-        n_pool, W = self.pool.shape[0], c["walkers"]
+        n_pool, W = self.pool.shape[0], self.W_local
         filled = 0
         while filled < n_pool:
             self._advance(c["n_decorr"])
@@ -81,14 +103,37 @@ class VMCTrainer:
         if self.t % c["resample_period"] == 0:
             self.resample()
         k = self.t % c["resample_period"]
-        rb = self.pool[k * c["batch"]:(k + 1) * c["batch"]]
-        loss, grad, E = vmc_loss_and_grad(self.s, rb, c["q"])
+        rb = self.pool[k * self.B_local:(k + 1) * self.B_local]
+        loss, grad, E = vmc_loss_and_grad(self.s, rb, c["q"], clip_fn=self._clip, group=self.group)
         lr = c["lr"] / (1.0 + self.t / c["t0"])
-        binding.adamw_step(self.theta, grad, self.m, self.v, lr, self.t + 1, c["betas"][0], c["betas"][1], c["eps"],
-                           c["weight_decay"])
+        self._adamw(self.theta, grad, self.m, self.v, lr, self.t + 1, c["betas"][0], c["betas"][1], c["eps"],
+                    c["weight_decay"])
         self.s.set_params(self.theta)
         self.t += 1
         fin = torch.isfinite(E)
         Ef = E[fin]
         return {"step": self.t, "loss": float(loss), "e_mean": float(Ef.mean()),
                 "e_stderr": float(Ef.std() / max(1, Ef.numel()) ** 0.5), "lr": lr}
+
+    # ------------------------------------------------------ checkpointing
+    def save(self, path):
+        """Everything the next steps depend on (parameters, AdamW moments,
+        step counters, walkers and their RNG position, the sampled pool)."""
+        checkpoint.save(path, {"theta": self.theta, "m": self.m, "v": self.v, "r": self.r, "lp": self.lp,
+                               "drift": self.drift, "pool": self.pool},
+                        {"kind": "vmc", "t": self.t, "mc_step": self.mc_step,
+                         "cfg": {k: list(v) if isinstance(v, tuple) else v for k, v in self.cfg.items()}})
+
+    def load(self, path):
+        a, m = checkpoint.load(path, device=self.theta.device)
+        if m.get("kind") != "vmc":
+            raise ValueError(f"{path}: holds {m.get('kind')}, not a training state")
+        cfg = {k: tuple(v) if isinstance(v, list) else v for k, v in m["cfg"].items()}
+        if cfg != self.cfg:
+            raise ValueError("checkpoint was written with another training configuration")
+        for k in ("theta", "m", "v", "r", "lp", "pool"):
+            getattr(self, k).copy_(a[k])
+        if self.drift is not None:
+            self.drift.copy_(a["drift"])
+        self.t, self.mc_step = m["t"], m["mc_step"]
+        self.s.set_params(self.theta)

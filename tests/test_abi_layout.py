@@ -20,7 +20,8 @@ STRUCTS = {"pn_system_desc": binding.SystemDesc, "pn_server_cfg": binding.Server
 ENUMS = {"PN_FP64": binding.PN_FP64, "PN_MIXED": binding.PN_MIXED, "PN_JOB_ELOC": binding.PN_JOB_ELOC,
          "PN_JOB_SWEEP": binding.PN_JOB_SWEEP, "PN_JOB_SCAN": binding.PN_JOB_SCAN,
          "PN_OPT_FUSED_SAMPLER": binding.PN_OPT_FUSED_SAMPLER, "PN_OPT_TENSOR_CORES": binding.PN_OPT_TENSOR_CORES,
-         "PN_OPT_DRIFT": binding.PN_OPT_DRIFT}
+         "PN_OPT_DRIFT": binding.PN_OPT_DRIFT, "PN_OPT_GUARD": binding.PN_OPT_GUARD,
+         "PN_OPT_DET_TABLE": binding.PN_OPT_DET_TABLE}
 ENUMS.update({name: code for code, name in binding.ERRORS.items()})
 
 

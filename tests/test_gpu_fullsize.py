@@ -38,6 +38,18 @@ def _grad_on_sample(s, r, idx, scale=1.0):
     return g.cpu().numpy()
 
 
+def _assert_grad_close(gi, go):
+    """Mixed gradient against the float64 oracle's, element by element: each
+    entry within 1e-3 of itself plus 1e-5 of the largest entry (float32
+    arithmetic carries about 6e-8 relative error per operation; the sums
+    over pairs, rows and walkers and their cancellations leave the
+    accumulated error near 1e-6 of the largest entry, kept here with a
+    margin of ten)."""
+    bound = 1e-3 * np.abs(go) + 1e-5 * np.abs(go).max()
+    bad = np.abs(gi - go) > bound
+    assert not bad.any(), (int(bad.sum()), float(np.max(np.abs(gi - go) / bound)))
+
+
 def test_h2_fp64_local_energy_full_batch(lib):
     sysd = synth.h2()
     o = Oracle(sysd)
@@ -94,7 +106,7 @@ def test_be_bench_step_full_size(lib, precision):
     if precision == 0:
         assert np.max(np.abs(gi - go)) <= 1e-9 * np.abs(go).max()
     else:
-        assert np.linalg.norm(gi - go) / np.linalg.norm(go) < 1e-4
+        _assert_grad_close(gi, go)
 
 
 def test_h10_mixed_local_energy_and_gradient_full_size(lib):
@@ -115,10 +127,10 @@ def test_h10_mixed_local_energy_and_gradient_full_size(lib):
     idx = _sample(W, 10, 6)
     Eo, _, _ = o.local_energy(rg[idx])
     err = np.abs(Eg[idx] - Eo)
-    assert err.max() < 1e-3 and np.median(err) < 1e-4, err
+    assert err.max() <= 1e-4, err
     gi = _grad_on_sample(s, r, idx)
     go = o.grad_logpsi(rg[idx], np.ones(len(idx)))
-    assert np.linalg.norm(gi - go) / np.linalg.norm(go) < 1e-4
+    _assert_grad_close(gi, go)
 
 
 def test_n2_mixed_vmc_step_full_size(lib):
@@ -146,7 +158,7 @@ def test_n2_mixed_vmc_step_full_size(lib):
     binding.clip_local_energy(E, Ec, cot)
     torch.cuda.synchronize()
     rg, Eg = r.cpu().numpy(), E.cpu().numpy()
-    idx = _sample(W, 3, 7)
+    idx = _sample(W, 8, 7)
     # the sweep: each sampled walker's move as the oracle makes it
     moved_same = 0
     for w in idx:
@@ -154,8 +166,8 @@ def test_n2_mixed_vmc_step_full_size(lib):
         moved_same += int(np.all(np.abs(rg[w] - ro[0]) < 1e-5))
     assert moved_same >= len(idx) - 1
     Eo, _, _ = o.local_energy(rg[idx])
-    assert np.all(np.abs(Eg[idx] - Eo) < 1e-3), np.abs(Eg[idx] - Eo)
+    assert np.all(np.abs(Eg[idx] - Eo) <= 1e-4), np.abs(Eg[idx] - Eo)
     assert np.all(np.isfinite(Ec.cpu().numpy()))
     gi = _grad_on_sample(s, r, idx[:2])
     go = o.grad_logpsi(rg[idx[:2]], np.ones(2))
-    assert np.linalg.norm(gi - go) / np.linalg.norm(go) < 1e-4
+    _assert_grad_close(gi, go)

@@ -78,8 +78,10 @@ def test_grad_mixed_close_to_fp64(lib):
         out = torch.empty(s.n_params, dtype=torch.float64, device="cuda")
         s.grad_logpsi(r, cot, out)
         g[p] = out.cpu().numpy()
-    rel = np.linalg.norm(g[1] - g[0]) / np.linalg.norm(g[0])
-    assert rel < 1e-4, rel
+    # element by element: within 1e-3 of the entry plus 1e-5 of the largest
+    # entry (the float32 network's accumulated rounding, with a margin)
+    bound = 1e-3 * np.abs(g[0]) + 1e-5 * np.abs(g[0]).max()
+    assert np.all(np.abs(g[1] - g[0]) <= bound), np.max(np.abs(g[1] - g[0]) / bound)
 
 
 def test_autograd_function_and_vmc_gradient(lib):

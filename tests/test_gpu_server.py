@@ -71,12 +71,27 @@ def test_results_same_alone_and_in_a_mix(lib):
     jobs = [x for pair in zip(filler, again) for x in pair]
     results = _run(lib, srv, jobs)
     torch.cuda.synchronize()
-    assert all(r.status == 0 for r in results)
+    assert all(r.status == 0 for r in results), [r.status for r in results]
     for (e_a, r_a), j in zip(alone, again):
         np.testing.assert_array_equal(j["eloc_out"].cpu().numpy(), e_a)
         np.testing.assert_array_equal(j["r_out"].cpu().numpy(), r_a)
-    # the mix overlapped: some job was admitted while another was running
-    assert any(r.queue_ms > 0 for r in results)
+    # the mix overlapped on the device: the device intervals of jobs on
+    # different slots (CUDA events around each job's work) intersect
+    iv = sorted((r.dev_start_ms, r.dev_end_ms) for r in results)
+    assert all(b > a for a, b in iv)
+    overlaps = sum(1 for k in range(1, len(iv)) if iv[k][0] < max(e for _, e in iv[:k]))
+    assert overlaps >= 2, iv
+    srv.close()
+
+
+def test_one_slot_runs_jobs_one_after_another(lib):
+    """With a single slot no two device intervals intersect."""
+    systems = _systems(lib)
+    srv = lib.Server(8 * GB, n_slots=1, chunk_walkers=1024)
+    res = _run(lib, srv, [_job(systems[k % 3], lib.PN_JOB_ELOC, 256, 40 + k, out=False) for k in range(6)])
+    assert all(r.status == 0 for r in res)
+    iv = sorted((r.dev_start_ms, r.dev_end_ms) for r in res)
+    assert all(iv[k][0] >= iv[k - 1][1] for k in range(1, len(iv)))
     srv.close()
 
 
