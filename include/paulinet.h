@@ -256,9 +256,10 @@ int pn_langevin_step(pn_system_t sys, double* r, double* logabs, double* drift,
  *   ahead; 4 (PN_MIXED) the tensor-core sampler -- a block per tile of
  *   walkers whose electrons and pairs fill 128-row tcgen05 tiles, every
  *   linear map one MMA group with three-piece bf16 operands and weights
- *   bulk-copied (TMA) one stage ahead -- falling back to 1 where the tiles
- *   do not fit; 0 (or a system too large for one tile) uses one kernel per
- *   stage.
+ *   bulk-copied (TMA) one stage ahead -- falling back, where the tiles do
+ *   not fit, to 1 for embeddings up to 64 wide and to 0 beyond (there the
+ *   staged value pass is the faster); 0 (or a system too large for one
+ *   tile) uses one kernel per stage.
  * PN_OPT_TENSOR_CORES (PN_MIXED only; default 0): a mask of the float32
  *   linear layers that run on tcgen05 with each operand split into three
  *   bf16 pieces (six products, float32 accumulation in tensor memory):
@@ -271,23 +272,28 @@ int pn_langevin_step(pn_system_t sys, double* r, double* logabs, double* drift,
  * PN_OPT_DRIFT (default 1): how pn_eval_drift and pn_langevin_step form
  *   grad_r ln|psi| -- 1 reverse mode (work linear in the electron count),
  *   0 the forward jet pass (3N + 2 rows per electron).
- * PN_OPT_GUARD (PN_MIXED only; default 20): the local-energy guard of
+ * PN_OPT_GUARD (PN_MIXED only; default 50): the local-energy guard of
  *   pn_eval_local_energy, value = tau in micro-hartree, 0 = off.  The
  *   float32 network's rounding reaches E_loc through the determinants and
  *   the squared gradient, and a few walkers in ten thousand amplify it past
  *   1e-4 Ha, with no cheap per-walker predictor of which.  With the guard on,
- *   every workspace chunk's heads (the Jastrow and backflow maps) are
- *   evaluated a second time on the other unit (tensor cores if they ran on
- *   CUDA cores, and back), which changes only their rounding; the
- *   determinants and E_loc are formed again from them, and every walker
+ *   every workspace chunk is evaluated a second time from the same network
+ *   output with different rounding (see PN_OPT_GUARD_PROBE) and every walker
  *   whose two energies differ by more than tau, or not finitely, is
  *   evaluated again in float64 and returned with its float64 E_loc, ln|psi|,
  *   sign and status.  Each guarded chunk reads one count back to the host
  *   (the call then synchronises its stream once per chunk).  Measured on
- *   walkers sampled from |psi|^2 with tau = 2e-5 Ha: 0.2-0.5 % of walkers
- *   re-evaluated and the largest remaining error below 7e-5 Ha on the
- *   H10-chain and N2-shaped systems.  pn_guard_count reports how many
+ *   16384 walkers sampled from |psi|^2 with the default probe and tau: 1.0 %
+ *   (H10 chain) and 0.46 % (N2 shape) of walkers re-evaluated, the largest
+ *   remaining error 7.0e-5 and 8.5e-5 Ha.  pn_guard_count reports how many
  *   walkers were re-evaluated.
+ * PN_OPT_GUARD_PROBE (default 1): the guard's second evaluation -- 1 the
+ *   backflow and Jastrow jets of the first pass perturbed by +-2^-19
+ *   relative (a deterministic sign per element, a stand-in for the
+ *   network's accumulated rounding) and the determinants and E_loc formed
+ *   again; 0 the heads (the Jastrow and backflow maps) evaluated again on
+ *   the other unit (tensor cores if they ran on CUDA cores, and back),
+ *   then the determinants and E_loc.
  * PN_OPT_DET_TABLE (default 1): how the local-energy pass forms the
  *   determinants' gradients and Laplacians -- 1 by the table method where
  *   the system allows it (every determinant reached from determinant 0 by
@@ -295,11 +301,12 @@ int pn_langevin_step(pn_system_t sys, double* r, double* logabs, double* drift,
  *   virtual orbitals per spin): det A_p = s_p det A_0 det(T[holes,
  *   particles]) with T = A_0^-1 A, so that the 3N tangents and the
  *   Laplacian of all determinants follow from those of determinant 0 and of
- *   T; a walker whose determinant-0 block has a pivot ratio beyond 1e4 is
- *   computed block by block; 0 block by block for every walker; 2 the table
+ *   T; a walker whose determinant-0 block has a 1-norm condition number
+ *   beyond 1e3 is computed block by block; 0 block by block for every walker; 2 the table
  *   kernel with every walker on its block-by-block path (a test of that
  *   path). */
-enum { PN_OPT_FUSED_SAMPLER = 1, PN_OPT_TENSOR_CORES = 2, PN_OPT_DRIFT = 3, PN_OPT_GUARD = 4, PN_OPT_DET_TABLE = 5 };
+enum { PN_OPT_FUSED_SAMPLER = 1, PN_OPT_TENSOR_CORES = 2, PN_OPT_DRIFT = 3, PN_OPT_GUARD = 4, PN_OPT_DET_TABLE = 5,
+       PN_OPT_GUARD_PROBE = 6 };
 int pn_set_option(pn_system_t sys, int option, int value);
 
 /* Walkers the local-energy guard (PN_OPT_GUARD) re-evaluated in float64

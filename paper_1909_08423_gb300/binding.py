@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpaulinet.so")
 PN_FP64, PN_MIXED = 0, 1
 PN_JOB_ELOC, PN_JOB_SWEEP, PN_JOB_SCAN = 0, 1, 2
 PN_OPT_FUSED_SAMPLER, PN_OPT_TENSOR_CORES, PN_OPT_DRIFT, PN_OPT_GUARD, PN_OPT_DET_TABLE = 1, 2, 3, 4, 5
+PN_OPT_GUARD_PROBE = 6
 ERRORS = {0: "PN_OK", 1: "PN_EINVAL", 2: "PN_ENOMEM", 3: "PN_EBUDGET", 4: "PN_ENOTREADY",
           5: "PN_ETIMEOUT", 6: "PN_EDEVICE", 7: "PN_ECANCELLED"}
 

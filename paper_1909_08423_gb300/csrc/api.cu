@@ -434,7 +434,11 @@ int pn_run_metropolis(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc
       if (ds.fused_sampler == 4)
         fused = pn_run_metropolis_tc(ds, net, rc, lc, Wn, (unsigned)c0, n_steps, sigma, seed, step0, w.n_acc, st);
     }
-    if (fused == PN_ENOTREADY && ds.fused_sampler)
+    // where the tensor-core sampler does not fit, embeddings wider than 64
+    // run faster through the staged value pass than through the fused
+    // CUDA-core kernels (N2 shape, 16384 walkers: 26 vs 35 ms per step)
+    const bool wide = ds.fused_sampler == 4 && ds.D > 64;
+    if (fused == PN_ENOTREADY && ds.fused_sampler && !wide)
       fused = pn_run_metropolis_fused<R>(ds, net, rc, lc, Wn, (unsigned)c0, n_steps, sigma, seed, step0, w.n_acc, st);
     if (fused != PN_OK && fused != PN_ENOTREADY) return fused;
     for (int k = 0; fused != PN_OK && k < n_steps; ++k) {
@@ -715,6 +719,10 @@ extern "C" int pn_set_option(pn_system_t s, int option, int value) {
       if (value > 0 && !s->guard_mem) { pn_set_error("the local-energy guard exists for PN_MIXED handles only"); return PN_EINVAL; }
       s->guard.tau = value * 1e-6;
       return PN_OK;
+    case PN_OPT_GUARD_PROBE:
+      if (value < 0 || value > 1) { pn_set_error("guard probe option takes 0 or 1"); return PN_EINVAL; }
+      s->ds.guard_probe = value;
+      return PN_OK;
     case PN_OPT_DET_TABLE:
       if (value < 0 || value > 2) { pn_set_error("determinant option takes 0..2"); return PN_EINVAL; }
       s->ds.no_table = value == 1 ? 0 : (value == 0 ? 1 : 2);
@@ -762,7 +770,7 @@ extern "C" int pn_clip_local_energy(const double* eloc, int W, double q, double*
   int n = 1;
   while (n < W) n <<= 1;
   const size_t smem = (size_t)n * 8;
-  PN_CUDA(cudaFuncSetAttribute(k_clip, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8));
+  PN_CUDA(pn_allow_max_smem(k_clip));
   PN_LAUNCH("k_clip", st, k_clip<<<1, 1024, smem, st>>>(e, W, q, o, c));
   if (host) {
     PN_CUDA(cudaMemcpyAsync(out, o, (size_t)W * 8, cudaMemcpyDefault, st));

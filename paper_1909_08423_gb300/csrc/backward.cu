@@ -991,7 +991,7 @@ static int filter_bwd_dist(const DevSys& s, const DevNet<R>& net, int n, const R
   const unsigned grid = nblk((size_t)Wn * s.Ppair, 8 * FB_ROWS);
   if (fb <= (size_t)maxsm) {
     if (fb > 48 * 1024)
-      PN_CUDA(cudaFuncSetAttribute(k_filter_bwd_dist<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb));
+      PN_CUDA(pn_allow_max_smem(k_filter_bwd_dist<R, true>));
     PN_LAUNCH("k_filter_bwd_dist", st,
               (k_filter_bwd_dist<R, true><<<grid, 256, fb, st>>>(s, net, n, Ah, ef, dw, Wn, dd)));
   } else {
@@ -1120,7 +1120,7 @@ static int grad_chunk(const DevSys& s, const DevNet<R>& net, Tape<R>& t, const d
       cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
       if (fb <= (size_t)maxsm) {
         if (fb > 48 * 1024)
-          PN_CUDA(cudaFuncSetAttribute(k_filter_bwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb));
+          PN_CUDA(pn_allow_max_smem(k_filter_bwd<R>));
         PN_LAUNCH("k_filter_bwd", st,
                   k_filter_bwd<R><<<nblk((size_t)Wn * P, 8 * FB_ROWS), 256, fb, st>>>(s, net, n, Ahn, t.dw, Wn,
                                                                                      t.dAh, t.Sh));

@@ -359,17 +359,17 @@ int max_smem() {
     switch (nj) {                                                                                    \
       case 2:                                                                                        \
         if (bytes > 48 * 1024)                                                                       \
-          PN_CUDA(cudaFuncSetAttribute(KERN<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)); \
+          PN_CUDA(pn_allow_max_smem(KERN<2>)); \
         PN_LAUNCH_W(NAME, st, ft_work, (KERN<2><<<ft.t0[3], 256, bytes, st>>>(__VA_ARGS__)));                  \
         break;                                                                                       \
       case 4:                                                                                        \
         if (bytes > 48 * 1024)                                                                       \
-          PN_CUDA(cudaFuncSetAttribute(KERN<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)); \
+          PN_CUDA(pn_allow_max_smem(KERN<4>)); \
         PN_LAUNCH_W(NAME, st, ft_work, (KERN<4><<<ft.t0[3], 256, bytes, st>>>(__VA_ARGS__)));                  \
         break;                                                                                       \
       default:                                                                                       \
         if (bytes > 48 * 1024)                                                                       \
-          PN_CUDA(cudaFuncSetAttribute(KERN<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)); \
+          PN_CUDA(pn_allow_max_smem(KERN<8>)); \
         PN_LAUNCH_W(NAME, st, ft_work, (KERN<8><<<ft.t0[3], 256, bytes, st>>>(__VA_ARGS__)));                  \
         break;                                                                                       \
     }                                                                                                \

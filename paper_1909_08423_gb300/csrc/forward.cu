@@ -401,6 +401,18 @@ __global__ void __launch_bounds__(256, TN == 8 ? 2 : 3)
   }
 }
 
+// h0 = x^(0) W_h + b_h of the first layer: one row, the same for every
+// electron of every walker.
+template <typename R>
+__global__ void k_h0_row(const R* __restrict__ x0, const R* __restrict__ W, const R* __restrict__ b, int D, int Zd,
+                         R* __restrict__ h0) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= Zd) return;
+  R acc = b[z];
+  for (int d = 0; d < D; ++d) acc += x0[d] * W[(size_t)d * Zd + z];
+  h0[z] = acc;
+}
+
 // x^(0): the shared electron embedding on value rows, zero derivatives.
 template <typename R>
 __global__ void k_init_x(const R* __restrict__ x0, R* __restrict__ X, size_t groups, int T, int D) {
@@ -507,8 +519,11 @@ __global__ void __launch_bounds__(256) k_message(DevSys s, const R* __restrict__
 // chunk, and the product-rule factor d d_ij / d r_{k,a} is resolved per
 // electron k, so a row costs one h load and two multiply-adds per partner.
 // Arithmetic per row is that of k_message.
+// HC: the first layer, whose h is one row h0 = H[0 .. Zd) shared by every
+// electron with no tangent or Laplacian (x^(0) is the same constant for all
+// electrons), so that its h GEMM and the x^(0) jet need not exist.
 constexpr int MSG_KC = 2;  // electrons per tangent-row chunk of k_message_c
-template <typename R>
+template <typename R, bool HC>
 __global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict__ Y, const double* __restrict__ geo,
                                                    const R* __restrict__ wj, const R* __restrict__ H, int ldH, int Wn,
                                                    int T, R* __restrict__ Zb, int ldZ) {
@@ -523,7 +538,7 @@ __global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict
   const int w = idx / ((size_t)Zd * N * nC);
   const int lap = T - 1;
   const bool si = i < s.n_up;
-  const R* Hw_ = H + (size_t)w * N * T * ldH + z;
+  const R* Hw_ = HC ? H + z : H + (size_t)w * N * T * ldH + z;
   const R* ww = wj + (size_t)w * s.Ppair * 3 * Zd + z;
   const double* gw = geo + (size_t)w * s.Ppair * 4;
   R* ob = Zb + (size_t)(w * N + i) * T * ldZ + z;
@@ -539,7 +554,7 @@ __global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict
       const R sg = i < j ? R(1) : R(-1);  // unit vector from j to i
       const R u[3] = {sg * (R)g[1], sg * (R)g[2], sg * (R)g[3]};
       const R w0 = ww[(size_t)p * 3 * Zd], w1 = ww[(size_t)p * 3 * Zd + Zd];
-      const R* hj = Hw_ + (size_t)j * T * ldH;
+      const R* hj = HC ? Hw_ : Hw_ + (size_t)j * T * ldH;
       const R h0 = hj[0];
       const bool same = (j < s.n_up) == si;
 #pragma unroll
@@ -549,7 +564,7 @@ __global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           const R dd = (k == i) ? u[a] : ((k == j) ? -u[a] : R(0));
-          const R v = w1 * dd * h0 + w0 * hj[(size_t)(1 + 3 * k + a) * ldH];
+          const R v = HC ? w1 * dd * h0 : w1 * dd * h0 + w0 * hj[(size_t)(1 + 3 * k + a) * ldH];
           if (same) zs[3 * kk + a] += v; else za[3 * kk + a] += v;
         }
       }
@@ -591,13 +606,15 @@ __global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict
     const R sg = i < j ? R(1) : R(-1);
     const R id = R(1) / (R)g[0];
     const R w0 = ww[(size_t)p * 3 * Zd], w1 = ww[(size_t)p * 3 * Zd + Zd], w2 = ww[(size_t)p * 3 * Zd + 2 * Zd];
-    const R* hj = Hw_ + (size_t)j * T * ldH;
+    const R* hj = HC ? Hw_ : Hw_ + (size_t)j * T * ldH;
     const R h0 = hj[0];
     R cross = 0;
-    for (int a = 0; a < 3; ++a)
-      cross += sg * (R)g[1 + a] * (hj[(size_t)(1 + 3 * i + a) * ldH] - hj[(size_t)(1 + 3 * j + a) * ldH]);
+    if (!HC)
+      for (int a = 0; a < 3; ++a)
+        cross += sg * (R)g[1 + a] * (hj[(size_t)(1 + 3 * i + a) * ldH] - hj[(size_t)(1 + 3 * j + a) * ldH]);
     const R v0 = w0 * h0;
-    const R vl = (R(2) * w2 + R(4) * w1 * id) * h0 + w0 * hj[(size_t)lap * ldH] + R(2) * w1 * cross;
+    const R vl = HC ? (R(2) * w2 + R(4) * w1 * id) * h0
+                    : (R(2) * w2 + R(4) * w1 * id) * h0 + w0 * hj[(size_t)lap * ldH] + R(2) * w1 * cross;
     if ((j < s.n_up) == si) { vs += v0; ls += vl; } else { va += v0; la += vl; }
   }
   for (int I = 0; I < M; ++I) {
@@ -615,6 +632,164 @@ __global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict
   ol[0] = ls;
   ol[Zd] = la;
   ol[2 * Zd] = lq;
+}
+
+// Same messages with the walker's operands staged in shared memory: a block
+// per (walker, tile of 32 columns z), one warp per electron i, lanes over z.
+// The block first copies the walker's h-jet rows [N][T][32], its pair
+// filter jets [P][3][32] and pair geometry (d, 1/d, unit vector) as float;
+// each thread then forms all T rows of z_i^same, z_i^anti and z_i^nuc for
+// its column from shared memory:
+//   value      z_i = sum_j w_ij h_j
+//   tangent    z_i[k,a] = sum_j w_ij h_j[k,a] + w'_ij (d d_ij / d r_ka) h_j
+//   Laplacian  z_i[lap] = sum_j (2 w''_ij + 4 w'_ij / d_ij) h_j + w_ij h_j[lap]
+//                         + 2 w'_ij u_ij . (grad_i h_j - grad_j h_j)
+// (electron pairs move with both electrons, so their Laplacian over all
+// coordinates is twice the one-electron one; nuclear pairs move with i only).
+// Requires Zd a multiple of 32; HC as in k_message_c.
+constexpr int MSGW_ZT = 32;
+constexpr int MSGW_NMAX = 16;  // electrons of the staged kernel (partner values in registers)
+template <typename R, bool HC>
+__global__ void k_message_w(DevSys s, const R* __restrict__ Y, const double* __restrict__ geo,
+                            const R* __restrict__ wj, const R* __restrict__ H, int ldH, int Wn, int T,
+                            R* __restrict__ Zb, int ldZ) {
+  extern __shared__ __align__(16) unsigned char mw_smem[];
+  const int N = s.N, M = s.M, Zd = s.Zd, P = s.Ppair, lap = T - 1;
+  const int ntile = Zd / MSGW_ZT;
+  const int w = blockIdx.x / ntile, z0 = (blockIdx.x % ntile) * MSGW_ZT;
+  const int lane = threadIdx.x & 31, i = threadIdx.x >> 5;
+  const int HT = HC ? 1 : T;  // rows of h staged per electron (one shared row for HC)
+  const int HN = HC ? 1 : N;
+  R* hs = (R*)mw_smem;                       // [HN][HT][32]
+  R* ws = hs + (size_t)HN * HT * MSGW_ZT;    // [P][3][32]
+  R* gs = ws + (size_t)P * 3 * MSGW_ZT;      // [P][5]: d, 1/d, unit vector
+  const int nth = blockDim.x;
+  if (HC) {
+    for (int q = threadIdx.x; q < MSGW_ZT; q += nth) hs[q] = H[z0 + q];
+  } else {
+    const R* Hw = H + (size_t)w * N * T * ldH + z0;
+    for (int q = threadIdx.x; q < N * T * MSGW_ZT; q += nth) {
+      const int row = q / MSGW_ZT, c = q - row * MSGW_ZT;
+      hs[q] = Hw[(size_t)row * ldH + c];
+    }
+  }
+  const R* Ww = wj + (size_t)w * P * 3 * Zd + z0;
+  for (int q = threadIdx.x; q < P * 3 * MSGW_ZT; q += nth) {
+    const int row = q / MSGW_ZT, c = q - row * MSGW_ZT;
+    ws[q] = Ww[(size_t)row * Zd + c];
+  }
+  const double* gw = geo + (size_t)w * P * 4;
+  for (int p = threadIdx.x; p < P; p += nth) {
+    const double d = gw[4 * p];
+    gs[5 * p] = (R)d;
+    gs[5 * p + 1] = (R)(1.0 / d);
+    gs[5 * p + 2] = (R)gw[4 * p + 1];
+    gs[5 * p + 3] = (R)gw[4 * p + 2];
+    gs[5 * p + 4] = (R)gw[4 * p + 3];
+  }
+  __syncthreads();
+  if (i >= N) return;
+  const int z = lane;
+  const bool si = i < s.n_up;
+  auto hrow = [&](int j, int t) -> R { return HC ? (t == 0 ? hs[z] : R(0)) : hs[((size_t)j * T + t) * MSGW_ZT + z]; };
+  auto pidx = [&](int j) { return i < j ? pn_pair_index(i, j, N) : pn_pair_index(j, i, N); };
+  R* ob = Zb + (size_t)(w * N + i) * T * ldZ + z0 + z;
+  // per-thread sums that the tangent rows of electron i itself reuse
+  R s1s[3] = {0, 0, 0}, s1a[3] = {0, 0, 0}, n1[3] = {0, 0, 0};
+  R vs = 0, va = 0, vn = 0, ls = 0, la = 0, ln = 0;
+  for (int j = 0; j < N; ++j) {
+    if (j == i) continue;
+    const int p = pidx(j);
+    const R sg = i < j ? R(1) : R(-1);  // unit vector from j to i
+    const R* g = gs + 5 * p;
+    const R w0 = ws[(3 * p) * MSGW_ZT + z], w1 = ws[(3 * p + 1) * MSGW_ZT + z], w2 = ws[(3 * p + 2) * MSGW_ZT + z];
+    const R h0 = hrow(j, 0);
+    const bool same = (j < s.n_up) == si;
+    R cross = 0;
+    if (!HC)
+      for (int a = 0; a < 3; ++a) cross += sg * g[2 + a] * (hrow(j, 1 + 3 * i + a) - hrow(j, 1 + 3 * j + a));
+    const R v0 = w0 * h0;
+    const R vl = HC ? (R(2) * w2 + R(4) * w1 * g[1]) * h0
+                    : (R(2) * w2 + R(4) * w1 * g[1]) * h0 + w0 * hrow(j, lap) + R(2) * w1 * cross;
+    if (same) {
+      vs += v0;
+      ls += vl;
+      for (int a = 0; a < 3; ++a) s1s[a] += w1 * sg * g[2 + a] * h0;
+    } else {
+      va += v0;
+      la += vl;
+      for (int a = 0; a < 3; ++a) s1a[a] += w1 * sg * g[2 + a] * h0;
+    }
+  }
+  for (int I = 0; I < M; ++I) {
+    const int p = s.Pee + i * M + I;
+    const R* g = gs + 5 * p;
+    const R y = Y[I * Zd + z0 + z];
+    const R w0 = ws[(3 * p) * MSGW_ZT + z], w1 = ws[(3 * p + 1) * MSGW_ZT + z], w2 = ws[(3 * p + 2) * MSGW_ZT + z];
+    vn += w0 * y;
+    ln += (w2 + R(2) * w1 * g[1]) * y;
+    for (int a = 0; a < 3; ++a) n1[a] += w1 * g[2 + a] * y;
+  }
+  ob[0] = vs;
+  ob[Zd] = va;
+  ob[2 * Zd] = vn;
+  R* ol = ob + (size_t)lap * ldZ;
+  ol[0] = ls;
+  ol[Zd] = la;
+  ol[2 * Zd] = ln;
+  // tangent rows t = 1 + 3k + a.  The partners' filter values, split by
+  // channel (zero for the other channel and for j = i), sit in registers,
+  // so a row costs one shared-memory load and two multiply-adds per partner.
+  R w0s[MSGW_NMAX], w0a[MSGW_NMAX];
+#pragma unroll
+  for (int j = 0; j < MSGW_NMAX; ++j) {
+    w0s[j] = w0a[j] = 0;
+    if (!HC && j < N && j != i) {
+      const R w0 = ws[(3 * pidx(j)) * MSGW_ZT + z];
+      if ((j < s.n_up) == si) w0s[j] = w0; else w0a[j] = w0;
+    }
+  }
+  for (int k = 0; k < N; ++k) {
+    // the partner k's own move: d d_ik / d r_ka = -u_ik[a]
+    R pk[3] = {0, 0, 0};
+    bool ksame = true;
+    if (k != i) {
+      const int p = pidx(k);
+      const R sg = i < k ? R(1) : R(-1);
+      const R f = -ws[(3 * p + 1) * MSGW_ZT + z] * sg * hrow(k, 0);
+      for (int a = 0; a < 3; ++a) pk[a] = f * gs[5 * p + 2 + a];
+      ksame = (k < s.n_up) == si;
+    }
+    for (int a = 0; a < 3; ++a) {
+      const int t = 1 + 3 * k + a;
+      R zs = 0, za = 0;
+      if (!HC) {
+        const R* hcol = hs + (size_t)t * MSGW_ZT + z;
+#pragma unroll
+        for (int j = 0; j < MSGW_NMAX; ++j) {
+          if (j < N) {
+            const R h = hcol[(size_t)j * T * MSGW_ZT];
+            zs += w0s[j] * h;
+            za += w0a[j] * h;
+          }
+        }
+      }
+      R zq = 0;
+      if (k == i) {
+        zs += s1s[a];
+        za += s1a[a];
+        zq = n1[a];
+      } else if (ksame) {
+        zs += pk[a];
+      } else {
+        za += pk[a];
+      }
+      R* o = ob + (size_t)t * ldZ;
+      o[0] = zs;
+      o[Zd] = za;
+      o[2 * Zd] = zq;
+    }
+  }
 }
 
 // ---------------------------------------------------- activation on a jet
@@ -766,6 +941,125 @@ __global__ void k_combine(DevSys s, const double* __restrict__ geo, const double
   if (status) status[w] = st;
 }
 
+// The same combination with a warp per walker: lanes over determinants for
+// the signed log-sum, over electron pairs for gamma and V, and over the 3N
+// coordinates for the gradient (three per lane at most).
+__device__ inline double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename R>
+__global__ void k_combine_w(DevSys s, const double* __restrict__ geo, const double* __restrict__ det,
+                            const R* __restrict__ Jj, int Wn, int T, int jet, double* __restrict__ logabs,
+                            double* __restrict__ sign, double* __restrict__ eloc, int* __restrict__ status,
+                            double* __restrict__ grad_out) {
+  const int lane = threadIdx.x & 31;
+  const int w = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (w >= Wn) return;
+  const int N = s.N, nd = s.n_det, stride = 3 + 3 * N, n3 = 3 * N;
+  const double* dw = det + (size_t)w * nd * 2 * stride;
+  double m = -INFINITY;
+  for (int p = lane; p < nd; p += 32) {
+    const double* u = dw + (size_t)(2 * p) * stride;
+    const double* d = u + stride;
+    if (s.ci[p] != 0.0 && u[1] != 0.0 && d[1] != 0.0) m = fmax(m, u[0] + d[0]);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  double S = 0;
+  if (m > -INFINITY)
+    for (int p = lane; p < nd; p += 32) {
+      const double* u = dw + (size_t)(2 * p) * stride;
+      const double* d = u + stride;
+      if (u[1] != 0.0 && d[1] != 0.0) S += s.ci[p] * u[1] * d[1] * exp(u[0] + d[0] - m);
+    }
+  S = wsum(S);
+  const double* gw = geo + (size_t)w * s.Ppair * 4;
+  double gam = 0, V = 0, lapg = 0;
+  for (int q = lane; q < s.Pee; q += 32) {
+    int a = 0, rem = q;
+    while (rem >= N - 1 - a) { rem -= N - 1 - a; ++a; }
+    const int b = a + 1 + rem;
+    const double d = gw[q * 4];
+    V += 1.0 / d;
+    if (s.use_gamma) {
+      const double c = ((a < s.n_up) == (b < s.n_up)) ? 0.25 : 0.5;
+      gam -= c / (1.0 + d);
+      const double e = 1.0 / (1.0 + d);
+      const double g1 = c * e * e, g2 = -2.0 * c * e * e * e;
+      lapg += 2.0 * (g2 + 2.0 * g1 / d);
+    }
+  }
+  for (int q = lane; q < s.Pen; q += 32) V -= s.Z[q % s.M] / gw[(s.Pee + q) * 4];
+  gam = wsum(gam);
+  V = wsum(V) + s.Vnn;
+  const R* J = Jj + (size_t)w * T;
+  int st = PN_WALKER_OK;
+  if (!(S != 0.0) || !(m > -INFINITY)) st = PN_WALKER_SINGULAR;
+  const double la = gam + (double)J[0] + m + log(fabs(S));
+  if (lane == 0) {
+    logabs[w] = la;
+    sign[w] = S > 0 ? 1.0 : (S < 0 ? -1.0 : 0.0);
+  }
+  if (!jet) {
+    if (st == PN_WALKER_OK && !isfinite(la)) st = PN_WALKER_NONFINITE;
+    if (status && lane == 0) status[w] = st;
+    return;
+  }
+  lapg = wsum(lapg);
+  double g[3] = {0, 0, 0}, sq = 0, lap0 = 0;
+  if (st == PN_WALKER_OK)
+    for (int p = 0; p < nd; ++p) {
+      const double* u = dw + (size_t)(2 * p) * stride;
+      const double* d = u + stride;
+      if (u[1] == 0.0 || d[1] == 0.0) continue;
+      const double om = s.ci[p] * u[1] * d[1] * exp(u[0] + d[0] - m) / S;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int t = lane + 32 * k;
+        if (t < n3) {
+          const double gt = u[3 + t] + d[3 + t];
+          g[k] += om * gt;
+          sq += om * gt * gt;
+        }
+      }
+      lap0 += om * (u[2] + d[2]);
+    }
+  double g2 = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) g2 += g[k] * g[k];
+  g2 = wsum(g2);
+  double lap = lap0 + wsum(sq) - g2 + (double)J[T - 1];
+  if (s.use_gamma) lap += lapg;
+  double gn = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int t = lane + 32 * k;
+    if (t >= n3) continue;
+    g[k] += (double)J[1 + t];
+    if (s.use_gamma) {
+      const int a = t / 3, x = t - 3 * a;
+      for (int b = 0; b < N; ++b) {
+        if (b == a) continue;
+        const int p = a < b ? pn_pair_index(a, b, N) : pn_pair_index(b, a, N);
+        const double* gg = gw + p * 4;
+        const double c = ((a < s.n_up) == (b < s.n_up)) ? 0.25 : 0.5;
+        const double e = 1.0 / (1.0 + gg[0]);
+        // gg holds (r_lo - r_hi)/d for the pair (lo, hi)
+        g[k] += (a < b ? 1.0 : -1.0) * c * e * e * gg[1 + x];
+      }
+    }
+    gn += g[k] * g[k];
+    if (grad_out) grad_out[(size_t)w * n3 + t] = g[k];
+  }
+  gn = wsum(gn);
+  const double E = -0.5 * (lap + gn) + V;
+  if (lane == 0) {
+    eloc[w] = E;
+    if (st == PN_WALKER_OK && !(isfinite(E) && isfinite(la))) st = PN_WALKER_NONFINITE;
+    if (status) status[w] = st;
+  }
+}
+
 }  // namespace pnk
 
 // ------------------------------------------------------------------ driver
@@ -814,9 +1108,11 @@ int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw
   if constexpr (sizeof(R) == 4) {
     // value passes (T == 1) use the PN_TC_VALUE bit, jet passes the group bit
     const int bit = T == 1 ? PN_TC_VALUE : grp;
-    if (s && (s->tensor_cores & bit) && pn_tc_supported(Nout))
-      return pn_linear_tc((const float*)X, ldx, (const float*)W, ldw, (const float*)b, (float*)Y, ldy, rows, Kd, Nout,
-                          T, acc, s->dev_err, st);
+    if (s && (s->tensor_cores & bit) && pn_tc_supported(Nout)) {
+      const int e = pn_linear_tc((const float*)X, ldx, (const float*)W, ldw, (const float*)b, (float*)Y, ldy, rows, Kd,
+                                 Nout, T, acc, s->dev_err, st);
+      if (e != PN_ENOTREADY) return e;  // else: the weight does not fit in shared memory, CUDA cores below
+    }
   }
   if constexpr (sizeof(R) == 4) {
     if (ldx % 4 == 0 && Kd % 4 == 0 && ((uintptr_t)X & 15) == 0) {
@@ -847,11 +1143,21 @@ int pn_network_layers(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn,
   const size_t groups = (size_t)Wn * s.N;
   const int rows = (int)(groups * T);
   PN_LAUNCH("k_features", st, k_features<R><<<nblk((size_t)Wn * s.Ppair * s.K, 256), 256, 0, st>>>(s, w.geo, Wn, jet, w.efeat));
-  PN_LAUNCH("k_init_x", st, k_init_x<R><<<nblk(groups * T * s.D, 256), 256, 0, st>>>(net.p + net.off.x0, w.X, groups, T, s.D));
+  // jet passes: the first layer's input is the constant x^(0), so its h is
+  // one row (k_h0_row, into the Xs scratch that the heads use later) and its
+  // receiving map writes X with x^(0) folded into the value rows' bias
+  const bool first_const = jet;
+  if (first_const)
+    PN_LAUNCH("k_h0_row", st, k_h0_row<R><<<nblk(s.Zd, 64), 64, 0, st>>>(net.p + net.off.x0, net.p + net.off.hW[0],
+                                                                        net.p + net.off.hb[0], s.D, s.Zd, w.Xs));
+  else
+    PN_LAUNCH("k_init_x", st, k_init_x<R><<<nblk(groups * T * s.D, 256), 256, 0, st>>>(net.p + net.off.x0, w.X, groups, T, s.D));
   for (int n = 0; n < s.L; ++n) {
-    if (int e = pn_linear<R>(&s, PN_TC_LAYERS, w.X, s.D, net.p + net.off.hW[n], s.Zd, net.p + net.off.hb[n], w.H, w.ldH, rows, s.D,
-                             s.Zd, T, 0, st))
-      return e;
+    const bool hc = first_const && n == 0;
+    if (!hc)
+      if (int e = pn_linear<R>(&s, PN_TC_LAYERS, w.X, s.D, net.p + net.off.hW[n], s.Zd, net.p + net.off.hb[n], w.H, w.ldH,
+                               rows, s.D, s.Zd, T, 0, st))
+        return e;
     // jet filters on pair-row tiles for large batches; below about 128 k pair
     // rows the per-row kernel's many small blocks hide latency better (Be,
     // 4096 walkers x 10 pairs: 0.154 ms per pass per-row, 0.174 ms tiled)
@@ -868,17 +1174,40 @@ int pn_network_layers(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn,
       // bytes that must cross HBM: the h rows and filter jets read once,
       // the message rows written once
       const double bytes = (double)sizeof(R) * Wn * ((double)s.N * T * s.Zd + 3.0 * s.Ppair * s.Zd + 3.0 * s.N * T * s.Zd);
-      PN_LAUNCH_W("k_message", st, bytes,
-                  k_message_c<R><<<nblk(nthr, 256), 256, 0, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H, w.ldH, Wn,
-                                                                   T, w.Zb, w.ldZ));
+      // staged per-walker kernel where Zd tiles by 32 and the walker's rows fit
+      const size_t mw_bytes = sizeof(R) * ((size_t)(hc ? 1 : s.N * T) * MSGW_ZT + (size_t)s.Ppair * 3 * MSGW_ZT +
+                                           (size_t)s.Ppair * 5);
+      const bool staged = s.Zd % MSGW_ZT == 0 && s.N <= MSGW_NMAX && mw_bytes <= 160 * 1024 && !s.msg_per_row;
+      if (staged) {
+        const unsigned grid = (unsigned)((size_t)Wn * (s.Zd / MSGW_ZT));
+        if (hc) {
+          PN_CUDA(pn_allow_max_smem(k_message_w<R, true>));
+          PN_LAUNCH_W("k_message", st, bytes,
+                      (k_message_w<R, true><<<grid, s.N * 32, mw_bytes, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.Xs,
+                                                                             0, Wn, T, w.Zb, w.ldZ)));
+        } else {
+          PN_CUDA(pn_allow_max_smem(k_message_w<R, false>));
+          PN_LAUNCH_W("k_message", st, bytes,
+                      (k_message_w<R, false><<<grid, s.N * 32, mw_bytes, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H,
+                                                                              w.ldH, Wn, T, w.Zb, w.ldZ)));
+        }
+      } else if (hc) {
+        PN_LAUNCH_W("k_message", st, bytes,
+                    (k_message_c<R, true><<<nblk(nthr, 256), 256, 0, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.Xs, 0,
+                                                                           Wn, T, w.Zb, w.ldZ)));
+      } else {
+        PN_LAUNCH_W("k_message", st, bytes,
+                    (k_message_c<R, false><<<nblk(nthr, 256), 256, 0, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H,
+                                                                            w.ldH, Wn, T, w.Zb, w.ldZ)));
+      }
     } else {
       PN_LAUNCH("k_message", st,
                 k_message<R><<<(unsigned)((size_t)Wn * s.N), std::min(256, (T * s.Zd + 31) / 32 * 32),
                                (size_t)(s.N - 1 + s.M) * 5 * sizeof(R), st>>>(
                     s, net.p + net.off.Y, w.geo, w.wjet, w.H, w.ldH, Wn, T, w.Zb, w.ldZ));
     }
-    if (int e = pn_linear<R>(&s, PN_TC_LAYERS, w.Zb, w.ldZ, net.Gcat + (size_t)n * 3 * s.Zd * s.D, s.D, net.Gb + (size_t)n * s.D, w.X,
-                             s.D, rows, 3 * s.Zd, s.D, T, 1, st))
+    if (int e = pn_linear<R>(&s, PN_TC_LAYERS, w.Zb, w.ldZ, net.Gcat + (size_t)n * 3 * s.Zd * s.D, s.D,
+                             hc ? net.Gbx0 : net.Gb + (size_t)n * s.D, w.X, s.D, rows, 3 * s.Zd, s.D, T, hc ? 0 : 1, st))
       return e;
   }
   return PN_OK;
@@ -947,26 +1276,48 @@ int pn_forward_chunk(const DevSys& s, const DevNet<R>& net, Work<R>& w, const do
   if (int e = pn_network_layers<R>(s, net, w, Wn, T, jet, st)) return e;
   if (int e = pn_heads<R>(s, net, w, Wn, T, st)) return e;
   if (int e = pn_slater<R>(s, w.phi, w.F, Wn, T, jet, w.det, st)) return e;
-  PN_LAUNCH("k_combine", st, k_combine<R><<<nblk(Wn, 64), 64, 0, st>>>(s, w.geo, w.det, w.Jj, Wn, T, jet, w.out_logabs, w.out_sign, w.out_eloc,
-                                            w.out_status, w.out_grad));
+  PN_LAUNCH("k_combine", st, k_combine_w<R><<<nblk((size_t)Wn * 32, 128), 128, 0, st>>>(s, w.geo, w.det, w.Jj, Wn, T, jet,
+                                                                                     w.out_logabs, w.out_sign,
+                                                                                     w.out_eloc, w.out_status,
+                                                                                     w.out_grad));
   return PN_OK;
 }
 
-// Second evaluation of a guarded mixed chunk: the heads again with the
-// other unit for their linear maps (their rounding differs), the
+// Relative perturbation of every element by +-eta, the sign a hash of the
+// element's index (a deterministic stand-in for rounding noise).
+__global__ void k_perturb(float* __restrict__ A, size_t n, float eta) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t h = (uint32_t)i * 0x9E3779B1u;
+  h ^= h >> 15;
+  h *= 0x85EBCA77u;
+  h ^= h >> 13;
+  A[i] *= (h & 1u) ? 1.0f + eta : 1.0f - eta;
+}
+
+// Second evaluation of a guarded mixed chunk.  Probe 0: the heads again
+// with the other unit for their linear maps (their rounding differs), the
 // determinants of the new backflow, and E_loc with the new Jastrow factor.
-// ln|psi| and sign of this pass go to scratch (the proposal buffers), E_loc
-// to e_probe; the first pass's outputs stay in w.
+// Probe 1: the first pass's backflow and Jastrow jets perturbed by
+// +-2^-19 relative, then the determinants and E_loc again.  ln|psi| and
+// sign of this pass go to scratch (the proposal buffers), E_loc to e_probe;
+// the first pass's outputs stay in w.
 int pn_probe_heads_chunk(const DevSys& s, const DevNet<float>& net, Work<float>& w, int Wn, double* e_probe,
                          cudaStream_t st) {
   if (Wn <= 0) return PN_OK;
   const int T = 3 * s.N + 2;
-  DevSys s2 = s;
-  s2.tensor_cores ^= PN_TC_HEADS;
-  if (int e = pn_heads<float>(s2, net, w, Wn, T, st)) return e;
+  if (s.guard_probe == 1) {
+    const size_t nf = (size_t)Wn * s.N * T * s.n_orb, nj = (size_t)Wn * T;
+    PN_LAUNCH("k_perturb", st, k_perturb<<<nblk(nf, 256), 256, 0, st>>>(w.F, nf, 1.9073486e-6f));
+    PN_LAUNCH("k_perturb", st, k_perturb<<<nblk(nj, 256), 256, 0, st>>>(w.Jj, nj, 1.9073486e-6f));
+  } else {
+    DevSys s2 = s;
+    s2.tensor_cores ^= PN_TC_HEADS;
+    if (int e = pn_heads<float>(s2, net, w, Wn, T, st)) return e;
+  }
   if (int e = pn_slater<float>(s, w.phi, w.F, Wn, T, 1, w.det, st)) return e;
-  PN_LAUNCH("k_combine", st, k_combine<float><<<nblk(Wn, 64), 64, 0, st>>>(s, w.geo, w.det, w.Jj, Wn, T, 1, w.lp_prop,
-                                                                          w.r_prop, e_probe, nullptr, nullptr));
+  PN_LAUNCH("k_combine", st, k_combine_w<float><<<nblk((size_t)Wn * 32, 128), 128, 0, st>>>(
+                                 s, w.geo, w.det, w.Jj, Wn, T, 1, w.lp_prop, w.r_prop, e_probe, nullptr, nullptr));
   return PN_OK;
 }
 

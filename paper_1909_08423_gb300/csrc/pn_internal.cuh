@@ -56,6 +56,20 @@ void pn_prof_work(const char* name, double work);
     PN_CHECK_LAUNCH();                   \
   } while (0)
 
+// Allow a kernel every dynamic shared-memory size up to the device's
+// opt-in limit.  Every caller sets the same value, so host threads that
+// launch one kernel with different sizes (serving slots of different
+// systems) cannot lower the limit under one another's launch.
+template <typename F>
+inline cudaError_t pn_allow_max_smem(F* f) {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (cudaError_t e = cudaFuncGetAttributes(&fa, f)) return e;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, v - (int)fa.sharedSizeBytes);
+}
+
 // ------------------------------------------------------------- parameters
 // Offsets (in elements) of every tensor inside the flat parameter vector.
 struct NetOff {
@@ -125,6 +139,8 @@ struct DevSys {
   int tab_wstride;        // doubles of shared memory per warp of the table kernel
   int tab_nv[2];          // virtual orbitals per spin
   int tab_k3[2];          // sum over determinants of k^3 per spin
+  int guard_probe;        // second evaluation of the guard: 0 heads on the other unit, 1 perturbed jets
+  int msg_per_row;        // 1: jet messages by the per-row kernel even where the staged one applies
   int no_table;           // 1: jet determinants block by block even where a table exists;
                           // 2: the table kernel with every walker on its direct fallback
   int fused_sampler;      // 1: Metropolis through the fused tile kernel when it fits
@@ -218,6 +234,7 @@ struct DevNet {
   const R* p;      // flat parameter vector in R
   const R* Gcat;   // [L][3 Zd][D]  same, anti, nuc receiving maps stacked
   const R* Gb;     // [L][D]        sum of the three receiving biases
+  const R* Gbx0;   // [D]           first layer's summed bias + x^(0)
   const R* wpack;  // sampler weight blocks, 16-byte aligned (see StageTab)
   NetOff off;
   StageTab stab;
@@ -267,6 +284,8 @@ struct pn_system_s {
   double* Gb64;
   float* Gcat32;
   float* Gb32;
+  double* Gbx0_64;
+  float* Gbx0_32;
   void* work_mem;
   size_t work_bytes;
   StageTab stab64, stab32;  // packed sampler weights per precision

@@ -908,12 +908,12 @@ int pn_run_metropolis_fused(const DevSys& s, const DevNet<R>& net, double* r, do
     const int smem = staged ? wbuf_off + 2 * wbuf_bytes : (int)(WL.bytes * warps);
     const int blocks = (W + warps - 1) / warps;
     if (staged) {
-      PN_CUDA(cudaFuncSetAttribute(k_metropolis_warp<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      PN_CUDA(pn_allow_max_smem(k_metropolis_warp<R, true>));
       PN_LAUNCH_W("k_metropolis_warp", st, (double)W * n_steps * pn_value_pass_flops(s),
                 k_metropolis_warp<R, true><<<blocks, warps * 32, smem, st>>>(
                     s, net, WL, stt, wp, wbuf_off, wbuf_bytes, r, lp, W, walker0, n_steps, sigma, seed, step0, n_acc));
     } else {
-      PN_CUDA(cudaFuncSetAttribute(k_metropolis_warp<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      PN_CUDA(pn_allow_max_smem(k_metropolis_warp<R, false>));
       PN_LAUNCH_W("k_metropolis_warp", st, (double)W * n_steps * pn_value_pass_flops(s),
                 k_metropolis_warp<R, false><<<blocks, warps * 32, smem, st>>>(
                     s, net, WL, stt, wp, 0, 0, r, lp, W, walker0, n_steps, sigma, seed, step0, n_acc));
@@ -924,7 +924,7 @@ int pn_run_metropolis_fused(const DevSys& s, const DevNet<R>& net, double* r, do
   const int WT = pn_fused_tile<R>(s, W, &smem);
   if (WT == 0) return PN_ENOTREADY;  // caller takes the staged path
   const Layout L = make_layout<R>(s, WT);
-  PN_CUDA(cudaFuncSetAttribute(k_metropolis_fused<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  PN_CUDA(pn_allow_max_smem(k_metropolis_fused<R>));
   const int tiles = (W + WT - 1) / WT;
   PN_LAUNCH_W("k_metropolis_fused", st, (double)W * n_steps * pn_value_pass_flops(s),
             k_metropolis_fused<R><<<tiles, 256, smem, st>>>(s, net, L, r, lp, W, walker0, n_steps, sigma, seed, step0,

@@ -825,7 +825,7 @@ int pn_run_metropolis_tc(const DevSys& s, const DevNet<float>& net, double* r, d
   const int widest = std::max(std::max(s.D, s.Hw), std::max(s.Zd, (s.n_orb + 15) / 16 * 16));
   if (3 * widest > 256) return PN_ENOTREADY;
   const uint32_t cols = 512u;
-  PN_CUDA(cudaFuncSetAttribute(k_metropolis_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes));
+  PN_CUDA(pn_allow_max_smem(k_metropolis_tc));
   const int blocks = (W + WT - 1) / WT;
   PN_LAUNCH_W("k_metropolis_tc", st, (double)W * n_steps * pn_value_pass_flops(s),
             k_metropolis_tc<<<blocks, NT, L.bytes, st>>>(s, net, net.tcst, net.tcpack, L, r, lp, W, walker0, n_steps,

@@ -16,8 +16,10 @@
 // The same quantities as the direct per-block kernel, exactly in exact
 // arithmetic, for about an eighth of the float64 work of the N2-shaped
 // system (32 determinants of 7 x 7 blocks).  T carries rounding amplified by
-// the condition of A_0, so a walker whose reference block has a pivot
-// ratio beyond kCondMax is computed directly, block by block.
+// the condition of A_0 (the derivatives about its square, through the
+// cancellation of the reference and minor terms), so a walker whose
+// reference block has a 1-norm condition number beyond kCondMax is computed
+// directly, block by block.
 //
 // One warp per (walker, spin); the warp's matrices live in shared memory.
 #include <math.h>
@@ -29,7 +31,7 @@
 namespace {
 
 constexpr int TW = 4;               // warps per block
-constexpr double kCondMax = 1e4;    // largest pivot ratio of A_0 for the table method
+constexpr double kCondMax = 1e3;    // largest 1-norm condition number of A_0 for the table method
 
 inline unsigned nblk(size_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(TW * 32) k_slater_table(DevSys s, const double
   for (int q = lane; q < n * n; q += 32) LU[q] = Af[(q / n) * ncol + q % n];
   __syncwarp();
   // LU of the reference block, rows spread over the lanes
-  double ld = 0, sgn = 1, pmin = INFINITY, pmax = 0;
+  double ld = 0, sgn = 1;
   bool sing = false;
   for (int c = 0; c < n; ++c) {
     double v = (lane >= c && lane < n) ? fabs(LU[lane * n + c]) : -1.0;
@@ -163,8 +165,6 @@ __global__ void __launch_bounds__(TW * 32) k_slater_table(DevSys s, const double
     const double piv = LU[c * n + c];
     if (piv < 0) sgn = -sgn;
     ld += log(fabs(piv));
-    pmin = fmin(pmin, fabs(piv));
-    pmax = fmax(pmax, fabs(piv));
     if (lane > c && lane < n) {
       const double f = LU[lane * n + c] / piv;
       LU[lane * n + c] = f;
@@ -172,14 +172,8 @@ __global__ void __launch_bounds__(TW * 32) k_slater_table(DevSys s, const double
     }
     __syncwarp();
   }
-  if (sing || pmax > kCondMax * pmin || s.no_table == 2) {
-    // ill-conditioned reference block: every determinant directly
-    for (int p = lane; p < nd; p += 32)
-      pn_slater_block<R, PN_TAB_NMAX>(s, phw, Fw, p, sg, T, 1, outw + (size_t)(2 * p + sg) * stride);
-    return;
-  }
   // M = A_0^-1, one column per lane
-  if (lane < n) {
+  if (!sing && lane < n) {
     double y[PN_TAB_NMAX];
     for (int r = 0; r < n; ++r) {
       double v = perm[r] == lane ? 1.0 : 0.0;
@@ -194,6 +188,23 @@ __global__ void __launch_bounds__(TW * 32) k_slater_table(DevSys s, const double
     for (int r = 0; r < n; ++r) M[r * n + lane] = y[r];
   }
   __syncwarp();
+  // 1-norm condition number of A_0: max column sums of |A_0| and |M|
+  double ca = 0, cm = 0;
+  if (!sing && lane < n)
+    for (int r = 0; r < n; ++r) {
+      ca += fabs(Af[r * ncol + lane]);
+      cm += fabs(M[r * n + lane]);
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    ca = fmax(ca, __shfl_xor_sync(0xffffffffu, ca, o));
+    cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+  }
+  if (sing || !(ca * cm <= kCondMax) || s.no_table == 2) {
+    // ill-conditioned reference block: every determinant directly
+    for (int p = lane; p < nd; p += 32)
+      pn_slater_block<R, PN_TAB_NMAX>(s, phw, Fw, p, sg, T, 1, outw + (size_t)(2 * p + sg) * stride);
+    return;
+  }
   for (int q = lane; q < n * nv; q += 32) {
     const int a = q / nv, v = q - a * nv;
     double x = 0;
@@ -343,7 +354,7 @@ int pn_slater_table_launch(const DevSys& s, const double* phi, const R* F, int W
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const size_t smem = (size_t)TW * s.tab_wstride * sizeof(double);
   if (smem > (size_t)maxsm) return PN_ENOTREADY;
-  PN_CUDA(cudaFuncSetAttribute(k_slater_table<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  PN_CUDA(pn_allow_max_smem(k_slater_table<R>));
   PN_LAUNCH_W("k_slater", st, Wn * pn_slater_table_flops(s),
               k_slater_table<R><<<nblk((size_t)2 * Wn, TW), TW * 32, smem, st>>>(s, phi, F, Wn, T, det));
   return PN_OK;

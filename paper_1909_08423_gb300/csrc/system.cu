@@ -314,6 +314,13 @@ static int upload_params(pn_system_s* s, const double* hp_user) {
   }
   PN_CUDA(cudaMemcpy(s->Gcat64, G.data(), G.size() * 8, cudaMemcpyHostToDevice));
   PN_CUDA(cudaMemcpy(s->Gb64, Gb.data(), Gb.size() * 8, cudaMemcpyHostToDevice));
+  {
+    std::vector<double> gx(d.D);
+    for (int k = 0; k < d.D; ++k) gx[k] = (d.L > 0 ? Gb[k] : 0.0) + hp[o.x0 + k];
+    std::vector<float> gx32(gx.begin(), gx.end());
+    PN_CUDA(cudaMemcpy(s->Gbx0_64, gx.data(), gx.size() * 8, cudaMemcpyHostToDevice));
+    PN_CUDA(cudaMemcpy(s->Gbx0_32, gx32.data(), gx32.size() * 4, cudaMemcpyHostToDevice));
+  }
   std::vector<float> G32(G.begin(), G.end()), Gb32(Gb.begin(), Gb.end());
   PN_CUDA(cudaMemcpy(s->Gcat32, G32.data(), G32.size() * 4, cudaMemcpyHostToDevice));
   PN_CUDA(cudaMemcpy(s->Gb32, Gb32.data(), Gb32.size() * 4, cudaMemcpyHostToDevice));
@@ -448,7 +455,7 @@ static size_t wpack_elems(const DevSys& d) {
 template <>
 DevNet<double> pn_devnet<double>(pn_system_s* s) {
   DevNet<double> n;
-  n.p = s->p64; n.Gcat = s->Gcat64; n.Gb = s->Gb64; n.off = s->off;
+  n.p = s->p64; n.Gcat = s->Gcat64; n.Gb = s->Gb64; n.Gbx0 = s->Gbx0_64; n.off = s->off;
   n.wpack = s->wpack64; n.stab = s->stab64;
   n.tcpack = nullptr; n.tcst = nullptr; n.tc_n = 0; n.tc_max_bytes = 0;
   return n;
@@ -456,7 +463,7 @@ DevNet<double> pn_devnet<double>(pn_system_s* s) {
 template <>
 DevNet<float> pn_devnet<float>(pn_system_s* s) {
   DevNet<float> n;
-  n.p = s->p32; n.Gcat = s->Gcat32; n.Gb = s->Gb32; n.off = s->off;
+  n.p = s->p32; n.Gcat = s->Gcat32; n.Gb = s->Gb32; n.Gbx0 = s->Gbx0_32; n.off = s->off;
   n.wpack = s->wpack32; n.stab = s->stab32;
   n.tcpack = s->tcpack; n.tcst = s->tcst_dev; n.tc_n = s->tcst.n; n.tc_max_bytes = s->tcst.max_bytes;
   return n;
@@ -768,6 +775,8 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   s->Gcat64 = dev_upload<double>(s, nullptr, gsz, &err);
   s->Gb64 = dev_upload<double>(s, nullptr, (size_t)std::max(d->L, 1) * d->D, &err);
   s->Gcat32 = dev_upload<float>(s, nullptr, gsz, &err);
+  s->Gbx0_64 = dev_upload<double>(s, nullptr, (size_t)d->D, &err);
+  s->Gbx0_32 = dev_upload<float>(s, nullptr, (size_t)d->D, &err);
   s->Gb32 = dev_upload<float>(s, nullptr, (size_t)std::max(d->L, 1) * d->D, &err);
   s->wpack64 = dev_upload<double>(s, nullptr, wpack_elems(ds), &err);
   s->wpack32 = dev_upload<float>(s, nullptr, wpack_elems(ds), &err);
@@ -812,7 +821,8 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
     delete s;
     return PN_EINVAL;
   }
-  // mixed handles: the local-energy guard, on by default with tau = 2e-5 Ha
+  // mixed handles: the local-energy guard, on by default (perturbed jets,
+  // tau = 5e-5 Ha)
   if (d->precision == PN_MIXED) {
     const int cap = std::min(s->Wc, 256);
     const size_t gb = pn_guard_bytes(ds, s->Wc, cap);
@@ -826,7 +836,8 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
     }
     s->guard = pn_carve_guard(ds, s->Wc, cap, s->guard_mem);
     s->guard.net64 = pn_devnet<double>(s);
-    s->guard.tau = 2e-5;
+    s->guard.tau = 5e-5;
+    s->ds.guard_probe = 1;
     PN_CUDA(cudaMemset(s->guard.n_total, 0, 8));
   }
   *out = s;

@@ -20,26 +20,32 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "pn_internal.cuh"
 
 namespace {
 
-constexpr int TC_M = 128;    // rows per CTA (UMMA M)
-constexpr int TC_KC = 32;    // K elements staged per round
-constexpr int TC_THREADS = 128;
-constexpr uint32_t TC_LBO = 128;              // bytes between core matrices along K
-constexpr uint32_t TC_SBO = TC_KC / 8 * 128;  // bytes between 8-row groups (8 bf16 per core row)
-constexpr int TC_PIECES = 3;
+constexpr int TC_M = 128;       // rows per tile (UMMA M)
+constexpr int TC_KC = 32;       // k-slice per pipeline stage
+constexpr int TC_NPROD = 4;     // producer warps
+constexpr int TC_NEPI = 4;      // epilogue warps
+constexpr int TC_WMMA = TC_NPROD;                      // warp 4 issues the MMAs
+constexpr int TC_THREADS = 32 * (TC_NPROD + 1 + TC_NEPI);
+constexpr uint32_t TC_LBO = 128;                       // bytes between core matrices along K
+constexpr uint32_t TC_SBO_A = TC_KC / 8 * 128;         // bytes between 8-row groups of an A stage
+constexpr uint32_t TC_STAGE = 3u * TC_M * TC_KC * 2;   // three bf16 pieces of a 128 x 32 slice
+constexpr int TC_SPIN = 1 << 22;                       // polls per bounded wait
 
 __device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Shared-memory matrix descriptor (sm_100 family): start address, leading
 // and stride byte offsets (all >> 4), version 1, no swizzle.
-__device__ inline uint64_t smem_desc(uint32_t saddr) {
+__device__ inline uint64_t smem_desc(uint32_t saddr, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)((TC_LBO >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((TC_SBO >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
   return d;
 }
@@ -50,171 +56,294 @@ __host__ __device__ inline uint32_t bf16_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// byte offset of bf16 element (row, k) inside a staged tile
-__device__ inline uint32_t tile_off(int row, int k) {
-  return (uint32_t)(row >> 3) * TC_SBO + (uint32_t)(k >> 3) * TC_LBO + (uint32_t)(row & 7) * 16u +
-         (uint32_t)(k & 7) * 2u;
+// byte offset of bf16 element (row, k) in a K-major tile whose 8-row groups
+// are sbo bytes apart
+__device__ inline uint32_t tile_off(int row, int k, uint32_t sbo) {
+  return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 3) * TC_LBO + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
 }
 
 // a -> three bf16 pieces, nearest rounding at each stage
-__device__ inline void split3(float a, unsigned short p[3]) {
+__device__ inline void split3(float a, unsigned short& p0, unsigned short& p1, unsigned short& p2) {
   const __nv_bfloat16 h0 = __float2bfloat16_rn(a);
   const float r1 = a - __bfloat162float(h0);
   const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
   const float r2 = r1 - __bfloat162float(h1);
   const __nv_bfloat16 h2 = __float2bfloat16_rn(r2);
-  p[0] = __bfloat16_as_ushort(h0);
-  p[1] = __bfloat16_as_ushort(h1);
-  p[2] = __bfloat16_as_ushort(h2);
+  p0 = __bfloat16_as_ushort(h0);
+  p1 = __bfloat16_as_ushort(h1);
+  p2 = __bfloat16_as_ushort(h2);
 }
 
-__device__ inline bool mbar_try(uint32_t bar, uint32_t phase) {
+__device__ inline bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(bar), "r"(phase)
+      : "r"(bar), "r"(parity)
       : "memory");
   return ok != 0;
 }
 
-__device__ inline bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
-  for (int it = 0; it < (1 << 22); ++it)
-    if (mbar_try(bar, phase)) return true;
+__device__ inline void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait that also gives up once another role of the CTA has given
+// up (*abort set); returns false then.
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  for (int it = 0; it < TC_SPIN; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63) == 63 && *abort) return false;
+  }
+  *abort = 1;
   return false;
 }
 
-__global__ void __launch_bounds__(TC_THREADS) k_linear_tc(const float* __restrict__ X, int ldx,
-                                                          const float* __restrict__ Wt, int ldw,
-                                                          const float* __restrict__ bias, float* __restrict__ Y,
-                                                          int ldy, int rows, int K, int Nout, int Npad, int T,
-                                                          int accumulate, uint32_t tmem_cols,
-                                                          int* __restrict__ err) {
+// Y (=|+=) X W + b on value rows; see the file comment.  VX: X rows are
+// 16-byte aligned (float4 loads).
+template <bool VX>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __restrict__ X, int ldx,
+                                                              const float* __restrict__ Wt, int ldw,
+                                                              const float* __restrict__ bias, float* __restrict__ Y,
+                                                              int ldy, int rows, int K, int Kp, int Nout, int Npad,
+                                                              int T, int accumulate, int nstage, uint32_t tmem_cols,
+                                                              int vy, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
-  // pieces 0..2 of the A tile (128 x KC bf16), then of the B tile (Npad x KC)
-  const uint32_t a_bytes = TC_M * TC_KC * 2, b_bytes = (uint32_t)Npad * TC_KC * 2;
-  unsigned char* sA = smem;
-  unsigned char* sB = smem + TC_PIECES * a_bytes;
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t bars[2 * 8 + 4 + 1];  // full[8], empty[8], acc_full[2], acc_empty[2], drain
   __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * TC_M;
+  const uint32_t b_piece = (uint32_t)Npad * Kp * 2;         // bytes of one weight piece
+  const uint32_t sbo_b = (uint32_t)(Kp / 8) * 128u;
+  unsigned char* sB = smem;                                  // 3 weight pieces [Npad][Kp]
+  unsigned char* sA = smem + 3 * b_piece;                    // nstage x 3 pieces [128][KC]
+  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[8]);
+  const uint32_t accf0 = smem_u32(&bars[16]), acce0 = smem_u32(&bars[18]), drain = smem_u32(&bars[20]);
+  const int ntiles = (rows + TC_M - 1) / TC_M;
+  const int nk = Kp / TC_KC;
 
-  if (warp == 0) {
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < nstage; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * s), "r"(TC_NPROD));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * s));
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(accf0 + 8 * b));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(acce0 + 8 * b), "r"(TC_NEPI));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(drain));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == TC_WMMA) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                  "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;");
+  // the weight's three pieces, once per CTA: B is [Npad][Kp] K-major
+  for (int idx = tid; idx < Npad * Kp; idx += TC_THREADS) {
+    const int n = idx / Kp, k = idx - n * Kp;
+    const float b = (n < Nout && k < K) ? Wt[(size_t)k * ldw + n] : 0.0f;
+    unsigned short p0, p1, p2;
+    split3(b, p0, p1, p2);
+    const uint32_t off = tile_off(n, k, sbo_b);
+    *(unsigned short*)(sB + off) = p0;
+    *(unsigned short*)(sB + b_piece + off) = p1;
+    *(unsigned short*)(sB + 2 * b_piece + off) = p2;
   }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t bar = smem_u32(&mbar);
-  const uint32_t idesc = bf16_idesc(TC_M, Npad);
-  uint32_t phase = 0;
-  bool ok = true;
+  volatile int* abort = &abort_flag;
 
-  for (int k0 = 0; k0 < K && ok; k0 += TC_KC) {
-    // stage A (128 x KC) and B (Npad x KC, from W[k][n]) as three bf16 pieces
-    for (int idx = tid; idx < TC_M * TC_KC; idx += TC_THREADS) {
-      const int row = idx / TC_KC, k = idx % TC_KC;
-      const int gr = m0 + row, gk = k0 + k;
-      const float a = (gr < rows && gk < K) ? X[(size_t)gr * ldx + gk] : 0.0f;
-      unsigned short p[3];
-      split3(a, p);
-      const uint32_t off = tile_off(row, k);
-      for (int q = 0; q < TC_PIECES; ++q) *(unsigned short*)(sA + q * a_bytes + off) = p[q];
+  if (warp < TC_NPROD) {
+    // ---------------------------------------------------------- producers
+    const int p = tid;  // 0..127
+    int g = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int r0 = tile * TC_M;
+      for (int kc = 0; kc < nk; ++kc, ++g) {
+        const int s = g % nstage;
+        if (!mbar_wait(empty0 + 8 * s, ((g / nstage) & 1) ^ 1, abort)) goto prod_done;
+        unsigned char* st = sA + (size_t)s * TC_STAGE;
+        const int k0 = kc * TC_KC;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int idx = p + 128 * j;        // (row, 8-wide k group)
+          const int row = idx >> 2, gk = (idx & 3) * 8;
+          const int gr = r0 + row;
+          float v[8];
+          if (VX && gr < rows && k0 + gk + 8 <= K) {
+            const float4* src = (const float4*)(X + (size_t)gr * ldx + k0 + gk);
+            const float4 a = src[0], b = src[1];
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int k = k0 + gk + e;
+              v[e] = (gr < rows && k < K) ? X[(size_t)gr * ldx + k] : 0.0f;
+            }
+          }
+          uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            unsigned short a0, a1, a2, b0, b1, b2;
+            split3(v[2 * e], a0, a1, a2);
+            split3(v[2 * e + 1], b0, b1, b2);
+            w0[e] = (uint32_t)a0 | ((uint32_t)b0 << 16);
+            w1[e] = (uint32_t)a1 | ((uint32_t)b1 << 16);
+            w2[e] = (uint32_t)a2 | ((uint32_t)b2 << 16);
+          }
+          const uint32_t off = tile_off(row, gk, TC_SBO_A);
+          *(uint4*)(st + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+          *(uint4*)(st + TC_M * TC_KC * 2 + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+          *(uint4*)(st + 2 * TC_M * TC_KC * 2 + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(full0 + 8 * s);
+      }
     }
-    for (int idx = tid; idx < Npad * TC_KC; idx += TC_THREADS) {
-      const int n = idx % Npad, k = idx / Npad;
-      const int gk = k0 + k;
-      const float b = (n < Nout && gk < K) ? Wt[(size_t)gk * ldw + n] : 0.0f;
-      unsigned short p[3];
-      split3(b, p);
-      const uint32_t off = tile_off(n, k);
-      for (int q = 0; q < TC_PIECES; ++q) *(unsigned short*)(sB + q * b_bytes + off) = p[q];
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+  prod_done:;
+  } else if (warp == TC_WMMA) {
+    // --------------------------------------------------------------- MMA
+    if (lane == 0) {
+      const uint32_t idesc = bf16_idesc(TC_M, Npad);
+      const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
       // (A piece, B piece) pairs whose weight reaches 2^-16, smallest first
       const int pa[6] = {1, 2, 0, 1, 0, 0};
       const int pb[6] = {1, 0, 2, 0, 1, 0};
-      for (int s = 0; s < TC_KC / 16; ++s) {
-        const uint32_t step = (uint32_t)s * 2u * TC_LBO;  // 16 bf16 = two core matrices along K
-        for (int t = 0; t < 6; ++t) {
-          const uint64_t da = smem_desc(a0 + pa[t] * a_bytes + step);
-          const uint64_t db = smem_desc(b0 + pb[t] * b_bytes + step);
-          const uint32_t acc_in = (k0 == 0 && s == 0 && t == 0) ? 0u : 1u;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-              "l"(da), "l"(db), "r"(idesc), "r"(acc_in));
+      int g = 0, it = 0;
+      bool issued = false;
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int buf = it & 1;
+        if (!mbar_wait(acce0 + 8 * buf, ((it >> 1) & 1) ^ 1, abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t dt = tmem + (uint32_t)(buf * Npad);
+        bool ok = true;
+        for (int kc = 0; kc < nk; ++kc, ++g) {
+          const int s = g % nstage;
+          if (!mbar_wait(full0 + 8 * s, (g / nstage) & 1, abort)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t a_st = a_base + (uint32_t)s * TC_STAGE;
+          for (int ks = 0; ks < TC_KC / 16; ++ks) {
+            const uint32_t a_step = (uint32_t)ks * 2u * TC_LBO;
+            const uint32_t b_step = (uint32_t)(kc * (TC_KC / 16) + ks) * 2u * TC_LBO;
+            for (int q = 0; q < 6; ++q) {
+              const uint64_t da = smem_desc(a_st + pa[q] * (TC_M * TC_KC * 2) + a_step, TC_SBO_A);
+              const uint64_t db = smem_desc(b_base + pb[q] * b_piece + b_step, sbo_b);
+              const uint32_t acc_in = (kc == 0 && ks == 0 && q == 0) ? 0u : 1u;
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                  "l"(da), "l"(db), "r"(idesc), "r"(acc_in));
+            }
+          }
+          issued = true;
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           empty0 + 8 * s)
+                       : "memory");
+        }
+        if (!ok) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(accf0 + 8 * buf)
+                     : "memory");
+      }
+      // every MMA issued has completed before the TMEM is freed
+      if (issued) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(drain)
+                     : "memory");
+        for (int k = 0; k < TC_SPIN && !mbar_try(drain, 0); ++k) {
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                   : "memory");
     }
-    ok = mbar_wait_bounded(bar, phase);
-    phase ^= 1u;
-    __syncthreads();
-  }
-  if (!ok) {
-    if (tid == 0) atomicExch(err, 1);
-    mbar_wait_bounded(bar, phase ^ 1u);  // give in-flight MMAs a last bounded chance
+    __syncwarp();
   } else {
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 = rows m0 + 32w + lane,
-    // 16 columns at a time, and writes them out through a shared-memory
-    // transpose so that each store instruction covers whole row segments
-    float* tr = (float*)smem + warp * 32 * 17;  // staging area is free now
-    for (int c0 = 0; c0 < Npad; c0 += 16) {
-      uint32_t v[16];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-          "%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    // ---------------------------------------------------------- epilogue
+    const int quarter = warp & 3;  // TMEM lanes 32 quarter .. 32 quarter + 31
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const int buf = it & 1;
+      if (!mbar_wait(accf0 + 8 * buf, (it >> 1) & 1, abort)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int row = tile * TC_M + quarter * 32 + lane;
+      const bool val = (row % T) == 0;
+      for (int c0 = 0; c0 < Npad; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * Npad + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < rows) {
+          float* yr = Y + (size_t)row * ldy;
+          if (vy && c0 + 16 <= Nout) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) tr[lane * 17 + j] = __uint_as_float(v[j]);
-      __syncwarp();
-      const int jj = lane & 15;
-      const int col = c0 + jj;
-      for (int rr = lane >> 4; rr < 32; rr += 2) {
-        const int row = m0 + warp * 32 + rr;
-        if (row < rows && col < Nout) {
-          const float y = tr[rr * 17 + jj] + ((bias && (row % T) == 0) ? bias[col] : 0.0f);
-          float* dst = Y + (size_t)row * ldy + col;
-          *dst = accumulate ? *dst + y : y;
+            for (int j = 0; j < 16; j += 4) {
+              float4 y = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
+                                     __uint_as_float(v[j + 3]));
+              if (bias && val) {
+                y.x += bias[c0 + j]; y.y += bias[c0 + j + 1]; y.z += bias[c0 + j + 2]; y.w += bias[c0 + j + 3];
+              }
+              if (accumulate) {
+                const float4 o = *(const float4*)(yr + c0 + j);
+                y.x += o.x; y.y += o.y; y.z += o.z; y.w += o.w;
+              }
+              *(float4*)(yr + c0 + j) = y;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int col = c0 + j;
+              if (col < Nout) {
+                float y = __uint_as_float(v[j]) + ((bias && val) ? bias[col] : 0.0f);
+                if (accumulate) y += yr[col];
+                yr[col] = y;
+              }
+            }
+          }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
+      if (lane == 0) mbar_arrive(acce0 + 8 * buf);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+  if (abort_flag && tid == 0) atomicExch(err, 1);
+  if (warp == TC_WMMA) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+  }
 }
 
 int* g_tc_err = nullptr;  // device flag per process (allocated on first use)
 
-}  // namespace
-
-size_t pn_tc_smem_bytes(int Nout) {
+// Shared memory of a launch: the weight's pieces plus as many pipeline
+// stages (2..8) as fit; 0 if fewer than two fit.
+size_t tc_plan(int K, int Nout, int* Kp_out, int* nstage_out) {
+  const int Kp = ((K + TC_KC - 1) / TC_KC) * TC_KC;
   const int Npad = ((Nout + 15) / 16) * 16;
-  return (size_t)TC_PIECES * (TC_M + Npad) * TC_KC * 2;
+  int dev = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t wbytes = (size_t)3 * Npad * Kp * 2;
+  const size_t room = (size_t)maxsm - 1024;  // static shared memory and slack
+  if (wbytes + 2 * TC_STAGE > room) return 0;
+  const int ns = (int)std::min<size_t>(8, (room - wbytes) / TC_STAGE);
+  *Kp_out = Kp;
+  *nstage_out = ns;
+  return wbytes + (size_t)ns * TC_STAGE;
 }
+
+}  // namespace
 
 bool pn_tc_supported(int Nout) { return Nout >= 1 && Nout <= 256; }
 
@@ -222,15 +351,30 @@ int pn_linear_tc(const float* X, int ldx, const float* W, int ldw, const float* 
                  int Nout, int T, int acc, int* err, cudaStream_t st) {
   if (rows <= 0) return PN_OK;
   if (!pn_tc_supported(Nout)) { pn_set_error("tensor-core linear: Nout %d outside 1..256", Nout); return PN_EINVAL; }
+  int Kp = 0, ns = 0;
+  const size_t smem = tc_plan(K, Nout, &Kp, &ns);
+  if (!smem) return PN_ENOTREADY;  // weight too large to stay resident: the caller uses CUDA cores
   const int Npad = ((Nout + 15) / 16) * 16;
   uint32_t cols = 32;
-  while ((int)cols < Npad) cols <<= 1;
-  const size_t smem = pn_tc_smem_bytes(Nout);
-  PN_CUDA(cudaFuncSetAttribute(k_linear_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int blocks = (rows + TC_M - 1) / TC_M;
-  PN_LAUNCH_W("k_linear_tc", st, 2.0 * rows * K * Nout,
-            k_linear_tc<<<blocks, TC_THREADS, smem, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, K, Nout, Npad, T, acc, cols,
-                                                          err));
+  while ((int)cols < 2 * Npad) cols <<= 1;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = (rows + TC_M - 1) / TC_M;
+  const int grid = std::min(tiles, sms);
+  const bool vx = ldx % 4 == 0 && ((uintptr_t)X & 15) == 0;
+  const int vy = ldy % 4 == 0 && ((uintptr_t)Y & 15) == 0;
+  if (vx) {
+    PN_CUDA(pn_allow_max_smem(k_linear_tc<true>));
+    PN_LAUNCH_W("k_linear_tc", st, 2.0 * rows * K * Nout,
+                (k_linear_tc<true><<<grid, TC_THREADS, smem, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, K, Kp, Nout, Npad, T,
+                                                                   acc, ns, cols, vy, err)));
+  } else {
+    PN_CUDA(pn_allow_max_smem(k_linear_tc<false>));
+    PN_LAUNCH_W("k_linear_tc", st, 2.0 * rows * K * Nout,
+                (k_linear_tc<false><<<grid, TC_THREADS, smem, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, K, Kp, Nout, Npad,
+                                                                    T, acc, ns, cols, vy, err)));
+  }
   return PN_OK;
 }
 
