@@ -129,8 +129,10 @@ class Model:
 
 
 def ssp(x):
-    """Shifted softplus ln(exp(x)/2 + 1/2), written without overflow."""
-    return torch.clamp(x, min=0) + torch.log1p(torch.exp(-torch.abs(x))) - LN2
+    """Shifted softplus ln(exp(x)/2 + 1/2) = x/2 + ln cosh(x/2): one smooth
+    expression, so that autograd gives its derivative, the logistic
+    function, at every x (x = 0 included)."""
+    return 0.5 * x + torch.log(torch.cosh(0.5 * x))
 
 
 def features(sys, d):

@@ -358,6 +358,35 @@ def test_philox_known_answer_vectors(ctr, key, expect):
     assert tuple(int(w[0]) for w in out) == expect
 
 
+def test_mlp_and_shifted_softplus_worked_example():
+    """The network's maps (reading A7: affine maps stored [in][out], shifted
+    softplus ln(e^x/2 + 1/2) between layers, none after the last), worked by
+    hand for x = (1, -2), W1 = [[1/2, -1], [2, 1/4]], b1 = (1/10, -3/10),
+    W2 = [[1], [-2]], b2 = (7/10):
+      a = x W1 + b1 = (1/2 - 4 + 1/10, -1 - 1/2 - 3/10) = (-17/5, -9/5)
+      h = ssp(a) = (ln((e^-3.4 + 1)/2), ln((e^-1.8 + 1)/2))
+        = (-0.66031871013507980, -0.54016957003387118)
+      y = h W2 + b2 = h_1 - 2 h_2 + 7/10 = 1.1200204299326626.
+    A transposed map, an activation after the last layer or an unshifted
+    softplus fails it; so do ssp(0) != 0, ssp'(0) != 1/2 and a large-x
+    limit other than x - ln 2."""
+    from oracle.ansatz import _mlp, ssp
+    x = torch.tensor([[1.0, -2.0]], dtype=DT)
+    W1 = torch.tensor([[0.5, -1.0], [2.0, 0.25]], dtype=DT)
+    b1 = torch.tensor([0.1, -0.3], dtype=DT)
+    W2 = torch.tensor([[1.0], [-2.0]], dtype=DT)
+    b2 = torch.tensor([0.7], dtype=DT)
+    y = _mlp(x, [(W1, b1), (W2, b2)])
+    assert abs(float(y[0, 0]) - 1.1200204299326626) < 1e-14
+    z = torch.tensor([0.0, 40.0, -3.4, -1.8], dtype=DT, requires_grad=True)
+    v = ssp(z)
+    assert float(v[0]) == 0.0
+    assert abs(float(v[1]) - (40.0 - math.log(2.0))) < 1e-13
+    np.testing.assert_allclose(v[2:].detach().numpy(), [-0.66031871013507980, -0.54016957003387118], rtol=1e-14)
+    (g,) = torch.autograd.grad(v[0], z)
+    assert abs(float(g[0]) - 0.5) < 1e-15
+
+
 def _golden_features():
     from fractions import Fraction
     import os
