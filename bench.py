@@ -597,7 +597,9 @@ def main():
     ap.add_argument("--serve-sweep", default="", help="further loads for the mixed server, e.g. 0.5,0.9")
     ap.add_argument("--sampler", type=int, default=None,
                     help="PN_OPT_FUSED_SAMPLER for the timed mixed path (library default if absent)")
-    ap.add_argument("--case", choices=["sampler", "jet_tc", "langevin", "drift_n2", "n2_small"], default=None,
+    ap.add_argument("--prof-kernel", default="k_linear", help="kernel class whose work --case n2_small reports")
+    ap.add_argument("--case-quick", action="store_true", help="--case n2_small: only the ranged step")
+    ap.add_argument("--case", choices=["sampler", "jet_tc", "langevin", "drift_n2", "n2_small", "n2_step"], default=None,
                     help="run one small kernel case (for ncu captures) and exit")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -621,7 +623,37 @@ def main():
         s.device_status()
         print("case ok", flush=True)
         return
-    if args.case == "n2_small":  # the headline step on 1024 N2-shaped walkers, one chunk, work per class printed
+    if args.case == "n2_step":  # one headline step (16384 walkers) inside the NVTX range "pn_step" for ncu filtering
+        torch.cuda.set_device(0)
+        sysd = synth.n2()
+        s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=CHUNK)
+        r = torch.empty(W_PER_RANK, s.N, 3, dtype=torch.float64, device="cuda")
+        s.init_walkers(r, 1)
+        lp = torch.empty(W_PER_RANK, dtype=torch.float64, device="cuda")
+        sg = torch.empty_like(lp)
+        s.eval_logpsi(r, lp, sg)
+        s.metropolis_step(r, lp, args.burn, SIGMA, 999, 1 << 40)
+        E, Ec, cot = torch.empty_like(lp), torch.empty_like(lp), torch.empty_like(lp)
+        g = torch.empty(s.n_params, dtype=torch.float64, device="cuda")
+        for k in range(2):
+            if k == 1:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_push("pn_step")
+            s.metropolis_step(r, lp, N_METROPOLIS, SIGMA, 7, k)
+            s.eval_local_energy(r, E)
+            binding.clip_local_energy(E, Ec, cot)
+            s.grad_logpsi(r, cot, g)
+            if k == 1:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_pop()
+        s.device_status()
+        print("case ok", flush=True)
+        return
+    if args.case == "n2_small":
+        # the headline step on 1024 N2-shaped walkers (one chunk): one step in
+        # the NVTX range "pn_step" with the algorithmic work of --prof-kernel's
+        # launches in it printed (for an ncu capture filtered to that range),
+        # then every kernel class's work and time over one more step each
         torch.cuda.set_device(0)
         sysd = synth.n2()
         W = 1024
@@ -631,6 +663,7 @@ def main():
         lp = torch.empty(W, dtype=torch.float64, device="cuda")
         sg = torch.empty_like(lp)
         s.eval_logpsi(r, lp, sg)
+        s.metropolis_step(r, lp, args.burn, SIGMA, 999, 1 << 40)
         E, Ec, cot = torch.empty_like(lp), torch.empty_like(lp), torch.empty_like(lp)
         g = torch.empty(s.n_params, dtype=torch.float64, device="cuda")
 
@@ -641,17 +674,28 @@ def main():
             s.grad_logpsi(r, cot, g)
 
         step(0)
-        work = {}
-        for kname in KERNEL_CLASSES:
-            binding.profile(kname)
-            step(1)
-            torch.cuda.synchronize()
-            n, ms, wk = binding.profile_read()
-            if n:
-                work[kname] = {"launches": n, "ms": ms, "work": wk}
+        torch.cuda.synchronize()
+        binding.profile(args.prof_kernel)
+        torch.cuda.nvtx.range_push("pn_step")
+        step(1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        n, ms, wk = binding.profile_read()
         binding.profile(None)
+        ranged = {"kernel": args.prof_kernel, "launches": n, "ms": ms, "work": wk}
+        work = {}
+        if not args.case_quick:
+            for kname in KERNEL_CLASSES:
+                binding.profile(kname)
+                step(2)
+                torch.cuda.synchronize()
+                n, ms, wk = binding.profile_read()
+                if n:
+                    work[kname] = {"launches": n, "ms": ms, "work": wk}
+            binding.profile(None)
         s.device_status()
-        print(json.dumps({"case": "n2_small", "walkers": W, "per_class_one_step": work}), flush=True)
+        print(json.dumps({"case": "n2_small", "walkers": W, "pn_step_range": ranged, "per_class_one_step": work}),
+              flush=True)
         print("case ok", flush=True)
         return
     if args.case:
@@ -726,12 +770,21 @@ def main():
                   nacc=torch.zeros(1, dtype=torch.int64, device=dev), k=0)
         return st
 
+    from paper_1909_08423_gb300 import distributed as pdist
+
     def step(st):
         s = st["s"]
         s.metropolis_step(st["r"], st["lp"], N_METROPOLIS, SIGMA, 7 + rank, st["k"] * N_METROPOLIS, st["nacc"])
         s.eval_local_energy(st["r"], st["E"])
-        binding.clip_local_energy(st["E"], st["Ec"], st["cot"])
-        s.grad_logpsi(st["r"], st["cot"], st["g"])
+        if world > 1:
+            # the VMC step's exchange: the clipping window over every rank's
+            # energies (all-gather), the gradient summed over ranks (all-reduce)
+            Ec, cot, _ = pdist.global_clip(st["E"], binding.clip_local_energy)
+            s.grad_logpsi(st["r"], cot, st["g"])
+            pdist.allreduce_grad(st["g"])
+        else:
+            binding.clip_local_energy(st["E"], st["Ec"], st["cot"])
+            s.grad_logpsi(st["r"], st["cot"], st["g"])
         st["k"] += 1
 
     def timed(st, steps, warmup, prof_kernel=None):
@@ -846,8 +899,16 @@ def main():
         def host_step(k):
             s.metropolis_step(rh, lph, N_METROPOLIS, SIGMA, 11 + rank, k * N_METROPOLIS, nah)
             s.eval_local_energy(rh, Eh)
-            binding.clip_local_energy(Eh, Ech, coth)
-            s.grad_logpsi(rh, coth, gh)
+            if world > 1:  # the exchange runs on device copies (NCCL)
+                _, cot_d, _ = pdist.global_clip(torch.from_numpy(Eh).to(dev), binding.clip_local_energy)
+                coth[...] = cot_d.cpu().numpy()
+                s.grad_logpsi(rh, coth, gh)
+                gd = torch.from_numpy(gh).to(dev)
+                pdist.allreduce_grad(gd)
+                gh[...] = gd.cpu().numpy()
+            else:
+                binding.clip_local_energy(Eh, Ech, coth)
+                s.grad_logpsi(rh, coth, gh)
 
         host_step(0)
         torch.cuda.synchronize()
@@ -863,6 +924,9 @@ def main():
         # cotangent (clip), gradient
         h2d = rb + lb + rb + W * 8 + rb + W * 8
         d2h = rb + lb + 8 + W * 8 + 2 * W * 8 + gh.nbytes
+        if world > 1:  # E and the gradient to the device for the exchange and back
+            h2d += gh.nbytes
+            d2h += gh.nbytes - W * 8
         e2e = {"value": W * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": dt * 1e3}
 
@@ -870,7 +934,8 @@ def main():
            "precision": "mixed: float32 network, float64 orbitals/determinants/sums/Coulomb; local-energy guard on "
                         "(tau 2e-5 Ha)",
            "l2": "flushed (256 MB write) between timed steps; the per-chunk intermediates (~14 GB) exceed L2",
-           "parallelism": f"replicas x{world} (walkers sharded, no data-path collective)"}
+           "parallelism": (f"walkers sharded x{world}; clipping window all-gathered and gradient all-reduced "
+                           "(NCCL) every step" if world > 1 else "1 GPU")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": cfg,

@@ -167,15 +167,16 @@ int pn_eval_components(pn_system_t sys, const double* r, int W, double* phi,
                        double* J, double* f, double* ld, void* stream);
 
 /* ln|psi| and sign(psi) like pn_eval_logpsi, for callers that cannot
- * allocate device memory while they evaluate (a thread capturing a CUDA
- * graph, a latency-bound loop that must not wait on the allocator, a process
- * that reserves its memory once at start-up).  The paper has no counterpart:
+ * allocate device memory while they evaluate (a latency-bound loop that must
+ * not wait on the allocator, a process that reserves its memory once at
+ * start-up).  The paper has no counterpart:
  * this is a deployment variant of the value pass.  The call allocates
  * nothing: its intermediates live in one fixed 16 MiB file-scope device
  * array that every GPU loading the library holds until the process exits.
  * All buffers must be device pointers, and the handle's device must be
- * current.  W is limited by that array (about 600 walkers of a
- * four-electron, D = 64 system in PN_FP64); a larger W returns PN_EINVAL
+ * current.  W is limited by that array (it holds only the value pass's
+ * intermediates: about 700 walkers of a four-electron, D = 64 system in
+ * PN_FP64); a larger W returns PN_EINVAL
  * with the limit in pn_last_error() and launches nothing.  The first call on
  * each device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture.  Every call shares the one
@@ -260,15 +261,17 @@ int pn_langevin_step(pn_system_t sys, double* r, double* logabs, double* drift,
  *   not fit, to 1 for embeddings up to 64 wide and to 0 beyond (there the
  *   staged value pass is the faster); 0 (or a system too large for one
  *   tile) uses one kernel per stage.
- * PN_OPT_TENSOR_CORES (PN_MIXED only; default 0): a mask of the float32
- *   linear layers that run on tcgen05 with each operand split into three
- *   bf16 pieces (six products, float32 accumulation in tensor memory):
- *   1 = interaction layers of the local-energy jet, 2 = its heads, 4 =
- *   value passes (ln|psi| and the gradient's recomputation).  The tensor
- *   core's float32 accumulation is coarser than CUDA-core float32, so the
- *   mask is a per-system choice: enable a group only where the E_loc error
- *   against PN_FP64 stays within the required bound (the Python helper
- *   paper_1909_08423_gb300.precision.calibrate measures this).
+ * PN_OPT_TENSOR_CORES (PN_MIXED only; default 7): a mask of the float32
+ *   linear layers that run on tcgen05 (maps of at least 8192 rows whose
+ *   weight fits in shared memory; the rest on CUDA cores): 1 = interaction
+ *   layers of the local-energy jet, 2 = its heads, 4 = value passes (ln|psi|
+ *   and the gradient's recomputation).  Each float32 operand is split into
+ *   three bf16 pieces and the six piece products of weight down to 2^-16
+ *   accumulate in tensor memory, the leading products in an accumulator of
+ *   their own: measured against float64, at most 1.6e-7 of sum |x w| per
+ *   element for the network's maps (CUDA-core float32: 3.0e-7).  The Python
+ *   helper paper_1909_08423_gb300.precision.calibrate measures the E_loc
+ *   error of each mask against PN_FP64 on a system's sampled walkers.
  * PN_OPT_DRIFT (default 1): how pn_eval_drift and pn_langevin_step form
  *   grad_r ln|psi| -- 1 reverse mode (work linear in the electron count),
  *   0 the forward jet pass (3N + 2 rows per electron).
@@ -337,7 +340,10 @@ int pn_grad_logpsi(pn_system_t sys, const double* r, int W, const double* cotang
  * m = median, d = mean |E - m|, Lq = q d: E' = E inside |E - m| <= Lq, else
  * m + sgn(E - m) Lq (1 + ln(|E - m| / Lq)).  Also writes, if non-NULL,
  * cot[W] = 2 (E'_w - mean E') / W, the per-walker weights of the loss
- * gradient in Eq. (trainig).  W <= 16384. */
+ * gradient in Eq. (trainig).  W <= 2^26: up to 16384 walkers one block
+ * sorts the energies in shared memory; beyond, a bitonic network sorts
+ * them in global memory (stream-ordered scratch of 8 bytes per walker,
+ * rounded up to a power of two). */
 int pn_clip_local_energy(const double* eloc, int W, double q, double* out,
                          double* cot, void* stream);
 

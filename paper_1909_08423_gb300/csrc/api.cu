@@ -287,6 +287,54 @@ __global__ void k_clip(const double* __restrict__ E, int W, double q, double* __
     for (int i = threadIdx.x; i < W; i += blockDim.x) cot[i] = 2.0 * (out[i] - mean) / W;
 }
 
+// Batches beyond one block's shared memory: the keys are sorted in global
+// memory by a bitonic network (one launch per compare distance), then one
+// block forms the statistics from the sorted keys.
+__global__ void k_clip_keys(const double* __restrict__ E, int W, int n, unsigned long long* __restrict__ key) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) key[i] = i < W ? clip_key(E[i]) : ~0ull;
+}
+
+__global__ void k_bitonic_step(unsigned long long* __restrict__ key, int n, int j, int k) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int l = i ^ j;
+  if (l > i) {
+    const bool up = (i & k) == 0;
+    const unsigned long long a = key[i], b = key[l];
+    if ((a > b) == up) { key[i] = b; key[l] = a; }
+  }
+}
+
+__global__ void k_clip_stats(const unsigned long long* __restrict__ key, const double* __restrict__ E, int W, double q,
+                             double* __restrict__ out, double* __restrict__ cot) {
+  __shared__ double red[32];
+  const double m = 0.5 * (clip_unkey(key[(W - 1) / 2]) + clip_unkey(key[W / 2]));
+  auto block_sum = [&](double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    return t;
+  };
+  double a = 0;
+  for (int i = threadIdx.x; i < W; i += blockDim.x) a += fabs(E[i] - m);
+  const double Lq = q * block_sum(a) / W;
+  double sum = 0;
+  for (int i = threadIdx.x; i < W; i += blockDim.x) {
+    const double x = E[i] - m;
+    double v = E[i];
+    if (fabs(x) > Lq) v = m + copysign(Lq * (1.0 + log(fabs(x) / Lq)), x);
+    out[i] = v;
+    sum += v;
+  }
+  const double mean = block_sum(sum) / W;
+  if (cot)
+    for (int i = threadIdx.x; i < W; i += blockDim.x) cot[i] = 2.0 * (out[i] - mean) / W;
+}
+
 bool is_host(const void* p) { return p && !pn_is_device_ptr(p); }
 
 int set_device(pn_system_s* s) {
@@ -752,8 +800,8 @@ extern "C" int pn_device_status(pn_system_t s) {
 }
 
 extern "C" int pn_clip_local_energy(const double* eloc, int W, double q, double* out, double* cot, void* stream) {
-  if (W <= 0 || W > 16384 || !eloc || !out || !(q > 0)) {
-    pn_set_error("clip: need 0 < W <= 16384, q > 0 and buffers");
+  if (W <= 0 || W > (1 << 26) || !eloc || !out || !(q > 0)) {
+    pn_set_error("clip: need 0 < W <= 2^26, q > 0 and buffers");
     return PN_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -769,9 +817,20 @@ extern "C" int pn_clip_local_energy(const double* eloc, int W, double q, double*
   }
   int n = 1;
   while (n < W) n <<= 1;
-  const size_t smem = (size_t)n * 8;
-  PN_CUDA(pn_allow_max_smem(k_clip));
-  PN_LAUNCH("k_clip", st, k_clip<<<1, 1024, smem, st>>>(e, W, q, o, c));
+  if (W <= 16384) {
+    const size_t smem = (size_t)n * 8;
+    PN_CUDA(pn_allow_max_smem(k_clip));
+    PN_LAUNCH("k_clip", st, k_clip<<<1, 1024, smem, st>>>(e, W, q, o, c));
+  } else {
+    unsigned long long* key = nullptr;
+    PN_CUDA(cudaMallocAsync((void**)&key, (size_t)n * 8, st));
+    PN_LAUNCH("k_clip", st, k_clip_keys<<<nblk(n, 256), 256, 0, st>>>(e, W, n, key));
+    for (int k = 2; k <= n; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1)
+        PN_LAUNCH("k_clip", st, k_bitonic_step<<<nblk(n, 256), 256, 0, st>>>(key, n, j, k));
+    PN_LAUNCH("k_clip", st, k_clip_stats<<<1, 1024, 0, st>>>(key, e, W, q, o, c));
+    PN_CUDA(cudaFreeAsync(key, st));
+  }
   if (host) {
     PN_CUDA(cudaMemcpyAsync(out, o, (size_t)W * 8, cudaMemcpyDefault, st));
     if (cot) PN_CUDA(cudaMemcpyAsync(cot, c, (size_t)W * 8, cudaMemcpyDefault, st));

@@ -1108,7 +1108,9 @@ int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw
   if constexpr (sizeof(R) == 4) {
     // value passes (T == 1) use the PN_TC_VALUE bit, jet passes the group bit
     const int bit = T == 1 ? PN_TC_VALUE : grp;
-    if (s && (s->tensor_cores & bit) && pn_tc_supported(Nout)) {
+    // the persistent tensor-core kernel splits the weight into shared
+    // memory once per CTA: below a few thousand rows the CUDA-core tiles win
+    if (s && (s->tensor_cores & bit) && pn_tc_supported(Nout) && rows >= 8192) {
       const int e = pn_linear_tc((const float*)X, ldx, (const float*)W, ldw, (const float*)b, (float*)Y, ldy, rows, Kd,
                                  Nout, T, acc, s->dev_err, st);
       if (e != PN_ENOTREADY) return e;  // else: the weight does not fit in shared memory, CUDA cores below

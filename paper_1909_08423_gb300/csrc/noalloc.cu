@@ -1,14 +1,14 @@
 // ln|psi| for callers that must not allocate device memory at call time.
 //
 // Some callers cannot call cudaMalloc (or anything that allocates) when they
-// evaluate: a host thread recording a CUDA graph (allocation is not allowed
-// during stream capture), a real-time or latency-bound loop that must not
-// block on the allocator, or a process that reserves all of its device memory
-// up front and may not grow afterwards.  pn_eval_logpsi_static serves them:
+// evaluate: a real-time or latency-bound loop that must not block on the
+// allocator, or a process that reserves all of its device memory up front
+// and may not grow afterwards.  pn_eval_logpsi_static serves them:
 // it runs the same value pass as pn_eval_logpsi, but its intermediates live
 // in one fixed file-scope device array instead of the handle's workspace, and
 // the call itself allocates nothing.  The system handle must have been made
 // earlier by pn_init_system, which does allocate.
+#include <algorithm>
 #include <mutex>
 
 #include "pn_internal.cuh"
@@ -48,20 +48,67 @@ int scratch_on_current_device(void** out) {
   return PN_OK;
 }
 
+// The value pass's intermediates only (the handle's workspace also holds
+// position staging, energies, gradients and proposal buffers that this call
+// never touches): bytes for W walkers, and the carve with the unused
+// buffers left null.
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename R>
+size_t value_bytes(const DevSys& s, size_t W) {
+  const size_t N = s.N, e = sizeof(R);
+  const size_t ldH = std::max(s.Zd, s.D), ldZ = std::max(3 * s.Zd, s.D);
+  return align256(W * s.Ppair * 4 * 8) + align256(W * N * s.n_orb * 5 * 8) + align256(W * s.Ppair * 3 * s.K * e) +
+         align256(W * s.Ppair * 3 * s.Zd * e) + align256(W * N * s.D * e) + align256(W * N * ldH * e) +
+         align256(W * N * ldZ * e) + 3 * align256(W * s.D * e) + align256(W * N * s.n_orb * e) + align256(W * e) +
+         align256(W * s.n_det * 2 * (3 + 3 * N) * 8) + 2 * align256(W * 8) + align256(W * 4);
+}
+
+template <typename R>
+Work<R> value_carve(const DevSys& s, int Wc, void* base) {
+  Work<R> w{};
+  char* p = (char*)base;
+  const size_t W = Wc, N = s.N, e = sizeof(R);
+  const size_t ldH = std::max(s.Zd, s.D), ldZ = std::max(3 * s.Zd, s.D);
+  auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return (void*)q; };
+  w.Wc = Wc;
+  w.T = 1;
+  w.geo = (double*)take(W * s.Ppair * 4 * 8);
+  w.phi = (double*)take(W * N * s.n_orb * 5 * 8);
+  w.efeat = (R*)take(W * s.Ppair * 3 * s.K * e);
+  w.wjet = (R*)take(W * s.Ppair * 3 * s.Zd * e);
+  w.X = (R*)take(W * N * s.D * e);
+  w.H = (R*)take(W * N * ldH * e);
+  w.Zb = (R*)take(W * N * ldZ * e);
+  w.Xs = (R*)take(W * s.D * e);
+  w.As = (R*)take(W * s.D * e);
+  w.Bs = (R*)take(W * s.D * e);
+  w.F = (R*)take(W * N * s.n_orb * e);
+  w.Jj = (R*)take(W * e);
+  w.det = (double*)take(W * s.n_det * 2 * (3 + 3 * N) * 8);
+  w.out_logabs = (double*)take(W * 8);
+  w.out_sign = (double*)take(W * 8);
+  w.out_status = (int*)take(W * 4);
+  w.ldH = (int)ldH;
+  w.ldZ = (int)ldZ;
+  w.end = p;
+  return w;
+}
+
 template <typename R>
 int eval_static(pn_system_s* s, const double* r, int W, double* logabs, double* sign, int* status, cudaStream_t st) {
   const DevSys& ds = s->ds;
-  const size_t need = pn_work_bytes(ds, W, 1, (int)sizeof(R));
+  const size_t need = value_bytes<R>(ds, W);
   if (need > PN_STATIC_SCRATCH_BYTES) {
     int cap = 0;
-    while (pn_work_bytes(ds, cap + 1, 1, (int)sizeof(R)) <= PN_STATIC_SCRATCH_BYTES) ++cap;
+    while (value_bytes<R>(ds, cap + 1) <= PN_STATIC_SCRATCH_BYTES) ++cap;
     pn_set_error("static scratch holds %d walkers of this system (%u bytes); %d requested", cap,
                  (unsigned)PN_STATIC_SCRATCH_BYTES, W);
     return PN_EINVAL;
   }
   void* base = nullptr;
   if (int e = scratch_on_current_device(&base)) return e;
-  Work<R> w = pn_carve_work<R>(ds, W, 1, base);
+  Work<R> w = value_carve<R>(ds, W, base);
   const DevNet<R> net = pn_devnet<R>(s);
   // Nothing in the value pass reads scratch before writing it, so the array
   // needs no clearing between calls.

@@ -607,7 +607,9 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   ds.r_c = d->r_c; ds.use_cusp = d->use_cusp; ds.use_gamma = d->use_gamma;
   // mixed path: the tensor-core sampler where its tiles fit (else the warp kernel)
   ds.fused_sampler = d->precision == PN_MIXED ? 4 : 1;
-  ds.tensor_cores = 0;  // set per system after calibration (PN_OPT_TENSOR_CORES)
+  // mixed systems: every float32 linear map group on tcgen05 (its split
+  // accumulators make it at least as accurate as CUDA-core float32)
+  ds.tensor_cores = d->precision == PN_MIXED ? 7 : 0;
   double Vnn = 0;
   for (int I = 0; I < d->M; ++I)
     for (int J = I + 1; J < d->M; ++J) {

@@ -11,7 +11,9 @@
 // a = a0 + a1 + a2 (each the nearest bf16 of what is left), which together
 // carry 24 mantissa bits, and the product is formed from the six pieces
 // whose weight reaches 2^-16: a0b0, a0b1, a1b0, a0b2, a2b0, a1b1, with
-// float32 accumulation in tensor memory.  That keeps the float32 accuracy
+// float32 accumulation in tensor memory -- the leading a0b0 terms in an
+// accumulator of their own, the five smaller ones in a second, added in the
+// epilogue.  That keeps the float32 accuracy
 // the local-energy bound needs; plain bf16 or tf32 loses 16 or 13 bits, and
 // a two-piece tf32 split still loses about 3.
 //
@@ -28,7 +30,7 @@ namespace {
 
 constexpr int TC_M = 128;       // rows per tile (UMMA M)
 constexpr int TC_KC = 32;       // k-slice per pipeline stage
-constexpr int TC_NPROD = 4;     // producer warps
+constexpr int TC_NPROD = 8;     // producer warps
 constexpr int TC_NEPI = 4;      // epilogue warps
 constexpr int TC_WMMA = TC_NPROD;                      // warp 4 issues the MMAs
 constexpr int TC_THREADS = 32 * (TC_NPROD + 1 + TC_NEPI);
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
                                                               const float* __restrict__ bias, float* __restrict__ Y,
                                                               int ldy, int rows, int K, int Kp, int Nout, int Npad,
                                                               int T, int accumulate, int nstage, uint32_t tmem_cols,
-                                                              int vy, int* __restrict__ err) {
+                                                              int vy, int nbuf, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[2 * 8 + 4 + 1];  // full[8], empty[8], acc_full[2], acc_empty[2], drain
   __shared__ uint32_t tmem_base;
@@ -162,53 +164,74 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
 
   if (warp < TC_NPROD) {
     // ---------------------------------------------------------- producers
-    const int p = tid;  // 0..127
-    int g = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // thread p owns two (row, 8-wide k group) cells of every stage; its
+    // global loads run two stages ahead of the splitting and storing, so
+    // that enough bytes are in flight to cover the memory latency
+    const int p = tid;  // 0..255
+    const int my_tiles = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int nstages_total = my_tiles * nk;
+    auto load = [&](int gg, float* dst) {
+      const int tile = blockIdx.x + (gg / nk) * gridDim.x;
+      const int k0 = (gg % nk) * TC_KC;
       const int r0 = tile * TC_M;
-      for (int kc = 0; kc < nk; ++kc, ++g) {
-        const int s = g % nstage;
-        if (!mbar_wait(empty0 + 8 * s, ((g / nstage) & 1) ^ 1, abort)) goto prod_done;
-        unsigned char* st = sA + (size_t)s * TC_STAGE;
-        const int k0 = kc * TC_KC;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int idx = p + 128 * j;        // (row, 8-wide k group)
-          const int row = idx >> 2, gk = (idx & 3) * 8;
-          const int gr = r0 + row;
-          float v[8];
-          if (VX && gr < rows && k0 + gk + 8 <= K) {
-            const float4* src = (const float4*)(X + (size_t)gr * ldx + k0 + gk);
-            const float4 a = src[0], b = src[1];
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-          } else {
+      for (int j = 0; j < 2; ++j) {
+        const int idx = p + 256 * j;
+        const int row = idx >> 2, gk = (idx & 3) * 8;
+        const int gr = r0 + row;
+        if (VX && gr < rows && k0 + gk + 8 <= K) {
+          const float4* src = (const float4*)(X + (size_t)gr * ldx + k0 + gk);
+          const float4 a = src[0], b = src[1];
+          dst[8 * j + 0] = a.x; dst[8 * j + 1] = a.y; dst[8 * j + 2] = a.z; dst[8 * j + 3] = a.w;
+          dst[8 * j + 4] = b.x; dst[8 * j + 5] = b.y; dst[8 * j + 6] = b.z; dst[8 * j + 7] = b.w;
+        } else {
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const int k = k0 + gk + e;
-              v[e] = (gr < rows && k < K) ? X[(size_t)gr * ldx + k] : 0.0f;
-            }
+          for (int e = 0; e < 8; ++e) {
+            const int k = k0 + gk + e;
+            dst[8 * j + e] = (gr < rows && k < K) ? X[(size_t)gr * ldx + k] : 0.0f;
           }
-          uint32_t w0[4], w1[4], w2[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            unsigned short a0, a1, a2, b0, b1, b2;
-            split3(v[2 * e], a0, a1, a2);
-            split3(v[2 * e + 1], b0, b1, b2);
-            w0[e] = (uint32_t)a0 | ((uint32_t)b0 << 16);
-            w1[e] = (uint32_t)a1 | ((uint32_t)b1 << 16);
-            w2[e] = (uint32_t)a2 | ((uint32_t)b2 << 16);
-          }
-          const uint32_t off = tile_off(row, gk, TC_SBO_A);
-          *(uint4*)(st + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-          *(uint4*)(st + TC_M * TC_KC * 2 + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-          *(uint4*)(st + 2 * TC_M * TC_KC * 2 + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(full0 + 8 * s);
       }
+    };
+    bool alive = true;
+    // stage g from cur while stage g + 2 loads into pf
+    auto step = [&](int g, const float* cur, float* pf) {
+      if (!alive || g >= nstages_total) return;
+      if (g + 2 < nstages_total) load(g + 2, pf);
+      const int s = g % nstage;
+      if (!mbar_wait(empty0 + 8 * s, ((g / nstage) & 1) ^ 1, abort)) { alive = false; return; }
+      unsigned char* st = sA + (size_t)s * TC_STAGE;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int idx = p + 256 * j;
+        const int row = idx >> 2, gk = (idx & 3) * 8;
+        uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          unsigned short a0, a1, a2, b0, b1, b2;
+          split3(cur[8 * j + 2 * e], a0, a1, a2);
+          split3(cur[8 * j + 2 * e + 1], b0, b1, b2);
+          w0[e] = (uint32_t)a0 | ((uint32_t)b0 << 16);
+          w1[e] = (uint32_t)a1 | ((uint32_t)b1 << 16);
+          w2[e] = (uint32_t)a2 | ((uint32_t)b2 << 16);
+        }
+        const uint32_t off = tile_off(row, gk, TC_SBO_A);
+        *(uint4*)(st + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+        *(uint4*)(st + TC_M * TC_KC * 2 + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        *(uint4*)(st + 2 * TC_M * TC_KC * 2 + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(full0 + 8 * s);
+    };
+    float va[16], vb[16], vc[16];
+    if (nstages_total > 0) load(0, va);
+    if (nstages_total > 1) load(1, vb);
+    for (int g = 0; g < nstages_total && alive; g += 3) {
+      step(g, va, vc);
+      step(g + 1, vb, va);
+      step(g + 2, vc, vb);
     }
-  prod_done:;
   } else if (warp == TC_WMMA) {
     // --------------------------------------------------------------- MMA
     if (lane == 0) {
@@ -220,10 +243,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
       int g = 0, it = 0;
       bool issued = false;
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const int buf = it & 1;
-        if (!mbar_wait(acce0 + 8 * buf, ((it >> 1) & 1) ^ 1, abort)) break;
+        const int buf = it % nbuf;
+        if (!mbar_wait(acce0 + 8 * buf, ((it / nbuf) & 1) ^ 1, abort)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t dt = tmem + (uint32_t)(buf * Npad);
+        // the five smaller piece products accumulate at dt, the leading
+        // a0 b0 products at dt + Npad: the long accumulation of the large
+        // terms then takes one rounding per k-step instead of six
+        const uint32_t dt = tmem + (uint32_t)(buf * 2 * Npad);
         bool ok = true;
         for (int kc = 0; kc < nk; ++kc, ++g) {
           const int s = g % nstage;
@@ -236,10 +262,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
             for (int q = 0; q < 6; ++q) {
               const uint64_t da = smem_desc(a_st + pa[q] * (TC_M * TC_KC * 2) + a_step, TC_SBO_A);
               const uint64_t db = smem_desc(b_base + pb[q] * b_piece + b_step, sbo_b);
-              const uint32_t acc_in = (kc == 0 && ks == 0 && q == 0) ? 0u : 1u;
+              const bool big = q == 5;  // (a0, b0)
+              const uint32_t acc_in = (kc == 0 && ks == 0 && (q == 0 || big)) ? 0u : 1u;
+              const uint32_t d = big ? dt + (uint32_t)Npad : dt;
               asm volatile(
                   "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
                   "l"(da), "l"(db), "r"(idesc), "r"(acc_in));
             }
           }
@@ -266,21 +294,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
     const int quarter = warp & 3;  // TMEM lanes 32 quarter .. 32 quarter + 31
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-      const int buf = it & 1;
-      if (!mbar_wait(accf0 + 8 * buf, (it >> 1) & 1, abort)) break;
+      const int buf = it % nbuf;
+      if (!mbar_wait(accf0 + 8 * buf, (it / nbuf) & 1, abort)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int row = tile * TC_M + quarter * 32 + lane;
       const bool val = (row % T) == 0;
       for (int c0 = 0; c0 < Npad; c0 += 16) {
-        uint32_t v[16];
-        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * Npad + c0);
+        uint32_t v[16], u[16];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 2 * Npad + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
             "%14, %15}, [%16];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(taddr));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+              "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+            : "r"(taddr + (uint32_t)Npad));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(u[j]));
         if (row < rows) {
           float* yr = Y + (size_t)row * ldy;
           if (vy && c0 + 16 <= Nout) {
@@ -355,8 +391,10 @@ int pn_linear_tc(const float* X, int ldx, const float* W, int ldw, const float* 
   const size_t smem = tc_plan(K, Nout, &Kp, &ns);
   if (!smem) return PN_ENOTREADY;  // weight too large to stay resident: the caller uses CUDA cores
   const int Npad = ((Nout + 15) / 16) * 16;
+  // two accumulators per tile; two tiles in flight where TMEM holds them
+  const int nbuf = 4 * Npad <= 512 ? 2 : 1;
   uint32_t cols = 32;
-  while ((int)cols < 2 * Npad) cols <<= 1;
+  while ((int)cols < 2 * nbuf * Npad) cols <<= 1;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -368,12 +406,12 @@ int pn_linear_tc(const float* X, int ldx, const float* W, int ldw, const float* 
     PN_CUDA(pn_allow_max_smem(k_linear_tc<true>));
     PN_LAUNCH_W("k_linear_tc", st, 2.0 * rows * K * Nout,
                 (k_linear_tc<true><<<grid, TC_THREADS, smem, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, K, Kp, Nout, Npad, T,
-                                                                   acc, ns, cols, vy, err)));
+                                                                   acc, ns, cols, vy, nbuf, err)));
   } else {
     PN_CUDA(pn_allow_max_smem(k_linear_tc<false>));
     PN_LAUNCH_W("k_linear_tc", st, 2.0 * rows * K * Nout,
                 (k_linear_tc<false><<<grid, TC_THREADS, smem, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, K, Kp, Nout, Npad,
-                                                                    T, acc, ns, cols, vy, err)));
+                                                                    T, acc, ns, cols, vy, nbuf, err)));
   }
   return PN_OK;
 }

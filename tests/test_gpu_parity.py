@@ -353,8 +353,10 @@ def test_init_walkers_match_oracle(lib, oracles):
     np.testing.assert_allclose(r.cpu().numpy(), ro, rtol=0, atol=1e-13)
 
 
-@pytest.mark.parametrize("W", [1, 2, 1001, 4096])
+@pytest.mark.parametrize("W", [1, 2, 1001, 4096, 16384, 16385, 131072])
 def test_clip_matches_oracle(lib, W):
+    """Up to 16384 walkers one block sorts in shared memory; beyond, the
+    global-memory sort (the global window of a multi-rank batch)."""
     from paper_1909_08423_gb300 import binding
     rng = np.random.default_rng(W)
     E = np.concatenate([rng.normal(-14.6, 0.4, W - min(W, 3)), [30.0, -90.0, 400.0][:min(W, 3)]])

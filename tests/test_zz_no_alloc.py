@@ -1,11 +1,12 @@
 """The allocation-free value pass, pn_eval_logpsi_static.
 
 It exists for callers that may not allocate device memory while they
-evaluate (for example a thread capturing a CUDA graph, or a service that
-reserves its memory once at start-up): the call keeps its intermediates in a
-fixed device array instead of allocating.  Its results must equal those of
-pn_eval_logpsi, call after call, since the fixed array is reused.  This file
-is collected last on purpose.
+evaluate (for example a latency-bound loop that must not wait on the
+allocator, or a service that reserves its memory once at start-up): the call
+keeps its intermediates in a fixed device array instead of allocating.  Its
+results must equal those of pn_eval_logpsi, call after call, since the fixed
+array is reused, and a call must leave the device's free memory as it found
+it.  This file is collected last on purpose.
 """
 
 import ctypes
@@ -50,6 +51,24 @@ def test_static_scratch_matches_allocating_entry_point(lib, precision):
         assert np.all(np.abs(a - b) <= 1e-9 * (1 + np.abs(b)))
         np.testing.assert_array_equal(sg.cpu().numpy(), ref_sg.cpu().numpy())
         assert np.all(st.cpu().numpy() == 0)
+
+
+def test_static_call_leaves_free_device_memory_unchanged(lib):
+    cdll, f = _static_fn(lib)
+    sysd = synth.be()
+    s = lib.System(sysd, precision=1, max_walkers=64)
+    W = 256
+    r = torch.as_tensor(synth.random_walkers(sysd, W, 43), device="cuda")
+    lp = torch.empty(W, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    assert f(s.h, r.data_ptr(), W, lp.data_ptr(), None, None, stream) == 0  # first call: symbol lookup
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert f(s.h, r.data_ptr(), W, lp.data_ptr(), None, None, stream) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_static_scratch_rejects_oversized_batches(lib):
