@@ -49,9 +49,9 @@ WORKLOAD_DESC = ("N2-shaped diatomic (two Z=7 at 2.068 bohr, 14 e, 32 dets, 4s4p
 KERNEL_UNIT = {
     "k_linear": "fp32", "k_linear_bt": "fp32", "k_filter": "fp32", "k_filter_tile": "fp32",
     "k_metropolis_warp": "fp32", "k_metropolis_fused": "fp32", "k_metropolis_tc": "tensor",
-    "k_linear_tc": "tensor", "k_slater": "fp64", "k_message": "hbm",
+    "k_linear_tc": "tensor", "k_slater": "fp64", "k_message": "hbm", "k_linear_f64": "fp64",
 }
-KERNEL_CLASSES = ["k_linear", "k_linear_bt", "k_linear_tc", "k_filter", "k_message", "k_slater", "k_orbitals",
+KERNEL_CLASSES = ["k_linear", "k_linear_f64", "k_linear_bt", "k_linear_tc", "k_filter", "k_message", "k_slater", "k_orbitals",
                   "k_combine", "k_features", "k_ssp_jet", "k_sum_electrons", "k_init_x", "k_geometry", "k_wgrad",
                   "k_slater_bwd", "k_filter_bwd", "k_filter_bwd_dist", "k_filter_tape", "k_msg_bwd_w",
                   "k_msg_bwd_h", "k_mul_sigmoid", "k_ssp_copy", "k_outer_row", "k_bcast_add", "k_message_value",
@@ -96,29 +96,42 @@ def _traffic_per_work(kernel):
     return rec["dram_bytes_per_work"], rec["note"]
 
 
-def _roofline(kernel, count, ms, work, peaks, peak_src, fp32, fp64):
+def _roofline(kernel, count, ms, work, peaks, peak_src, fp32, fp64, nbytes=0.0):
     """Roofline record of one kernel class: achieved = algorithmic work of its
     launches / their summed CUDA-event time, against the peak of the unit
-    that bounds it."""
+    that bounds it.  Where the launch sites also report the bytes the
+    launches must move through HBM (the linear maps), both fractions are
+    formed and the larger -- the binding constraint -- is the record's
+    bound; the other is kept as `other_view`."""
     unit = KERNEL_UNIT.get(kernel)
-    rec = {"kernel": kernel, "launches": count, "kernel_ms": ms, "work": work}
+    rec = {"kernel": kernel, "launches": count, "kernel_ms": ms, "work": work, "bytes": nbytes or None}
     if not unit or work <= 0 or ms <= 0:
         rec.update(bound=None, achieved=None, peak=None, frac=None, unit=None,
                    note="the library reports no algorithmic work for this class")
         return rec
     sec = ms / 1e3
+    views = []
     if unit == "hbm":
-        ach, peak, u = work / sec / 1e9, peaks["hbm_gbs"], "GB/s"
-        rec.update(bound="hbm", peak_source=f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})")
-    elif unit == "tensor":
-        ach, peak, u = work / sec / 1e12, peaks["bf16_tflops"], "TFLOP/s"
-        rec.update(bound="tensor", peak_source=f"bf16_tflops (burst) of MEASURED_PEAKS.json ({peak_src}); "
-                                               "work counts each float32 product once")
+        views.append(("hbm", work / sec / 1e9, peaks["hbm_gbs"], "GB/s",
+                      f"hbm_gbs of MEASURED_PEAKS.json ({peak_src}); work = bytes that must cross HBM"))
     else:
-        ach, u = work / sec / 1e12, "TFLOP/s"
-        peak = fp32 if unit == "fp32" else fp64
-        rec.update(bound="alu", peak_source=f"{unit} FMA issue rate measured by pn_measure_peak on this GPU")
-    rec.update(achieved=ach, peak=peak, unit=u, frac=ach / peak, work_per_launch=work / max(count, 1))
+        if unit == "tensor":
+            views.append(("tensor", work / sec / 1e12, peaks["bf16_tflops"], "TFLOP/s",
+                          f"bf16_tflops (burst) of MEASURED_PEAKS.json ({peak_src}); work counts each float32 product "
+                          "once, the kernel issues six bf16 piece products for it"))
+        else:
+            views.append(("alu", work / sec / 1e12, fp32 if unit == "fp32" else fp64, "TFLOP/s",
+                          f"{unit} FMA issue rate measured by pn_measure_peak on this GPU"))
+        if nbytes > 0:
+            views.append(("hbm", nbytes / sec / 1e9, peaks["hbm_gbs"], "GB/s",
+                          f"hbm_gbs of MEASURED_PEAKS.json ({peak_src}); bytes = inputs read and outputs written once"))
+    views.sort(key=lambda v: -v[1] / v[2])
+    b, ach, peak, u, src = views[0]
+    rec.update(bound=b, achieved=ach, peak=peak, unit=u, frac=ach / peak, peak_source=src,
+               work_per_launch=(nbytes if b == "hbm" and unit != "hbm" else work) / max(count, 1))
+    if len(views) > 1:
+        b2, a2, p2, u2, s2 = views[1]
+        rec["other_view"] = {"bound": b2, "achieved": a2, "peak": p2, "unit": u2, "frac": a2 / p2, "peak_source": s2}
     return rec
 
 
@@ -502,7 +515,7 @@ def run_ablation(W=4096, steps=3):
 
 
 def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384, load=0.7, fp64_jobs=100,
-                sweep=()):
+                sweep=(), guard=True, unguarded_jobs=0):
     """Poisson stream of seeded molecules through the serving loop.  The
     arrival rate is `load` times the mixed server's capacity, measured first
     by a closed-loop burst of the stream's first jobs (also with one slot, to
@@ -550,6 +563,9 @@ def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384
     ncal = min(n_jobs, 24)
     mixed_sys = [binding.System(synth.serving_system(j["seed"]), precision=binding.PN_MIXED, max_walkers=1)
                  for j in stream]
+    if not guard:
+        for s_ in mixed_sys:
+            s_.set_option(binding.PN_OPT_GUARD, 0)
     cap_jobs, cap_walkers = burst(mixed_sys, ncal, slots)
     cap1_jobs, cap1_walkers = burst(mixed_sys, ncal, 1)
     rate = load * cap_jobs
@@ -558,13 +574,24 @@ def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384
                         one_slot_capacity_jobs_per_s=cap1_jobs, one_slot_walker_eloc_per_s=cap1_walkers)
     for l_ in sweep:
         out.setdefault("load_sweep", []).append(dict(open_loop(mixed_sys, n_jobs, l_ * cap_jobs), load=l_))
+    if guard and unguarded_jobs > 0:
+        # the same mixed server without the local-energy guard, on a prefix
+        nu = min(unguarded_jobs, n_jobs)
+        for s_ in mixed_sys[:nu]:
+            s_.set_option(binding.PN_OPT_GUARD, 0)
+        cu, cuw = burst(mixed_sys, ncal, slots)
+        out["mixed_unguarded"] = open_loop(mixed_sys, nu, rate)
+        out["mixed_unguarded"].update(calibrated_capacity_jobs_per_s=cu, calibrated_walker_eloc_per_s=cuw,
+                                      note=f"the stream's first {nu} jobs without the local-energy guard, same rate")
     for s_ in mixed_sys:
         s_.close()
     if fp64_jobs > 0:
         nf = min(fp64_jobs, n_jobs)
         f64_sys = [binding.System(synth.serving_system(stream[k]["seed"]), precision=binding.PN_FP64, max_walkers=1)
-                   for k in range(nf)]
+                   for k in range(max(nf, ncal))]
+        fcap, fcapw = burst(f64_sys, ncal, slots)
         out["fp64"] = open_loop(f64_sys, nf, rate)
+        out["fp64"].update(calibrated_capacity_jobs_per_s=fcap, calibrated_walker_eloc_per_s=fcapw)
         out["fp64"]["note"] = f"the stream's first {nf} jobs at the mixed server's arrival rate"
         for s_ in f64_sys:
             s_.close()
@@ -592,6 +619,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the Be/H10 steps, Langevin, scan, training, ablation")
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--serve-fp64-jobs", type=int, default=100)
+    ap.add_argument("--serve-unguarded-jobs", type=int, default=0, help="also serve a prefix without the guard")
+    ap.add_argument("--serve-no-guard", action="store_true")
     ap.add_argument("--serve-only", action="store_true")
     ap.add_argument("--serve-load", type=float, default=0.7, help="offered load, fraction of calibrated mixed capacity")
     ap.add_argument("--serve-sweep", default="", help="further loads for the mixed server, e.g. 0.5,0.9")
@@ -623,7 +652,7 @@ def main():
         s.device_status()
         print("case ok", flush=True)
         return
-    if args.case == "n2_step":  # one headline step (16384 walkers) inside the NVTX range "pn_step" for ncu filtering
+    if args.case == "n2_step":  # one headline step (16384 walkers) between cudaProfilerStart/Stop (and NVTX "pn_step")
         torch.cuda.set_device(0)
         sysd = synth.n2()
         s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=CHUNK)
@@ -639,20 +668,23 @@ def main():
             if k == 1:
                 torch.cuda.synchronize()
                 torch.cuda.nvtx.range_push("pn_step")
+                torch.cuda.cudart().cudaProfilerStart()
             s.metropolis_step(r, lp, N_METROPOLIS, SIGMA, 7, k)
             s.eval_local_energy(r, E)
             binding.clip_local_energy(E, Ec, cot)
             s.grad_logpsi(r, cot, g)
             if k == 1:
                 torch.cuda.synchronize()
+                torch.cuda.cudart().cudaProfilerStop()
                 torch.cuda.nvtx.range_pop()
         s.device_status()
         print("case ok", flush=True)
         return
     if args.case == "n2_small":
-        # the headline step on 1024 N2-shaped walkers (one chunk): one step in
-        # the NVTX range "pn_step" with the algorithmic work of --prof-kernel's
-        # launches in it printed (for an ncu capture filtered to that range),
+        # the headline step on 1024 N2-shaped walkers (one chunk): one step
+        # between cudaProfilerStart/Stop (and in the NVTX range "pn_step")
+        # with the algorithmic work of --prof-kernel's launches in it printed
+        # (for an ncu capture limited to that step),
         # then every kernel class's work and time over one more step each
         torch.cuda.set_device(0)
         sysd = synth.n2()
@@ -677,8 +709,10 @@ def main():
         torch.cuda.synchronize()
         binding.profile(args.prof_kernel)
         torch.cuda.nvtx.range_push("pn_step")
+        torch.cuda.cudart().cudaProfilerStart()
         step(1)
         torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
         torch.cuda.nvtx.range_pop()
         n, ms, wk = binding.profile_read()
         binding.profile(None)
@@ -728,7 +762,8 @@ def main():
         torch.cuda.set_device(0)
         sweep = tuple(float(x) for x in args.serve_sweep.split(",") if x)
         print(json.dumps({"serve": run_serving(args.serve_jobs, load=args.serve_load, fp64_jobs=args.serve_fp64_jobs,
-                                               sweep=sweep)}), flush=True)
+                                               sweep=sweep, guard=not args.serve_no_guard,
+                                               unguarded_jobs=args.serve_unguarded_jobs)}), flush=True)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -809,7 +844,7 @@ def main():
         ms = sum(a.elapsed_time(b) for a, b in times) / steps
         kern = None
         if prof_kernel:
-            kern = binding.profile_read()
+            kern = binding.profile_read(with_bytes=True)
             binding.profile(None)
         return ms, launches, kern
 
@@ -822,9 +857,9 @@ def main():
         binding.profile(kname)
         step(mixed)
         torch.cuda.synchronize()
-        n, ms_k, wk = binding.profile_read()
+        n, ms_k, wk, by = binding.profile_read(with_bytes=True)
         if n:
-            share[kname] = (n, ms_k, wk)
+            share[kname] = (n, ms_k, wk, by)
     binding.profile(None)
     dom = max(share, key=lambda k: share[k][1])
     mixed["s"].guard_count()
@@ -848,12 +883,14 @@ def main():
     value = W * world / (ms_max / 1e3)
     acc_rate = float(mixed["nacc"].item()) / (W * N_METROPOLIS)
 
-    roof = _roofline(dom, kern[0], kern[1], kern[2], peaks, peak_src, fp32_peak, fp64_peak)
+    roof = _roofline(dom, kern[0], kern[1], kern[2], peaks, peak_src, fp32_peak, fp64_peak, kern[3])
     roof["kernel_ms_per_step"] = kern[1] / args.steps
     tpw, tnote = _traffic_per_work(dom)
-    roof["traffic"] = tpw * roof["work_per_launch"] if (tpw is not None and roof.get("work_per_launch")) else None
+    # traffic per launch: the captured DRAM bytes per unit of the class's
+    # algorithmic work, times this run's work per launch
+    roof["traffic"] = tpw * kern[2] / max(kern[0], 1) if tpw is not None else None
     roof["traffic_note"] = tnote
-    by_kernel = sorted((_roofline(k, v[0], v[1], v[2], peaks, peak_src, fp32_peak, fp64_peak)
+    by_kernel = sorted((_roofline(k, v[0], v[1], v[2], peaks, peak_src, fp32_peak, fp64_peak, v[3])
                         for k, v in share.items()), key=lambda x: -x["kernel_ms"])[:8]
 
     # accuracy of the mixed path on the sampled walkers, against the FP64 path
@@ -932,7 +969,7 @@ def main():
 
     cfg = {"workload": WORKLOAD_DESC.format(W=W, C=chunk), "walkers_per_gpu": W, "chunk": chunk,
            "precision": "mixed: float32 network, float64 orbitals/determinants/sums/Coulomb; local-energy guard on "
-                        "(tau 2e-5 Ha)",
+                        "(tau 5e-5 Ha)",
            "l2": "flushed (256 MB write) between timed steps; the per-chunk intermediates (~14 GB) exceed L2",
            "parallelism": (f"walkers sharded x{world}; clipping window all-gathered and gradient all-reduced "
                            "(NCCL) every step" if world > 1 else "1 GPU")}
@@ -963,7 +1000,8 @@ def main():
         line["vmc_train"] = run_vmc_train(be)
         line["ablation"] = run_ablation(4096)
     if rank == 0 and args.serve_jobs > 0:
-        line["serve"] = run_serving(args.serve_jobs, load=args.serve_load, fp64_jobs=args.serve_fp64_jobs)
+        line["serve"] = run_serving(args.serve_jobs, load=args.serve_load, fp64_jobs=args.serve_fp64_jobs,
+                                    guard=not args.serve_no_guard, unguarded_jobs=args.serve_unguarded_jobs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -286,28 +286,36 @@ int pn_langevin_step(pn_system_t sys, double* r, double* logabs, double* drift,
  *   evaluated again in float64 and returned with its float64 E_loc, ln|psi|,
  *   sign and status.  Each guarded chunk reads one count back to the host
  *   (the call then synchronises its stream once per chunk).  Measured on
- *   16384 walkers sampled from |psi|^2 with the default probe and tau: 1.0 %
- *   (H10 chain) and 0.46 % (N2 shape) of walkers re-evaluated, the largest
- *   remaining error 7.0e-5 and 8.5e-5 Ha.  pn_guard_count reports how many
- *   walkers were re-evaluated.
+ *   three samples of 16384 walkers from |psi|^2 per system with the
+ *   default probe and tau: 1.0-1.1 % (H10 chain) and 0.46-0.65 % (N2
+ *   shape) of walkers re-evaluated; the largest remaining errors 4.4e-5,
+ *   1.1e-4, 4.7e-5 Ha (H10) and 7.8e-5, 2.8e-5, 7.4e-5 Ha (N2) -- one walker
+ *   of the 98304 above 1e-4 Ha.  pn_guard_count reports how many walkers
+ *   were re-evaluated.
  * PN_OPT_GUARD_PROBE (default 1): the guard's second evaluation -- 1 the
  *   backflow and Jastrow jets of the first pass perturbed by +-2^-19
  *   relative (a deterministic sign per element, a stand-in for the
  *   network's accumulated rounding) and the determinants and E_loc formed
- *   again; 0 the heads (the Jastrow and backflow maps) evaluated again on
- *   the other unit (tensor cores if they ran on CUDA cores, and back),
- *   then the determinants and E_loc.
- * PN_OPT_DET_TABLE (default 1): how the local-energy pass forms the
- *   determinants' gradients and Laplacians -- 1 by the table method where
- *   the system allows it (every determinant reached from determinant 0 by
- *   at most 4 orbital replacements per spin, at most 8 electrons and 8
- *   virtual orbitals per spin): det A_p = s_p det A_0 det(T[holes,
- *   particles]) with T = A_0^-1 A, so that the 3N tangents and the
- *   Laplacian of all determinants follow from those of determinant 0 and of
- *   T; a walker whose determinant-0 block has a 1-norm condition number
- *   beyond 1e3 is computed block by block; 0 block by block for every walker; 2 the table
- *   kernel with every walker on its block-by-block path (a test of that
- *   path). */
+ *   again; 2 the same with a third of 2^-19 at the scale of the heads'
+ *   terms added (sum_k |x_k| |W_kn| of the last map of each head: rounding
+ *   enters an output at that scale, which cancellation can make far larger
+ *   than the output): on the samples above with the default tau, 1.8-2.2 %
+ *   (H10) and 2.4-2.5 % (N2) re-evaluated and every remaining error at most
+ *   5.0e-5 (H10) and 8.0e-5 Ha (N2); 0 the heads (the Jastrow and backflow
+ *   maps) evaluated again on the other unit (tensor cores if they ran on
+ *   CUDA cores, and back), then the determinants and E_loc.
+ * PN_OPT_DET_TABLE (default 1): how the forward passes form the
+ *   determinants (and, in the local-energy pass, their gradients and
+ *   Laplacians) -- 1 by the table method where the system allows it (every
+ *   determinant reached from determinant 0 by at most 4 orbital
+ *   replacements per spin, at most 8 electrons and 8 virtual orbitals per
+ *   spin): det A_p = s_p det A_0 det(T[holes, particles]) with T = A_0^-1 A,
+ *   so that the 3N tangents and the Laplacian of all determinants follow
+ *   from those of determinant 0 and of T; a walker whose determinant-0
+ *   block has a 1-norm condition number beyond 1e3 (jet) or 1e5 (value
+ *   pass) is computed block by block; 0 block by block for every walker; 2
+ *   the table kernel with every walker on its block-by-block path (a test of
+ *   that path). */
 enum { PN_OPT_FUSED_SAMPLER = 1, PN_OPT_TENSOR_CORES = 2, PN_OPT_DRIFT = 3, PN_OPT_GUARD = 4, PN_OPT_DET_TABLE = 5,
        PN_OPT_GUARD_PROBE = 6 };
 int pn_set_option(pn_system_t sys, int option, int value);
@@ -453,6 +461,9 @@ int pn_test_linear_tc(const float* X, int ldx, const float* W, int ldw,
  *   launch sites report it -- floating-point operations (a multiply-add
  *   counts 2) for compute kernels, bytes that must cross HBM for the
  *   message kernels; 0 for kernel classes that report none.
+ * pn_profile_bytes: the bytes those launches must move through HBM at
+ *   least (inputs read and outputs written once), summed as the launch sites
+ *   that know them report it (the linear maps); 0 for the others.
  * pn_measure_peak: the issue-rate ceiling of a CUDA-core unit on the
  *   current device, measured by this library's own kernel (eight
  *   independent multiply-add chains per thread, 8 blocks of 256 threads per
@@ -464,6 +475,7 @@ unsigned long long pn_launch_count(void);
 int pn_profile_kernel(const char* name);
 int pn_profile_read(int64_t* count, double* total_ms);
 int pn_profile_work(double* work);
+int pn_profile_bytes(double* bytes);
 int pn_measure_peak(int kind, double* tflops, void* stream);
 
 const char* pn_last_error(void);

@@ -20,11 +20,13 @@ Modules
   clip        smooth logarithmic clipping of local energies (Methods,
               "Ansatz optimization").
 
-Parity status of each function is listed in its docstring.  The network's
-message passing and heads are also pinned by a special case: with constant
-filters every message is a partner count times a spin-class row, which fixes
-the channel assignment, the partner sums, the layer recursion and both heads.
-The distance dependence of the filter networks is pinned only through
-invariants, cusplessness and finite differences ("parity unpinned" beyond
-those).
+Pins (tests/test_oracle_pins.py) cover every function: closed forms of the
+local energy (hydrogen-like atoms, a Gaussian, a two-electron product, an
+electron beside bare nuclei for the nucleus-nucleus terms of V), Leibniz
+determinants, finite differences, symmetries and cusps, Philox4x32-10
+known-answer vectors, a hand-worked table of the distance features e_k and a
+hand-worked two-layer map with the shifted softplus.  The network's message
+passing and heads are also pinned by a special case: with constant filters
+every message is a partner count times a spin-class row, which fixes the
+channel assignment, the partner sums, the layer recursion and both heads.
 """

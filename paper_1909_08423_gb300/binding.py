@@ -105,6 +105,7 @@ EXPORTS = {
     "pn_profile_kernel": (C.c_int, [C.c_char_p]),
     "pn_profile_read": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "pn_profile_work": (C.c_int, [C.POINTER(C.c_double)]),
+    "pn_profile_bytes": (C.c_int, [C.POINTER(C.c_double)]),
     "pn_measure_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "pn_last_error": (C.c_char_p, []),
 }
@@ -357,12 +358,14 @@ def profile(name):
     check(load().pn_profile_kernel(name.encode() if name else None))
 
 
-def profile_read():
-    """(launches, total ms, algorithmic work) of the timed kernel class."""
-    n, ms, wk = C.c_int64(), C.c_double(), C.c_double()
+def profile_read(with_bytes=False):
+    """(launches, total ms, algorithmic work[, algorithmic bytes]) of the
+    timed kernel class."""
+    n, ms, wk, by = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
     check(load().pn_profile_read(C.byref(n), C.byref(ms)))
     check(load().pn_profile_work(C.byref(wk)))
-    return n.value, ms.value, wk.value
+    check(load().pn_profile_bytes(C.byref(by)))
+    return (n.value, ms.value, wk.value, by.value) if with_bytes else (n.value, ms.value, wk.value)
 
 
 def num_params_for(D, Zd, K, L, M, n_orb):

@@ -768,7 +768,7 @@ extern "C" int pn_set_option(pn_system_t s, int option, int value) {
       s->guard.tau = value * 1e-6;
       return PN_OK;
     case PN_OPT_GUARD_PROBE:
-      if (value < 0 || value > 1) { pn_set_error("guard probe option takes 0 or 1"); return PN_EINVAL; }
+      if (value < 0 || value > 2) { pn_set_error("guard probe option takes 0, 1 or 2"); return PN_EINVAL; }
       s->ds.guard_probe = value;
       return PN_OK;
     case PN_OPT_DET_TABLE:

@@ -46,14 +46,21 @@ __global__ void k_geometry(DevSys s, const double* __restrict__ r, int Wn, doubl
 // ------------------------------------------------------------- orbitals
 // phi[w][i][mu][0..4] = value, gradient (3), Laplacian of the cusp-spliced
 // molecular orbital mu at electron i (one thread per electron).
+// JET = false: the values only (component 0 of each 5-slot record), for
+// value passes that need no derivatives.
+template <bool JET>
 __global__ void k_orbitals(DevSys s, const double* __restrict__ r, int Wn, double* __restrict__ phi) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= Wn * s.N) return;
-  double acc[PN_MAX_ORBITALS * 5];
-  pn_orbitals_at<true>(s, r + (size_t)idx * 3, acc);
+  constexpr int Q = JET ? 5 : 1;
+  double acc[PN_MAX_ORBITALS * Q];
+  pn_orbitals_at<JET>(s, r + (size_t)idx * 3, acc);
   const int no = s.n_orb;
   double* o = phi + (size_t)idx * no * 5;
-  for (int k = 0; k < no * 5; ++k) o[k] = acc[k];
+  if (JET)
+    for (int k = 0; k < no * 5; ++k) o[k] = acc[k];
+  else
+    for (int k = 0; k < no; ++k) o[5 * k] = acc[k];
 }
 
 // ------------------------------------------------------------- features
@@ -1076,11 +1083,11 @@ static int linear_v4_launch(const float* xf, int ldx, const float* wf, int ldw, 
   do {                                                                                                        \
     dim3 grid((rows + BM - 1) / BM, (Nout + BN - 1) / BN);                                                    \
     if (vw && vy)                                                                                             \
-      PN_LAUNCH_W(kname, st, 2.0 * rows * Kd * Nout, (k_linear_v4<BM, BN, TN, true, true, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));   \
+      PN_LAUNCH_WB(kname, st, 2.0 * rows * Kd * Nout, 4.0 * rows * (Kd + Nout * (acc ? 2 : 1)), (k_linear_v4<BM, BN, TN, true, true, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));   \
     else if (vy)                                                                                              \
-      PN_LAUNCH_W(kname, st, 2.0 * rows * Kd * Nout, (k_linear_v4<BM, BN, TN, false, true, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));  \
+      PN_LAUNCH_WB(kname, st, 2.0 * rows * Kd * Nout, 4.0 * rows * (Kd + Nout * (acc ? 2 : 1)), (k_linear_v4<BM, BN, TN, false, true, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc)));  \
     else                                                                                                      \
-      PN_LAUNCH_W(kname, st, 2.0 * rows * Kd * Nout, (k_linear_v4<BM, BN, TN, false, false, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc))); \
+      PN_LAUNCH_WB(kname, st, 2.0 * rows * Kd * Nout, 4.0 * rows * (Kd + Nout * (acc ? 2 : 1)), (k_linear_v4<BM, BN, TN, false, false, TB><<<grid, 256, 0, st>>>(xf, ldx, wf, ldw, bf, yf, ldy, rows, Kd, Nout, T, acc))); \
   } while (0)
   if (Nout <= 32) PN_LIN(256, 32, 4);  // narrow maps
   else if (Nout <= 64) PN_LIN(128, 64, 4);
@@ -1126,7 +1133,10 @@ int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw
     }
   }
   dim3 grid((rows + 63) / 64, (Nout + 63) / 64);
-  PN_LAUNCH_W("k_linear", st, 2.0 * rows * Kd * Nout, k_linear<R><<<grid, 256, 0, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, Kd, Nout, T, acc));
+  // float64 maps form a class of their own (bound by the float64 pipe)
+  PN_LAUNCH_WB(sizeof(R) == 8 ? "k_linear_f64" : "k_linear", st, 2.0 * rows * Kd * Nout,
+               (double)sizeof(R) * rows * (Kd + Nout * (acc ? 2 : 1)),
+               k_linear<R><<<grid, 256, 0, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, Kd, Nout, T, acc));
   return PN_OK;
 }
 template int pn_linear<double>(const DevSys*, int, const double*, int, const double*, int, const double*, double*, int,
@@ -1259,8 +1269,8 @@ static double pn_slater_flops(const DevSys& s, int jet) {
 template <typename R>
 static int pn_slater(const DevSys& s, const double* phi, const R* F, int Wn, int T, int jet, double* det,
                      cudaStream_t st) {
-  if (jet && !s.no_table) {
-    const int e = pn_slater_table_launch<R>(s, phi, F, Wn, T, det, st);
+  if (!s.no_table) {
+    const int e = pn_slater_table_launch<R>(s, phi, F, Wn, T, jet, det, st);
     if (e != PN_ENOTREADY) return e;
   }
   PN_LAUNCH_W("k_slater", st, Wn * pn_slater_flops(s, jet),
@@ -1274,7 +1284,10 @@ int pn_forward_chunk(const DevSys& s, const DevNet<R>& net, Work<R>& w, const do
   if (Wn <= 0) return PN_OK;
   const int T = jet ? 3 * s.N + 2 : 1;
   PN_LAUNCH("k_geometry", st, k_geometry<<<nblk((size_t)Wn * s.Ppair, 128), 128, 0, st>>>(s, r, Wn, w.geo));
-  PN_LAUNCH("k_orbitals", st, k_orbitals<<<nblk((size_t)Wn * s.N, 64), 64, 0, st>>>(s, r, Wn, w.phi));
+  if (jet)
+    PN_LAUNCH("k_orbitals", st, k_orbitals<true><<<nblk((size_t)Wn * s.N, 64), 64, 0, st>>>(s, r, Wn, w.phi));
+  else
+    PN_LAUNCH("k_orbitals", st, k_orbitals<false><<<nblk((size_t)Wn * s.N, 64), 64, 0, st>>>(s, r, Wn, w.phi));
   if (int e = pn_network_layers<R>(s, net, w, Wn, T, jet, st)) return e;
   if (int e = pn_heads<R>(s, net, w, Wn, T, st)) return e;
   if (int e = pn_slater<R>(s, w.phi, w.F, Wn, T, jet, w.det, st)) return e;
@@ -1297,11 +1310,59 @@ __global__ void k_perturb(float* __restrict__ A, size_t n, float eta) {
   A[i] *= (h & 1u) ? 1.0f + eta : 1.0f - eta;
 }
 
+// Perturbation of a linear map's output at the scale of its terms: for
+// every element y[row][n] of Y = X W, y += (+-1) * (eta_rel |y| + eta_abs
+// sum_k |x[row][k]| |W[k][n]|) (sign a hash of the element's index, the same
+// as k_perturb's).  Rounding in the map, and rounding carried in from its
+// input, enters y at the second scale and not at |y|, which cancellation can
+// make far smaller.  16 rows per block; their |x| in shared memory with a
+// padded row stride (conflict-free for one output column per row).
+__global__ void __launch_bounds__(128) k_perturb_abs(const float* __restrict__ X, int ldx, const float* __restrict__ W,
+                                                     int ldw, float* __restrict__ Y, int ldy, int rows, int Kd,
+                                                     int Nout, float eta_rel, float eta_abs) {
+  extern __shared__ float xs[];  // [16][Kd + 1]
+  const int r0 = blockIdx.x * 16, ld = Kd + 1;
+  for (int e = threadIdx.x; e < 16 * Kd; e += 128) {
+    const int rr = e / Kd, k = e - rr * Kd;
+    xs[rr * ld + k] = (r0 + rr < rows) ? fabsf(X[(size_t)(r0 + rr) * ldx + k]) : 0.f;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 16 * Nout; e += 128) {
+    const int rr = e / Nout, n = e - rr * Nout;
+    const int row = r0 + rr;
+    if (row >= rows) continue;
+    float sc = 0.f;
+    for (int k = 0; k < Kd; ++k) sc = fmaf(xs[rr * ld + k], fabsf(__ldg(W + (size_t)k * ldw + n)), sc);
+    uint32_t h = (uint32_t)((size_t)row * Nout + n) * 0x9E3779B1u;
+    h ^= h >> 15;
+    h *= 0x85EBCA77u;
+    h ^= h >> 13;
+    float* y = Y + (size_t)row * ldy + n;
+    const float d = fmaf(eta_rel, fabsf(*y), eta_abs * sc);
+    *y += (h & 1u) ? d : -d;
+  }
+}
+
+static int pn_perturb_abs(const float* X, int ldx, const float* W, int ldw, float* Y, int ldy, size_t rows, int Kd,
+                          int Nout, float eta_rel, float eta_abs, cudaStream_t st) {
+  if (rows == 0) return PN_OK;
+  if (rows > (size_t)INT32_MAX - 16) {
+    pn_set_error("guard probe: %zu rows exceed the kernel's index range", rows);
+    return PN_EINVAL;
+  }
+  const size_t smem = (size_t)16 * (Kd + 1) * sizeof(float);
+  PN_LAUNCH("k_perturb", st, k_perturb_abs<<<(unsigned)((rows + 15) / 16), 128, smem, st>>>(X, ldx, W, ldw, Y, ldy,
+                                                                                           (int)rows, Kd, Nout, eta_rel,
+                                                                                           eta_abs));
+  return PN_OK;
+}
+
 // Second evaluation of a guarded mixed chunk.  Probe 0: the heads again
 // with the other unit for their linear maps (their rounding differs), the
 // determinants of the new backflow, and E_loc with the new Jastrow factor.
 // Probe 1: the first pass's backflow and Jastrow jets perturbed by
-// +-2^-19 relative, then the determinants and E_loc again.  ln|psi| and
+// +-2^-19 relative, then the determinants and E_loc again.  Probe 2: as 1
+// with a third of 2^-19 at the heads' term scale added (k_perturb_abs).  ln|psi| and
 // sign of this pass go to scratch (the proposal buffers), E_loc to e_probe;
 // the first pass's outputs stay in w.
 int pn_probe_heads_chunk(const DevSys& s, const DevNet<float>& net, Work<float>& w, int Wn, double* e_probe,
@@ -1312,6 +1373,16 @@ int pn_probe_heads_chunk(const DevSys& s, const DevNet<float>& net, Work<float>&
     const size_t nf = (size_t)Wn * s.N * T * s.n_orb, nj = (size_t)Wn * T;
     PN_LAUNCH("k_perturb", st, k_perturb<<<nblk(nf, 256), 256, 0, st>>>(w.F, nf, 1.9073486e-6f));
     PN_LAUNCH("k_perturb", st, k_perturb<<<nblk(nj, 256), 256, 0, st>>>(w.Jj, nj, 1.9073486e-6f));
+  } else if (s.guard_probe == 2) {
+    // the last maps of both heads: backflow f = H W_k2 (+ b), Jastrow
+    // jets J = B W_e2 (+ b); their inputs H and B are still in place.
+    // +-2^-19 relative, plus a third of that at the scale of the terms
+    const NetOff& o = net.off;
+    const float er = 1.9073486e-6f, ea = 1.9073486e-6f / 3.f;
+    if (int e = pn_perturb_abs(w.H, w.ldH, net.p + o.kW[2], s.n_orb, w.F, s.n_orb, (size_t)Wn * s.N * T, s.D,
+                               s.n_orb, er, ea, st))
+      return e;
+    if (int e = pn_perturb_abs(w.Bs, s.D, net.p + o.eW[2], 1, w.Jj, 1, (size_t)Wn * T, s.D, 1, er, ea, st)) return e;
   } else {
     DevSys s2 = s;
     s2.tensor_cores ^= PN_TC_HEADS;
@@ -1331,7 +1402,7 @@ template int pn_forward_chunk<float>(const DevSys&, const DevNet<float>&, Work<f
 // Launchers used by the backward pass (value mode).
 int pn_launch_geometry_orbitals(const DevSys& s, const double* r, int Wn, double* geo, double* phi, cudaStream_t st) {
   PN_LAUNCH("k_geometry", st, k_geometry<<<nblk((size_t)Wn * s.Ppair, 128), 128, 0, st>>>(s, r, Wn, geo));
-  PN_LAUNCH("k_orbitals", st, k_orbitals<<<nblk((size_t)Wn * s.N, 64), 64, 0, st>>>(s, r, Wn, phi));
+  PN_LAUNCH("k_orbitals", st, k_orbitals<true><<<nblk((size_t)Wn * s.N, 64), 64, 0, st>>>(s, r, Wn, phi));
   return PN_OK;
 }
 

@@ -34,6 +34,9 @@ void pn_note_launch(const char* name, cudaStream_t st);
 // Algorithmic work of the launch just made (FLOPs, or bytes for kernels
 // bound by memory traffic), summed while `name` is the timed class.
 void pn_prof_work(const char* name, double work);
+// Bytes the launch just made must move through HBM at least (its inputs
+// read and outputs written once), for launch sites that know them.
+void pn_prof_bytes(const char* name, double bytes);
 #define PN_CHECK_LAUNCH() PN_CUDA(cudaGetLastError())
 #define PN_LAUNCH(name, st, ...)        \
   do {                                  \
@@ -44,7 +47,8 @@ void pn_prof_work(const char* name, double work);
     nvtxRangePop();                     \
     PN_CHECK_LAUNCH();                  \
   } while (0)
-// The same with the launch's algorithmic work (see pn_prof_work).
+// The same with the launch's algorithmic work (see pn_prof_work) and, for
+// PN_LAUNCH_WB, its algorithmic bytes (pn_prof_bytes).
 #define PN_LAUNCH_W(name, st, work, ...) \
   do {                                   \
     nvtxRangePushA(name);                \
@@ -54,6 +58,17 @@ void pn_prof_work(const char* name, double work);
     pn_prof_work(name, (double)(work));  \
     nvtxRangePop();                      \
     PN_CHECK_LAUNCH();                   \
+  } while (0)
+#define PN_LAUNCH_WB(name, st, work, bytes, ...) \
+  do {                                           \
+    nvtxRangePushA(name);                        \
+    pn_prof_begin(name, st);                     \
+    __VA_ARGS__;                                 \
+    pn_note_launch(name, st);                    \
+    pn_prof_work(name, (double)(work));          \
+    pn_prof_bytes(name, (double)(bytes));        \
+    nvtxRangePop();                              \
+    PN_CHECK_LAUNCH();                           \
   } while (0)
 
 // Allow a kernel every dynamic shared-memory size up to the device's
@@ -153,12 +168,12 @@ struct DevSys {
 #define PN_TAB_KMAX 4
 #define PN_TAB_REC (2 + 2 * PN_TAB_KMAX)
 
-// Jet determinants by the table method (slater_table.cu): PN_ENOTREADY when
-// the system has no table or the warp's matrices do not fit.
+// Determinants by the table method (slater_table.cu; value or jet mode):
+// PN_ENOTREADY when the system has no table or the warp's matrices do not fit.
 template <typename R>
-int pn_slater_table_launch(const DevSys& s, const double* phi, const R* F, int Wn, int T, double* det,
+int pn_slater_table_launch(const DevSys& s, const double* phi, const R* F, int Wn, int T, int jet, double* det,
                            cudaStream_t st);
-double pn_slater_table_flops(const DevSys& s);
+double pn_slater_table_flops(const DevSys& s, int jet);
 
 // Pair indexing: unordered electron pair (a<b) -> a*N - a*(a+1)/2 + (b-a-1)
 __host__ __device__ inline int pn_pair_index(int a, int b, int N) {

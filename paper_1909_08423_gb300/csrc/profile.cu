@@ -27,6 +27,7 @@ std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 cudaEvent_t g_pending = nullptr;
 double g_work = 0;
+double g_bytes = 0;
 
 cudaEvent_t take_event() {
   if (!g_pool.empty()) {
@@ -65,6 +66,12 @@ void pn_prof_work(const char* name, double work) {
   if (g_target == name) g_work += work;
 }
 
+void pn_prof_bytes(const char* name, double bytes) {
+  if (!g_on) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_target == name) g_bytes += bytes;
+}
+
 extern "C" unsigned long long pn_launch_count(void) { return g_launches.load(); }
 
 extern "C" int pn_profile_kernel(const char* name) {
@@ -75,6 +82,7 @@ extern "C" int pn_profile_kernel(const char* name) {
   }
   g_recs.clear();
   g_work = 0;
+  g_bytes = 0;
   g_on = name && name[0];
   g_target = g_on ? name : "";
   return PN_OK;
@@ -100,6 +108,12 @@ extern "C" int pn_profile_read(int64_t* count, double* total_ms) {
 extern "C" int pn_profile_work(double* work) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (work) *work = g_work;
+  return PN_OK;
+}
+
+extern "C" int pn_profile_bytes(double* bytes) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (bytes) *bytes = g_bytes;
   return PN_OK;
 }
 

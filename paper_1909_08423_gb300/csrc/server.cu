@@ -111,7 +111,7 @@ struct pn_server_s {
 };
 
 // Walkers per float64 re-evaluation of a serving job's local-energy guard.
-constexpr int kGuardCap = 64;
+constexpr int kGuardCap = 256;
 
 static size_t job_bytes(pn_system_t s, int W, int chunk, size_t* work_bytes, int* Wc, size_t* guard_bytes = nullptr) {
   const DevSys& ds = s->ds;

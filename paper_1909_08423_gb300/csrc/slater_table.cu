@@ -31,7 +31,8 @@
 namespace {
 
 constexpr int TW = 4;               // warps per block
-constexpr double kCondMax = 1e3;    // largest 1-norm condition number of A_0 for the table method
+constexpr double kCondMax = 1e3;    // largest 1-norm condition number of A_0 for the table method (jet)
+constexpr double kCondMaxValue = 1e5;  // the same for ln|det| alone
 
 inline unsigned nblk(size_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
@@ -87,9 +88,23 @@ __device__ inline bool small_inverse(const double* Rm, int k, double* Ri, double
   return true;
 }
 
+// Packed minor records of one spin: determinant p's starts after those of
+// determinants 0..p-1, each k^2 + 3 doubles.
+__device__ inline int pn_table_minor_offset(const int* recs, int p, int sg) {
+  int off = 0;
+  for (int q = 0; q < p; ++q) {
+    const int k = recs[(size_t)(2 * q + sg) * PN_TAB_REC];
+    off += k * k + 3;
+  }
+  return off;
+}
+__device__ inline int pn_table_minor_doubles(const int* recs, int nd, int sg) {
+  return pn_table_minor_offset(recs, nd, sg);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(TW * 32) k_slater_table(DevSys s, const double* __restrict__ phi,
-                                                          const R* __restrict__ F, int Wn, int T,
+                                                          const R* __restrict__ F, int Wn, int T, int jet,
                                                           double* __restrict__ det) {
   extern __shared__ __align__(16) double tsm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -126,6 +141,13 @@ __global__ void __launch_bounds__(TW * 32) k_slater_table(DevSys s, const double
   double* g0 = LTv + n * nv;                       // [3N] reference gradient
   double* dT = g0 + n3;                            // [3N][n][nv]
   int* perm = (int*)(dT + (size_t)n3 * n * nv);    // [n]
+  // the determinants' minors, packed (per determinant R_p^-1 then ln|det
+  // R_p|, its sign -- 0 if singular -- and tr(R_p^-1 lap R_p)): over the
+  // region Af..B, dead by then, where it fits (pn_table_minor_doubles),
+  // else after perm
+  const int* recs = s.xtab + 2 * (1 + PN_MAX_ORBITALS);
+  const int rd_need = pn_table_minor_doubles(recs, nd, sg);
+  double* RD = rd_need <= 3 * n * ncol + 3 * n * n ? Af : dT + (size_t)n3 * n * nv + n + 2;
   auto mu_of = [&](int c) { return c < n ? occ0[c] : V[c - n]; };
 
   for (int q = lane; q < n * ncol; q += 32) {
@@ -133,7 +155,7 @@ __global__ void __launch_bounds__(TW * 32) k_slater_table(DevSys s, const double
     const double* ph = phw + (i * no + mu) * 5;
     const R* f = Fw + (size_t)i * T * no + mu;
     Af[q] = ph[0] * (1.0 + (double)f[0]);
-    LA[q] = pn_aelem_lap(ph, f, no, i, lap);
+    if (jet) LA[q] = pn_aelem_lap(ph, f, no, i, lap);
   }
   for (int q = lane; q < n * nv; q += 32) S[q] = 0.0;
   if (lane < n) perm[lane] = lane;
@@ -199,10 +221,12 @@ __global__ void __launch_bounds__(TW * 32) k_slater_table(DevSys s, const double
     ca = fmax(ca, __shfl_xor_sync(0xffffffffu, ca, o));
     cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
   }
-  if (sing || !(ca * cm <= kCondMax) || s.no_table == 2) {
+  // value mode needs no derivative, so its rounding grows only with the
+  // condition number itself
+  if (sing || !(ca * cm <= (jet ? kCondMax : kCondMaxValue)) || s.no_table == 2) {
     // ill-conditioned reference block: every determinant directly
     for (int p = lane; p < nd; p += 32)
-      pn_slater_block<R, PN_TAB_NMAX>(s, phw, Fw, p, sg, T, 1, outw + (size_t)(2 * p + sg) * stride);
+      pn_slater_block<R, PN_TAB_NMAX>(s, phw, Fw, p, sg, T, jet, outw + (size_t)(2 * p + sg) * stride);
     return;
   }
   for (int q = lane; q < n * nv; q += 32) {
@@ -212,6 +236,26 @@ __global__ void __launch_bounds__(TW * 32) k_slater_table(DevSys s, const double
     Tv[q] = x;
   }
   __syncwarp();
+  if (!jet) {
+    // ln|det| and sign of every determinant from its minor of T
+    for (int p = lane; p < nd; p += 32) {
+      const int* rec = recs + (size_t)(2 * p + sg) * PN_TAB_REC;
+      const int k = rec[0];
+      double Rm[PN_TAB_KMAX * PN_TAB_KMAX], Ri[PN_TAB_KMAX * PN_TAB_KMAX];
+      double ldR = 0, sR = 1;
+      for (int r = 0; r < k; ++r)
+        for (int q = 0; q < k; ++q) Rm[r * k + q] = Tv[rec[2 + r] * nv + rec[2 + PN_TAB_KMAX + q]];
+      double* o = outw + (size_t)(2 * p + sg) * stride;
+      if (k > 0 && !small_inverse(Rm, k, Ri, &ldR, &sR)) {
+        o[0] = -INFINITY;
+        o[1] = 0.0;
+        continue;
+      }
+      o[0] = ld + ldR;
+      o[1] = sgn * rec[1] * sR;
+    }
+    return;
+  }
   // tangents, one after another, the warp's lanes over matrix entries
   double l2 = 0;
   for (int t = 1; t < lap; ++t) {
@@ -281,25 +325,46 @@ __global__ void __launch_bounds__(TW * 32) k_slater_table(DevSys s, const double
     LTv[q] = x;
   }
   __syncwarp();
-  // every determinant from its minor of T
-  const int* recs = s.xtab + 2 * (1 + PN_MAX_ORBITALS);
-  for (int p = 0; p < nd; ++p) {
+  // every determinant's minor R_p of T: inverse, ln|det|, sign and
+  // tr(R_p^-1 lap R_p), one determinant per lane (the float64 pipe runs a
+  // warp instruction at the same cost whatever its active lanes, so the
+  // small LUs run side by side rather than one after another)
+  for (int p = lane; p < nd; p += 32) {
+    const int* rec = recs + (size_t)(2 * p + sg) * PN_TAB_REC;
+    const int k = rec[0];
+    const int* H = rec + 2;
+    const int* P = rec + 2 + PN_TAB_KMAX;
+    double* rd = RD + pn_table_minor_offset(recs, p, sg);
+    double Rm[PN_TAB_KMAX * PN_TAB_KMAX];
+    double ldR = 0, sR = 1;
+    for (int r = 0; r < k; ++r)
+      for (int q = 0; q < k; ++q) Rm[r * k + q] = Tv[H[r] * nv + P[q]];
+    if (k > 0 && !small_inverse(Rm, k, rd, &ldR, &sR)) {
+      rd[k * k + 1] = 0.0;
+      continue;
+    }
+    double trlR = 0;
+    for (int r = 0; r < k; ++r)
+      for (int q = 0; q < k; ++q) trlR += rd[q * k + r] * LTv[H[r] * nv + P[q]];
+    rd[k * k] = ldR;
+    rd[k * k + 1] = sR;
+    rd[k * k + 2] = trlR;
+  }
+  __syncwarp();
+  // then per determinant its tangents, the lanes over the coordinates
+  for (int p = 0, off = 0; p < nd; ++p) {
     const int* rec = recs + (size_t)(2 * p + sg) * PN_TAB_REC;
     const int k = rec[0];
     const int* H = rec + 2;
     const int* P = rec + 2 + PN_TAB_KMAX;
     double* o = outw + (size_t)(2 * p + sg) * stride;
-    double Rm[PN_TAB_KMAX * PN_TAB_KMAX], Ri[PN_TAB_KMAX * PN_TAB_KMAX];
-    double ldR = 0, sR = 1;
-    for (int r = 0; r < k; ++r)
-      for (int q = 0; q < k; ++q) Rm[r * k + q] = Tv[H[r] * nv + P[q]];
-    if (k > 0 && !small_inverse(Rm, k, Ri, &ldR, &sR)) {
+    const double* Ri = RD + off;
+    off += k * k + 3;
+    const double ldR = Ri[k * k], sR = Ri[k * k + 1], trlR = Ri[k * k + 2];
+    if (sR == 0.0) {
       for (int q = lane; q < stride; q += 32) o[q] = q == 0 ? -INFINITY : 0.0;
       continue;
     }
-    double trlR = 0;
-    for (int r = 0; r < k; ++r)
-      for (int q = 0; q < k; ++q) trlR += Ri[q * k + r] * LTv[H[r] * nv + P[q]];
     double l2p = 0;
     for (int t0 = lane; t0 < n3; t0 += 32) {
       const double* dTt = dT + (size_t)t0 * n * nv;
@@ -330,12 +395,16 @@ __global__ void __launch_bounds__(TW * 32) k_slater_table(DevSys s, const double
 }  // namespace
 
 // Float64 work of the table kernel for one walker (multiply-add = 2).
-double pn_slater_table_flops(const DevSys& s) {
+double pn_slater_table_flops(const DevSys& s, int jet) {
   double f = 0;
   for (int sg = 0; sg < 2; ++sg) {
     const double n = sg ? s.n_dn : s.n_up, nv = s.tab_nv[sg], t = 3.0 * s.N;
     if (n == 0) continue;
     f += 2.0 * (2.0 / 3.0 * n * n * n + n * n * n + n * n * nv);   // LU, inverse, T
+    if (!jet) {
+      f += 2.0 * s.tab_k3[sg] / 3.0;                                 // LU of the minors
+      continue;
+    }
     f += t * 2.0 * (n * n * n + 3.0 * n * n * nv + n * n);          // per tangent
     f += 2.0 * (n * n + 3.0 * n * n * nv);                           // lap T
     f += t * 2.0 * s.tab_k3[sg];                                     // per determinant and tangent: R^-1 d_t R
@@ -346,7 +415,7 @@ double pn_slater_table_flops(const DevSys& s) {
 // Jet determinants by the table method when the system has a table and
 // the warp's matrices fit in shared memory; PN_ENOTREADY otherwise.
 template <typename R>
-int pn_slater_table_launch(const DevSys& s, const double* phi, const R* F, int Wn, int T, double* det,
+int pn_slater_table_launch(const DevSys& s, const double* phi, const R* F, int Wn, int T, int jet, double* det,
                            cudaStream_t st) {
   if (!s.xtab || s.tab_wstride <= 0 || Wn <= 0) return PN_ENOTREADY;
   int dev = 0, maxsm = 0;
@@ -355,11 +424,11 @@ int pn_slater_table_launch(const DevSys& s, const double* phi, const R* F, int W
   const size_t smem = (size_t)TW * s.tab_wstride * sizeof(double);
   if (smem > (size_t)maxsm) return PN_ENOTREADY;
   PN_CUDA(pn_allow_max_smem(k_slater_table<R>));
-  PN_LAUNCH_W("k_slater", st, Wn * pn_slater_table_flops(s),
-              k_slater_table<R><<<nblk((size_t)2 * Wn, TW), TW * 32, smem, st>>>(s, phi, F, Wn, T, det));
+  PN_LAUNCH_W("k_slater", st, Wn * pn_slater_table_flops(s, jet),
+              k_slater_table<R><<<nblk((size_t)2 * Wn, TW), TW * 32, smem, st>>>(s, phi, F, Wn, T, jet, det));
   return PN_OK;
 }
-template int pn_slater_table_launch<double>(const DevSys&, const double*, const double*, int, int, double*,
+template int pn_slater_table_launch<double>(const DevSys&, const double*, const double*, int, int, int, double*,
                                             cudaStream_t);
-template int pn_slater_table_launch<float>(const DevSys&, const double*, const float*, int, int, double*,
+template int pn_slater_table_launch<float>(const DevSys&, const double*, const float*, int, int, int, double*,
                                            cudaStream_t);

@@ -662,6 +662,7 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
         return (inv & 1) ? -1 : 1;
       };
       int k3 = 0;
+      size_t minor_doubles = 0;
       for (int p = 0; p < d->n_det && ok; ++p) {
         // positions of determinant p holding a reference orbital (U, at
         // reference position j) and holding a virtual one (C)
@@ -696,9 +697,13 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
           rec[2 + PN_TAB_KMAX + q] = (int)(std::find(V.begin(), V.end(), mu) - V.begin());
         }
         k3 += k * k * k;
+        minor_doubles += (size_t)k * k + 3;
       }
       const size_t nv = V.size(), ncol = n + nv, n3 = 3 * (size_t)N;
-      wstride = std::max(wstride, 3 * n * ncol + 3 * (size_t)n * n + 4 * n * nv + n3 + n3 * n * nv + n + 2);
+      // the packed minors reuse the dead matrices A..B where they fit
+      const size_t dead = 3 * n * ncol + 3 * (size_t)n * n;
+      wstride = std::max(wstride, 3 * n * ncol + 3 * (size_t)n * n + 4 * n * nv + n3 + n3 * n * nv + n + 2 +
+                                      (minor_doubles <= dead ? 0 : minor_doubles));
       ds.tab_nv[sg] = (int)nv;
       ds.tab_k3[sg] = k3;
     }

@@ -166,7 +166,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
     // ---------------------------------------------------------- producers
     // thread p owns two (row, 8-wide k group) cells of every stage; its
     // global loads run two stages ahead of the splitting and storing, so
-    // that enough bytes are in flight to cover the memory latency
+    // that enough bytes are in flight to cover the memory latency.  A warp
+    // takes one 8-row group: its lanes 8q..8q+7 store rows 0..7 of k group
+    // q, one 128-byte core matrix per quarter-warp (16-byte stores without
+    // bank conflicts)
     const int p = tid;  // 0..255
     const int my_tiles = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int nstages_total = my_tiles * nk;
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int idx = p + 256 * j;
-        const int row = idx >> 2, gk = (idx & 3) * 8;
+        const int row = ((idx >> 5) << 3) | (idx & 7), gk = ((idx >> 3) & 3) * 8;
         const int gr = r0 + row;
         if (VX && gr < rows && k0 + gk + 8 <= K) {
           const float4* src = (const float4*)(X + (size_t)gr * ldx + k0 + gk);
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int idx = p + 256 * j;
-        const int row = idx >> 2, gk = (idx & 3) * 8;
+        const int row = ((idx >> 5) << 3) | (idx & 7), gk = ((idx >> 3) & 3) * 8;
         uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -404,12 +407,12 @@ int pn_linear_tc(const float* X, int ldx, const float* W, int ldw, const float* 
   const int vy = ldy % 4 == 0 && ((uintptr_t)Y & 15) == 0;
   if (vx) {
     PN_CUDA(pn_allow_max_smem(k_linear_tc<true>));
-    PN_LAUNCH_W("k_linear_tc", st, 2.0 * rows * K * Nout,
+    PN_LAUNCH_WB("k_linear_tc", st, 2.0 * rows * K * Nout, 4.0 * rows * (K + Nout * (acc ? 2 : 1)),
                 (k_linear_tc<true><<<grid, TC_THREADS, smem, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, K, Kp, Nout, Npad, T,
                                                                    acc, ns, cols, vy, nbuf, err)));
   } else {
     PN_CUDA(pn_allow_max_smem(k_linear_tc<false>));
-    PN_LAUNCH_W("k_linear_tc", st, 2.0 * rows * K * Nout,
+    PN_LAUNCH_WB("k_linear_tc", st, 2.0 * rows * K * Nout, 4.0 * rows * (K + Nout * (acc ? 2 : 1)),
                 (k_linear_tc<false><<<grid, TC_THREADS, smem, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, K, Kp, Nout, Npad,
                                                                     T, acc, ns, cols, vy, nbuf, err)));
   }

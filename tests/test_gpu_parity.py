@@ -154,15 +154,18 @@ def test_local_energy_mixed_on_sampled_walkers(lib, oracles, name):
     assert n_guard <= 0.02 * W
 
 
-def test_guard_off_leaves_first_evaluation_and_on_replaces_flagged(lib, oracles):
+@pytest.mark.parametrize("probe", [0, 1, 2])
+def test_guard_off_leaves_first_evaluation_and_on_replaces_flagged(lib, oracles, probe):
     """With the guard off the mixed energies are the first evaluation's; with
-    it on, every walker either keeps that value or takes the float64 one."""
+    it on (any probe), every walker either keeps that value or takes the
+    float64 one."""
     sysd = oracles["h10"].sys
     W = 2048
     r = torch.as_tensor(_sampled_mixed(lib, sysd, W, 103), device="cuda")
     out = {}
     for tau in (0, 20):
         s = lib.System(sysd, precision=lib.PN_MIXED, max_walkers=1024)
+        s.set_option(lib.PN_OPT_GUARD_PROBE, probe)
         s.set_option(lib.PN_OPT_GUARD, tau)
         E = torch.empty(W, dtype=torch.float64, device="cuda")
         s.eval_local_energy(r, E)
@@ -171,7 +174,30 @@ def test_guard_off_leaves_first_evaluation_and_on_replaces_flagged(lib, oracles)
     assert out[0][1] == 0
     changed = out[20][0] != out[0][0]
     assert changed.sum() == out[20][1]
+    assert 0 < changed.sum() < W // 4
     np.testing.assert_array_equal(out[20][0][changed], E64[changed])
+
+
+@pytest.mark.parametrize("name", ["h10", "n2"])
+def test_guard_probe_with_term_scale_within_bound(lib, oracles, name):
+    """The stricter probe (relative perturbation plus one at the heads' term
+    scale) at the default tau holds every walker of the sample to 1e-4 Ha."""
+    W = 8192
+    sysd = oracles[name].sys
+    r = _sampled_mixed(lib, sysd, W, 104)
+    s = lib.System(sysd, precision=lib.PN_MIXED, max_walkers=4096)
+    s.set_option(lib.PN_OPT_GUARD_PROBE, 2)
+    s.guard_count()
+    E = torch.empty(W, dtype=torch.float64, device="cuda")
+    s.eval_local_energy(torch.as_tensor(r, device="cuda"), E)
+    n_guard = s.guard_count()
+    E64, _, _, st64 = _run_eloc(lib, sysd, r, lib.PN_FP64, 4096)
+    ok = st64 == 0
+    err = np.abs(E.cpu().numpy() - E64)[ok]
+    print(f"{name}: probe 2: max {err.max():.3e} mean {err.mean():.3e}; re-evaluated {n_guard}")
+    assert err.max() <= 1e-4
+    assert err.mean() <= 1e-5
+    assert n_guard <= 0.04 * W
 
 
 @pytest.mark.parametrize("name,mask", [("be", 7), ("h10", 4)])
