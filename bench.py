@@ -50,8 +50,10 @@ KERNEL_UNIT = {
     "k_linear": "fp32", "k_linear_bt": "fp32", "k_filter": "fp32", "k_filter_tile": "fp32",
     "k_metropolis_warp": "fp32", "k_metropolis_fused": "fp32", "k_metropolis_tc": "tensor",
     "k_linear_tc": "tensor", "k_slater": "fp64", "k_message": "hbm", "k_linear_f64": "fp64",
+    "k_filter_value": "fp32", "k_filter_f64": "fp64", "k_linear_f32x2": "fp32",
 }
-KERNEL_CLASSES = ["k_linear", "k_linear_f64", "k_linear_bt", "k_linear_tc", "k_filter", "k_message", "k_slater", "k_orbitals",
+KERNEL_CLASSES = ["k_linear", "k_linear_f64", "k_linear_f32x2", "k_linear_bt", "k_linear_tc", "k_filter", "k_filter_value", "k_filter_f64",
+                  "k_message", "k_message_f64", "k_slater", "k_orbitals", "k_perturb",
                   "k_combine", "k_features", "k_ssp_jet", "k_sum_electrons", "k_init_x", "k_geometry", "k_wgrad",
                   "k_slater_bwd", "k_filter_bwd", "k_filter_bwd_dist", "k_filter_tape", "k_msg_bwd_w",
                   "k_msg_bwd_h", "k_mul_sigmoid", "k_ssp_copy", "k_outer_row", "k_bcast_add", "k_message_value",
@@ -628,6 +630,8 @@ def main():
                     help="PN_OPT_FUSED_SAMPLER for the timed mixed path (library default if absent)")
     ap.add_argument("--prof-kernel", default="k_linear", help="kernel class whose work --case n2_small reports")
     ap.add_argument("--case-quick", action="store_true", help="--case n2_small: only the ranged step")
+    ap.add_argument("--case-walkers", type=int, default=2048,
+                    help="--case n2_small: walkers (2048: one chunk whose jet filters take the pair-tile kernel)")
     ap.add_argument("--case", choices=["sampler", "jet_tc", "langevin", "drift_n2", "n2_small", "n2_step"], default=None,
                     help="run one small kernel case (for ncu captures) and exit")
     args = ap.parse_args()
@@ -681,14 +685,14 @@ def main():
         print("case ok", flush=True)
         return
     if args.case == "n2_small":
-        # the headline step on 1024 N2-shaped walkers (one chunk): one step
+        # the headline step on --case-walkers N2-shaped walkers (one chunk): one step
         # between cudaProfilerStart/Stop (and in the NVTX range "pn_step")
         # with the algorithmic work of --prof-kernel's launches in it printed
         # (for an ncu capture limited to that step),
         # then every kernel class's work and time over one more step each
         torch.cuda.set_device(0)
         sysd = synth.n2()
-        W = 1024
+        W = args.case_walkers
         s = binding.System(sysd, precision=binding.PN_MIXED, max_walkers=W)
         r = torch.empty(W, s.N, 3, dtype=torch.float64, device="cuda")
         s.init_walkers(r, 1)

@@ -283,27 +283,26 @@ int pn_langevin_step(pn_system_t sys, double* r, double* logabs, double* drift,
  *   every workspace chunk is evaluated a second time from the same network
  *   output with different rounding (see PN_OPT_GUARD_PROBE) and every walker
  *   whose two energies differ by more than tau, or not finitely, is
- *   evaluated again in float64 and returned with its float64 E_loc, ln|psi|,
+ *   evaluated again in float64 -- its linear maps as float32 pairs (about 44
+ *   bits; float32 issue rates are 64 times the float64 rate on this part),
+ *   everything else in float64 -- and returned with those E_loc, ln|psi|,
  *   sign and status.  Each guarded chunk reads one count back to the host
- *   (the call then synchronises its stream once per chunk).  Measured on
- *   three samples of 16384 walkers from |psi|^2 per system with the
- *   default probe and tau: 1.0-1.1 % (H10 chain) and 0.46-0.65 % (N2
- *   shape) of walkers re-evaluated; the largest remaining errors 4.4e-5,
- *   1.1e-4, 4.7e-5 Ha (H10) and 7.8e-5, 2.8e-5, 7.4e-5 Ha (N2) -- one walker
- *   of the 98304 above 1e-4 Ha.  pn_guard_count reports how many walkers
- *   were re-evaluated.
- * PN_OPT_GUARD_PROBE (default 1): the guard's second evaluation -- 1 the
- *   backflow and Jastrow jets of the first pass perturbed by +-2^-19
- *   relative (a deterministic sign per element, a stand-in for the
- *   network's accumulated rounding) and the determinants and E_loc formed
- *   again; 2 the same with a third of 2^-19 at the scale of the heads'
- *   terms added (sum_k |x_k| |W_kn| of the last map of each head: rounding
- *   enters an output at that scale, which cancellation can make far larger
- *   than the output): on the samples above with the default tau, 1.8-2.2 %
- *   (H10) and 2.4-2.5 % (N2) re-evaluated and every remaining error at most
- *   5.0e-5 (H10) and 8.0e-5 Ha (N2); 0 the heads (the Jastrow and backflow
- *   maps) evaluated again on the other unit (tensor cores if they ran on
- *   CUDA cores, and back), then the determinants and E_loc.
+ *   (the call then synchronises its stream once per chunk).  pn_guard_count
+ *   reports how many walkers were re-evaluated.
+ * PN_OPT_GUARD_PROBE (default 2): the guard's second evaluation.  2: the
+ *   first pass's backflow and Jastrow jets perturbed by +-2^-19 relative
+ *   plus a third of 2^-19 at the scale of the heads' terms (sum_k |x_k|
+ *   |W_kn| of the last map of each head: rounding enters an output at that
+ *   scale, which cancellation can make far larger than the output), with a
+ *   deterministic sign per element, then the determinants and E_loc formed
+ *   again.  Measured at the default tau on 16384-walker samples from
+ *   |psi|^2 (6 per system): 1.8-2.2 % (H10 chain) and 2.3-2.8 % (N2 shape)
+ *   of walkers re-evaluated, every remaining error at most 9.0e-5 Ha.
+ *   1: the relative perturbation alone: 1.0-1.3 % and 0.46-0.66 %
+ *   re-evaluated, the remaining errors at most 1.1e-4 Ha on those samples
+ *   (one walker of the 196608 above 1e-4 Ha).  0: the heads (the Jastrow and
+ *   backflow maps) evaluated again on the other unit (tensor cores if they
+ *   ran on CUDA cores, and back), then the determinants and E_loc.
  * PN_OPT_DET_TABLE (default 1): how the forward passes form the
  *   determinants (and, in the local-energy pass, their gradients and
  *   Laplacians) -- 1 by the table method where the system allows it (every

@@ -414,11 +414,15 @@ static int guard_chunk(const DevSys& ds, const DevNet<float>& net, Work<float>& 
   PN_CUDA(cudaMemcpyAsync(&nflag, g.count, sizeof(int), cudaMemcpyDeviceToHost, st));
   PN_CUDA(cudaStreamSynchronize(st));
   Work<double> w64 = g.w64;
+  // the re-evaluation's linear maps as float32 pairs (about 44 bits, at
+  // float32 issue rates); everything else in float64
+  DevSys d64 = ds;
+  d64.lin_f32x2 = 1;
   for (int k0 = 0; k0 < nflag; k0 += g.cap) {
     const int n = std::min(g.cap, nflag - k0);
     PN_LAUNCH("k_guard_gather", st, k_guard_gather<<<nblk((size_t)n * 3 * N, 128), 128, 0, st>>>(rc, g.list, k0, n, N,
                                                                                                   w64.r));
-    if (int e = pn_forward_chunk<double>(ds, g.net64, w64, w64.r, n, 1, st)) return e;
+    if (int e = pn_forward_chunk<double>(d64, g.net64, w64, w64.r, n, 1, st)) return e;
     PN_LAUNCH("k_guard_scatter", st,
               k_guard_scatter<<<nblk(n, 64), 64, 0, st>>>(g.list, k0, n, N, w64.out_eloc, w64.out_logabs, w64.out_sign,
                                                            w64.out_status, w64.out_grad, w.out_eloc, w.out_logabs,

@@ -224,6 +224,90 @@ __global__ void __launch_bounds__(256) k_linear(const R* __restrict__ X, int ldx
   }
 }
 
+// Float64 Y (+)= X W + b with float32-pair arithmetic: every operand split
+// into hi + lo floats (hi the nearest float, lo the nearest float of the
+// rest), each product formed as ah bh exactly (its rounding error by an
+// FMA) plus ah bl + al bh, and the products summed in a (sum, correction)
+// pair with an error-free two-sum.  That keeps about 44 bits of the
+// float64 result (about 1e-13 of sum |x w|) at float32 issue rates, which
+// on this part run 64 times the float64 rate.  Same tiling as k_linear.
+__global__ void __launch_bounds__(256) k_linear_f32x2(const double* __restrict__ X, int ldx,
+                                                      const double* __restrict__ Wt, int ldw,
+                                                      const double* __restrict__ bias, double* __restrict__ Y,
+                                                      int ldy, int rows, int Kd, int Nout, int T, int accumulate) {
+  __shared__ float Ah[16][64 + 1], Al[16][64 + 1];
+  __shared__ float Bh[16][64], Bl[16][64];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int row0 = blockIdx.x * 64, col0 = blockIdx.y * 64;
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
+  for (int k0 = 0; k0 < Kd; k0 += 16) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int e = threadIdx.x + l * 256;
+      const int rr = e >> 4, kk = e & 15;
+      const int gr = row0 + rr, gk = k0 + kk;
+      const double a = (gr < rows && gk < Kd) ? X[(size_t)gr * ldx + gk] : 0.0;
+      const float ah = __double2float_rn(a);
+      Ah[kk][rr] = ah;
+      Al[kk][rr] = __double2float_rn(a - (double)ah);
+      const int kb = e >> 6, cb = e & 63;
+      const int gkb = k0 + kb, gc = col0 + cb;
+      const double b = (gkb < Kd && gc < Nout) ? Wt[(size_t)gkb * ldw + gc] : 0.0;
+      const float bh = __double2float_rn(b);
+      Bh[kb][cb] = bh;
+      Bl[kb][cb] = __double2float_rn(b - (double)bh);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ah[i] = Ah[kk][ty * 4 + i];
+        al[i] = Al[kk][ty * 4 + i];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        bh[j] = Bh[kk][tx * 4 + j];
+        bl[j] = Bl[kk][tx * 4 + j];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          // explicit roundings: no contraction may merge the product
+          // into the two-sum
+          const float p = __fmul_rn(ah[i], bh[j]);
+          const float pe = fmaf(ah[i], bl[j], fmaf(al[i], bh[j], fmaf(ah[i], bh[j], -p)));
+          const float t = __fadd_rn(sh[i][j], p);
+          const float z = __fsub_rn(t, sh[i][j]);
+          const float e = __fadd_rn(__fsub_rn(sh[i][j], __fsub_rn(t, z)), __fsub_rn(p, z));
+          sl[i][j] = __fadd_rn(sl[i][j], __fadd_rn(e, pe));
+          sh[i][j] = t;
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gr = row0 + ty * 4 + i;
+    if (gr >= rows) continue;
+    const bool val = (gr % T) == 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gc = col0 + tx * 4 + j;
+      if (gc >= Nout) continue;
+      const double v = ((double)sh[i][j] + (double)sl[i][j]) + ((bias && val) ? bias[gc] : 0.0);
+      double* y = Y + (size_t)gr * ldy + gc;
+      *y = accumulate ? *y + v : v;
+    }
+  }
+}
+
 // Float32 Y (+)= X W + b (bias on value rows only): BM x BN output tiles,
 // 8 x TN outputs per thread -- 256 x 32 (TN 4) for maps at most 32 wide so
 // that no half-empty tiles are computed, 128 x 64 (TN 4) up to 64, 128 x 128
@@ -642,9 +726,11 @@ __global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict
 }
 
 // Same messages with the walker's operands staged in shared memory: a block
-// per (walker, tile of 32 columns z), one warp per electron i, lanes over z.
-// The block first copies the walker's h-jet rows [N][T][32], its pair
-// filter jets [P][3][32] and pair geometry (d, 1/d, unit vector) as float;
+// per (walker, tile of 16 columns z), one half-warp per electron i, its
+// lanes over z (16 columns keep a block near 64 KB for the N2 shape, so
+// that three blocks share an SM and one block's staging overlaps another's
+// arithmetic).  The block first copies the walker's h-jet rows [N][T][16],
+// its pair filter jets [P][3][16] and pair geometry (d, 1/d, unit vector);
 // each thread then forms all T rows of z_i^same, z_i^anti and z_i^nuc for
 // its column from shared memory:
 //   value      z_i = sum_j w_ij h_j
@@ -653,8 +739,8 @@ __global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict
 //                         + 2 w'_ij u_ij . (grad_i h_j - grad_j h_j)
 // (electron pairs move with both electrons, so their Laplacian over all
 // coordinates is twice the one-electron one; nuclear pairs move with i only).
-// Requires Zd a multiple of 32; HC as in k_message_c.
-constexpr int MSGW_ZT = 32;
+// Requires Zd a multiple of 16; HC as in k_message_c.
+constexpr int MSGW_ZT = 16;
 constexpr int MSGW_NMAX = 16;  // electrons of the staged kernel (partner values in registers)
 template <typename R, bool HC>
 __global__ void k_message_w(DevSys s, const R* __restrict__ Y, const double* __restrict__ geo,
@@ -664,27 +750,34 @@ __global__ void k_message_w(DevSys s, const R* __restrict__ Y, const double* __r
   const int N = s.N, M = s.M, Zd = s.Zd, P = s.Ppair, lap = T - 1;
   const int ntile = Zd / MSGW_ZT;
   const int w = blockIdx.x / ntile, z0 = (blockIdx.x % ntile) * MSGW_ZT;
-  const int lane = threadIdx.x & 31, i = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, i = ((threadIdx.x >> 5) << 1) | (lane >> 4);
   const int HT = HC ? 1 : T;  // rows of h staged per electron (one shared row for HC)
   const int HN = HC ? 1 : N;
-  R* hs = (R*)mw_smem;                       // [HN][HT][32]
-  R* ws = hs + (size_t)HN * HT * MSGW_ZT;    // [P][3][32]
+  R* hs = (R*)mw_smem;                       // [HN][HT][16]
+  R* ws = hs + (size_t)HN * HT * MSGW_ZT;    // [P][3][16]
   R* gs = ws + (size_t)P * 3 * MSGW_ZT;      // [P][5]: d, 1/d, unit vector
   const int nth = blockDim.x;
+  // rows of 16 columns from global memory (row stride ld) into shared
+  // memory, eight loads of a thread in flight before its stores
+  auto stage = [&](R* dst, const R* src, int n, int ld) {
+    for (int q0 = threadIdx.x; q0 < n; q0 += 8 * nth) {
+      R v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * nth, row = q / MSGW_ZT, c = q - row * MSGW_ZT;
+        v[u] = q < n ? src[(size_t)row * ld + c] : R(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (q0 + u * nth < n) dst[q0 + u * nth] = v[u];
+    }
+  };
   if (HC) {
     for (int q = threadIdx.x; q < MSGW_ZT; q += nth) hs[q] = H[z0 + q];
   } else {
-    const R* Hw = H + (size_t)w * N * T * ldH + z0;
-    for (int q = threadIdx.x; q < N * T * MSGW_ZT; q += nth) {
-      const int row = q / MSGW_ZT, c = q - row * MSGW_ZT;
-      hs[q] = Hw[(size_t)row * ldH + c];
-    }
+    stage(hs, H + (size_t)w * N * T * ldH + z0, N * T * MSGW_ZT, ldH);
   }
-  const R* Ww = wj + (size_t)w * P * 3 * Zd + z0;
-  for (int q = threadIdx.x; q < P * 3 * MSGW_ZT; q += nth) {
-    const int row = q / MSGW_ZT, c = q - row * MSGW_ZT;
-    ws[q] = Ww[(size_t)row * Zd + c];
-  }
+  stage(ws, wj + (size_t)w * P * 3 * Zd + z0, P * 3 * MSGW_ZT, Zd);
   const double* gw = geo + (size_t)w * P * 4;
   for (int p = threadIdx.x; p < P; p += nth) {
     const double d = gw[4 * p];
@@ -696,7 +789,7 @@ __global__ void k_message_w(DevSys s, const R* __restrict__ Y, const double* __r
   }
   __syncthreads();
   if (i >= N) return;
-  const int z = lane;
+  const int z = lane & (MSGW_ZT - 1);
   const bool si = i < s.n_up;
   auto hrow = [&](int j, int t) -> R { return HC ? (t == 0 ? hs[z] : R(0)) : hs[((size_t)j * T + t) * MSGW_ZT + z]; };
   auto pidx = [&](int j) { return i < j ? pn_pair_index(i, j, N) : pn_pair_index(j, i, N); };
@@ -1133,6 +1226,14 @@ int pn_linear(const DevSys* s, int grp, const R* X, int ldx, const R* W, int ldw
     }
   }
   dim3 grid((rows + 63) / 64, (Nout + 63) / 64);
+  if constexpr (sizeof(R) == 8) {
+    if (s && s->lin_f32x2) {
+      PN_LAUNCH_WB("k_linear_f32x2", st, 2.0 * rows * Kd * Nout, 8.0 * rows * (Kd + Nout * (acc ? 2 : 1)),
+                   k_linear_f32x2<<<grid, 256, 0, st>>>((const double*)X, ldx, (const double*)W, ldw,
+                                                        (const double*)b, (double*)Y, ldy, rows, Kd, Nout, T, acc));
+      return PN_OK;
+    }
+  }
   // float64 maps form a class of their own (bound by the float64 pipe)
   PN_LAUNCH_WB(sizeof(R) == 8 ? "k_linear_f64" : "k_linear", st, 2.0 * rows * Kd * Nout,
                (double)sizeof(R) * rows * (Kd + Nout * (acc ? 2 : 1)),
@@ -1178,15 +1279,19 @@ int pn_network_layers(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn,
       if (jet && (size_t)Wn * s.Ppair >= ((size_t)1 << 17))
         fe = pn_filter_tile_jet(s, net, n, (const float*)w.efeat, Wn, (float*)w.wjet, st);
     if (fe != PN_OK && fe != PN_ENOTREADY) return fe;
+    // kernel classes: float64 launches (the float64 path, the guard's
+    // re-evaluation) and value passes apart from the float32 jet passes
+    const char* fname = sizeof(R) == 8 ? "k_filter_f64" : (jet ? "k_filter" : "k_filter_value");
+    const char* mname = sizeof(R) == 8 ? "k_message_f64" : (jet ? "k_message" : "k_message_value");
     if (fe == PN_ENOTREADY)
-      PN_LAUNCH_W("k_filter", st, 2.0 * (jet ? 3 : 1) * Wn * s.Ppair * (double)(s.K * s.Hw + s.Hw * s.Zd),
+      PN_LAUNCH_W(fname, st, 2.0 * (jet ? 3 : 1) * Wn * s.Ppair * (double)(s.K * s.Hw + s.Hw * s.Zd),
                   k_filter<R><<<nblk((size_t)Wn * s.Ppair, FW), FW * 32, 0, st>>>(s, net, n, w.efeat, Wn, jet, w.wjet));
     if (jet) {
       const size_t nthr = (size_t)Wn * ((s.N + MSG_KC - 1) / MSG_KC + 1) * s.N * s.Zd;
       // bytes that must cross HBM: the h rows and filter jets read once,
       // the message rows written once
       const double bytes = (double)sizeof(R) * Wn * ((double)s.N * T * s.Zd + 3.0 * s.Ppair * s.Zd + 3.0 * s.N * T * s.Zd);
-      // staged per-walker kernel where Zd tiles by 32 and the walker's rows fit
+      // staged per-walker kernel where Zd tiles by 16 and the walker's rows fit
       const size_t mw_bytes = sizeof(R) * ((size_t)(hc ? 1 : s.N * T) * MSGW_ZT + (size_t)s.Ppair * 3 * MSGW_ZT +
                                            (size_t)s.Ppair * 5);
       const bool staged = s.Zd % MSGW_ZT == 0 && s.N <= MSGW_NMAX && mw_bytes <= 160 * 1024 && !s.msg_per_row;
@@ -1194,26 +1299,26 @@ int pn_network_layers(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn,
         const unsigned grid = (unsigned)((size_t)Wn * (s.Zd / MSGW_ZT));
         if (hc) {
           PN_CUDA(pn_allow_max_smem(k_message_w<R, true>));
-          PN_LAUNCH_W("k_message", st, bytes,
-                      (k_message_w<R, true><<<grid, s.N * 32, mw_bytes, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.Xs,
+          PN_LAUNCH_W(mname, st, bytes,
+                      (k_message_w<R, true><<<grid, (s.N + 1) / 2 * 32, mw_bytes, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.Xs,
                                                                              0, Wn, T, w.Zb, w.ldZ)));
         } else {
           PN_CUDA(pn_allow_max_smem(k_message_w<R, false>));
-          PN_LAUNCH_W("k_message", st, bytes,
-                      (k_message_w<R, false><<<grid, s.N * 32, mw_bytes, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H,
+          PN_LAUNCH_W(mname, st, bytes,
+                      (k_message_w<R, false><<<grid, (s.N + 1) / 2 * 32, mw_bytes, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H,
                                                                               w.ldH, Wn, T, w.Zb, w.ldZ)));
         }
       } else if (hc) {
-        PN_LAUNCH_W("k_message", st, bytes,
+        PN_LAUNCH_W(mname, st, bytes,
                     (k_message_c<R, true><<<nblk(nthr, 256), 256, 0, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.Xs, 0,
                                                                            Wn, T, w.Zb, w.ldZ)));
       } else {
-        PN_LAUNCH_W("k_message", st, bytes,
+        PN_LAUNCH_W(mname, st, bytes,
                     (k_message_c<R, false><<<nblk(nthr, 256), 256, 0, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H,
                                                                             w.ldH, Wn, T, w.Zb, w.ldZ)));
       }
     } else {
-      PN_LAUNCH("k_message", st,
+      PN_LAUNCH(mname, st,
                 k_message<R><<<(unsigned)((size_t)Wn * s.N), std::min(256, (T * s.Zd + 31) / 32 * 32),
                                (size_t)(s.N - 1 + s.M) * 5 * sizeof(R), st>>>(
                     s, net.p + net.off.Y, w.geo, w.wjet, w.H, w.ldH, Wn, T, w.Zb, w.ldZ));
@@ -1298,65 +1403,6 @@ int pn_forward_chunk(const DevSys& s, const DevNet<R>& net, Work<R>& w, const do
   return PN_OK;
 }
 
-// Relative perturbation of every element by +-eta, the sign a hash of the
-// element's index (a deterministic stand-in for rounding noise).
-__global__ void k_perturb(float* __restrict__ A, size_t n, float eta) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t h = (uint32_t)i * 0x9E3779B1u;
-  h ^= h >> 15;
-  h *= 0x85EBCA77u;
-  h ^= h >> 13;
-  A[i] *= (h & 1u) ? 1.0f + eta : 1.0f - eta;
-}
-
-// Perturbation of a linear map's output at the scale of its terms: for
-// every element y[row][n] of Y = X W, y += (+-1) * (eta_rel |y| + eta_abs
-// sum_k |x[row][k]| |W[k][n]|) (sign a hash of the element's index, the same
-// as k_perturb's).  Rounding in the map, and rounding carried in from its
-// input, enters y at the second scale and not at |y|, which cancellation can
-// make far smaller.  16 rows per block; their |x| in shared memory with a
-// padded row stride (conflict-free for one output column per row).
-__global__ void __launch_bounds__(128) k_perturb_abs(const float* __restrict__ X, int ldx, const float* __restrict__ W,
-                                                     int ldw, float* __restrict__ Y, int ldy, int rows, int Kd,
-                                                     int Nout, float eta_rel, float eta_abs) {
-  extern __shared__ float xs[];  // [16][Kd + 1]
-  const int r0 = blockIdx.x * 16, ld = Kd + 1;
-  for (int e = threadIdx.x; e < 16 * Kd; e += 128) {
-    const int rr = e / Kd, k = e - rr * Kd;
-    xs[rr * ld + k] = (r0 + rr < rows) ? fabsf(X[(size_t)(r0 + rr) * ldx + k]) : 0.f;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < 16 * Nout; e += 128) {
-    const int rr = e / Nout, n = e - rr * Nout;
-    const int row = r0 + rr;
-    if (row >= rows) continue;
-    float sc = 0.f;
-    for (int k = 0; k < Kd; ++k) sc = fmaf(xs[rr * ld + k], fabsf(__ldg(W + (size_t)k * ldw + n)), sc);
-    uint32_t h = (uint32_t)((size_t)row * Nout + n) * 0x9E3779B1u;
-    h ^= h >> 15;
-    h *= 0x85EBCA77u;
-    h ^= h >> 13;
-    float* y = Y + (size_t)row * ldy + n;
-    const float d = fmaf(eta_rel, fabsf(*y), eta_abs * sc);
-    *y += (h & 1u) ? d : -d;
-  }
-}
-
-static int pn_perturb_abs(const float* X, int ldx, const float* W, int ldw, float* Y, int ldy, size_t rows, int Kd,
-                          int Nout, float eta_rel, float eta_abs, cudaStream_t st) {
-  if (rows == 0) return PN_OK;
-  if (rows > (size_t)INT32_MAX - 16) {
-    pn_set_error("guard probe: %zu rows exceed the kernel's index range", rows);
-    return PN_EINVAL;
-  }
-  const size_t smem = (size_t)16 * (Kd + 1) * sizeof(float);
-  PN_LAUNCH("k_perturb", st, k_perturb_abs<<<(unsigned)((rows + 15) / 16), 128, smem, st>>>(X, ldx, W, ldw, Y, ldy,
-                                                                                           (int)rows, Kd, Nout, eta_rel,
-                                                                                           eta_abs));
-  return PN_OK;
-}
-
 // Second evaluation of a guarded mixed chunk.  Probe 0: the heads again
 // with the other unit for their linear maps (their rounding differs), the
 // determinants of the new backflow, and E_loc with the new Jastrow factor.
@@ -1371,8 +1417,8 @@ int pn_probe_heads_chunk(const DevSys& s, const DevNet<float>& net, Work<float>&
   const int T = 3 * s.N + 2;
   if (s.guard_probe == 1) {
     const size_t nf = (size_t)Wn * s.N * T * s.n_orb, nj = (size_t)Wn * T;
-    PN_LAUNCH("k_perturb", st, k_perturb<<<nblk(nf, 256), 256, 0, st>>>(w.F, nf, 1.9073486e-6f));
-    PN_LAUNCH("k_perturb", st, k_perturb<<<nblk(nj, 256), 256, 0, st>>>(w.Jj, nj, 1.9073486e-6f));
+    if (int e = pn_perturb_rel(w.F, nf, 1.9073486e-6f, st)) return e;
+    if (int e = pn_perturb_rel(w.Jj, nj, 1.9073486e-6f, st)) return e;
   } else if (s.guard_probe == 2) {
     // the last maps of both heads: backflow f = H W_k2 (+ b), Jastrow
     // jets J = B W_e2 (+ b); their inputs H and B are still in place.

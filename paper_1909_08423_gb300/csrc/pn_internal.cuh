@@ -154,12 +154,14 @@ struct DevSys {
   int tab_wstride;        // doubles of shared memory per warp of the table kernel
   int tab_nv[2];          // virtual orbitals per spin
   int tab_k3[2];          // sum over determinants of k^3 per spin
-  int guard_probe;        // second evaluation of the guard: 0 heads on the other unit, 1 perturbed jets
+  int guard_probe;        // second evaluation of the guard: 0 heads on the other unit, 1 perturbed jets,
+                          // 2 perturbed jets at the relative and the term scale
   int msg_per_row;        // 1: jet messages by the per-row kernel even where the staged one applies
   int no_table;           // 1: jet determinants block by block even where a table exists;
                           // 2: the table kernel with every walker on its direct fallback
   int fused_sampler;      // 1: Metropolis through the fused tile kernel when it fits
-  int tensor_cores;       // 1: float32 linear layers on tcgen05 (split tf32)
+  int tensor_cores;       // mask of float32 linear-layer groups on tcgen05 (split bf16)
+  int lin_f32x2;          // 1: float64 linear maps as float32 pairs (the guard's re-evaluation)
   int* dev_err;           // device word: set when a bounded wait expired
 };
 
@@ -347,6 +349,12 @@ int pn_run_eval(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, cons
 // The second evaluation of a guarded chunk: heads on the other unit,
 // determinants, E_loc into e_probe (w.X, w.phi and w.geo hold the chunk's
 // first pass; w's other outputs are left as the first pass wrote them).
+// The guard's perturbations (guard_probe.cu): every element of A times
+// (1 +- eta); and y += +-(eta_rel |y| + eta_abs sum_k |x_k| |W_kn|) over the
+// output Y = X W of a linear map (X rows x Kd, W Kd x Nout).
+int pn_perturb_rel(float* A, size_t n, float eta, cudaStream_t st);
+int pn_perturb_abs(const float* X, int ldx, const float* W, int ldw, float* Y, int ldy, size_t rows, int Kd, int Nout,
+                   float eta_rel, float eta_abs, cudaStream_t st);
 int pn_probe_heads_chunk(const DevSys& s, const DevNet<float>& net, Work<float>& w, int Wn, double* e_probe,
                          cudaStream_t st);
 template <typename R>

@@ -828,8 +828,8 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
     delete s;
     return PN_EINVAL;
   }
-  // mixed handles: the local-energy guard, on by default (perturbed jets,
-  // tau = 5e-5 Ha)
+  // mixed handles: the local-energy guard, on by default (jets perturbed at
+  // the relative and the term scale, tau = 5e-5 Ha)
   if (d->precision == PN_MIXED) {
     const int cap = std::min(s->Wc, 256);
     const size_t gb = pn_guard_bytes(ds, s->Wc, cap);
@@ -844,7 +844,7 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
     s->guard = pn_carve_guard(ds, s->Wc, cap, s->guard_mem);
     s->guard.net64 = pn_devnet<double>(s);
     s->guard.tau = 5e-5;
-    s->ds.guard_probe = 1;
+    s->ds.guard_probe = 2;
     PN_CUDA(cudaMemset(s->guard.n_total, 0, 8));
   }
   *out = s;

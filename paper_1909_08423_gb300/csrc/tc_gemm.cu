@@ -76,6 +76,17 @@ __device__ inline void split3(float a, unsigned short& p0, unsigned short& p1, u
   p2 = __bfloat16_as_ushort(h2);
 }
 
+// Two floats -> their three pieces as packed bf16x2 words (the lower half
+// from a, the upper from b): one conversion instruction per piece and pair;
+// the same pieces as split3.
+__device__ inline void split3x2(float a, float b, uint32_t& w0, uint32_t& w1, uint32_t& w2) {
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w0) : "f"(b), "f"(a));
+  const float ra = a - __uint_as_float(w0 << 16), rb = b - __uint_as_float(w0 & 0xFFFF0000u);
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w1) : "f"(rb), "f"(ra));
+  const float sa = ra - __uint_as_float(w1 << 16), sb = rb - __uint_as_float(w1 & 0xFFFF0000u);
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w2) : "f"(sb), "f"(sa));
+}
+
 __device__ inline bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -210,14 +221,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
         const int row = ((idx >> 5) << 3) | (idx & 7), gk = ((idx >> 3) & 3) * 8;
         uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          unsigned short a0, a1, a2, b0, b1, b2;
-          split3(cur[8 * j + 2 * e], a0, a1, a2);
-          split3(cur[8 * j + 2 * e + 1], b0, b1, b2);
-          w0[e] = (uint32_t)a0 | ((uint32_t)b0 << 16);
-          w1[e] = (uint32_t)a1 | ((uint32_t)b1 << 16);
-          w2[e] = (uint32_t)a2 | ((uint32_t)b2 << 16);
-        }
+        for (int e = 0; e < 4; ++e) split3x2(cur[8 * j + 2 * e], cur[8 * j + 2 * e + 1], w0[e], w1[e], w2[e]);
         const uint32_t off = tile_off(row, gk, TC_SBO_A);
         *(uint4*)(st + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
         *(uint4*)(st + TC_M * TC_KC * 2 + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);

@@ -151,14 +151,15 @@ def test_local_energy_mixed_on_sampled_walkers(lib, oracles, name):
           f"p99.9 {np.quantile(err, 0.999):.3e}; guard re-evaluated {n_guard}")
     assert err.max() <= 1e-4
     assert err.mean() <= 1e-5
-    assert n_guard <= 0.02 * W
+    assert n_guard <= 0.04 * W
 
 
 @pytest.mark.parametrize("probe", [0, 1, 2])
 def test_guard_off_leaves_first_evaluation_and_on_replaces_flagged(lib, oracles, probe):
     """With the guard off the mixed energies are the first evaluation's; with
     it on (any probe), every walker either keeps that value or takes the
-    float64 one."""
+    float64 one (the re-evaluation's linear maps run as float32 pairs,
+    about 44 bits, so the two agree far inside the bound)."""
     sysd = oracles["h10"].sys
     W = 2048
     r = torch.as_tensor(_sampled_mixed(lib, sysd, W, 103), device="cuda")
@@ -175,29 +176,35 @@ def test_guard_off_leaves_first_evaluation_and_on_replaces_flagged(lib, oracles,
     changed = out[20][0] != out[0][0]
     assert changed.sum() == out[20][1]
     assert 0 < changed.sum() < W // 4
-    np.testing.assert_array_equal(out[20][0][changed], E64[changed])
+    d = np.abs(out[20][0][changed] - E64[changed])
+    assert np.all(d <= 1e-7 * (1 + np.abs(E64[changed]))), d.max()
 
 
 @pytest.mark.parametrize("name", ["h10", "n2"])
-def test_guard_probe_with_term_scale_within_bound(lib, oracles, name):
-    """The stricter probe (relative perturbation plus one at the heads' term
-    scale) at the default tau holds every walker of the sample to 1e-4 Ha."""
+def test_guard_relative_probe_trades_tail_for_fewer_reevaluations(lib, oracles, name):
+    """The cheaper probe (relative perturbation only) at the default tau
+    re-evaluates fewer walkers than the default probe and keeps the mean
+    bound; its tail is looser (about one walker in 10^5 between 1e-4 and
+    2e-4 Ha on samples of these systems), so it is held to 2e-4 here."""
     W = 8192
     sysd = oracles[name].sys
     r = _sampled_mixed(lib, sysd, W, 104)
-    s = lib.System(sysd, precision=lib.PN_MIXED, max_walkers=4096)
-    s.set_option(lib.PN_OPT_GUARD_PROBE, 2)
-    s.guard_count()
-    E = torch.empty(W, dtype=torch.float64, device="cuda")
-    s.eval_local_energy(torch.as_tensor(r, device="cuda"), E)
-    n_guard = s.guard_count()
+    rd = torch.as_tensor(r, device="cuda")
     E64, _, _, st64 = _run_eloc(lib, sysd, r, lib.PN_FP64, 4096)
     ok = st64 == 0
-    err = np.abs(E.cpu().numpy() - E64)[ok]
-    print(f"{name}: probe 2: max {err.max():.3e} mean {err.mean():.3e}; re-evaluated {n_guard}")
-    assert err.max() <= 1e-4
-    assert err.mean() <= 1e-5
-    assert n_guard <= 0.04 * W
+    counts = {}
+    for probe in (1, 2):
+        s = lib.System(sysd, precision=lib.PN_MIXED, max_walkers=4096)
+        s.set_option(lib.PN_OPT_GUARD_PROBE, probe)
+        s.guard_count()
+        E = torch.empty(W, dtype=torch.float64, device="cuda")
+        s.eval_local_energy(rd, E)
+        counts[probe] = s.guard_count()
+        err = np.abs(E.cpu().numpy() - E64)[ok]
+        print(f"{name}: probe {probe}: max {err.max():.3e} mean {err.mean():.3e}; re-evaluated {counts[probe]}")
+        assert err.max() <= (2e-4 if probe == 1 else 1e-4)
+        assert err.mean() <= 1e-5
+    assert counts[1] < counts[2]
 
 
 @pytest.mark.parametrize("name,mask", [("be", 7), ("h10", 4)])
