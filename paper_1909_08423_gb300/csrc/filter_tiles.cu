@@ -119,7 +119,8 @@ __device__ inline void zero_acc(float acc[4][NJ]) {
 template <int NJ>
 __global__ void __launch_bounds__(256) k_filter_tile_value(DevSys s, DevNet<float> net, int n,
                                                            const float* __restrict__ ef, int Wn, FTiles ft,
-                                                           float* __restrict__ Ah, float* __restrict__ wv) {
+                                                           float* __restrict__ Ah, float* __restrict__ wv,
+                                                           int ldw) {
   extern __shared__ __align__(16) float fsm[];
   __shared__ int sgr[RB];
   const int K = s.K, Hw = s.Hw, Zd = s.Zd, LW = 16 * NJ;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(256) k_filter_tile_value(DevSys s, DevNet<floa
     for (int i = 0; i < 4; ++i) {
       const int row = ty * 4 + i, g = sgr[row];
       const float a = acc[i][j];
-      if (g >= 0) Ah[(size_t)g * Hw + h] = a;
+      if (Ah && g >= 0) Ah[(size_t)g * Hw + h] = a;
       Ht[h * LA + row] = sspf_(a);
     }
   }
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(256) k_filter_tile_value(DevSys s, DevNet<floa
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int g = sgr[ty * 4 + i];
-      if (g >= 0) wv[(size_t)g * Zd + z] = acc[i][j];
+      if (g >= 0) wv[(size_t)g * ldw + z] = acc[i][j];
     }
   }
 }
@@ -382,7 +383,16 @@ int pn_filter_tile_value(const DevSys& s, const DevNet<float>& net, int n, const
                          float* wv, cudaStream_t st) {
 #define BYTES(LW) ((size_t)s.K * (LW) + (size_t)s.Hw * (LW) + (size_t)s.K * LA + (size_t)(LW) * LA)
   const double ft_work = 2.0 * Wn * s.Ppair * ((double)s.K * s.Hw + (double)s.Hw * s.Zd);
-  PN_FT_LAUNCH("k_filter_tape", k_filter_tile_value, BYTES, s, net, n, ef, Wn, ft, Ah, wv);
+  PN_FT_LAUNCH("k_filter_tape", k_filter_tile_value, BYTES, s, net, n, ef, Wn, ft, Ah, wv, s.Zd);
+#undef BYTES
+}
+
+int pn_filter_tile_value_fwd(const DevSys& s, const DevNet<float>& net, int n, const float* ef, int Wn, float* wj,
+                             cudaStream_t st) {
+#define BYTES(LW) ((size_t)s.K * (LW) + (size_t)s.Hw * (LW) + (size_t)s.K * LA + (size_t)(LW) * LA)
+  const double ft_work = 2.0 * Wn * s.Ppair * ((double)s.K * s.Hw + (double)s.Hw * s.Zd);
+  // the forward workspace's layout: value rows of [P][3][Zd] filter jets
+  PN_FT_LAUNCH("k_filter_value", k_filter_tile_value, BYTES, s, net, n, ef, Wn, ft, (float*)nullptr, wj, 3 * s.Zd);
 #undef BYTES
 }
 

@@ -1276,8 +1276,9 @@ int pn_network_layers(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn,
     // 4096 walkers x 10 pairs: 0.154 ms per pass per-row, 0.174 ms tiled)
     int fe = PN_ENOTREADY;
     if constexpr (sizeof(R) == 4)
-      if (jet && (size_t)Wn * s.Ppair >= ((size_t)1 << 17))
-        fe = pn_filter_tile_jet(s, net, n, (const float*)w.efeat, Wn, (float*)w.wjet, st);
+      if ((size_t)Wn * s.Ppair >= ((size_t)1 << 17))
+        fe = jet ? pn_filter_tile_jet(s, net, n, (const float*)w.efeat, Wn, (float*)w.wjet, st)
+                 : pn_filter_tile_value_fwd(s, net, n, (const float*)w.efeat, Wn, (float*)w.wjet, st);
     if (fe != PN_OK && fe != PN_ENOTREADY) return fe;
     // kernel classes: float64 launches (the float64 path, the guard's
     // re-evaluation) and value passes apart from the float32 jet passes
@@ -1423,12 +1424,25 @@ int pn_probe_heads_chunk(const DevSys& s, const DevNet<float>& net, Work<float>&
     // the last maps of both heads: backflow f = H W_k2 (+ b), Jastrow
     // jets J = B W_e2 (+ b); their inputs H and B are still in place.
     // +-2^-19 relative, plus a third of that at the scale of the terms
+    // The terms' scale |x| |W| comes from the tensor-core map in
+    // absolute-value mode into the first head's hidden buffer Zb (free by
+    // now), else from the CUDA-core kernel.
     const NetOff& o = net.off;
     const float er = 1.9073486e-6f, ea = 1.9073486e-6f / 3.f;
-    if (int e = pn_perturb_abs(w.H, w.ldH, net.p + o.kW[2], s.n_orb, w.F, s.n_orb, (size_t)Wn * s.N * T, s.D,
-                               s.n_orb, er, ea, st))
-      return e;
-    if (int e = pn_perturb_abs(w.Bs, s.D, net.p + o.eW[2], 1, w.Jj, 1, (size_t)Wn * T, s.D, 1, er, ea, st)) return e;
+    const size_t zb = (size_t)Wn * s.N * T * w.ldZ;
+    const size_t rf = (size_t)Wn * s.N * T, rj = (size_t)Wn * T;
+    int e = (s.tensor_cores & PN_TC_HEADS)
+                ? pn_perturb_abs_tc(w.H, w.ldH, net.p + o.kW[2], s.n_orb, w.F, s.n_orb, rf, s.D, s.n_orb, er, ea, w.Zb,
+                                    zb, s.dev_err, st)
+                : PN_ENOTREADY;
+    if (e == PN_ENOTREADY)
+      e = pn_perturb_abs(w.H, w.ldH, net.p + o.kW[2], s.n_orb, w.F, s.n_orb, rf, s.D, s.n_orb, er, ea, st);
+    if (e) return e;
+    e = (s.tensor_cores & PN_TC_HEADS)
+            ? pn_perturb_abs_tc(w.Bs, s.D, net.p + o.eW[2], 1, w.Jj, 1, rj, s.D, 1, er, ea, w.Zb, zb, s.dev_err, st)
+            : PN_ENOTREADY;
+    if (e == PN_ENOTREADY) e = pn_perturb_abs(w.Bs, s.D, net.p + o.eW[2], 1, w.Jj, 1, rj, s.D, 1, er, ea, st);
+    if (e) return e;
   } else {
     DevSys s2 = s;
     s2.tensor_cores ^= PN_TC_HEADS;

@@ -113,6 +113,35 @@ int pn_perturb_abs(const float* X, int ldx, const float* W, int ldw, float* Y, i
 }
 
 
+// y += (+-1) (eta_rel |y| + eta_abs S) with S the term scale already formed
+// (by the tensor-core map in absolute-value mode), S rows of stride lds.
+static __global__ void k_perturb_apply(float* __restrict__ Y, int ldy, const float* __restrict__ S, int lds, size_t rows,
+                                int Nout, float eta_rel, float eta_abs) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * Nout) return;
+  const size_t row = idx / Nout;
+  const int n = (int)(idx - row * Nout);
+  uint32_t h = (uint32_t)idx * 0x9E3779B1u;
+  h ^= h >> 15;
+  h *= 0x85EBCA77u;
+  h ^= h >> 13;
+  float* y = Y + row * ldy + n;
+  const float d = fmaf(eta_rel, fabsf(*y), eta_abs * S[row * lds + n]);
+  *y += (h & 1u) ? d : -d;
+}
+
+int pn_perturb_abs_tc(const float* X, int ldx, const float* W, int ldw, float* Y, int ldy, size_t rows, int Kd,
+                      int Nout, float eta_rel, float eta_abs, float* scratch, size_t scratch_floats, int* err,
+                      cudaStream_t st) {
+  if (rows == 0) return PN_OK;
+  if (rows * (size_t)Nout > scratch_floats || rows > (size_t)INT32_MAX) return PN_ENOTREADY;
+  const int e = pn_linear_tc(X, ldx, W, ldw, nullptr, scratch, Nout, (int)rows, Kd, Nout, 1, 0, err, st, 1);
+  if (e) return e;
+  PN_LAUNCH("k_perturb", st, k_perturb_apply<<<nblk(rows * Nout, 256), 256, 0, st>>>(Y, ldy, scratch, Nout, rows, Nout,
+                                                                                     eta_rel, eta_abs));
+  return PN_OK;
+}
+
 int pn_perturb_rel(float* A, size_t n, float eta, cudaStream_t st) {
   if (n == 0) return PN_OK;
   PN_LAUNCH("k_perturb", st, k_perturb<<<nblk(n, 256), 256, 0, st>>>(A, n, eta));

@@ -74,6 +74,9 @@ int pn_launch_sum_electrons(const R* X, R* Xs, int Wn, int N, int D, cudaStream_
 // (dd += ...).  PN_ENOTREADY when a tile does not fit in shared memory.
 int pn_filter_tile_value(const DevSys& s, const DevNet<float>& net, int n, const float* ef, int Wn, float* Ah,
                          float* wv, cudaStream_t st);
+// the forward value pass: w into the jet layout's value rows ([P][3][Zd]), no Ah
+int pn_filter_tile_value_fwd(const DevSys& s, const DevNet<float>& net, int n, const float* ef, int Wn, float* wj,
+                             cudaStream_t st);
 int pn_filter_tile_jet(const DevSys& s, const DevNet<float>& net, int n, const float* ef, int Wn, float* wj,
                        cudaStream_t st);
 int pn_filter_tile_bwd(const DevSys& s, const DevNet<float>& net, int n, const float* Ah, const float* dw, int Wn,

@@ -336,7 +336,8 @@ DevNet<R> pn_devnet(pn_system_s* sys);
 // Tensor-core linear layer (tc_gemm.cu).
 bool pn_tc_supported(int Nout);
 int pn_linear_tc(const float* X, int ldx, const float* W, int ldw, const float* b, float* Y, int ldy, int rows, int K,
-                 int Nout, int T, int acc, int* err, cudaStream_t st);
+                 int Nout, int T, int acc, int* err, cudaStream_t st,
+                 int absval = 0);
 
 
 // Chunked drivers over an explicit workspace (used by the C ABI with the
@@ -355,6 +356,12 @@ int pn_run_eval(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, cons
 int pn_perturb_rel(float* A, size_t n, float eta, cudaStream_t st);
 int pn_perturb_abs(const float* X, int ldx, const float* W, int ldw, float* Y, int ldy, size_t rows, int Kd, int Nout,
                    float eta_rel, float eta_abs, cudaStream_t st);
+// The same with the term scale formed by the tensor-core map in
+// absolute-value mode into scratch (rows x Nout floats); PN_ENOTREADY when
+// scratch is too small or the map does not fit.
+int pn_perturb_abs_tc(const float* X, int ldx, const float* W, int ldw, float* Y, int ldy, size_t rows, int Kd,
+                      int Nout, float eta_rel, float eta_abs, float* scratch, size_t scratch_floats, int* err,
+                      cudaStream_t st);
 int pn_probe_heads_chunk(const DevSys& s, const DevNet<float>& net, Work<float>& w, int Wn, double* e_probe,
                          cudaStream_t st);
 template <typename R>

@@ -115,14 +115,15 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* ab
 }
 
 // Y (=|+=) X W + b on value rows; see the file comment.  VX: X rows are
-// 16-byte aligned (float4 loads).
+// 16-byte aligned (float4 loads).  absval: |X| |W| instead (the scale of the
+// product's terms, for the local-energy guard's probe).
 template <bool VX>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __restrict__ X, int ldx,
                                                               const float* __restrict__ Wt, int ldw,
                                                               const float* __restrict__ bias, float* __restrict__ Y,
                                                               int ldy, int rows, int K, int Kp, int Nout, int Npad,
                                                               int T, int accumulate, int nstage, uint32_t tmem_cols,
-                                                              int vy, int nbuf, int* __restrict__ err) {
+                                                              int vy, int nbuf, int* __restrict__ err, int absval) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[2 * 8 + 4 + 1];  // full[8], empty[8], acc_full[2], acc_empty[2], drain
   __shared__ uint32_t tmem_base;
@@ -158,7 +159,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
   // the weight's three pieces, once per CTA: B is [Npad][Kp] K-major
   for (int idx = tid; idx < Npad * Kp; idx += TC_THREADS) {
     const int n = idx / Kp, k = idx - n * Kp;
-    const float b = (n < Nout && k < K) ? Wt[(size_t)k * ldw + n] : 0.0f;
+    float b = (n < Nout && k < K) ? Wt[(size_t)k * ldw + n] : 0.0f;
+    if (absval) b = fabsf(b);
     unsigned short p0, p1, p2;
     split3(b, p0, p1, p2);
     const uint32_t off = tile_off(n, k, sbo_b);
@@ -221,7 +223,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
         const int row = ((idx >> 5) << 3) | (idx & 7), gk = ((idx >> 3) & 3) * 8;
         uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) split3x2(cur[8 * j + 2 * e], cur[8 * j + 2 * e + 1], w0[e], w1[e], w2[e]);
+        for (int e = 0; e < 4; ++e) {
+          const float x0 = cur[8 * j + 2 * e], x1 = cur[8 * j + 2 * e + 1];
+          split3x2(absval ? fabsf(x0) : x0, absval ? fabsf(x1) : x1, w0[e], w1[e], w2[e]);
+        }
         const uint32_t off = tile_off(row, gk, TC_SBO_A);
         *(uint4*)(st + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
         *(uint4*)(st + TC_M * TC_KC * 2 + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
@@ -391,7 +396,7 @@ size_t tc_plan(int K, int Nout, int* Kp_out, int* nstage_out) {
 bool pn_tc_supported(int Nout) { return Nout >= 1 && Nout <= 256; }
 
 int pn_linear_tc(const float* X, int ldx, const float* W, int ldw, const float* b, float* Y, int ldy, int rows, int K,
-                 int Nout, int T, int acc, int* err, cudaStream_t st) {
+                 int Nout, int T, int acc, int* err, cudaStream_t st, int absval) {
   if (rows <= 0) return PN_OK;
   if (!pn_tc_supported(Nout)) { pn_set_error("tensor-core linear: Nout %d outside 1..256", Nout); return PN_EINVAL; }
   int Kp = 0, ns = 0;
@@ -413,12 +418,12 @@ int pn_linear_tc(const float* X, int ldx, const float* W, int ldw, const float* 
     PN_CUDA(pn_allow_max_smem(k_linear_tc<true>));
     PN_LAUNCH_WB("k_linear_tc", st, 2.0 * rows * K * Nout, 4.0 * rows * (K + Nout * (acc ? 2 : 1)),
                 (k_linear_tc<true><<<grid, TC_THREADS, smem, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, K, Kp, Nout, Npad, T,
-                                                                   acc, ns, cols, vy, nbuf, err)));
+                                                                   acc, ns, cols, vy, nbuf, err, absval)));
   } else {
     PN_CUDA(pn_allow_max_smem(k_linear_tc<false>));
     PN_LAUNCH_WB("k_linear_tc", st, 2.0 * rows * K * Nout, 4.0 * rows * (K + Nout * (acc ? 2 : 1)),
                 (k_linear_tc<false><<<grid, TC_THREADS, smem, st>>>(X, ldx, W, ldw, b, Y, ldy, rows, K, Kp, Nout, Npad,
-                                                                    T, acc, ns, cols, vy, nbuf, err)));
+                                                                    T, acc, ns, cols, vy, nbuf, err, absval)));
   }
   return PN_OK;
 }
