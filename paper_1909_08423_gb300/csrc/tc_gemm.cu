@@ -250,8 +250,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
       const uint32_t idesc = bf16_idesc(TC_M, Npad);
       const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
       // (A piece, B piece) pairs whose weight reaches 2^-16, smallest first
-      const int pa[6] = {1, 2, 0, 1, 0, 0};
-      const int pb[6] = {1, 0, 2, 0, 1, 0};
+      constexpr int pa[6] = {1, 2, 0, 1, 0, 0};
+      constexpr int pb[6] = {1, 0, 2, 0, 1, 0};
+      // Descriptors: the start-address field holds the byte address >> 4 in
+      // its low 14 bits and shared memory ends below 2^18 bytes, so the
+      // descriptor of base + offset is the base's plus offset >> 4 (no
+      // carry).  Base descriptors once, the per-MMA offsets from constants.
+      const uint64_t da0 = smem_desc(a_base, TC_SBO_A), db0 = smem_desc(b_base, sbo_b);
+      uint32_t ob[TC_KC / 16][6];
+#pragma unroll
+      for (int ks = 0; ks < TC_KC / 16; ++ks)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) ob[ks][q] = (uint32_t)(pb[q] * b_piece + ks * 2u * TC_LBO) >> 4;
       int g = 0, it = 0;
       bool issued = false;
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -267,13 +277,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
           const int s = g % nstage;
           if (!mbar_wait(full0 + 8 * s, (g / nstage) & 1, abort)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t a_st = a_base + (uint32_t)s * TC_STAGE;
+          const uint64_t da_s = da0 + (((uint32_t)s * TC_STAGE) >> 4);
+          const uint64_t db_k = db0 + (((uint32_t)kc * (TC_KC / 16) * 2u * TC_LBO) >> 4);
+#pragma unroll
           for (int ks = 0; ks < TC_KC / 16; ++ks) {
-            const uint32_t a_step = (uint32_t)ks * 2u * TC_LBO;
-            const uint32_t b_step = (uint32_t)(kc * (TC_KC / 16) + ks) * 2u * TC_LBO;
+#pragma unroll
             for (int q = 0; q < 6; ++q) {
-              const uint64_t da = smem_desc(a_st + pa[q] * (TC_M * TC_KC * 2) + a_step, TC_SBO_A);
-              const uint64_t db = smem_desc(b_base + pb[q] * b_piece + b_step, sbo_b);
+              const uint64_t da = da_s + ((uint32_t)(pa[q] * (TC_M * TC_KC * 2) + ks * 2 * TC_LBO) >> 4);
+              const uint64_t db = db_k + ob[ks][q];
               const bool big = q == 5;  // (a0, b0)
               const uint32_t acc_in = (kc == 0 && ks == 0 && (q == 0 || big)) ? 0u : 1u;
               const uint32_t d = big ? dt + (uint32_t)Npad : dt;
