@@ -190,7 +190,9 @@ __global__ void k_guard_gather(const double* __restrict__ r, const int* __restri
   out[q] = r[(size_t)list[k0 + k] * 3 * N + m];
 }
 
-// Float64 results of the flagged walkers back into the chunk's outputs.
+// Float64 results of the flagged walkers back into the outputs (the
+// chunk's workspace, or the caller's arrays at global indices; null
+// destinations are skipped).
 __global__ void k_guard_scatter(const int* __restrict__ list, int k0, int n, int N, const double* __restrict__ e64,
                                 const double* __restrict__ l64, const double* __restrict__ s64,
                                 const int* __restrict__ st64, const double* __restrict__ g64, double* __restrict__ e,
@@ -199,12 +201,20 @@ __global__ void k_guard_scatter(const int* __restrict__ list, int k0, int n, int
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int w = list[k0 + k];
-  e[w] = e64[k];
-  l[w] = l64[k];
-  sg[w] = s64[k];
-  st[w] = st64[k];
-  for (int m = 0; m < 3 * N; ++m) g[(size_t)w * 3 * N + m] = g64[(size_t)k * 3 * N + m];
+  if (e) e[w] = e64[k];
+  if (l) l[w] = l64[k];
+  if (sg) sg[w] = s64[k];
+  if (st) st[w] = st64[k];
+  if (g)
+    for (int m = 0; m < 3 * N; ++m) g[(size_t)w * 3 * N + m] = g64[(size_t)k * 3 * N + m];
   if (k == 0) atomicAdd((unsigned long long*)n_total, (unsigned long long)n);
+}
+
+// The chunk's flagged walkers (local indices) appended to the pending list
+// as global indices.
+__global__ void k_guard_append(const int* __restrict__ list, int n, int c0, int* __restrict__ pend) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) pend[k] = c0 + list[k];
 }
 
 // Value-pass components for step-by-step checks.
@@ -400,33 +410,40 @@ int metropolis_impl(pn_system_s* s, double* r, double* logabs, int W, int n_step
 }  // namespace
 
 // ------------------------------------------------------ drivers with explicit workspace
-// The guard of a mixed jet chunk (see Guard): second evaluation of the
-// heads, flags, float64 re-evaluation of the flagged walkers in pieces of
-// g.cap.  Reads the flag count back to the host (one synchronisation).
-static int guard_chunk(const DevSys& ds, const DevNet<float>& net, Work<float>& w, const Guard& g, const double* rc,
-                       int Wn, cudaStream_t st) {
-  const int N = ds.N;
+// The guard of a mixed jet chunk (see Guard), first half: the second
+// evaluation and the flags.  Reads the flag count back to the host (one
+// synchronisation) and returns it.
+static int guard_flag_chunk(const DevSys& ds, const DevNet<float>& net, Work<float>& w, const Guard& g, int Wn,
+                            int* nflag, cudaStream_t st) {
   if (int e = pn_probe_heads_chunk(ds, net, w, Wn, g.e_probe, st)) return e;
   PN_CUDA(cudaMemsetAsync(g.count, 0, sizeof(int), st));
   PN_LAUNCH("k_guard_flag", st, k_guard_flag<<<nblk(Wn, 128), 128, 0, st>>>(w.out_eloc, g.e_probe, w.out_status, Wn,
                                                                             g.tau, g.list, g.count));
-  int nflag = 0;
-  PN_CUDA(cudaMemcpyAsync(&nflag, g.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PN_CUDA(cudaMemcpyAsync(nflag, g.count, sizeof(int), cudaMemcpyDeviceToHost, st));
   PN_CUDA(cudaStreamSynchronize(st));
+  return PN_OK;
+}
+
+// Second half: the float64 re-evaluation of the walkers list[0 .. n) (their
+// positions in r) in pieces of g.cap, the results scattered to the given
+// outputs at the same indices (any may be null).  The re-evaluation's
+// linear maps run as float32 pairs (about 44 bits, at float32 issue rates);
+// everything else in float64.
+static int guard_reevaluate(const DevSys& ds, const Guard& g, const int* list, int n_all, const double* r, double* eloc,
+                            double* logabs, double* sign, int* status, double* grad, cudaStream_t st) {
+  const int N = ds.N;
   Work<double> w64 = g.w64;
-  // the re-evaluation's linear maps as float32 pairs (about 44 bits, at
-  // float32 issue rates); everything else in float64
   DevSys d64 = ds;
   d64.lin_f32x2 = 1;
-  for (int k0 = 0; k0 < nflag; k0 += g.cap) {
-    const int n = std::min(g.cap, nflag - k0);
-    PN_LAUNCH("k_guard_gather", st, k_guard_gather<<<nblk((size_t)n * 3 * N, 128), 128, 0, st>>>(rc, g.list, k0, n, N,
+  for (int k0 = 0; k0 < n_all; k0 += g.cap) {
+    const int n = std::min(g.cap, n_all - k0);
+    PN_LAUNCH("k_guard_gather", st, k_guard_gather<<<nblk((size_t)n * 3 * N, 128), 128, 0, st>>>(r, list, k0, n, N,
                                                                                                   w64.r));
     if (int e = pn_forward_chunk<double>(d64, g.net64, w64, w64.r, n, 1, st)) return e;
     PN_LAUNCH("k_guard_scatter", st,
-              k_guard_scatter<<<nblk(n, 64), 64, 0, st>>>(g.list, k0, n, N, w64.out_eloc, w64.out_logabs, w64.out_sign,
-                                                           w64.out_status, w64.out_grad, w.out_eloc, w.out_logabs,
-                                                           w.out_sign, w.out_status, w.out_grad, g.n_total));
+              k_guard_scatter<<<nblk(n, 64), 64, 0, st>>>(list, k0, n, N, w64.out_eloc, w64.out_logabs, w64.out_sign,
+                                                           w64.out_status, w64.out_grad, eloc, logabs, sign, status,
+                                                           grad, g.n_total));
   }
   return PN_OK;
 }
@@ -437,6 +454,14 @@ int pn_run_eval(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, cons
   const int N = ds.N;
   const bool rdev = pn_is_device_ptr(r);
   const bool sync = !rdev || is_host(eloc) || is_host(logabs) || is_host(sign) || is_host(status);
+  const bool guarded = sizeof(R) == 4 && jet && g && g->tau > 0;
+  // With the positions and every output on the device, the guard's flagged
+  // walkers of successive chunks are collected (global indices, up to g.cap)
+  // and re-evaluated together, writing the caller's arrays: larger float64
+  // batches than one chunk's.  Otherwise each chunk's are re-evaluated into
+  // its workspace before its outputs are copied.
+  const bool batch = guarded && !sync;
+  int pending = 0;
   for (int c0 = 0; c0 < W; c0 += Wc) {
     const int Wn = std::min(Wc, W - c0);
     const double* rc = r + (size_t)c0 * N * 3;
@@ -446,13 +471,32 @@ int pn_run_eval(const DevSys& ds, const DevNet<R>& net, Work<R>& w, int Wc, cons
     }
     if (int e = pn_forward_chunk<R>(ds, net, w, rc, Wn, jet, st)) return e;
     if constexpr (sizeof(R) == 4) {
-      if (jet && g && g->tau > 0)
-        if (int e = guard_chunk(ds, net, w, *g, rc, Wn, st)) return e;
+      if (guarded) {
+        int nflag = 0;
+        if (int e = guard_flag_chunk(ds, net, w, *g, Wn, &nflag, st)) return e;
+        if (!batch || nflag > g->cap) {
+          if (int e = guard_reevaluate(ds, *g, g->list, nflag, rc, w.out_eloc, w.out_logabs, w.out_sign, w.out_status,
+                                       w.out_grad, st))
+            return e;
+        } else if (nflag > 0) {
+          if (pending + nflag > g->cap) {
+            if (int e = guard_reevaluate(ds, *g, g->pend, pending, r, eloc, logabs, sign, status, nullptr, st)) return e;
+            pending = 0;
+          }
+          PN_LAUNCH("k_guard_gather", st, k_guard_append<<<nblk(nflag, 128), 128, 0, st>>>(g->list, nflag, c0,
+                                                                                          g->pend + pending));
+          pending += nflag;
+        }
+      }
     }
     if (eloc && jet) PN_CUDA(cudaMemcpyAsync(eloc + c0, w.out_eloc, Wn * 8, cudaMemcpyDefault, st));
     if (logabs) PN_CUDA(cudaMemcpyAsync(logabs + c0, w.out_logabs, Wn * 8, cudaMemcpyDefault, st));
     if (sign) PN_CUDA(cudaMemcpyAsync(sign + c0, w.out_sign, Wn * 8, cudaMemcpyDefault, st));
     if (status) PN_CUDA(cudaMemcpyAsync(status + c0, w.out_status, Wn * 4, cudaMemcpyDefault, st));
+  }
+  if constexpr (sizeof(R) == 4) {
+    if (pending > 0)
+      if (int e = guard_reevaluate(ds, *g, g->pend, pending, r, eloc, logabs, sign, status, nullptr, st)) return e;
   }
   if (sync) PN_CUDA(cudaStreamSynchronize(st));
   return PN_OK;

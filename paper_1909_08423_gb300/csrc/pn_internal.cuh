@@ -277,6 +277,7 @@ struct Guard {
   DevNet<double> net64;  // float64 parameters of the same system
   double* e_probe;       // [Wc] E_loc of the second evaluation
   int* list;             // [Wc] flagged walkers of the chunk
+  int* pend;             // [cap] flagged walkers of earlier chunks of the call, global indices
   int* count;            // [2] device: flagged walkers, walkers re-evaluated so far
   int64_t* n_total;      // [1] device: walkers re-evaluated since the last read
 };

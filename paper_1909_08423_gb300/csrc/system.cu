@@ -267,7 +267,7 @@ template Work<float> pn_carve_work<float>(const DevSys&, int, int, void*);
 // then the per-chunk probe energies, flag list and counters.
 size_t pn_guard_bytes(const DevSys& s, int Wc, int cap) {
   return align_up(pn_work_bytes(s, cap, 3 * s.N + 2, 8)) + align_up((size_t)Wc * 8) + align_up((size_t)Wc * 4) +
-         align_up(2 * sizeof(int)) + align_up(8);
+         align_up((size_t)cap * 4) + align_up(2 * sizeof(int)) + align_up(8);
 }
 
 Guard pn_carve_guard(const DevSys& s, int Wc, int cap, void* base) {
@@ -281,6 +281,8 @@ Guard pn_carve_guard(const DevSys& s, int Wc, int cap, void* base) {
   p += align_up((size_t)Wc * 8);
   g.list = (int*)p;
   p += align_up((size_t)Wc * 4);
+  g.pend = (int*)p;
+  p += align_up((size_t)cap * 4);
   g.count = (int*)p;
   p += align_up(2 * sizeof(int));
   g.n_total = (int64_t*)p;
@@ -831,7 +833,7 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   // mixed handles: the local-energy guard, on by default (jets perturbed at
   // the relative and the term scale, tau = 5e-5 Ha)
   if (d->precision == PN_MIXED) {
-    const int cap = std::min(s->Wc, 256);
+    const int cap = std::min(s->Wc, 1024);
     const size_t gb = pn_guard_bytes(ds, s->Wc, cap);
     if (cudaMalloc(&s->guard_mem, gb) != cudaSuccess) {
       cudaGetLastError();
