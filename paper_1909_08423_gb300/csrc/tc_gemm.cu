@@ -30,9 +30,11 @@ namespace {
 
 constexpr int TC_M = 128;       // rows per tile (UMMA M)
 constexpr int TC_KC = 32;       // k-slice per pipeline stage
-constexpr int TC_NPROD = 8;     // producer warps
+constexpr int TC_NPROD = 16;    // producer warps
 constexpr int TC_NEPI = 4;      // epilogue warps
-constexpr int TC_WMMA = TC_NPROD;                      // warp 4 issues the MMAs
+constexpr int TC_WMMA = TC_NPROD;                      // the warp after the producers issues the MMAs
+constexpr int TC_CELLS = TC_M * TC_KC / 8 / (32 * TC_NPROD);  // (row, 8-wide k group) cells per producer thread
+static_assert(TC_CELLS >= 1 && TC_CELLS * 8 * 32 * TC_NPROD == TC_M * TC_KC, "producers must tile a stage");
 constexpr int TC_THREADS = 32 * (TC_NPROD + 1 + TC_NEPI);
 constexpr uint32_t TC_LBO = 128;                       // bytes between core matrices along K
 constexpr uint32_t TC_SBO_A = TC_KC / 8 * 128;         // bytes between 8-row groups of an A stage
@@ -177,13 +179,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
 
   if (warp < TC_NPROD) {
     // ---------------------------------------------------------- producers
-    // thread p owns two (row, 8-wide k group) cells of every stage; its
+    // thread p owns TC_CELLS (row, 8-wide k group) cells of every stage; its
     // global loads run two stages ahead of the splitting and storing, so
     // that enough bytes are in flight to cover the memory latency.  A warp
     // takes one 8-row group: its lanes 8q..8q+7 store rows 0..7 of k group
     // q, one 128-byte core matrix per quarter-warp (16-byte stores without
     // bank conflicts)
-    const int p = tid;  // 0..255
+    const int p = tid;  // 0 .. 32 TC_NPROD - 1
     const int my_tiles = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int nstages_total = my_tiles * nk;
     auto load = [&](int gg, float* dst) {
@@ -191,8 +193,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
       const int k0 = (gg % nk) * TC_KC;
       const int r0 = tile * TC_M;
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int idx = p + 256 * j;
+      for (int j = 0; j < TC_CELLS; ++j) {
+        const int idx = p + 32 * TC_NPROD * j;
         const int row = ((idx >> 5) << 3) | (idx & 7), gk = ((idx >> 3) & 3) * 8;
         const int gr = r0 + row;
         if (VX && gr < rows && k0 + gk + 8 <= K) {
@@ -218,8 +220,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
       if (!mbar_wait(empty0 + 8 * s, ((g / nstage) & 1) ^ 1, abort)) { alive = false; return; }
       unsigned char* st = sA + (size_t)s * TC_STAGE;
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int idx = p + 256 * j;
+      for (int j = 0; j < TC_CELLS; ++j) {
+        const int idx = p + 32 * TC_NPROD * j;
         const int row = ((idx >> 5) << 3) | (idx & 7), gk = ((idx >> 3) & 3) * 8;
         uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_linear_tc(const float* __rest
       __syncwarp();
       if (lane == 0) mbar_arrive(full0 + 8 * s);
     };
-    float va[16], vb[16], vc[16];
+    float va[8 * TC_CELLS], vb[8 * TC_CELLS], vc[8 * TC_CELLS];
     if (nstages_total > 0) load(0, va);
     if (nstages_total > 1) load(1, vb);
     for (int g = 0; g < nstages_total && alive; g += 3) {
