@@ -529,8 +529,8 @@ def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384
                 sweep=(), guard=True, unguarded_jobs=0):
     """Poisson stream of seeded molecules through the serving loop.  The
     arrival rate is `load` times the mixed server's capacity, measured first
-    by a closed-loop burst of the stream's first jobs (also with one slot, to
-    show what running jobs side by side gains).  The mixed server serves the
+    by a closed-loop burst of 64 jobs spread evenly over the stream (also with
+    one slot, to show what running jobs side by side gains).  The mixed server serves the
     whole stream; the plain FP64 server serves its first fp64_jobs jobs at the
     same arrival rate.  `sweep` lists further loads at which the mixed server
     is measured again (the latency-load curve)."""
@@ -539,15 +539,18 @@ def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384
     stream = synth.serving_stream(n_jobs, seed, rate_per_s=1.0, wmax=wmax)
     kind = lambda j: binding.PN_JOB_SWEEP if j["kind"] == "sweep" else binding.PN_JOB_ELOC
 
-    def burst(systems, n, n_slots):
+    def burst(systems, idx, n_slots):
         srv = binding.Server(budget_gb << 30, n_slots=n_slots, chunk_walkers=chunk)
         t0 = time.perf_counter()
         ids = [srv.submit(systems[k], kind(stream[k]), stream[k]["W"], n_steps=stream[k]["n_steps"], sigma=0.2,
-                          seed=stream[k]["seed"]) for k in range(n)]
+                          seed=stream[k]["seed"]) for k in idx]
         walkers = sum(srv.poll(i, timeout_us=-1).W for i in ids)
         dt = time.perf_counter() - t0
         srv.close()
-        return n / dt, walkers / dt
+        return len(idx) / dt, walkers / dt
+
+    def spread(n_all, n):
+        return [int(k) for k in np.unique(np.linspace(0, n_all - 1, min(n_all, n)).astype(int))]
 
     def open_loop(systems, n, rate):
         srv = binding.Server(budget_gb << 30, n_slots=slots, chunk_walkers=chunk)
@@ -571,14 +574,14 @@ def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384
                 "walker_eloc_per_s": walkers / span, "jobs_per_s": n / span, "arrival_rate_jobs_per_s": rate}
 
     out = {}
-    ncal = min(n_jobs, 48)
+    cal = spread(n_jobs, 64)
     mixed_sys = [binding.System(synth.serving_system(j["seed"]), precision=binding.PN_MIXED, max_walkers=1)
                  for j in stream]
     if not guard:
         for s_ in mixed_sys:
             s_.set_option(binding.PN_OPT_GUARD, 0)
-    cap_jobs, cap_walkers = burst(mixed_sys, ncal, slots)
-    cap1_jobs, cap1_walkers = burst(mixed_sys, ncal, 1)
+    cap_jobs, cap_walkers = burst(mixed_sys, cal, slots)
+    cap1_jobs, cap1_walkers = burst(mixed_sys, cal, 1)
     rate = load * cap_jobs
     out["mixed"] = open_loop(mixed_sys, n_jobs, rate)
     out["mixed"].update(calibrated_capacity_jobs_per_s=cap_jobs, calibrated_walker_eloc_per_s=cap_walkers,
@@ -590,7 +593,7 @@ def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384
         nu = min(unguarded_jobs, n_jobs)
         for s_ in mixed_sys[:nu]:
             s_.set_option(binding.PN_OPT_GUARD, 0)
-        cu, cuw = burst(mixed_sys, ncal, slots)
+        cu, cuw = burst(mixed_sys, spread(nu, 64), slots)
         out["mixed_unguarded"] = open_loop(mixed_sys, nu, rate)
         out["mixed_unguarded"].update(calibrated_capacity_jobs_per_s=cu, calibrated_walker_eloc_per_s=cuw,
                                       note=f"the stream's first {nu} jobs without the local-energy guard, same rate")
@@ -598,19 +601,22 @@ def run_serving(n_jobs, seed=2024, slots=4, chunk=2048, budget_gb=64, wmax=16384
         s_.close()
     if fp64_jobs > 0:
         nf = min(fp64_jobs, n_jobs)
-        f64_sys = [binding.System(synth.serving_system(stream[k]["seed"]), precision=binding.PN_FP64, max_walkers=1)
-                   for k in range(max(nf, ncal))]
-        fcap, fcapw = burst(f64_sys, ncal, slots)
+        fcal = spread(n_jobs, 24)
+        f64_sys = {k: binding.System(synth.serving_system(stream[k]["seed"]), precision=binding.PN_FP64, max_walkers=1)
+                   for k in sorted(set(range(nf)) | set(fcal))}
+        fcap, fcapw = burst(f64_sys, fcal, slots)
         out["fp64"] = open_loop(f64_sys, nf, rate)
         out["fp64"].update(calibrated_capacity_jobs_per_s=fcap, calibrated_walker_eloc_per_s=fcapw)
-        out["fp64"]["note"] = f"the stream's first {nf} jobs at the mixed server's arrival rate"
-        for s_ in f64_sys:
+        out["fp64"]["note"] = (f"the stream's first {nf} jobs at the mixed server's arrival rate; capacity from "
+                               f"a burst of {len(fcal)} jobs spread over the stream")
+        for s_ in f64_sys.values():
             s_.close()
     out["arrival_rate_jobs_per_s"] = rate
     out["jobs"] = n_jobs
     out["stream"] = (f"{n_jobs} Poisson jobs, seeded neutral molecules of 1-6 nuclei, Z 1-10, 2-30 electrons, "
                      f"1-32 determinants, 256-{wmax} walkers log-uniform, E_loc or 10-step sweep 50/50; "
-                     f"{slots} slots, load {load} of the calibrated mixed capacity")
+                     f"{slots} slots, load {load} of the mixed capacity measured on {len(cal)} jobs spread over "
+                     f"the stream")
     return out
 
 

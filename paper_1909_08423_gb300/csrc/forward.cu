@@ -97,6 +97,78 @@ template <typename R>
 __device__ inline R sigm_(R x) { return R(1) / (R(1) + exp(-x)); }
 
 // ------------------------------------------------------------- filters
+// (sh, sl) += (ah + al)(bh + bl) in float32-pair arithmetic: the product's
+// rounding error by an FMA, the sum's by an error-free two-sum (explicit
+// roundings, so that no contraction merges the steps).
+__device__ inline void f32x2_mac(float& sh, float& sl, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  const float pe = fmaf(a.x, b.y, fmaf(a.y, b.x, fmaf(a.x, b.x, -p)));
+  const float t = __fadd_rn(sh, p);
+  const float z = __fsub_rn(t, sh);
+  const float er = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+  sl = __fadd_rn(sl, __fadd_rn(er, pe));
+  sh = t;
+}
+__device__ inline float2 f32x2_split(double x) {
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
+// One pair row of the float64 filter net (the guard's re-evaluation) with
+// its dot products in float32-pair arithmetic on the (hi, lo) weight copy;
+// biases, activations and outputs in float64.  e2 and h2 are the warp's
+// shared rows (3 K and 3 Hw pairs).
+__device__ inline void pn_filter_row_f32x2(const DevSys& s, const DevNet<double>& net, int n, int ch,
+                                           const double* __restrict__ e, int nc, int lane, float2* e2, float2* h2,
+                                           double* __restrict__ o) {
+  const int K = s.K, Hw = s.Hw, Zd = s.Zd;
+  for (int k = lane; k < K; k += 32)
+    for (int c = 0; c < nc; ++c) e2[c * K + k] = f32x2_split(e[c * K + k]);
+  __syncwarp();
+  const float2* W1 = (const float2*)net.p2 + net.off.W1[n][ch];
+  const float2* W2 = (const float2*)net.p2 + net.off.W2[n][ch];
+  const double* b1 = net.p + net.off.b1[n][ch];
+  const double* b2 = net.p + net.off.b2[n][ch];
+  for (int h = lane; h < Hw; h += 32) {
+    const float2 bb = f32x2_split(b1[h]);
+    float a0h = bb.x, a0l = bb.y, a1h = 0.f, a1l = 0.f, a2h = 0.f, a2l = 0.f;
+    for (int k = 0; k < K; ++k) {
+      const float2 wv = W1[k * Hw + h];
+      f32x2_mac(a0h, a0l, e2[k], wv);
+      if (nc == 3) {
+        f32x2_mac(a1h, a1l, e2[K + k], wv);
+        f32x2_mac(a2h, a2l, e2[2 * K + k], wv);
+      }
+    }
+    const double a0 = (double)a0h + (double)a0l;
+    const double sg = sigm_(a0);
+    h2[h] = f32x2_split(ssp_(a0));
+    if (nc == 3) {
+      const double a1 = (double)a1h + (double)a1l, a2 = (double)a2h + (double)a2l;
+      h2[Hw + h] = f32x2_split(sg * a1);
+      h2[2 * Hw + h] = f32x2_split(sg * a2 + sg * (1.0 - sg) * a1 * a1);
+    }
+  }
+  __syncwarp();
+  for (int z = lane; z < Zd; z += 32) {
+    const float2 bb = f32x2_split(b2[z]);
+    float o0h = bb.x, o0l = bb.y, o1h = 0.f, o1l = 0.f, o2h = 0.f, o2l = 0.f;
+    for (int h = 0; h < Hw; ++h) {
+      const float2 wv = W2[h * Zd + z];
+      f32x2_mac(o0h, o0l, h2[h], wv);
+      if (nc == 3) {
+        f32x2_mac(o1h, o1l, h2[Hw + h], wv);
+        f32x2_mac(o2h, o2l, h2[2 * Hw + h], wv);
+      }
+    }
+    o[z] = (double)o0h + (double)o0l;
+    if (nc == 3) {
+      o[Zd + z] = (double)o1h + (double)o1l;
+      o[2 * Zd + z] = (double)o2h + (double)o2l;
+    }
+  }
+}
+
 // w^{(n,c)}(e) = W2 ssp(W1 e + b1) + b2 for every pair, carrying the jet in
 // the scalar distance (value, d/dd, d2/dd2).  One warp per pair row.
 // Channel: same-spin electron pair 0, opposite spin 1, electron-nucleus 2.
@@ -122,6 +194,13 @@ __global__ void __launch_bounds__(FW * 32) k_filter(DevSys s, DevNet<R> net, int
   const int K = s.K, Hw = s.Hw, Zd = s.Zd;
   const int nc = jet ? 3 : 1;
   const R* e = ef + row * 3 * K;
+  if constexpr (sizeof(R) == 8) {
+    if (s.lin_f32x2 && net.p2) {
+      pn_filter_row_f32x2(s, net, n, ch, (const double*)e, nc, lane, (float2*)sh_e[wid], (float2*)sh_h[wid],
+                          (double*)(wj + row * 3 * Zd));
+      return;
+    }
+  }
   for (int k = lane; k < K; k += 32)
     for (int c = 0; c < nc; ++c) sh_e[wid][c * K + k] = e[c * K + k];
   __syncwarp();

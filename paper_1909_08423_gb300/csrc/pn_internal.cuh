@@ -249,6 +249,7 @@ struct TcStages {
 template <typename R>
 struct DevNet {
   const R* p;      // flat parameter vector in R
+  const float* p2; // float64 networks: the same as (hi, lo) float pairs (float32-pair arithmetic); else null
   const R* Gcat;   // [L][3 Zd][D]  same, anti, nuc receiving maps stacked
   const R* Gb;     // [L][D]        sum of the three receiving biases
   const R* Gbx0;   // [D]           first layer's summed bias + x^(0)
@@ -298,6 +299,7 @@ struct pn_system_s {
   std::vector<void*> allocs;
   double* p64;
   float* p32;
+  float* p2_64;  // p64 as (hi, lo) float pairs
   double* Gcat64;
   double* Gb64;
   float* Gcat32;

@@ -301,6 +301,16 @@ static int upload_params(pn_system_s* s, const double* hp_user) {
   if (s->no_backflow) std::fill(masked.begin() + o.kW[2], masked.begin() + o.kb[2] + d.n_orb, 0.0);
   const double* hp = masked.data();
   PN_CUDA(cudaMemcpy(s->p64, hp, o.total * 8, cudaMemcpyHostToDevice));
+  {
+    // hi = the nearest float, lo = the nearest float of the rest
+    std::vector<float> p2(2 * (size_t)o.total);
+    for (int64_t k = 0; k < o.total; ++k) {
+      const float hi = (float)hp[k];
+      p2[2 * k] = hi;
+      p2[2 * k + 1] = (float)(hp[k] - (double)hi);
+    }
+    PN_CUDA(cudaMemcpy(s->p2_64, p2.data(), p2.size() * 4, cudaMemcpyHostToDevice));
+  }
   std::vector<float> p32(hp, hp + o.total);
   PN_CUDA(cudaMemcpy(s->p32, p32.data(), o.total * 4, cudaMemcpyHostToDevice));
   // stacked receiving maps and summed biases per layer
@@ -457,7 +467,7 @@ static size_t wpack_elems(const DevSys& d) {
 template <>
 DevNet<double> pn_devnet<double>(pn_system_s* s) {
   DevNet<double> n;
-  n.p = s->p64; n.Gcat = s->Gcat64; n.Gb = s->Gb64; n.Gbx0 = s->Gbx0_64; n.off = s->off;
+  n.p = s->p64; n.p2 = s->p2_64; n.Gcat = s->Gcat64; n.Gb = s->Gb64; n.Gbx0 = s->Gbx0_64; n.off = s->off;
   n.wpack = s->wpack64; n.stab = s->stab64;
   n.tcpack = nullptr; n.tcst = nullptr; n.tc_n = 0; n.tc_max_bytes = 0;
   return n;
@@ -465,7 +475,7 @@ DevNet<double> pn_devnet<double>(pn_system_s* s) {
 template <>
 DevNet<float> pn_devnet<float>(pn_system_s* s) {
   DevNet<float> n;
-  n.p = s->p32; n.Gcat = s->Gcat32; n.Gb = s->Gb32; n.Gbx0 = s->Gbx0_32; n.off = s->off;
+  n.p = s->p32; n.p2 = nullptr; n.Gcat = s->Gcat32; n.Gb = s->Gb32; n.Gbx0 = s->Gbx0_32; n.off = s->off;
   n.wpack = s->wpack32; n.stab = s->stab32;
   n.tcpack = s->tcpack; n.tcst = s->tcst_dev; n.tc_n = s->tcst.n; n.tc_max_bytes = s->tcst.max_bytes;
   return n;
@@ -780,6 +790,7 @@ extern "C" int pn_init_system(const pn_system_desc* d, pn_system_t* out) {
   }
   s->p64 = dev_upload<double>(s, nullptr, off.total, &err);
   s->p32 = dev_upload<float>(s, nullptr, off.total, &err);
+  s->p2_64 = dev_upload<float>(s, nullptr, 2 * (size_t)off.total, &err);
   size_t gsz = (size_t)std::max(d->L, 1) * 3 * d->Zd * d->D;
   s->Gcat64 = dev_upload<double>(s, nullptr, gsz, &err);
   s->Gb64 = dev_upload<double>(s, nullptr, (size_t)std::max(d->L, 1) * d->D, &err);
