@@ -109,9 +109,24 @@ __device__ inline void f32x2_mac(float& sh, float& sl, float2 a, float2 b) {
   sl = __fadd_rn(sl, __fadd_rn(er, pe));
   sh = t;
 }
+// x = hi + lo to about 48 bits.  For the usual magnitudes by integer work
+// on the bits alone (hi: the sign, exponent and leading 23 stored mantissa
+// bits; lo: the remaining 29 bits, rounded to a float and scaled), since
+// float64 arithmetic issues at 1/64 of the float32 rate on this part; zero,
+// tiny, huge and non-finite values take the float64 route.
 __device__ inline float2 f32x2_split(double x) {
-  const float hi = __double2float_rn(x);
-  return make_float2(hi, __double2float_rn(x - (double)hi));
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hiw = (unsigned)(u >> 32), sign = hiw & 0x80000000u;
+  if ((u << 1) == 0ull) return make_float2(__uint_as_float(sign), 0.f);
+  const int e = (int)((hiw >> 20) & 0x7FFu);
+  if (e < 949 || e > 1150) {
+    const float hi = __double2float_rn(x);
+    return make_float2(hi, __double2float_rn(x - (double)hi));
+  }
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29));
+  const float lo = __uint2float_rn((unsigned)(m & 0x1FFFFFFFull)) * __uint_as_float((unsigned)(e - 948) << 23);
+  return make_float2(hi, __uint_as_float(__float_as_uint(lo) ^ sign));
 }
 
 // One pair row of the float64 filter net (the guard's re-evaluation) with
@@ -304,8 +319,7 @@ __global__ void __launch_bounds__(256) k_linear(const R* __restrict__ X, int ldx
 }
 
 // Float64 Y (+)= X W + b with float32-pair arithmetic: every operand split
-// into hi + lo floats (hi the nearest float, lo the nearest float of the
-// rest), each product formed as ah bh exactly (its rounding error by an
+// into hi + lo floats (f32x2_split), each product formed as ah bh exactly (its rounding error by an
 // FMA) plus ah bl + al bh, and the products summed in a (sum, correction)
 // pair with an error-free two-sum.  That keeps about 44 bits of the
 // float64 result (about 1e-13 of sum |x w|) at float32 issue rates, which
@@ -329,16 +343,14 @@ __global__ void __launch_bounds__(256) k_linear_f32x2(const double* __restrict__
       const int e = threadIdx.x + l * 256;
       const int rr = e >> 4, kk = e & 15;
       const int gr = row0 + rr, gk = k0 + kk;
-      const double a = (gr < rows && gk < Kd) ? X[(size_t)gr * ldx + gk] : 0.0;
-      const float ah = __double2float_rn(a);
-      Ah[kk][rr] = ah;
-      Al[kk][rr] = __double2float_rn(a - (double)ah);
+      const float2 a = f32x2_split((gr < rows && gk < Kd) ? X[(size_t)gr * ldx + gk] : 0.0);
+      Ah[kk][rr] = a.x;
+      Al[kk][rr] = a.y;
       const int kb = e >> 6, cb = e & 63;
       const int gkb = k0 + kb, gc = col0 + cb;
-      const double b = (gkb < Kd && gc < Nout) ? Wt[(size_t)gkb * ldw + gc] : 0.0;
-      const float bh = __double2float_rn(b);
-      Bh[kb][cb] = bh;
-      Bl[kb][cb] = __double2float_rn(b - (double)bh);
+      const float2 b = f32x2_split((gkb < Kd && gc < Nout) ? Wt[(size_t)gkb * ldw + gc] : 0.0);
+      Bh[kb][cb] = b.x;
+      Bl[kb][cb] = b.y;
     }
     __syncthreads();
 #pragma unroll
