@@ -180,6 +180,26 @@ def test_guard_off_leaves_first_evaluation_and_on_replaces_flagged(lib, oracles,
     assert np.all(d <= 1e-7 * (1 + np.abs(E64[changed]))), d.max()
 
 
+def test_guard_batched_and_per_chunk_reevaluation_agree(lib, oracles):
+    """Device buffers let the guard re-evaluate the flagged walkers of all
+    chunks in one batch; host buffers re-evaluate each chunk's before its
+    outputs are copied.  Every walker's float64 re-evaluation is independent
+    of the batch it is in, so both give the same energies bit for bit."""
+    sysd = oracles["h10"].sys
+    W = 3000
+    r = _sampled_mixed(lib, sysd, W, 105)
+    s = lib.System(sysd, precision=lib.PN_MIXED, max_walkers=1024)  # three chunks
+    s.guard_count()
+    Ed = torch.empty(W, dtype=torch.float64, device="cuda")
+    s.eval_local_energy(torch.as_tensor(r, device="cuda"), Ed)
+    nd = s.guard_count()
+    Eh = np.empty(W)
+    s.eval_local_energy(np.ascontiguousarray(r), Eh)
+    nh = s.guard_count()
+    assert nd == nh > 0
+    np.testing.assert_array_equal(Ed.cpu().numpy(), Eh)
+
+
 @pytest.mark.parametrize("name", ["h10", "n2"])
 def test_guard_relative_probe_trades_tail_for_fewer_reevaluations(lib, oracles, name):
     """The cheaper probe (relative perturbation only) at the default tau
