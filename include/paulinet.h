@@ -283,12 +283,16 @@ int pn_langevin_step(pn_system_t sys, double* r, double* logabs, double* drift,
  *   every workspace chunk is evaluated a second time from the same network
  *   output with different rounding (see PN_OPT_GUARD_PROBE) and every walker
  *   whose two energies differ by more than tau, or not finitely, is
- *   evaluated again in float64 -- its linear maps as float32 pairs (about 44
- *   bits; float32 issue rates are 64 times the float64 rate on this part),
- *   everything else in float64 -- and returned with those E_loc, ln|psi|,
- *   sign and status.  Each guarded chunk reads one count back to the host
- *   (the call then synchronises its stream once per chunk).  pn_guard_count
- *   reports how many walkers were re-evaluated.
+ *   evaluated again in float64 -- its linear maps and filter nets as
+ *   float32 pairs (about 44 bits; float32 issue rates are 64 times the
+ *   float64 rate on this part), everything else in float64 -- and returned
+ *   with those E_loc, ln|psi|, sign and status.  Each guarded chunk reads
+ *   one count back to the host (the call then synchronises its stream once
+ *   per chunk).  With positions and outputs in device memory the flagged
+ *   walkers of successive chunks are re-evaluated together (up to 1024 at a
+ *   time); with host buffers, each chunk's before its outputs are copied
+ *   (the same values either way).  pn_guard_count reports how many walkers
+ *   were re-evaluated.
  * PN_OPT_GUARD_PROBE (default 2): the guard's second evaluation.  2: the
  *   first pass's backflow and Jastrow jets perturbed by +-2^-19 relative
  *   plus a third of 2^-19 at the scale of the heads' terms (sum_k |x_k|
