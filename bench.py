@@ -988,8 +988,9 @@ def main():
                "ms_per_step": dt * 1e3}
 
     cfg = {"workload": WORKLOAD_DESC.format(W=W, C=chunk), "walkers_per_gpu": W, "chunk": chunk,
-           "precision": "mixed: float32 network, float64 orbitals/determinants/sums/Coulomb; local-energy guard on "
-                        "(tau 5e-5 Ha)",
+           "precision": "mixed: float32 network (tcgen05 maps on three-piece bf16 operands), float64 "
+                        "orbitals/determinants/sums/Coulomb; local-energy guard on (probe 2, tau 5e-5 Ha: flagged "
+                        "walkers re-evaluated in float64 with float32-pair maps and filters)",
            "l2": "flushed (256 MB write) between timed steps; the per-chunk intermediates (~14 GB) exceed L2",
            "parallelism": (f"walkers sharded x{world}; clipping window all-gathered and gradient all-reduced "
                            "(NCCL) every step" if world > 1 else "1 GPU")}
