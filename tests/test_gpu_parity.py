@@ -180,15 +180,19 @@ def test_guard_off_leaves_first_evaluation_and_on_replaces_flagged(lib, oracles,
     assert np.all(d <= 1e-7 * (1 + np.abs(E64[changed]))), d.max()
 
 
-def test_guard_batched_and_per_chunk_reevaluation_agree(lib, oracles):
+@pytest.mark.parametrize("chunk,tau", [(1024, 50), (64, 20)])
+def test_guard_batched_and_per_chunk_reevaluation_agree(lib, oracles, chunk, tau):
     """Device buffers let the guard re-evaluate the flagged walkers of all
     chunks in one batch; host buffers re-evaluate each chunk's before its
     outputs are copied.  Every walker's float64 re-evaluation is independent
-    of the batch it is in, so both give the same energies bit for bit."""
+    of the batch it is in, so both give the same energies bit for bit.  With
+    64-walker chunks the batch (at most one chunk's worth of walkers) fills up
+    and is re-evaluated in the middle of the call."""
     sysd = oracles["h10"].sys
     W = 3000
     r = _sampled_mixed(lib, sysd, W, 105)
-    s = lib.System(sysd, precision=lib.PN_MIXED, max_walkers=1024)  # three chunks
+    s = lib.System(sysd, precision=lib.PN_MIXED, max_walkers=chunk)
+    s.set_option(lib.PN_OPT_GUARD, tau)
     s.guard_count()
     Ed = torch.empty(W, dtype=torch.float64, device="cuda")
     s.eval_local_energy(torch.as_tensor(r, device="cuda"), Ed)
@@ -197,6 +201,8 @@ def test_guard_batched_and_per_chunk_reevaluation_agree(lib, oracles):
     s.eval_local_energy(np.ascontiguousarray(r), Eh)
     nh = s.guard_count()
     assert nd == nh > 0
+    if chunk == 64:
+        assert nd > chunk  # more flagged walkers than one batch holds
     np.testing.assert_array_equal(Ed.cpu().numpy(), Eh)
 
 
