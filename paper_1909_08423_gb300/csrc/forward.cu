@@ -833,10 +833,56 @@ __global__ void __launch_bounds__(256) k_message_c(DevSys s, const R* __restrict
 // Requires Zd a multiple of 16; HC as in k_message_c.
 constexpr int MSGW_ZT = 16;
 constexpr int MSGW_NMAX = 16;  // electrons of the staged kernel (partner values in registers)
-template <typename R, bool HC>
+// Double-float numbers (hi + lo floats, about 44 bits) for the float64
+// messages of the guard's re-evaluation: float32 issue rates are 64 times
+// the float64 rate on this part.  Products by an FMA-exact hi product plus
+// the cross terms, sums by a two-sum of the high parts; every result
+// renormalised.  Explicit roundings keep contraction out of the steps.
+struct FF {
+  float hi, lo;
+  __device__ FF() {}
+  __device__ FF(int x) : hi((float)x), lo(0.f) {}
+  __device__ FF(float h, float l) : hi(h), lo(l) {}
+};
+__device__ inline FF ff_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return FF(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ inline FF operator+(FF a, FF b) {
+  const float s = __fadd_rn(a.hi, b.hi), z = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, z)), __fsub_rn(b.hi, z));
+  return ff_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ inline FF operator-(FF a) { return FF(-a.hi, -a.lo); }
+__device__ inline FF operator-(FF a, FF b) { return a + (-b); }
+__device__ inline FF operator*(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  return ff_norm(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p))));
+}
+__device__ inline FF& operator+=(FF& a, FF b) { return a = a + b; }
+
+// Conversions between a buffer type R and a compute type C.
+template <typename C>
+__device__ inline C to_c(double x) { return (C)x; }
+template <>
+__device__ inline FF to_c<FF>(double x) {
+  const float2 p = f32x2_split(x);
+  return FF(p.x, p.y);
+}
+template <typename C>
+__device__ inline C to_c(float x) { return (C)x; }
+template <typename R>
+__device__ inline R from_c(R x) { return x; }
+template <typename R>
+__device__ inline R from_c(FF x) { return (R)((double)x.hi + (double)x.lo); }
+
+// C: the arithmetic type (R, or FF for float64 buffers in float32-pair
+// arithmetic); shared-memory rows hold C.
+template <typename R, bool HC, typename C = R>
 __global__ void k_message_w(DevSys s, const R* __restrict__ Y, const double* __restrict__ geo,
                             const R* __restrict__ wj, const R* __restrict__ H, int ldH, int Wn, int T,
                             R* __restrict__ Zb, int ldZ) {
+  static_assert(sizeof(C) == sizeof(R), "shared rows are sized for R");
   extern __shared__ __align__(16) unsigned char mw_smem[];
   const int N = s.N, M = s.M, Zd = s.Zd, P = s.Ppair, lap = T - 1;
   const int ntile = Zd / MSGW_ZT;
@@ -844,13 +890,13 @@ __global__ void k_message_w(DevSys s, const R* __restrict__ Y, const double* __r
   const int lane = threadIdx.x & 31, i = ((threadIdx.x >> 5) << 1) | (lane >> 4);
   const int HT = HC ? 1 : T;  // rows of h staged per electron (one shared row for HC)
   const int HN = HC ? 1 : N;
-  R* hs = (R*)mw_smem;                       // [HN][HT][16]
-  R* ws = hs + (size_t)HN * HT * MSGW_ZT;    // [P][3][16]
-  R* gs = ws + (size_t)P * 3 * MSGW_ZT;      // [P][5]: d, 1/d, unit vector
+  C* hs = (C*)mw_smem;                       // [HN][HT][16]
+  C* ws = hs + (size_t)HN * HT * MSGW_ZT;    // [P][3][16]
+  C* gs = ws + (size_t)P * 3 * MSGW_ZT;      // [P][5]: d, 1/d, unit vector
   const int nth = blockDim.x;
   // rows of 16 columns from global memory (row stride ld) into shared
   // memory, eight loads of a thread in flight before its stores
-  auto stage = [&](R* dst, const R* src, int n, int ld) {
+  auto stage = [&](C* dst, const R* src, int n, int ld) {
     for (int q0 = threadIdx.x; q0 < n; q0 += 8 * nth) {
       R v[8];
 #pragma unroll
@@ -860,11 +906,11 @@ __global__ void k_message_w(DevSys s, const R* __restrict__ Y, const double* __r
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u)
-        if (q0 + u * nth < n) dst[q0 + u * nth] = v[u];
+        if (q0 + u * nth < n) dst[q0 + u * nth] = to_c<C>(v[u]);
     }
   };
   if (HC) {
-    for (int q = threadIdx.x; q < MSGW_ZT; q += nth) hs[q] = H[z0 + q];
+    for (int q = threadIdx.x; q < MSGW_ZT; q += nth) hs[q] = to_c<C>(H[z0 + q]);
   } else {
     stage(hs, H + (size_t)w * N * T * ldH + z0, N * T * MSGW_ZT, ldH);
   }
@@ -872,100 +918,106 @@ __global__ void k_message_w(DevSys s, const R* __restrict__ Y, const double* __r
   const double* gw = geo + (size_t)w * P * 4;
   for (int p = threadIdx.x; p < P; p += nth) {
     const double d = gw[4 * p];
-    gs[5 * p] = (R)d;
-    gs[5 * p + 1] = (R)(1.0 / d);
-    gs[5 * p + 2] = (R)gw[4 * p + 1];
-    gs[5 * p + 3] = (R)gw[4 * p + 2];
-    gs[5 * p + 4] = (R)gw[4 * p + 3];
+    gs[5 * p] = to_c<C>(d);
+    gs[5 * p + 1] = to_c<C>(1.0 / d);
+    gs[5 * p + 2] = to_c<C>(gw[4 * p + 1]);
+    gs[5 * p + 3] = to_c<C>(gw[4 * p + 2]);
+    gs[5 * p + 4] = to_c<C>(gw[4 * p + 3]);
   }
   __syncthreads();
   if (i >= N) return;
   const int z = lane & (MSGW_ZT - 1);
   const bool si = i < s.n_up;
-  auto hrow = [&](int j, int t) -> R { return HC ? (t == 0 ? hs[z] : R(0)) : hs[((size_t)j * T + t) * MSGW_ZT + z]; };
+  auto hrow = [&](int j, int t) -> C { return HC ? (t == 0 ? hs[z] : C(0)) : hs[((size_t)j * T + t) * MSGW_ZT + z]; };
   auto pidx = [&](int j) { return i < j ? pn_pair_index(i, j, N) : pn_pair_index(j, i, N); };
   R* ob = Zb + (size_t)(w * N + i) * T * ldZ + z0 + z;
   // per-thread sums that the tangent rows of electron i itself reuse
-  R s1s[3] = {0, 0, 0}, s1a[3] = {0, 0, 0}, n1[3] = {0, 0, 0};
-  R vs = 0, va = 0, vn = 0, ls = 0, la = 0, ln = 0;
+  C s1s[3] = {C(0), C(0), C(0)}, s1a[3] = {C(0), C(0), C(0)}, n1[3] = {C(0), C(0), C(0)};
+  C vs = C(0), va = C(0), vn = C(0), ls = C(0), la = C(0), ln = C(0);
   for (int j = 0; j < N; ++j) {
     if (j == i) continue;
     const int p = pidx(j);
-    const R sg = i < j ? R(1) : R(-1);  // unit vector from j to i
-    const R* g = gs + 5 * p;
-    const R w0 = ws[(3 * p) * MSGW_ZT + z], w1 = ws[(3 * p + 1) * MSGW_ZT + z], w2 = ws[(3 * p + 2) * MSGW_ZT + z];
-    const R h0 = hrow(j, 0);
+    const C sg = i < j ? C(1) : C(-1);  // unit vector from j to i
+    const C* g = gs + 5 * p;
+    const C w0 = ws[(3 * p) * MSGW_ZT + z], w1 = ws[(3 * p + 1) * MSGW_ZT + z], w2 = ws[(3 * p + 2) * MSGW_ZT + z];
+    const C h0 = hrow(j, 0);
     const bool same = (j < s.n_up) == si;
-    R cross = 0;
+    C cross = C(0);
     if (!HC)
+#pragma unroll
       for (int a = 0; a < 3; ++a) cross += sg * g[2 + a] * (hrow(j, 1 + 3 * i + a) - hrow(j, 1 + 3 * j + a));
-    const R v0 = w0 * h0;
-    const R vl = HC ? (R(2) * w2 + R(4) * w1 * g[1]) * h0
-                    : (R(2) * w2 + R(4) * w1 * g[1]) * h0 + w0 * hrow(j, lap) + R(2) * w1 * cross;
+    const C v0 = w0 * h0;
+    const C vl = HC ? (C(2) * w2 + C(4) * w1 * g[1]) * h0
+                    : (C(2) * w2 + C(4) * w1 * g[1]) * h0 + w0 * hrow(j, lap) + C(2) * w1 * cross;
     if (same) {
       vs += v0;
       ls += vl;
+#pragma unroll
       for (int a = 0; a < 3; ++a) s1s[a] += w1 * sg * g[2 + a] * h0;
     } else {
       va += v0;
       la += vl;
+#pragma unroll
       for (int a = 0; a < 3; ++a) s1a[a] += w1 * sg * g[2 + a] * h0;
     }
   }
   for (int I = 0; I < M; ++I) {
     const int p = s.Pee + i * M + I;
-    const R* g = gs + 5 * p;
-    const R y = Y[I * Zd + z0 + z];
-    const R w0 = ws[(3 * p) * MSGW_ZT + z], w1 = ws[(3 * p + 1) * MSGW_ZT + z], w2 = ws[(3 * p + 2) * MSGW_ZT + z];
+    const C* g = gs + 5 * p;
+    const C y = to_c<C>(Y[I * Zd + z0 + z]);
+    const C w0 = ws[(3 * p) * MSGW_ZT + z], w1 = ws[(3 * p + 1) * MSGW_ZT + z], w2 = ws[(3 * p + 2) * MSGW_ZT + z];
     vn += w0 * y;
-    ln += (w2 + R(2) * w1 * g[1]) * y;
+    ln += (w2 + C(2) * w1 * g[1]) * y;
+#pragma unroll
     for (int a = 0; a < 3; ++a) n1[a] += w1 * g[2 + a] * y;
   }
-  ob[0] = vs;
-  ob[Zd] = va;
-  ob[2 * Zd] = vn;
+  ob[0] = from_c<R>(vs);
+  ob[Zd] = from_c<R>(va);
+  ob[2 * Zd] = from_c<R>(vn);
   R* ol = ob + (size_t)lap * ldZ;
-  ol[0] = ls;
-  ol[Zd] = la;
-  ol[2 * Zd] = ln;
+  ol[0] = from_c<R>(ls);
+  ol[Zd] = from_c<R>(la);
+  ol[2 * Zd] = from_c<R>(ln);
   // tangent rows t = 1 + 3k + a.  The partners' filter values, split by
   // channel (zero for the other channel and for j = i), sit in registers,
   // so a row costs one shared-memory load and two multiply-adds per partner.
-  R w0s[MSGW_NMAX], w0a[MSGW_NMAX];
+  C w0s[MSGW_NMAX], w0a[MSGW_NMAX];
 #pragma unroll
   for (int j = 0; j < MSGW_NMAX; ++j) {
-    w0s[j] = w0a[j] = 0;
+    w0s[j] = w0a[j] = C(0);
     if (!HC && j < N && j != i) {
-      const R w0 = ws[(3 * pidx(j)) * MSGW_ZT + z];
+      const C w0 = ws[(3 * pidx(j)) * MSGW_ZT + z];
       if ((j < s.n_up) == si) w0s[j] = w0; else w0a[j] = w0;
     }
   }
   for (int k = 0; k < N; ++k) {
     // the partner k's own move: d d_ik / d r_ka = -u_ik[a]
-    R pk[3] = {0, 0, 0};
+    C pk[3] = {C(0), C(0), C(0)};
     bool ksame = true;
     if (k != i) {
       const int p = pidx(k);
-      const R sg = i < k ? R(1) : R(-1);
-      const R f = -ws[(3 * p + 1) * MSGW_ZT + z] * sg * hrow(k, 0);
+      const C sg = i < k ? C(1) : C(-1);
+      const C f = -ws[(3 * p + 1) * MSGW_ZT + z] * sg * hrow(k, 0);
+#pragma unroll
       for (int a = 0; a < 3; ++a) pk[a] = f * gs[5 * p + 2 + a];
       ksame = (k < s.n_up) == si;
     }
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int t = 1 + 3 * k + a;
-      R zs = 0, za = 0;
+      C zs = C(0), za = C(0);
       if (!HC) {
-        const R* hcol = hs + (size_t)t * MSGW_ZT + z;
+        const C* hcol = hs + (size_t)t * MSGW_ZT + z;
 #pragma unroll
         for (int j = 0; j < MSGW_NMAX; ++j) {
           if (j < N) {
-            const R h = hcol[(size_t)j * T * MSGW_ZT];
+            const C h = hcol[(size_t)j * T * MSGW_ZT];
             zs += w0s[j] * h;
             za += w0a[j] * h;
           }
         }
       }
-      R zq = 0;
+      C zq = C(0);
       if (k == i) {
         zs += s1s[a];
         za += s1a[a];
@@ -976,9 +1028,9 @@ __global__ void k_message_w(DevSys s, const R* __restrict__ Y, const double* __r
         za += pk[a];
       }
       R* o = ob + (size_t)t * ldZ;
-      o[0] = zs;
-      o[Zd] = za;
-      o[2 * Zd] = zq;
+      o[0] = from_c<R>(zs);
+      o[Zd] = from_c<R>(za);
+      o[2 * Zd] = from_c<R>(zq);
     }
   }
 }
@@ -1389,16 +1441,32 @@ int pn_network_layers(const DevSys& s, const DevNet<R>& net, Work<R>& w, int Wn,
       const bool staged = s.Zd % MSGW_ZT == 0 && s.N <= MSGW_NMAX && mw_bytes <= 160 * 1024 && !s.msg_per_row;
       if (staged) {
         const unsigned grid = (unsigned)((size_t)Wn * (s.Zd / MSGW_ZT));
-        if (hc) {
+        const unsigned blk = (unsigned)((s.N + 1) / 2 * 32);
+        const R* hsrc = hc ? w.Xs : w.H;
+        const int ldh = hc ? 0 : w.ldH;
+        // float64 buffers of the guard's re-evaluation: float32-pair arithmetic
+        bool pair = false;
+        if constexpr (sizeof(R) == 8) pair = s.lin_f32x2 != 0;
+        if (pair) {
+          if constexpr (sizeof(R) == 8) {
+            if (hc) {
+              PN_CUDA(pn_allow_max_smem(k_message_w<double, true, FF>));
+              PN_LAUNCH_W(mname, st, bytes, (k_message_w<double, true, FF><<<grid, blk, mw_bytes, st>>>(
+                                                s, net.p + net.off.Y, w.geo, w.wjet, hsrc, ldh, Wn, T, w.Zb, w.ldZ)));
+            } else {
+              PN_CUDA(pn_allow_max_smem(k_message_w<double, false, FF>));
+              PN_LAUNCH_W(mname, st, bytes, (k_message_w<double, false, FF><<<grid, blk, mw_bytes, st>>>(
+                                                s, net.p + net.off.Y, w.geo, w.wjet, hsrc, ldh, Wn, T, w.Zb, w.ldZ)));
+            }
+          }
+        } else if (hc) {
           PN_CUDA(pn_allow_max_smem(k_message_w<R, true>));
-          PN_LAUNCH_W(mname, st, bytes,
-                      (k_message_w<R, true><<<grid, (s.N + 1) / 2 * 32, mw_bytes, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.Xs,
-                                                                             0, Wn, T, w.Zb, w.ldZ)));
+          PN_LAUNCH_W(mname, st, bytes, (k_message_w<R, true><<<grid, blk, mw_bytes, st>>>(
+                                            s, net.p + net.off.Y, w.geo, w.wjet, hsrc, ldh, Wn, T, w.Zb, w.ldZ)));
         } else {
           PN_CUDA(pn_allow_max_smem(k_message_w<R, false>));
-          PN_LAUNCH_W(mname, st, bytes,
-                      (k_message_w<R, false><<<grid, (s.N + 1) / 2 * 32, mw_bytes, st>>>(s, net.p + net.off.Y, w.geo, w.wjet, w.H,
-                                                                              w.ldH, Wn, T, w.Zb, w.ldZ)));
+          PN_LAUNCH_W(mname, st, bytes, (k_message_w<R, false><<<grid, blk, mw_bytes, st>>>(
+                                            s, net.p + net.off.Y, w.geo, w.wjet, hsrc, ldh, Wn, T, w.Zb, w.ldZ)));
         }
       } else if (hc) {
         PN_LAUNCH_W(mname, st, bytes,
