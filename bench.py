@@ -237,11 +237,11 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_sample(n_per_core=ORACLE_PER_CORE):
+def cpu_baseline_sample(n_per_core=ORACLE_PER_CORE, cores=None):
     """Oracle timing on the host cores for the cpu_baseline key: one VMC step
     of the headline workload on a sample of walkers (n_per_core per core),
     after one untimed step of one walker per core (the workers' set-up)."""
-    pool = OraclePool(WORKLOAD)
+    pool = OraclePool(WORKLOAD, cores)
     pool.step(_oracle_walkers(WORKLOAD, pool.cores), 0, N_METROPOLIS)
     Ws = n_per_core * pool.cores
     r = _oracle_walkers(WORKLOAD, Ws)
@@ -251,8 +251,18 @@ def cpu_baseline_sample(n_per_core=ORACLE_PER_CORE):
     pool.close()
     return {"value": Ws / dt, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
             "sample": f"{Ws} walkers of the N2-shaped workload, one step ({N_METROPOLIS} Metropolis step + E_loc + "
-                      f"clip + grad), {pool.cores} processes of one thread, after one untimed warm-up step",
+                      f"clip + grad), {pool.cores} process{'es' if pool.cores > 1 else ''} of one thread, after one "
+                      "untimed warm-up step",
             "seconds": dt}
+
+
+def cpu_baseline_line(n_per_core=ORACLE_PER_CORE):
+    """The cpu_baseline key: the oracle on all host cores, and the same
+    per-core sample on one core (how far the pool scales over the cores)."""
+    line = cpu_baseline_sample(n_per_core)
+    one = cpu_baseline_sample(n_per_core, cores=1)
+    line["one_core"] = {"value": one["value"], "unit": UNIT, "sample": one["sample"], "seconds": one["seconds"]}
+    return line
 
 
 def run_be_step(W=4096, steps=3, n_metro=100):
@@ -1011,7 +1021,7 @@ def main():
     del mixed
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample()
+        line["cpu_baseline"] = cpu_baseline_line()
     if rank == 0 and not args.no_extras:
         line["be"] = run_be_step()
         line["h10"] = run_h10_step()

@@ -24,3 +24,15 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_reports_all_cores_and_one_core():
+    """The cpu_baseline key carries the oracle's rate on every host core and,
+    for the same per-core sample, on one core."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    d = bench.cpu_baseline_line(n_per_core=1)
+    assert d["kind"] == "oracle" and d["cores"] >= 1 and d["value"] > 0
+    assert d["one_core"]["value"] > 0 and d["one_core"]["unit"] == d["unit"]
+    assert "1 process of one thread" in d["one_core"]["sample"]
