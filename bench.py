@@ -1022,7 +1022,9 @@ def main():
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line()
-    if rank == 0 and not args.no_extras:
+    # the single-GPU extras and the serving stream run in the one-GPU line
+    # only: under torchrun they would hold every rank's GPU for one rank's work
+    if rank == 0 and world == 1 and not args.no_extras:
         line["be"] = run_be_step()
         line["h10"] = run_h10_step()
         be = synth.be()
@@ -1030,7 +1032,7 @@ def main():
         line["line_scan"] = run_line_scan()
         line["vmc_train"] = run_vmc_train(be)
         line["ablation"] = run_ablation(4096)
-    if rank == 0 and args.serve_jobs > 0:
+    if rank == 0 and world == 1 and args.serve_jobs > 0:
         line["serve"] = run_serving(args.serve_jobs, load=args.serve_load, fp64_jobs=args.serve_fp64_jobs,
                                     guard=not args.serve_no_guard, unguarded_jobs=args.serve_unguarded_jobs)
     if rank == 0:
