@@ -30,7 +30,11 @@
 
 namespace {
 
-constexpr int TW = 4;               // warps per block
+// warps per block: two, so that a warp that takes long (the block-by-block
+// path of an ill-conditioned walker) holds only one other warp's shared
+// memory until it ends
+constexpr int TW = 2;
+constexpr int TW_BLOCKS = 10;  // blocks per SM the registers must allow (at most 102 a thread: 20 warps)
 constexpr double kCondMax = 1e3;    // largest 1-norm condition number of A_0 for the table method (jet)
 constexpr double kCondMaxValue = 1e5;  // the same for ln|det| alone
 
@@ -103,7 +107,7 @@ __device__ inline int pn_table_minor_doubles(const int* recs, int nd, int sg) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(TW * 32) k_slater_table(DevSys s, const double* __restrict__ phi,
+__global__ void __launch_bounds__(TW * 32, TW_BLOCKS) k_slater_table(DevSys s, const double* __restrict__ phi,
                                                           const R* __restrict__ F, int Wn, int T, int jet,
                                                           double* __restrict__ det) {
   extern __shared__ __align__(16) double tsm[];
