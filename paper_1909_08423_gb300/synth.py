@@ -365,11 +365,11 @@ def single_gto(Z=1.0, alpha=0.7):
                     [[0]], np.zeros((1, 0)), [1.0])
 
 
-def helium_like_product(Z=2.0, zeta=1.6875):
+def helium_like_product(Z=2.0, zeta=1.6875, use_gamma=0):
     """Two electrons (1 up, 1 down) in exp(-zeta r1) exp(-zeta r2); the
-    electronic cusp factor and the network are off."""
+    network is off, the electronic cusp factor off unless use_gamma."""
     return _special([Z], [[0, 0, 0]], [(0, -1, [zeta], [1.0])], 1, 1, np.ones((1, 1)),
-                    [[0]], [[0]], [1.0], use_gamma=0)
+                    [[0]], [[0]], [1.0], use_gamma=use_gamma)
 
 
 def with_params(sys, params):

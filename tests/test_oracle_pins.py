@@ -65,6 +65,35 @@ def test_helium_like_product_closed_form():
     assert np.max(np.abs(E - (-zeta ** 2 + (zeta - Z) * (1 / r1 + 1 / r2) + 1 / r12))) < 1e-11
 
 
+@pytest.mark.parametrize("Z,zeta", [(2.0, 1.6875), (3.0, 2.4)])
+def test_helium_like_product_with_electronic_cusp_factor_closed_form(Z, zeta):
+    """exp(-zeta (r1 + r2) + u(r12)), 1 up 1 down, with the paper's
+    electronic cusp factor u(r) = -c/(1 + r), c = 1/2 for opposite spins
+    (cusp conditions, Methods).  By hand, with u' = c/(1+r)^2 and
+    u'' = -2c/(1+r)^3 and unit vectors e1, e2, e12 = (r1 - r2)/r12:
+      lap ln psi = -2 zeta/r1 - 2 zeta/r2 + 2 u'' + 4 u'/r12,
+      |grad ln psi|^2 = 2 zeta^2 + 2 u'^2 - 2 zeta u' (e1 - e2) . e12,
+    and E_loc = -(lap + |grad|^2)/2 - Z/r1 - Z/r2 + 1/r12.  A wrong form
+    with the right slope at contact (-c e^-r), a wrong sign of the factor,
+    the same-spin c for this pair or a dropped cross term fails it (forms
+    that differ by a constant, such as c r/(1 + r), give the same E_loc)."""
+    c = 0.5
+    o = Oracle(synth.helium_like_product(Z, zeta, use_gamma=1))
+    r = _pts(64, 2, seed=11)
+    E, _, _ = o.local_energy(r)
+    r1v, r2v = r[:, 0], r[:, 1]
+    r1 = np.linalg.norm(r1v, axis=-1)
+    r2 = np.linalg.norm(r2v, axis=-1)
+    r12 = np.linalg.norm(r1v - r2v, axis=-1)
+    e1, e2, e12 = r1v / r1[:, None], r2v / r2[:, None], (r1v - r2v) / r12[:, None]
+    up = c / (1 + r12) ** 2
+    upp = -2 * c / (1 + r12) ** 3
+    lap = -2 * zeta / r1 - 2 * zeta / r2 + 2 * upp + 4 * up / r12
+    g2 = 2 * zeta ** 2 + 2 * up ** 2 - 2 * zeta * up * ((e1 - e2) * e12).sum(-1)
+    exact = -0.5 * (lap + g2) - Z / r1 - Z / r2 + 1 / r12
+    assert np.max(np.abs(E - exact)) < 1e-11
+
+
 @pytest.mark.parametrize("zeta", [1.0, 1.3])
 def test_nucleus_nucleus_repulsion_closed_form(zeta):
     """exp(-zeta r_A) on nucleus A (Z_A = 1) beside bare nuclei B, C (no
