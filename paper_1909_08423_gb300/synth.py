@@ -372,6 +372,16 @@ def helium_like_product(Z=2.0, zeta=1.6875, use_gamma=0):
                     [[0]], [[0]], [1.0], use_gamma=use_gamma)
 
 
+def two_orbital_product(Z=3.0, zetas=(2.7, 0.9), coefs=(1.3, 0.6), mo=((0.8, 0.3), (0.5, 1.1))):
+    """Two Slater 1s functions d_b exp(-zeta_b r) on one nucleus, two
+    molecular orbitals phi_mu = sum_b mo[b][mu] chi_b, the up electron in
+    orbital 0 and the down electron in orbital 1; the network and the
+    electronic cusp factor are off."""
+    shells = [(0, -1, [zetas[0]], [coefs[0]]), (0, -1, [zetas[1]], [coefs[1]])]
+    return _special([Z], [[0, 0, 0]], shells, 1, 1, np.asarray(mo, dtype=np.float64), [[0]], [[1]], [1.0],
+                    use_gamma=0)
+
+
 def with_params(sys, params):
     out = dict(sys)
     out["params"] = params

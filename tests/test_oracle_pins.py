@@ -94,6 +94,32 @@ def test_helium_like_product_with_electronic_cusp_factor_closed_form(Z, zeta):
     assert np.max(np.abs(E - exact)) < 1e-11
 
 
+def test_two_orbital_product_closed_form():
+    """Up electron in phi_0, down electron in phi_1, phi_mu = sum_b
+    C[b][mu] d_b exp(-zeta_b r) (the molecular orbitals of the ansatz, Eq.
+    (ansatz), with the network off): each electron's kinetic part is
+    sum_b C[b][mu] d_b (-zeta_b^2/2 + zeta_b/r) exp(-zeta_b r) / phi_mu(r), so
+    E_loc = that for electron 1 in phi_0 and electron 2 in phi_1
+            - Z/r1 - Z/r2 + 1/r12.
+    A transposed coefficient matrix or the spins' orbitals swapped fails it."""
+    Z, zetas, coefs = 3.0, (2.7, 0.9), (1.3, 0.6)
+    C = np.array([[0.8, 0.3], [0.5, 1.1]])
+    o = Oracle(synth.two_orbital_product(Z, zetas, coefs, C))
+    r = _pts(64, 2, seed=12)
+    E, _, _ = o.local_energy(r)
+
+    def kinetic_over_phi(d, mu):
+        num = sum(C[b, mu] * coefs[b] * (-zetas[b] ** 2 / 2 + zetas[b] / d) * np.exp(-zetas[b] * d) for b in range(2))
+        den = sum(C[b, mu] * coefs[b] * np.exp(-zetas[b] * d) for b in range(2))
+        return num / den
+
+    r1 = np.linalg.norm(r[:, 0], axis=-1)
+    r2 = np.linalg.norm(r[:, 1], axis=-1)
+    r12 = np.linalg.norm(r[:, 0] - r[:, 1], axis=-1)
+    exact = kinetic_over_phi(r1, 0) + kinetic_over_phi(r2, 1) - Z / r1 - Z / r2 + 1 / r12
+    assert np.max(np.abs(E - exact)) < 1e-10
+
+
 @pytest.mark.parametrize("zeta", [1.0, 1.3])
 def test_nucleus_nucleus_repulsion_closed_form(zeta):
     """exp(-zeta r_A) on nucleus A (Z_A = 1) beside bare nuclei B, C (no
