@@ -52,6 +52,30 @@ def test_single_gaussian_closed_form(Z, alpha):
     assert np.max(np.abs(E - (-0.5 * (4 * alpha ** 2 * d ** 2 - 6 * alpha) - Z / d))) < 1e-10
 
 
+@pytest.mark.parametrize("l,component", [(1, k) for k in range(3)] + [(2, k) for k in range(6)])
+def test_cartesian_gaussian_closed_form(l, component):
+    """x^a y^b z^c exp(-alpha r^2): lap psi / psi = 4 alpha^2 r^2
+    - (6 + 4(a + b + c)) alpha + a(a-1)/x^2 + b(b-1)/y^2 + c(c-1)/z^2
+    (product rule), and ln|psi| = a ln|x| + b ln|y| + c ln|z| - alpha r^2:
+    pins each Cartesian component's powers."""
+    Z, alpha = 2.0, 0.8
+    a, b, c = synth.CART[l][component]
+    o = Oracle(synth.single_cartesian_gto(Z, alpha, l, component))
+    r = _pts(64, 1, seed=13)
+    E, _, _ = o.local_energy(r)
+    x, y, z = r[:, 0, 0], r[:, 0, 1], r[:, 0, 2]
+    d2 = x * x + y * y + z * z
+    ratio = (4 * alpha ** 2 * d2 - (6 + 4 * (a + b + c)) * alpha
+             + a * (a - 1) / x ** 2 + b * (b - 1) / y ** 2 + c * (c - 1) / z ** 2)
+    exact = -0.5 * ratio - Z / np.sqrt(d2)
+    assert np.max(np.abs(E - exact) / (1 + np.abs(exact))) < 1e-10
+    # the value fixes which axis each power belongs to (the p components
+    # share one E_loc formula)
+    lp, _ = o.eval_logpsi(r)
+    ln_chi = a * np.log(np.abs(x)) + b * np.log(np.abs(y)) + c * np.log(np.abs(z)) - alpha * d2
+    assert np.max(np.abs(lp - ln_chi)) < 1e-12
+
+
 def test_helium_like_product_closed_form():
     """exp(-zeta (r1 + r2)), 1 up 1 down, gamma off:
     E_loc = -zeta^2 + (zeta - Z)(1/r1 + 1/r2) + 1/r12."""
