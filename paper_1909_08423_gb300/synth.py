@@ -365,12 +365,14 @@ def single_gto(Z=1.0, alpha=0.7):
                     [[0]], np.zeros((1, 0)), [1.0])
 
 
-def single_cartesian_gto(Z=1.0, alpha=0.7, l=1, component=0):
-    """One electron in one Cartesian component x^a y^b z^c exp(-alpha r^2)
-    of an l-shell (components in the order of CART[l])."""
+def single_cartesian_gto(Z=1.0, alpha=0.7, l=1, component=0, coefs=(1.0,)):
+    """One electron in one Cartesian component x^a y^b z^c sum_k d_k
+    exp(-alpha_k r^2) of an l-shell (components in the order of CART[l]);
+    alpha a number or one exponent per coefficient d_k."""
+    alphas = list(np.broadcast_to(np.asarray(alpha, dtype=np.float64), (len(coefs),)))
     mo = np.zeros((len(CART[l]), 1))
     mo[component, 0] = 1.0
-    return _special([Z], [[0, 0, 0]], [(0, l, [alpha], [1.0])], 1, 0, mo, [[0]], np.zeros((1, 0)), [1.0])
+    return _special([Z], [[0, 0, 0]], [(0, l, alphas, list(coefs))], 1, 0, mo, [[0]], np.zeros((1, 0)), [1.0])
 
 
 def helium_like_product(Z=2.0, zeta=1.6875, use_gamma=0):

@@ -76,6 +76,27 @@ def test_cartesian_gaussian_closed_form(l, component):
     assert np.max(np.abs(lp - ln_chi)) < 1e-12
 
 
+@pytest.mark.parametrize("l,component", [(0, 0), (1, 2), (2, 1)])
+def test_contracted_gaussian_closed_form(l, component):
+    """A contraction of three primitives, x^a y^b z^c sum_k d_k g_k with
+    g_k = exp(-alpha_k r^2): lap psi / psi = sum_k d_k [4 alpha_k^2 r^2
+    - (6 + 4(a + b + c)) alpha_k] g_k / sum_k d_k g_k + a(a-1)/x^2 + ...;
+    a primitive dropped, or one exponent paired with another's
+    coefficient, fails it."""
+    Z, alphas, coefs = 2.0, np.array([3.1, 0.9, 0.25]), np.array([0.3, 0.8, 0.45])
+    a, b, c = synth.CART[l][component]
+    o = Oracle(synth.single_cartesian_gto(Z, alphas, l, component, coefs=tuple(coefs)))
+    r = _pts(64, 1, seed=14)
+    E, _, _ = o.local_energy(r)
+    x, y, z = r[:, 0, 0], r[:, 0, 1], r[:, 0, 2]
+    d2 = x * x + y * y + z * z
+    g = coefs[None, :] * np.exp(-alphas[None, :] * d2[:, None])
+    rad = (g * (4 * alphas[None, :] ** 2 * d2[:, None] - (6 + 4 * (a + b + c)) * alphas[None, :])).sum(1) / g.sum(1)
+    ratio = rad + a * (a - 1) / x ** 2 + b * (b - 1) / y ** 2 + c * (c - 1) / z ** 2
+    exact = -0.5 * ratio - Z / np.sqrt(d2)
+    assert np.max(np.abs(E - exact) / (1 + np.abs(exact))) < 1e-10
+
+
 def test_helium_like_product_closed_form():
     """exp(-zeta (r1 + r2)), 1 up 1 down, gamma off:
     E_loc = -zeta^2 + (zeta - Z)(1/r1 + 1/r2) + 1/r12."""
