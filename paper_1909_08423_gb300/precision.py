@@ -1,11 +1,13 @@
 """Per-system precision policy for the mixed path.
 
-The tensor-core layers (tcgen05, three-piece bf16 operands) keep float32
-operand precision but accumulate more coarsely than CUDA-core float32, and
-how much that matters depends on the molecule (core electrons of heavy
-atoms amplify it).  ``calibrate`` measures the local-energy error of each
-tensor-core layer mask against the PN_FP64 path on walkers sampled from
-|psi|^2 and returns the largest mask that keeps the stated bounds.
+The tensor-core layers (tcgen05, three-piece bf16 operands, the leading
+piece products accumulated apart from the others) are about as accurate as
+CUDA-core float32, but how far the float32 network's rounding reaches the
+local energy depends on the molecule (core electrons of heavy atoms and
+walkers near nodes amplify it).  ``calibrate`` measures the local-energy
+error of each tensor-core layer mask against the PN_FP64 path on walkers
+sampled from |psi|^2 and returns the largest mask that keeps the stated
+bounds.
 """
 
 from __future__ import annotations

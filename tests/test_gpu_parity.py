@@ -236,9 +236,8 @@ def test_guard_relative_probe_trades_tail_for_fewer_reevaluations(lib, oracles, 
 @pytest.mark.parametrize("name,mask", [("be", 7), ("h10", 4)])
 def test_tensor_core_layers_within_bound(lib, oracles, name, mask):
     """The mixed path with linear layers on tcgen05 (three-piece bf16
-    operands) against the same path on CUDA cores, for layer masks that keep
-    the bound on these systems (Be: every group; H10: value passes -- its
-    jet layers sit at the bound, see the precision calibration)."""
+    operands) against the same path on CUDA cores, for the layer masks
+    checked on these systems (Be: every group; H10: the value passes)."""
     sysd = oracles[name].sys
     r = torch.as_tensor(_equilibrated(lib, sysd, 512, 7), device="cuda")
     out = {}
