@@ -433,6 +433,34 @@ def test_cusp_splice_is_smooth_at_rc(make):
     d_in = (inside[0] - inside[1]) / hs
     d_out = (outside[1] - outside[0]) / hs
     np.testing.assert_allclose(d_in, d_out, atol=2e-2 * max(1, np.abs(d_out).max()))
+    # curvature at r_c from either side: the one-sided second derivative of
+    # second order, (2 f0 - 5 f1 + 4 f2 - f3) / h^2 with f_k at r_c -+ k h
+    # (a plain second difference is off by h times the third derivative,
+    # larger than a kink would be)
+    hc = 1e-4
+    fin = [phi(rc - 1e-9 - k * hc) for k in range(4)]
+    fout = [phi(rc + 1e-9 + k * hc) for k in range(4)]
+    c_in = (2 * fin[0] - 5 * fin[1] + 4 * fin[2] - fin[3]) / hc ** 2
+    c_out = (2 * fout[0] - 5 * fout[1] + 4 * fout[2] - fout[3]) / hc ** 2
+    np.testing.assert_allclose(c_in, c_out, atol=1e-3 * max(1, np.abs(c_out).max()))
+
+
+@pytest.mark.parametrize("make", [synth.h2, synth.be, synth.n2])
+def test_cusp_splice_keeps_the_value_at_the_nucleus(make):
+    """With the nucleus value phi0 at its default (the l = 0 part's own value
+    there), the spliced orbitals equal the unspliced ones at the nucleus:
+    p(0) = ln|phi0 - C| puts C + s exp(p(0)) = phi0 in place of that part."""
+    from oracle.ansatz import basis_values
+    S = make()
+    o = Oracle(S)
+    for I in range(len(S["Z"])):
+        at = torch.as_tensor(S["R"][I], dtype=DT).reshape(1, 1, 3)
+        with torch.no_grad():
+            spliced = o.orbitals(at).numpy()[0, 0]
+            plain = (basis_values(S, at) @ o.C).numpy()[0, 0]
+        active = np.asarray(o.cusp[I]["active"], dtype=bool)
+        assert active.any()
+        np.testing.assert_allclose(spliced, plain, rtol=1e-12, atol=1e-14 * np.abs(plain).max())
 
 
 # ----------------------------------------------------------------- sampling
