@@ -751,6 +751,24 @@ def test_clipping_window_and_smoothness():
         assert abs(slope - 1) < 1e-3
 
 
+def test_clipping_hand_worked_even_count():
+    """Six energies (-2, -1, 1, 2, 3, 100), worked by hand from the clipping
+    rule (Methods, ansatz optimization) with the even-count median read as
+    the mean of the two middle values: m = (1 + 2)/2 = 3/2; the deviations
+    7/2, 5/2, 1/2, 1/2, 3/2, 197/2 sum to 107, so d = 107/6 and the window
+    is L = 5 d = 535/6; only 100 lies outside (deviation 197/2 > 535/6) and
+    becomes m + L (1 + ln((197/2)/(535/6))) = 3/2 + (535/6)(1 + ln(591/535)).
+    The loss weights of Eq. (trainig) are 2 (E' - mean E') / 6."""
+    E = np.array([-2.0, -1.0, 1.0, 2.0, 3.0, 100.0])
+    out = oclip.clip_local_energy(E)
+    expect = E.copy()
+    expect[5] = 1.5 + (535.0 / 6.0) * (1.0 + math.log(591.0 / 535.0))
+    np.testing.assert_allclose(out, expect, rtol=1e-15, atol=1e-13)
+    cot = oclip.loss_cotangent(out)
+    np.testing.assert_allclose(cot, 2.0 * (expect - expect.sum() / 6.0) / 6.0, rtol=1e-14, atol=1e-15)
+    assert abs(cot.sum()) < 1e-13
+
+
 # ---------------------------------------------------------------- gradient
 
 @pytest.mark.parametrize("make", [synth.be, synth.h10])
